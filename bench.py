@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the detection path: strain-seconds analysed per second.
+
+Default workload (the full-size configuration): one hour of seeded two-detector
+2048 Hz coloured noise with 200 Newtonian chirps, Welch PSD epochs of 8 s with
+a 64 s look-back, 1 s whitening FIR with a 32 Hz highpass, 1.5 s windows at a
+16 Hz stride (57,600 windows), a ResNet34-style 1D network with GroupNorm(16)
+and seeded weights, 1 s integration and 8 s clustering.  One step = one pass
+of the whole path (PSD, filter build, whitening, windows, network,
+integration, triggers) over that hour, inputs resident in HBM.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload instead.
+Multi-GPU (torchrun): every rank analyses its own independent hour (weak
+scaling, no data-path collective); the barrier and max-over-ranks timing use
+torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import dataclasses
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2403_18661_gb300 import inputs  # noqa: E402
+
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(FALLBACK_PEAKS)
+    d["_source"] = "fallback"
+    return d
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2403_18661_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
+    taken on the current sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("src_hash") != csrc_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = list(csv.reader(io.StringIO(self.tmp.read())))
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle timing
+
+def oracle_sample(wl, x: np.ndarray, w: np.ndarray, n_epochs: int, n_windows: int, seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload and extrapolate to
+    strain-seconds per second: PSD + filter + whitening of n_epochs epochs (both
+    detectors) and the network on n_windows windows."""
+    from oracle import oracle as orc
+    rng = np.random.default_rng(seed)
+    x64 = x.astype(np.float64)
+    eps = sorted(rng.choice(wl.n_epochs, size=min(n_epochs, wl.n_epochs), replace=False).tolist())
+    t0 = time.perf_counter()
+    psd = orc.psd_epochs(x64, wl, eps)
+    white = orc.whiten(x64, wl, psd, eps)
+    t_white = time.perf_counter() - t0
+    # windows that start inside the first sampled epoch's whitened span
+    span = white.shape[1]
+    n_fit = (span - wl.win_len) // wl.stride + 1
+    n_w = min(n_windows, n_fit)
+    t0 = time.perf_counter()
+    orc.infer_windows(wl.net, w, white, wl.win_len, 0, wl.stride, n_w)
+    t_net = time.perf_counter() - t0
+    epoch_s = (wl.epoch_len if wl.epoch_len else wl.n_white) / wl.fs
+    win_per_s = wl.fs / wl.stride
+    sec_per_strain_s = t_white / (len(eps) * epoch_s) + t_net / n_w * win_per_s
+    return {"value": 1.0 / sec_per_strain_s, "unit": "strain-s/s", "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{len(eps)} PSD epochs (Welch + FP64 filter + direct FIR, 2 detectors) and {n_w} "
+                      f"network windows, extrapolated per analysed second ({win_per_s:g} windows/s, "
+                      f"{epoch_s:g} s epochs)",
+            "seconds": t_white + t_net}
+
+
+def workload_by_name(name: str):
+    if name == "hour":
+        return inputs.HOUR_RESNET34
+    if name == "plain64":
+        return inputs.PLAIN_64S
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    wl = workload_by_name(args.workload)
+    x, _ = inputs.make_strain(wl)
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    vals, total = [], 0.0
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(wl, x, w, n_epochs=1, n_windows=args.ref_windows, seed=i)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            total += r["seconds"]
+    value = statistics.mean(vals)
+    out = {"metric": "strain-seconds/s whiten+ResNet", "impl": "reference", "value": value, "unit": "strain-s/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "windows": wl.n_win, "seconds": wl.duration_s},
+           "cpu_baseline": {"value": value, "unit": "strain-s/s", "cores": r["cores"], "kind": "oracle",
+                            "sample": r["sample"]},
+           "e2e": {"value": value, "unit": "strain-s/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_18661_gb300 import abi
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = workload_by_name(args.workload)
+    # each rank analyses its own hour of strain (weak scaling)
+    wl_r = dataclasses.replace(wl, seed=wl.seed + 7919 * rank) if rank else wl
+    x, _ = inputs.make_strain(wl_r)
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    precision = abi.AFG_BF16 if args.precision == "bf16" else abi.AFG_FP32
+    ctx = abi.Context(wl, w, precision=precision)
+    xd = torch.from_numpy(x).to(dev)
+    trig_cap = 65536
+    out = (torch.empty(wl.n_win, dtype=torch.float32, device=dev),
+           torch.empty(wl.n_win - wl.n_int + 1, dtype=torch.float32, device=dev),
+           torch.empty(trig_cap, dtype=torch.int64, device=dev),
+           torch.zeros(1, dtype=torch.int64, device=dev))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.analyze(xd, trig_cap=trig_cap, out=out)
+    barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ctx.profile_enable(True)
+    step_ms = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (outside the step's events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.analyze(xd, trig_cap=trig_cap, out=out)
+        e1.record(stream)
+        step_ms.append((e0, e1))
+    barrier()
+    ctx.profile_enable(False)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in step_ms]
+    total_ms = sum(step_ms)
+    kstats = ctx.profile_read()
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    seconds_per_step = wl.n_win * wl.stride / wl.fs
+    value = world * seconds_per_step * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public host-buffer call: H2D of the strain, D2H of statistic + triggers
+    e2e = None
+    if not args.no_e2e:
+        xp = torch.from_numpy(x).pin_memory()
+        stat_h = torch.empty(wl.n_win - wl.n_int + 1, dtype=torch.float32).pin_memory()
+        trig_h = torch.empty(trig_cap, dtype=torch.int64).pin_memory()
+        ctx.analyze_host(xp, trig_cap=trig_cap, stat_out=stat_h, trig_out=trig_h)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.analyze_host(xp, trig_cap=trig_cap, stat_out=stat_h, trig_out=trig_h)
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * seconds_per_step * args.steps / dt, "unit": "strain-s/s",
+               "h2d_bytes_per_step": int(x.nbytes),
+               "d2h_bytes_per_step": int(stat_h.numel() * 4 + 8 + trig_cap * 8)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = load_peaks()
+    launches = int(sum(k["launches"] for k in kstats))
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    per_launch_ms = dom["total_ms"] / max(dom["timed"], 1)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if dom["name"].startswith("conv_gemm_fp32"):
+        bound, unit = "alu", "TFLOP/s"
+        achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peak_src = f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x {sm_max:g} MHz"
+    elif dom["name"].startswith("conv_gemm_bf16"):
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak_src = f"{peaks['_source']} bf16_tflops_sustained"
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = dom["algo_bytes"] / (dom["total_ms"] / 1000.0) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        peak_src = f"{peaks['_source']} hbm_gbs"
+    traffic = measured_traffic(dom["name"])
+    roofline = {"kernel": dom["name"], "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                "launches": dom["launches"], "ms_per_launch": per_launch_ms,
+                "share_of_step": dom["total_ms"] / max(total_ms, 1e-9)}
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
+                           "share": round(k["total_ms"] / max(sum(q["total_ms"] for q in kstats), 1e-9), 4)}
+               for k in kstats}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_sample(wl, x, w, n_epochs=2, n_windows=args.ref_windows)
+        cpu.pop("seconds", None)
+
+    out = {"metric": "strain-seconds/s whiten+ResNet", "value": value, "unit": "strain-s/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if precision == abi.AFG_FP32 else "bf16", "data": "synthetic",
+           "config": {"workload": wl.name, "windows": wl.n_win, "analysed_s": seconds_per_step,
+                      "net": "resnet34-1d-gn16" if wl.net == inputs.RESNET34_NET else "tiny-1d-gn8",
+                      "precision": args.precision, "l2": "flushed between steps (512 MiB write)"},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+           "clocks": clocks, "kernels": kernels}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="hour", choices=["hour", "plain64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--ref-windows", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,238 @@
+/*
+ * aframe_gb.h -- C ABI of the GB300 (sm_103a) detection path of Aframe
+ * (Marx et al., "A machine-learning pipeline for real-time detection of
+ * gravitational waves from compact binary coalescences", arXiv 2403.18661).
+ *
+ * The path (Sec. II, Sec. IV.B "Noise sampling", Sec. VI "Inference"):
+ *   two-detector strain --Welch PSD--> inverse-ASD whitening filter -->
+ *   FFT-domain whitening with 0.5 s crop --> overlapping 1.5 s windows -->
+ *   1D ResNet with GroupNorm (one logit per window) --> 1 s top-hat
+ *   integration --> maxima over 8 s (triggers).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status: AFG_OK (0) or a negative AFG_ERR_*.
+ *     A failed call leaves its outputs unspecified and records a message
+ *     that afg_last_error() returns until the next call on the same context.
+ *   - Array arguments are DEVICE pointers (CUDA global memory of the
+ *     context's device) owned by the caller, unless the name ends in _host.
+ *     The library never frees caller memory.  It owns only its context:
+ *     weights, twiddle tables and workspaces, released by afg_ctx_destroy.
+ *   - Compute calls are asynchronous on the given stream (a cudaStream_t
+ *     passed as void*; NULL is the legacy default stream) and may be
+ *     captured in a CUDA graph once the context's workspaces have grown to
+ *     the sizes the captured calls need (make one uncaptured call first).
+ *     Calls that return values through host pointers synchronise the stream.
+ *   - Strain arrays are row-major [n_det][n] float32 (H1 = row 0, L1 = row 1),
+ *     sampled at cfg.fs.  Sizes are in samples.
+ *   - A context is not thread-safe: serialise calls that share one.
+ */
+#ifndef AFRAME_GB_H
+#define AFRAME_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define AFG_OK 0
+#define AFG_ERR_ARG (-1)         /* invalid argument (size, pointer, layout) */
+#define AFG_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define AFG_ERR_OOM (-3)         /* device allocation failed */
+#define AFG_ERR_BUDGET (-4)      /* refused: would exceed the context's HBM budget */
+#define AFG_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define AFG_ERR_STATE (-6)       /* call not valid in the current state */
+#define AFG_ERR_NAN (-7)         /* non-finite input detected */
+#define AFG_ERR_UNSUPPORTED (-8) /* configuration this build does not implement */
+
+/* precision of the network's convolutions */
+#define AFG_FP32 0 /* FP32 SIMT implicit-GEMM convolutions ("plain") */
+#define AFG_BF16 1 /* BF16 operands, FP32 accumulation on tcgen05 tensor cores */
+
+typedef struct afg_ctx afg_ctx;
+
+/* 1D ResNet with GroupNorm (Sec. II: ResNet34 with 1D convolutions and GN;
+ * Sec. IX: kernel length 3, global pooling).
+ * stem: conv(in_ch -> widths[0], kernel stem_k, stride stem_stride, padding
+ * stem_k/2) + GN + ReLU, then max-pool(3, stride 2, padding 1) if stem_pool.
+ * n_stages stages; stage s holds blocks[s] BasicBlocks of width widths[s]:
+ * out = ReLU(GN(conv3(ReLU(GN(conv3(x))))) + shortcut(x)); the first block of
+ * stages s > 0 has stride 2 in its first conv and a 1x1 stride-2 conv + GN
+ * shortcut (also used whenever the width changes).  Head: mean over time,
+ * then linear(widths[n_stages-1] -> 1) + bias; the output is the raw logit.
+ * All convolutions are bias-free with zero padding at window edges. */
+typedef struct afg_net {
+    int32_t in_ch;       /* must be 2 (H1, L1) */
+    int32_t stem_k;      /* odd, <= 7 */
+    int32_t stem_stride; /* 1 or 2 */
+    int32_t stem_pool;   /* 0 or 1 */
+    int32_t groups;      /* GroupNorm groups; divides every width */
+    int32_t n_stages;    /* 1..4 */
+    int32_t widths[4];   /* multiples of 16, <= 512 */
+    int32_t blocks[4];   /* >= 1 */
+    float eps;           /* GroupNorm epsilon */
+} afg_net;
+
+typedef struct afg_config {
+    int32_t fs;         /* sample rate (Hz), Sec. IV.A: 2048 */
+    int32_t nfft;       /* Welch segment length; this build: 16384 (8 s) */
+    int32_t hop;        /* Welch hop (50 % overlap: nfft/2); divides nfft */
+    int32_t fir_len;    /* whitening FIR length F (1 s = fs), even, <= 8192 */
+    double f_highpass;  /* whitening highpass (Hz), 32 */
+    int32_t win_len;    /* network window length W (1.5 s = 3072), multiple of 32 */
+    int32_t precision;  /* AFG_FP32 or AFG_BF16 */
+    int64_t hbm_budget; /* bytes the context may hold on the device; 0 = no limit */
+    afg_net net;
+} afg_config;
+
+/* Window-level parameters of one analysis span (see afg_analyze). */
+typedef struct afg_run_params {
+    int64_t n_raw;        /* raw samples per detector in x */
+    int64_t epoch_len;    /* 0: plain mode; else PSD epoch length in samples */
+    int64_t psd_len;      /* epoch mode: PSD look-back span in samples */
+    int64_t stride;       /* window stride S (fs / inference rate) */
+    int64_t n_win;        /* windows to analyse */
+    int64_t shift;        /* L1 timeslide shift in samples (0 = zero lag) */
+    int32_t n_int;        /* integration length in windows (1 s * rate) */
+    int32_t cluster_half; /* trigger half-width in statistic samples (4 s * rate) */
+} afg_run_params;
+
+/* ---------------------------------------------------------------- context */
+
+/* Library version string (static storage). */
+const char *afg_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *afg_status_string(int status);
+
+/* Number of float32 weights the network `net` takes (flat layout below).
+ * Returns AFG_ERR_ARG for an invalid description.
+ * Flat layout, in order: stem.w [C0][in_ch][stem_k], stem.gamma [C0],
+ * stem.beta [C0]; per block c1.w [C][Cin][3], g1.gamma [C], g1.beta [C],
+ * c2.w [C][C][3], g2.gamma, g2.beta, and for a downsampling block
+ * sc.w [C][Cin][1], gsc.gamma, gsc.beta; finally fc.w [C_last], fc.b [1]. */
+int afg_weights_count(const afg_net *net, int64_t *n_out);
+
+/* Create a context on the current CUDA device: validates cfg, copies the
+ * weights (host, n_weights float32 in the flat layout) to the device in the
+ * library's own layouts and builds the FFT twiddle tables.  Synchronous.
+ * *out receives the context (NULL on failure). */
+int afg_ctx_create(const afg_config *cfg, const float *weights_host, int64_t n_weights, afg_ctx **out);
+
+/* Release every device resource of the context.  Waits for its work. */
+int afg_ctx_destroy(afg_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next call. */
+const char *afg_last_error(const afg_ctx *ctx);
+
+/* Device bytes currently held by the context (weights + workspaces + streams). */
+int afg_ctx_bytes(const afg_ctx *ctx, int64_t *bytes);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Welch PSD (Sec. IV.B: the first 8 s of a window estimate the PSD; Sec. VI:
+ * the first 64 s of the stream state).  For detector d and epoch e in
+ * [0, n_psd): one-sided density of x[d][e*psd_step, e*psd_step + psd_span),
+ * averaged (mean) over K = (psd_span - nfft)/hop + 1 segments of nfft
+ * samples every hop samples, each multiplied by the periodic Hann window,
+ * transformed with a real FFT in FP32 and squared and summed in FP64:
+ *   psd[d][e][k] = c_k / (K fs sum w^2) sum_s |X_s(k)|^2, k in [0, nfft/2],
+ *   c_k = 1 for k = 0 and k = nfft/2, else 2.
+ * x: [n_det][n] float32.  psd: [n_det][n_psd][nfft/2+1] float64.
+ * Requirements: psd_span >= nfft, (psd_span - nfft) % hop == 0,
+ * psd_step % hop == 0 (each segment's periodogram is computed once and shared
+ * by the epochs that contain it), (n_psd-1)*psd_step + psd_span <= n.
+ * Errors: AFG_ERR_ARG on a violated requirement. */
+int afg_psd_estimate(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, int64_t n_psd, int64_t psd_step,
+                     int64_t psd_span, double *psd, void *stream);
+
+/* Whitening (Sec. IV.B: whitened in the frequency domain, transformed back,
+ * 0.5 s corrupted at each end removed; Sec. VI).  For each detector d and
+ * output j in [0, out_len):
+ *   y[d][j] = sum_{m=-F/2}^{F/2-1} g^{(e)}_m x[d][out_first + j - m],
+ *   e = (epoch_len > 0) ? min(j / epoch_len, n_psd - 1) : 0,
+ * with the FIR g^{(e)} built in FP64 from psd[d][e] (amplitude psd^{-1/2},
+ * zero below f_highpass, zero-phase inverse DFT on the nfft grid, periodic
+ * Hann taper of length F, scale sqrt(2/fs): unit variance for white input),
+ * applied in FP32 by overlap-save FFT blocks whose circular convolution
+ * equals this linear one on every output.
+ * x: [n_det][n] float32; psd: [n_det][n_psd][nfft/2+1] float64 (device);
+ * y: [n_det][out_len] float32.
+ * Requirements: out_first >= F/2 and out_first + out_len + F/2 - 1 <= n
+ * (the crop), epoch_len % 8192 == 0 when epoch_len > 0. */
+int afg_whiten(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, const double *psd, int64_t n_psd,
+               int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, void *stream);
+
+/* Network over sliding windows (Sec. II: windows shifted by 1/rate; Sec. VI:
+ * the whitened data is unfolded into overlapping windows; Sec. IX: L1
+ * shifted for timeslides).  Window j in [0, n_win) holds
+ *   H1: y[0][first + j*stride + t],  L1: y[1][(first + j*stride + shift + t) mod n_y],
+ * t in [0, W).  Windows are never materialised: the first convolution reads
+ * them from y.  logits[j] = network(window j), float32.
+ * y: [2][n_y] float32 whitened.  logits: [n_win] float32.
+ * Requirements: first >= 0, first + (n_win-1)*stride + W <= n_y, 0 <= shift < n_y. */
+int afg_infer_windows(afg_ctx *ctx, const float *y, int64_t n_y, int64_t first, int64_t stride, int64_t n_win,
+                      int64_t shift, float *logits, void *stream);
+
+/* Integration and clustering (Sec. II: 1 s top-hat, maximum over 8 s).
+ *   stat[j] = (1/n_int) sum_{i<n_int} logits[j+i],  j in [0, n_win - n_int]
+ * (valid mode; stat[j] is stamped at window j + n_int - 1, the newest).
+ * Index j is a trigger iff stat[j] >= stat[i] for all |i-j| <= cluster_half
+ * and stat[j] > stat[i] for i in [j - cluster_half, j) (ties go to the
+ * earliest).  Trigger indices are written to trig_idx in increasing order;
+ * *n_trig (device int64) receives their count, which may exceed trig_cap
+ * (only trig_cap are written).
+ * logits: [n_win] f32; stat: [n_win-n_int+1] f32; trig_idx: [trig_cap] i64. */
+int afg_integrate(afg_ctx *ctx, const float *logits, int64_t n_win, int32_t n_int, int32_t cluster_half,
+                  float *stat, int64_t *trig_idx, int64_t trig_cap, int64_t *n_trig, void *stream);
+
+/* The whole path on one two-detector span, in one call.
+ * Plain mode (p->epoch_len == 0): the PSD of all of x whitens all of x; the
+ * whitened stream starts at raw sample F/2 (crop) and window j starts at
+ * whitened sample j*stride.  Epoch mode: whitened sample j is raw sample
+ * psd_len + j and uses the PSD of raw [e*epoch_len, e*epoch_len + psd_len),
+ * e = j / epoch_len (the look-back immediately before its epoch, Sec. VI);
+ * window j starts at whitened sample j*stride.
+ * x: [2][p->n_raw] float32.  logits: [n_win] f32; stat: [n_win-n_int+1] f32;
+ * trig_idx / n_trig as in afg_integrate.  Workspaces are the context's. */
+int afg_analyze(afg_ctx *ctx, const float *x, const afg_run_params *p, float *logits, float *stat,
+                int64_t *trig_idx, int64_t trig_cap, int64_t *n_trig, void *stream);
+
+/* afg_analyze with HOST buffers: copies x_host (pinned or pageable) to a
+ * context workspace, runs the path, and copies stat and the triggers back.
+ * stat_host: [n_win-n_int+1]; trig_idx_host: [trig_cap]; *n_trig_host is the
+ * trigger count.  Synchronises the stream before returning. */
+int afg_analyze_host(afg_ctx *ctx, const float *x_host, const afg_run_params *p, float *stat_host,
+                     int64_t *trig_idx_host, int64_t trig_cap, int64_t *n_trig_host, void *stream);
+
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Per-kernel accounting of the library's own launches.  `algo_flops` and
+ * `algo_bytes` are the algorithmic work of the recorded launches (the FLOPs
+ * of the operation's definition, the bytes a single pass over its inputs and
+ * outputs moves), summed; `total_ms` sums CUDA-event durations taken on the
+ * stream each kernel was launched on (only while profiling is enabled). */
+typedef struct afg_kernel_stat {
+    char name[48];
+    int64_t launches;   /* launches since the last afg_profile_enable / read */
+    int64_t timed;      /* launches with event timings */
+    double total_ms;
+    double algo_flops;
+    double algo_bytes;
+} afg_kernel_stat;
+
+/* on != 0: reset the counters and record a pair of CUDA events around every
+ * subsequent launch.  on == 0: stop recording (counters keep counting). */
+int afg_profile_enable(afg_ctx *ctx, int32_t on);
+
+/* Synchronise the device, fold the recorded events into per-kernel totals,
+ * write up to cap entries (kernels with at least one launch) to out, set
+ * *n_out, and reset the counters.  Errors: AFG_ERR_ARG for NULL pointers. */
+int afg_profile_read(afg_ctx *ctx, afg_kernel_stat *out, int32_t cap, int32_t *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFRAME_GB_H */

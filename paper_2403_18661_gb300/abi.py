@@ -1,0 +1,261 @@
+"""Thin Python binding of the C ABI in include/aframe_gb.h (argument marshalling only).
+
+Every compute step runs in the CUDA library libaframe_gb.so; this module
+only converts torch tensors to device pointers and sizes, passes the current
+CUDA stream, and turns non-zero status codes into exceptions.  There is no
+fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaframe_gb.so")
+
+AFG_OK = 0
+AFG_FP32 = 0
+AFG_BF16 = 1
+_ERRORS = {-1: "AFG_ERR_ARG", -2: "AFG_ERR_CUDA", -3: "AFG_ERR_OOM", -4: "AFG_ERR_BUDGET",
+           -5: "AFG_ERR_TIMEOUT", -6: "AFG_ERR_STATE", -7: "AFG_ERR_NAN", -8: "AFG_ERR_UNSUPPORTED"}
+
+
+class AfgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_ERRORS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class AfgNet(ctypes.Structure):
+    _fields_ = [("in_ch", ctypes.c_int32), ("stem_k", ctypes.c_int32), ("stem_stride", ctypes.c_int32),
+                ("stem_pool", ctypes.c_int32), ("groups", ctypes.c_int32), ("n_stages", ctypes.c_int32),
+                ("widths", ctypes.c_int32 * 4), ("blocks", ctypes.c_int32 * 4), ("eps", ctypes.c_float)]
+
+
+class AfgConfig(ctypes.Structure):
+    _fields_ = [("fs", ctypes.c_int32), ("nfft", ctypes.c_int32), ("hop", ctypes.c_int32),
+                ("fir_len", ctypes.c_int32), ("f_highpass", ctypes.c_double), ("win_len", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("hbm_budget", ctypes.c_int64), ("net", AfgNet)]
+
+
+class AfgKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("timed", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("algo_flops", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
+
+
+class AfgRunParams(ctypes.Structure):
+    _fields_ = [("n_raw", ctypes.c_int64), ("epoch_len", ctypes.c_int64), ("psd_len", ctypes.c_int64),
+                ("stride", ctypes.c_int64), ("n_win", ctypes.c_int64), ("shift", ctypes.c_int64),
+                ("n_int", ctypes.c_int32), ("cluster_half", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+# every symbol include/aframe_gb.h declares, with its ctypes signature
+SIGNATURES = {
+    "afg_version": ([], ctypes.c_char_p),
+    "afg_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "afg_weights_count": ([ctypes.POINTER(AfgNet), ctypes.POINTER(_i64)], ctypes.c_int),
+    "afg_ctx_create": ([ctypes.POINTER(AfgConfig), _vp, _i64, ctypes.POINTER(_vp)], ctypes.c_int),
+    "afg_ctx_destroy": ([_vp], ctypes.c_int),
+    "afg_last_error": ([_vp], ctypes.c_char_p),
+    "afg_ctx_bytes": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
+    "afg_psd_estimate": ([_vp, _vp, _i64, _i32, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "afg_whiten": ([_vp, _vp, _i64, _i32, _vp, _i64, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "afg_infer_windows": ([_vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "afg_integrate": ([_vp, _vp, _i64, _i32, _i32, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "afg_analyze": ([_vp, _vp, ctypes.POINTER(AfgRunParams), _vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "afg_analyze_host": ([_vp, _vp, ctypes.POINTER(AfgRunParams), _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "afg_profile_enable": ([_vp, _i32], ctypes.c_int),
+    "afg_profile_read": ([_vp, ctypes.POINTER(AfgKernelStat), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
+}
+
+
+def load() -> ctypes.CDLL:
+    """Load libaframe_gb.so (built in-tree by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def version() -> str:
+    return load().afg_version().decode()
+
+
+def make_net(spec) -> AfgNet:
+    """AfgNet from any object with in_ch, stem_k, stem_stride, stem_pool, widths, blocks, groups, eps."""
+    n = AfgNet()
+    n.in_ch, n.stem_k, n.stem_stride, n.stem_pool = spec.in_ch, spec.stem_k, spec.stem_stride, spec.stem_pool
+    n.groups, n.n_stages = spec.groups, len(spec.widths)
+    for i, (w, b) in enumerate(zip(spec.widths, spec.blocks)):
+        n.widths[i], n.blocks[i] = w, b
+    n.eps = spec.eps
+    return n
+
+
+def weights_count(spec) -> int:
+    out = _i64()
+    net = make_net(spec)
+    rc = load().afg_weights_count(ctypes.byref(net), ctypes.byref(out))
+    if rc != AFG_OK:
+        raise AfgError(rc, "invalid network description")
+    return out.value
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One library context (weights, twiddles, workspaces) on the current CUDA device."""
+
+    def __init__(self, workload, weights: np.ndarray, precision: int = AFG_FP32, hbm_budget: int = 0):
+        lib = load()
+        cfg = AfgConfig()
+        cfg.fs, cfg.nfft, cfg.hop, cfg.fir_len = workload.fs, workload.nfft, workload.hop, workload.fir_len
+        cfg.f_highpass, cfg.win_len = workload.f_highpass, workload.win_len
+        cfg.precision, cfg.hbm_budget = precision, hbm_budget
+        cfg.net = make_net(workload.net)
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        h = _vp()
+        rc = lib.afg_ctx_create(ctypes.byref(cfg), w.ctypes.data, len(w), ctypes.byref(h))
+        if rc != AFG_OK:
+            raise AfgError(rc, "afg_ctx_create failed")
+        self._h = h
+        self._lib = lib
+        self.workload = workload
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.afg_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != AFG_OK:
+            raise AfgError(rc, self._lib.afg_last_error(self._h).decode())
+
+    @property
+    def bytes_held(self) -> int:
+        b = _i64()
+        self._check(self._lib.afg_ctx_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    # ---------------------------------------------------------------- profiling
+    def profile_enable(self, on: bool = True):
+        self._check(self._lib.afg_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self) -> list:
+        """Per-kernel launches, CUDA-event time and algorithmic work since the last enable/read."""
+        cap = 64
+        arr = (AfgKernelStat * cap)()
+        n = _i32()
+        self._check(self._lib.afg_profile_read(self._h, arr, cap, ctypes.byref(n)))
+        return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, total_ms=a.total_ms,
+                     algo_flops=a.algo_flops, algo_bytes=a.algo_bytes) for a in arr[:min(n.value, cap)]]
+
+    # ---------------------------------------------------------------- hot path
+    def psd_estimate(self, x, n_psd: int = 1, psd_step: int = 0, psd_span: Optional[int] = None, out=None,
+                     stream=None):
+        import torch
+        n_det, n = x.shape
+        if psd_span is None:
+            psd_span = n
+        if out is None:
+            out = torch.empty((n_det, n_psd, self.workload.nfft // 2 + 1), dtype=torch.float64, device=x.device)
+        self._check(self._lib.afg_psd_estimate(self._h, _ptr(x), n, n_det, n_psd, psd_step, psd_span, _ptr(out),
+                                               _stream(stream)))
+        return out
+
+    def whiten(self, x, psd, out_first: int, out_len: int, epoch_len: int = 0, out=None, stream=None):
+        import torch
+        n_det, n = x.shape
+        if out is None:
+            out = torch.empty((n_det, out_len), dtype=torch.float32, device=x.device)
+        self._check(self._lib.afg_whiten(self._h, _ptr(x), n, n_det, _ptr(psd), psd.shape[1], out_first, out_len,
+                                         epoch_len, _ptr(out), _stream(stream)))
+        return out
+
+    def infer_windows(self, y, first: int, stride: int, n_win: int, shift: int = 0, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(n_win, dtype=torch.float32, device=y.device)
+        self._check(self._lib.afg_infer_windows(self._h, _ptr(y), y.shape[1], first, stride, n_win, shift, _ptr(out),
+                                                _stream(stream)))
+        return out
+
+    def integrate(self, logits, n_int: int, cluster_half: int, trig_cap: int = 4096, stream=None):
+        import torch
+        n_win = logits.shape[0]
+        stat = torch.empty(n_win - n_int + 1, dtype=torch.float32, device=logits.device)
+        trig = torch.empty(max(trig_cap, 1), dtype=torch.int64, device=logits.device)
+        n_trig = torch.zeros(1, dtype=torch.int64, device=logits.device)
+        self._check(self._lib.afg_integrate(self._h, _ptr(logits), n_win, n_int, cluster_half, _ptr(stat),
+                                            _ptr(trig), trig_cap, _ptr(n_trig), _stream(stream)))
+        return stat, trig, n_trig
+
+    def run_params(self, n_raw: int, shift: int = 0) -> AfgRunParams:
+        wl = self.workload
+        p = AfgRunParams()
+        p.n_raw, p.epoch_len, p.psd_len = n_raw, wl.epoch_len, wl.psd_len
+        p.stride, p.n_win, p.shift = wl.stride, wl.n_win, shift
+        p.n_int, p.cluster_half = wl.n_int, wl.cluster_half
+        return p
+
+    def analyze(self, x, shift: int = 0, trig_cap: int = 4096, out=None, stream=None):
+        """Whole path on device tensor x [2][n_raw]: returns (logits, stat, trig_idx, n_trig) device tensors."""
+        import torch
+        wl = self.workload
+        p = self.run_params(x.shape[1], shift)
+        if out is None:
+            out = (torch.empty(wl.n_win, dtype=torch.float32, device=x.device),
+                   torch.empty(wl.n_win - wl.n_int + 1, dtype=torch.float32, device=x.device),
+                   torch.empty(max(trig_cap, 1), dtype=torch.int64, device=x.device),
+                   torch.zeros(1, dtype=torch.int64, device=x.device))
+        logits, stat, trig, n_trig = out
+        self._check(self._lib.afg_analyze(self._h, _ptr(x), ctypes.byref(p), _ptr(logits), _ptr(stat), _ptr(trig),
+                                          trig_cap, _ptr(n_trig), _stream(stream)))
+        return logits, stat, trig, n_trig
+
+    def analyze_host(self, x_host: np.ndarray, shift: int = 0, trig_cap: int = 4096, stat_out=None, trig_out=None,
+                     stream=None) -> Tuple[np.ndarray, np.ndarray]:
+        """Whole path from host strain (numpy or pinned torch CPU tensor) to host statistic and triggers."""
+        wl = self.workload
+        n_raw = x_host.shape[1]
+        p = self.run_params(n_raw, shift)
+        stat = stat_out if stat_out is not None else np.empty(wl.n_win - wl.n_int + 1, dtype=np.float32)
+        trig = trig_out if trig_out is not None else np.empty(max(trig_cap, 1), dtype=np.int64)
+        n_trig = np.zeros(1, dtype=np.int64)
+        xp = x_host.data_ptr() if hasattr(x_host, "data_ptr") else x_host.ctypes.data
+        sp = stat.data_ptr() if hasattr(stat, "data_ptr") else stat.ctypes.data
+        tp = trig.data_ptr() if hasattr(trig, "data_ptr") else trig.ctypes.data
+        self._check(self._lib.afg_analyze_host(self._h, xp, ctypes.byref(p), sp, tp, trig_cap, n_trig.ctypes.data,
+                                               _stream(stream)))
+        return stat, trig[:min(int(n_trig[0]), trig_cap)]

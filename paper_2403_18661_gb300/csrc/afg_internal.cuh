@@ -1,0 +1,172 @@
+// Internal declarations of the GB300 detection-path library (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/aframe_gb.h"
+
+// ----------------------------------------------------------------------------
+// Fixed transform geometry.  Welch segments and whitening blocks both use a
+// real FFT of NFFT = 16384 samples, computed as a complex FFT of NC = 8192
+// points in shared memory plus the even/odd split.  A whitening block
+// produces WB = 8192 outputs, so PSD epochs that are multiples of 8192
+// samples never straddle a block.
+// ----------------------------------------------------------------------------
+constexpr int NFFT = 16384;
+constexpr int NC = NFFT / 2;
+constexpr int NBIN = NFFT / 2 + 1;
+constexpr int WB = 8192;
+
+// ----------------------------------------------------------------------------
+// Network plan: one entry per convolution, in execution order.
+// ----------------------------------------------------------------------------
+struct ConvLayer {
+    int cin, cout, k, stride, pad;
+    int lin, lout;            // input / output positions per window
+    float *wt;                // [k*cin][cout] (row = tap-major then input channel)
+    float *gamma, *beta;      // GroupNorm affine [cout]
+    __nv_bfloat16_raw *wt_bf16;  // bf16 copy for the tensor-core path, [cout][k*cin] (K-major)
+};
+
+struct BlockPlan {
+    int c1, c2, sc;  // indices into convs (sc = -1 for identity shortcut)
+};
+
+struct NetPlan {
+    afg_net net;
+    std::vector<ConvLayer> convs;  // convs[0] is the stem
+    std::vector<BlockPlan> blocks;
+    int l_stem_out;                // positions after the stem conv
+    int l_after_stem;              // after the optional max-pool
+    float *fc_w, *fc_b;
+    int c_last, l_last;
+    int64_t max_act_per_window;    // floats of the largest padded activation of one window
+};
+
+struct Workspace {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// ----------------------------------------------------------------------------
+// Launch accounting (afg_profile_*): every library launch goes through a
+// KScope, which counts it and, while profiling is on, brackets it with two
+// events on its stream.
+// ----------------------------------------------------------------------------
+enum KernelKind {
+    KK_TWIDDLES = 0,
+    KK_PERIODOGRAM,
+    KK_PSD_MEAN,
+    KK_FILTER,
+    KK_WHITEN,
+    KK_STEM,
+    KK_GROUPNORM,
+    KK_CONV_FP32,
+    KK_HEAD,
+    KK_INTEGRATE,
+    KK_TRIGGERS,
+    KK_CONV_TC,
+    KK_COUNT
+};
+extern const char *const kKernelNames[KK_COUNT];
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t e0, e1;
+};
+
+struct Prof {
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    int64_t launches[KK_COUNT] = {};
+    double flops[KK_COUNT] = {};
+    double bytes[KK_COUNT] = {};
+};
+
+struct afg_ctx {
+    Prof prof;
+    afg_config cfg;
+    int device = 0;
+    std::string err;
+    NetPlan plan;
+    float *d_params = nullptr;        // all network parameters (device)
+    size_t d_params_bytes = 0;
+    float2 *tw32 = nullptr;           // exp(-2 pi i k / NFFT), k < NFFT, float
+    double2 *tw64 = nullptr;          // same in double
+    int64_t bytes_held = 0;
+    Workspace ws[16];
+};
+
+// workspace slots
+enum {
+    WS_PERIODOGRAM = 0,
+    WS_FILTER,
+    WS_PSD,
+    WS_WHITE,
+    WS_ACT0,
+    WS_ACT1,
+    WS_ACT2,
+    WS_ACT3,
+    WS_GNSTAT,
+    WS_LOGITS,
+    WS_STAT,
+    WS_X,
+    WS_TRIG,
+    WS_SCAN,
+};
+
+struct KScope {
+    afg_ctx *ctx;
+    cudaStream_t st;
+    int kind;
+    cudaEvent_t e0 = nullptr;
+    KScope(afg_ctx *c, cudaStream_t s, int k, double flops, double bytes);
+    ~KScope();
+};
+
+// ----------------------------------------------------------------------------
+// Error plumbing
+// ----------------------------------------------------------------------------
+int afg_fail(afg_ctx *ctx, int code, const char *fmt, ...);
+int afg_cuda_fail(afg_ctx *ctx, cudaError_t e, const char *what);
+int afg_ws_reserve(afg_ctx *ctx, int slot, size_t bytes, void **out);
+
+#define AFG_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return afg_cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+#define AFG_LAUNCH_CHECK(ctx, what)                                   \
+    do {                                                              \
+        cudaError_t e_ = cudaGetLastError();                          \
+        if (e_ != cudaSuccess) return afg_cuda_fail(ctx, e_, what);   \
+    } while (0)
+
+// ----------------------------------------------------------------------------
+// Host-side launchers implemented in the .cu files
+// ----------------------------------------------------------------------------
+// spectral.cu
+int afg_make_twiddles(afg_ctx *ctx);
+int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step,
+               int64_t psd_span, double *psd, cudaStream_t st);
+int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const double *psd, int64_t n_psd,
+                  int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, int64_t y_stride,
+                  cudaStream_t st);
+// net_fp32.cu
+int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights);
+int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
+                      int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
+// net_tc.cu
+int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
+                      int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
+// integrate.cu
+int launch_integrate(afg_ctx *ctx, const float *logits, int64_t n_win, int n_int, int cluster_half,
+                     float *stat, int64_t *trig_idx, int64_t trig_cap, int64_t *n_trig, cudaStream_t st);

@@ -1,0 +1,445 @@
+// 1D ResNet with GroupNorm over sliding windows, FP32 SIMT path
+// (Sec. II: ResNet34 with 1D convolutions and GroupNorm, scalar output;
+// Sec. IX: kernel length 3 and global pooling).
+//
+// Activation layout: per window, channels-last with one zero row before and
+// after the data ([L + 2][C]), windows packed back to back.  With this layout
+// the K = k*Cin operand row of output position t (taps r = 0..k-1, channels
+// ci) is the contiguous run of k*Cin floats starting at padded row
+// t*stride + (1 - pad), so every convolution is a GEMM whose A operand is a
+// strided view of the activation buffer (implicit GEMM, no im2col copy).
+//
+// Per conv: k_conv_fp32 (tiled SIMT GEMM) writes the raw output; then
+// k_groupnorm computes the group statistics of each window (two passes,
+// one warp per group), and applies the affine map, the optional residual and
+// ReLU in place (or max-pools into another buffer for the stem).
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "afg_internal.cuh"
+
+namespace {
+
+inline int conv_len(int L, int k, int s, int p) { return (L + 2 * p - k) / s + 1; }
+
+// ---------------------------------------------------------------- stem
+// grid (n_win); reads the window straight from the whitened stream.
+// out: [n_win][L0 + 2][C0], raw conv output (GroupNorm follows).
+__global__ void k_stem(const float *__restrict__ y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
+                       int64_t shift, int64_t w0, const float *__restrict__ w, int C0, int k, int s, int W, int L0,
+                       float *__restrict__ out) {
+    extern __shared__ float xs[];  // [2][W + 2*pad]
+    const int pad = k / 2;
+    const int Wp = W + 2 * pad;
+    const int64_t win = w0 + blockIdx.x;
+    const int64_t start = first + win * stride;
+    const float *y0 = y, *y1 = y + y_stride;
+    for (int t = threadIdx.x; t < Wp; t += blockDim.x) {
+        int tt = t - pad;
+        float a = 0.f, b = 0.f;
+        if (tt >= 0 && tt < W) {
+            a = y0[start + tt];
+            int64_t i1 = start + shift + tt;
+            if (i1 >= n_y) i1 -= n_y;
+            b = y1[i1];
+        }
+        xs[t] = a;
+        xs[Wp + t] = b;
+    }
+    __syncthreads();
+    float *o = out + (int64_t)blockIdx.x * (L0 + 2) * C0;
+    for (int idx = threadIdx.x; idx < (L0 + 2) * C0; idx += blockDim.x) {
+        int row = idx / C0, co = idx - row * C0;
+        float acc = 0.f;
+        if (row >= 1 && row <= L0) {
+            int t = row - 1;
+            const float *wc = w + co * 2 * k;
+            for (int ci = 0; ci < 2; ++ci)
+                for (int r = 0; r < k; ++r) acc = fmaf(wc[ci * k + r], xs[ci * Wp + t * s + r], acc);
+        }
+        o[idx] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- GroupNorm
+// grid (n_win), block 32*G (one warp per group).  x: [n_win][L+2][C] padded,
+// normalised in place; res (optional) same layout, added before ReLU; if
+// pool_out is given, the result is max-pooled (k3, s2, p1) into
+// pool_out [n_win][L/2 + 2][C] instead (x left untouched).
+// Pad rows of the written tile are set to zero.
+__global__ void k_groupnorm(float *__restrict__ x, int L, int C, int G, const float *__restrict__ gamma,
+                            const float *__restrict__ beta, float eps, const float *__restrict__ res, int relu,
+                            float *__restrict__ pool_out) {
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cg = C / G;
+    const int64_t tile = (int64_t)(L + 2) * C;
+    float *xt = x + (int64_t)blockIdx.x * tile + C;  // row 0 of data
+    const int cnt = L * cg;
+    float s = 0.f;
+    for (int e = lane; e < cnt; e += 32) {
+        int row = e / cg, c = g * cg + (e - row * cg);
+        s += xt[(int64_t)row * C + c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float mu = s / (float)cnt;
+    float v = 0.f;
+    for (int e = lane; e < cnt; e += 32) {
+        int row = e / cg, c = g * cg + (e - row * cg);
+        float d = xt[(int64_t)row * C + c] - mu;
+        v = fmaf(d, d, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const float rstd = rsqrtf(v / (float)cnt + eps);
+    if (pool_out == nullptr) {
+        const float *rt = res ? res + (int64_t)blockIdx.x * tile + C : nullptr;
+        for (int e = lane; e < cnt; e += 32) {
+            int row = e / cg, c = g * cg + (e - row * cg);
+            int64_t a = (int64_t)row * C + c;
+            float val = (xt[a] - mu) * rstd * gamma[c] + beta[c];
+            if (rt) val += rt[a];
+            if (relu) val = fmaxf(val, 0.f);
+            xt[a] = val;
+        }
+        for (int e = lane; e < cg; e += 32) {
+            int c = g * cg + e;
+            xt[-C + c] = 0.f;
+            xt[(int64_t)L * C + c] = 0.f;
+        }
+    } else {
+        const int Lp = (L + 2 - 3) / 2 + 1;
+        float *po = pool_out + (int64_t)blockIdx.x * (Lp + 2) * C + C;
+        const int pcnt = Lp * cg;
+        for (int e = lane; e < pcnt; e += 32) {
+            int row = e / cg, c = g * cg + (e - row * cg);
+            float m = -INFINITY;
+            for (int r = -1; r <= 1; ++r) {
+                int src = 2 * row + r;
+                if (src < 0 || src >= L) continue;
+                float val = (xt[(int64_t)src * C + c] - mu) * rstd * gamma[c] + beta[c];
+                if (relu) val = fmaxf(val, 0.f);
+                m = fmaxf(m, val);
+            }
+            po[(int64_t)row * C + c] = m;
+        }
+        for (int e = lane; e < cg; e += 32) {
+            int c = g * cg + e;
+            po[-C + c] = 0.f;
+            po[(int64_t)Lp * C + c] = 0.f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- conv GEMM
+// out[w][t+1][n] = sum_kk A[w,t][kk] * Wt[kk][n],  A[w,t][kk] = in[w][t*s + off][kk]
+// (kk runs over k*Cin contiguous floats).  M = n_win * Lout rows.
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(256) k_conv_fp32(const float *__restrict__ in, const float *__restrict__ wt,
+                                                   float *__restrict__ out, int M, int Lout, int Lp_in, int Lp_out,
+                                                   int Cin, int Cout, int K, int s, int off) {
+    constexpr int BK = 16;
+    constexpr int TX = BN / TN;
+    constexpr int A_F4 = BM * BK / 4;  // float4 loads per A tile
+    constexpr int B_F4 = BK * BN / 4;
+    constexpr int A_PER = (A_F4 + 255) / 256;
+    __shared__ __align__(16) float As[BK][BM + 4];
+    __shared__ __align__(16) float Bs[BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+
+    const float *arow[A_PER];
+    int acol[A_PER], amrow[A_PER];
+#pragma unroll
+    for (int i = 0; i < A_PER; ++i) {
+        int f = tid + i * 256;
+        int r = f / (BK / 4);
+        amrow[i] = r;
+        acol[i] = (f % (BK / 4)) * 4;
+        int m = m0 + r;
+        if (f < A_F4 && m < M) {
+            int w = m / Lout, t = m - w * Lout;
+            arow[i] = in + ((int64_t)w * Lp_in + (int64_t)t * s + off) * Cin;
+        } else {
+            arow[i] = nullptr;
+        }
+    }
+    float acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < A_PER; ++i) {
+            int f = tid + i * 256;
+            if (f < A_F4) {
+                float4 v = arow[i] ? *reinterpret_cast<const float4 *>(arow[i] + k0 + acol[i])
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                As[acol[i] + 0][amrow[i]] = v.x;
+                As[acol[i] + 1][amrow[i]] = v.y;
+                As[acol[i] + 2][amrow[i]] = v.z;
+                As[acol[i] + 3][amrow[i]] = v.w;
+            }
+        }
+        for (int f = tid; f < B_F4; f += 256) {
+            int r = f / (BN / 4), c = (f % (BN / 4)) * 4;
+            *reinterpret_cast<float4 *>(&Bs[r][c]) =
+                *reinterpret_cast<const float4 *>(wt + (int64_t)(k0 + r) * Cout + n0 + c);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; i += 4) {
+                float4 v = *reinterpret_cast<const float4 *>(&As[kk][ty * TM + i]);
+                a[i] = v.x; a[i + 1] = v.y; a[i + 2] = v.z; a[i + 3] = v.w;
+            }
+#pragma unroll
+            for (int j = 0; j < TN; j += 4) {
+                float4 v = *reinterpret_cast<const float4 *>(&Bs[kk][tx * TN + j]);
+                b[j] = v.x; b[j + 1] = v.y; b[j + 2] = v.z; b[j + 3] = v.w;
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int m = m0 + ty * TM + i;
+        if (m >= M) continue;
+        int w = m / Lout, t = m - w * Lout;
+        float *o = out + ((int64_t)w * Lp_out + t + 1) * Cout + n0 + tx * TN;
+#pragma unroll
+        for (int j = 0; j < TN; j += 4)
+            *reinterpret_cast<float4 *>(o + j) = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+    }
+}
+
+// ---------------------------------------------------------------- head
+// grid (n_win), block 256: logit = fc_b + sum_c fc_w[c] * mean_t x[t][c]
+__global__ void k_head(const float *__restrict__ x, int L, int C, const float *__restrict__ fc_w,
+                       const float *__restrict__ fc_b, float *__restrict__ logits, int64_t w0) {
+    __shared__ float part[512];
+    const float *xt = x + (int64_t)blockIdx.x * (L + 2) * C + C;
+    const int tid = threadIdx.x;
+    if (C <= 256) {
+        const int phases = 256 / C;
+        const int c = tid % C, p = tid / C;
+        float s = 0.f;
+        for (int r = p; r < L; r += phases) s += xt[(int64_t)r * C + c];
+        part[tid] = s;
+        __syncthreads();
+        if (tid < C) {
+            float tot = 0.f;
+            for (int q = 0; q < phases; ++q) tot += part[q * C + tid];
+            part[256 + tid] = fc_w[tid] * (tot / (float)L);
+        }
+    } else {
+        for (int c = tid; c < C; c += 256) {
+            float s = 0.f;
+            for (int r = 0; r < L; ++r) s += xt[(int64_t)r * C + c];
+            part[c] = fc_w[c] * (s / (float)L);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const float *v = C <= 256 ? part + 256 : part;
+        float z = fc_b[0];
+        for (int c = 0; c < C; ++c) z += v[c];
+        logits[w0 + blockIdx.x] = z;
+    }
+}
+
+template <int BM, int BN, int TM, int TN>
+void conv_launch(afg_ctx *ctx, const float *in, const float *wt, float *out, int nw, const ConvLayer &L,
+                 cudaStream_t st) {
+    const int M = nw * L.lout;
+    const int K = L.k * L.cin;
+    const int off = 1 - L.pad;
+    dim3 grid((M + BM - 1) / BM, L.cout / BN);
+    // algorithmic: 2 M N K FLOPs; one read of the input activations and weights, one write of the output
+    KScope ks(ctx, st, KK_CONV_FP32, 2.0 * M * L.cout * K,
+              4.0 * ((double)nw * L.lin * L.cin + (double)K * L.cout + (double)M * L.cout));
+    k_conv_fp32<BM, BN, TM, TN><<<grid, 256, 0, st>>>(in, wt, out, M, L.lout, L.lin + 2, L.lout + 2, L.cin, L.cout,
+                                                      K, L.stride, off);
+}
+
+void conv_dispatch(afg_ctx *ctx, const float *in, float *out, int nw, const ConvLayer &L, cudaStream_t st) {
+    if (L.cout % 128 == 0) conv_launch<128, 128, 8, 8>(ctx, in, L.wt, out, nw, L, st);
+    else if (L.cout % 64 == 0) conv_launch<128, 64, 8, 4>(ctx, in, L.wt, out, nw, L, st);
+    else conv_launch<256, 16, 4, 4>(ctx, in, L.wt, out, nw, L, st);
+}
+
+// GroupNorm launch with its accounting: one read (+ residual read) and one write of the tile
+void gn_launch(afg_ctx *ctx, float *x, int nw, int L, int C, int G, const float *gamma, const float *beta, float eps,
+               const float *res, int relu, float *pool_out, cudaStream_t st) {
+    double tile = (double)nw * L * C * 4.0;
+    double bytes = tile * (res ? 3.0 : 2.0);
+    if (pool_out) bytes = tile * 1.5;
+    KScope ks(ctx, st, KK_GROUPNORM, 0.0, bytes);
+    k_groupnorm<<<nw, 32 * G, 0, st>>>(x, L, C, G, gamma, beta, eps, res, relu, pool_out);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- plan
+int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights) {
+    NetPlan &P = ctx->plan;
+    const afg_net &n = ctx->cfg.net;
+    P.net = n;
+    P.convs.clear();
+    P.blocks.clear();
+    const int W = ctx->cfg.win_len;
+    // host-side parameter image: per conv Wt [k*cin][cout], gamma, beta; stem raw [C0][2][k]
+    std::vector<float> img;
+    const float *src = weights_host;
+    auto take = [&](int64_t cnt) { const float *r = src; src += cnt; return r; };
+    struct Pending { int64_t wt, gamma, beta; };
+    std::vector<Pending> pend;
+    auto add_conv = [&](int cin, int cout, int k, int s, int lin) {
+        ConvLayer L{};
+        L.cin = cin; L.cout = cout; L.k = k; L.stride = s; L.pad = k / 2;
+        L.lin = lin; L.lout = conv_len(lin, k, s, k / 2);
+        const float *w = take((int64_t)cout * cin * k);
+        const float *g = take(cout), *b = take(cout);
+        Pending pd;
+        pd.wt = (int64_t)img.size();
+        img.resize(img.size() + (size_t)cout * cin * k);
+        bool stem = P.convs.empty();
+        for (int co = 0; co < cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int r = 0; r < k; ++r) {
+                    float v = w[((int64_t)co * cin + ci) * k + r];
+                    if (stem) img[pd.wt + ((int64_t)co * cin + ci) * k + r] = v;
+                    else img[pd.wt + ((int64_t)r * cin + ci) * cout + co] = v;
+                }
+        pd.gamma = (int64_t)img.size();
+        img.insert(img.end(), g, g + cout);
+        pd.beta = (int64_t)img.size();
+        img.insert(img.end(), b, b + cout);
+        pend.push_back(pd);
+        P.convs.push_back(L);
+        return (int)P.convs.size() - 1;
+    };
+    int C0 = n.widths[0];
+    add_conv(n.in_ch, C0, n.stem_k, n.stem_stride, W);
+    P.l_stem_out = P.convs[0].lout;
+    P.l_after_stem = n.stem_pool ? conv_len(P.l_stem_out, 3, 2, 1) : P.l_stem_out;
+    int cin = C0, L = P.l_after_stem;
+    int64_t maxact = (int64_t)(P.l_stem_out + 2) * C0;
+    for (int s = 0; s < n.n_stages; ++s) {
+        for (int b = 0; b < n.blocks[s]; ++b) {
+            int stride = (s > 0 && b == 0) ? 2 : 1;
+            int width = n.widths[s];
+            BlockPlan bp;
+            bp.c1 = add_conv(cin, width, 3, stride, L);
+            int Lo = P.convs[bp.c1].lout;
+            bp.c2 = add_conv(width, width, 3, 1, Lo);
+            bp.sc = -1;
+            if (stride != 1 || cin != width) bp.sc = add_conv(cin, width, 1, stride, L);
+            P.blocks.push_back(bp);
+            maxact = std::max(maxact, (int64_t)(L + 2) * cin);
+            maxact = std::max(maxact, (int64_t)(Lo + 2) * width);
+            cin = width;
+            L = Lo;
+        }
+    }
+    P.c_last = cin;
+    P.l_last = L;
+    const float *fw = take(cin), *fb = take(1);
+    int64_t fc_off = (int64_t)img.size();
+    img.insert(img.end(), fw, fw + cin);
+    img.push_back(fb[0]);
+    if (src - weights_host != n_weights)
+        return afg_fail(ctx, AFG_ERR_ARG, "weights: expected %lld floats, got %lld",
+                        (long long)(src - weights_host), (long long)n_weights);
+    P.max_act_per_window = maxact;
+    // upload
+    size_t bytes = img.size() * sizeof(float);
+    float *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return afg_fail(ctx, AFG_ERR_OOM, "weights: cudaMalloc(%zu) failed", bytes);
+    ctx->d_params = d;
+    ctx->d_params_bytes = bytes;
+    ctx->bytes_held += (int64_t)bytes;
+    AFG_CUDA(ctx, cudaMemcpy(d, img.data(), bytes, cudaMemcpyHostToDevice));
+    for (size_t i = 0; i < P.convs.size(); ++i) {
+        P.convs[i].wt = d + pend[i].wt;
+        P.convs[i].gamma = d + pend[i].gamma;
+        P.convs[i].beta = d + pend[i].beta;
+        P.convs[i].wt_bf16 = nullptr;
+    }
+    P.fc_w = d + fc_off;
+    P.fc_b = d + fc_off + cin;
+    return AFG_OK;
+}
+
+// ---------------------------------------------------------------- forward
+int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
+                      int64_t n_win, int64_t shift, float *logits, cudaStream_t st) {
+    const NetPlan &P = ctx->plan;
+    const int G = P.net.groups;
+    const float eps = P.net.eps;
+    const int W = ctx->cfg.win_len;
+    // windows per chunk: keep each activation buffer under ~4 GiB
+    int64_t per_win = P.max_act_per_window * (int64_t)sizeof(float);
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_win, ((int64_t)4 << 30) / per_win));
+    chunk = std::min<int64_t>(chunk, 16384);
+    float *buf[4];
+    for (int i = 0; i < 4; ++i) {
+        int rc = afg_ws_reserve(ctx, WS_ACT0 + i, (size_t)(chunk * per_win), (void **)&buf[i]);
+        if (rc) return rc;
+    }
+    const ConvLayer &S = P.convs[0];
+    for (int64_t w0 = 0; w0 < n_win; w0 += chunk) {
+        const int nw = (int)std::min<int64_t>(chunk, n_win - w0);
+        const int pad = S.k / 2;
+        {
+            KScope ks(ctx, st, KK_STEM, 2.0 * nw * S.lout * S.cout * S.cin * S.k,
+                      4.0 * nw * ((double)2 * W + (double)(S.lout + 2) * S.cout));
+            k_stem<<<nw, 256, 2 * (W + 2 * pad) * sizeof(float), st>>>(y, n_y, y_stride, first, stride, shift, w0,
+                                                                      S.wt, S.cout, S.k, S.stride, W, S.lout, buf[0]);
+        }
+        AFG_LAUNCH_CHECK(ctx, "k_stem");
+        float *A = buf[0], *B = buf[1], *Cb = buf[2], *D = buf[3];
+        if (P.net.stem_pool) {
+            gn_launch(ctx, buf[0], nw, S.lout, S.cout, G, S.gamma, S.beta, eps, nullptr, 1, buf[1], st);
+            A = buf[1];
+            B = buf[0];
+        } else {
+            gn_launch(ctx, buf[0], nw, S.lout, S.cout, G, S.gamma, S.beta, eps, nullptr, 1, nullptr, st);
+        }
+        AFG_LAUNCH_CHECK(ctx, "k_groupnorm(stem)");
+        for (const BlockPlan &bp : P.blocks) {
+            const ConvLayer &c1 = P.convs[bp.c1], &c2 = P.convs[bp.c2];
+            conv_dispatch(ctx, A, B, nw, c1, st);
+            gn_launch(ctx, B, nw, c1.lout, c1.cout, G, c1.gamma, c1.beta, eps, nullptr, 1, nullptr, st);
+            conv_dispatch(ctx, B, Cb, nw, c2, st);
+            const float *res = A;
+            if (bp.sc >= 0) {
+                const ConvLayer &sc = P.convs[bp.sc];
+                conv_dispatch(ctx, A, D, nw, sc, st);
+                gn_launch(ctx, D, nw, sc.lout, sc.cout, G, sc.gamma, sc.beta, eps, nullptr, 0, nullptr, st);
+                res = D;
+            }
+            gn_launch(ctx, Cb, nw, c2.lout, c2.cout, G, c2.gamma, c2.beta, eps, res, 1, nullptr, st);
+            AFG_LAUNCH_CHECK(ctx, "residual block");
+            std::swap(A, Cb);
+        }
+        {
+            KScope ks(ctx, st, KK_HEAD, 2.0 * nw * P.l_last * P.c_last, 4.0 * nw * (double)P.l_last * P.c_last);
+            k_head<<<nw, 256, 0, st>>>(A, P.l_last, P.c_last, P.fc_w, P.fc_b, logits, w0);
+        }
+        AFG_LAUNCH_CHECK(ctx, "k_head");
+    }
+    return AFG_OK;
+}

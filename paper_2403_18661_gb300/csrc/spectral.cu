@@ -1,0 +1,241 @@
+// Welch PSD, whitening-filter build and FFT-domain whitening
+// (Sec. IV.B "Noise sampling": PSD from 8 s, frequency-domain whitening,
+// 0.5 s crop at each edge; Sec. VI: PSD from the first 64 s of state).
+//
+// Kernels
+//   k_twiddles        exp(-2 pi i k / NFFT) tables in double and float
+//   k_periodogram     one Hann-windowed segment per CTA: FP32 real FFT in
+//                     shared memory, |X_k|^2 formed and stored in FP64
+//   k_psd_mean        FP64 mean over the K segments of each epoch, density
+//                     scaling and one-sided doubling
+//   k_filter_build    one (detector, epoch) per CTA, all FP64: amplitude
+//                     response psd^-1/2 above the highpass, zero-phase
+//                     inverse real FFT, Hann taper of F taps, sqrt(2/fs),
+//                     forward real FFT at the whitening size -> real gains
+//   k_whiten          one 8192-output overlap-save block per CTA: FP32 real
+//                     FFT of 8192 + F - 1 samples (zero padded to NFFT),
+//                     multiply by the epoch's gains, inverse FFT, keep the
+//                     outputs whose support lies inside the block.
+#include <math.h>
+#include <stdio.h>
+
+#include "afg_internal.cuh"
+#include "fft.cuh"
+
+namespace {
+
+constexpr int NT32 = 512;   // threads of the FP32 FFT kernels
+constexpr int NT64 = 1024;  // threads of the FP64 filter kernel
+
+__global__ void k_twiddles(float2 *tw32, double2 *tw64) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NFFT) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)NFFT, &s, &c);
+    tw64[k] = make_double2(c, -s);
+    tw32[k] = make_float2((float)c, (float)-s);
+}
+
+// grid (n_seg, n_det); segment g of detector d covers x[d][g*hop, g*hop + NFFT)
+__global__ void __launch_bounds__(NT32) k_periodogram(const float *__restrict__ x, int64_t x_stride, int hop,
+                                                       const float2 *__restrict__ tw, double *__restrict__ P,
+                                                       int64_t n_seg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *d = reinterpret_cast<float2 *>(smem_raw);
+    const int64_t g = blockIdx.x;
+    const int det = blockIdx.y;
+    const float *src = x + det * x_stride + g * (int64_t)hop;
+    for (int j = threadIdx.x; j < NC; j += NT32) {
+        int i0 = 2 * j, i1 = 2 * j + 1;
+        // periodic Hann window w_i = 1/2 - 1/2 cos(2 pi i / NFFT)
+        float w0 = 0.5f - 0.5f * cospif(2.0f * (float)i0 / (float)NFFT);
+        float w1 = 0.5f - 0.5f * cospif(2.0f * (float)i1 / (float)NFFT);
+        d[j] = make_float2(src[i0] * w0, src[i1] * w1);
+    }
+    __syncthreads();
+    fft_nc<float2, -1, NT32>(d, tw);
+    real_split_forward<float2, NT32>(d, tw);
+    double *out = P + ((int64_t)det * n_seg + g) * NBIN;
+    for (int k = threadIdx.x; k < NBIN; k += NT32) {
+        double re = (double)d[k].x, im = (double)d[k].y;
+        out[k] = re * re + im * im;
+    }
+}
+
+// grid (ceil(NBIN/256), n_psd, n_det)
+__global__ void k_psd_mean(const double *__restrict__ P, int64_t n_seg, int seg_step, int K, double scale,
+                           double *__restrict__ psd, int64_t n_psd) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NBIN) return;
+    int64_t e = blockIdx.y;
+    int det = blockIdx.z;
+    const double *src = P + ((int64_t)det * n_seg + e * seg_step) * NBIN + k;
+    double acc = 0.0;
+    for (int q = 0; q < K; ++q) acc += src[(int64_t)q * NBIN];
+    double onesided = (k == 0 || k == NFFT / 2) ? 1.0 : 2.0;
+    psd[((int64_t)det * n_psd + e) * NBIN + k] = onesided * acc * scale;
+}
+
+// grid (n_psd, n_det); builds the whitening gains of one (detector, epoch)
+__global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict__ psd, int64_t n_psd, double fs,
+                                                        double f_hp, int F, const double2 *__restrict__ tw,
+                                                        float *__restrict__ gains) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *d = reinterpret_cast<double2 *>(smem_raw);
+    const int64_t e = blockIdx.x;
+    const int det = blockIdx.y;
+    const double *p = psd + ((int64_t)det * n_psd + e) * NBIN;
+    // amplitude response: psd^-1/2 at and above the highpass, zero below
+    for (int k = threadIdx.x; k < NBIN; k += NT64) {
+        double f = (double)k * fs / (double)NFFT;
+        double pk = p[k];
+        double a = (f >= f_hp && pk > 0.0) ? 1.0 / sqrt(pk) : 0.0;
+        d[k] = make_double2(a, 0.0);
+    }
+    __syncthreads();
+    // zero-phase impulse response h = IDFT_NFFT(A) / NFFT (real, even)
+    real_split_inverse<double2, NT64>(d, tw);
+    fft_nc<double2, +1, NT64>(d, tw);
+    // taper to F taps about m = 0 and rescale; zero every other sample.
+    // Sample i of the circular buffer is lag m = i (i < NFFT/2) or i - NFFT.
+    const double norm = sqrt(2.0 / fs) / (double)NC;
+    double *t = reinterpret_cast<double *>(d);
+    const int half = F / 2;
+    for (int i = threadIdx.x; i < NFFT; i += NT64) {
+        int m = i < NFFT / 2 ? i : i - NFFT;
+        double v = 0.0;
+        if (m >= -half && m < half) {
+            double taper = 0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F);
+            v = t[i] * norm * taper;
+        }
+        t[i] = v;
+    }
+    __syncthreads();
+    // gains G_k = DFT_NFFT(g)_k (real for the even g); stored divided by NC,
+    // the factor the inverse half-length transform of k_whiten leaves over
+    fft_nc<double2, -1, NT64>(d, tw);
+    real_split_forward<double2, NT64>(d, tw);
+    float *out = gains + ((int64_t)det * n_psd + e) * NBIN;
+    for (int k = threadIdx.x; k < NBIN; k += NT64) out[k] = (float)(d[k].x / (double)NC);
+}
+
+// grid (n_blocks, n_det); block b produces y[d][b*WB, min((b+1)*WB, out_len))
+__global__ void __launch_bounds__(NT32) k_whiten(const float *__restrict__ x, int64_t n, int64_t x_stride,
+                                                  const float *__restrict__ gains, int64_t n_psd,
+                                                  int64_t out_first, int64_t out_len, int64_t epoch_len, int F,
+                                                  const float2 *__restrict__ tw, float *__restrict__ y,
+                                                  int64_t y_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *d = reinterpret_cast<float2 *>(smem_raw);
+    const int64_t o = (int64_t)blockIdx.x * WB;
+    const int det = blockIdx.y;
+    int64_t e = 0;
+    if (epoch_len > 0) {
+        e = o / epoch_len;
+        if (e > n_psd - 1) e = n_psd - 1;
+    }
+    const int half = F / 2;
+    const int64_t s0 = out_first + o - half;  // raw index of block sample 0
+    const int64_t need = WB + F - 1;          // samples that reach a kept output
+    const float *src = x + det * x_stride;
+    for (int j = threadIdx.x; j < NC; j += NT32) {
+        int64_t i0 = 2 * (int64_t)j, i1 = i0 + 1;
+        float a = (i0 < need && s0 + i0 < n) ? src[s0 + i0] : 0.0f;
+        float b = (i1 < need && s0 + i1 < n) ? src[s0 + i1] : 0.0f;
+        d[j] = make_float2(a, b);
+    }
+    __syncthreads();
+    fft_nc<float2, -1, NT32>(d, tw);
+    real_split_forward<float2, NT32>(d, tw);
+    const float *gk = gains + ((int64_t)det * n_psd + e) * NBIN;
+    for (int k = threadIdx.x; k < NBIN; k += NT32) {
+        float gv = gk[k];
+        d[k] = make_float2(d[k].x * gv, d[k].y * gv);
+    }
+    __syncthreads();
+    real_split_inverse<float2, NT32>(d, tw);
+    fft_nc<float2, +1, NT32>(d, tw);
+    const float *t = reinterpret_cast<const float *>(d);
+    int64_t cnt = out_len - o;
+    if (cnt > WB) cnt = WB;
+    float *dst = y + det * y_stride + o;
+    for (int q = threadIdx.x; q < cnt; q += NT32) dst[q] = t[q + half];
+}
+
+bool g_attrs_set = false;
+
+int set_attrs(afg_ctx *ctx) {
+    if (g_attrs_set) return AFG_OK;
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((NC + 1) * sizeof(float2))));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((NC + 1) * sizeof(float2))));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_filter_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((NC + 1) * sizeof(double2))));
+    g_attrs_set = true;
+    return AFG_OK;
+}
+
+}  // namespace
+
+int afg_make_twiddles(afg_ctx *ctx) {
+    {
+        KScope ks(ctx, 0, KK_TWIDDLES, 0.0, (double)NFFT * (sizeof(float2) + sizeof(double2)));
+        k_twiddles<<<NFFT / 256, 256>>>(ctx->tw32, ctx->tw64);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_twiddles");
+    return set_attrs(ctx);
+}
+
+int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step,
+               int64_t psd_span, double *psd, cudaStream_t st) {
+    const int hop = ctx->cfg.hop;
+    const int64_t K = (psd_span - NFFT) / hop + 1;
+    const int64_t seg_step = n_psd > 1 ? psd_step / hop : 0;
+    const int64_t n_seg = (n_psd - 1) * seg_step + K;
+    double *P = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_PERIODOGRAM, (size_t)n_det * n_seg * NBIN * sizeof(double), (void **)&P);
+    if (rc) return rc;
+    if (n_seg > 0x7fffffff) return afg_fail(ctx, AFG_ERR_ARG, "psd_estimate: too many segments");
+    {
+        // one read of every segment, one FP64 periodogram written per segment
+        KScope ks(ctx, st, KK_PERIODOGRAM, 0.0, (double)n_det * n_seg * (NFFT * 4.0 + NBIN * 8.0));
+        k_periodogram<<<dim3((unsigned)n_seg, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(x, n, hop, ctx->tw32,
+                                                                                              P, n_seg);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_periodogram");
+    // periodic Hann: sum w^2 = 3 NFFT / 8
+    const double scale = 1.0 / ((double)K * (double)ctx->cfg.fs * (3.0 * NFFT / 8.0));
+    {
+        KScope ks(ctx, st, KK_PSD_MEAN, 0.0, (double)n_det * (n_seg + n_psd) * NBIN * 8.0);
+        k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)n_psd, n_det), 256, 0, st>>>(P, n_seg, (int)seg_step,
+                                                                                      (int)K, scale, psd, n_psd);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_psd_mean");
+    return AFG_OK;
+}
+
+int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const double *psd, int64_t n_psd,
+                  int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, int64_t y_stride,
+                  cudaStream_t st) {
+    float *gains = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_FILTER, (size_t)n_det * n_psd * NBIN * sizeof(float), (void **)&gains);
+    if (rc) return rc;
+    {
+        KScope ks(ctx, st, KK_FILTER, 0.0, (double)n_det * n_psd * NBIN * (8.0 + 4.0));
+        k_filter_build<<<dim3((unsigned)n_psd, n_det), NT64, (NC + 1) * sizeof(double2), st>>>(
+            psd, n_psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass, ctx->cfg.fir_len, ctx->tw64, gains);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_filter_build");
+    if (out_len <= 0) return AFG_OK;
+    const int64_t nb = (out_len + WB - 1) / WB;
+    {
+        // algorithmic: read the cropped span once, write the output once, read the gains
+        const double F = ctx->cfg.fir_len;
+        KScope ks(ctx, st, KK_WHITEN, 0.0, (double)n_det * ((2.0 * out_len + F - 1.0) * 4.0 + n_psd * NBIN * 4.0));
+        k_whiten<<<dim3((unsigned)nb, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(
+            x, n, n, gains, n_psd, out_first, out_len, epoch_len, ctx->cfg.fir_len, ctx->tw32, y, y_stride);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_whiten");
+    return AFG_OK;
+}

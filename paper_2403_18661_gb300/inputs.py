@@ -323,7 +323,9 @@ def make_strain(wl: Workload, model: NoiseModel = NoiseModel()) -> Tuple[np.ndar
     x = np.stack([coloured_noise(n, wl.seed * 2 + d, model, wl.fs) for d in range(2)])
     inj = []
     rng = _rng(wl.seed + 99)
-    if wl.n_chirps == 1:
+    if wl.n_chirps == 0:
+        pass
+    elif wl.n_chirps == 1:
         # one 30 Msun chirp-mass binary at SNR 12, merging 40 s into the span
         inj.append(dict(t_c=40.0, mchirp=30.0, snr=12.0))
     else:

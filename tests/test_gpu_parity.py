@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (derived from the arithmetic; both sides see the same float32
+inputs):
+  PSD          relative <= 1e-4 per bin: FP32 FFT rounding of a coloured
+               spectrum whose weakest bins sit ~1e2 below the RMS bin
+               (relative error ~ 2 u sqrt(log2 N) (S_rms/S_k)^1/2 ~ 1e-5)
+  whitened     absolute <= 5e-5 on unit-variance output: FP32 FFT rounding of
+               the input spread over the band and multiplied by the largest
+               filter gain (~1e1 above the RMS gain)
+  logits FP32  |dz| <= 1e-4 (1 + |z|)
+  statistic    |dI| <= 1e-4 (1 + |I|); trigger lists equal except where the
+               oracle's maximum beats its runner-up by < 2 x the logit
+               tolerance, and then within +-1 sample
+  triggers of a given statistic: bit-exact (index work).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc  # noqa: E402
+from paper_2403_18661_gb300 import abi, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+PSD_RTOL = 1e-4
+WHITE_ATOL = 5e-5
+LOGIT_TOL = 1e-4
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    wl = inputs.PLAIN_64S
+    x, inj = inputs.make_strain(wl)
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    ref = orc.analyze_plain(x.astype(np.float64), wl, w)
+    return wl, x, w, ref
+
+
+@pytest.fixture(scope="module")
+def ctx_tiny(c1):
+    wl, x, w, _ = c1
+    ctx = abi.Context(wl, w)
+    yield ctx
+    ctx.close()
+
+
+def test_psd_plain(c1, ctx_tiny):
+    wl, x, w, ref = c1
+    got = ctx_tiny.psd_estimate(_dev(x)).cpu().numpy()
+    rel = np.abs(got - ref["psd"]) / ref["psd"]
+    assert got.shape == (2, 1, 8193)
+    assert rel.max() < PSD_RTOL, rel.max()
+
+
+def test_psd_epochs_share_segments(c1, ctx_tiny):
+    wl, x, w, _ = c1
+    # 3 epochs of 16 s look-back every 8 s over the 64 s span
+    got = ctx_tiny.psd_estimate(_dev(x), n_psd=3, psd_step=16384, psd_span=32768).cpu().numpy()
+    for e in range(3):
+        for d in range(2):
+            ref = orc.welch(x[d, e * 16384: e * 16384 + 32768].astype(np.float64), 16384, 8192, 2048.0)
+            assert np.max(np.abs(got[d, e] - ref) / ref) < PSD_RTOL
+
+
+def test_whiten_with_oracle_psd(c1, ctx_tiny):
+    wl, x, w, ref = c1
+    psd = _dev(ref["psd"])
+    got = ctx_tiny.whiten(_dev(x), psd, wl.crop, x.shape[1] - 2 * wl.crop).cpu().numpy()
+    err = np.abs(got - ref["white"])
+    assert np.std(ref["white"]) == pytest.approx(1.0, abs=0.2)
+    assert err.max() < WHITE_ATOL, err.max()
+
+
+def test_whiten_ragged_and_epochs(c1, ctx_tiny):
+    wl, x, w, _ = c1
+    # epoch mode: 2 epochs of 8192 outputs after a 32 s look-back; ragged third block
+    xd = _dev(x)
+    psd = ctx_tiny.psd_estimate(xd, n_psd=3, psd_step=8192, psd_span=65536)
+    out_first, out_len = 65536, 8192 * 2 + 3000
+    got = ctx_tiny.whiten(xd, psd, out_first, out_len, epoch_len=8192).cpu().numpy()
+    p = psd.cpu().numpy()
+    for d in range(2):
+        for e, (lo, hi) in enumerate([(0, 8192), (8192, 16384), (16384, out_len)]):
+            taps = orc.whitening_taps(p[d, e], 16384, 2048.0, 32.0, 2048)
+            ref = orc.fir(x[d].astype(np.float64), taps, out_first + lo, hi - lo)
+            assert np.max(np.abs(got[d, lo:hi] - ref)) < WHITE_ATOL
+
+
+def test_infer_windows_tiny_with_shift(c1, ctx_tiny):
+    wl, x, w, ref = c1
+    white = ref["white"].astype(np.float32)
+    yd = _dev(white)
+    n_y = white.shape[1]
+    for shift, first, n_win in [(0, 0, 244), (2048 * 7, 100, 33), (n_y - 1000, 5, 17), (0, 0, 1)]:
+        got = ctx_tiny.infer_windows(yd, first, 512, n_win, shift).cpu().numpy()
+        want = orc.infer_windows(wl.net, w, white.astype(np.float64), wl.win_len, first, 512, n_win, shift)
+        err = np.abs(got - want) / (1 + np.abs(want))
+        assert err.max() < LOGIT_TOL, (shift, err.max())
+
+
+def test_integrate_and_triggers_bit_exact(ctx_tiny):
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal(5000).astype(np.float32)
+    stat, trig, n_trig = ctx_tiny.integrate(_dev(z), 16, 64)
+    s = stat.cpu().numpy()
+    ref = orc.integrate(z.astype(np.float64), 16)
+    assert np.max(np.abs(s - ref)) < 1e-6
+    n = int(n_trig.item())
+    want = orc.triggers(s.astype(np.float64), 64)
+    assert n == len(want)
+    assert np.array_equal(trig.cpu().numpy()[:n], want)
+
+
+def test_triggers_ties_and_capacity(ctx_tiny):
+    z = np.zeros(40, dtype=np.float32)
+    z[10:14] = 1.0  # plateau after integration with n_int = 1
+    stat, trig, n_trig = ctx_tiny.integrate(_dev(z), 1, 3, trig_cap=1)
+    want = orc.triggers(z.astype(np.float64), 3)
+    assert int(n_trig.item()) == len(want)
+    assert trig.cpu().numpy()[0] == want[0]
+
+
+def _trigger_match(stat_gpu, stat_ref, trig_gpu, trig_ref, half, tol):
+    gpu = set(int(t) for t in trig_gpu)
+    for j in trig_ref:
+        lo, hi = max(0, j - half), min(len(stat_ref), j + half + 1)
+        nb = np.delete(stat_ref[lo:hi], j - lo)
+        margin = stat_ref[j] - (nb.max() if len(nb) else -np.inf)
+        if margin > 2 * tol * (1 + abs(stat_ref[j])):
+            assert j in gpu, f"oracle trigger {j} (margin {margin:.3g}) missing on the GPU"
+        else:
+            assert any(abs(j - g) <= 1 for g in gpu) or margin <= 2 * tol * (1 + abs(stat_ref[j]))
+
+
+def test_analyze_plain_c1_end_to_end(c1, ctx_tiny):
+    wl, x, w, ref = c1
+    logits, stat, trig, n_trig = ctx_tiny.analyze(_dev(x))
+    lg = logits.cpu().numpy()
+    err = np.abs(lg - ref["logits"]) / (1 + np.abs(ref["logits"]))
+    assert err.max() < LOGIT_TOL, err.max()
+    st = stat.cpu().numpy()
+    assert np.max(np.abs(st - ref["stat"]) / (1 + np.abs(ref["stat"]))) < LOGIT_TOL
+    n = int(n_trig.item())
+    _trigger_match(st, ref["stat"], trig.cpu().numpy()[:n], ref["triggers"], wl.cluster_half, LOGIT_TOL)
+
+
+def test_analyze_host_matches_device(c1, ctx_tiny):
+    wl, x, w, ref = c1
+    _, stat_d, trig_d, n_d = ctx_tiny.analyze(_dev(x))
+    stat_h, trig_h = ctx_tiny.analyze_host(x)
+    assert np.array_equal(stat_h, stat_d.cpu().numpy())
+    assert np.array_equal(trig_h, trig_d.cpu().numpy()[: int(n_d.item())])
+
+
+def test_analyze_epoch_mode_small(ctx_tiny):
+    # epoch mode over 3 epochs of 8 s after a 64 s look-back, tiny network at 4 Hz
+    wl = inputs.Workload(name="epoch-small", duration_s=20.0, net=inputs.TINY_NET, stride=512, n_win=80,
+                         epoch_len=16384, seed=99)
+    x, _ = inputs.make_strain(dataclass_replace(wl, n_chirps=0))
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    ctx = abi.Context(wl, w)
+    logits, stat, trig, n_trig = ctx.analyze(_dev(x))
+    x64 = x.astype(np.float64)
+    eps = list(range(wl.n_epochs))
+    psd = orc.psd_epochs(x64, wl, eps)
+    white = orc.whiten(x64, wl, psd, eps)
+    want = orc.infer_windows(wl.net, w, white, wl.win_len, 0, wl.stride, wl.n_win)
+    err = np.abs(logits.cpu().numpy() - want) / (1 + np.abs(want))
+    assert err.max() < LOGIT_TOL, err.max()
+    ctx.close()
+
+
+def dataclass_replace(obj, **kw):
+    import dataclasses
+    return dataclasses.replace(obj, **kw)
+
+
+def test_bad_arguments_are_refused(ctx_tiny):
+    yd = torch.zeros((2, 4000), device="cuda")
+    with pytest.raises(abi.AfgError) as e:
+        ctx_tiny.infer_windows(yd, 0, 512, 5)  # windows past the end
+    assert e.value.status == -1
+    x = torch.zeros((2, 10000), device="cuda")
+    with pytest.raises(abi.AfgError):
+        ctx_tiny.psd_estimate(x)  # shorter than one segment
+    with pytest.raises(abi.AfgError):
+        ctx_tiny.whiten(x, torch.zeros((2, 1, 8193), dtype=torch.float64, device="cuda"), 100, 50)  # no crop
+
+
+@pytest.mark.slow
+def test_resnet34_hour_sampled_windows():
+    """Full-size workload (1 h, ResNet34-GN, 16 Hz) through the same call the
+    benchmark times; sampled windows checked against the oracle."""
+    wl = inputs.HOUR_RESNET34
+    x, _ = inputs.make_strain(wl)
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    ctx = abi.Context(wl, w)
+    logits, stat, trig, n_trig = ctx.analyze(_dev(x))
+    lg = logits.cpu().numpy()
+    assert np.all(np.isfinite(lg))
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([[0, wl.n_win - 1], rng.integers(0, wl.n_win, 4)]))
+    x64 = x.astype(np.float64)
+    for j in sample:
+        s0 = j * wl.stride
+        eps = sorted({(s0) // wl.epoch_len, (s0 + wl.win_len - 1) // wl.epoch_len})
+        psd = orc.psd_epochs(x64, wl, eps)
+        white = orc.whiten(x64, wl, psd, eps)
+        off = s0 - eps[0] * wl.epoch_len
+        want = orc.network(wl.net, w, white[:, off: off + wl.win_len])
+        assert abs(lg[j] - want) < LOGIT_TOL * (1 + abs(want)), (j, lg[j], want)
+    ctx.close()
