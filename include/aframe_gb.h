@@ -232,6 +232,45 @@ int afg_profile_enable(afg_ctx *ctx, int32_t on);
  * *n_out, and reset the counters.  Errors: AFG_ERR_ARG for NULL pointers. */
 int afg_profile_read(afg_ctx *ctx, afg_kernel_stat *out, int32_t cap, int32_t *n_out);
 
+/* ---------------------------------------------------------------- allocation-free PSD */
+
+/* Largest n_det * (distinct Welch segments) one afg_psd_estimate_noalloc call accepts. */
+#define AFG_NOALLOC_MAX_PERIODOGRAMS 64
+
+/* Welch PSD for callers that cannot allocate device memory.  The paper has
+ * no counterpart to this entry point; it exists for integrations of this
+ * library, not for the method.  Some hosts cannot call cudaMalloc: an
+ * application (an inference-server backend, a framework plugin) that owns
+ * every byte of device memory through its own pool and forbids allocations
+ * behind its back, or a latency-critical loop where cudaMalloc/cudaFree
+ * would add an implicit device-wide synchronisation.  The context API
+ * allocates its workspaces on first use, so such callers use this instead.
+ *
+ * Result: exactly what afg_psd_estimate computes (same kernels, same
+ * arguments, nfft = 16384, periodic Hann, FP32 FFT, FP64 averaging), but
+ * without a context: fs and hop are passed directly.
+ * x: [n_det][n] float32 (device); psd: [n_det][n_psd][8193] float64 (device).
+ *
+ * Memory: the periodogram scratch (AFG_NOALLOC_MAX_PERIODOGRAMS x 8193
+ * doubles, 4.2 MB) and a 128 KiB twiddle table are static __device__ arrays
+ * that every GPU which loads the library holds until the process exits.
+ * This call allocates and frees nothing.  It refuses with AFG_ERR_BUDGET
+ * when n_det * ((n_psd-1)*psd_step/hop + (psd_span-nfft)/hop + 1) exceeds
+ * AFG_NOALLOC_MAX_PERIODOGRAMS, and with AFG_ERR_ARG on the requirements of
+ * afg_psd_estimate.  AFG_ERR_CUDA if a launch or the set-up fails.
+ *
+ * Set-up: the first call on each device (made with that device current)
+ * resolves the arrays' device addresses, configures the kernel and fills the
+ * twiddle table, synchronising `stream`; make that first call before any
+ * stream capture.  Later calls only launch kernels on `stream`.
+ *
+ * Sharing: all calls on a device use the same scratch, which keeps the last
+ * call's contents (every value a call reads is written earlier in that same
+ * call, so nothing needs clearing).  Calls that overlap on the GPU (other
+ * streams, other host threads) race on the scratch: serialise them. */
+int afg_psd_estimate_noalloc(const float *x, int64_t n, int32_t n_det, int64_t n_psd, int64_t psd_step,
+                             int64_t psd_span, int32_t fs, int32_t hop, double *psd, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

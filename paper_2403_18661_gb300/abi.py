@@ -74,6 +74,7 @@ SIGNATURES = {
     "afg_analyze_host": ([_vp, _vp, ctypes.POINTER(AfgRunParams), _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "afg_profile_enable": ([_vp, _i32], ctypes.c_int),
     "afg_profile_read": ([_vp, ctypes.POINTER(AfgKernelStat), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
+    "afg_psd_estimate_noalloc": ([_vp, _i64, _i32, _i64, _i64, _i64, _i32, _i32, _vp, _vp], ctypes.c_int),
 }
 
 
@@ -125,6 +126,27 @@ def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def psd_estimate_noalloc(x, n_psd: int = 1, psd_step: int = 0, psd_span: Optional[int] = None, fs: int = 2048,
+                         hop: int = 8192, out=None, stream=None):
+    """Welch PSD through afg_psd_estimate_noalloc: no context, no device allocation by the library.
+
+    For hosts that cannot let a library call cudaMalloc; `out` (float64
+    [n_det][n_psd][8193], on x's device) may be passed in so that this call
+    allocates nothing at all.
+    """
+    import torch
+    n_det, n = x.shape
+    if psd_span is None:
+        psd_span = n
+    if out is None:
+        out = torch.empty((n_det, n_psd, 8193), dtype=torch.float64, device=x.device)
+    rc = load().afg_psd_estimate_noalloc(_ptr(x), n, n_det, n_psd, psd_step, psd_span, fs, hop, _ptr(out),
+                                         _stream(stream))
+    if rc != AFG_OK:
+        raise AfgError(rc, "afg_psd_estimate_noalloc failed")
+    return out
 
 
 class Context:

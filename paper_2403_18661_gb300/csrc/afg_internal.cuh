@@ -160,6 +160,9 @@ int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd
 int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const double *psd, int64_t n_psd,
                   int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, int64_t y_stride,
                   cudaStream_t st);
+cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step, int64_t psd_span,
+                          int hop, int fs, const float2 *tw, double *P, double *psd, cudaStream_t st);
+cudaError_t prepare_psd_kernels();
 // net_fp32.cu
 int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights);
 int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,

@@ -239,3 +239,25 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
     AFG_LAUNCH_CHECK(ctx, "k_whiten");
     return AFG_OK;
 }
+
+// The Welch kernels on caller-provided scratch and twiddles (no workspace,
+// no context, no accounting).  P must hold n_det * n_seg * NBIN doubles.
+cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step, int64_t psd_span,
+                          int hop, int fs, const float2 *tw, double *P, double *psd, cudaStream_t st) {
+    const int64_t K = (psd_span - NFFT) / hop + 1;
+    const int64_t seg_step = n_psd > 1 ? psd_step / hop : 0;
+    const int64_t n_seg = (n_psd - 1) * seg_step + K;
+    k_periodogram<<<dim3((unsigned)n_seg, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(x, n, hop, tw, P, n_seg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const double scale = 1.0 / ((double)K * (double)fs * (3.0 * NFFT / 8.0));
+    k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)n_psd, n_det), 256, 0, st>>>(P, n_seg, (int)seg_step, (int)K,
+                                                                                  scale, psd, n_psd);
+    return cudaGetLastError();
+}
+
+// Opt the periodogram kernel into its 64 KiB of dynamic shared memory on the current device.
+cudaError_t prepare_psd_kernels() {
+    return cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((NC + 1) * sizeof(float2)));
+}
