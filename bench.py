@@ -55,27 +55,24 @@ def load_peaks():
     return d
 
 
-def csrc_hash() -> str:
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2403_18661_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        with open(os.path.join(d, fn), "rb") as f:
-            h.update(fn.encode() + f.read())
-    return h.hexdigest()[:16]
+def file_hash(rel: str) -> str:
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def measured_traffic(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
-    taken on the current sources (else None)."""
+def measured_traffic(kernel: str, algo_bytes_per_launch: float):
+    """Per-launch DRAM bytes of `kernel`: the DRAM/algorithmic ratio of the committed
+    ncu capture (profiles/traffic.json) times this run's algorithmic bytes per launch;
+    None if there is no capture or its source file changed since."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e or e.get("src_hash") != csrc_hash():
+    if not e or file_hash(e["source"]) != e.get("src_sha256_16"):
         return None
-    return e.get("dram_bytes_per_launch_full_size")
+    return e["dram_over_algorithmic"] * algo_bytes_per_launch
 
 
 class ClockSampler:
@@ -162,12 +159,19 @@ def oracle_sample(wl, x: np.ndarray, w: np.ndarray, n_epochs: int, n_windows: in
             "seconds": t_white + t_net}
 
 
-def workload_by_name(name: str):
+def workload_by_name(name: str, n_win: int = 0):
     if name == "hour":
-        return inputs.HOUR_RESNET34
-    if name == "plain64":
-        return inputs.PLAIN_64S
-    raise SystemExit(f"unknown workload {name}")
+        wl = inputs.HOUR_RESNET34
+    elif name == "plain64":
+        wl = inputs.PLAIN_64S
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if n_win:
+        if wl.epoch_len == 0:
+            raise SystemExit("--n-win applies to the epoch workloads")
+        wl = dataclasses.replace(wl, n_win=n_win, n_chirps=max(1, wl.n_chirps * n_win // wl.n_win),
+                                 name=f"{wl.name}-{n_win}win", duration_s=n_win * wl.stride / wl.fs)
+    return wl
 
 
 def dist_setup():
@@ -181,7 +185,7 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
-    wl = workload_by_name(args.workload)
+    wl = workload_by_name(args.workload, args.n_win)
     x, _ = inputs.make_strain(wl)
     w = inputs.make_weights(wl.net, wl.weight_seed)
     vals, total = [], 0.0
@@ -216,7 +220,7 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = workload_by_name(args.workload)
+    wl = workload_by_name(args.workload, args.n_win)
     # each rank analyses its own hour of strain (weak scaling)
     wl_r = dataclasses.replace(wl, seed=wl.seed + 7919 * rank) if rank else wl
     x, _ = inputs.make_strain(wl_r)
@@ -313,7 +317,7 @@ def run_ours(args):
         achieved = dom["algo_bytes"] / (dom["total_ms"] / 1000.0) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         peak_src = f"{peaks['_source']} hbm_gbs"
-    traffic = measured_traffic(dom["name"])
+    traffic = measured_traffic(dom["name"], dom["algo_bytes"] / max(dom["launches"], 1))
     roofline = {"kernel": dom["name"], "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                 "launches": dom["launches"], "ms_per_launch": per_launch_ms,
@@ -352,6 +356,7 @@ def main():
     ap.add_argument("--workload", default="hour", choices=["hour", "plain64"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--ref-windows", type=int, default=32)
+    ap.add_argument("--n-win", type=int, default=0, help="analyse this many windows instead (smaller workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
