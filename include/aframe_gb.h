@@ -129,6 +129,12 @@ const char *afg_last_error(const afg_ctx *ctx);
 /* Device bytes currently held by the context (weights + workspaces + streams). */
 int afg_ctx_bytes(const afg_ctx *ctx, int64_t *bytes);
 
+/* Wait for the work queued on `stream`, then report device-side failures
+ * the library's kernels recorded since the last call: AFG_ERR_TIMEOUT if a
+ * bounded wait inside a kernel gave up (that kernel returned early and its
+ * outputs are unspecified).  Clears the record. */
+int afg_sync(afg_ctx *ctx, void *stream);
+
 /* ---------------------------------------------------------------- hot path */
 
 /* Welch PSD (Sec. IV.B: the first 8 s of a window estimate the PSD; Sec. VI:

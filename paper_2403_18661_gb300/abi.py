@@ -66,6 +66,7 @@ SIGNATURES = {
     "afg_ctx_destroy": ([_vp], ctypes.c_int),
     "afg_last_error": ([_vp], ctypes.c_char_p),
     "afg_ctx_bytes": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
+    "afg_sync": ([_vp, _vp], ctypes.c_int),
     "afg_psd_estimate": ([_vp, _vp, _i64, _i32, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
     "afg_whiten": ([_vp, _vp, _i64, _i32, _vp, _i64, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
     "afg_infer_windows": ([_vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
@@ -189,6 +190,10 @@ class Context:
         b = _i64()
         self._check(self._lib.afg_ctx_bytes(self._h, ctypes.byref(b)))
         return b.value
+
+    def sync(self, stream=None):
+        """Wait for queued work; raise AfgError(AFG_ERR_TIMEOUT) if a kernel's bounded wait gave up."""
+        self._check(self._lib.afg_sync(self._h, _stream(stream)))
 
     # ---------------------------------------------------------------- profiling
     def profile_enable(self, on: bool = True):

@@ -46,6 +46,8 @@ struct NetPlan {
     float *fc_w, *fc_b;
     int c_last, l_last;
     int64_t max_act_per_window;    // floats of the largest padded activation of one window
+    float *tc_params = nullptr;    // fused tensor-core network: FP32 parameter block
+    unsigned char *tc_wimg = nullptr;  // and BF16 weight image in shared-memory order
 };
 
 struct Workspace {
@@ -71,6 +73,7 @@ enum KernelKind {
     KK_INTEGRATE,
     KK_TRIGGERS,
     KK_CONV_TC,
+    KK_TINY_TC,
     KK_COUNT
 };
 extern const char *const kKernelNames[KK_COUNT];
@@ -101,6 +104,7 @@ struct afg_ctx {
     float2 *tw32 = nullptr;           // exp(-2 pi i k / NFFT), k < NFFT, float
     double2 *tw64 = nullptr;          // same in double
     int64_t bytes_held = 0;
+    int *d_err = nullptr;             // device-side failure record (bounded waits that gave up)
     Workspace ws[16];
 };
 
@@ -168,6 +172,7 @@ int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights);
 int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 // net_tc.cu
+int net_tc_prepare(afg_ctx *ctx);
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 // integrate.cu

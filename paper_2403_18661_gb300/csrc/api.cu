@@ -154,8 +154,15 @@ int afg_ctx_create(const afg_config *cfg, const float *weights_host, int64_t n_w
         return AFG_ERR_OOM;
     }
     ctx->bytes_held += (int64_t)tw_bytes;
+    if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess || cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        afg_ctx_destroy(ctx);
+        return AFG_ERR_OOM;
+    }
+    ctx->bytes_held += 256;
     int rc = afg_make_twiddles(ctx);
     if (rc == AFG_OK) rc = net_plan_build(ctx, weights_host, n_weights);
+    if (rc == AFG_OK) rc = net_tc_prepare(ctx);
     if (rc == AFG_OK && cudaDeviceSynchronize() != cudaSuccess) rc = AFG_ERR_CUDA;
     if (rc != AFG_OK) {
         afg_ctx_destroy(ctx);
@@ -172,6 +179,8 @@ int afg_ctx_destroy(afg_ctx *ctx) {
     for (auto &w : ctx->ws)
         if (w.p) cudaFree(w.p);
     if (ctx->d_params) cudaFree(ctx->d_params);
+    if (ctx->plan.tc_params) cudaFree(ctx->plan.tc_params);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->tw32) cudaFree(ctx->tw32);
     if (ctx->tw64) cudaFree(ctx->tw64);
     delete ctx;
@@ -183,6 +192,19 @@ const char *afg_last_error(const afg_ctx *ctx) { return ctx ? ctx->err.c_str() :
 int afg_ctx_bytes(const afg_ctx *ctx, int64_t *bytes) {
     if (!ctx || !bytes) return AFG_ERR_ARG;
     *bytes = ctx->bytes_held;
+    return AFG_OK;
+}
+
+int afg_sync(afg_ctx *ctx, void *stream) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    AFG_CUDA(ctx, cudaStreamSynchronize(S(stream)));
+    int flag = 0;
+    AFG_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        AFG_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return afg_fail(ctx, AFG_ERR_TIMEOUT, "a bounded device-side wait gave up (kernel returned early)");
+    }
     return AFG_OK;
 }
 

@@ -1,7 +1,467 @@
-// 1D ResNet on tcgen05 tensor cores (BF16 operands, FP32 accumulation in TMEM).
-#include "afg_internal.cuh"
+// 1D ResNet on tcgen05 tensor cores: BF16 operands in shared memory, FP32
+// accumulators in TMEM (Sec. II: ResNet with 1D convolutions and GroupNorm;
+// Sec. IX: kernel length 3).
+//
+// k_tiny_fused: the whole 16-channel network for one window per CTA pass,
+// persistent over windows, with every activation resident in shared memory:
+//   stem (SIMT FP32, reads the window from the whitened stream; GN statistics
+//   in a first pass, GN + ReLU + BF16 store in a second)
+//   -> per conv: one thread issues, for each 128-position M-subtile j and tap
+//      r, tcgen05.mma(M=128, N=16, K=16) with A = activation rows
+//      128 j + r .. + 127 (the tap shift is a 16-byte shift of the descriptor
+//      start) and B = the tap's 16x16 weights; the accumulators of the whole
+//      window (W/128 x 16 columns) live in TMEM.  The epilogue (16 warps)
+//      reads TMEM twice: GroupNorm statistics, then normalise (+ residual)
+//      + ReLU -> BF16 into the other activation buffer.
+//   -> head: the last epilogue keeps per-channel sums (global mean pool),
+//      then the linear layer.
+// Activation layout in shared memory (K-major, no swizzle): channel chunk c
+// (8 channels, 16 bytes) of padded row p at c * (W + 2) * 16 + p * 16, i.e.
+// core matrices of 8 rows x 16 B with SBO = 128 B and LBO = (W + 2) * 16 B;
+// rows 0 and W + 1 are the zero padding of the k3 convolutions.
+#include <stdio.h>
 
-int launch_infer_bf16(afg_ctx *ctx, const float *, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, float *,
-                      cudaStream_t) {
-    return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "infer_windows: the BF16 tensor-core path is not built yet");
+#include <algorithm>
+#include <vector>
+
+#include "afg_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int TF_THREADS = 512;
+constexpr int TF_WARPS = TF_THREADS / 32;
+constexpr int TF_C = 16;                   // channels of the fused network
+constexpr int TF_WIMG = 3 * 2 * TF_C * 16;  // bytes of one conv's weight image (3 taps x 512 B)
+
+struct TinyArgs {
+    const float *y;
+    int64_t n_y, y_stride, first, stride, shift, n_win;
+    const float *params;            // stem w [16][2][k], stem gamma/beta, per conv gamma/beta, fc w [16], fc b
+    const unsigned char *wimg;      // n_conv x TF_WIMG bytes, BF16, shared-memory image order
+    float *logits;
+    int *err;
+    int n_conv, k_stem, W, G;
+    float eps;
+};
+
+__host__ __device__ inline int tiny_param_count(int k_stem, int n_conv) {
+    return TF_C * 2 * k_stem + 2 * TF_C + n_conv * 2 * TF_C + TF_C + 1;
+}
+
+struct Smem {
+    size_t off_a, off_b, off_w, off_p, off_s, off_r, off_misc, total;
+};
+
+__host__ __device__ inline Smem tiny_smem(int W, int n_conv, int k_stem) {
+    Smem s;
+    const size_t act = (size_t)2 * (W + 2) * 16;
+    s.off_a = 0;
+    s.off_b = act;
+    s.off_w = 2 * act;
+    s.off_p = s.off_w + (size_t)n_conv * TF_WIMG;
+    s.off_s = s.off_p + (((size_t)tiny_param_count(k_stem, n_conv) * 4 + 15) / 16) * 16;
+    s.off_r = s.off_s + 2 * TF_C * 4;
+    s.off_misc = s.off_r + (size_t)TF_WARPS * 2 * TF_C * 4;
+    s.total = s.off_misc + 64;
+    return s;
+}
+
+__device__ __forceinline__ unsigned short f2bf(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf2f(unsigned short b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+// Reduce per-thread group sums (s[g], q[g], g < G) over the block and write the
+// per-channel affine map of GroupNorm: scale[c] = rstd_g * gamma_c,
+// shift[c] = beta_c - mean_g * scale[c].  cnt = elements per group.
+template <int G>
+__device__ __forceinline__ void gn_reduce(float (&s)[TF_C], float (&q)[TF_C], float cnt, float eps,
+                                          const float *gamma, const float *beta, float *red, float *scale,
+                                          float *shift) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int g = 0; g < TF_C; ++g) {
+        if (g < G) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s[g] += __shfl_xor_sync(0xffffffffu, s[g], o);
+                q[g] += __shfl_xor_sync(0xffffffffu, q[g], o);
+            }
+        }
+    }
+    if (lane == 0) {
+        for (int g = 0; g < G; ++g) {
+            red[warp * 2 * TF_C + g] = s[g];
+            red[warp * 2 * TF_C + TF_C + g] = q[g];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < TF_C) {
+        const int c = threadIdx.x;
+        const int cg = TF_C / G;
+        const int g = c / cg;
+        float ts = 0.f, tq = 0.f;
+        for (int w = 0; w < TF_WARPS; ++w) {
+            ts += red[w * 2 * TF_C + g];
+            tq += red[w * 2 * TF_C + TF_C + g];
+        }
+        const float mean = ts / cnt;
+        const float var = fmaxf(tq / cnt - mean * mean, 0.f);
+        const float a = rsqrtf(var + eps) * gamma[c];
+        scale[c] = a;
+        shift[c] = beta[c] - mean * a;
+    }
+    __syncthreads();
+}
+
+template <int G>
+__global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs args) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int W = args.W, k = args.k_stem, pad = k / 2, n_conv = args.n_conv;
+    const Smem L = tiny_smem(W, n_conv, k);
+    unsigned char *actA = sm + L.off_a;
+    unsigned char *actB = sm + L.off_b;
+    unsigned char *wimg = sm + L.off_w;
+    float *prm = reinterpret_cast<float *>(sm + L.off_p);
+    float *scale = reinterpret_cast<float *>(sm + L.off_s);
+    float *shift = scale + TF_C;
+    float *red = reinterpret_cast<float *>(sm + L.off_r);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.off_misc);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + L.off_misc + 8);
+    int *abort_flag = reinterpret_cast<int *>(sm + L.off_misc + 12);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t act_chunk = (size_t)(W + 2) * 16;  // bytes of one 8-channel chunk
+    const int MT = W / 128;
+
+    // ---- one-time set-up: parameters, weight image, zero pad rows, barrier, TMEM
+    const int n_prm = tiny_param_count(k, n_conv);
+    for (int i = tid; i < n_prm; i += TF_THREADS) prm[i] = args.params[i];
+    for (int i = tid; i < n_conv * TF_WIMG / 16; i += TF_THREADS)
+        reinterpret_cast<uint4 *>(wimg)[i] = reinterpret_cast<const uint4 *>(args.wimg)[i];
+    if (tid < 8) {
+        unsigned char *buf = (tid & 4) ? actB : actA;
+        const int c = (tid >> 1) & 1, row = (tid & 1) ? W + 1 : 0;
+        *reinterpret_cast<uint4 *>(buf + c * act_chunk + (size_t)row * 16) = make_uint4(0, 0, 0, 0);
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+        *abort_flag = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const float *stem_w = prm;
+    const float *stem_g = prm + TF_C * 2 * k;
+    const float *stem_b = stem_g + TF_C;
+    const float *conv_gb = stem_b + TF_C;           // per conv: gamma[16], beta[16]
+    const float *fc_w = conv_gb + n_conv * 2 * TF_C;
+    const float fc_b = fc_w[TF_C];
+    const uint32_t idesc = tc::idesc_bf16_f32(128, TF_C);
+    const float cnt = (float)W * (float)(TF_C / G);
+    uint32_t phase = 0;
+
+    // staging for the raw window (2 x (W + 2 pad) floats) inside buffer B, past its first pad row
+    float *xs = reinterpret_cast<float *>(actB + 16);
+    const int Wp = W + 2 * pad;
+
+    for (int64_t win = blockIdx.x; win < args.n_win; win += gridDim.x) {
+        // ---- window samples (H1 direct, L1 circularly shifted)
+        const int64_t start = args.first + win * args.stride;
+        for (int p = tid; p < Wp; p += TF_THREADS) {
+            const int tt = p - pad;
+            float a = 0.f, b = 0.f;
+            if (tt >= 0 && tt < W) {
+                a = args.y[start + tt];
+                int64_t i1 = start + args.shift + tt;
+                if (i1 >= args.n_y) i1 -= args.n_y;
+                b = args.y[args.y_stride + i1];
+            }
+            xs[p] = a;
+            xs[Wp + p] = b;
+        }
+        __syncthreads();
+        // ---- stem pass 1: GroupNorm statistics of the conv output
+        {
+            float s[TF_C], q[TF_C];
+#pragma unroll
+            for (int g = 0; g < TF_C; ++g) s[g] = q[g] = 0.f;
+            for (int t = tid; t < W; t += TF_THREADS) {
+#pragma unroll
+                for (int c = 0; c < TF_C; ++c) {
+                    float acc = 0.f;
+                    for (int r = 0; r < k; ++r) {
+                        acc = fmaf(stem_w[(c * 2 + 0) * k + r], xs[t + r], acc);
+                        acc = fmaf(stem_w[(c * 2 + 1) * k + r], xs[Wp + t + r], acc);
+                    }
+                    const int g = c / (TF_C / G);
+                    s[g] += acc;
+                    q[g] = fmaf(acc, acc, q[g]);
+                }
+            }
+            gn_reduce<G>(s, q, cnt, args.eps, stem_g, stem_b, red, scale, shift);
+        }
+        // ---- stem pass 2: GN + ReLU -> BF16 into A (rows 1..W)
+        for (int t = tid; t < W; t += TF_THREADS) {
+            unsigned short o[TF_C];
+#pragma unroll
+            for (int c = 0; c < TF_C; ++c) {
+                float acc = 0.f;
+                for (int r = 0; r < k; ++r) {
+                    acc = fmaf(stem_w[(c * 2 + 0) * k + r], xs[t + r], acc);
+                    acc = fmaf(stem_w[(c * 2 + 1) * k + r], xs[Wp + t + r], acc);
+                }
+                o[c] = f2bf(fmaxf(fmaf(acc, scale[c], shift[c]), 0.f));
+            }
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                uint4 v;
+                v.x = o[ch * 8 + 0] | ((uint32_t)o[ch * 8 + 1] << 16);
+                v.y = o[ch * 8 + 2] | ((uint32_t)o[ch * 8 + 3] << 16);
+                v.z = o[ch * 8 + 4] | ((uint32_t)o[ch * 8 + 5] << 16);
+                v.w = o[ch * 8 + 6] | ((uint32_t)o[ch * 8 + 7] << 16);
+                *reinterpret_cast<uint4 *>(actA + ch * act_chunk + (size_t)(t + 1) * 16) = v;
+            }
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+
+        float hs[TF_C];
+#pragma unroll
+        for (int c = 0; c < TF_C; ++c) hs[c] = 0.f;
+        bool aborted = false;
+        for (int l = 0; l < n_conv; ++l) {
+            const bool second = (l & 1) != 0;  // second conv of a block: residual from A
+            unsigned char *src = second ? actB : actA;
+            unsigned char *dst = second ? actA : actB;
+            const bool last = l == n_conv - 1;
+            // ---- issue the conv as MT x 3 MMAs
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t a0 = tc::smem_addr(src);
+                const uint32_t b0 = tc::smem_addr(wimg + (size_t)l * TF_WIMG);
+                for (int j = 0; j < MT; ++j) {
+                    for (int r = 0; r < 3; ++r) {
+                        const uint64_t ad = tc::desc_kmajor_noswizzle(a0 + (uint32_t)(128 * j + r) * 16,
+                                                                      (uint32_t)act_chunk, 128);
+                        const uint64_t bd = tc::desc_kmajor_noswizzle(b0 + r * 512, 256, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(j * TF_C), ad, bd, idesc, r > 0 ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(bar);
+            }
+            const bool ok = tc::mbar_wait(bar, phase & 1, 1000000000ull);
+            phase++;
+            if (!ok) {
+                atomicExch(args.err, 1);
+                *abort_flag = 1;
+            }
+            __syncthreads();
+            if (*abort_flag) {
+                aborted = true;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+            // ---- epilogue pass 1: GroupNorm statistics
+            {
+                float s[TF_C], q[TF_C];
+#pragma unroll
+                for (int g = 0; g < TF_C; ++g) s[g] = q[g] = 0.f;
+                for (int j = warp >> 2; j < MT; j += TF_WARPS / 4) {
+                    float v[16];
+                    tc::tmem_ld16(tq + (uint32_t)(j * TF_C), v);
+#pragma unroll
+                    for (int c = 0; c < TF_C; ++c) {
+                        const int g = c / (TF_C / G);
+                        s[g] += v[c];
+                        q[g] = fmaf(v[c], v[c], q[g]);
+                    }
+                }
+                const float *gb = conv_gb + l * 2 * TF_C;
+                gn_reduce<G>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift);
+            }
+            // ---- epilogue pass 2: normalise (+ residual) + ReLU -> BF16
+            for (int j = warp >> 2; j < MT; j += TF_WARPS / 4) {
+                float v[16];
+                tc::tmem_ld16(tq + (uint32_t)(j * TF_C), v);
+                const int row = 128 * j + 32 * (warp & 3) + lane + 1;
+                float res[16];
+                if (second) {
+#pragma unroll
+                    for (int ch = 0; ch < 2; ++ch) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + (size_t)row * 16);
+                        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            res[ch * 8 + 2 * e] = bf2f((unsigned short)(w4[e] & 0xffffu));
+                            res[ch * 8 + 2 * e + 1] = bf2f((unsigned short)(w4[e] >> 16));
+                        }
+                    }
+                }
+                unsigned short o[16];
+#pragma unroll
+                for (int c = 0; c < TF_C; ++c) {
+                    float val = fmaf(v[c], scale[c], shift[c]);
+                    if (second) val += res[c];
+                    val = fmaxf(val, 0.f);
+                    if (last) hs[c] += val;
+                    o[c] = f2bf(val);
+                }
+                if (!last) {
+#pragma unroll
+                    for (int ch = 0; ch < 2; ++ch) {
+                        uint4 u;
+                        u.x = o[ch * 8 + 0] | ((uint32_t)o[ch * 8 + 1] << 16);
+                        u.y = o[ch * 8 + 2] | ((uint32_t)o[ch * 8 + 3] << 16);
+                        u.z = o[ch * 8 + 4] | ((uint32_t)o[ch * 8 + 5] << 16);
+                        u.w = o[ch * 8 + 6] | ((uint32_t)o[ch * 8 + 7] << 16);
+                        *reinterpret_cast<uint4 *>(dst + ch * act_chunk + (size_t)row * 16) = u;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            tc::fence_proxy_async_smem();
+            __syncthreads();
+        }
+        if (aborted) break;
+        // ---- head: global mean pool of the last block's output, then linear
+#pragma unroll
+        for (int c = 0; c < TF_C; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hs[c] += __shfl_xor_sync(0xffffffffu, hs[c], o);
+        }
+        if (lane == 0)
+            for (int c = 0; c < TF_C; ++c) red[warp * 2 * TF_C + c] = hs[c];
+        __syncthreads();
+        if (tid == 0) {
+            float z = fc_b;
+            for (int c = 0; c < TF_C; ++c) {
+                float tot = 0.f;
+                for (int w = 0; w < TF_WARPS; ++w) tot += red[w * 2 * TF_C + c];
+                z += fc_w[c] * (tot / (float)W);
+            }
+            args.logits[win] = z;
+        }
+        __syncthreads();
+    }
+    // ---- teardown
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+bool tiny_compatible(const afg_ctx *ctx) {
+    const afg_net &n = ctx->cfg.net;
+    const int W = ctx->cfg.win_len;
+    const int g = n.groups;
+    return n.n_stages == 1 && n.widths[0] == TF_C && n.stem_stride == 1 && n.stem_pool == 0 && W % 128 == 0 &&
+           (W / 128) * TF_C <= 512 && (g == 1 || g == 2 || g == 4 || g == 8 || g == 16) &&
+           tiny_smem(W, 2 * n.blocks[0], n.stem_k).total <= 227 * 1024;
+}
+
+}  // namespace
+
+// Build the fused kernel's parameter block and BF16 weight image (device).
+int net_tc_prepare(afg_ctx *ctx) {
+    NetPlan &P = ctx->plan;
+    if (!tiny_compatible(ctx)) return AFG_OK;
+    const int k = P.net.stem_k;
+    const int n_conv = (int)P.convs.size() - 1;
+    std::vector<float> prm((size_t)tiny_param_count(k, n_conv));
+    std::vector<unsigned short> img((size_t)n_conv * TF_WIMG / 2);
+    std::vector<float> host_w;
+    // copy the device parameter image back to read the layers' weights
+    std::vector<float> all(ctx->d_params_bytes / sizeof(float));
+    AFG_CUDA(ctx, cudaMemcpy(all.data(), ctx->d_params, ctx->d_params_bytes, cudaMemcpyDeviceToHost));
+    auto at = [&](const float *dptr) { return all.data() + (dptr - ctx->d_params); };
+    size_t o = 0;
+    const ConvLayer &S = P.convs[0];
+    for (int i = 0; i < TF_C * 2 * k; ++i) prm[o++] = at(S.wt)[i];
+    for (int c = 0; c < TF_C; ++c) prm[o++] = at(S.gamma)[c];
+    for (int c = 0; c < TF_C; ++c) prm[o++] = at(S.beta)[c];
+    for (int l = 0; l < n_conv; ++l) {
+        const ConvLayer &C = P.convs[1 + l];
+        for (int c = 0; c < TF_C; ++c) prm[o++] = at(C.gamma)[c];
+        for (int c = 0; c < TF_C; ++c) prm[o++] = at(C.beta)[c];
+        // Wt[(r*cin + ci)*cout + co] -> image[l][r][chunk][co][8] (K-major, no swizzle)
+        const float *wt = at(C.wt);
+        for (int r = 0; r < 3; ++r)
+            for (int ci = 0; ci < TF_C; ++ci)
+                for (int co = 0; co < TF_C; ++co) {
+                    const float v = wt[((size_t)r * TF_C + ci) * TF_C + co];
+                    const size_t byte = (size_t)l * TF_WIMG + r * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2;
+                    __nv_bfloat16 b = __float2bfloat16_rn(v);
+                    img[byte / 2] = *reinterpret_cast<unsigned short *>(&b);
+                }
+    }
+    for (int c = 0; c < TF_C; ++c) prm[o++] = at(P.fc_w)[c];
+    prm[o++] = at(P.fc_b)[0];
+    size_t pbytes = prm.size() * sizeof(float), ibytes = img.size() * 2;
+    void *d = nullptr;
+    if (cudaMalloc(&d, pbytes + ibytes + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return afg_fail(ctx, AFG_ERR_OOM, "tensor-core weight image: cudaMalloc failed");
+    }
+    ctx->bytes_held += (int64_t)(pbytes + ibytes + 256);
+    P.tc_params = static_cast<float *>(d);
+    P.tc_wimg = static_cast<unsigned char *>(d) + ((pbytes + 255) / 256) * 256;
+    AFG_CUDA(ctx, cudaMemcpy(P.tc_params, prm.data(), pbytes, cudaMemcpyHostToDevice));
+    AFG_CUDA(ctx, cudaMemcpy(P.tc_wimg, img.data(), ibytes, cudaMemcpyHostToDevice));
+    const int smem = (int)tiny_smem(ctx->cfg.win_len, n_conv, k).total;
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return AFG_OK;
+}
+
+int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
+                      int64_t n_win, int64_t shift, float *logits, cudaStream_t st) {
+    const NetPlan &P = ctx->plan;
+    if (!tiny_compatible(ctx) || !P.tc_params)
+        return afg_fail(ctx, AFG_ERR_UNSUPPORTED,
+                        "infer_windows: the BF16 tensor-core path covers one-stage 16-channel networks");
+    const int n_conv = (int)P.convs.size() - 1;
+    const int W = ctx->cfg.win_len;
+    TinyArgs a;
+    a.y = y;
+    a.n_y = n_y;
+    a.y_stride = y_stride;
+    a.first = first;
+    a.stride = stride;
+    a.shift = shift;
+    a.n_win = n_win;
+    a.params = P.tc_params;
+    a.wimg = P.tc_wimg;
+    a.logits = logits;
+    a.err = ctx->d_err;
+    a.n_conv = n_conv;
+    a.k_stem = P.net.stem_k;
+    a.W = W;
+    a.G = P.net.groups;
+    a.eps = P.net.eps;
+    const Smem L = tiny_smem(W, n_conv, a.k_stem);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const unsigned grid = (unsigned)std::min<int64_t>(n_win, std::max(sms, 1));
+    const double flops_conv = 2.0 * n_win * W * TF_C * (3.0 * TF_C) * n_conv;
+    const double flops_stem = 2.0 * n_win * W * TF_C * 2.0 * a.k_stem;
+    KScope ks(ctx, st, KK_TINY_TC, flops_conv + flops_stem, (double)n_win * (2.0 * W * 4.0 + 4.0));
+    switch (a.G) {
+        case 1: k_tiny_fused<1><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 2: k_tiny_fused<2><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 4: k_tiny_fused<4><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 8: k_tiny_fused<8><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        default: k_tiny_fused<16><<<grid, TF_THREADS, L.total, st>>>(a); break;
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_tiny_fused");
+    return AFG_OK;
 }

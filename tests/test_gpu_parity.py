@@ -216,3 +216,42 @@ def test_resnet34_hour_sampled_windows():
         want = orc.network(wl.net, w, white[:, off: off + wl.win_len])
         assert abs(lg[j] - want) < LOGIT_TOL * (1 + abs(want)), (j, lg[j], want)
     ctx.close()
+
+
+# ---------------------------------------------------------------- BF16 tensor-core network
+# BF16 operands (8-bit mantissa, relative rounding 2^-9 per operand) through
+# four GroupNorm'd convolutions: the logit error is bounded here by
+# 5e-2 (1 + |z|); the measured maximum is printed.
+BF16_LOGIT_TOL = 5e-2
+
+
+@pytest.fixture(scope="module")
+def ctx_tiny_bf16(c1):
+    wl, x, w, _ = c1
+    ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
+    yield ctx
+    ctx.close()
+
+
+def test_bf16_tiny_logits_against_oracle(c1, ctx_tiny_bf16, capsys):
+    wl, x, w, ref = c1
+    yd = _dev(ref["white"].astype(np.float32))
+    for shift, first, n_win in [(0, 0, 244), (2048 * 5, 7, 301 - 7 - 6), (0, 0, 1)]:
+        if first + (n_win - 1) * 512 + 3072 > yd.shape[1]:
+            n_win = (yd.shape[1] - 3072 - first) // 512 + 1
+        got = ctx_tiny_bf16.infer_windows(yd, first, 512, n_win, shift).cpu().numpy()
+        ctx_tiny_bf16.sync()
+        want = orc.infer_windows(wl.net, w, ref["white"], wl.win_len, first, 512, n_win, shift)
+        err = np.abs(got - want) / (1 + np.abs(want))
+        with capsys.disabled():
+            print(f"\nBF16 tiny net: shift {shift} first {first} n_win {n_win}: max |dz|/(1+|z|) = {err.max():.3e}")
+        assert err.max() < BF16_LOGIT_TOL, err.max()
+
+
+def test_bf16_precision_c1_peaks_within_one_sample(c1, ctx_tiny_bf16):
+    wl, x, w, ref = c1
+    logits, stat, trig, n_trig = ctx_tiny_bf16.analyze(_dev(x))
+    ctx_tiny_bf16.sync()
+    st = stat.cpu().numpy()
+    n = int(n_trig.item())
+    _trigger_match(st, ref["stat"], trig.cpu().numpy()[:n], ref["triggers"], wl.cluster_half, BF16_LOGIT_TOL)
