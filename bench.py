@@ -162,6 +162,8 @@ def oracle_sample(wl, x: np.ndarray, w: np.ndarray, n_epochs: int, n_windows: in
 def workload_by_name(name: str, n_win: int = 0):
     if name == "hour":
         wl = inputs.HOUR_RESNET34
+    elif name == "timeslides":
+        return inputs.TIMESLIDE_DAY
     elif name == "plain64":
         wl = inputs.PLAIN_64S
     else:
@@ -179,6 +181,32 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def roofline_for(dom: dict, peaks: dict, step_ms_total: float) -> dict:
+    """Roofline of the dominant kernel from its live CUDA-event time and algorithmic work."""
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    name = dom["name"]
+    if name.startswith("conv_gemm_fp32"):
+        bound, unit = "alu", "TFLOP/s"
+        achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        src = f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x {sm_max:g} MHz"
+    elif "bf16" in name:
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        src = f"{peaks['_source']} bf16_tflops_sustained"
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = dom["algo_bytes"] / (dom["total_ms"] / 1000.0) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        src = f"{peaks['_source']} hbm_gbs"
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "peak_source": src,
+            "traffic": measured_traffic(name, dom["algo_bytes"] / max(dom["launches"], 1)),
+            "launches": dom["launches"], "ms_per_launch": dom["total_ms"] / max(dom["timed"], 1),
+            "share_of_step": dom["total_ms"] / max(step_ms_total, 1e-9)}
 
 
 def run_reference(args):
@@ -300,28 +328,7 @@ def run_ours(args):
     peaks = load_peaks()
     launches = int(sum(k["launches"] for k in kstats))
     dom = max(kstats, key=lambda k: k["total_ms"])
-    per_launch_ms = dom["total_ms"] / max(dom["timed"], 1)
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if dom["name"].startswith("conv_gemm_fp32"):
-        bound, unit = "alu", "TFLOP/s"
-        achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
-        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        peak_src = f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x {sm_max:g} MHz"
-    elif dom["name"].startswith("conv_gemm_bf16"):
-        bound, unit = "tensor", "TFLOP/s"
-        achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak_src = f"{peaks['_source']} bf16_tflops_sustained"
-    else:
-        bound, unit = "hbm", "GB/s"
-        achieved = dom["algo_bytes"] / (dom["total_ms"] / 1000.0) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        peak_src = f"{peaks['_source']} hbm_gbs"
-    traffic = measured_traffic(dom["name"], dom["algo_bytes"] / max(dom["launches"], 1))
-    roofline = {"kernel": dom["name"], "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
-                "launches": dom["launches"], "ms_per_launch": per_launch_ms,
-                "share_of_step": dom["total_ms"] / max(total_ms, 1e-9)}
+    roofline = roofline_for(dom, peaks, total_ms)
     kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
                            "share": round(k["total_ms"] / max(sum(q["total_ms"] for q in kstats), 1e-9), 4)}
                for k in kstats}
@@ -347,14 +354,109 @@ def run_ours(args):
     return 0
 
 
+def run_timeslides(args):
+    """One step = the whole timeslide background of ~1 day: whitening of every
+    segment, every window of every (segment, timeslide) series through the
+    network in one persistent launch, integration and clustering of every
+    series; replayed as one CUDA graph."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_18661_gb300 import abi
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = inputs.TIMESLIDE_DAY
+    lengths = inputs.segment_lengths(n_seg=40, total_s=86400)[: args.n_seg]
+    x, segs = inputs.make_segments(lengths, seed=wl.seed + 7919 * rank, chirp_every_s=300.0)
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    precision = abi.AFG_BF16 if args.precision == "bf16" else abi.AFG_FP32
+    ctx = abi.Context(wl, w, precision=precision)
+    xd = torch.from_numpy(x).to(dev)
+    n_win, tw, ts = ctx.batch_layout(segs, args.n_shift, wl.fs)
+    livetime = tw * wl.stride / wl.fs  # background seconds analysed per step
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    out = None
+    with torch.cuda.stream(stream):
+        # one uninstrumented direct call for the per-kernel shares, then the captured graph
+        ctx.profile_enable(True)
+        out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, out=out, stream=stream)
+        kstats = ctx.profile_read()
+        for _ in range(args.warmup):
+            out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, use_graph=True, out=out, stream=stream)
+    barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ctx.profile_enable(False)
+    evs = []
+    barrier()
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.batch_run(xd, segs, args.n_shift, wl.fs, use_graph=True, out=out, stream=stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+    barrier()
+    ctx.sync(stream)
+    clocks = sampler.stop() if sampler else None
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * livetime * args.steps / (total_ms / 1000.0)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    peaks = load_peaks()
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    launches_per_step = int(sum(k["launches"] for k in kstats))
+    roofline = roofline_for(dom, peaks, sum(k["total_ms"] for k in kstats))
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3)} for k in kstats}
+    res = {"metric": "strain-seconds/s whiten+ResNet (timeslide background livetime)", "value": value,
+           "unit": "strain-s/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16" if precision == abi.AFG_BF16 else "f32", "data": "synthetic",
+           "config": {"workload": wl.name, "segments": len(segs), "strain_s": int(sum(lengths)),
+                      "timeslides": args.n_shift, "windows": tw, "livetime_s": livetime,
+                      "graph": "one CUDA graph per step", "l2": "flushed between steps (512 MiB write)"},
+           "roofline": roofline, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+           "kernels_direct_call": kernels}
+    print(json.dumps(res), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="hour", choices=["hour", "plain64"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--workload", default="hour", choices=["hour", "plain64", "timeslides"])
+    ap.add_argument("--n-shift", type=int, default=100, help="timeslides per segment (timeslides workload)")
+    ap.add_argument("--n-seg", type=int, default=40, help="segments (timeslides workload)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16"],
+                    help="default: fp32 for hour and plain64, bf16 for timeslides")
     ap.add_argument("--ref-windows", type=int, default=32)
     ap.add_argument("--n-win", type=int, default=0, help="analyse this many windows instead (smaller workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -362,8 +464,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.precision is None:
+        args.precision = "bf16" if args.workload == "timeslides" else "fp32"
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "timeslides":
+        return run_timeslides(args)
     return run_ours(args)
 
 

@@ -69,7 +69,7 @@ typedef struct afg_net {
     int32_t stem_pool;   /* 0 or 1 */
     int32_t groups;      /* GroupNorm groups; divides every width */
     int32_t n_stages;    /* 1..4 */
-    int32_t widths[4];   /* multiples of 16, <= 512 */
+    int32_t widths[4];   /* powers of two in [16, 512] */
     int32_t blocks[4];   /* >= 1 */
     float eps;           /* GroupNorm epsilon */
 } afg_net;
@@ -212,6 +212,54 @@ int afg_analyze(afg_ctx *ctx, const float *x, const afg_run_params *p, float *lo
 int afg_analyze_host(afg_ctx *ctx, const float *x_host, const afg_run_params *p, float *stat_host,
                      int64_t *trig_idx_host, int64_t trig_cap, int64_t *n_trig_host, void *stream);
 
+
+
+/* ---------------------------------------------------------------- timeslide batches */
+
+/* One strain segment inside a longer two-detector buffer. */
+typedef struct afg_segment {
+    int64_t offset; /* first raw sample of the segment in each detector row */
+    int64_t n_raw;  /* raw samples of the segment */
+} afg_segment;
+
+typedef struct afg_batch_params {
+    int64_t psd_len;      /* PSD look-back (64 s = 131072 samples); nfft + a multiple of hop */
+    int64_t epoch_len;    /* PSD epoch (8 s = 16384 samples); a multiple of 8192 */
+    int64_t stride;       /* window stride in samples */
+    int64_t shift_step;   /* timeslide step in samples (1 s = fs) */
+    int32_t n_shift;      /* timeslides k = 1 .. n_shift (zero lag is not background) */
+    int32_t n_int;        /* integration length in windows */
+    int32_t cluster_half; /* trigger half-width in statistic samples */
+    int32_t use_graph;    /* 1: capture the whole batch into a CUDA graph on the first call
+                             and replay it while the arguments stay the same */
+} afg_batch_params;
+
+/* Sizes of a batch (host only, no GPU work): for every segment, the windows
+ * of one timeslide (n_win_host[i], may be NULL), the total windows over all
+ * segments and timeslides, and the total statistic samples.  Segment i is
+ * analysed in epoch mode (Sec. VI: the first 64 s estimate the PSD and the
+ * rest is whitened): it yields floor((n_raw - psd_len - fir_len/2) /
+ * epoch_len) whole epochs of whitened data and (n_white - W)/stride + 1
+ * windows.  AFG_ERR_ARG if a segment is too short for one epoch, n_int
+ * windows, or n_shift * shift_step whitened samples. */
+int afg_batch_layout(afg_ctx *ctx, const afg_segment *segs_host, int32_t n_seg, const afg_batch_params *p,
+                     int64_t *n_win_host, int64_t *total_windows, int64_t *total_stat);
+
+/* Timeslide background over many segments in one call (Sec. IX: Hanford
+ * fixed, Livingston shifted in 1 s steps until the livetime is reached).
+ * Each detector of each segment is whitened once on its own axis (epoch
+ * mode); series s = i * n_shift + (k - 1) pairs H1 of segment i with its L1
+ * circularly shifted by k * shift_step samples within the segment's whitened
+ * span.  All windows of all series go through one persistent network launch.
+ * Outputs, concatenated in series order: logits [total_windows] (may be
+ * NULL: a context workspace is used), stat [total_stat] (each series
+ * integrated on its own, valid mode), and the triggers of every series (its
+ * own 8 s clustering) as indices into stat, in increasing order; *n_trig
+ * (device) is their count (only trig_cap are written).
+ * x: [2][x_len] float32, segments given by offset/n_raw. */
+int afg_batch_run(afg_ctx *ctx, const float *x, int64_t x_len, const afg_segment *segs_host, int32_t n_seg,
+                  const afg_batch_params *p, float *logits, float *stat, int64_t *trig_idx, int64_t trig_cap,
+                  int64_t *n_trig, void *stream);
 
 /* ---------------------------------------------------------------- profiling */
 

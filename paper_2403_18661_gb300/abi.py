@@ -52,6 +52,16 @@ class AfgRunParams(ctypes.Structure):
                 ("n_int", ctypes.c_int32), ("cluster_half", ctypes.c_int32)]
 
 
+class AfgSegment(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int64), ("n_raw", ctypes.c_int64)]
+
+
+class AfgBatchParams(ctypes.Structure):
+    _fields_ = [("psd_len", ctypes.c_int64), ("epoch_len", ctypes.c_int64), ("stride", ctypes.c_int64),
+                ("shift_step", ctypes.c_int64), ("n_shift", ctypes.c_int32), ("n_int", ctypes.c_int32),
+                ("cluster_half", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -73,6 +83,10 @@ SIGNATURES = {
     "afg_integrate": ([_vp, _vp, _i64, _i32, _i32, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "afg_analyze": ([_vp, _vp, ctypes.POINTER(AfgRunParams), _vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "afg_analyze_host": ([_vp, _vp, ctypes.POINTER(AfgRunParams), _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "afg_batch_layout": ([_vp, _vp, _i32, ctypes.POINTER(AfgBatchParams), _vp, ctypes.POINTER(_i64),
+                          ctypes.POINTER(_i64)], ctypes.c_int),
+    "afg_batch_run": ([_vp, _vp, _i64, _vp, _i32, ctypes.POINTER(AfgBatchParams), _vp, _vp, _vp, _i64, _vp, _vp],
+                      ctypes.c_int),
     "afg_profile_enable": ([_vp, _i32], ctypes.c_int),
     "afg_profile_read": ([_vp, ctypes.POINTER(AfgKernelStat), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_psd_estimate_noalloc": ([_vp, _i64, _i32, _i64, _i64, _i64, _i32, _i32, _vp, _vp], ctypes.c_int),
@@ -269,6 +283,44 @@ class Context:
         logits, stat, trig, n_trig = out
         self._check(self._lib.afg_analyze(self._h, _ptr(x), ctypes.byref(p), _ptr(logits), _ptr(stat), _ptr(trig),
                                           trig_cap, _ptr(n_trig), _stream(stream)))
+        return logits, stat, trig, n_trig
+
+    # ---------------------------------------------------------------- timeslide batches
+    def _batch_args(self, segments, n_shift: int, shift_step: int, use_graph: bool):
+        wl = self.workload
+        segs = (AfgSegment * len(segments))()
+        for i, (off, n) in enumerate(segments):
+            segs[i].offset, segs[i].n_raw = off, n
+        p = AfgBatchParams()
+        p.psd_len, p.epoch_len, p.stride, p.shift_step = wl.psd_len, wl.epoch_len, wl.stride, shift_step
+        p.n_shift, p.n_int, p.cluster_half, p.use_graph = n_shift, wl.n_int, wl.cluster_half, int(use_graph)
+        return segs, p
+
+    def batch_layout(self, segments, n_shift: int, shift_step: int):
+        """(windows per timeslide of each segment, total windows, total statistic samples)."""
+        segs, p = self._batch_args(segments, n_shift, shift_step, False)
+        n_win = (ctypes.c_int64 * len(segments))()
+        tw, ts = _i64(), _i64()
+        self._check(self._lib.afg_batch_layout(self._h, segs, len(segments), ctypes.byref(p), n_win, ctypes.byref(tw),
+                                               ctypes.byref(ts)))
+        return list(n_win), tw.value, ts.value
+
+    def batch_run(self, x, segments, n_shift: int, shift_step: int, trig_cap: int = 1 << 20, use_graph: bool = False,
+                  out=None, stream=None):
+        """Timeslide background over `segments` [(offset, n_raw)] of device strain x [2][x_len]:
+        returns (logits, stat, trig_idx, n_trig) device tensors, concatenated in series order."""
+        import torch
+        segs, p = self._batch_args(segments, n_shift, shift_step, use_graph)
+        _, tw, ts = self.batch_layout(segments, n_shift, shift_step)
+        if out is None:
+            out = (torch.empty(tw, dtype=torch.float32, device=x.device),
+                   torch.empty(ts, dtype=torch.float32, device=x.device),
+                   torch.empty(max(trig_cap, 1), dtype=torch.int64, device=x.device),
+                   torch.zeros(1, dtype=torch.int64, device=x.device))
+        logits, stat, trig, n_trig = out
+        self._check(self._lib.afg_batch_run(self._h, _ptr(x), x.shape[1], segs, len(segments), ctypes.byref(p),
+                                            _ptr(logits), _ptr(stat), _ptr(trig), trig_cap, _ptr(n_trig),
+                                            _stream(stream)))
         return logits, stat, trig, n_trig
 
     def analyze_host(self, x_host: np.ndarray, shift: int = 0, trig_cap: int = 4096, stat_out=None, trig_out=None,

@@ -50,6 +50,16 @@ struct NetPlan {
     unsigned char *tc_wimg = nullptr;  // and BF16 weight image in shared-memory order
 };
 
+// One segment of a timeslide batch: its whitened span in the concatenated
+// whitened buffer and the windows it contributes (n_shift x n_win).
+struct SegDesc {
+    int64_t y_off;        // first whitened sample of the segment (per detector row)
+    int64_t n_y;          // whitened samples of the segment
+    int64_t n_win;        // windows per timeslide
+    int64_t win_first;    // first global window index of the segment (all its timeslides)
+    int64_t shift_first;  // timeslide step of the segment's first series (1 for k = 1)
+};
+
 struct Workspace {
     void *p = nullptr;
     size_t bytes = 0;
@@ -93,8 +103,11 @@ struct Prof {
     double bytes[KK_COUNT] = {};
 };
 
+struct BatchCache;
+
 struct afg_ctx {
     Prof prof;
+    BatchCache *batch = nullptr;      // captured timeslide-batch graph (batch.cu)
     afg_config cfg;
     int device = 0;
     std::string err;
@@ -105,7 +118,7 @@ struct afg_ctx {
     double2 *tw64 = nullptr;          // same in double
     int64_t bytes_held = 0;
     int *d_err = nullptr;             // device-side failure record (bounded waits that gave up)
-    Workspace ws[16];
+    Workspace ws[24];
 };
 
 // workspace slots
@@ -124,6 +137,8 @@ enum {
     WS_X,
     WS_TRIG,
     WS_SCAN,
+    WS_BATCH_SEGS,
+    WS_BATCH_SERIES,
 };
 
 struct KScope {
@@ -141,6 +156,7 @@ struct KScope {
 int afg_fail(afg_ctx *ctx, int code, const char *fmt, ...);
 int afg_cuda_fail(afg_ctx *ctx, cudaError_t e, const char *what);
 int afg_ws_reserve(afg_ctx *ctx, int slot, size_t bytes, void **out);
+void batch_cache_release(afg_ctx *ctx);
 
 #define AFG_CUDA(ctx, call)                                   \
     do {                                                      \
@@ -159,11 +175,12 @@ int afg_ws_reserve(afg_ctx *ctx, int slot, size_t bytes, void **out);
 // ----------------------------------------------------------------------------
 // spectral.cu
 int afg_make_twiddles(afg_ctx *ctx);
+// x_stride: samples between detector rows of x (0: n)
 int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step,
-               int64_t psd_span, double *psd, cudaStream_t st);
+               int64_t psd_span, double *psd, cudaStream_t st, int64_t x_stride = 0);
 int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const double *psd, int64_t n_psd,
                   int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, int64_t y_stride,
-                  cudaStream_t st);
+                  cudaStream_t st, int64_t x_stride = 0);
 cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step, int64_t psd_span,
                           int hop, int fs, const float2 *tw, double *P, double *psd, cudaStream_t st);
 cudaError_t prepare_psd_kernels();
@@ -173,6 +190,8 @@ int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 // net_tc.cu
 int net_tc_prepare(afg_ctx *ctx);
+int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, const SegDesc *segs_dev, int n_seg,
+                            int64_t total_win, int64_t stride, int64_t shift_step, float *logits, cudaStream_t st);
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 // integrate.cu

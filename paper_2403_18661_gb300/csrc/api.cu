@@ -80,9 +80,8 @@ static int check_net(const afg_net *n, char *why, size_t len) {
     if (!(n->eps > 0.f)) { snprintf(why, len, "net.eps must be > 0"); return 0; }
     for (int s = 0; s < n->n_stages; ++s) {
         int w = n->widths[s];
-        if (w < 16 || w > 512 || w % 16) { snprintf(why, len, "net.widths[%d] must be a multiple of 16 in [16, 512]", s); return 0; }
+        if (w < 16 || w > 512 || (w & (w - 1))) { snprintf(why, len, "net.widths[%d] must be a power of two in [16, 512]", s); return 0; }
         if (w % n->groups) { snprintf(why, len, "net.groups must divide widths[%d]", s); return 0; }
-        if (w > 256 && w % 256) { snprintf(why, len, "net.widths[%d] above 256 must be a multiple of 256", s); return 0; }
         if (n->blocks[s] < 1 || n->blocks[s] > 64) { snprintf(why, len, "net.blocks[%d] must be 1..64", s); return 0; }
     }
     return 1;
@@ -176,6 +175,7 @@ int afg_ctx_destroy(afg_ctx *ctx) {
     if (!ctx) return AFG_ERR_ARG;
     cudaDeviceSynchronize();
     prof_release(ctx);
+    batch_cache_release(ctx);
     for (auto &w : ctx->ws)
         if (w.p) cudaFree(w.p);
     if (ctx->d_params) cudaFree(ctx->d_params);

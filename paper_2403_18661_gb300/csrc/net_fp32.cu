@@ -64,69 +64,121 @@ __global__ void k_stem(const float *__restrict__ y, int64_t n_y, int64_t y_strid
 }
 
 // ---------------------------------------------------------------- GroupNorm
-// grid (n_win), block 32*G (one warp per group).  x: [n_win][L+2][C] padded,
-// normalised in place; res (optional) same layout, added before ReLU; if
-// pool_out is given, the result is max-pooled (k3, s2, p1) into
-// pool_out [n_win][L/2 + 2][C] instead (x left untouched).
-// Pad rows of the written tile are set to zero.
-__global__ void k_groupnorm(float *__restrict__ x, int L, int C, int G, const float *__restrict__ gamma,
-                            const float *__restrict__ beta, float eps, const float *__restrict__ res, int relu,
-                            float *__restrict__ pool_out) {
-    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// grid (n_win), block GN_T.  x: [n_win][L+2][C] padded, normalised in place;
+// res (optional) same layout, added before ReLU; if pool_out is given, the
+// result is max-pooled (k3, s2, p1) into pool_out [n_win][L/2 + 2][C]
+// instead (x left untouched).  Pad rows of the written tile are set to zero.
+// Thread t reads float4 chunks t, t + GN_T, ... of the tile; since C/4
+// divides GN_T, its 4 channels are fixed.  Per-channel partial sums are
+// reduced in a fixed order (two passes: mean, then centred variance).
+constexpr int GN_T = 256;
+
+__device__ __forceinline__ void gn_channel_reduce(float (&a)[4], float *red, float *chs, int C) {
+    // red: [GN_T][4] partials; chs: [C] per-channel totals
+    const int tid = threadIdx.x;
+    for (int e = 0; e < 4; ++e) red[tid * 4 + e] = a[e];
+    __syncthreads();
+    const int q = C / 4;  // channel quads
+    for (int c = tid; c < C; c += GN_T) {
+        const int quad = c / 4, e = c % 4;
+        float s = 0.f;
+        for (int t = quad; t < GN_T; t += q) s += red[t * 4 + e];
+        chs[c] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(GN_T) k_groupnorm(float *__restrict__ x, int L, int C, int G,
+                                                    const float *__restrict__ gamma, const float *__restrict__ beta,
+                                                    float eps, const float *__restrict__ res, int relu,
+                                                    float *__restrict__ pool_out) {
+    __shared__ float red[GN_T * 4];
+    __shared__ float chs[512];
+    __shared__ float gmean[32], grstd[32];
+    const int tid = threadIdx.x;
     const int cg = C / G;
     const int64_t tile = (int64_t)(L + 2) * C;
     float *xt = x + (int64_t)blockIdx.x * tile + C;  // row 0 of data
-    const int cnt = L * cg;
-    float s = 0.f;
-    for (int e = lane; e < cnt; e += 32) {
-        int row = e / cg, c = g * cg + (e - row * cg);
-        s += xt[(int64_t)row * C + c];
+    const int n4 = L * C / 4;
+    const int c0 = (tid % (C / 4)) * 4;  // first channel of this thread's float4s
+    const float4 *x4 = reinterpret_cast<const float4 *>(xt);
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = tid; i < n4; i += GN_T) {
+        const float4 v = x4[i];
+        a[0] += v.x; a[1] += v.y; a[2] += v.z; a[3] += v.w;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const float mu = s / (float)cnt;
-    float v = 0.f;
-    for (int e = lane; e < cnt; e += 32) {
-        int row = e / cg, c = g * cg + (e - row * cg);
-        float d = xt[(int64_t)row * C + c] - mu;
-        v = fmaf(d, d, v);
+    gn_channel_reduce(a, red, chs, C);
+    if (tid < G) {
+        float s = 0.f;
+        for (int c = tid * cg; c < (tid + 1) * cg; ++c) s += chs[c];
+        gmean[tid] = s / (float)(L * cg);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const float rstd = rsqrtf(v / (float)cnt + eps);
+    __syncthreads();
+    float mu[4];
+    for (int e = 0; e < 4; ++e) mu[e] = gmean[(c0 + e) / cg];
+    for (int e = 0; e < 4; ++e) a[e] = 0.f;
+    for (int i = tid; i < n4; i += GN_T) {
+        const float4 v = x4[i];
+        float d;
+        d = v.x - mu[0]; a[0] = fmaf(d, d, a[0]);
+        d = v.y - mu[1]; a[1] = fmaf(d, d, a[1]);
+        d = v.z - mu[2]; a[2] = fmaf(d, d, a[2]);
+        d = v.w - mu[3]; a[3] = fmaf(d, d, a[3]);
+    }
+    gn_channel_reduce(a, red, chs, C);
+    if (tid < G) {
+        float s = 0.f;
+        for (int c = tid * cg; c < (tid + 1) * cg; ++c) s += chs[c];
+        grstd[tid] = rsqrtf(s / (float)(L * cg) + eps);
+    }
+    __syncthreads();
+    float sc[4], sh[4];
+    for (int e = 0; e < 4; ++e) {
+        const int c = c0 + e, g = c / cg;
+        sc[e] = grstd[g] * gamma[c];
+        sh[e] = beta[c] - gmean[g] * sc[e];
+    }
     if (pool_out == nullptr) {
-        const float *rt = res ? res + (int64_t)blockIdx.x * tile + C : nullptr;
-        for (int e = lane; e < cnt; e += 32) {
-            int row = e / cg, c = g * cg + (e - row * cg);
-            int64_t a = (int64_t)row * C + c;
-            float val = (xt[a] - mu) * rstd * gamma[c] + beta[c];
-            if (rt) val += rt[a];
-            if (relu) val = fmaxf(val, 0.f);
-            xt[a] = val;
+        const float4 *r4 = res ? reinterpret_cast<const float4 *>(res + (int64_t)blockIdx.x * tile + C) : nullptr;
+        float4 *w4 = reinterpret_cast<float4 *>(xt);
+        for (int i = tid; i < n4; i += GN_T) {
+            float4 v = x4[i];
+            float o[4] = {fmaf(v.x, sc[0], sh[0]), fmaf(v.y, sc[1], sh[1]), fmaf(v.z, sc[2], sh[2]),
+                          fmaf(v.w, sc[3], sh[3])};
+            if (r4) {
+                const float4 r = r4[i];
+                o[0] += r.x; o[1] += r.y; o[2] += r.z; o[3] += r.w;
+            }
+            if (relu)
+                for (int e = 0; e < 4; ++e) o[e] = fmaxf(o[e], 0.f);
+            w4[i] = make_float4(o[0], o[1], o[2], o[3]);
         }
-        for (int e = lane; e < cg; e += 32) {
-            int c = g * cg + e;
+        for (int c = tid; c < C; c += GN_T) {
             xt[-C + c] = 0.f;
             xt[(int64_t)L * C + c] = 0.f;
         }
     } else {
         const int Lp = (L + 2 - 3) / 2 + 1;
         float *po = pool_out + (int64_t)blockIdx.x * (Lp + 2) * C + C;
-        const int pcnt = Lp * cg;
-        for (int e = lane; e < pcnt; e += 32) {
-            int row = e / cg, c = g * cg + (e - row * cg);
-            float m = -INFINITY;
+        float4 *p4 = reinterpret_cast<float4 *>(po);
+        const int C4 = C / 4;
+        for (int i = tid; i < Lp * C4; i += GN_T) {
+            const int row = i / C4, q = i - row * C4;
+            float m[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
             for (int r = -1; r <= 1; ++r) {
-                int src = 2 * row + r;
+                const int src = 2 * row + r;
                 if (src < 0 || src >= L) continue;
-                float val = (xt[(int64_t)src * C + c] - mu) * rstd * gamma[c] + beta[c];
-                if (relu) val = fmaxf(val, 0.f);
-                m = fmaxf(m, val);
+                const float4 v = x4[(int64_t)src * C4 + q];
+                float o[4] = {fmaf(v.x, sc[0], sh[0]), fmaf(v.y, sc[1], sh[1]), fmaf(v.z, sc[2], sh[2]),
+                              fmaf(v.w, sc[3], sh[3])};
+                for (int e = 0; e < 4; ++e) {
+                    if (relu) o[e] = fmaxf(o[e], 0.f);
+                    m[e] = fmaxf(m[e], o[e]);
+                }
             }
-            po[(int64_t)row * C + c] = m;
+            p4[i] = make_float4(m[0], m[1], m[2], m[3]);
         }
-        for (int e = lane; e < cg; e += 32) {
-            int c = g * cg + e;
+        for (int c = tid; c < C; c += GN_T) {
             po[-C + c] = 0.f;
             po[(int64_t)Lp * C + c] = 0.f;
         }
@@ -286,7 +338,7 @@ void gn_launch(afg_ctx *ctx, float *x, int nw, int L, int C, int G, const float 
     double bytes = tile * (res ? 3.0 : 2.0);
     if (pool_out) bytes = tile * 1.5;
     KScope ks(ctx, st, KK_GROUPNORM, 0.0, bytes);
-    k_groupnorm<<<nw, 32 * G, 0, st>>>(x, L, C, G, gamma, beta, eps, res, relu, pool_out);
+    k_groupnorm<<<nw, GN_T, 0, st>>>(x, L, C, G, gamma, beta, eps, res, relu, pool_out);
 }
 
 }  // namespace

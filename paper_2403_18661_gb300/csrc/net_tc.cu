@@ -37,6 +37,9 @@ constexpr int TF_WIMG = 3 * 2 * TF_C * 16;  // bytes of one conv's weight image 
 struct TinyArgs {
     const float *y;
     int64_t n_y, y_stride, first, stride, shift, n_win;
+    const SegDesc *segs;            // batch mode (n_seg > 0): per-segment window descriptors
+    int n_seg;
+    int64_t shift_step;
     const float *params;            // stem w [16][2][k], stem gamma/beta, per conv gamma/beta, fc w [16], fc b
     const unsigned char *wimg;      // n_conv x TF_WIMG bytes, BF16, shared-memory image order
     float *logits;
@@ -172,16 +175,34 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     const int Wp = W + 2 * pad;
 
     for (int64_t win = blockIdx.x; win < args.n_win; win += gridDim.x) {
-        // ---- window samples (H1 direct, L1 circularly shifted)
-        const int64_t start = args.first + win * args.stride;
+        // ---- locate the window: single series, or (segment, timeslide, window) in batch mode
+        const float *y0 = args.y;
+        int64_t n_y = args.n_y, start = args.first + win * args.stride, l1_shift = args.shift, out = win;
+        if (args.n_seg > 0) {
+            int lo = 0, hi = args.n_seg - 1;  // last segment with win_first <= win
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (args.segs[mid].win_first <= win) lo = mid;
+                else hi = mid - 1;
+            }
+            const SegDesc sd = args.segs[lo];
+            const int64_t local = win - sd.win_first;
+            const int64_t k = local / sd.n_win;  // timeslide index (0-based)
+            const int64_t j = local - k * sd.n_win;
+            y0 = args.y + sd.y_off;
+            n_y = sd.n_y;
+            start = j * args.stride;
+            l1_shift = (sd.shift_first + k) * args.shift_step;
+            out = win;
+        }
+        const float *y1 = y0 + args.y_stride;
         for (int p = tid; p < Wp; p += TF_THREADS) {
             const int tt = p - pad;
             float a = 0.f, b = 0.f;
             if (tt >= 0 && tt < W) {
-                a = args.y[start + tt];
-                int64_t i1 = start + args.shift + tt;
-                if (i1 >= args.n_y) i1 -= args.n_y;
-                b = args.y[args.y_stride + i1];
+                a = y0[start + tt];
+                int64_t i1 = (start + l1_shift + tt) % n_y;
+                b = y1[i1];
             }
             xs[p] = a;
             xs[Wp + p] = b;
@@ -347,7 +368,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 for (int w = 0; w < TF_WARPS; ++w) tot += red[w * 2 * TF_C + c];
                 z += fc_w[c] * (tot / (float)W);
             }
-            args.logits[win] = z;
+            args.logits[out] = z;
         }
         __syncthreads();
     }
@@ -423,6 +444,50 @@ int net_tc_prepare(afg_ctx *ctx) {
     return AFG_OK;
 }
 
+int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, const SegDesc *segs_dev, int n_seg,
+                            int64_t total_win, int64_t stride, int64_t shift_step, float *logits, cudaStream_t st) {
+    const NetPlan &P = ctx->plan;
+    if (!tiny_compatible(ctx) || !P.tc_params)
+        return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "batch: the BF16 path covers one-stage 16-channel networks");
+    const int n_conv = (int)P.convs.size() - 1;
+    const int W = ctx->cfg.win_len;
+    TinyArgs a;
+    a.y = white;
+    a.n_y = 0;
+    a.y_stride = y_stride;
+    a.first = 0;
+    a.stride = stride;
+    a.shift = 0;
+    a.n_win = total_win;
+    a.segs = segs_dev;
+    a.n_seg = n_seg;
+    a.shift_step = shift_step;
+    a.params = P.tc_params;
+    a.wimg = P.tc_wimg;
+    a.logits = logits;
+    a.err = ctx->d_err;
+    a.n_conv = n_conv;
+    a.k_stem = P.net.stem_k;
+    a.W = W;
+    a.G = P.net.groups;
+    a.eps = P.net.eps;
+    const Smem L = tiny_smem(W, n_conv, a.k_stem);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const unsigned grid = (unsigned)std::min<int64_t>(total_win, std::max(sms, 1));
+    const double flops = 2.0 * total_win * W * TF_C * ((3.0 * TF_C) * n_conv + 2.0 * a.k_stem);
+    KScope ks(ctx, st, KK_TINY_TC, flops, (double)total_win * (2.0 * W * 4.0 + 4.0));
+    switch (a.G) {
+        case 1: k_tiny_fused<1><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 2: k_tiny_fused<2><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 4: k_tiny_fused<4><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 8: k_tiny_fused<8><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        default: k_tiny_fused<16><<<grid, TF_THREADS, L.total, st>>>(a); break;
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_tiny_fused(batch)");
+    return AFG_OK;
+}
+
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
                       int64_t n_win, int64_t shift, float *logits, cudaStream_t st) {
     const NetPlan &P = ctx->plan;
@@ -432,6 +497,9 @@ int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
     const int n_conv = (int)P.convs.size() - 1;
     const int W = ctx->cfg.win_len;
     TinyArgs a;
+    a.segs = nullptr;
+    a.n_seg = 0;
+    a.shift_step = 0;
     a.y = y;
     a.n_y = n_y;
     a.y_stride = y_stride;

@@ -23,7 +23,9 @@ KScope::KScope(afg_ctx *c, cudaStream_t s, int k, double flops, double bytes) : 
     p.launches[k] += 1;
     p.flops[k] += flops;
     p.bytes[k] += bytes;
-    if (p.on) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    // no event timing while a stream is being captured into a graph
+    if (p.on && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
         e0 = take_event(p);
         if (e0) cudaEventRecord(e0, st);
     }

@@ -188,7 +188,8 @@ int afg_make_twiddles(afg_ctx *ctx) {
 }
 
 int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step,
-               int64_t psd_span, double *psd, cudaStream_t st) {
+               int64_t psd_span, double *psd, cudaStream_t st, int64_t x_stride) {
+    if (x_stride <= 0) x_stride = n;
     const int hop = ctx->cfg.hop;
     const int64_t K = (psd_span - NFFT) / hop + 1;
     const int64_t seg_step = n_psd > 1 ? psd_step / hop : 0;
@@ -200,8 +201,8 @@ int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd
     {
         // one read of every segment, one FP64 periodogram written per segment
         KScope ks(ctx, st, KK_PERIODOGRAM, 0.0, (double)n_det * n_seg * (NFFT * 4.0 + NBIN * 8.0));
-        k_periodogram<<<dim3((unsigned)n_seg, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(x, n, hop, ctx->tw32,
-                                                                                              P, n_seg);
+        k_periodogram<<<dim3((unsigned)n_seg, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(x, x_stride, hop,
+                                                                                              ctx->tw32, P, n_seg);
     }
     AFG_LAUNCH_CHECK(ctx, "k_periodogram");
     // periodic Hann: sum w^2 = 3 NFFT / 8
@@ -217,7 +218,8 @@ int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd
 
 int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const double *psd, int64_t n_psd,
                   int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, int64_t y_stride,
-                  cudaStream_t st) {
+                  cudaStream_t st, int64_t x_stride) {
+    if (x_stride <= 0) x_stride = n;
     float *gains = nullptr;
     int rc = afg_ws_reserve(ctx, WS_FILTER, (size_t)n_det * n_psd * NBIN * sizeof(float), (void **)&gains);
     if (rc) return rc;
@@ -234,7 +236,7 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
         const double F = ctx->cfg.fir_len;
         KScope ks(ctx, st, KK_WHITEN, 0.0, (double)n_det * ((2.0 * out_len + F - 1.0) * 4.0 + n_psd * NBIN * 4.0));
         k_whiten<<<dim3((unsigned)nb, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(
-            x, n, n, gains, n_psd, out_first, out_len, epoch_len, ctx->cfg.fir_len, ctx->tw32, y, y_stride);
+            x, n, x_stride, gains, n_psd, out_first, out_len, epoch_len, ctx->cfg.fir_len, ctx->tw32, y, y_stride);
     }
     AFG_LAUNCH_CHECK(ctx, "k_whiten");
     return AFG_OK;

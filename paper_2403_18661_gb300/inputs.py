@@ -59,10 +59,29 @@ def coloured_noise(n: int, seed: int, model: NoiseModel = NoiseModel(), fs: int 
     White N(0,1) samples are shaped in the frequency domain by sqrt(S fs / 2),
     which gives E[2 |DFT(x)_k|^2 / (fs n)] = S(f_k).
     """
-    w = _rng(seed).standard_normal(n)
+    # shaped on a padded length with small prime factors (a fast FFT size); the
+    # first n samples of the circulant process are a stationary sample of the same PSD
+    m = _fast_len(n)
+    w = _rng(seed).standard_normal(m)
     W = np.fft.rfft(w)
-    f = np.fft.rfftfreq(n, 1.0 / fs)
-    return np.fft.irfft(W * np.sqrt(model.psd(f) * fs / 2.0), n)
+    f = np.fft.rfftfreq(m, 1.0 / fs)
+    return np.fft.irfft(W * np.sqrt(model.psd(f) * fs / 2.0), m)[:n]
+
+
+def _fast_len(n: int) -> int:
+    """Smallest 2^a 3^b 5^c >= n."""
+    best = 1 << max(0, int(n - 1).bit_length())
+    p5 = 1
+    while p5 < best:
+        p35 = p5
+        while p35 < best:
+            v = p35
+            while v < n:
+                v *= 2
+            best = min(best, v)
+            p35 *= 3
+        p5 *= 5
+    return best
 
 
 # --------------------------------------------------------------------------
@@ -338,3 +357,52 @@ def make_strain(wl: Workload, model: NoiseModel = NoiseModel()) -> Tuple[np.ndar
     for i, p in enumerate(inj):
         inject_chirp(x, p["t_c"], p["mchirp"], p["snr"], seed=wl.seed * 1000 + i, model=model, fs=wl.fs)
     return x.astype(np.float32), inj
+
+
+# --------------------------------------------------------------------------
+# Timeslide batch workload
+# --------------------------------------------------------------------------
+
+
+def segment_lengths(n_seg: int = 40, total_s: int = 86400, lo_s: int = 500, hi_s: int = 20000,
+                    seed: int = 2024) -> List[int]:
+    """Uneven seeded segment lengths in whole seconds: lengths lo + (total - n lo) u_i / sum(u),
+    u_i ~ Exp(1), clipped at hi with the excess spread over the others, summing to total."""
+    u = _rng(seed).exponential(1.0, size=n_seg)
+    free = total_s - n_seg * lo_s
+    extra = free * u / u.sum()
+    for _ in range(64):
+        over = np.maximum(lo_s + extra - hi_s, 0.0)
+        if over.sum() <= 0:
+            break
+        extra -= over
+        room = (lo_s + extra) < hi_s
+        extra[room] += over.sum() * extra[room] / extra[room].sum()
+    lengths = np.floor(lo_s + extra).astype(np.int64)
+    lengths[np.argmax(hi_s - lengths)] += total_s - lengths.sum()
+    return [int(v) for v in lengths]
+
+
+TIMESLIDE_DAY = Workload(name="timeslides-40seg-1day-tiny-4Hz-100shifts", duration_s=86400.0, net=TINY_NET,
+                         stride=512, n_win=0, epoch_len=16384, seed=777)
+
+
+def make_segments(lengths_s: Sequence[int], seed: int, model: NoiseModel = NoiseModel(), fs: int = FS,
+                  chirp_every_s: float = 0.0) -> Tuple[np.ndarray, List[Tuple[int, int]]]:
+    """Concatenated two-detector float32 strain [2][sum n] of independent coloured-noise
+    segments, plus [(offset, n_raw)] per segment; optional chirps every chirp_every_s."""
+    ns = [int(l) * fs for l in lengths_s]
+    x = np.empty((2, sum(ns)), dtype=np.float32)
+    segs, off = [], 0
+    rng = _rng(seed + 5)
+    for i, n in enumerate(ns):
+        seg = np.stack([coloured_noise(n, seed * 1000 + 2 * i + d, model, fs) for d in range(2)])
+        if chirp_every_s > 0:
+            for j in range(int(n / fs // chirp_every_s)):
+                t_c = (j + 0.5) * chirp_every_s + rng.uniform(-1, 1)
+                inject_chirp(seg, t_c, float(rng.uniform(10, 60)), float(rng.uniform(4, 20)),
+                             seed=seed * 7919 + i * 131 + j, model=model, fs=fs)
+        x[:, off:off + n] = seg
+        segs.append((off, n))
+        off += n
+    return x, segs

@@ -56,7 +56,8 @@ def test_weights_count_matches_flat_layout(lib, net):
 
 def test_weights_count_rejects_bad_nets(lib):
     import dataclasses
-    for bad in [dict(in_ch=3), dict(stem_k=4), dict(widths=(20,)), dict(groups=3), dict(stem_stride=3)]:
+    for bad in [dict(in_ch=3), dict(stem_k=4), dict(widths=(20,)), dict(widths=(48,)), dict(groups=3),
+                dict(stem_stride=3)]:
         spec = dataclasses.replace(inputs.TINY_NET, **bad)
         with pytest.raises(abi.AfgError):
             abi.weights_count(spec)
