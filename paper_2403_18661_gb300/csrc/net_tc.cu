@@ -65,7 +65,7 @@ __host__ __device__ inline Smem tiny_smem(int W, int n_conv, int k_stem) {
     s.off_p = s.off_w + (size_t)n_conv * TF_WIMG;
     s.off_s = s.off_p + (((size_t)tiny_param_count(k_stem, n_conv) * 4 + 15) / 16) * 16;
     s.off_r = s.off_s + 2 * TF_C * 4;
-    s.off_misc = s.off_r + (size_t)TF_WARPS * 2 * TF_C * 4;
+    s.off_misc = s.off_r + (size_t)(TF_WARPS * 32 + 64) * 4;  // partials [16][32] + moments and channel stats
     s.total = s.off_misc + 64;
     return s;
 }
@@ -192,62 +192,142 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             y0 = args.y + sd.y_off;
             n_y = sd.n_y;
             start = j * args.stride;
-            l1_shift = (sd.shift_first + k) * args.shift_step;
+            l1_shift = ((sd.shift_first + k) * args.shift_step) % n_y;
             out = win;
         }
+        // start + t < n_y and l1_shift < n_y: one conditional subtraction wraps L1
         const float *y1 = y0 + args.y_stride;
         for (int p = tid; p < Wp; p += TF_THREADS) {
             const int tt = p - pad;
             float a = 0.f, b = 0.f;
             if (tt >= 0 && tt < W) {
                 a = y0[start + tt];
-                int64_t i1 = (start + l1_shift + tt) % n_y;
+                int64_t i1 = start + l1_shift + tt;
+                if (i1 >= n_y) i1 -= n_y;
                 b = y1[i1];
             }
             xs[p] = a;
             xs[Wp + p] = b;
         }
         __syncthreads();
-        // ---- stem pass 1: GroupNorm statistics of the conv output
+        // ---- stem pass 1: GroupNorm statistics of the k = 3 stem from the moments
+        // of its six inputs u = (x0[t..t+2], x1[t..t+2]):  sum_t y_c = w_c . S and
+        // sum_t y_c^2 = w_c^T M w_c, with S = sum_t u and M = sum_t u u^T
         {
-            float s[TF_C], q[TF_C];
+            float S[6], M[21];
 #pragma unroll
-            for (int g = 0; g < TF_C; ++g) s[g] = q[g] = 0.f;
+            for (int i = 0; i < 6; ++i) S[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 21; ++i) M[i] = 0.f;
             for (int t = tid; t < W; t += TF_THREADS) {
+                float u[6];
 #pragma unroll
-                for (int c = 0; c < TF_C; ++c) {
-                    float acc = 0.f;
-                    for (int r = 0; r < k; ++r) {
-                        acc = fmaf(stem_w[(c * 2 + 0) * k + r], xs[t + r], acc);
-                        acc = fmaf(stem_w[(c * 2 + 1) * k + r], xs[Wp + t + r], acc);
+                for (int r = 0; r < 3; ++r) {
+                    u[r] = xs[t + r];
+                    u[3 + r] = xs[Wp + t + r];
+                }
+                int m = 0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    S[i] += u[i];
+#pragma unroll
+                    for (int jj = i; jj < 6; ++jj) {
+                        M[m] = fmaf(u[i], u[jj], M[m]);
+                        ++m;
                     }
-                    const int g = c / (TF_C / G);
-                    s[g] += acc;
-                    q[g] = fmaf(acc, acc, q[g]);
                 }
             }
-            gn_reduce<G>(s, q, cnt, args.eps, stem_g, stem_b, red, scale, shift);
+            // block reduction of the 27 moments (fixed order)
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) S[i] += __shfl_xor_sync(0xffffffffu, S[i], o);
+#pragma unroll
+            for (int i = 0; i < 21; ++i)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) M[i] += __shfl_xor_sync(0xffffffffu, M[i], o);
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) red[warp * 32 + i] = S[i];
+#pragma unroll
+                for (int i = 0; i < 21; ++i) red[warp * 32 + 6 + i] = M[i];
+            }
+            __syncthreads();
+            if (tid < 27) {
+                float tot = 0.f;
+                for (int w = 0; w < TF_WARPS; ++w) tot += red[w * 32 + tid];
+                red[TF_WARPS * 32 + tid] = tot;
+            }
+            __syncthreads();
+            if (tid < TF_C) {
+                const float *mom = red + TF_WARPS * 32;
+                const float *wc = stem_w + tid * 6;  // [ci][r] = u order
+                float mean = 0.f, e2 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) mean = fmaf(wc[i], mom[i], mean);
+                int m = 6;
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+#pragma unroll
+                    for (int jj = i; jj < 6; ++jj) {
+                        const float v = wc[i] * wc[jj] * mom[m++];
+                        e2 += (jj == i) ? v : 2.f * v;
+                    }
+                red[TF_WARPS * 32 + 32 + tid] = mean / (float)W;
+                red[TF_WARPS * 32 + 48 + tid] = e2 / (float)W;
+            }
+            __syncthreads();
+            if (tid < TF_C) {
+                const int cg = TF_C / G, g = tid / cg;
+                const float *cm = red + TF_WARPS * 32 + 32, *ce = red + TF_WARPS * 32 + 48;
+                float mean = 0.f, e2 = 0.f;
+                for (int c = g * cg; c < (g + 1) * cg; ++c) {
+                    mean += cm[c];
+                    e2 += ce[c];
+                }
+                mean /= (float)cg;
+                e2 /= (float)cg;
+                const float a = rsqrtf(fmaxf(e2 - mean * mean, 0.f) + args.eps) * stem_g[tid];
+                scale[tid] = a;
+                shift[tid] = stem_b[tid] - mean * a;
+            }
+            __syncthreads();
         }
-        // ---- stem pass 2: GN + ReLU -> BF16 into A (rows 1..W)
-        for (int t = tid; t < W; t += TF_THREADS) {
-            unsigned short o[TF_C];
+        // ---- stem pass 2: conv + GN + ReLU -> BF16 into A (rows 1..W); each thread
+        // owns one 8-channel chunk with its 48 weights in registers
+        {
+            const int h = tid & 1;
+            float wr[8][6], sc8[8], sh8[8];
 #pragma unroll
-            for (int c = 0; c < TF_C; ++c) {
-                float acc = 0.f;
-                for (int r = 0; r < k; ++r) {
-                    acc = fmaf(stem_w[(c * 2 + 0) * k + r], xs[t + r], acc);
-                    acc = fmaf(stem_w[(c * 2 + 1) * k + r], xs[Wp + t + r], acc);
-                }
-                o[c] = f2bf(fmaxf(fmaf(acc, scale[c], shift[c]), 0.f));
+            for (int c = 0; c < 8; ++c) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) wr[c][i] = stem_w[(h * 8 + c) * 6 + i];
+                sc8[c] = scale[h * 8 + c];
+                sh8[c] = shift[h * 8 + c];
             }
+            unsigned char *dstc = actA + h * act_chunk;
+            for (int t = tid >> 1; t < W; t += TF_THREADS / 2) {
+                float u[6];
 #pragma unroll
-            for (int ch = 0; ch < 2; ++ch) {
-                uint4 v;
-                v.x = o[ch * 8 + 0] | ((uint32_t)o[ch * 8 + 1] << 16);
-                v.y = o[ch * 8 + 2] | ((uint32_t)o[ch * 8 + 3] << 16);
-                v.z = o[ch * 8 + 4] | ((uint32_t)o[ch * 8 + 5] << 16);
-                v.w = o[ch * 8 + 6] | ((uint32_t)o[ch * 8 + 7] << 16);
-                *reinterpret_cast<uint4 *>(actA + ch * act_chunk + (size_t)(t + 1) * 16) = v;
+                for (int r = 0; r < 3; ++r) {
+                    u[r] = xs[t + r];
+                    u[3 + r] = xs[Wp + t + r];
+                }
+                uint32_t pk[4];
+#pragma unroll
+                for (int c = 0; c < 8; c += 2) {
+                    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        a0 = fmaf(wr[c][i], u[i], a0);
+                        a1 = fmaf(wr[c + 1][i], u[i], a1);
+                    }
+                    a0 = fmaxf(fmaf(a0, sc8[c], sh8[c]), 0.f);
+                    a1 = fmaxf(fmaf(a1, sc8[c + 1], sh8[c + 1]), 0.f);
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(a0, a1);
+                    pk[c / 2] = *reinterpret_cast<uint32_t *>(&b2);
+                }
+                *reinterpret_cast<uint4 *>(dstc + (size_t)(t + 1) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
         tc::fence_proxy_async_smem();
@@ -295,55 +375,85 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 float s[TF_C], q[TF_C];
 #pragma unroll
                 for (int g = 0; g < TF_C; ++g) s[g] = q[g] = 0.f;
-                for (int j = warp >> 2; j < MT; j += TF_WARPS / 4) {
-                    float v[16];
-                    tc::tmem_ld16(tq + (uint32_t)(j * TF_C), v);
+                for (int j0 = warp >> 2; j0 < MT; j0 += 2 * (TF_WARPS / 4)) {
+                    const int j1 = j0 + TF_WARPS / 4;
+                    uint32_t r0[16], r1[16];
+                    tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
+                    if (j1 < MT) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
+                    tc::tmem_wait_ld();
 #pragma unroll
                     for (int c = 0; c < TF_C; ++c) {
                         const int g = c / (TF_C / G);
-                        s[g] += v[c];
-                        q[g] = fmaf(v[c], v[c], q[g]);
+                        const float v = __uint_as_float(r0[c]);
+                        s[g] += v;
+                        q[g] = fmaf(v, v, q[g]);
+                    }
+                    if (j1 < MT) {
+#pragma unroll
+                        for (int c = 0; c < TF_C; ++c) {
+                            const int g = c / (TF_C / G);
+                            const float v = __uint_as_float(r1[c]);
+                            s[g] += v;
+                            q[g] = fmaf(v, v, q[g]);
+                        }
                     }
                 }
                 const float *gb = conv_gb + l * 2 * TF_C;
                 gn_reduce<G>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift);
             }
-            // ---- epilogue pass 2: normalise (+ residual) + ReLU -> BF16
-            for (int j = warp >> 2; j < MT; j += TF_WARPS / 4) {
-                float v[16];
-                tc::tmem_ld16(tq + (uint32_t)(j * TF_C), v);
-                const int row = 128 * j + 32 * (warp & 3) + lane + 1;
-                float res[16];
-                if (second) {
-#pragma unroll
-                    for (int ch = 0; ch < 2; ++ch) {
-                        const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + (size_t)row * 16);
-                        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            res[ch * 8 + 2 * e] = bf2f((unsigned short)(w4[e] & 0xffffu));
-                            res[ch * 8 + 2 * e + 1] = bf2f((unsigned short)(w4[e] >> 16));
-                        }
-                    }
-                }
-                unsigned short o[16];
+            // ---- epilogue pass 2: normalise (+ residual) + ReLU -> BF16 (two subtiles per TMEM wait)
+            {
+                float sc[TF_C], sh[TF_C];
 #pragma unroll
                 for (int c = 0; c < TF_C; ++c) {
-                    float val = fmaf(v[c], scale[c], shift[c]);
-                    if (second) val += res[c];
-                    val = fmaxf(val, 0.f);
-                    if (last) hs[c] += val;
-                    o[c] = f2bf(val);
+                    sc[c] = scale[c];
+                    sh[c] = shift[c];
                 }
-                if (!last) {
+                for (int j0 = warp >> 2; j0 < MT; j0 += 2 * (TF_WARPS / 4)) {
+                    const int j1 = j0 + TF_WARPS / 4;
+                    const bool two = j1 < MT;
+                    uint32_t r0[16], r1[16];
+                    tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
+                    if (two) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                    for (int ch = 0; ch < 2; ++ch) {
-                        uint4 u;
-                        u.x = o[ch * 8 + 0] | ((uint32_t)o[ch * 8 + 1] << 16);
-                        u.y = o[ch * 8 + 2] | ((uint32_t)o[ch * 8 + 3] << 16);
-                        u.z = o[ch * 8 + 4] | ((uint32_t)o[ch * 8 + 5] << 16);
-                        u.w = o[ch * 8 + 6] | ((uint32_t)o[ch * 8 + 7] << 16);
-                        *reinterpret_cast<uint4 *>(dst + ch * act_chunk + (size_t)row * 16) = u;
+                    for (int half = 0; half < 2; ++half) {
+                        if (half == 1 && !two) break;
+                        const int j = half ? j1 : j0;
+                        const uint32_t *rr = half ? r1 : r0;
+                        const int row = 128 * j + 32 * (warp & 3) + lane + 1;
+#pragma unroll
+                        for (int ch = 0; ch < 2; ++ch) {
+                            float val[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                val[e] = fmaf(__uint_as_float(rr[ch * 8 + e]), sc[ch * 8 + e], sh[ch * 8 + e]);
+                            if (second) {
+                                const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk +
+                                                                                 (size_t)row * 16);
+                                const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    val[2 * e] += __uint_as_float(w4[e] << 16);
+                                    val[2 * e + 1] += __uint_as_float(w4[e] & 0xffff0000u);
+                                }
+                            }
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) val[e] = fmaxf(val[e], 0.f);
+                            if (last) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) hs[ch * 8 + e] += val[e];
+                            } else {
+                                uint32_t pk[4];
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * e], val[2 * e + 1]);
+                                    pk[e] = *reinterpret_cast<uint32_t *>(&b2);
+                                }
+                                *reinterpret_cast<uint4 *>(dst + ch * act_chunk + (size_t)row * 16) =
+                                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            }
+                        }
                     }
                 }
             }
@@ -382,7 +492,8 @@ bool tiny_compatible(const afg_ctx *ctx) {
     const afg_net &n = ctx->cfg.net;
     const int W = ctx->cfg.win_len;
     const int g = n.groups;
-    return n.n_stages == 1 && n.widths[0] == TF_C && n.stem_stride == 1 && n.stem_pool == 0 && W % 128 == 0 &&
+    return n.n_stages == 1 && n.widths[0] == TF_C && n.stem_k == 3 && n.stem_stride == 1 && n.stem_pool == 0 &&
+           W % 128 == 0 &&
            (W / 128) * TF_C <= 512 && (g == 1 || g == 2 || g == 4 || g == 8 || g == 16) &&
            tiny_smem(W, 2 * n.blocks[0], n.stem_k).total <= 227 * 1024;
 }
