@@ -446,13 +446,112 @@ def run_timeslides(args):
     return 0
 
 
+def run_serving(args):
+    """Continuous-batching serving of n streams of 0.25 s chunks.
+
+    Phase 1 (not timed) fills every stream past its 64 s PSD look-back.
+    Phase 2 (latency) pushes chunks with Poisson arrivals at 4 per second per
+    stream for >= 9191 pushes and reports p50/p99 push-to-statistic latency.
+    Phase 3 (throughput) pushes the rest as fast as the host can and reports
+    the aggregate strain-seconds analysed per second of wall time."""
+    import heapq
+
+    import torch
+
+    from paper_2403_18661_gb300 import abi
+
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    wl = inputs.SERVING_128
+    n_streams = args.n_streams
+    chunk = 512
+    warm_s, lat_s, thr_s = 66.0, max(1.0, 9300 / (4.0 * n_streams)), args.serve_seconds
+    total_s = warm_s + lat_s * 1.6 + thr_s + 2.0
+    n_tot = int(total_s * wl.fs)
+    xs = [np.stack([inputs.coloured_noise(n_tot, wl.seed * 1000 + 2 * i + d) for d in range(2)]).astype(np.float32)
+          for i in range(n_streams)]
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
+    ctx.stream_start(max_streams=n_streams, max_chunk=4096)
+    sids = [ctx.stream_open() for _ in range(n_streams)]
+    pos = [0] * n_streams
+    n_warm = int(warm_s * wl.fs)
+    for i, sid in enumerate(sids):
+        for a in range(0, n_warm, 4096):
+            ctx.stream_push(sid, xs[i][:, a:a + 4096])
+        pos[i] = n_warm
+    ctx.stream_flush(120.0)
+    for sid in sids:
+        ctx.stream_poll(sid)
+    # phase 2: Poisson arrivals, real time
+    rng = np.random.default_rng(11)
+    t0 = time.perf_counter()
+    heap = [(float(rng.exponential(0.25)), i) for i in range(n_streams)]
+    heapq.heapify(heap)
+    pushes = 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    while pushes < 9191 or heap[0][0] < lat_s:
+        t_next, i = heapq.heappop(heap)
+        dt = t0 + t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ctx.stream_push(sids[i], xs[i][:, pos[i]:pos[i] + chunk])
+        pos[i] += chunk
+        pushes += 1
+        heapq.heappush(heap, (t_next + float(rng.exponential(0.25)), i))
+        if pos[i] + chunk > n_tot - int(thr_s * wl.fs):
+            break
+    ctx.stream_flush(120.0)
+    lat = []
+    for sid in sids:
+        r = ctx.stream_poll(sid)
+        lat.append(r["t_done"] - r["t_push"])
+    lat = np.concatenate(lat) * 1000.0
+    # phase 3: maximum offered load
+    stats0 = ctx.stream_stats()
+    t1 = time.perf_counter()
+    n_thr = int(thr_s * wl.fs)
+    pushed_samples = 0
+    for a in range(0, n_thr, chunk):
+        for i, sid in enumerate(sids):
+            ctx.stream_push(sid, xs[i][:, pos[i] + a:pos[i] + a + chunk])
+            pushed_samples += chunk
+    ctx.stream_flush(300.0)
+    wall = time.perf_counter() - t1
+    clocks = sampler.stop()
+    stats1 = ctx.stream_stats()
+    for sid in sids:
+        ctx.stream_poll(sid)
+    value = pushed_samples / wl.fs / wall
+    out = {"metric": "strain-seconds/s whiten+ResNet (serving, continuous batching)", "value": value,
+           "unit": "strain-s/s", "n_gpus": 1, "steps": int(stats1["steps"] - stats0["steps"]), "warmup": 0,
+           "ms_per_step": 1000.0 * wall / max(1, stats1["steps"] - stats0["steps"]), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": wl.name, "streams": n_streams, "chunk_samples": chunk,
+                      "arrivals": "Poisson, 4 pushes/s per stream", "latency_pushes": pushes,
+                      "throughput_seconds_per_stream": thr_s},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                          "p99": float(np.percentile(lat, 99)), "results": int(lat.size)},
+           "windows_per_s": (stats1["windows"] - stats0["windows"]) / wall, "clocks": clocks,
+           "e2e": {"value": value, "unit": "strain-s/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                   "note": "wall time from the first host push to the last result on the host"}}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="hour", choices=["hour", "plain64", "timeslides"])
+    ap.add_argument("--workload", default="hour", choices=["hour", "plain64", "timeslides", "serving"])
+    ap.add_argument("--n-streams", type=int, default=128, help="streams (serving workload)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="strain per stream in the throughput phase")
     ap.add_argument("--n-shift", type=int, default=100, help="timeslides per segment (timeslides workload)")
     ap.add_argument("--n-seg", type=int, default=40, help="segments (timeslides workload)")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16"],
@@ -470,6 +569,8 @@ def main():
         return run_reference(args)
     if args.workload == "timeslides":
         return run_timeslides(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

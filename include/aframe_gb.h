@@ -261,6 +261,71 @@ int afg_batch_run(afg_ctx *ctx, const float *x, int64_t x_len, const afg_segment
                   const afg_batch_params *p, float *logits, float *stat, int64_t *trig_idx, int64_t trig_cap,
                   int64_t *n_trig, void *stream);
 
+
+/* ---------------------------------------------------------------- streaming */
+
+/* Streaming analysis with continuous batching (Sec. VI: clients send strain
+ * updates; a snapshotter caches the overlapping state on the server; the
+ * whitener estimates the PSD from the first 64 s of that state and whitens
+ * the rest; overlapping windows go to the network; Sec. II: 1 s
+ * integration).  Per stream the device holds a ring of raw strain, a ring of
+ * whitened strain, the whitening gains of two epochs and a ring of logits.
+ * Whitened sample j of a stream is raw sample psd_len + j, whitened with the
+ * PSD of raw [e*epoch_len, e*epoch_len + psd_len), e = j / epoch_len (the
+ * 64 s before its epoch; refreshed every epoch_len samples); window w covers
+ * whitened [w*stride, w*stride + W); its statistic is the mean of the logits
+ * of windows w - n_int + 1 .. w.  Results appear once a window's data,
+ * including the 0.5 s whitening crop after it, has been pushed.
+ * A host engine thread per context forms one GPU step from every chunk
+ * pushed so far (all streams, one launch per stage); chunks pushed while a
+ * step runs join the next step.  Streams run the BF16 tensor-core network
+ * (precision AFG_BF16, a 16-channel one-stage network).  While streams are
+ * active, make no other calls on the same context except the stream calls. */
+typedef struct afg_stream_params {
+    int64_t psd_len;     /* PSD look-back (64 s = 131072) */
+    int64_t epoch_len;   /* PSD refresh period (8 s = 16384) */
+    int64_t stride;      /* window stride (16 Hz = 128) */
+    int32_t n_int;       /* integration length in windows (<= 64) */
+    int32_t max_streams; /* stream slots */
+    int32_t max_chunk;   /* largest push in samples per detector (<= 8192 - W - stride) */
+} afg_stream_params;
+
+typedef struct afg_stream_result {
+    int64_t window; /* window index w within the stream */
+    float stat;     /* integrated statistic of windows w - n_int + 1 .. w */
+    float logit;    /* logit of window w */
+    double t_push;  /* host monotonic time (s) of the push that completed the window's data */
+    double t_done;  /* host monotonic time (s) at which the result reached the host */
+} afg_stream_result;
+
+/* Start the engine (allocates its step buffers; once per context). */
+int afg_stream_start(afg_ctx *ctx, const afg_stream_params *p);
+
+/* Admit a stream: allocates its device state (~3 MB).  AFG_ERR_BUDGET when
+ * every slot is taken or the context's hbm_budget would be exceeded. */
+int afg_stream_open(afg_ctx *ctx, int64_t *stream_id);
+
+/* Queue n samples per detector (chunk_host: [2][n] float32, host memory;
+ * copied before returning).  Returns immediately; *ticket (may be NULL)
+ * receives the push's sequence number within the stream.  AFG_ERR_NAN for a
+ * non-finite sample, AFG_ERR_STATE for a stream that is not open. */
+int afg_stream_push(afg_ctx *ctx, int64_t id, const float *chunk_host, int64_t n, int64_t *ticket);
+
+/* Move up to cap available results of the stream (oldest first) to out;
+ * waits up to wait_s seconds if none is available yet. */
+int afg_stream_poll(afg_ctx *ctx, int64_t id, afg_stream_result *out, int64_t cap, int64_t *n_out, double wait_s);
+
+/* Wait up to wait_s seconds until every pushed chunk has been processed
+ * (AFG_ERR_TIMEOUT otherwise). */
+int afg_stream_flush(afg_ctx *ctx, double wait_s);
+
+/* Close a stream: drops its queued chunks and results; its device state is
+ * released once its work in flight completes. */
+int afg_stream_close(afg_ctx *ctx, int64_t id);
+
+/* Engine counters: GPU steps, windows evaluated, samples per detector ingested. */
+int afg_stream_stats(afg_ctx *ctx, int64_t *steps, int64_t *windows, int64_t *samples);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Per-kernel accounting of the library's own launches.  `algo_flops` and

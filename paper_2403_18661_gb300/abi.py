@@ -62,6 +62,20 @@ class AfgBatchParams(ctypes.Structure):
                 ("cluster_half", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
+class AfgStreamParams(ctypes.Structure):
+    _fields_ = [("psd_len", ctypes.c_int64), ("epoch_len", ctypes.c_int64), ("stride", ctypes.c_int64),
+                ("n_int", ctypes.c_int32), ("max_streams", ctypes.c_int32), ("max_chunk", ctypes.c_int32)]
+
+
+class AfgStreamResult(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int64), ("stat", ctypes.c_float), ("logit", ctypes.c_float),
+                ("t_push", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+STREAM_RESULT_DTYPE = np.dtype([("window", np.int64), ("stat", np.float32), ("logit", np.float32),
+                                ("t_push", np.float64), ("t_done", np.float64)])
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -87,6 +101,13 @@ SIGNATURES = {
                           ctypes.POINTER(_i64)], ctypes.c_int),
     "afg_batch_run": ([_vp, _vp, _i64, _vp, _i32, ctypes.POINTER(AfgBatchParams), _vp, _vp, _vp, _i64, _vp, _vp],
                       ctypes.c_int),
+    "afg_stream_start": ([_vp, ctypes.POINTER(AfgStreamParams)], ctypes.c_int),
+    "afg_stream_open": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
+    "afg_stream_push": ([_vp, _i64, _vp, _i64, ctypes.POINTER(_i64)], ctypes.c_int),
+    "afg_stream_poll": ([_vp, _i64, _vp, _i64, ctypes.POINTER(_i64), ctypes.c_double], ctypes.c_int),
+    "afg_stream_flush": ([_vp, ctypes.c_double], ctypes.c_int),
+    "afg_stream_close": ([_vp, _i64], ctypes.c_int),
+    "afg_stream_stats": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
     "afg_profile_enable": ([_vp, _i32], ctypes.c_int),
     "afg_profile_read": ([_vp, ctypes.POINTER(AfgKernelStat), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_psd_estimate_noalloc": ([_vp, _i64, _i32, _i64, _i64, _i64, _i32, _i32, _vp, _vp], ctypes.c_int),
@@ -322,6 +343,42 @@ class Context:
                                             _ptr(logits), _ptr(stat), _ptr(trig), trig_cap, _ptr(n_trig),
                                             _stream(stream)))
         return logits, stat, trig, n_trig
+
+    # ---------------------------------------------------------------- streams
+    def stream_start(self, max_streams: int = 128, max_chunk: int = 4096):
+        wl = self.workload
+        p = AfgStreamParams()
+        p.psd_len, p.epoch_len, p.stride = wl.psd_len, wl.epoch_len or 16384, wl.stride
+        p.n_int, p.max_streams, p.max_chunk = wl.n_int, max_streams, max_chunk
+        self._check(self._lib.afg_stream_start(self._h, ctypes.byref(p)))
+
+    def stream_open(self) -> int:
+        i = _i64()
+        self._check(self._lib.afg_stream_open(self._h, ctypes.byref(i)))
+        return i.value
+
+    def stream_push(self, sid: int, chunk: np.ndarray) -> int:
+        c = np.ascontiguousarray(chunk, dtype=np.float32)
+        t = _i64()
+        self._check(self._lib.afg_stream_push(self._h, sid, c.ctypes.data, c.shape[1], ctypes.byref(t)))
+        return t.value
+
+    def stream_poll(self, sid: int, cap: int = 65536, wait_s: float = 0.0) -> np.ndarray:
+        out = np.empty(cap, dtype=STREAM_RESULT_DTYPE)
+        n = _i64()
+        self._check(self._lib.afg_stream_poll(self._h, sid, out.ctypes.data, cap, ctypes.byref(n), wait_s))
+        return out[: n.value]
+
+    def stream_flush(self, wait_s: float = 30.0):
+        self._check(self._lib.afg_stream_flush(self._h, wait_s))
+
+    def stream_close(self, sid: int):
+        self._check(self._lib.afg_stream_close(self._h, sid))
+
+    def stream_stats(self):
+        a, b, c = _i64(), _i64(), _i64()
+        self._check(self._lib.afg_stream_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(steps=a.value, windows=b.value, samples=c.value)
 
     def analyze_host(self, x_host: np.ndarray, shift: int = 0, trig_cap: int = 4096, stat_out=None, trig_out=None,
                      stream=None) -> Tuple[np.ndarray, np.ndarray]:

@@ -60,6 +60,26 @@ struct SegDesc {
     int64_t shift_first;  // timeslide step of the segment's first series (1 for k = 1)
 };
 
+// One window of a list-mode network launch: H1 and L1 rows (W contiguous
+// samples each) and where its logit goes.
+struct WinPtr {
+    const float *y0;
+    const float *y1;
+    float *out;
+};
+
+// One piece of a multi-stream whitening launch (at most WB outputs, one epoch's gains)
+struct WhitenPiece {
+    const float *x;     // raw sample of output 0 minus F/2, detector row 0
+    int64_t x_stride;   // samples between detector rows of x
+    const float *gains; // [2][NBIN] gains of the piece's epoch
+    float *y;           // mirrored whitened ring, detector row 0
+    int64_t y_stride;   // samples between detector rows of y
+    int64_t y_ring;     // ring length (each row holds 2 * y_ring samples)
+    int64_t y_pos;      // ring slot of output 0 (< y_ring)
+    int64_t cnt;        // outputs of the piece (<= WB)
+};
+
 struct Workspace {
     void *p = nullptr;
     size_t bytes = 0;
@@ -84,6 +104,7 @@ enum KernelKind {
     KK_TRIGGERS,
     KK_CONV_TC,
     KK_TINY_TC,
+    KK_SCATTER,
     KK_COUNT
 };
 extern const char *const kKernelNames[KK_COUNT];
@@ -104,10 +125,12 @@ struct Prof {
 };
 
 struct BatchCache;
+struct ServeEngine;
 
 struct afg_ctx {
     Prof prof;
     BatchCache *batch = nullptr;      // captured timeslide-batch graph (batch.cu)
+    ServeEngine *serve = nullptr;     // streaming engine (serve.cu)
     afg_config cfg;
     int device = 0;
     std::string err;
@@ -157,6 +180,7 @@ int afg_fail(afg_ctx *ctx, int code, const char *fmt, ...);
 int afg_cuda_fail(afg_ctx *ctx, cudaError_t e, const char *what);
 int afg_ws_reserve(afg_ctx *ctx, int slot, size_t bytes, void **out);
 void batch_cache_release(afg_ctx *ctx);
+void serve_release(afg_ctx *ctx);
 
 #define AFG_CUDA(ctx, call)                                   \
     do {                                                      \
@@ -184,6 +208,9 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
 cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step, int64_t psd_span,
                           int hop, int fs, const float2 *tw, double *P, double *psd, cudaStream_t st);
 cudaError_t prepare_psd_kernels();
+int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st);
+int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,
+                        cudaStream_t st);
 // net_fp32.cu
 int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights);
 int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
@@ -192,6 +219,7 @@ int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
 int net_tc_prepare(afg_ctx *ctx);
 int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, const SegDesc *segs_dev, int n_seg,
                             int64_t total_win, int64_t stride, int64_t shift_step, float *logits, cudaStream_t st);
+int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, cudaStream_t st);
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 // integrate.cu

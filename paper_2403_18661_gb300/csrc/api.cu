@@ -173,6 +173,7 @@ int afg_ctx_create(const afg_config *cfg, const float *weights_host, int64_t n_w
 
 int afg_ctx_destroy(afg_ctx *ctx) {
     if (!ctx) return AFG_ERR_ARG;
+    serve_release(ctx);
     cudaDeviceSynchronize();
     prof_release(ctx);
     batch_cache_release(ctx);

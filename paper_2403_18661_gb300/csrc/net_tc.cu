@@ -20,6 +20,7 @@
 // core matrices of 8 rows x 16 B with SBO = 128 B and LBO = (W + 2) * 16 B;
 // rows 0 and W + 1 are the zero padding of the k3 convolutions.
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -39,6 +40,7 @@ struct TinyArgs {
     int64_t n_y, y_stride, first, stride, shift, n_win;
     const SegDesc *segs;            // batch mode (n_seg > 0): per-segment window descriptors
     int n_seg;
+    const WinPtr *wins;             // list mode (non-null): window i reads wins[i].y0 / y1, writes *wins[i].out
     int64_t shift_step;
     const float *params;            // stem w [16][2][k], stem gamma/beta, per conv gamma/beta, fc w [16], fc b
     const unsigned char *wimg;      // n_conv x TF_WIMG bytes, BF16, shared-memory image order
@@ -70,10 +72,6 @@ __host__ __device__ inline Smem tiny_smem(int W, int n_conv, int k_stem) {
     return s;
 }
 
-__device__ __forceinline__ unsigned short f2bf(float x) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-__device__ __forceinline__ float bf2f(unsigned short b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 
 // Reduce per-thread group sums (s[g], q[g], g < G) over the block and write the
 // per-channel affine map of GroupNorm: scale[c] = rstd_g * gamma_c,
@@ -177,8 +175,18 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     for (int64_t win = blockIdx.x; win < args.n_win; win += gridDim.x) {
         // ---- locate the window: single series, or (segment, timeslide, window) in batch mode
         const float *y0 = args.y;
+        const float *y1 = nullptr;
+        float *out_ptr = nullptr;
         int64_t n_y = args.n_y, start = args.first + win * args.stride, l1_shift = args.shift, out = win;
-        if (args.n_seg > 0) {
+        if (args.wins) {
+            const WinPtr wp = args.wins[win];
+            y0 = wp.y0;
+            y1 = wp.y1;
+            out_ptr = wp.out;
+            start = 0;
+            l1_shift = 0;
+            n_y = INT64_MAX / 4;
+        } else if (args.n_seg > 0) {
             int lo = 0, hi = args.n_seg - 1;  // last segment with win_first <= win
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             out = win;
         }
         // start + t < n_y and l1_shift < n_y: one conditional subtraction wraps L1
-        const float *y1 = y0 + args.y_stride;
+        if (!y1) y1 = y0 + args.y_stride;
         for (int p = tid; p < Wp; p += TF_THREADS) {
             const int tt = p - pad;
             float a = 0.f, b = 0.f;
@@ -478,7 +486,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 for (int w = 0; w < TF_WARPS; ++w) tot += red[w * 2 * TF_C + c];
                 z += fc_w[c] * (tot / (float)W);
             }
-            args.logits[out] = z;
+            if (out_ptr) *out_ptr = z;
+            else args.logits[out] = z;
         }
         __syncthreads();
     }
@@ -572,6 +581,7 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     a.n_win = total_win;
     a.segs = segs_dev;
     a.n_seg = n_seg;
+    a.wins = nullptr;
     a.shift_step = shift_step;
     a.params = P.tc_params;
     a.wimg = P.tc_wimg;
@@ -599,6 +609,43 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     return AFG_OK;
 }
 
+int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, cudaStream_t st) {
+    const NetPlan &P = ctx->plan;
+    if (!tiny_compatible(ctx) || !P.tc_params)
+        return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "streams: the BF16 path covers one-stage 16-channel networks");
+    if (n_win <= 0) return AFG_OK;
+    const int n_conv = (int)P.convs.size() - 1;
+    const int W = ctx->cfg.win_len;
+    TinyArgs a;
+    memset(&a, 0, sizeof a);
+    a.wins = wins_dev;
+    a.n_win = n_win;
+    a.stride = 1;
+    a.params = P.tc_params;
+    a.wimg = P.tc_wimg;
+    a.err = ctx->d_err;
+    a.n_conv = n_conv;
+    a.k_stem = P.net.stem_k;
+    a.W = W;
+    a.G = P.net.groups;
+    a.eps = P.net.eps;
+    const Smem L = tiny_smem(W, n_conv, a.k_stem);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const unsigned grid = (unsigned)std::min<int64_t>(n_win, std::max(sms, 1));
+    const double flops = 2.0 * n_win * W * TF_C * ((3.0 * TF_C) * n_conv + 2.0 * a.k_stem);
+    KScope ks(ctx, st, KK_TINY_TC, flops, (double)n_win * (2.0 * W * 4.0 + 4.0));
+    switch (a.G) {
+        case 1: k_tiny_fused<1><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 2: k_tiny_fused<2><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 4: k_tiny_fused<4><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 8: k_tiny_fused<8><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        default: k_tiny_fused<16><<<grid, TF_THREADS, L.total, st>>>(a); break;
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_tiny_fused(list)");
+    return AFG_OK;
+}
+
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
                       int64_t n_win, int64_t shift, float *logits, cudaStream_t st) {
     const NetPlan &P = ctx->plan;
@@ -610,6 +657,7 @@ int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
     TinyArgs a;
     a.segs = nullptr;
     a.n_seg = 0;
+    a.wins = nullptr;
     a.shift_step = 0;
     a.y = y;
     a.n_y = n_y;

@@ -119,6 +119,35 @@ __global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict_
     for (int k = threadIdx.x; k < NBIN; k += NT64) out[k] = (float)(d[k].x / (double)NC);
 }
 
+// One overlap-save block: the FIR of src[0 .. WB + F - 1) (samples past
+// `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value).
+// d: NC + 1 float2 of shared memory.
+template <typename Out>
+__device__ __forceinline__ void whiten_block(float2 *d, const float *__restrict__ src, int64_t avail,
+                                             const float *__restrict__ gk, int F, int64_t cnt,
+                                             const float2 *__restrict__ tw, Out out) {
+    const int half = F / 2;
+    const int64_t need = WB + F - 1;  // samples that reach a kept output
+    for (int j = threadIdx.x; j < NC; j += NT32) {
+        int64_t i0 = 2 * (int64_t)j, i1 = i0 + 1;
+        float a = (i0 < need && i0 < avail) ? src[i0] : 0.0f;
+        float b = (i1 < need && i1 < avail) ? src[i1] : 0.0f;
+        d[j] = make_float2(a, b);
+    }
+    __syncthreads();
+    fft_nc<float2, -1, NT32>(d, tw);
+    real_split_forward<float2, NT32>(d, tw);
+    for (int k = threadIdx.x; k < NBIN; k += NT32) {
+        float gv = gk[k];
+        d[k] = make_float2(d[k].x * gv, d[k].y * gv);
+    }
+    __syncthreads();
+    real_split_inverse<float2, NT32>(d, tw);
+    fft_nc<float2, +1, NT32>(d, tw);
+    const float *t = reinterpret_cast<const float *>(d);
+    for (int q = threadIdx.x; q < cnt; q += NT32) out(q, t[q + half]);
+}
+
 // grid (n_blocks, n_det); block b produces y[d][b*WB, min((b+1)*WB, out_len))
 __global__ void __launch_bounds__(NT32) k_whiten(const float *__restrict__ x, int64_t n, int64_t x_stride,
                                                   const float *__restrict__ gains, int64_t n_psd,
@@ -134,32 +163,34 @@ __global__ void __launch_bounds__(NT32) k_whiten(const float *__restrict__ x, in
         e = o / epoch_len;
         if (e > n_psd - 1) e = n_psd - 1;
     }
-    const int half = F / 2;
-    const int64_t s0 = out_first + o - half;  // raw index of block sample 0
-    const int64_t need = WB + F - 1;          // samples that reach a kept output
-    const float *src = x + det * x_stride;
-    for (int j = threadIdx.x; j < NC; j += NT32) {
-        int64_t i0 = 2 * (int64_t)j, i1 = i0 + 1;
-        float a = (i0 < need && s0 + i0 < n) ? src[s0 + i0] : 0.0f;
-        float b = (i1 < need && s0 + i1 < n) ? src[s0 + i1] : 0.0f;
-        d[j] = make_float2(a, b);
-    }
-    __syncthreads();
-    fft_nc<float2, -1, NT32>(d, tw);
-    real_split_forward<float2, NT32>(d, tw);
-    const float *gk = gains + ((int64_t)det * n_psd + e) * NBIN;
-    for (int k = threadIdx.x; k < NBIN; k += NT32) {
-        float gv = gk[k];
-        d[k] = make_float2(d[k].x * gv, d[k].y * gv);
-    }
-    __syncthreads();
-    real_split_inverse<float2, NT32>(d, tw);
-    fft_nc<float2, +1, NT32>(d, tw);
-    const float *t = reinterpret_cast<const float *>(d);
+    const int64_t s0 = out_first + o - F / 2;  // raw index of block sample 0
     int64_t cnt = out_len - o;
     if (cnt > WB) cnt = WB;
     float *dst = y + det * y_stride + o;
-    for (int q = threadIdx.x; q < cnt; q += NT32) dst[q] = t[q + half];
+    whiten_block(d, x + det * x_stride + s0, n - s0, gains + ((int64_t)det * n_psd + e) * NBIN, F, cnt, tw,
+                 [dst](int64_t q, float v) { dst[q] = v; });
+}
+
+// Whitening pieces of many streams in one launch: grid (n_desc, 2).  Piece i
+// whitens raw samples src(d) = desc.x + d * x_stride + [0, cnt + F - 1) with
+// gains desc.gains + d * NBIN into the mirrored ring desc.y (row stride
+// y_stride, ring length y_ring): output q goes to ring slots
+// (y_pos + q) mod y_ring and that + y_ring.
+__global__ void __launch_bounds__(NT32) k_whiten_multi(const WhitenPiece *__restrict__ pieces, int F,
+                                                        const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *d = reinterpret_cast<float2 *>(smem_raw);
+    const WhitenPiece pc = pieces[blockIdx.x];
+    const int det = blockIdx.y;
+    float *yr = pc.y + det * pc.y_stride;
+    const int64_t ring = pc.y_ring, pos = pc.y_pos;
+    whiten_block(d, pc.x + det * pc.x_stride, pc.cnt + F - 1, pc.gains + det * NBIN, F, pc.cnt, tw,
+                 [yr, ring, pos](int64_t q, float v) {
+                     int64_t m = pos + q;
+                     if (m >= ring) m -= ring;
+                     yr[m] = v;
+                     yr[m + ring] = v;
+                 });
 }
 
 bool g_attrs_set = false;
@@ -169,6 +200,8 @@ int set_attrs(afg_ctx *ctx) {
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((NC + 1) * sizeof(float2))));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((NC + 1) * sizeof(float2))));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((NC + 1) * sizeof(float2))));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_filter_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((NC + 1) * sizeof(double2))));
@@ -239,6 +272,26 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
             x, n, x_stride, gains, n_psd, out_first, out_len, epoch_len, ctx->cfg.fir_len, ctx->tw32, y, y_stride);
     }
     AFG_LAUNCH_CHECK(ctx, "k_whiten");
+    return AFG_OK;
+}
+
+// Filter build only: gains [n_det][n_psd][NBIN] from psd (FP64), on st.
+int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st) {
+    KScope ks(ctx, st, KK_FILTER, 0.0, (double)n_det * n_psd * NBIN * (8.0 + 4.0));
+    k_filter_build<<<dim3((unsigned)n_psd, n_det), NT64, (NC + 1) * sizeof(double2), st>>>(
+        psd, n_psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass, ctx->cfg.fir_len, ctx->tw64, gains);
+    AFG_LAUNCH_CHECK(ctx, "k_filter_build");
+    return AFG_OK;
+}
+
+int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,
+                        cudaStream_t st) {
+    if (n_pieces <= 0) return AFG_OK;
+    const double F = ctx->cfg.fir_len;
+    KScope ks(ctx, st, KK_WHITEN, 0.0, 2.0 * ((2.0 * total_out + n_pieces * (F - 1.0)) * 4.0 + n_pieces * NBIN * 4.0));
+    k_whiten_multi<<<dim3((unsigned)n_pieces, 2), NT32, (NC + 1) * sizeof(float2), st>>>(pieces_dev, ctx->cfg.fir_len,
+                                                                                        ctx->tw32);
+    AFG_LAUNCH_CHECK(ctx, "k_whiten_multi");
     return AFG_OK;
 }
 

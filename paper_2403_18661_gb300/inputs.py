@@ -406,3 +406,7 @@ def make_segments(lengths_s: Sequence[int], seed: int, model: NoiseModel = Noise
         segs.append((off, n))
         off += n
     return x, segs
+
+
+SERVING_128 = Workload(name="serving-128streams-0.25s-chunks-16Hz-tiny", duration_s=0.0, net=TINY_NET,
+                       stride=128, n_win=0, epoch_len=16384, seed=555)

@@ -1,0 +1,147 @@
+"""Streaming analysis with continuous batching (afg_stream_*) against the FP64
+oracle, and the same results alone and in a mix of streams."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc  # noqa: E402
+from paper_2403_18661_gb300 import abi, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+BF16_LOGIT_TOL = 5e-2
+# alone vs in the mix: the only difference is the overlap-save block alignment of
+# the whitening (FP32 rounding order), so the FP32 logit tolerance applies
+MIX_TOL = 1e-4
+WL = inputs.SERVING_128
+
+
+def _strain(seconds, seed):
+    n = int(seconds * WL.fs)
+    x = np.stack([inputs.coloured_noise(n, seed * 2 + d) for d in range(2)])
+    return x.astype(np.float32)
+
+
+def _push_all(ctx, sid, x, chunk=512):
+    for a in range(0, x.shape[1], chunk):
+        ctx.stream_push(sid, x[:, a:a + chunk])
+
+
+def _oracle_stream(x, w):
+    """Epoch-mode whitening of everything pushed, windows at the stream stride, 1 s integration."""
+    x64 = x.astype(np.float64)
+    P = x.shape[1]
+    q = P - WL.psd_len - WL.crop + 1  # whitened samples available
+    white = np.empty((2, q))
+    for e in range((q + WL.epoch_len - 1) // WL.epoch_len):
+        lo, hi = e * WL.epoch_len, min(q, (e + 1) * WL.epoch_len)
+        for d in range(2):
+            psd = orc.welch(x64[d, e * WL.epoch_len: e * WL.epoch_len + WL.psd_len], WL.nfft, WL.hop, WL.fs)
+            taps = orc.whitening_taps(psd, WL.nfft, WL.fs, WL.f_highpass, WL.fir_len)
+            white[d, lo:hi] = orc.fir(x64[d], taps, WL.psd_len + lo, hi - lo)
+    n_win = (q - WL.win_len) // WL.stride + 1
+    z = orc.infer_windows(WL.net, w, white, WL.win_len, 0, WL.stride, n_win)
+    return z, orc.integrate(z, WL.n_int)
+
+
+@pytest.fixture(scope="module")
+def weights():
+    return inputs.make_weights(WL.net, WL.weight_seed)
+
+
+def test_stream_matches_oracle(weights, capsys):
+    x = _strain(85.0, 3)
+    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
+    ctx.stream_start(max_streams=4)
+    sid = ctx.stream_open()
+    _push_all(ctx, sid, x)
+    ctx.stream_flush()
+    r = ctx.stream_poll(sid)
+    z, st = _oracle_stream(x, weights)
+    assert len(r) == len(st) and np.array_equal(r["window"], np.arange(WL.n_int - 1, len(z)))
+    err_z = np.abs(r["logit"] - z[WL.n_int - 1:]) / (1 + np.abs(z[WL.n_int - 1:]))
+    err_s = np.abs(r["stat"] - st) / (1 + np.abs(st))
+    with capsys.disabled():
+        print(f"\nstream: {len(r)} results, max |dz|/(1+|z|) = {err_z.max():.3e}, stat {err_s.max():.3e}")
+    assert err_z.max() < BF16_LOGIT_TOL and err_s.max() < BF16_LOGIT_TOL
+    assert np.all(r["t_done"] >= r["t_push"])
+    ctx.close()
+
+
+def test_stream_same_alone_and_in_the_mix(weights):
+    xa = _strain(80.0, 7)
+    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
+    ctx.stream_start(max_streams=16)
+    a = ctx.stream_open()
+    _push_all(ctx, a, xa)
+    ctx.stream_flush()
+    alone = ctx.stream_poll(a)
+    ctx.stream_close(a)
+    # the same stream again, now interleaved with 11 others of random chunk sizes
+    rng = np.random.default_rng(1)
+    others = [(ctx.stream_open(), _strain(80.0, 100 + i)) for i in range(11)]
+    a = ctx.stream_open()
+    cursors = {sid: 0 for sid, _ in others}
+    pos_a = 0
+    while pos_a < xa.shape[1]:
+        for sid, x in others:
+            n = int(rng.choice([128, 512, 1000, 2048]))
+            c = cursors[sid]
+            if c < x.shape[1]:
+                ctx.stream_push(sid, x[:, c:c + n])
+                cursors[sid] = c + n
+        ctx.stream_push(a, xa[:, pos_a:pos_a + 512])
+        pos_a += 512
+    ctx.stream_flush()
+    mixed = ctx.stream_poll(a)
+    assert np.array_equal(mixed["window"], alone["window"])
+    for key in ("logit", "stat"):
+        d = np.abs(mixed[key] - alone[key]) / (1 + np.abs(alone[key]))
+        assert d.max() <= MIX_TOL, (key, d.max())
+    st = ctx.stream_stats()
+    assert st["steps"] > 0 and st["windows"] > len(alone)
+    ctx.close()
+
+
+def test_stream_admission_by_hbm_budget(weights):
+    probe = abi.Context(WL, weights, precision=abi.AFG_BF16)
+    probe.stream_start(max_streams=8)
+    base = probe.bytes_held
+    s0 = probe.stream_open()
+    per_stream = probe.bytes_held - base
+    probe.close()
+    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16, hbm_budget=base + int(2.5 * per_stream))
+    ctx.stream_start(max_streams=8)
+    s1, s2 = ctx.stream_open(), ctx.stream_open()
+    with pytest.raises(abi.AfgError) as e:
+        ctx.stream_open()
+    assert e.value.status == -4
+    ctx.stream_close(s1)
+    ctx.stream_flush()
+    import time
+    deadline = time.time() + 5
+    while True:  # the slot's memory is released by the engine once its work is done
+        try:
+            s3 = ctx.stream_open()
+            break
+        except abi.AfgError:
+            assert time.time() < deadline
+            time.sleep(0.05)
+    ctx.close()
+
+
+def test_stream_refuses_nan_and_closed_streams(weights):
+    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
+    ctx.stream_start(max_streams=2)
+    sid = ctx.stream_open()
+    bad = np.zeros((2, 64), dtype=np.float32)
+    bad[1, 5] = np.nan
+    with pytest.raises(abi.AfgError) as e:
+        ctx.stream_push(sid, bad)
+    assert e.value.status == -7
+    ctx.stream_close(sid)
+    with pytest.raises(abi.AfgError) as e:
+        ctx.stream_push(sid, np.zeros((2, 64), dtype=np.float32))
+    assert e.value.status == -6
+    ctx.close()
