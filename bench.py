@@ -36,6 +36,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2403_18661_gb300 import dist as pdist  # noqa: E402
 from paper_2403_18661_gb300 import inputs  # noqa: E402
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
@@ -177,10 +178,7 @@ def workload_by_name(name: str, n_win: int = 0):
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return pdist.env()
 
 
 def roofline_for(dom: dict, peaks: dict, step_ms_total: float) -> dict:
@@ -250,7 +248,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     wl = workload_by_name(args.workload, args.n_win)
     # each rank analyses its own hour of strain (weak scaling)
-    wl_r = dataclasses.replace(wl, seed=wl.seed + 7919 * rank) if rank else wl
+    wl_r = dataclasses.replace(wl, seed=pdist.rank_seed(wl.seed, rank)) if rank else wl
     x, _ = inputs.make_strain(wl_r)
     w = inputs.make_weights(wl.net, wl.weight_seed)
     precision = abi.AFG_BF16 if args.precision == "bf16" else abi.AFG_FP32
@@ -292,12 +290,9 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in step_ms]
     total_ms = sum(step_ms)
     kstats = ctx.profile_read()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     seconds_per_step = wl.n_win * wl.stride / wl.fs
-    value = world * seconds_per_step * args.steps / (total_ms / 1000.0)
+    value, _, job_s = pdist.job_throughput(seconds_per_step * args.steps, total_ms / 1000.0, world)
+    total_ms = job_s * 1000.0
 
     # end to end through the public host-buffer call: H2D of the strain, D2H of statistic + triggers
     e2e = None
@@ -312,11 +307,8 @@ def run_ours(args):
             ctx.analyze_host(xp, trig_cap=trig_cap, stat_out=stat_h, trig_out=trig_h)
         barrier()
         dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * seconds_per_step * args.steps / dt, "unit": "strain-s/s",
+        e2e_value, _, _ = pdist.job_throughput(seconds_per_step * args.steps, dt, world)
+        e2e = {"value": e2e_value, "unit": "strain-s/s",
                "h2d_bytes_per_step": int(x.nbytes),
                "d2h_bytes_per_step": int(stat_h.numel() * 4 + 8 + trig_cap * 8)}
 
@@ -373,7 +365,7 @@ def run_timeslides(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     wl = inputs.TIMESLIDE_DAY
     lengths = inputs.segment_lengths(n_seg=40, total_s=86400)[: args.n_seg]
-    x, segs = inputs.make_segments(lengths, seed=wl.seed + 7919 * rank, chirp_every_s=300.0)
+    x, segs = inputs.make_segments(lengths, seed=pdist.rank_seed(wl.seed, rank), chirp_every_s=300.0)
     w = inputs.make_weights(wl.net, wl.weight_seed)
     precision = abi.AFG_BF16 if args.precision == "bf16" else abi.AFG_FP32
     ctx = abi.Context(wl, w, precision=precision)
@@ -416,11 +408,8 @@ def run_timeslides(args):
     ctx.sync(stream)
     clocks = sampler.stop() if sampler else None
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * livetime * args.steps / (total_ms / 1000.0)
+    value, _, job_s = pdist.job_throughput(livetime * args.steps, total_ms / 1000.0, world)
+    total_ms = job_s * 1000.0
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
