@@ -105,6 +105,7 @@ enum KernelKind {
     KK_CONV_TC,
     KK_TINY_TC,
     KK_SCATTER,
+    KK_CONVERT,
     KK_COUNT
 };
 extern const char *const kKernelNames[KK_COUNT];
@@ -126,11 +127,13 @@ struct Prof {
 
 struct BatchCache;
 struct ServeEngine;
+struct TcPlan;
 
 struct afg_ctx {
     Prof prof;
     BatchCache *batch = nullptr;      // captured timeslide-batch graph (batch.cu)
     ServeEngine *serve = nullptr;     // streaming engine (serve.cu)
+    TcPlan *tcplan = nullptr;         // per-layer tensor-core plan of wide networks (net_tc_layers.cu)
     afg_config cfg;
     int device = 0;
     std::string err;
@@ -215,6 +218,14 @@ int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_piece
 int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights);
 int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
+int launch_stem_gn_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
+                        int64_t shift, int64_t w0, int nw, float *f0, float *f1, cudaStream_t st);
+// net_tc_layers.cu
+int net_tc_layers_prepare(afg_ctx *ctx);
+void net_tc_layers_release(afg_ctx *ctx);
+bool net_tc_layers_available(const afg_ctx *ctx);
+int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
+                           int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 // net_tc.cu
 int net_tc_prepare(afg_ctx *ctx);
 int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, const SegDesc *segs_dev, int n_seg,

@@ -162,6 +162,7 @@ int afg_ctx_create(const afg_config *cfg, const float *weights_host, int64_t n_w
     int rc = afg_make_twiddles(ctx);
     if (rc == AFG_OK) rc = net_plan_build(ctx, weights_host, n_weights);
     if (rc == AFG_OK) rc = net_tc_prepare(ctx);
+    if (rc == AFG_OK && cfg->precision == AFG_BF16) rc = net_tc_layers_prepare(ctx);
     if (rc == AFG_OK && cudaDeviceSynchronize() != cudaSuccess) rc = AFG_ERR_CUDA;
     if (rc != AFG_OK) {
         afg_ctx_destroy(ctx);
@@ -177,6 +178,7 @@ int afg_ctx_destroy(afg_ctx *ctx) {
     cudaDeviceSynchronize();
     prof_release(ctx);
     batch_cache_release(ctx);
+    net_tc_layers_release(ctx);
     for (auto &w : ctx->ws)
         if (w.p) cudaFree(w.p);
     if (ctx->d_params) cudaFree(ctx->d_params);

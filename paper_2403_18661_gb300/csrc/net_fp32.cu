@@ -435,6 +435,27 @@ int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights) {
     return AFG_OK;
 }
 
+// Stem conv (reading the windows from the whitened stream) + GroupNorm + ReLU
+// (+ max-pool) for windows [w0, w0 + nw): raw conv output in f0, the result
+// in f0 (no pool) or f1 (pool).
+int launch_stem_gn_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
+                        int64_t shift, int64_t w0, int nw, float *f0, float *f1, cudaStream_t st) {
+    const NetPlan &P = ctx->plan;
+    const ConvLayer &S = P.convs[0];
+    const int W = ctx->cfg.win_len, G = P.net.groups, pad = S.k / 2;
+    {
+        KScope ks(ctx, st, KK_STEM, 2.0 * nw * S.lout * S.cout * S.cin * S.k,
+                  4.0 * nw * ((double)2 * W + (double)(S.lout + 2) * S.cout));
+        k_stem<<<nw, 256, 2 * (W + 2 * pad) * sizeof(float), st>>>(y, n_y, y_stride, first, stride, shift, w0, S.wt,
+                                                                  S.cout, S.k, S.stride, W, S.lout, f0);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_stem");
+    gn_launch(ctx, f0, nw, S.lout, S.cout, G, S.gamma, S.beta, P.net.eps, nullptr, 1, P.net.stem_pool ? f1 : nullptr,
+              st);
+    AFG_LAUNCH_CHECK(ctx, "k_groupnorm(stem)");
+    return AFG_OK;
+}
+
 // ---------------------------------------------------------------- forward
 int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
                       int64_t n_win, int64_t shift, float *logits, cudaStream_t st) {

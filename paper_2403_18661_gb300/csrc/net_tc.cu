@@ -649,9 +649,12 @@ int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, 
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first, int64_t stride,
                       int64_t n_win, int64_t shift, float *logits, cudaStream_t st) {
     const NetPlan &P = ctx->plan;
-    if (!tiny_compatible(ctx) || !P.tc_params)
+    if (!tiny_compatible(ctx) || !P.tc_params) {
+        if (net_tc_layers_available(ctx))
+            return launch_infer_bf16_full(ctx, y, n_y, y_stride, first, stride, n_win, shift, logits, st);
         return afg_fail(ctx, AFG_ERR_UNSUPPORTED,
-                        "infer_windows: the BF16 tensor-core path covers one-stage 16-channel networks");
+                        "infer_windows: no BF16 tensor-core path for this network (widths 16 fused, or 64..512)");
+    }
     const int n_conv = (int)P.convs.size() - 1;
     const int W = ctx->cfg.win_len;
     TinyArgs a;

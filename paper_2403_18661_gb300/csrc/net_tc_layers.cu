@@ -1,0 +1,698 @@
+// Per-layer tcgen05 implicit-GEMM convolutions for wide 1D ResNets (the
+// ResNet34 with GroupNorm of Sec. II): BF16 activations in HBM, channels-last
+// with one zero row before and after each window ([W][L + 2][C]).
+//
+// One kernel per convolution, persistent over tiles, warp-specialised:
+//   warp 0  producer: TMA boxes of 8 channels x rows x 1 window into shared
+//           memory in the no-swizzle K-major layout [chunk][row][16 B]
+//           (plus, for channel-major tiles, a bulk copy of the weight block)
+//   warp 1  MMA issuer: tcgen05.mma kind::f16, FP32 accumulators in TMEM
+//   warps 4..11 epilogue: GroupNorm statistics from TMEM, normalise,
+//           optional residual, optional ReLU, BF16 store (+ zero pad rows)
+// Taps are 16-byte row shifts of the activation descriptor; stride-2 convs
+// read the "pair-row" view [(L+2)/2][2C], where tap 0/1/2 are the even
+// half / odd half / even half one pair-row down (the 1x1 stride-2 shortcut
+// reads the odd half).
+//
+// Orientations (both keep one tile's accumulators in 384 TMEM columns):
+//   POS  M = 128 output positions per MMA, N = C_out; a tile is one window;
+//        weights resident in shared memory; the window's input is one K-block.
+//   CH   M = 128 output channels per MMA, N = L_out positions; a tile is a
+//        128-channel slice x wpc windows; K-blocks of KB input channels
+//        stream weights (bulk copy) and activations (TMA) through a ring.
+#include <cuda.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "afg_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int LT = 384;            // threads: 12 warps
+constexpr int EPI_W0 = 4;          // first epilogue warp
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_T = EPI_WARPS * 32;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+struct LayerArgs {
+    int orient;          // 0 POS, 1 CH
+    int n_win;
+    int Lout, Cout, Cin, stride, taps;
+    int rows_pad;        // rows per chunk in shared memory (box_rows * n_box)
+    int box_rows, n_box;
+    int KB;              // real input channels per K-block
+    int halves;          // 1: view chunks of one half; 2: even + odd halves (stride-2 k3)
+    int half0;           // first half loaded (1 for the stride-2 1x1 shortcut)
+    int n_kb;            // K-blocks per tile
+    int wpc, slices;     // CH tiling
+    int NB;              // pipeline stages
+    int G;
+    float eps;
+    int relu;
+    uint32_t act_stage_bytes;  // activation bytes per stage (all tile windows)
+    uint32_t w_block_bytes;    // CH: weight bytes per K-block; POS: whole image
+    const unsigned char *wimg;
+    const float *gamma, *beta;
+    const __nv_bfloat16 *res;
+    __nv_bfloat16 *out;
+    int *err;
+};
+
+struct LSmem {
+    uint32_t off_w, off_act, off_red, off_sc, off_bar, total;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline LSmem layer_smem(const LayerArgs &a) {
+    LSmem s;
+    const uint32_t wbytes = a.orient == 0 ? a.w_block_bytes : a.w_block_bytes * a.NB;
+    s.off_w = 0;
+    s.off_act = align_up(wbytes, 1024);
+    s.off_red = align_up(s.off_act + a.act_stage_bytes * a.NB, 16);
+    s.off_sc = s.off_red + EPI_WARPS * 32 * 4;
+    s.off_bar = align_up(s.off_sc + 2 * 512 * 4, 16);
+    s.total = s.off_bar + 8 * (2 * 4 + 4) + 16;
+    return s;
+}
+
+// shared-memory chunk (of the K-block's view chunks) and row offset of tap r
+__device__ __forceinline__ void tap_offsets(const LayerArgs &a, int r, int &chunk, int &row) {
+    if (a.stride == 1) {
+        chunk = 0;
+        row = a.taps == 1 ? 1 : r;
+    } else if (a.taps == 1) {
+        chunk = 0;  // only the odd half was loaded
+        row = 0;
+    } else {
+        chunk = (r == 1) ? a.KB / 8 : 0;
+        row = (r == 2) ? 1 : 0;
+    }
+}
+
+__device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
+    if (tc::mbar_wait(bar, parity, WAIT_NS)) return true;
+    atomicExch(err, 1);
+    *(volatile int *)abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(EPI_T) : "memory"); }
+
+__global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const LayerArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const LSmem L = layer_smem(a);
+    unsigned char *wsm = sm + L.off_w;
+    unsigned char *act = sm + L.off_act;
+    float *red = reinterpret_cast<float *>(sm + L.off_red);
+    float *scale = reinterpret_cast<float *>(sm + L.off_sc);
+    float *shift = scale + 512;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + L.off_bar);
+    uint64_t *empty = full + 4;
+    uint64_t *acc_full = empty + 4;
+    uint64_t *acc_empty = acc_full + 1;
+    uint64_t *wbar = acc_empty + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
+    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = a.orient == 0 ? a.n_win : ((a.n_win + a.wpc - 1) / a.wpc) * a.slices;
+    const uint32_t chunk_bytes = (uint32_t)a.rows_pad * 16;
+    const int view_chunks = a.halves * a.KB / 8;                  // chunks per window per K-block
+    const uint32_t win_bytes = (uint32_t)view_chunks * chunk_bytes;  // one window's K-block activations
+    const int Nw = a.orient == 0 ? a.Cout : 128;                  // rows of the weight tile
+
+    if (tid == 0) {
+        for (int i = 0; i < a.NB; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(acc_full, 1);
+        tc::mbar_init(acc_empty, 1);
+        tc::mbar_init(wbar, 1);
+        tc::fence_mbar_init();
+        *abort_flag = 0;
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            if (a.orient == 0) {
+                tc::mbar_expect_tx(wbar, a.w_block_bytes);
+                for (uint32_t o = 0; o < a.w_block_bytes; o += 32768)
+                    tc::bulk_load(wsm + o, a.wimg + o, min(32768u, a.w_block_bytes - o), wbar);
+            }
+            uint32_t k = 0;  // stage uses
+            for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x) {
+                const int slice = a.orient == 0 ? 0 : t % a.slices;
+                const int w0 = a.orient == 0 ? t : (t / a.slices) * a.wpc;
+                const int nwt = a.orient == 0 ? 1 : a.wpc;
+                for (int kb = 0; kb < a.n_kb; ++kb, ++k) {
+                    const int s = k % a.NB;
+                    if (k >= (uint32_t)a.NB && !bounded_wait(&empty[s], ((k / a.NB) - 1) & 1, abort_flag, a.err))
+                        break;
+                    const uint32_t wb = a.orient == 1 ? a.w_block_bytes : 0;
+                    tc::mbar_expect_tx(&full[s], a.act_stage_bytes + wb);
+                    if (a.orient == 1) {
+                        const unsigned char *src = a.wimg + ((size_t)slice * a.n_kb + kb) * a.w_block_bytes;
+                        unsigned char *dst = wsm + (size_t)s * a.w_block_bytes;
+                        for (uint32_t o = 0; o < wb; o += 32768) tc::bulk_load(dst + o, src + o, min(32768u, wb - o), &full[s]);
+                    }
+                    unsigned char *ab = act + (size_t)s * a.act_stage_bytes;
+                    for (int i = 0; i < nwt; ++i) {
+                        for (int h = 0; h < a.halves; ++h) {
+                            const int half = a.half0 + h;
+                            for (int c = 0; c < a.KB / 8; ++c) {
+                                const int vchunk = half * (a.Cin / 8) + kb * (a.KB / 8) + c;
+                                unsigned char *d = ab + (size_t)i * win_bytes + (size_t)(h * (a.KB / 8) + c) * chunk_bytes;
+                                for (int b = 0; b < a.n_box; ++b)
+                                    tc::tma_load_3d(d + (size_t)b * a.box_rows * 16, &tmap, &full[s], vchunk * 8,
+                                                    b * a.box_rows, w0 + i);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            if (a.orient == 0) bounded_wait(wbar, 0, abort_flag, a.err);
+            const uint32_t idesc = a.orient == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.Lout);
+            const int MT = a.Lout / 128;
+            uint32_t k = 0, tiles = 0;
+            for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x, ++tiles) {
+                if (tiles > 0 && !bounded_wait(acc_empty, (tiles - 1) & 1, abort_flag, a.err)) break;
+                tc::fence_after_sync();
+                bool ok = true;
+                for (int kb = 0; kb < a.n_kb; ++kb, ++k) {
+                    const int s = k % a.NB;
+                    if (!bounded_wait(&full[s], (k / a.NB) & 1, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t ab = tc::smem_addr(act + (size_t)s * a.act_stage_bytes);
+                    const uint32_t wb = tc::smem_addr(wsm + (a.orient == 1 ? (size_t)s * a.w_block_bytes : 0));
+                    for (int r = 0; r < a.taps; ++r) {
+                        int coff, roff;
+                        tap_offsets(a, r, coff, roff);
+                        for (int kk = 0; kk < a.KB / 16; ++kk) {
+                            const uint32_t wdesc_addr =
+                                wb + (uint32_t)((r * (a.KB / 8) + 2 * kk) * Nw * 16) +
+                                (a.orient == 0 ? (uint32_t)(kb * a.taps * (a.KB / 8) * Nw * 16) : 0u);
+                            const uint64_t wd = tc::desc_kmajor_noswizzle(wdesc_addr, (uint32_t)Nw * 16, 128);
+                            const uint32_t acc = (kb > 0 || r > 0 || kk > 0) ? 1u : 0u;
+                            if (a.orient == 0) {
+                                for (int j = 0; j < MT; ++j) {
+                                    const uint32_t aa = ab + (uint32_t)(coff + 2 * kk) * chunk_bytes +
+                                                        (uint32_t)(128 * j + roff) * 16;
+                                    const uint64_t ad = tc::desc_kmajor_noswizzle(aa, chunk_bytes, 128);
+                                    tc::mma_bf16(tmem + (uint32_t)(j * a.Cout), ad, wd, idesc, acc);
+                                }
+                            } else {
+                                for (int i = 0; i < a.wpc; ++i) {
+                                    const uint32_t bb = ab + (uint32_t)i * win_bytes +
+                                                        (uint32_t)(coff + 2 * kk) * chunk_bytes + (uint32_t)roff * 16;
+                                    const uint64_t bd = tc::desc_kmajor_noswizzle(bb, chunk_bytes, 128);
+                                    tc::mma_bf16(tmem + (uint32_t)(i * a.Lout), wd, bd, idesc, acc);
+                                }
+                            }
+                        }
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(acc_full);
+            }
+        }
+    } else if (warp >= EPI_W0) {
+        // ------------------------------------------------------------ epilogue
+        const int e = warp - EPI_W0;        // 0..7
+        const int q = warp & 3;             // TMEM lane quarter
+        const int hsel = e >> 2;            // which half of the subtiles / windows
+        const int et = tid - EPI_W0 * 32;   // 0..255
+        const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+        uint32_t tiles = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tiles) {
+            bounded_wait(acc_full, tiles & 1, abort_flag, a.err);
+            epi_sync();  // every epilogue thread sees the same abort decision
+            if (*(volatile int *)abort_flag) break;
+            tc::fence_after_sync();
+            if (a.orient == 0) {
+                // rows = positions; thread: row 32q + lane of subtiles j = hsel, hsel + 2, ...
+                const int w = t;
+                const int MT = a.Lout / 128;
+                const int cg = a.Cout / a.G;
+                float s[16], qq[16];
+#pragma unroll
+                for (int g = 0; g < 16; ++g) s[g] = qq[g] = 0.f;
+                for (int j = hsel; j < MT; j += 2)
+                    for (int c0 = 0; c0 < a.Cout; c0 += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tq + (uint32_t)(j * a.Cout + c0), v);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const int g = (c0 + c) / cg;
+#pragma unroll
+                            for (int gg = 0; gg < 16; ++gg)
+                                if (gg == g) {
+                                    s[gg] += v[c];
+                                    qq[gg] = fmaf(v[c], v[c], qq[gg]);
+                                }
+                        }
+                    }
+#pragma unroll
+                for (int g = 0; g < 16; ++g)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s[g] += __shfl_xor_sync(0xffffffffu, s[g], o);
+                        qq[g] += __shfl_xor_sync(0xffffffffu, qq[g], o);
+                    }
+                if (lane == 0)
+                    for (int g = 0; g < 16; ++g) {
+                        red[e * 32 + g] = s[g];
+                        red[e * 32 + 16 + g] = qq[g];
+                    }
+                epi_sync();
+                if (et < a.Cout) {
+                    const int g = et / cg;
+                    float ts = 0.f, tq2 = 0.f;
+                    for (int i = 0; i < EPI_WARPS; ++i) {
+                        ts += red[i * 32 + g];
+                        tq2 += red[i * 32 + 16 + g];
+                    }
+                    const float cnt = (float)a.Lout * (float)cg;
+                    const float mean = ts / cnt;
+                    const float var = fmaxf(tq2 / cnt - mean * mean, 0.f);
+                    const float sc = rsqrtf(var + a.eps) * a.gamma[et];
+                    scale[et] = sc;
+                    shift[et] = a.beta[et] - mean * sc;
+                }
+                epi_sync();
+                const size_t ld = (size_t)(a.Lout + 2) * a.Cout;  // elements per window
+                __nv_bfloat16 *ow = a.out + (size_t)w * ld;
+                const __nv_bfloat16 *rw = a.res ? a.res + (size_t)w * ld : nullptr;
+                for (int j = hsel; j < MT; j += 2) {
+                    const int row = 128 * j + 32 * q + lane + 1;
+                    for (int c0 = 0; c0 < a.Cout; c0 += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tq + (uint32_t)(j * a.Cout + c0), v);
+                        float rv[16];
+                        if (rw) {
+                            const uint4 *rp = reinterpret_cast<const uint4 *>(rw + (size_t)row * a.Cout + c0);
+                            const uint4 r0 = rp[0], r1 = rp[1];
+                            const uint32_t u[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                rv[2 * i] = __uint_as_float(u[i] << 16);
+                                rv[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+                            }
+                        }
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float x0 = fmaf(v[2 * i], scale[c0 + 2 * i], shift[c0 + 2 * i]);
+                            float x1 = fmaf(v[2 * i + 1], scale[c0 + 2 * i + 1], shift[c0 + 2 * i + 1]);
+                            if (rw) {
+                                x0 += rv[2 * i];
+                                x1 += rv[2 * i + 1];
+                            }
+                            if (a.relu) {
+                                x0 = fmaxf(x0, 0.f);
+                                x1 = fmaxf(x1, 0.f);
+                            }
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+                            pk[i] = *reinterpret_cast<uint32_t *>(&b2);
+                        }
+                        uint4 *op = reinterpret_cast<uint4 *>(ow + (size_t)row * a.Cout + c0);
+                        op[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        op[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                    if (row == 1 || row == a.Lout) {  // zero pad rows
+                        uint4 *zp = reinterpret_cast<uint4 *>(ow + (size_t)(row == 1 ? 0 : a.Lout + 1) * a.Cout);
+                        for (int c = 0; c < a.Cout / 8; ++c) zp[c] = make_uint4(0, 0, 0, 0);
+                    }
+                }
+            } else {
+                // rows = channels of the slice; thread: channel 32q + lane, windows i = hsel, hsel + 2, ...
+                const int slice = t % a.slices;
+                const int w0 = (t / a.slices) * a.wpc;
+                const int cl = 32 * q + lane;
+                const int c = slice * 128 + cl;
+                const int cg = a.Cout / a.G;  // 16 or 32: lanes of one group are contiguous
+                const float gam = a.gamma[c], bet = a.beta[c];
+                for (int i = hsel; i < a.wpc; i += 2) {
+                    const int w = w0 + i;
+                    float s = 0.f, qq = 0.f;
+                    for (int p0 = 0; p0 < a.Lout; p0 += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tq + (uint32_t)(i * a.Lout + p0), v);
+#pragma unroll
+                        for (int p = 0; p < 16; ++p) {
+                            s += v[p];
+                            qq = fmaf(v[p], v[p], qq);
+                        }
+                    }
+                    for (int o = cg / 2; o > 0; o >>= 1) {
+                        s += __shfl_xor_sync(0xffffffffu, s, o);
+                        qq += __shfl_xor_sync(0xffffffffu, qq, o);
+                    }
+                    const float cnt = (float)a.Lout * (float)cg;
+                    const float mean = s / cnt;
+                    const float var = fmaxf(qq / cnt - mean * mean, 0.f);
+                    const float sc = rsqrtf(var + a.eps) * gam;
+                    const float sh = bet - mean * sc;
+                    if (w >= a.n_win) continue;
+                    const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
+                    __nv_bfloat16 *ow = a.out + (size_t)w * ld + c;
+                    const __nv_bfloat16 *rw = a.res ? a.res + (size_t)w * ld + c : nullptr;
+                    for (int p0 = 0; p0 < a.Lout; p0 += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tq + (uint32_t)(i * a.Lout + p0), v);
+#pragma unroll
+                        for (int p = 0; p < 16; ++p) {
+                            const size_t o = (size_t)(p0 + p + 1) * a.Cout;
+                            float x = fmaf(v[p], sc, sh);
+                            if (rw) x += __bfloat162float(rw[o]);
+                            if (a.relu) x = fmaxf(x, 0.f);
+                            ow[o] = __float2bfloat16_rn(x);
+                        }
+                    }
+                    ow[0] = __float2bfloat16_rn(0.f);
+                    ow[(size_t)(a.Lout + 1) * a.Cout] = __float2bfloat16_rn(0.f);
+                }
+            }
+            tc::fence_before_sync();
+            epi_sync();
+            if (et == 0) tc::mbar_arrive(acc_empty);
+        }
+    }
+    // ---- teardown: every role is done; free TMEM
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// fp32 padded [n][L+2][C] -> bf16 (same layout)
+__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i * 4 >= n) return;
+    const float4 v = reinterpret_cast<const float4 *>(x)[i];
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    reinterpret_cast<uint2 *>(y)[i] = make_uint2(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b));
+}
+
+// grid (n_win), block 256: logit = fc_b + sum_c fc_w[c] * mean_t x[t][c] (bf16 input)
+__global__ void k_head_bf16(const __nv_bfloat16 *__restrict__ x, int L, int C, const float *__restrict__ fc_w,
+                            const float *__restrict__ fc_b, float *__restrict__ logits, int64_t w0) {
+    __shared__ float part[512];
+    const __nv_bfloat16 *xt = x + (int64_t)blockIdx.x * (L + 2) * C + C;
+    const int tid = threadIdx.x;
+    for (int c = tid; c < C; c += 256) {
+        float s = 0.f;
+        for (int r = 0; r < L; ++r) s += __bfloat162float(xt[(int64_t)r * C + c]);
+        part[c] = fc_w[c] * (s / (float)L);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float z = fc_b[0];
+        for (int c = 0; c < C; ++c) z += part[c];
+        logits[w0 + blockIdx.x] = z;
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+// Per-layer plan of the tensor-core path (built once per context).
+struct TcLayer {
+    LayerArgs a;                 // everything but pointers and n_win
+    unsigned char *wimg = nullptr;
+    int view_c, view_rows;       // tensor map of the input view: channels, rows per window
+};
+
+struct TcPlan {
+    std::vector<TcLayer> layers;  // indexed like NetPlan::convs (index 0 unused: the stem runs SIMT)
+    void *mem = nullptr;
+};
+
+static void fill_geometry(const ConvLayer &C, int G, float eps, TcLayer &T) {
+    LayerArgs &a = T.a;
+    memset(&a, 0, sizeof a);
+    a.Lout = C.lout;
+    a.Cout = C.cout;
+    a.Cin = C.cin;
+    a.stride = C.stride;
+    a.taps = C.k;
+    a.G = G;
+    a.eps = eps;
+    const bool pos = (C.lout % 128 == 0) && (C.lout / 128) * C.cout <= 512 && C.cout <= 256;
+    a.orient = pos ? 0 : 1;
+    T.view_c = C.stride * C.cin;
+    T.view_rows = (C.lin + 2) / C.stride;
+    // TMA boxes of 8 channels x box_rows rows: a tiled TMA destination must be 128-byte aligned,
+    // so box_rows is a multiple of 8 (16 B rows); the box count minimises the padded rows
+    const int R = T.view_rows;
+    a.n_box = 0;
+    for (int nb = 1; nb <= 32; ++nb) {
+        const int br = ((R + nb - 1) / nb + 7) / 8 * 8;
+        if (br > 256) continue;
+        if (a.n_box == 0 || br * nb < a.rows_pad) {
+            a.n_box = nb;
+            a.box_rows = br;
+            a.rows_pad = br * nb;
+        }
+    }
+    a.halves = (C.stride == 2 && C.k == 3) ? 2 : 1;
+    a.half0 = (C.stride == 2 && C.k == 1) ? 1 : 0;
+    if (pos) {
+        a.KB = C.cin;
+        a.n_kb = 1;
+        a.wpc = 1;
+        a.slices = 1;
+        a.w_block_bytes = (uint32_t)(C.k * C.cin * C.cout * 2);
+    } else {
+        a.wpc = 384 / C.lout;
+        a.slices = C.cout / 128;
+        a.KB = (C.stride == 2 && C.k == 3) ? 32 : 64;
+        a.n_kb = C.cin / a.KB;
+        a.w_block_bytes = (uint32_t)(C.k * a.KB * 128 * 2);
+    }
+    const uint32_t chunk_bytes = (uint32_t)a.rows_pad * 16;
+    a.act_stage_bytes = (uint32_t)a.wpc * a.halves * (a.KB / 8) * chunk_bytes;
+    // deepest ring that fits
+    a.NB = 1;
+    for (int nb = 4; nb >= 1; --nb) {
+        a.NB = nb;
+        if (layer_smem(a).total <= 227 * 1024) break;
+    }
+}
+
+// BF16 weight image of one conv in the layout its orientation reads
+static void pack_weights(const ConvLayer &C, const float *wt_host /* [(r*cin+ci)*cout+co] */, const TcLayer &T,
+                         std::vector<unsigned short> &img) {
+    const LayerArgs &a = T.a;
+    auto bf = [](float v) {
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        return *reinterpret_cast<unsigned short *>(&b);
+    };
+    if (a.orient == 0) {
+        // [tap][chunk (cin/8)][cout][8]
+        img.assign((size_t)C.k * C.cin * C.cout, 0);
+        for (int r = 0; r < C.k; ++r)
+            for (int ci = 0; ci < C.cin; ++ci)
+                for (int co = 0; co < C.cout; ++co)
+                    img[(((size_t)r * (C.cin / 8) + ci / 8) * C.cout + co) * 8 + ci % 8] =
+                        bf(wt_host[((size_t)r * C.cin + ci) * C.cout + co]);
+    } else {
+        // [slice][kb][tap][chunk (KB/8)][128][8]
+        img.assign((size_t)C.k * C.cin * C.cout, 0);
+        const int KB = a.KB;
+        for (int sl = 0; sl < a.slices; ++sl)
+            for (int kb = 0; kb < a.n_kb; ++kb)
+                for (int r = 0; r < C.k; ++r)
+                    for (int c = 0; c < KB / 8; ++c)
+                        for (int m = 0; m < 128; ++m)
+                            for (int e = 0; e < 8; ++e) {
+                                const int ci = kb * KB + c * 8 + e, co = sl * 128 + m;
+                                const size_t idx =
+                                    (((((size_t)sl * a.n_kb + kb) * C.k + r) * (KB / 8) + c) * 128 + m) * 8 + e;
+                                img[idx] = bf(wt_host[((size_t)r * C.cin + ci) * C.cout + co]);
+                            }
+    }
+}
+
+static bool full_net_supported(const afg_ctx *ctx) {
+    const NetPlan &P = ctx->plan;
+    for (size_t i = 1; i < P.convs.size(); ++i) {
+        const ConvLayer &C = P.convs[i];
+        if (C.cin % 64 || C.cout % 64 || C.cout > 512) return false;
+        const bool pos = (C.lout % 128 == 0) && (C.lout / 128) * C.cout <= 512 && C.cout <= 256;
+        if (!pos && (C.cout % 128 || 384 % C.lout || C.lout % 16 || C.lout > 256 || C.cout / P.net.groups > 32))
+            return false;
+        if (pos && (C.cout / P.net.groups > 32 || P.net.groups > 16)) return false;
+    }
+    return true;
+}
+
+int net_tc_layers_prepare(afg_ctx *ctx) {
+    NetPlan &P = ctx->plan;
+    if (P.convs.size() < 2 || !full_net_supported(ctx)) return AFG_OK;
+    if (!encode_fn()) return AFG_OK;  // no tensor-map encoder: the path stays unavailable
+    TcPlan *tp = new TcPlan();
+    tp->layers.resize(P.convs.size());
+    std::vector<float> all(ctx->d_params_bytes / sizeof(float));
+    AFG_CUDA(ctx, cudaMemcpy(all.data(), ctx->d_params, ctx->d_params_bytes, cudaMemcpyDeviceToHost));
+    std::vector<std::vector<unsigned short>> imgs(P.convs.size());
+    size_t total = 0;
+    for (size_t i = 1; i < P.convs.size(); ++i) {
+        fill_geometry(P.convs[i], P.net.groups, P.net.eps, tp->layers[i]);
+        pack_weights(P.convs[i], all.data() + (P.convs[i].wt - ctx->d_params), tp->layers[i], imgs[i]);
+        total += (imgs[i].size() * 2 + 1023) / 1024 * 1024;
+    }
+    void *d = nullptr;
+    if (cudaMalloc(&d, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete tp;
+        return afg_fail(ctx, AFG_ERR_OOM, "tensor-core weight images: cudaMalloc(%zu) failed", total);
+    }
+    ctx->bytes_held += (int64_t)total;
+    tp->mem = d;
+    size_t off = 0;
+    for (size_t i = 1; i < P.convs.size(); ++i) {
+        tp->layers[i].wimg = static_cast<unsigned char *>(d) + off;
+        AFG_CUDA(ctx, cudaMemcpy(tp->layers[i].wimg, imgs[i].data(), imgs[i].size() * 2, cudaMemcpyHostToDevice));
+        off += (imgs[i].size() * 2 + 1023) / 1024 * 1024;
+    }
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    ctx->tcplan = tp;
+    return AFG_OK;
+}
+
+void net_tc_layers_release(afg_ctx *ctx) {
+    if (!ctx->tcplan) return;
+    if (ctx->tcplan->mem) cudaFree(ctx->tcplan->mem);
+    delete ctx->tcplan;
+    ctx->tcplan = nullptr;
+}
+
+bool net_tc_layers_available(const afg_ctx *ctx) { return ctx->tcplan != nullptr; }
+
+static int conv_tc(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, const __nv_bfloat16 *res, int relu,
+                   __nv_bfloat16 *out, int nw, const ConvLayer &C, cudaStream_t st) {
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)T.view_c, (cuuint64_t)T.view_rows, (cuuint64_t)nw};
+    const cuuint64_t strides[2] = {(cuuint64_t)T.view_c * 2, (cuuint64_t)T.view_c * 2 * T.view_rows};
+    const cuuint32_t box[3] = {8, (cuuint32_t)T.a.box_rows, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(in), dims, strides,
+                             box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return afg_fail(ctx, AFG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    LayerArgs a = T.a;
+    a.n_win = nw;
+    a.relu = relu;
+    a.wimg = T.wimg;
+    a.gamma = C.gamma;
+    a.beta = C.beta;
+    a.res = res;
+    a.out = out;
+    a.err = ctx->d_err;
+    const int n_tiles = a.orient == 0 ? nw : ((nw + a.wpc - 1) / a.wpc) * a.slices;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const unsigned grid = (unsigned)std::max(1, std::min(n_tiles, sms));
+    const double flops = 2.0 * nw * C.lout * C.cout * (double)C.k * C.cin;
+    const double bytes = 2.0 * nw * ((double)(C.lin + 2) * C.cin + (double)(C.lout + 2) * C.cout * (res ? 2 : 1)) +
+                         2.0 * C.k * C.cin * C.cout;
+    KScope ks(ctx, st, KK_CONV_TC, flops, bytes);
+    k_conv_tc<<<grid, LT, layer_smem(a).total, st>>>(map, a);
+    AFG_LAUNCH_CHECK(ctx, "k_conv_tc");
+    return AFG_OK;
+}
+
+// Full-network BF16 forward over sliding windows (stem in FP32 SIMT, every
+// other convolution on tcgen05).
+int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
+                           int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st) {
+    const NetPlan &P = ctx->plan;
+    const TcPlan &TP = *ctx->tcplan;
+    const ConvLayer &S = P.convs[0];
+    const int64_t per_win32 = P.max_act_per_window * (int64_t)sizeof(float);
+    const int64_t per_win16 = P.max_act_per_window * 2;
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_win, ((int64_t)2 << 30) / per_win32));
+    chunk = std::min<int64_t>(chunk, 8192);
+    // fp32 stem buffers (reused as two bf16 activation buffers once converted) + two bf16 buffers
+    float *f0 = nullptr, *f1 = nullptr;
+    __nv_bfloat16 *bA = nullptr, *bC = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_ACT0, (size_t)(chunk * per_win32), (void **)&f0);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT1, (size_t)(chunk * per_win32), (void **)&f1);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT2, (size_t)(chunk * per_win16), (void **)&bA);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT3, (size_t)(chunk * per_win16), (void **)&bC);
+    if (rc) return rc;
+    __nv_bfloat16 *bB = reinterpret_cast<__nv_bfloat16 *>(f0);
+    __nv_bfloat16 *bD = reinterpret_cast<__nv_bfloat16 *>(f1);
+    for (int64_t w0 = 0; w0 < n_win; w0 += chunk) {
+        const int nw = (int)std::min<int64_t>(chunk, n_win - w0);
+        int rc2 = launch_stem_gn_fp32(ctx, y, n_y, y_stride, first, stride, shift, w0, nw, f0, f1, st);
+        if (rc2) return rc2;
+        const float *stem_out = P.net.stem_pool ? f1 : f0;
+        const int L0 = P.l_after_stem, C0 = S.cout;
+        const int64_t n_el = (int64_t)nw * (L0 + 2) * C0;
+        {
+            KScope ks(ctx, st, KK_CONVERT, 0.0, (double)n_el * 6.0);
+            k_to_bf16<<<(unsigned)((n_el / 4 + 255) / 256), 256, 0, st>>>(stem_out, bA, n_el);
+        }
+        AFG_LAUNCH_CHECK(ctx, "k_to_bf16");
+        __nv_bfloat16 *A = bA, *Cb = bC, *B = bB, *D = bD;
+        for (const BlockPlan &bp : P.blocks) {
+            const ConvLayer &c1 = P.convs[bp.c1], &c2 = P.convs[bp.c2];
+            int e = conv_tc(ctx, TP.layers[bp.c1], A, nullptr, 1, B, nw, c1, st);
+            const __nv_bfloat16 *res = A;
+            if (!e && bp.sc >= 0) {
+                e = conv_tc(ctx, TP.layers[bp.sc], A, nullptr, 0, D, nw, P.convs[bp.sc], st);
+                res = D;
+            }
+            if (!e) e = conv_tc(ctx, TP.layers[bp.c2], B, res, 1, Cb, nw, c2, st);
+            if (e) return e;
+            std::swap(A, Cb);
+        }
+        {
+            KScope ks(ctx, st, KK_HEAD, 2.0 * nw * P.l_last * P.c_last, 2.0 * nw * (double)P.l_last * P.c_last);
+            k_head_bf16<<<nw, 256, 0, st>>>(A, P.l_last, P.c_last, P.fc_w, P.fc_b, logits, w0);
+        }
+        AFG_LAUNCH_CHECK(ctx, "k_head_bf16");
+    }
+    return AFG_OK;
+}

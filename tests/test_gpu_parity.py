@@ -255,3 +255,36 @@ def test_bf16_precision_c1_peaks_within_one_sample(c1, ctx_tiny_bf16):
     st = stat.cpu().numpy()
     n = int(n_trig.item())
     _trigger_match(st, ref["stat"], trig.cpu().numpy()[:n], ref["triggers"], wl.cluster_half, BF16_LOGIT_TOL)
+
+
+def test_bf16_resnet34_tensor_core_layers(capsys):
+    """ResNet34-GN on per-layer tcgen05 convolutions (TMA-fed, position- and
+    channel-major tiles) against the FP64 oracle on sampled windows, and
+    against the FP32 path on every window."""
+    import dataclasses
+    wl = dataclasses.replace(inputs.HOUR_RESNET34, n_win=600, n_chirps=2, name="resnet34-600win")
+    x, _ = inputs.make_strain(wl)
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    xd = _dev(x)
+    c16 = abi.Context(wl, w, precision=abi.AFG_BF16)
+    z16 = c16.analyze(xd)[0].cpu().numpy()
+    c16.sync()
+    c32 = abi.Context(wl, w, precision=abi.AFG_FP32)
+    z32 = c32.analyze(xd)[0].cpu().numpy()
+    d = np.abs(z16 - z32) / (1 + np.abs(z32))
+    x64 = x.astype(np.float64)
+    worst = 0.0
+    for j in [0, 1, 127, 128, 333, 599]:
+        s0 = j * wl.stride
+        eps = sorted({s0 // wl.epoch_len, (s0 + wl.win_len - 1) // wl.epoch_len})
+        psd = orc.psd_epochs(x64, wl, eps)
+        white = orc.whiten(x64, wl, psd, eps)
+        off = s0 - eps[0] * wl.epoch_len
+        want = orc.network(wl.net, w, white[:, off: off + wl.win_len])
+        worst = max(worst, abs(z16[j] - want) / (1 + abs(want)))
+    with capsys.disabled():
+        print(f"\nBF16 ResNet34: vs FP32 max {d.max():.3e}, vs oracle (6 windows) max {worst:.3e}")
+    assert np.all(np.isfinite(z16))
+    assert d.max() < BF16_LOGIT_TOL and worst < BF16_LOGIT_TOL
+    c16.close()
+    c32.close()
