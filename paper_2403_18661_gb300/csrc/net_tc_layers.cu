@@ -49,6 +49,7 @@ struct LayerArgs {
     int half0;           // first half loaded (1 for the stride-2 1x1 shortcut)
     int n_kb;            // K-blocks per tile
     int wpc, slices;     // CH tiling
+    int nsplit;          // CH: MMAs per window along N (L_out / nsplit <= 256 positions each)
     int NB;              // pipeline stages
     int G;
     float eps;
@@ -103,7 +104,36 @@ __device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, int
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(EPI_T) : "memory"); }
 
+// Fold the per-channel partial sums of a 16-channel chunk into GroupNorm groups of
+// CG channels, reduce them over the warp, and let lane 0 add them to its warp's row.
+template <int CG>
+__device__ __forceinline__ void fold_chunk(const float (&cs)[16], const float (&cq)[16], int c0, int lane,
+                                           float *red_row) {
+    constexpr int W = CG < 16 ? CG : 16;  // channels of one group inside the chunk
+#pragma unroll
+    for (int gl = 0; gl < 16 / W; ++gl) {
+        float a = 0.f, b = 0.f;
+#pragma unroll
+        for (int c = gl * W; c < (gl + 1) * W; ++c) {
+            a += cs[c];
+            b += cq[c];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            const int g = (c0 + gl * W) / CG;
+            red_row[g] += a;
+            red_row[16 + g] += b;
+        }
+    }
+}
+
+template <int ORIENT>
 __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const LayerArgs a) {
+    // ORIENT (= a.orient) is compile-time: each instantiation keeps only its own path
     extern __shared__ __align__(1024) unsigned char sm[];
     const LSmem L = layer_smem(a);
     unsigned char *wsm = sm + L.off_w;
@@ -119,11 +149,11 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_tiles = a.orient == 0 ? a.n_win : ((a.n_win + a.wpc - 1) / a.wpc) * a.slices;
+    const int n_tiles = ORIENT == 0 ? a.n_win : ((a.n_win + a.wpc - 1) / a.wpc) * a.slices;
     const uint32_t chunk_bytes = (uint32_t)a.rows_pad * 16;
     const int view_chunks = a.halves * a.KB / 8;                  // chunks per window per K-block
     const uint32_t win_bytes = (uint32_t)view_chunks * chunk_bytes;  // one window's K-block activations
-    const int Nw = a.orient == 0 ? a.Cout : 128;                  // rows of the weight tile
+    const int Nw = ORIENT == 0 ? a.Cout : 128;                  // rows of the weight tile
 
     if (tid == 0) {
         for (int i = 0; i < a.NB; ++i) {
@@ -148,26 +178,27 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            if (a.orient == 0) {
+            if (ORIENT == 0) {
                 tc::mbar_expect_tx(wbar, a.w_block_bytes);
                 for (uint32_t o = 0; o < a.w_block_bytes; o += 32768)
                     tc::bulk_load(wsm + o, a.wimg + o, min(32768u, a.w_block_bytes - o), wbar);
             }
             uint32_t k = 0;  // stage uses
             for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x) {
-                const int slice = a.orient == 0 ? 0 : t % a.slices;
-                const int w0 = a.orient == 0 ? t : (t / a.slices) * a.wpc;
-                const int nwt = a.orient == 0 ? 1 : a.wpc;
+                const int slice = ORIENT == 0 ? 0 : t % a.slices;
+                const int w0 = ORIENT == 0 ? t : (t / a.slices) * a.wpc;
+                const int nwt = ORIENT == 0 ? 1 : a.wpc;
                 for (int kb = 0; kb < a.n_kb; ++kb, ++k) {
                     const int s = k % a.NB;
                     if (k >= (uint32_t)a.NB && !bounded_wait(&empty[s], ((k / a.NB) - 1) & 1, abort_flag, a.err))
                         break;
-                    const uint32_t wb = a.orient == 1 ? a.w_block_bytes : 0;
+                    const uint32_t wb = ORIENT == 1 ? a.w_block_bytes : 0;
                     tc::mbar_expect_tx(&full[s], a.act_stage_bytes + wb);
-                    if (a.orient == 1) {
+                    if (ORIENT == 1) {
                         const unsigned char *src = a.wimg + ((size_t)slice * a.n_kb + kb) * a.w_block_bytes;
                         unsigned char *dst = wsm + (size_t)s * a.w_block_bytes;
-                        for (uint32_t o = 0; o < wb; o += 32768) tc::bulk_load(dst + o, src + o, min(32768u, wb - o), &full[s]);
+                        for (uint32_t o = 0; o + 1 <= wb; o += 32768)
+                            tc::bulk_load(dst + o, src + o, min(32768u, wb - o), &full[s]);
                     }
                     unsigned char *ab = act + (size_t)s * a.act_stage_bytes;
                     for (int i = 0; i < nwt; ++i) {
@@ -188,9 +219,9 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            if (a.orient == 0) bounded_wait(wbar, 0, abort_flag, a.err);
-            const uint32_t idesc = a.orient == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.Lout);
-            const int MT = a.Lout / 128;
+            if (ORIENT == 0) bounded_wait(wbar, 0, abort_flag, a.err);
+            const uint32_t idesc =
+                ORIENT == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.Lout / a.nsplit);
             uint32_t k = 0, tiles = 0;
             for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x, ++tiles) {
                 if (tiles > 0 && !bounded_wait(acc_empty, (tiles - 1) & 1, abort_flag, a.err)) break;
@@ -204,30 +235,35 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     }
                     tc::fence_after_sync();
                     const uint32_t ab = tc::smem_addr(act + (size_t)s * a.act_stage_bytes);
-                    const uint32_t wb = tc::smem_addr(wsm + (a.orient == 1 ? (size_t)s * a.w_block_bytes : 0));
+                    const uint32_t wb = tc::smem_addr(wsm + (ORIENT == 1 ? (size_t)s * a.w_block_bytes : 0));
+                    // descriptors of (tap 0, k-step 0); every other MMA adds address deltas (in 16-byte
+                    // units) to these, which stay inside the 14-bit start-address field (smem < 256 KB)
+                    const uint64_t wd00 = tc::desc_kmajor_noswizzle(
+                        wb + (ORIENT == 0 ? (uint32_t)(kb * a.taps * (a.KB / 8) * Nw * 16) : 0u), (uint32_t)Nw * 16, 128);
+                    const uint64_t ad00 = tc::desc_kmajor_noswizzle(ab, chunk_bytes, 128);
+                    const uint64_t w_tap = (uint64_t)((a.KB / 8) * Nw);  // (KB/8 * Nw * 16) >> 4
+                    const uint64_t w_kk = (uint64_t)(2 * Nw);            // (2 * Nw * 16) >> 4
+                    const uint64_t a_kk = (uint64_t)(2 * chunk_bytes / 16);
+                    const uint64_t a_win = (uint64_t)(win_bytes / 16);
+                    const int ns = ORIENT == 1 ? a.Lout / a.nsplit : 0;
+                    const int MT = a.Lout / 128;
                     for (int r = 0; r < a.taps; ++r) {
                         int coff, roff;
                         tap_offsets(a, r, coff, roff);
+                        const uint64_t wdr = wd00 + (uint64_t)r * w_tap;
+                        const uint64_t adr = ad00 + (uint64_t)(coff * (chunk_bytes / 16) + roff);
                         for (int kk = 0; kk < a.KB / 16; ++kk) {
-                            const uint32_t wdesc_addr =
-                                wb + (uint32_t)((r * (a.KB / 8) + 2 * kk) * Nw * 16) +
-                                (a.orient == 0 ? (uint32_t)(kb * a.taps * (a.KB / 8) * Nw * 16) : 0u);
-                            const uint64_t wd = tc::desc_kmajor_noswizzle(wdesc_addr, (uint32_t)Nw * 16, 128);
+                            const uint64_t wd = wdr + (uint64_t)kk * w_kk;
+                            const uint64_t adk = adr + (uint64_t)kk * a_kk;
                             const uint32_t acc = (kb > 0 || r > 0 || kk > 0) ? 1u : 0u;
-                            if (a.orient == 0) {
-                                for (int j = 0; j < MT; ++j) {
-                                    const uint32_t aa = ab + (uint32_t)(coff + 2 * kk) * chunk_bytes +
-                                                        (uint32_t)(128 * j + roff) * 16;
-                                    const uint64_t ad = tc::desc_kmajor_noswizzle(aa, chunk_bytes, 128);
-                                    tc::mma_bf16(tmem + (uint32_t)(j * a.Cout), ad, wd, idesc, acc);
-                                }
+                            if (ORIENT == 0) {
+                                for (int j = 0; j < MT; ++j)
+                                    tc::mma_bf16(tmem + (uint32_t)(j * a.Cout), adk + (uint64_t)(128 * j), wd, idesc, acc);
                             } else {
-                                for (int i = 0; i < a.wpc; ++i) {
-                                    const uint32_t bb = ab + (uint32_t)i * win_bytes +
-                                                        (uint32_t)(coff + 2 * kk) * chunk_bytes + (uint32_t)roff * 16;
-                                    const uint64_t bd = tc::desc_kmajor_noswizzle(bb, chunk_bytes, 128);
-                                    tc::mma_bf16(tmem + (uint32_t)(i * a.Lout), wd, bd, idesc, acc);
-                                }
+                                for (int i = 0; i < a.wpc; ++i)
+                                    for (int h = 0; h < a.nsplit; ++h)
+                                        tc::mma_bf16(tmem + (uint32_t)(i * a.Lout + h * ns), wd,
+                                                     adk + (uint64_t)i * a_win + (uint64_t)(h * ns), idesc, acc);
                             }
                         }
                     }
@@ -250,41 +286,46 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
             epi_sync();  // every epilogue thread sees the same abort decision
             if (*(volatile int *)abort_flag) break;
             tc::fence_after_sync();
-            if (a.orient == 0) {
+            if (ORIENT == 0) {
                 // rows = positions; thread: row 32q + lane of subtiles j = hsel, hsel + 2, ...
                 const int w = t;
                 const int MT = a.Lout / 128;
                 const int cg = a.Cout / a.G;
-                float s[16], qq[16];
+                // per-warp group partials in red[e][g] (sum) and red[e][16 + g] (sum of squares)
+                if (lane < 32) red[e * 32 + lane] = 0.f;
+                __syncwarp();
+                for (int c0 = 0; c0 < a.Cout; c0 += 16) {
+                    // per-channel sums of this 16-channel chunk over the thread's subtiles
+                    // (up to 4 TMEM loads in flight, one wait) ...
+                    float cs[16], cq[16];
 #pragma unroll
-                for (int g = 0; g < 16; ++g) s[g] = qq[g] = 0.f;
-                for (int j = hsel; j < MT; j += 2)
-                    for (int c0 = 0; c0 < a.Cout; c0 += 16) {
-                        float v[16];
-                        tc::tmem_ld16(tq + (uint32_t)(j * a.Cout + c0), v);
+                    for (int c = 0; c < 16; ++c) cs[c] = cq[c] = 0.f;
+                    for (int j0 = hsel; j0 < MT; j0 += 8) {
+                        uint32_t r[4][16];
+                        const int nj = min(4, (MT - j0 + 1) / 2);
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            const int g = (c0 + c) / cg;
+                        for (int u = 0; u < 4; ++u)
+                            if (u < nj) tc::tmem_ld16_nowait(tq + (uint32_t)((j0 + 2 * u) * a.Cout + c0), r[u]);
+                        tc::tmem_wait_ld();
 #pragma unroll
-                            for (int gg = 0; gg < 16; ++gg)
-                                if (gg == g) {
-                                    s[gg] += v[c];
-                                    qq[gg] = fmaf(v[c], v[c], qq[gg]);
+                        for (int u = 0; u < 4; ++u)
+                            if (u < nj) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) {
+                                    const float v = __uint_as_float(r[u][c]);
+                                    cs[c] += v;
+                                    cq[c] = fmaf(v, v, cq[c]);
                                 }
-                        }
+                            }
                     }
-#pragma unroll
-                for (int g = 0; g < 16; ++g)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        s[g] += __shfl_xor_sync(0xffffffffu, s[g], o);
-                        qq[g] += __shfl_xor_sync(0xffffffffu, qq[g], o);
+                    // ... folded into the chunk's groups and reduced over the warp
+                    switch (cg) {
+                        case 4: fold_chunk<4>(cs, cq, c0, lane, red + e * 32); break;
+                        case 8: fold_chunk<8>(cs, cq, c0, lane, red + e * 32); break;
+                        case 16: fold_chunk<16>(cs, cq, c0, lane, red + e * 32); break;
+                        default: fold_chunk<32>(cs, cq, c0, lane, red + e * 32); break;
                     }
-                if (lane == 0)
-                    for (int g = 0; g < 16; ++g) {
-                        red[e * 32 + g] = s[g];
-                        red[e * 32 + 16 + g] = qq[g];
-                    }
+                }
                 epi_sync();
                 if (et < a.Cout) {
                     const int g = et / cg;
@@ -302,32 +343,31 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                 }
                 epi_sync();
                 const size_t ld = (size_t)(a.Lout + 2) * a.Cout;  // elements per window
-                __nv_bfloat16 *ow = a.out + (size_t)w * ld;
-                const __nv_bfloat16 *rw = a.res ? a.res + (size_t)w * ld : nullptr;
+                __nv_bfloat16 *__restrict__ ow = a.out + (size_t)w * ld;
+                const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + (size_t)w * ld : nullptr;
                 for (int j = hsel; j < MT; j += 2) {
                     const int row = 128 * j + 32 * q + lane + 1;
-                    for (int c0 = 0; c0 < a.Cout; c0 += 16) {
-                        float v[16];
-                        tc::tmem_ld16(tq + (uint32_t)(j * a.Cout + c0), v);
-                        float rv[16];
+                    for (int c0 = 0; c0 < a.Cout; c0 += 32) {
+                        uint4 rr[4];
                         if (rw) {
                             const uint4 *rp = reinterpret_cast<const uint4 *>(rw + (size_t)row * a.Cout + c0);
-                            const uint4 r0 = rp[0], r1 = rp[1];
-                            const uint32_t u[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                rv[2 * i] = __uint_as_float(u[i] << 16);
-                                rv[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
-                            }
+                            for (int i = 0; i < 4; ++i) rr[i] = __ldg(rp + i);
                         }
-                        uint32_t pk[8];
+                        float v[32];
+                        tc::tmem_ld32(tq + (uint32_t)(j * a.Cout + c0), v);
+                        uint32_t pk[16];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
+                        for (int i = 0; i < 16; ++i) {
                             float x0 = fmaf(v[2 * i], scale[c0 + 2 * i], shift[c0 + 2 * i]);
                             float x1 = fmaf(v[2 * i + 1], scale[c0 + 2 * i + 1], shift[c0 + 2 * i + 1]);
                             if (rw) {
-                                x0 += rv[2 * i];
-                                x1 += rv[2 * i + 1];
+                                const uint32_t u = (i & 3) == 0 ? rr[i >> 2].x
+                                                   : (i & 3) == 1 ? rr[i >> 2].y
+                                                   : (i & 3) == 2 ? rr[i >> 2].z
+                                                                  : rr[i >> 2].w;
+                                x0 += __uint_as_float(u << 16);
+                                x1 += __uint_as_float(u & 0xffff0000u);
                             }
                             if (a.relu) {
                                 x0 = fmaxf(x0, 0.f);
@@ -337,8 +377,8 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                             pk[i] = *reinterpret_cast<uint32_t *>(&b2);
                         }
                         uint4 *op = reinterpret_cast<uint4 *>(ow + (size_t)row * a.Cout + c0);
-                        op[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        op[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) op[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
                     }
                     if (row == 1 || row == a.Lout) {  // zero pad rows
                         uint4 *zp = reinterpret_cast<uint4 *>(ow + (size_t)(row == 1 ? 0 : a.Lout + 1) * a.Cout);
@@ -356,11 +396,11 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                 for (int i = hsel; i < a.wpc; i += 2) {
                     const int w = w0 + i;
                     float s = 0.f, qq = 0.f;
-                    for (int p0 = 0; p0 < a.Lout; p0 += 16) {
-                        float v[16];
-                        tc::tmem_ld16(tq + (uint32_t)(i * a.Lout + p0), v);
+                    for (int p0 = 0; p0 < a.Lout; p0 += 32) {
+                        float v[32];
+                        tc::tmem_ld32(tq + (uint32_t)(i * a.Lout + p0), v);
 #pragma unroll
-                        for (int p = 0; p < 16; ++p) {
+                        for (int p = 0; p < 32; ++p) {
                             s += v[p];
                             qq = fmaf(v[p], v[p], qq);
                         }
@@ -376,18 +416,23 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     const float sh = bet - mean * sc;
                     if (w >= a.n_win) continue;
                     const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
-                    __nv_bfloat16 *ow = a.out + (size_t)w * ld + c;
-                    const __nv_bfloat16 *rw = a.res ? a.res + (size_t)w * ld + c : nullptr;
-                    for (int p0 = 0; p0 < a.Lout; p0 += 16) {
-                        float v[16];
-                        tc::tmem_ld16(tq + (uint32_t)(i * a.Lout + p0), v);
+                    __nv_bfloat16 *__restrict__ ow = a.out + (size_t)w * ld + c;
+                    const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + (size_t)w * ld + c : nullptr;
+                    for (int p0 = 0; p0 < a.Lout; p0 += 32) {
+                        float rv[32];
+                        if (rw) {
 #pragma unroll
-                        for (int p = 0; p < 16; ++p) {
-                            const size_t o = (size_t)(p0 + p + 1) * a.Cout;
+                            for (int p = 0; p < 32; ++p)
+                                rv[p] = __bfloat162float(__ldg(rw + (size_t)(p0 + p + 1) * a.Cout));
+                        }
+                        float v[32];
+                        tc::tmem_ld32(tq + (uint32_t)(i * a.Lout + p0), v);
+#pragma unroll
+                        for (int p = 0; p < 32; ++p) {
                             float x = fmaf(v[p], sc, sh);
-                            if (rw) x += __bfloat162float(rw[o]);
+                            if (rw) x += rv[p];
                             if (a.relu) x = fmaxf(x, 0.f);
-                            ow[o] = __float2bfloat16_rn(x);
+                            ow[(size_t)(p0 + p + 1) * a.Cout] = __float2bfloat16_rn(x);
                         }
                     }
                     ow[0] = __float2bfloat16_rn(0.f);
@@ -467,6 +512,11 @@ struct TcPlan {
     void *mem = nullptr;
 };
 
+// position-major tiles only where a 128-channel slice does not exist (C_out < 128)
+static bool use_pos(const ConvLayer &C) {
+    return C.cout < 128 && C.lout % 128 == 0 && (C.lout / 128) * C.cout <= 512;
+}
+
 static void fill_geometry(const ConvLayer &C, int G, float eps, TcLayer &T) {
     LayerArgs &a = T.a;
     memset(&a, 0, sizeof a);
@@ -477,7 +527,7 @@ static void fill_geometry(const ConvLayer &C, int G, float eps, TcLayer &T) {
     a.taps = C.k;
     a.G = G;
     a.eps = eps;
-    const bool pos = (C.lout % 128 == 0) && (C.lout / 128) * C.cout <= 512 && C.cout <= 256;
+    const bool pos = use_pos(C);
     a.orient = pos ? 0 : 1;
     T.view_c = C.stride * C.cin;
     T.view_rows = (C.lin + 2) / C.stride;
@@ -503,7 +553,8 @@ static void fill_geometry(const ConvLayer &C, int G, float eps, TcLayer &T) {
         a.slices = 1;
         a.w_block_bytes = (uint32_t)(C.k * C.cin * C.cout * 2);
     } else {
-        a.wpc = 384 / C.lout;
+        a.wpc = std::max(1, 384 / C.lout);
+        a.nsplit = (C.lout + 255) / 256;
         a.slices = C.cout / 128;
         a.KB = (C.stride == 2 && C.k == 3) ? 32 : 64;
         a.n_kb = C.cin / a.KB;
@@ -558,8 +609,11 @@ static bool full_net_supported(const afg_ctx *ctx) {
     for (size_t i = 1; i < P.convs.size(); ++i) {
         const ConvLayer &C = P.convs[i];
         if (C.cin % 64 || C.cout % 64 || C.cout > 512) return false;
-        const bool pos = (C.lout % 128 == 0) && (C.lout / 128) * C.cout <= 512 && C.cout <= 256;
-        if (!pos && (C.cout % 128 || 384 % C.lout || C.lout % 16 || C.lout > 256 || C.cout / P.net.groups > 32))
+        const bool pos = use_pos(C);
+        const int nsplit = (C.lout + 255) / 256;
+        const int wpc = std::max(1, 384 / C.lout);
+        if (!pos && (C.cout % 128 || C.lout % nsplit || (C.lout / nsplit) % 16 || wpc * C.lout > 512 ||
+                     C.lout % 32 || C.cout / P.net.groups > 32))
             return false;
         if (pos && (C.cout / P.net.groups > 32 || P.net.groups > 16)) return false;
     }
@@ -595,7 +649,8 @@ int net_tc_layers_prepare(afg_ctx *ctx) {
         AFG_CUDA(ctx, cudaMemcpy(tp->layers[i].wimg, imgs[i].data(), imgs[i].size() * 2, cudaMemcpyHostToDevice));
         off += (imgs[i].size() * 2 + 1023) / 1024 * 1024;
     }
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     ctx->tcplan = tp;
     return AFG_OK;
 }
@@ -637,7 +692,8 @@ static int conv_tc(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, cons
     const double bytes = 2.0 * nw * ((double)(C.lin + 2) * C.cin + (double)(C.lout + 2) * C.cout * (res ? 2 : 1)) +
                          2.0 * C.k * C.cin * C.cout;
     KScope ks(ctx, st, KK_CONV_TC, flops, bytes);
-    k_conv_tc<<<grid, LT, layer_smem(a).total, st>>>(map, a);
+    if (a.orient == 0) k_conv_tc<0><<<grid, LT, layer_smem(a).total, st>>>(map, a);
+    else k_conv_tc<1><<<grid, LT, layer_smem(a).total, st>>>(map, a);
     AFG_LAUNCH_CHECK(ctx, "k_conv_tc");
     return AFG_OK;
 }
