@@ -207,6 +207,41 @@ def roofline_for(dom: dict, peaks: dict, step_ms_total: float) -> dict:
             "share_of_step": dom["total_ms"] / max(step_ms_total, 1e-9)}
 
 
+def time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world):
+    """The same workload through the BF16 tensor-core network (context of its own),
+    timed like the FP32 value; returned as a sub-result with the ratio to FP32."""
+    import torch
+
+    from paper_2403_18661_gb300 import abi
+    ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
+    out = None
+    for _ in range(args.warmup):
+        out = ctx.analyze(xd, trig_cap=65536, out=out)
+    ctx.sync()
+    ctx.profile_enable(True)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.analyze(xd, trig_cap=65536, out=out)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ctx.profile_enable(False)
+    kstats = ctx.profile_read()
+    ctx.sync()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    value, _, job_s = pdist.job_throughput(wl.n_win * wl.stride / wl.fs * args.steps, total_ms / 1000.0, world)
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    ctx.close()
+    return {"value": value, "unit": "strain-s/s", "ms_per_step": job_s * 1000.0 / args.steps, "dtype": "bf16",
+            "roofline": roofline_for(dom, peaks, job_s * 1000.0),
+            "gpu_launches": int(sum(k["launches"] for k in kstats))}
+
+
 def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
@@ -312,12 +347,16 @@ def run_ours(args):
                "h2d_bytes_per_step": int(x.nbytes),
                "d2h_bytes_per_step": int(stat_h.numel() * 4 + 8 + trig_cap * 8)}
 
+    peaks = load_peaks()
+    bf16 = None  # same workload through the BF16 tensor-core network (every rank: it reduces across ranks)
+    if precision == abi.AFG_FP32 and not args.no_bf16 and wl.net == inputs.RESNET34_NET:
+        bf16 = time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world)
+        bf16["ratio_vs_fp32"] = bf16["value"] / value
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    peaks = load_peaks()
     launches = int(sum(k["launches"] for k in kstats))
     dom = max(kstats, key=lambda k: k["total_ms"])
     roofline = roofline_for(dom, peaks, total_ms)
@@ -338,6 +377,7 @@ def run_ours(args):
                       "net": "resnet34-1d-gn16" if wl.net == inputs.RESNET34_NET else "tiny-1d-gn8",
                       "precision": args.precision, "l2": "flushed between steps (512 MiB write)"},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+           "bf16": bf16,
            "clocks": clocks, "kernels": kernels}
     print(json.dumps(out), flush=True)
     ctx.close()
@@ -549,6 +589,7 @@ def main():
     ap.add_argument("--n-win", type=int, default=0, help="analyse this many windows instead (smaller workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 comparison of the FP32 workload")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -188,8 +188,11 @@ __global__ void __launch_bounds__(GN_T) k_groupnorm(float *__restrict__ x, int L
 // ---------------------------------------------------------------- conv GEMM
 // out[w][t+1][n] = sum_kk A[w,t][kk] * Wt[kk][n],  A[w,t][kk] = in[w][t*s + off][kk]
 // (kk runs over k*Cin contiguous floats).  M = n_win * Lout rows.
+// Tiles of BM x BN per CTA (256 threads, TM x TN outputs each), K in steps of
+// BK: the next step's A/B tiles are loaded into registers while the current
+// step is multiplied out of shared memory (double-buffered, one barrier per step).
 template <int BM, int BN, int TM, int TN>
-__global__ void __launch_bounds__(256) k_conv_fp32(const float *__restrict__ in, const float *__restrict__ wt,
+__global__ void __launch_bounds__(256, 2) k_conv_fp32(const float *__restrict__ in, const float *__restrict__ wt,
                                                    float *__restrict__ out, int M, int Lout, int Lp_in, int Lp_out,
                                                    int Cin, int Cout, int K, int s, int off) {
     constexpr int BK = 16;
@@ -197,8 +200,9 @@ __global__ void __launch_bounds__(256) k_conv_fp32(const float *__restrict__ in,
     constexpr int A_F4 = BM * BK / 4;  // float4 loads per A tile
     constexpr int B_F4 = BK * BN / 4;
     constexpr int A_PER = (A_F4 + 255) / 256;
-    __shared__ __align__(16) float As[BK][BM + 4];
-    __shared__ __align__(16) float Bs[BK][BN];
+    constexpr int B_PER = (B_F4 + 255) / 256;
+    __shared__ __align__(16) float As[2][BK][BM + 4];
+    __shared__ __align__(16) float Bs[2][BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -219,42 +223,67 @@ __global__ void __launch_bounds__(256) k_conv_fp32(const float *__restrict__ in,
             arow[i] = nullptr;
         }
     }
+    float4 ra[A_PER], rb[B_PER];
+    auto load_tiles = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < A_PER; ++i) {
+            const int f = tid + i * 256;
+            ra[i] = (f < A_F4 && arow[i]) ? __ldg(reinterpret_cast<const float4 *>(arow[i] + k0 + acol[i]))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < B_PER; ++i) {
+            const int f = tid + i * 256;
+            if (f < B_F4) {
+                const int r = f / (BN / 4), c = (f % (BN / 4)) * 4;
+                rb[i] = __ldg(reinterpret_cast<const float4 *>(wt + (int64_t)(k0 + r) * Cout + n0 + c));
+            }
+        }
+    };
+    auto store_tiles = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < A_PER; ++i) {
+            const int f = tid + i * 256;
+            if (f < A_F4) {
+                As[buf][acol[i] + 0][amrow[i]] = ra[i].x;
+                As[buf][acol[i] + 1][amrow[i]] = ra[i].y;
+                As[buf][acol[i] + 2][amrow[i]] = ra[i].z;
+                As[buf][acol[i] + 3][amrow[i]] = ra[i].w;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < B_PER; ++i) {
+            const int f = tid + i * 256;
+            if (f < B_F4) {
+                const int r = f / (BN / 4), c = (f % (BN / 4)) * 4;
+                *reinterpret_cast<float4 *>(&Bs[buf][r][c]) = rb[i];
+            }
+        }
+    };
     float acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
 
+    load_tiles(0);
+    store_tiles(0);
+    __syncthreads();
+    int cur = 0;
     for (int k0 = 0; k0 < K; k0 += BK) {
-#pragma unroll
-        for (int i = 0; i < A_PER; ++i) {
-            int f = tid + i * 256;
-            if (f < A_F4) {
-                float4 v = arow[i] ? *reinterpret_cast<const float4 *>(arow[i] + k0 + acol[i])
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-                As[acol[i] + 0][amrow[i]] = v.x;
-                As[acol[i] + 1][amrow[i]] = v.y;
-                As[acol[i] + 2][amrow[i]] = v.z;
-                As[acol[i] + 3][amrow[i]] = v.w;
-            }
-        }
-        for (int f = tid; f < B_F4; f += 256) {
-            int r = f / (BN / 4), c = (f % (BN / 4)) * 4;
-            *reinterpret_cast<float4 *>(&Bs[r][c]) =
-                *reinterpret_cast<const float4 *>(wt + (int64_t)(k0 + r) * Cout + n0 + c);
-        }
-        __syncthreads();
+        const bool more = k0 + BK < K;
+        if (more) load_tiles(k0 + BK);  // global loads in flight during the math below
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             float a[TM], b[TN];
 #pragma unroll
             for (int i = 0; i < TM; i += 4) {
-                float4 v = *reinterpret_cast<const float4 *>(&As[kk][ty * TM + i]);
+                float4 v = *reinterpret_cast<const float4 *>(&As[cur][kk][ty * TM + i]);
                 a[i] = v.x; a[i + 1] = v.y; a[i + 2] = v.z; a[i + 3] = v.w;
             }
 #pragma unroll
             for (int j = 0; j < TN; j += 4) {
-                float4 v = *reinterpret_cast<const float4 *>(&Bs[kk][tx * TN + j]);
+                float4 v = *reinterpret_cast<const float4 *>(&Bs[cur][kk][tx * TN + j]);
                 b[j] = v.x; b[j + 1] = v.y; b[j + 2] = v.z; b[j + 3] = v.w;
             }
 #pragma unroll
@@ -262,7 +291,9 @@ __global__ void __launch_bounds__(256) k_conv_fp32(const float *__restrict__ in,
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
+        if (more) store_tiles(cur ^ 1);
         __syncthreads();
+        cur ^= 1;
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
