@@ -207,6 +207,23 @@ def roofline_for(dom: dict, peaks: dict, step_ms_total: float) -> dict:
             "share_of_step": dom["total_ms"] / max(step_ms_total, 1e-9)}
 
 
+def tune_tiles(ctx, stream, n_win: int = 1024):
+    """Autotune the conv tiles of a BF16 context (set-up, outside every timed region).
+    Returns a summary, or None where the network runs fused (no per-layer tiles)."""
+    from paper_2403_18661_gb300 import abi
+    try:
+        ctx.autotune(n_win, stream=stream)
+    except abi.AfgError as e:
+        if e.status == abi.AFG_ERR_UNSUPPORTED:
+            return None
+        raise
+    tiles = ctx.tiles()
+    return {"n_win": n_win, "layers": len(tiles),
+            "sum_us_default": round(sum(t["us_default"] for t in tiles), 1),
+            "sum_us_chosen": round(sum(t["us_chosen"] for t in tiles), 1),
+            "chosen": sorted({(t["orient"], t["wpc"], t["kb"], t["stages"], t["acc_bufs"]) for t in tiles})}
+
+
 def time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world):
     """The same workload through the BF16 tensor-core network (context of its own),
     timed like the FP32 value; returned as a sub-result with the ratio to FP32."""
@@ -214,6 +231,7 @@ def time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world):
 
     from paper_2403_18661_gb300 import abi
     ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
+    tiles = None if args.no_tune else tune_tiles(ctx, stream)
     out = None
     for _ in range(args.warmup):
         out = ctx.analyze(xd, trig_cap=65536, out=out)
@@ -239,7 +257,7 @@ def time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world):
     ctx.close()
     return {"value": value, "unit": "strain-s/s", "ms_per_step": job_s * 1000.0 / args.steps, "dtype": "bf16",
             "roofline": roofline_for(dom, peaks, job_s * 1000.0),
-            "gpu_launches": int(sum(k["launches"] for k in kstats))}
+            "gpu_launches": int(sum(k["launches"] for k in kstats)), "tiles": tiles}
 
 
 def run_reference(args):
@@ -289,6 +307,7 @@ def run_ours(args):
     precision = abi.AFG_BF16 if args.precision == "bf16" else abi.AFG_FP32
     ctx = abi.Context(wl, w, precision=precision)
     xd = torch.from_numpy(x).to(dev)
+    tiles = tune_tiles(ctx, torch.cuda.current_stream()) if precision == abi.AFG_BF16 and not args.no_tune else None
     trig_cap = 65536
     out = (torch.empty(wl.n_win, dtype=torch.float32, device=dev),
            torch.empty(wl.n_win - wl.n_int + 1, dtype=torch.float32, device=dev),
@@ -377,7 +396,7 @@ def run_ours(args):
                       "net": "resnet34-1d-gn16" if wl.net == inputs.RESNET34_NET else "tiny-1d-gn8",
                       "precision": args.precision, "l2": "flushed between steps (512 MiB write)"},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-           "bf16": bf16,
+           "bf16": bf16, "tiles": tiles,
            "clocks": clocks, "kernels": kernels}
     print(json.dumps(out), flush=True)
     ctx.close()
@@ -590,6 +609,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 comparison of the FP32 workload")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default conv tiles (no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -351,6 +351,51 @@ int afg_profile_enable(afg_ctx *ctx, int32_t on);
  * *n_out, and reset the counters.  Errors: AFG_ERR_ARG for NULL pointers. */
 int afg_profile_read(afg_ctx *ctx, afg_kernel_stat *out, int32_t cap, int32_t *n_out);
 
+/* ---------------------------------------------------------------- conv tile autotuning */
+
+/* Tile of one convolution of the BF16 tensor-core path for wide networks
+ * (widths 64..512: every convolution after the stem is one tcgen05 implicit
+ * GEMM launch).  The network is the 1D ResNet of Sec. II; the tiles are an
+ * implementation choice with no counterpart in the paper.  Every tile of a
+ * layer computes the same convolution (accumulation order aside). */
+typedef struct afg_tile {
+    int32_t layer;        /* convolution index in execution order (1 = first after the stem) */
+    int32_t cin, cout, lin, lout, stride, taps;
+    int32_t residual;     /* 1 if the epilogue adds the block's shortcut */
+    int32_t orient;       /* 0: position-major (M = 128 positions, N = C_out, C_out <= 128);
+                             1: channel-major (M = 128 output channels, N = positions of `wpc` windows) */
+    int32_t wpc;          /* windows per tile (1 for position-major) */
+    int32_t kb;           /* input channels per K-block (32, 64 or 128; C_in for position-major) */
+    int32_t stages;       /* shared-memory ring depth, 1..8 */
+    int32_t acc_bufs;     /* TMEM accumulator buffers: 2 overlaps a tile's epilogue with the next tile's MMAs */
+    int32_t tuned;        /* 1: chosen by afg_autotune (or set so by afg_tiles_set); 0: default heuristic */
+    int32_t n_candidates; /* tiles timed for this layer's geometry */
+    float us_chosen;      /* microseconds per launch of the chosen tile at the tuning size (0: not timed) */
+    float us_default;     /* microseconds per launch of the default tile at the tuning size (0: not timed) */
+} afg_tile;
+
+/* Time every valid tile of each distinct layer geometry (channels, lengths,
+ * stride, taps, residual) on n_win synthetic windows (n_win <= 0: 1024; at
+ * most 4096) and keep the fastest for later inference calls.  Synchronous:
+ * synchronises `stream` and returns when done.  Uses the context's activation
+ * workspaces.  Errors: AFG_ERR_UNSUPPORTED if the context has no per-layer
+ * tensor-core plan (FP32 contexts, or the fused 16-channel network);
+ * AFG_ERR_STATE if `stream` is capturing; AFG_ERR_TIMEOUT if a bounded
+ * device wait gave up; AFG_ERR_CUDA / AFG_ERR_OOM / AFG_ERR_BUDGET. */
+int afg_autotune(afg_ctx *ctx, int64_t n_win, void *stream);
+
+/* Current tile of every convolution after the stem, in execution order:
+ * writes min(cap, count) entries to out and the count to *n_out. */
+int afg_tiles_get(afg_ctx *ctx, afg_tile *out, int32_t cap, int32_t *n_out);
+
+/* Every tile the tuner would time for `layer` (the timing fields are 0). */
+int afg_tile_candidates(afg_ctx *ctx, int32_t layer, afg_tile *out, int32_t cap, int32_t *n_out);
+
+/* Apply tiles (e.g. a saved tuning): each entry's layer, orient, wpc, kb,
+ * stages and acc_bufs.  All entries are checked first; AFG_ERR_ARG (and no
+ * change) if one does not fit its layer. */
+int afg_tiles_set(afg_ctx *ctx, const afg_tile *tiles, int32_t n);
+
 /* ---------------------------------------------------------------- allocation-free PSD */
 
 /* Largest n_det * (distinct Welch segments) one afg_psd_estimate_noalloc call accepts. */

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libaframe_gb.so")
 AFG_OK = 0
 AFG_FP32 = 0
 AFG_BF16 = 1
+AFG_ERR_ARG, AFG_ERR_CUDA, AFG_ERR_OOM, AFG_ERR_BUDGET = -1, -2, -3, -4
+AFG_ERR_TIMEOUT, AFG_ERR_STATE, AFG_ERR_NAN, AFG_ERR_UNSUPPORTED = -5, -6, -7, -8
 _ERRORS = {-1: "AFG_ERR_ARG", -2: "AFG_ERR_CUDA", -3: "AFG_ERR_OOM", -4: "AFG_ERR_BUDGET",
            -5: "AFG_ERR_TIMEOUT", -6: "AFG_ERR_STATE", -7: "AFG_ERR_NAN", -8: "AFG_ERR_UNSUPPORTED"}
 
@@ -72,6 +74,17 @@ class AfgStreamResult(ctypes.Structure):
                 ("t_push", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
+class AfgTile(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("layer", "cin", "cout", "lin", "lout", "stride", "taps", "residual",
+                                               "orient", "wpc", "kb", "stages", "acc_bufs", "tuned",
+                                               "n_candidates")] + \
+               [("us_chosen", ctypes.c_float), ("us_default", ctypes.c_float)]
+
+
+def _tile_dict(t: AfgTile) -> dict:
+    return {name: getattr(t, name) for name, _ in AfgTile._fields_}
+
+
 STREAM_RESULT_DTYPE = np.dtype([("window", np.int64), ("stat", np.float32), ("logit", np.float32),
                                 ("t_push", np.float64), ("t_done", np.float64)])
 
@@ -110,6 +123,10 @@ SIGNATURES = {
     "afg_stream_stats": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
     "afg_profile_enable": ([_vp, _i32], ctypes.c_int),
     "afg_profile_read": ([_vp, ctypes.POINTER(AfgKernelStat), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
+    "afg_autotune": ([_vp, _i64, _vp], ctypes.c_int),
+    "afg_tiles_get": ([_vp, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
+    "afg_tile_candidates": ([_vp, _i32, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
+    "afg_tiles_set": ([_vp, ctypes.POINTER(AfgTile), _i32], ctypes.c_int),
     "afg_psd_estimate_noalloc": ([_vp, _i64, _i32, _i64, _i64, _i64, _i32, _i32, _vp, _vp], ctypes.c_int),
 }
 
@@ -242,6 +259,34 @@ class Context:
         self._check(self._lib.afg_profile_read(self._h, arr, cap, ctypes.byref(n)))
         return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, total_ms=a.total_ms,
                      algo_flops=a.algo_flops, algo_bytes=a.algo_bytes) for a in arr[:min(n.value, cap)]]
+
+    # ---------------------------------------------------------------- conv tiles
+    def autotune(self, n_win: int = 1024, stream=None):
+        """Time every tile of each layer geometry of the BF16 tensor-core path and keep the fastest."""
+        self._check(self._lib.afg_autotune(self._h, int(n_win), _stream(stream)))
+
+    def tiles(self) -> list:
+        cap = 256
+        arr = (AfgTile * cap)()
+        n = _i32()
+        self._check(self._lib.afg_tiles_get(self._h, arr, cap, ctypes.byref(n)))
+        return [_tile_dict(t) for t in arr[:min(n.value, cap)]]
+
+    def tile_candidates(self, layer: int) -> list:
+        cap = 256
+        arr = (AfgTile * cap)()
+        n = _i32()
+        self._check(self._lib.afg_tile_candidates(self._h, int(layer), arr, cap, ctypes.byref(n)))
+        return [_tile_dict(t) for t in arr[:min(n.value, cap)]]
+
+    def set_tiles(self, tiles: list):
+        """Apply tiles given as dicts with the afg_tile fields (e.g. a saved tuning)."""
+        arr = (AfgTile * max(1, len(tiles)))()
+        for i, d in enumerate(tiles):
+            for name, _ in AfgTile._fields_:
+                if name in d:
+                    setattr(arr[i], name, d[name])
+        self._check(self._lib.afg_tiles_set(self._h, arr, len(tiles)))
 
     # ---------------------------------------------------------------- hot path
     def psd_estimate(self, x, n_psd: int = 1, psd_step: int = 0, psd_span: Optional[int] = None, out=None,

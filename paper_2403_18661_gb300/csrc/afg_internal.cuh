@@ -226,6 +226,10 @@ void net_tc_layers_release(afg_ctx *ctx);
 bool net_tc_layers_available(const afg_ctx *ctx);
 int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                            int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
+int net_tc_autotune(afg_ctx *ctx, int64_t n_win, cudaStream_t st);
+int net_tc_tiles_get(afg_ctx *ctx, afg_tile *out, int cap, int *n_out);
+int net_tc_tile_candidates(afg_ctx *ctx, int layer, afg_tile *out, int cap, int *n_out);
+int net_tc_tiles_set(afg_ctx *ctx, const afg_tile *in, int n);
 // net_tc.cu
 int net_tc_prepare(afg_ctx *ctx);
 int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, const SegDesc *segs_dev, int n_seg,

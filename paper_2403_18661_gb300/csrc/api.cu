@@ -353,4 +353,38 @@ int afg_analyze_host(afg_ctx *ctx, const float *x_host, const afg_run_params *p,
     return AFG_OK;
 }
 
+int afg_autotune(afg_ctx *ctx, int64_t n_win, void *stream) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    return net_tc_autotune(ctx, n_win, S(stream));
+}
+
+int afg_tiles_get(afg_ctx *ctx, afg_tile *out, int32_t cap, int32_t *n_out) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (!n_out || cap < 0 || (cap > 0 && !out)) return afg_fail(ctx, AFG_ERR_ARG, "tiles_get: bad output arguments");
+    int n = 0;
+    int rc = net_tc_tiles_get(ctx, out, cap, &n);
+    *n_out = n;
+    return rc;
+}
+
+int afg_tile_candidates(afg_ctx *ctx, int32_t layer, afg_tile *out, int32_t cap, int32_t *n_out) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (!n_out || cap < 0 || (cap > 0 && !out))
+        return afg_fail(ctx, AFG_ERR_ARG, "tile_candidates: bad output arguments");
+    int n = 0;
+    int rc = net_tc_tile_candidates(ctx, layer, out, cap, &n);
+    *n_out = n;
+    return rc;
+}
+
+int afg_tiles_set(afg_ctx *ctx, const afg_tile *tiles, int32_t n) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && !tiles)) return afg_fail(ctx, AFG_ERR_ARG, "tiles_set: bad arguments");
+    return net_tc_tiles_set(ctx, tiles, n);
+}
+
 }  // extern "C"

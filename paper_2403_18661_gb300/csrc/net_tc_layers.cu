@@ -14,12 +14,21 @@
 // half / odd half / even half one pair-row down (the 1x1 stride-2 shortcut
 // reads the odd half).
 //
-// Orientations (both keep one tile's accumulators in 384 TMEM columns):
+// Orientations:
 //   POS  M = 128 output positions per MMA, N = C_out; a tile is one window;
 //        weights resident in shared memory; the window's input is one K-block.
 //   CH   M = 128 output channels per MMA, N = L_out positions; a tile is a
 //        128-channel slice x wpc windows; K-blocks of KB input channels
 //        stream weights (bulk copy) and activations (TMA) through a ring.
+// A tile's accumulators take at most 512 TMEM columns; tiles of at most 256
+// columns may use two accumulator buffers, so that the epilogue of one tile
+// overlaps the MMAs of the next.  The tile knobs (orientation, windows per
+// tile, KB, ring depth, accumulator buffers) are chosen per layer geometry by
+// measurement (net_tc_autotune) or by a default heuristic.
+//
+// Weight image of a layer (BF16, K-major core matrices): slices of
+// Ms = min(C_out, 128) output channels, [slice][C_in/8][tap][Ms][8], so one
+// K-block of any KB is a contiguous run and one image serves every knob.
 #include <cuda.h>
 #include <stdio.h>
 #include <string.h>
@@ -37,6 +46,8 @@ constexpr int EPI_W0 = 4;          // first epilogue warp
 constexpr int EPI_WARPS = 8;
 constexpr int EPI_T = EPI_WARPS * 32;
 constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr int NB_MAX = 8;          // deepest shared-memory ring
+constexpr uint32_t SMEM_LIMIT = 227 * 1024;
 
 struct LayerArgs {
     int orient;          // 0 POS, 1 CH
@@ -50,7 +61,8 @@ struct LayerArgs {
     int n_kb;            // K-blocks per tile
     int wpc, slices;     // CH tiling
     int nsplit;          // CH: MMAs per window along N (L_out / nsplit <= 256 positions each)
-    int NB;              // pipeline stages
+    int NB;              // pipeline stages (<= NB_MAX)
+    int nacc;            // TMEM accumulator buffers (1, or 2 with buffer b at column 256 b)
     int G;
     float eps;
     int relu;
@@ -77,7 +89,7 @@ __host__ __device__ inline LSmem layer_smem(const LayerArgs &a) {
     s.off_red = align_up(s.off_act + a.act_stage_bytes * a.NB, 16);
     s.off_sc = s.off_red + EPI_WARPS * 32 * 4;
     s.off_bar = align_up(s.off_sc + 2 * 512 * 4, 16);
-    s.total = s.off_bar + 8 * (2 * 4 + 4) + 16;
+    s.total = s.off_bar + 8 * (2 * NB_MAX + 5) + 16;  // full, empty, acc_full[2], acc_empty[2], wbar; slot, flag
     return s;
 }
 
@@ -131,6 +143,32 @@ __device__ __forceinline__ void fold_chunk(const float (&cs)[16], const float (&
     }
 }
 
+// Channel-major epilogue store of 16 * NQ consecutive positions of one channel: normalise
+// the accumulators (one TMEM wait), add the residual, ReLU, BF16 store into padded row p + 1.
+template <int NQ>
+__device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, float sh,
+                                         const __nv_bfloat16 *__restrict__ rw, __nv_bfloat16 *__restrict__ ow, int C,
+                                         int relu) {
+    float rv[16 * NQ];
+    if (rw) {
+#pragma unroll
+        for (int p = 0; p < 16 * NQ; ++p) rv[p] = __bfloat162float(__ldg(rw + (size_t)(p_first + p + 1) * C));
+    }
+    uint32_t r[NQ][16];
+#pragma unroll
+    for (int g = 0; g < NQ; ++g) tc::tmem_ld16_nowait(taddr + (uint32_t)(16 * g), r[g]);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int g = 0; g < NQ; ++g)
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            float x = fmaf(__uint_as_float(r[g][p]), sc, sh);
+            if (rw) x += rv[16 * g + p];
+            if (relu) x = fmaxf(x, 0.f);
+            ow[(size_t)(p_first + 16 * g + p + 1) * C] = __float2bfloat16_rn(x);
+        }
+}
+
 template <int ORIENT>
 __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const LayerArgs a) {
     // ORIENT (= a.orient) is compile-time: each instantiation keeps only its own path
@@ -142,10 +180,10 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
     float *scale = reinterpret_cast<float *>(sm + L.off_sc);
     float *shift = scale + 512;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + L.off_bar);
-    uint64_t *empty = full + 4;
-    uint64_t *acc_full = empty + 4;
-    uint64_t *acc_empty = acc_full + 1;
-    uint64_t *wbar = acc_empty + 1;
+    uint64_t *empty = full + NB_MAX;
+    uint64_t *acc_full = empty + NB_MAX;  // [2]
+    uint64_t *acc_empty = acc_full + 2;   // [2]
+    uint64_t *wbar = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -160,8 +198,10 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
-        tc::mbar_init(acc_full, 1);
-        tc::mbar_init(acc_empty, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 1);
+        }
         tc::mbar_init(wbar, 1);
         tc::fence_mbar_init();
         *abort_flag = 0;
@@ -195,7 +235,7 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     const uint32_t wb = ORIENT == 1 ? a.w_block_bytes : 0;
                     tc::mbar_expect_tx(&full[s], a.act_stage_bytes + wb);
                     if (ORIENT == 1) {
-                        const unsigned char *src = a.wimg + ((size_t)slice * a.n_kb + kb) * a.w_block_bytes;
+                        const unsigned char *src = a.wimg + ((size_t)slice * a.n_kb + kb) * a.w_block_bytes;  // [slice][C_in/8][tap][128][8]
                         unsigned char *dst = wsm + (size_t)s * a.w_block_bytes;
                         for (uint32_t o = 0; o + 1 <= wb; o += 32768)
                             tc::bulk_load(dst + o, src + o, min(32768u, wb - o), &full[s]);
@@ -222,10 +262,14 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
             if (ORIENT == 0) bounded_wait(wbar, 0, abort_flag, a.err);
             const uint32_t idesc =
                 ORIENT == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.Lout / a.nsplit);
+            const uint32_t wlbo = (uint32_t)(a.taps * Nw * 16);  // next 8-channel chunk of a weight tile
             uint32_t k = 0, tiles = 0;
             for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x, ++tiles) {
-                if (tiles > 0 && !bounded_wait(acc_empty, (tiles - 1) & 1, abort_flag, a.err)) break;
+                const int buf = (int)(tiles % (uint32_t)a.nacc);
+                const uint32_t use = tiles / (uint32_t)a.nacc;
+                if (use > 0 && !bounded_wait(&acc_empty[buf], (use - 1) & 1, abort_flag, a.err)) break;
                 tc::fence_after_sync();
+                const uint32_t dt = tmem + (uint32_t)(buf * 256);
                 bool ok = true;
                 for (int kb = 0; kb < a.n_kb; ++kb, ++k) {
                     const int s = k % a.NB;
@@ -238,11 +282,11 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     const uint32_t wb = tc::smem_addr(wsm + (ORIENT == 1 ? (size_t)s * a.w_block_bytes : 0));
                     // descriptors of (tap 0, k-step 0); every other MMA adds address deltas (in 16-byte
                     // units) to these, which stay inside the 14-bit start-address field (smem < 256 KB)
-                    const uint64_t wd00 = tc::desc_kmajor_noswizzle(
-                        wb + (ORIENT == 0 ? (uint32_t)(kb * a.taps * (a.KB / 8) * Nw * 16) : 0u), (uint32_t)Nw * 16, 128);
+                    // weight tile [KB/8][tap][Nw][8] (POS: the whole image, n_kb = 1)
+                    const uint64_t wd00 = tc::desc_kmajor_noswizzle(wb, wlbo, 128);
                     const uint64_t ad00 = tc::desc_kmajor_noswizzle(ab, chunk_bytes, 128);
-                    const uint64_t w_tap = (uint64_t)((a.KB / 8) * Nw);  // (KB/8 * Nw * 16) >> 4
-                    const uint64_t w_kk = (uint64_t)(2 * Nw);            // (2 * Nw * 16) >> 4
+                    const uint64_t w_tap = (uint64_t)Nw;                // (Nw * 16) >> 4
+                    const uint64_t w_kk = (uint64_t)(2 * a.taps * Nw);  // two chunks
                     const uint64_t a_kk = (uint64_t)(2 * chunk_bytes / 16);
                     const uint64_t a_win = (uint64_t)(win_bytes / 16);
                     const int ns = ORIENT == 1 ? a.Lout / a.nsplit : 0;
@@ -258,11 +302,11 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                             const uint32_t acc = (kb > 0 || r > 0 || kk > 0) ? 1u : 0u;
                             if (ORIENT == 0) {
                                 for (int j = 0; j < MT; ++j)
-                                    tc::mma_bf16(tmem + (uint32_t)(j * a.Cout), adk + (uint64_t)(128 * j), wd, idesc, acc);
+                                    tc::mma_bf16(dt + (uint32_t)(j * a.Cout), adk + (uint64_t)(128 * j), wd, idesc, acc);
                             } else {
                                 for (int i = 0; i < a.wpc; ++i)
                                     for (int h = 0; h < a.nsplit; ++h)
-                                        tc::mma_bf16(tmem + (uint32_t)(i * a.Lout + h * ns), wd,
+                                        tc::mma_bf16(dt + (uint32_t)(i * a.Lout + h * ns), wd,
                                                      adk + (uint64_t)i * a_win + (uint64_t)(h * ns), idesc, acc);
                             }
                         }
@@ -270,7 +314,7 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     tc::mma_commit(&empty[s]);
                 }
                 if (!ok) break;
-                tc::mma_commit(acc_full);
+                tc::mma_commit(&acc_full[buf]);
             }
         }
     } else if (warp >= EPI_W0) {
@@ -282,10 +326,12 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
         const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
         uint32_t tiles = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tiles) {
-            bounded_wait(acc_full, tiles & 1, abort_flag, a.err);
+            const int buf = (int)(tiles % (uint32_t)a.nacc);
+            bounded_wait(&acc_full[buf], (tiles / (uint32_t)a.nacc) & 1, abort_flag, a.err);
             epi_sync();  // every epilogue thread sees the same abort decision
             if (*(volatile int *)abort_flag) break;
             tc::fence_after_sync();
+            const uint32_t tb = tq + (uint32_t)(buf * 256);
             if (ORIENT == 0) {
                 // rows = positions; thread: row 32q + lane of subtiles j = hsel, hsel + 2, ...
                 const int w = t;
@@ -305,7 +351,7 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                         const int nj = min(4, (MT - j0 + 1) / 2);
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (u < nj) tc::tmem_ld16_nowait(tq + (uint32_t)((j0 + 2 * u) * a.Cout + c0), r[u]);
+                            if (u < nj) tc::tmem_ld16_nowait(tb + (uint32_t)((j0 + 2 * u) * a.Cout + c0), r[u]);
                         tc::tmem_wait_ld();
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
@@ -355,7 +401,7 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                             for (int i = 0; i < 4; ++i) rr[i] = __ldg(rp + i);
                         }
                         float v[32];
-                        tc::tmem_ld32(tq + (uint32_t)(j * a.Cout + c0), v);
+                        tc::tmem_ld32(tb + (uint32_t)(j * a.Cout + c0), v);
                         uint32_t pk[16];
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
@@ -386,62 +432,73 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     }
                 }
             } else {
-                // rows = channels of the slice; thread: channel 32q + lane, windows i = hsel, hsel + 2, ...
+                // rows = channels of the slice; thread: channel 32q + lane; the two warp halves
+                // take the two halves of every window's positions and exchange GroupNorm partials
                 const int slice = t % a.slices;
                 const int w0 = (t / a.slices) * a.wpc;
                 const int cl = 32 * q + lane;
                 const int c = slice * 128 + cl;
-                const int cg = a.Cout / a.G;  // 16 or 32: lanes of one group are contiguous
+                const int cg = a.Cout / a.G;  // <= 32: lanes of one group are contiguous
                 const float gam = a.gamma[c], bet = a.beta[c];
-                for (int i = hsel; i < a.wpc; i += 2) {
+                const int Lh = a.Lout >> 1;
+                const int pb = hsel * Lh;
+                float *xch = scale;  // [window parity][half][128 channels][sum, sum of squares]
+                const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
+                for (int i = 0; i < a.wpc; ++i) {
                     const int w = w0 + i;
+                    const uint32_t tw = tb + (uint32_t)(i * a.Lout + pb);
                     float s = 0.f, qq = 0.f;
-                    for (int p0 = 0; p0 < a.Lout; p0 += 32) {
-                        float v[32];
-                        tc::tmem_ld32(tq + (uint32_t)(i * a.Lout + p0), v);
+                    int p0 = 0;
+                    for (; p0 + 32 <= Lh; p0 += 32) {
+                        uint32_t r0[16], r1[16];
+                        tc::tmem_ld16_nowait(tw + (uint32_t)p0, r0);
+                        tc::tmem_ld16_nowait(tw + (uint32_t)(p0 + 16), r1);
+                        tc::tmem_wait_ld();
 #pragma unroll
-                        for (int p = 0; p < 32; ++p) {
-                            s += v[p];
-                            qq = fmaf(v[p], v[p], qq);
+                        for (int p = 0; p < 16; ++p) {
+                            const float v0 = __uint_as_float(r0[p]), v1 = __uint_as_float(r1[p]);
+                            s += v0 + v1;
+                            qq = fmaf(v0, v0, fmaf(v1, v1, qq));
+                        }
+                    }
+                    if (p0 < Lh) {
+                        uint32_t r0[16];
+                        tc::tmem_ld16_nowait(tw + (uint32_t)p0, r0);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int p = 0; p < 16; ++p) {
+                            const float v0 = __uint_as_float(r0[p]);
+                            s += v0;
+                            qq = fmaf(v0, v0, qq);
                         }
                     }
                     for (int o = cg / 2; o > 0; o >>= 1) {
                         s += __shfl_xor_sync(0xffffffffu, s, o);
                         qq += __shfl_xor_sync(0xffffffffu, qq, o);
                     }
+                    float *mine = xch + (((i & 1) * 2 + hsel) * 128 + cl) * 2;
+                    const float *other = xch + (((i & 1) * 2 + (hsel ^ 1)) * 128 + cl) * 2;
+                    mine[0] = s;
+                    mine[1] = qq;
+                    epi_sync();
+                    s += other[0];
+                    qq += other[1];
                     const float cnt = (float)a.Lout * (float)cg;
                     const float mean = s / cnt;
                     const float var = fmaxf(qq / cnt - mean * mean, 0.f);
                     const float sc = rsqrtf(var + a.eps) * gam;
                     const float sh = bet - mean * sc;
                     if (w >= a.n_win) continue;
-                    const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
                     __nv_bfloat16 *__restrict__ ow = a.out + (size_t)w * ld + c;
                     const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + (size_t)w * ld + c : nullptr;
-                    for (int p0 = 0; p0 < a.Lout; p0 += 32) {
-                        float rv[32];
-                        if (rw) {
-#pragma unroll
-                            for (int p = 0; p < 32; ++p)
-                                rv[p] = __bfloat162float(__ldg(rw + (size_t)(p0 + p + 1) * a.Cout));
-                        }
-                        float v[32];
-                        tc::tmem_ld32(tq + (uint32_t)(i * a.Lout + p0), v);
-#pragma unroll
-                        for (int p = 0; p < 32; ++p) {
-                            float x = fmaf(v[p], sc, sh);
-                            if (rw) x += rv[p];
-                            if (a.relu) x = fmaxf(x, 0.f);
-                            ow[(size_t)(p0 + p + 1) * a.Cout] = __float2bfloat16_rn(x);
-                        }
-                    }
-                    ow[0] = __float2bfloat16_rn(0.f);
-                    ow[(size_t)(a.Lout + 1) * a.Cout] = __float2bfloat16_rn(0.f);
+                    for (p0 = 0; p0 + 32 <= Lh; p0 += 32) ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.Cout, a.relu);
+                    if (p0 < Lh) ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.Cout, a.relu);
+                    ow[hsel ? (size_t)(a.Lout + 1) * a.Cout : 0] = __float2bfloat16_rn(0.f);  // zero pad row
                 }
             }
             tc::fence_before_sync();
             epi_sync();
-            if (et == 0) tc::mbar_arrive(acc_empty);
+            if (et == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
     }
     // ---- teardown: every role is done; free TMEM
@@ -500,11 +557,23 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
+// Tile knobs of one convolution (see the header comment).
+struct TileKnobs {
+    int orient = 1, wpc = 1, KB = 64, NB = 1, nacc = 1;
+    bool operator==(const TileKnobs &o) const {
+        return orient == o.orient && wpc == o.wpc && KB == o.KB && NB == o.NB && nacc == o.nacc;
+    }
+};
+
 // Per-layer plan of the tensor-core path (built once per context).
 struct TcLayer {
     LayerArgs a;                 // everything but pointers and n_win
+    TileKnobs knobs;
     unsigned char *wimg = nullptr;
     int view_c, view_rows;       // tensor map of the input view: channels, rows per window
+    int residual = 0, relu = 1;  // epilogue of this layer in the network
+    int tuned = 0, n_cand = 0;
+    float us_chosen = 0.f, us_default = 0.f;
 };
 
 struct TcPlan {
@@ -512,13 +581,9 @@ struct TcPlan {
     void *mem = nullptr;
 };
 
-// position-major tiles only where a 128-channel slice does not exist (C_out < 128)
-static bool use_pos(const ConvLayer &C) {
-    return C.cout < 128 && C.lout % 128 == 0 && (C.lout / 128) * C.cout <= 512;
-}
-
-static void fill_geometry(const ConvLayer &C, int G, float eps, TcLayer &T) {
-    LayerArgs &a = T.a;
+// Geometry of a layer under the given knobs; false if the knobs do not fit the layer.
+static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs &k, LayerArgs &a, int &view_c,
+                           int &view_rows) {
     memset(&a, 0, sizeof a);
     a.Lout = C.lout;
     a.Cout = C.cout;
@@ -527,13 +592,21 @@ static void fill_geometry(const ConvLayer &C, int G, float eps, TcLayer &T) {
     a.taps = C.k;
     a.G = G;
     a.eps = eps;
-    const bool pos = use_pos(C);
-    a.orient = pos ? 0 : 1;
-    T.view_c = C.stride * C.cin;
-    T.view_rows = (C.lin + 2) / C.stride;
+    a.orient = k.orient;
+    a.nacc = k.nacc;
+    a.NB = k.NB;
+    if (k.nacc != 1 && k.nacc != 2) return false;
+    if (k.NB < 1 || k.NB > NB_MAX) return false;
+    if (C.cin % 32 || C.cout % 16 || G < 1 || C.cout % G) return false;
+    if (!(C.k == 3 || (C.k == 1 && C.stride == 2))) return false;
+    const int cg = C.cout / G;
+    if (cg & (cg - 1)) return false;
+    const int acc_cols = k.nacc == 2 ? 256 : 512;
+    view_c = C.stride * C.cin;
+    view_rows = (C.lin + 2) / C.stride;
     // TMA boxes of 8 channels x box_rows rows: a tiled TMA destination must be 128-byte aligned,
     // so box_rows is a multiple of 8 (16 B rows); the box count minimises the padded rows
-    const int R = T.view_rows;
+    const int R = view_rows;
     a.n_box = 0;
     for (int nb = 1; nb <= 32; ++nb) {
         const int br = ((R + nb - 1) / nb + 7) / 8 * 8;
@@ -544,64 +617,105 @@ static void fill_geometry(const ConvLayer &C, int G, float eps, TcLayer &T) {
             a.rows_pad = br * nb;
         }
     }
+    if (a.n_box == 0) return false;
     a.halves = (C.stride == 2 && C.k == 3) ? 2 : 1;
     a.half0 = (C.stride == 2 && C.k == 1) ? 1 : 0;
-    if (pos) {
+    if (k.orient == 0) {
+        // position-major: one window per tile, all input channels one K-block, weights resident
+        if (C.cout > 128 || C.lout % 128 || (C.lout / 128) * C.cout > acc_cols) return false;
+        if (!(cg == 4 || cg == 8 || cg == 16 || cg == 32) || G > 16) return false;
+        if (k.wpc != 1) return false;
         a.KB = C.cin;
         a.n_kb = 1;
         a.wpc = 1;
         a.slices = 1;
+        a.nsplit = 1;
         a.w_block_bytes = (uint32_t)(C.k * C.cin * C.cout * 2);
     } else {
-        a.wpc = std::max(1, 384 / C.lout);
+        if (C.cout % 128 || cg > 32) return false;
+        if (!(k.KB == 32 || k.KB == 64 || k.KB == 128) || C.cin % k.KB) return false;
         a.nsplit = (C.lout + 255) / 256;
+        if (C.lout % 32 || C.lout % a.nsplit || (C.lout / a.nsplit) % 16) return false;
+        if (k.wpc < 1 || k.wpc * C.lout > acc_cols) return false;
+        a.wpc = k.wpc;
         a.slices = C.cout / 128;
-        a.KB = (C.stride == 2 && C.k == 3) ? 32 : 64;
-        a.n_kb = C.cin / a.KB;
+        a.KB = k.KB;
+        a.n_kb = C.cin / k.KB;
         a.w_block_bytes = (uint32_t)(C.k * a.KB * 128 * 2);
     }
     const uint32_t chunk_bytes = (uint32_t)a.rows_pad * 16;
     a.act_stage_bytes = (uint32_t)a.wpc * a.halves * (a.KB / 8) * chunk_bytes;
-    // deepest ring that fits
-    a.NB = 1;
-    for (int nb = 4; nb >= 1; --nb) {
-        a.NB = nb;
-        if (layer_smem(a).total <= 227 * 1024) break;
-    }
+    return layer_smem(a).total <= SMEM_LIMIT;
 }
 
-// BF16 weight image of one conv in the layout its orientation reads
-static void pack_weights(const ConvLayer &C, const float *wt_host /* [(r*cin+ci)*cout+co] */, const TcLayer &T,
+// deepest ring that fits (0 if none)
+static int deepest_ring(const ConvLayer &C, int G, float eps, TileKnobs k) {
+    LayerArgs a;
+    int vc, vr;
+    for (int nb = NB_MAX; nb >= 1; --nb) {
+        k.NB = nb;
+        if (layer_geometry(C, G, eps, k, a, vc, vr)) return nb;
+    }
+    return 0;
+}
+
+// The heuristic used until the layer is tuned: position-major tiles only where a
+// 128-channel slice does not exist, about 384 accumulator columns per tile.
+static TileKnobs default_knobs(const ConvLayer &C, int G, float eps) {
+    TileKnobs k;
+    k.orient = C.cout < 128 ? 0 : 1;
+    k.wpc = k.orient == 0 ? 1 : std::max(1, 384 / C.lout);
+    k.KB = (C.stride == 2 && C.k == 3) ? 32 : 64;
+    k.nacc = 1;
+    k.NB = std::min(4, deepest_ring(C, G, eps, k));
+    return k;
+}
+
+// Every knob combination the tuner times for this layer (deepest ring for each).
+static void tile_candidates(const ConvLayer &C, int G, float eps, std::vector<TileKnobs> &out) {
+    out.clear();
+    for (int orient = 0; orient < 2; ++orient)
+        for (int nacc = 1; nacc <= 2; ++nacc)
+            for (int wpc = 1; wpc <= (orient == 0 ? 1 : 8); ++wpc)
+                for (int KB : {32, 64, 128}) {
+                    if (orient == 0 && KB != 64) continue;  // KB is C_in for position-major tiles
+                    TileKnobs k;
+                    k.orient = orient;
+                    k.nacc = nacc;
+                    k.wpc = wpc;
+                    k.KB = orient == 0 ? C.cin : KB;
+                    k.NB = deepest_ring(C, G, eps, k);
+                    if (k.NB > 0) out.push_back(k);
+                }
+}
+
+static bool build_layer(const ConvLayer &C, int G, float eps, const TileKnobs &k, TcLayer &T) {
+    LayerArgs a;
+    int vc, vr;
+    if (!layer_geometry(C, G, eps, k, a, vc, vr)) return false;
+    T.a = a;
+    T.knobs = k;
+    T.view_c = vc;
+    T.view_rows = vr;
+    return true;
+}
+
+// BF16 weight image of one conv: [slice][C_in/8][tap][Ms][8], Ms = min(C_out, 128)
+static void pack_weights(const ConvLayer &C, const float *wt_host /* [(r*cin+ci)*cout+co] */,
                          std::vector<unsigned short> &img) {
-    const LayerArgs &a = T.a;
     auto bf = [](float v) {
         __nv_bfloat16 b = __float2bfloat16_rn(v);
         return *reinterpret_cast<unsigned short *>(&b);
     };
-    if (a.orient == 0) {
-        // [tap][chunk (cin/8)][cout][8]
-        img.assign((size_t)C.k * C.cin * C.cout, 0);
-        for (int r = 0; r < C.k; ++r)
-            for (int ci = 0; ci < C.cin; ++ci)
-                for (int co = 0; co < C.cout; ++co)
-                    img[(((size_t)r * (C.cin / 8) + ci / 8) * C.cout + co) * 8 + ci % 8] =
-                        bf(wt_host[((size_t)r * C.cin + ci) * C.cout + co]);
-    } else {
-        // [slice][kb][tap][chunk (KB/8)][128][8]
-        img.assign((size_t)C.k * C.cin * C.cout, 0);
-        const int KB = a.KB;
-        for (int sl = 0; sl < a.slices; ++sl)
-            for (int kb = 0; kb < a.n_kb; ++kb)
-                for (int r = 0; r < C.k; ++r)
-                    for (int c = 0; c < KB / 8; ++c)
-                        for (int m = 0; m < 128; ++m)
-                            for (int e = 0; e < 8; ++e) {
-                                const int ci = kb * KB + c * 8 + e, co = sl * 128 + m;
-                                const size_t idx =
-                                    (((((size_t)sl * a.n_kb + kb) * C.k + r) * (KB / 8) + c) * 128 + m) * 8 + e;
-                                img[idx] = bf(wt_host[((size_t)r * C.cin + ci) * C.cout + co]);
-                            }
-    }
+    const int Ms = std::min(C.cout, 128);
+    img.assign((size_t)C.k * C.cin * C.cout, 0);
+    for (int r = 0; r < C.k; ++r)
+        for (int ci = 0; ci < C.cin; ++ci)
+            for (int co = 0; co < C.cout; ++co) {
+                const int sl = co / Ms, m = co % Ms;
+                const size_t idx = ((((size_t)sl * (C.cin / 8) + ci / 8) * C.k + r) * Ms + m) * 8 + ci % 8;
+                img[idx] = bf(wt_host[((size_t)r * C.cin + ci) * C.cout + co]);
+            }
 }
 
 static bool full_net_supported(const afg_ctx *ctx) {
@@ -609,13 +723,10 @@ static bool full_net_supported(const afg_ctx *ctx) {
     for (size_t i = 1; i < P.convs.size(); ++i) {
         const ConvLayer &C = P.convs[i];
         if (C.cin % 64 || C.cout % 64 || C.cout > 512) return false;
-        const bool pos = use_pos(C);
-        const int nsplit = (C.lout + 255) / 256;
-        const int wpc = std::max(1, 384 / C.lout);
-        if (!pos && (C.cout % 128 || C.lout % nsplit || (C.lout / nsplit) % 16 || wpc * C.lout > 512 ||
-                     C.lout % 32 || C.cout / P.net.groups > 32))
-            return false;
-        if (pos && (C.cout / P.net.groups > 32 || P.net.groups > 16)) return false;
+        const TileKnobs k = default_knobs(C, P.net.groups, P.net.eps);
+        if (k.NB < 1) return false;
+        TcLayer T;
+        if (!build_layer(C, P.net.groups, P.net.eps, k, T)) return false;
     }
     return true;
 }
@@ -626,13 +737,18 @@ int net_tc_layers_prepare(afg_ctx *ctx) {
     if (!encode_fn()) return AFG_OK;  // no tensor-map encoder: the path stays unavailable
     TcPlan *tp = new TcPlan();
     tp->layers.resize(P.convs.size());
+    for (const BlockPlan &bp : P.blocks) {
+        tp->layers[bp.c2].residual = 1;
+        if (bp.sc >= 0) tp->layers[bp.sc].relu = 0;
+    }
     std::vector<float> all(ctx->d_params_bytes / sizeof(float));
     AFG_CUDA(ctx, cudaMemcpy(all.data(), ctx->d_params, ctx->d_params_bytes, cudaMemcpyDeviceToHost));
     std::vector<std::vector<unsigned short>> imgs(P.convs.size());
     size_t total = 0;
     for (size_t i = 1; i < P.convs.size(); ++i) {
-        fill_geometry(P.convs[i], P.net.groups, P.net.eps, tp->layers[i]);
-        pack_weights(P.convs[i], all.data() + (P.convs[i].wt - ctx->d_params), tp->layers[i], imgs[i]);
+        const ConvLayer &C = P.convs[i];
+        build_layer(C, P.net.groups, P.net.eps, default_knobs(C, P.net.groups, P.net.eps), tp->layers[i]);
+        pack_weights(C, all.data() + (C.wt - ctx->d_params), imgs[i]);
         total += (imgs[i].size() * 2 + 1023) / 1024 * 1024;
     }
     void *d = nullptr;
@@ -649,8 +765,8 @@ int net_tc_layers_prepare(afg_ctx *ctx) {
         AFG_CUDA(ctx, cudaMemcpy(tp->layers[i].wimg, imgs[i].data(), imgs[i].size() * 2, cudaMemcpyHostToDevice));
         off += (imgs[i].size() * 2 + 1023) / 1024 * 1024;
     }
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
     ctx->tcplan = tp;
     return AFG_OK;
 }
@@ -664,8 +780,9 @@ void net_tc_layers_release(afg_ctx *ctx) {
 
 bool net_tc_layers_available(const afg_ctx *ctx) { return ctx->tcplan != nullptr; }
 
-static int conv_tc(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, const __nv_bfloat16 *res, int relu,
-                   __nv_bfloat16 *out, int nw, const ConvLayer &C, cudaStream_t st) {
+// encode the input view's tensor map and launch one layer (no accounting)
+static int conv_tc_raw(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, const __nv_bfloat16 *res, int relu,
+                       __nv_bfloat16 *out, int nw, const ConvLayer &C, cudaStream_t st) {
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)T.view_c, (cuuint64_t)T.view_rows, (cuuint64_t)nw};
     const cuuint64_t strides[2] = {(cuuint64_t)T.view_c * 2, (cuuint64_t)T.view_c * 2 * T.view_rows};
@@ -688,13 +805,204 @@ static int conv_tc(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, cons
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const unsigned grid = (unsigned)std::max(1, std::min(n_tiles, sms));
+    if (a.orient == 0) k_conv_tc<0><<<grid, LT, layer_smem(a).total, st>>>(map, a);
+    else k_conv_tc<1><<<grid, LT, layer_smem(a).total, st>>>(map, a);
+    AFG_LAUNCH_CHECK(ctx, "k_conv_tc");
+    return AFG_OK;
+}
+
+static int conv_tc(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, const __nv_bfloat16 *res, int relu,
+                   __nv_bfloat16 *out, int nw, const ConvLayer &C, cudaStream_t st) {
     const double flops = 2.0 * nw * C.lout * C.cout * (double)C.k * C.cin;
     const double bytes = 2.0 * nw * ((double)(C.lin + 2) * C.cin + (double)(C.lout + 2) * C.cout * (res ? 2 : 1)) +
                          2.0 * C.k * C.cin * C.cout;
     KScope ks(ctx, st, KK_CONV_TC, flops, bytes);
-    if (a.orient == 0) k_conv_tc<0><<<grid, LT, layer_smem(a).total, st>>>(map, a);
-    else k_conv_tc<1><<<grid, LT, layer_smem(a).total, st>>>(map, a);
-    AFG_LAUNCH_CHECK(ctx, "k_conv_tc");
+    return conv_tc_raw(ctx, T, in, res, relu, out, nw, C, st);
+}
+
+// deterministic pseudo-random BF16 in [-1, 1) (tuning inputs)
+__global__ void k_fill_bf16(__nv_bfloat16 *x, int64_t n, uint32_t seed) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B1u ^ seed;
+        h ^= h >> 16;
+        h *= 0x85EBCA6Bu;
+        h ^= h >> 13;
+        x[i] = __float2bfloat16_rn((float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f);
+    }
+}
+
+// Time every candidate tile of each distinct layer geometry on nw synthetic windows and
+// keep the fastest.  Synchronises the device; refuses during stream capture.
+int net_tc_autotune(afg_ctx *ctx, int64_t n_win, cudaStream_t st) {
+    if (!ctx->tcplan) return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "autotune: no per-layer tensor-core plan");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    AFG_CUDA(ctx, cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return afg_fail(ctx, AFG_ERR_STATE, "autotune: stream is capturing");
+    const NetPlan &P = ctx->plan;
+    TcPlan &TP = *ctx->tcplan;
+    const int nw = (int)std::max<int64_t>(1, std::min<int64_t>(n_win > 0 ? n_win : 1024, 4096));
+    const int64_t per_win16 = P.max_act_per_window * 2;
+    __nv_bfloat16 *in = nullptr, *res = nullptr, *out = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_ACT0, (size_t)(nw * per_win16), (void **)&in);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT1, (size_t)(nw * per_win16), (void **)&res);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT2, (size_t)(nw * per_win16), (void **)&out);
+    if (rc) return rc;
+    const int64_t n_el = nw * P.max_act_per_window;
+    k_fill_bf16<<<1024, 256, 0, st>>>(in, n_el, 0x1234567u);
+    k_fill_bf16<<<1024, 256, 0, st>>>(res, n_el, 0x7654321u);
+    AFG_LAUNCH_CHECK(ctx, "k_fill_bf16");
+    cudaEvent_t e0, e1;
+    AFG_CUDA(ctx, cudaEventCreate(&e0));
+    AFG_CUDA(ctx, cudaEventCreate(&e1));
+    const int reps = 3;
+    auto time_layer = [&](const TcLayer &T, const ConvLayer &C, float &us) -> int {
+        const __nv_bfloat16 *r = T.residual ? res : nullptr;
+        int e = conv_tc_raw(ctx, T, in, r, T.relu, out, nw, C, st);  // warm
+        if (e) return e;
+        AFG_CUDA(ctx, cudaEventRecord(e0, st));
+        for (int i = 0; i < reps && !e; ++i) e = conv_tc_raw(ctx, T, in, r, T.relu, out, nw, C, st);
+        if (e) return e;
+        AFG_CUDA(ctx, cudaEventRecord(e1, st));
+        AFG_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        AFG_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        us = ms * 1000.f / reps;
+        return AFG_OK;
+    };
+    int err = AFG_OK;
+    for (size_t i = 1; i < P.convs.size() && !err; ++i) {
+        const ConvLayer &C = P.convs[i];
+        TcLayer &L = TP.layers[i];
+        // a layer with the geometry and epilogue of an earlier one takes its result
+        size_t same = 0;
+        for (size_t j = 1; j < i && !same; ++j) {
+            const ConvLayer &D = P.convs[j];
+            if (D.cin == C.cin && D.cout == C.cout && D.lin == C.lin && D.lout == C.lout && D.stride == C.stride &&
+                D.k == C.k && TP.layers[j].residual == L.residual && TP.layers[j].relu == L.relu)
+                same = j;
+        }
+        if (same) {
+            const TcLayer &S = TP.layers[same];
+            build_layer(C, P.net.groups, P.net.eps, S.knobs, L);
+            L.tuned = S.tuned;
+            L.n_cand = S.n_cand;
+            L.us_chosen = S.us_chosen;
+            L.us_default = S.us_default;
+            continue;
+        }
+        std::vector<TileKnobs> cands;
+        tile_candidates(C, P.net.groups, P.net.eps, cands);
+        const TileKnobs dflt = default_knobs(C, P.net.groups, P.net.eps);
+        if (std::find(cands.begin(), cands.end(), dflt) == cands.end()) cands.push_back(dflt);
+        float best = 0.f, t_dflt = 0.f;
+        TileKnobs best_k = dflt;
+        for (const TileKnobs &k : cands) {
+            TcLayer T = L;
+            if (!build_layer(C, P.net.groups, P.net.eps, k, T)) continue;
+            float us = 0.f;
+            err = time_layer(T, C, us);
+            if (err) break;
+            if (k == dflt) t_dflt = us;
+            if (best == 0.f || us < best) {
+                best = us;
+                best_k = k;
+            }
+        }
+        if (err) break;
+        build_layer(C, P.net.groups, P.net.eps, best_k, L);
+        L.tuned = 1;
+        L.n_cand = (int)cands.size();
+        L.us_chosen = best;
+        L.us_default = t_dflt;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err) return err;
+    AFG_CUDA(ctx, cudaStreamSynchronize(st));
+    int flag = 0;
+    AFG_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        AFG_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return afg_fail(ctx, AFG_ERR_TIMEOUT, "autotune: a bounded device-side wait gave up");
+    }
+    return AFG_OK;
+}
+
+static void tile_record(const ConvLayer &C, const TcLayer &L, int layer, const TileKnobs &k, afg_tile &t) {
+    memset(&t, 0, sizeof t);
+    t.layer = layer;
+    t.cin = C.cin;
+    t.cout = C.cout;
+    t.lin = C.lin;
+    t.lout = C.lout;
+    t.stride = C.stride;
+    t.taps = C.k;
+    t.residual = L.residual;
+    t.orient = k.orient;
+    t.wpc = k.wpc;
+    t.kb = k.orient == 0 ? C.cin : k.KB;
+    t.stages = k.NB;
+    t.acc_bufs = k.nacc;
+}
+
+int net_tc_tiles_get(afg_ctx *ctx, afg_tile *out, int cap, int *n_out) {
+    if (!ctx->tcplan) return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "tiles: no per-layer tensor-core plan");
+    const NetPlan &P = ctx->plan;
+    const TcPlan &TP = *ctx->tcplan;
+    int n = 0;
+    for (size_t i = 1; i < P.convs.size(); ++i, ++n) {
+        if (n >= cap) continue;
+        const TcLayer &L = TP.layers[i];
+        tile_record(P.convs[i], L, (int)i, L.knobs, out[n]);
+        out[n].tuned = L.tuned;
+        out[n].n_candidates = L.n_cand;
+        out[n].us_chosen = L.us_chosen;
+        out[n].us_default = L.us_default;
+    }
+    *n_out = n;
+    return AFG_OK;
+}
+
+int net_tc_tile_candidates(afg_ctx *ctx, int layer, afg_tile *out, int cap, int *n_out) {
+    if (!ctx->tcplan) return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "tiles: no per-layer tensor-core plan");
+    const NetPlan &P = ctx->plan;
+    if (layer < 1 || layer >= (int)P.convs.size()) return afg_fail(ctx, AFG_ERR_ARG, "tiles: layer out of range");
+    std::vector<TileKnobs> cands;
+    tile_candidates(P.convs[layer], P.net.groups, P.net.eps, cands);
+    int n = 0;
+    for (const TileKnobs &k : cands) {
+        if (n < cap) tile_record(P.convs[layer], ctx->tcplan->layers[layer], layer, k, out[n]);
+        ++n;
+    }
+    *n_out = n;
+    return AFG_OK;
+}
+
+int net_tc_tiles_set(afg_ctx *ctx, const afg_tile *in, int n) {
+    if (!ctx->tcplan) return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "tiles: no per-layer tensor-core plan");
+    const NetPlan &P = ctx->plan;
+    TcPlan &TP = *ctx->tcplan;
+    std::vector<TcLayer> next = TP.layers;
+    for (int j = 0; j < n; ++j) {
+        const afg_tile &t = in[j];
+        if (t.layer < 1 || t.layer >= (int)P.convs.size())
+            return afg_fail(ctx, AFG_ERR_ARG, "tiles_set: entry %d: layer %d out of range", j, t.layer);
+        const ConvLayer &C = P.convs[t.layer];
+        TileKnobs k;
+        k.orient = t.orient;
+        k.wpc = t.wpc;
+        k.KB = t.kb;
+        k.NB = t.stages;
+        k.nacc = t.acc_bufs;
+        if ((k.orient != 0 && k.orient != 1) || (k.orient == 0 && k.KB != C.cin) ||
+            !build_layer(C, P.net.groups, P.net.eps, k, next[t.layer]))
+            return afg_fail(ctx, AFG_ERR_ARG, "tiles_set: entry %d: knobs do not fit layer %d", j, t.layer);
+        next[t.layer].tuned = t.tuned;
+        next[t.layer].n_cand = t.n_candidates;
+        next[t.layer].us_chosen = t.us_chosen;
+        next[t.layer].us_default = t.us_default;
+    }
+    TP.layers = next;
     return AFG_OK;
 }
 
