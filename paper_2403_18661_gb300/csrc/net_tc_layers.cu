@@ -1,18 +1,21 @@
 // Per-layer tcgen05 implicit-GEMM convolutions for wide 1D ResNets (the
-// ResNet34 with GroupNorm of Sec. II): BF16 activations in HBM, channels-last
-// with one zero row before and after each window ([W][L + 2][C]).
+// ResNet34 with GroupNorm of Sec. II): BF16 activations in HBM, chunk-major:
+// per window, C/8 chunks of 8 channels, each (L + 2) rows of 16 bytes with a
+// zero row before and after ([W][C/8][L + 2][8]).  A chunk is the no-swizzle
+// K-major core-matrix layout the tensor core reads, so one TMA box of
+// 8 channels x rows x chunks is one contiguous run in HBM and lands in shared
+// memory unchanged.
 //
 // One kernel per convolution, persistent over tiles, warp-specialised:
-//   warp 0  producer: TMA boxes of 8 channels x rows x 1 window into shared
-//           memory in the no-swizzle K-major layout [chunk][row][16 B]
+//   warp 0  producer: TMA boxes into shared memory [chunk][row][16 B]
 //           (plus, for channel-major tiles, a bulk copy of the weight block)
 //   warp 1  MMA issuer: tcgen05.mma kind::f16, FP32 accumulators in TMEM
 //   warps 4..11 epilogue: GroupNorm statistics from TMEM, normalise,
 //           optional residual, optional ReLU, BF16 store (+ zero pad rows)
 // Taps are 16-byte row shifts of the activation descriptor; stride-2 convs
-// read the "pair-row" view [(L+2)/2][2C], where tap 0/1/2 are the even
-// half / odd half / even half one pair-row down (the 1x1 stride-2 shortcut
-// reads the odd half).
+// read each chunk as pairs of rows (a 5-D view [W][C/8][(L+2)/2][2][8]),
+// where tap 0/1/2 are the even rows / odd rows / even rows one pair down
+// (the 1x1 stride-2 shortcut reads the odd rows).
 //
 // Orientations:
 //   POS  M = 128 output positions per MMA, N = C_out; a tile is one window;
@@ -62,6 +65,7 @@ struct LayerArgs {
     int wpc, slices;     // CH tiling
     int nsplit;          // CH: MMAs per window along N (L_out / nsplit <= 256 positions each)
     int NB;              // pipeline stages (<= NB_MAX)
+    int shape;           // index of the unrolled MMA sequence of one stage (-1: generic loops)
     int nacc;            // TMEM accumulator buffers (1, or 2 with buffer b at column 256 b)
     int G;
     float eps;
@@ -143,8 +147,108 @@ __device__ __forceinline__ void fold_chunk(const float (&cs)[16], const float (&
     }
 }
 
+// Stage shapes with a fully unrolled MMA sequence.  A loop around single tcgen05.mma
+// instructions costs 150-270 cycles per iteration on the issuing thread (measured), so
+// one stage's MMAs are issued as straight-line code: channel-major (taps, k-steps,
+// windows, N splits) and position-major (taps, k-steps, M subtiles).
+#define AFG_CH_SHAPES(X) \
+    X(0, 3, 2, 1, 2) X(1, 3, 4, 1, 2) X(2, 3, 8, 1, 2) X(3, 1, 2, 1, 2) X(4, 1, 4, 1, 2) \
+    X(5, 1, 8, 1, 2) X(6, 3, 2, 1, 1) X(7, 3, 4, 1, 1) X(8, 3, 8, 1, 1) X(9, 1, 2, 1, 1) \
+    X(10, 1, 4, 1, 1) X(11, 1, 8, 1, 1) X(12, 3, 2, 2, 1) X(13, 3, 4, 2, 1) X(14, 3, 8, 2, 1) \
+    X(15, 1, 2, 2, 1) X(16, 1, 4, 2, 1) X(17, 1, 8, 2, 1) X(18, 3, 2, 3, 1) X(19, 3, 4, 3, 1) \
+    X(20, 3, 8, 3, 1) X(21, 1, 2, 3, 1) X(22, 1, 4, 3, 1) X(23, 1, 8, 3, 1) X(24, 3, 2, 4, 1) \
+    X(25, 3, 4, 4, 1) X(26, 3, 8, 4, 1) X(27, 1, 2, 4, 1) X(28, 1, 4, 4, 1) X(29, 1, 8, 4, 1) \
+    X(30, 3, 2, 5, 1) X(31, 3, 4, 5, 1) X(32, 3, 8, 5, 1) X(33, 1, 2, 5, 1) X(34, 1, 4, 5, 1) \
+    X(35, 1, 8, 5, 1)
+#define AFG_POS_SHAPES(X) \
+    X(0, 3, 4, 6) X(1, 3, 4, 3) X(2, 1, 4, 3) X(3, 3, 8, 3) X(4, 1, 8, 3) X(5, 3, 8, 6)
+
+struct StageGeo {
+    uint32_t dt;              // TMEM accumulator base of the tile
+    uint64_t wd00, ad00;      // weight / activation descriptors of (tap 0, k-step 0)
+    uint32_t toff0, toff1, toff2;  // activation descriptor offset of each tap (16-byte units)
+    uint64_t w_tap, w_kk, a_kk, a_win;
+    uint32_t n_step;          // TMEM columns between the N splits (= descriptor rows of a split)
+    uint32_t win_cols;        // TMEM columns per window (channel-major) / per M subtile (position-major)
+    uint32_t idesc;
+    uint32_t first;           // 1 for the tile's first K-block (the first MMA of each accumulator overwrites)
+};
+
+__device__ __forceinline__ uint32_t tap_off(const StageGeo &g, int r) {
+    return r == 0 ? g.toff0 : r == 1 ? g.toff1 : g.toff2;
+}
+
+template <int TAPS, int NKK, int WPC, int NSPLIT>
+__device__ __forceinline__ void issue_ch(const StageGeo &g) {
+#pragma unroll
+    for (int r = 0; r < TAPS; ++r)
+#pragma unroll
+        for (int kk = 0; kk < NKK; ++kk) {
+            const uint64_t wd = g.wd00 + (uint64_t)r * g.w_tap + (uint64_t)kk * g.w_kk;
+            const uint64_t adk = g.ad00 + (uint64_t)tap_off(g, r) + (uint64_t)kk * g.a_kk;
+            const uint32_t acc = (g.first && r == 0 && kk == 0) ? 0u : 1u;
+#pragma unroll
+            for (int i = 0; i < WPC; ++i)
+#pragma unroll
+                for (int h = 0; h < NSPLIT; ++h)
+                    tc::mma_bf16(g.dt + (uint32_t)i * g.win_cols + (uint32_t)h * g.n_step, wd,
+                                 adk + (uint64_t)i * g.a_win + (uint64_t)(h * g.n_step), g.idesc, acc);
+        }
+}
+
+template <int TAPS, int NKK, int MT>
+__device__ __forceinline__ void issue_pos(const StageGeo &g) {
+#pragma unroll
+    for (int r = 0; r < TAPS; ++r)
+#pragma unroll
+        for (int kk = 0; kk < NKK; ++kk) {
+            const uint64_t wd = g.wd00 + (uint64_t)r * g.w_tap + (uint64_t)kk * g.w_kk;
+            const uint64_t adk = g.ad00 + (uint64_t)tap_off(g, r) + (uint64_t)kk * g.a_kk;
+            const uint32_t acc = (g.first && r == 0 && kk == 0) ? 0u : 1u;
+#pragma unroll
+            for (int j = 0; j < MT; ++j)
+                tc::mma_bf16(g.dt + (uint32_t)j * g.win_cols, adk + (uint64_t)(128 * j), wd, g.idesc, acc);
+        }
+}
+
+// host: index of (taps, k-steps, windows | subtiles, splits) in the shape tables, -1 if absent
+static int stage_shape(int orient, int taps, int nkk, int wpc_or_mt, int nsplit) {
+#define AFG_FIND_CH(I, T, K, W, S) \
+    if (orient == 1 && taps == T && nkk == K && wpc_or_mt == W && nsplit == S) return I;
+#define AFG_FIND_POS(I, T, K, M) \
+    if (orient == 0 && taps == T && nkk == K && wpc_or_mt == M) return I;
+    AFG_CH_SHAPES(AFG_FIND_CH)
+    AFG_POS_SHAPES(AFG_FIND_POS)
+#undef AFG_FIND_CH
+#undef AFG_FIND_POS
+    return -1;
+}
+
+// device: issue one stage with the unrolled sequence of shape `shape` (false if none)
+template <int ORIENT>
+__device__ __forceinline__ bool issue_stage(int shape, const StageGeo &g) {
+    if (ORIENT == 1) {
+        switch (shape) {
+#define AFG_CASE_CH(I, T, K, W, S) \
+    case I: issue_ch<T, K, W, S>(g); return true;
+            AFG_CH_SHAPES(AFG_CASE_CH)
+#undef AFG_CASE_CH
+            default: return false;
+        }
+    } else {
+        switch (shape) {
+#define AFG_CASE_POS(I, T, K, M) \
+    case I: issue_pos<T, K, M>(g); return true;
+            AFG_POS_SHAPES(AFG_CASE_POS)
+#undef AFG_CASE_POS
+            default: return false;
+        }
+    }
+}
+
 // Channel-major epilogue store of 16 * NQ consecutive positions of one channel: normalise
-// the accumulators (one TMEM wait), add the residual, ReLU, BF16 store into padded row p + 1.
+// the accumulators (one TMEM wait), add the residual, ReLU, BF16 store into padded row p + 1
+// (rows C elements apart).
 template <int NQ>
 __device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, float sh,
                                          const __nv_bfloat16 *__restrict__ rw, __nv_bfloat16 *__restrict__ ow, int C,
@@ -240,16 +344,21 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                         for (uint32_t o = 0; o + 1 <= wb; o += 32768)
                             tc::bulk_load(dst + o, src + o, min(32768u, wb - o), &full[s]);
                     }
+                    // view coordinates {channel, row parity, row (pair), chunk, window}; with one box
+                    // per chunk column (n_box == 1) a box carries all KB/8 chunks of the K-block
                     unsigned char *ab = act + (size_t)s * a.act_stage_bytes;
+                    const int c0 = kb * (a.KB / 8);
                     for (int i = 0; i < nwt; ++i) {
                         for (int h = 0; h < a.halves; ++h) {
-                            const int half = a.half0 + h;
-                            for (int c = 0; c < a.KB / 8; ++c) {
-                                const int vchunk = half * (a.Cin / 8) + kb * (a.KB / 8) + c;
-                                unsigned char *d = ab + (size_t)i * win_bytes + (size_t)(h * (a.KB / 8) + c) * chunk_bytes;
-                                for (int b = 0; b < a.n_box; ++b)
-                                    tc::tma_load_3d(d + (size_t)b * a.box_rows * 16, &tmap, &full[s], vchunk * 8,
-                                                    b * a.box_rows, w0 + i);
+                            unsigned char *d = ab + (size_t)i * win_bytes + (size_t)h * (a.KB / 8) * chunk_bytes;
+                            if (a.n_box == 1) {
+                                tc::tma_load_5d(d, &tmap, &full[s], 0, a.half0 + h, 0, c0, w0 + i);
+                            } else {
+                                for (int c = 0; c < a.KB / 8; ++c)
+                                    for (int b = 0; b < a.n_box; ++b)
+                                        tc::tma_load_5d(d + (size_t)c * chunk_bytes + (size_t)b * a.box_rows * 16,
+                                                        &tmap, &full[s], 0, a.half0 + h, b * a.box_rows, c0 + c,
+                                                        w0 + i);
                             }
                         }
                     }
@@ -263,6 +372,18 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
             const uint32_t idesc =
                 ORIENT == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.Lout / a.nsplit);
             const uint32_t wlbo = (uint32_t)(a.taps * Nw * 16);  // next 8-channel chunk of a weight tile
+            uint32_t toff0 = 0, toff1 = 0, toff2 = 0;  // activation offset of each tap (16-byte units)
+            {
+                int coff, roff;
+                tap_offsets(a, 0, coff, roff);
+                toff0 = (uint32_t)(coff * (chunk_bytes / 16) + roff);
+                if (a.taps > 1) {
+                    tap_offsets(a, 1, coff, roff);
+                    toff1 = (uint32_t)(coff * (chunk_bytes / 16) + roff);
+                    tap_offsets(a, 2, coff, roff);
+                    toff2 = (uint32_t)(coff * (chunk_bytes / 16) + roff);
+                }
+            }
             uint32_t k = 0, tiles = 0;
             for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x, ++tiles) {
                 const int buf = (int)(tiles % (uint32_t)a.nacc);
@@ -283,33 +404,39 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     // descriptors of (tap 0, k-step 0); every other MMA adds address deltas (in 16-byte
                     // units) to these, which stay inside the 14-bit start-address field (smem < 256 KB)
                     // weight tile [KB/8][tap][Nw][8] (POS: the whole image, n_kb = 1)
-                    const uint64_t wd00 = tc::desc_kmajor_noswizzle(wb, wlbo, 128);
-                    const uint64_t ad00 = tc::desc_kmajor_noswizzle(ab, chunk_bytes, 128);
-                    const uint64_t w_tap = (uint64_t)Nw;                // (Nw * 16) >> 4
-                    const uint64_t w_kk = (uint64_t)(2 * a.taps * Nw);  // two chunks
-                    const uint64_t a_kk = (uint64_t)(2 * chunk_bytes / 16);
-                    const uint64_t a_win = (uint64_t)(win_bytes / 16);
-                    const int ns = ORIENT == 1 ? a.Lout / a.nsplit : 0;
-                    const int MT = a.Lout / 128;
-                    for (int r = 0; r < a.taps; ++r) {
-                        int coff, roff;
-                        tap_offsets(a, r, coff, roff);
-                        const uint64_t wdr = wd00 + (uint64_t)r * w_tap;
-                        const uint64_t adr = ad00 + (uint64_t)(coff * (chunk_bytes / 16) + roff);
-                        for (int kk = 0; kk < a.KB / 16; ++kk) {
-                            const uint64_t wd = wdr + (uint64_t)kk * w_kk;
-                            const uint64_t adk = adr + (uint64_t)kk * a_kk;
-                            const uint32_t acc = (kb > 0 || r > 0 || kk > 0) ? 1u : 0u;
-                            if (ORIENT == 0) {
-                                for (int j = 0; j < MT; ++j)
-                                    tc::mma_bf16(dt + (uint32_t)(j * a.Cout), adk + (uint64_t)(128 * j), wd, idesc, acc);
-                            } else {
-                                for (int i = 0; i < a.wpc; ++i)
-                                    for (int h = 0; h < a.nsplit; ++h)
-                                        tc::mma_bf16(dt + (uint32_t)(i * a.Lout + h * ns), wd,
-                                                     adk + (uint64_t)i * a_win + (uint64_t)(h * ns), idesc, acc);
+                    StageGeo g;
+                    g.dt = dt;
+                    g.wd00 = tc::desc_kmajor_noswizzle(wb, wlbo, 128);
+                    g.ad00 = tc::desc_kmajor_noswizzle(ab, chunk_bytes, 128);
+                    g.w_tap = (uint64_t)Nw;                // (Nw * 16) >> 4
+                    g.w_kk = (uint64_t)(2 * a.taps * Nw);  // two chunks
+                    g.a_kk = (uint64_t)(2 * chunk_bytes / 16);
+                    g.a_win = (uint64_t)(win_bytes / 16);
+                    g.toff0 = toff0;
+                    g.toff1 = toff1;
+                    g.toff2 = toff2;
+                    g.n_step = ORIENT == 1 ? (uint32_t)(a.Lout / a.nsplit) : 0u;
+                    g.win_cols = ORIENT == 1 ? (uint32_t)a.Lout : (uint32_t)a.Cout;
+                    g.idesc = idesc;
+                    g.first = kb == 0 ? 1u : 0u;
+                    if (!issue_stage<ORIENT>(a.shape, g)) {
+                        // generic loops (shapes without an unrolled sequence)
+                        const int MT = a.Lout / 128;
+                        for (int r = 0; r < a.taps; ++r)
+                            for (int kk = 0; kk < a.KB / 16; ++kk) {
+                                const uint64_t wd = g.wd00 + (uint64_t)r * g.w_tap + (uint64_t)kk * g.w_kk;
+                                const uint64_t adk = g.ad00 + (uint64_t)tap_off(g, r) + (uint64_t)kk * g.a_kk;
+                                const uint32_t acc = (kb > 0 || r > 0 || kk > 0) ? 1u : 0u;
+                                if (ORIENT == 0) {
+                                    for (int j = 0; j < MT; ++j)
+                                        tc::mma_bf16(dt + (uint32_t)(j * a.Cout), adk + (uint64_t)(128 * j), wd, idesc, acc);
+                                } else {
+                                    for (int i = 0; i < a.wpc; ++i)
+                                        for (int h = 0; h < a.nsplit; ++h)
+                                            tc::mma_bf16(dt + (uint32_t)(i * a.Lout) + (uint32_t)h * g.n_step, wd,
+                                                         adk + (uint64_t)i * g.a_win + (uint64_t)(h * g.n_step), idesc, acc);
+                                }
                             }
-                        }
                     }
                     tc::mma_commit(&empty[s]);
                 }
@@ -389,16 +516,17 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                 }
                 epi_sync();
                 const size_t ld = (size_t)(a.Lout + 2) * a.Cout;  // elements per window
+                const size_t cs = (size_t)(a.Lout + 2) * 8;       // elements per chunk
                 __nv_bfloat16 *__restrict__ ow = a.out + (size_t)w * ld;
                 const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + (size_t)w * ld : nullptr;
                 for (int j = hsel; j < MT; j += 2) {
                     const int row = 128 * j + 32 * q + lane + 1;
                     for (int c0 = 0; c0 < a.Cout; c0 += 32) {
+                        const size_t o0 = (size_t)(c0 / 8) * cs + (size_t)row * 8;  // chunk c0/8 + i at o0 + i cs
                         uint4 rr[4];
                         if (rw) {
-                            const uint4 *rp = reinterpret_cast<const uint4 *>(rw + (size_t)row * a.Cout + c0);
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) rr[i] = __ldg(rp + i);
+                            for (int i = 0; i < 4; ++i) rr[i] = __ldg(reinterpret_cast<const uint4 *>(rw + o0 + i * cs));
                         }
                         float v[32];
                         tc::tmem_ld32(tb + (uint32_t)(j * a.Cout + c0), v);
@@ -422,13 +550,15 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                             __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
                             pk[i] = *reinterpret_cast<uint32_t *>(&b2);
                         }
-                        uint4 *op = reinterpret_cast<uint4 *>(ow + (size_t)row * a.Cout + c0);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) op[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                        for (int i = 0; i < 4; ++i)
+                            *reinterpret_cast<uint4 *>(ow + o0 + i * cs) =
+                                make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
                     }
                     if (row == 1 || row == a.Lout) {  // zero pad rows
-                        uint4 *zp = reinterpret_cast<uint4 *>(ow + (size_t)(row == 1 ? 0 : a.Lout + 1) * a.Cout);
-                        for (int c = 0; c < a.Cout / 8; ++c) zp[c] = make_uint4(0, 0, 0, 0);
+                        const size_t pr = (size_t)(row == 1 ? 0 : a.Lout + 1) * 8;
+                        for (int c = 0; c < a.Cout / 8; ++c)
+                            *reinterpret_cast<uint4 *>(ow + (size_t)c * cs + pr) = make_uint4(0, 0, 0, 0);
                     }
                 }
             } else {
@@ -489,11 +619,12 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     const float sc = rsqrtf(var + a.eps) * gam;
                     const float sh = bet - mean * sc;
                     if (w >= a.n_win) continue;
-                    __nv_bfloat16 *__restrict__ ow = a.out + (size_t)w * ld + c;
-                    const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + (size_t)w * ld + c : nullptr;
-                    for (p0 = 0; p0 + 32 <= Lh; p0 += 32) ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.Cout, a.relu);
-                    if (p0 < Lh) ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.Cout, a.relu);
-                    ow[hsel ? (size_t)(a.Lout + 1) * a.Cout : 0] = __float2bfloat16_rn(0.f);  // zero pad row
+                    const size_t co = (size_t)w * ld + (size_t)(c >> 3) * (a.Lout + 2) * 8 + (c & 7);  // row 0 of c
+                    __nv_bfloat16 *__restrict__ ow = a.out + co;
+                    const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + co : nullptr;
+                    for (p0 = 0; p0 + 32 <= Lh; p0 += 32) ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, 8, a.relu);
+                    if (p0 < Lh) ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, 8, a.relu);
+                    ow[hsel ? (size_t)(a.Lout + 1) * 8 : 0] = __float2bfloat16_rn(0.f);  // zero pad row
                 }
             }
             tc::fence_before_sync();
@@ -510,31 +641,63 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
     }
 }
 
-// fp32 padded [n][L+2][C] -> bf16 (same layout)
-__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i * 4 >= n) return;
-    const float4 v = reinterpret_cast<const float4 *>(x)[i];
-    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-    reinterpret_cast<uint2 *>(y)[i] = make_uint2(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b));
+// fp32 padded channels-last [n][L2][C] -> bf16 chunk-major [n][C/8][L2][8]; one thread per
+// (window, chunk, row), rows fastest: 32-byte reads, contiguous 16-byte writes
+__global__ void k_to_bf16_chunked(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int L2, int C,
+                                  int64_t n_win) {
+    const int nch = C / 8;
+    const int64_t n = n_win * nch * L2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(i % L2);
+        const int64_t wc = i / L2;
+        const int ch = (int)(wc % nch);
+        const int64_t w = wc / nch;
+        const float4 *src = reinterpret_cast<const float4 *>(x + (w * L2 + row) * C + ch * 8);
+        const float4 u = src[0], v = src[1];
+        __nv_bfloat162 a = __floats2bfloat162_rn(u.x, u.y), b = __floats2bfloat162_rn(u.z, u.w);
+        __nv_bfloat162 c = __floats2bfloat162_rn(v.x, v.y), d = __floats2bfloat162_rn(v.z, v.w);
+        reinterpret_cast<uint4 *>(y)[i] =
+            make_uint4(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b),
+                       *reinterpret_cast<uint32_t *>(&c), *reinterpret_cast<uint32_t *>(&d));
+    }
 }
 
-// grid (n_win), block 256: logit = fc_b + sum_c fc_w[c] * mean_t x[t][c] (bf16 input)
+// grid (n_win), block 256: logit = fc_b + sum_c fc_w[c] * mean_t x[t][c] (bf16 chunk-major input,
+// C / 8 <= 256 chunks); each thread sums 8 channels of one chunk over a subset of rows
 __global__ void k_head_bf16(const __nv_bfloat16 *__restrict__ x, int L, int C, const float *__restrict__ fc_w,
                             const float *__restrict__ fc_b, float *__restrict__ logits, int64_t w0) {
-    __shared__ float part[512];
-    const __nv_bfloat16 *xt = x + (int64_t)blockIdx.x * (L + 2) * C + C;
-    const int tid = threadIdx.x;
+    __shared__ float part[256][9];
+    const int tid = threadIdx.x, nch = C / 8, tpc = 256 / nch;  // threads per chunk
+    const int ch = tid % nch, r0 = tid / nch;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r0 < tpc) {
+        const uint4 *xc = reinterpret_cast<const uint4 *>(x + ((int64_t)blockIdx.x * nch + ch) * (L + 2) * 8) + 1;
+        for (int r = r0; r < L; r += tpc) {
+            const uint4 u = __ldg(xc + r);
+            const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                s[2 * e] += __uint_as_float(w4[e] << 16);
+                s[2 * e + 1] += __uint_as_float(w4[e] & 0xffff0000u);
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) part[tid][e] = s[e];
+    __syncthreads();
+    __shared__ float term[512];
     for (int c = tid; c < C; c += 256) {
-        float s = 0.f;
-        for (int r = 0; r < L; ++r) s += __bfloat162float(xt[(int64_t)r * C + c]);
-        part[c] = fc_w[c] * (s / (float)L);
+        float t = 0.f;
+        for (int g = 0; g < tpc; ++g) t += part[g * nch + c / 8][c % 8];
+        term[c] = fc_w[c] * (t / (float)L);
     }
     __syncthreads();
-    if (tid == 0) {
-        float z = fc_b[0];
-        for (int c = 0; c < C; ++c) z += part[c];
-        logits[w0 + blockIdx.x] = z;
+    if (tid < 32) {
+        float z = 0.f;
+        for (int c = tid; c < C; c += 32) z += term[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (tid == 0) logits[w0 + blockIdx.x] = fc_b[0] + z;
     }
 }
 
@@ -645,6 +808,7 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
     }
     const uint32_t chunk_bytes = (uint32_t)a.rows_pad * 16;
     a.act_stage_bytes = (uint32_t)a.wpc * a.halves * (a.KB / 8) * chunk_bytes;
+    a.shape = stage_shape(a.orient, a.taps, a.KB / 16, a.orient == 0 ? a.Lout / 128 : a.wpc, a.nsplit);
     return layer_smem(a).total <= SMEM_LIMIT;
 }
 
@@ -783,12 +947,15 @@ bool net_tc_layers_available(const afg_ctx *ctx) { return ctx->tcplan != nullptr
 // encode the input view's tensor map and launch one layer (no accounting)
 static int conv_tc_raw(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, const __nv_bfloat16 *res, int relu,
                        __nv_bfloat16 *out, int nw, const ConvLayer &C, cudaStream_t st) {
+    // chunk-major input [nw][C_in/8][L_in + 2][8] viewed as {channel, row parity, row (pair), chunk, window}
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)T.view_c, (cuuint64_t)T.view_rows, (cuuint64_t)nw};
-    const cuuint64_t strides[2] = {(cuuint64_t)T.view_c * 2, (cuuint64_t)T.view_c * 2 * T.view_rows};
-    const cuuint32_t box[3] = {8, (cuuint32_t)T.a.box_rows, 1};
-    const cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(in), dims, strides,
+    const int s = C.stride;
+    const cuuint64_t rows = (cuuint64_t)(C.lin + 2);
+    const cuuint64_t dims[5] = {8, (cuuint64_t)s, rows / s, (cuuint64_t)(C.cin / 8), (cuuint64_t)nw};
+    const cuuint64_t strides[4] = {16, 16 * (cuuint64_t)s, rows * 16, rows * 16 * (cuuint64_t)(C.cin / 8)};
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)T.a.box_rows, (cuuint32_t)(T.a.n_box == 1 ? T.a.KB / 8 : 1), 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(in), dims, strides,
                              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return afg_fail(ctx, AFG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -1036,7 +1203,9 @@ int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_
         const int64_t n_el = (int64_t)nw * (L0 + 2) * C0;
         {
             KScope ks(ctx, st, KK_CONVERT, 0.0, (double)n_el * 6.0);
-            k_to_bf16<<<(unsigned)((n_el / 4 + 255) / 256), 256, 0, st>>>(stem_out, bA, n_el);
+            const int64_t n_thr = n_el / 8;
+            k_to_bf16_chunked<<<(unsigned)std::min<int64_t>((n_thr + 255) / 256, 152 * 64), 256, 0, st>>>(
+                stem_out, bA, L0 + 2, C0, nw);
         }
         AFG_LAUNCH_CHECK(ctx, "k_to_bf16");
         __nv_bfloat16 *A = bA, *Cb = bC, *B = bB, *D = bD;
