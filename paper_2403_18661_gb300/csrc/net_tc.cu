@@ -116,6 +116,19 @@ __device__ __forceinline__ void gn_reduce(float (&s)[TF_C], float (&q)[TF_C], fl
     __syncthreads();
 }
 
+// One conv of the fused network as straight-line MMAs (M subtile j, tap r): A = activation
+// rows 128 j + r .. (a 16-byte shift per row), B = the tap's 16 x 16 weights.  Issued without
+// loops: a loop around single tcgen05.mma instructions costs 150-270 cycles per iteration.
+template <int MT>
+__device__ __forceinline__ void tiny_issue(uint32_t tmem, uint64_t ad00, uint64_t bd00, uint32_t idesc) {
+#pragma unroll
+    for (int j = 0; j < MT; ++j)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            tc::mma_bf16(tmem + (uint32_t)(j * TF_C), ad00 + (uint64_t)(128 * j + r), bd00 + (uint64_t)(32 * r), idesc,
+                         r > 0 ? 1u : 0u);
+}
+
 template <int G>
 __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs args) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -353,15 +366,15 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             // ---- issue the conv as MT x 3 MMAs
             if (tid == 0) {
                 tc::fence_after_sync();
-                const uint32_t a0 = tc::smem_addr(src);
-                const uint32_t b0 = tc::smem_addr(wimg + (size_t)l * TF_WIMG);
-                for (int j = 0; j < MT; ++j) {
-                    for (int r = 0; r < 3; ++r) {
-                        const uint64_t ad = tc::desc_kmajor_noswizzle(a0 + (uint32_t)(128 * j + r) * 16,
-                                                                      (uint32_t)act_chunk, 128);
-                        const uint64_t bd = tc::desc_kmajor_noswizzle(b0 + r * 512, 256, 128);
-                        tc::mma_bf16(tmem + (uint32_t)(j * TF_C), ad, bd, idesc, r > 0 ? 1u : 0u);
-                    }
+                const uint64_t ad00 = tc::desc_kmajor_noswizzle(tc::smem_addr(src), (uint32_t)act_chunk, 128);
+                const uint64_t bd00 = tc::desc_kmajor_noswizzle(tc::smem_addr(wimg + (size_t)l * TF_WIMG), 256, 128);
+                if (MT == 24) {
+                    tiny_issue<24>(tmem, ad00, bd00, idesc);  // 1.5 s windows at 2048 Hz
+                } else {
+                    for (int j = 0; j < MT; ++j)
+                        for (int r = 0; r < 3; ++r)
+                            tc::mma_bf16(tmem + (uint32_t)(j * TF_C), ad00 + (uint64_t)(128 * j + r), bd00 + (uint64_t)(32 * r),
+                                         idesc, r > 0 ? 1u : 0u);
                 }
                 tc::mma_commit(bar);
             }

@@ -246,31 +246,99 @@ __device__ __forceinline__ bool issue_stage(int shape, const StageGeo &g) {
     }
 }
 
-// Channel-major epilogue store of 16 * NQ consecutive positions of one channel: normalise
-// the accumulators (one TMEM wait), add the residual, ReLU, BF16 store into padded row p + 1
-// (rows C elements apart).
+// 8 x 8 transpose of 16-bit values inside each octet of lanes (lanes 8g .. 8g + 7): on entry
+// lane e holds row e (columns 0..7 as four packed pairs), on exit column e.  Three butterfly
+// stages swap the off-diagonal 4 x 4, 2 x 2 and 1 x 1 blocks.
+__device__ __forceinline__ void transpose8_b16(uint32_t (&P)[4], int lane) {
+    {
+        const bool hi = lane & 4;
+        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, hi ? P[0] : P[2], 4);
+        const uint32_t y1 = __shfl_xor_sync(0xffffffffu, hi ? P[1] : P[3], 4);
+        if (hi) {
+            P[0] = y0;
+            P[1] = y1;
+        } else {
+            P[2] = y0;
+            P[3] = y1;
+        }
+    }
+    {
+        const bool hi = lane & 2;
+        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, hi ? P[0] : P[1], 2);
+        const uint32_t y1 = __shfl_xor_sync(0xffffffffu, hi ? P[2] : P[3], 2);
+        if (hi) {
+            P[0] = y0;
+            P[2] = y1;
+        } else {
+            P[1] = y0;
+            P[3] = y1;
+        }
+    }
+    {
+        const bool hi = lane & 1;  // even lanes send their odd columns, odd lanes their even ones
+        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, __byte_perm(P[0], P[1], hi ? 0x5410 : 0x7632), 1);
+        const uint32_t y1 = __shfl_xor_sync(0xffffffffu, __byte_perm(P[2], P[3], hi ? 0x5410 : 0x7632), 1);
+        if (hi) {
+            P[0] = __byte_perm(P[0], y0, 0x3254);
+            P[1] = __byte_perm(P[1], y0, 0x3276);
+            P[2] = __byte_perm(P[2], y1, 0x3254);
+            P[3] = __byte_perm(P[3], y1, 0x3276);
+        } else {
+            P[0] = __byte_perm(P[0], y0, 0x5410);
+            P[1] = __byte_perm(P[1], y0, 0x7610);
+            P[2] = __byte_perm(P[2], y1, 0x5410);
+            P[3] = __byte_perm(P[3], y1, 0x7610);
+        }
+    }
+}
+
+// Channel-major epilogue of 16 * NQ consecutive positions of one channel per lane: normalise
+// the accumulators (one TMEM wait), add the residual, ReLU, BF16.  Blocks of 8 positions are
+// transposed inside each lane octet (8 channels = one chunk), so every lane loads and stores
+// one 16-byte row: position p_first + 8 b + e of its octet's chunk at ow8 + (row) * 8.
 template <int NQ>
 __device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, float sh,
-                                         const __nv_bfloat16 *__restrict__ rw, __nv_bfloat16 *__restrict__ ow, int C,
-                                         int relu) {
-    float rv[16 * NQ];
-    if (rw) {
+                                         const __nv_bfloat16 *__restrict__ rw8, __nv_bfloat16 *__restrict__ ow8,
+                                         int relu, int lane) {
+    const int e = lane & 7;
+    uint4 rr[2 * NQ];
+    if (rw8) {
 #pragma unroll
-        for (int p = 0; p < 16 * NQ; ++p) rv[p] = __bfloat162float(__ldg(rw + (size_t)(p_first + p + 1) * C));
+        for (int b = 0; b < 2 * NQ; ++b)
+            rr[b] = __ldg(reinterpret_cast<const uint4 *>(rw8 + (size_t)(p_first + 8 * b + e + 1) * 8));
     }
     uint32_t r[NQ][16];
 #pragma unroll
     for (int g = 0; g < NQ; ++g) tc::tmem_ld16_nowait(taddr + (uint32_t)(16 * g), r[g]);
     tc::tmem_wait_ld();
 #pragma unroll
-    for (int g = 0; g < NQ; ++g)
+    for (int b = 0; b < 2 * NQ; ++b) {
+        float x[8];
 #pragma unroll
-        for (int p = 0; p < 16; ++p) {
-            float x = fmaf(__uint_as_float(r[g][p]), sc, sh);
-            if (rw) x += rv[16 * g + p];
-            if (relu) x = fmaxf(x, 0.f);
-            ow[(size_t)(p_first + 16 * g + p + 1) * C] = __float2bfloat16_rn(x);
+        for (int j = 0; j < 8; ++j) x[j] = fmaf(__uint_as_float(r[b >> 1][(b & 1) * 8 + j]), sc, sh);
+        if (rw8) {
+            uint32_t R[4] = {rr[b].x, rr[b].y, rr[b].z, rr[b].w};
+            transpose8_b16(R, lane);  // now: this lane's channel at the block's 8 positions
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                x[2 * j] += __uint_as_float(R[j] << 16);
+                x[2 * j + 1] += __uint_as_float(R[j] & 0xffff0000u);
+            }
         }
+        uint32_t P[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float x0 = x[2 * j], x1 = x[2 * j + 1];
+            if (relu) {
+                x0 = fmaxf(x0, 0.f);
+                x1 = fmaxf(x1, 0.f);
+            }
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+            P[j] = *reinterpret_cast<uint32_t *>(&b2);
+        }
+        transpose8_b16(P, lane);  // now: the octet's 8 channels at position p_first + 8 b + e
+        *reinterpret_cast<uint4 *>(ow8 + (size_t)(p_first + 8 * b + e + 1) * 8) = make_uint4(P[0], P[1], P[2], P[3]);
+    }
 }
 
 template <int ORIENT>
@@ -619,12 +687,14 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     const float sc = rsqrtf(var + a.eps) * gam;
                     const float sh = bet - mean * sc;
                     if (w >= a.n_win) continue;
-                    const size_t co = (size_t)w * ld + (size_t)(c >> 3) * (a.Lout + 2) * 8 + (c & 7);  // row 0 of c
+                    const size_t co = (size_t)w * ld + (size_t)(c >> 3) * (a.Lout + 2) * 8;  // row 0 of c's chunk
                     __nv_bfloat16 *__restrict__ ow = a.out + co;
                     const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + co : nullptr;
-                    for (p0 = 0; p0 + 32 <= Lh; p0 += 32) ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, 8, a.relu);
-                    if (p0 < Lh) ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, 8, a.relu);
-                    ow[hsel ? (size_t)(a.Lout + 1) * 8 : 0] = __float2bfloat16_rn(0.f);  // zero pad row
+                    for (p0 = 0; p0 + 32 <= Lh; p0 += 32)
+                        ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane);
+                    if (p0 < Lh) ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane);
+                    if ((lane & 7) == 0)  // zero pad row of the chunk
+                        *reinterpret_cast<uint4 *>(ow + (hsel ? (size_t)(a.Lout + 1) * 8 : 0)) = make_uint4(0, 0, 0, 0);
                 }
             }
             tc::fence_before_sync();
@@ -641,24 +711,176 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
     }
 }
 
-// fp32 padded channels-last [n][L2][C] -> bf16 chunk-major [n][C/8][L2][8]; one thread per
-// (window, chunk, row), rows fastest: 32-byte reads, contiguous 16-byte writes
-__global__ void k_to_bf16_chunked(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int L2, int C,
-                                  int64_t n_win) {
-    const int nch = C / 8;
-    const int64_t n = n_win * nch * L2;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int row = (int)(i % L2);
-        const int64_t wc = i / L2;
-        const int ch = (int)(wc % nch);
-        const int64_t w = wc / nch;
-        const float4 *src = reinterpret_cast<const float4 *>(x + (w * L2 + row) * C + ch * 8);
-        const float4 u = src[0], v = src[1];
-        __nv_bfloat162 a = __floats2bfloat162_rn(u.x, u.y), b = __floats2bfloat162_rn(u.z, u.w);
-        __nv_bfloat162 c = __floats2bfloat162_rn(v.x, v.y), d = __floats2bfloat162_rn(v.z, v.w);
-        reinterpret_cast<uint4 *>(y)[i] =
-            make_uint4(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b),
-                       *reinterpret_cast<uint32_t *>(&c), *reinterpret_cast<uint32_t *>(&d));
+// Stem of the wide network in one pass per window, straight into the first tensor-core
+// layer's input: conv (k taps, stride s, 2 -> C0 channels) read from the whitened stream,
+// GroupNorm, ReLU, optional max-pool (k3, s2, p1), BF16 chunk-major [C0/8][L + 2][8].
+// grid (n_win), block STEM_T; warp w owns the 8-channel chunks w, w + 8, ... (their 16 k
+// weights in registers), lanes own positions.  Pass 1 computes the conv for the GroupNorm
+// sums (sum and sum of squares per channel); pass 2 recomputes it, normalises, and pools
+// across neighbouring lanes before writing.
+constexpr int STEM_T = 256;
+constexpr int STEM_KMAX = 7;
+
+// weights [c][ci][r] of the 8 channels of chunk ch, zero past k taps
+__device__ __forceinline__ void stem_weights(const float *__restrict__ wt, int ch, int k, float (&wa)[8][STEM_KMAX],
+                                             float (&wb)[8][STEM_KMAX]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int r = 0; r < STEM_KMAX; ++r) {
+            wa[c][r] = r < k ? wt[(ch * 8 + c) * 2 * k + r] : 0.f;
+            wb[c][r] = r < k ? wt[(ch * 8 + c) * 2 * k + k + r] : 0.f;
+        }
+}
+
+// conv of the 8 channels at the window position whose first padded input is x0
+__device__ __forceinline__ void stem_conv8(const float *xs, int Wp, int x0, int k, const float (&wa)[8][STEM_KMAX],
+                                           const float (&wb)[8][STEM_KMAX], float (&acc)[8]) {
+    float u0[STEM_KMAX], u1[STEM_KMAX];
+#pragma unroll
+    for (int r = 0; r < STEM_KMAX; ++r) {
+        u0[r] = r < k ? xs[x0 + r] : 0.f;
+        u1[r] = r < k ? xs[Wp + x0 + r] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float a = 0.f;
+#pragma unroll
+        for (int r = 0; r < STEM_KMAX; ++r) {
+            a = fmaf(wa[c][r], u0[r], a);
+            a = fmaf(wb[c][r], u1[r], a);
+        }
+        acc[c] = a;
+    }
+}
+
+__global__ void __launch_bounds__(STEM_T) k_stem_bf16(const float *__restrict__ y, int64_t n_y, int64_t y_stride,
+                                                      int64_t first, int64_t stride, int64_t shift, int64_t w0,
+                                                      const float *__restrict__ wt, const float *__restrict__ gamma,
+                                                      const float *__restrict__ beta, int C0, int k, int s, int W,
+                                                      int L0, int pool, int G, float eps,
+                                                      __nv_bfloat16 *__restrict__ out) {
+    extern __shared__ float xs[];  // [2][W + 2 pad], then per-channel sums [2][C0], scale/shift [2][C0]
+    const int pad = k / 2, Wp = W + 2 * pad;
+    float *csum = xs + 2 * Wp, *csq = csum + C0, *scl = csq + C0, *shf = scl + C0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t win = w0 + blockIdx.x;
+    const int64_t start = first + win * stride;
+    const float *y0 = y, *y1 = y + y_stride;
+    for (int t = tid; t < Wp; t += STEM_T) {
+        const int tt = t - pad;
+        float a = 0.f, b = 0.f;
+        if (tt >= 0 && tt < W) {
+            a = y0[start + tt];
+            int64_t i1 = start + shift + tt;
+            if (i1 >= n_y) i1 -= n_y;
+            b = y1[i1];
+        }
+        xs[t] = a;
+        xs[Wp + t] = b;
+    }
+    for (int c = tid; c < C0; c += STEM_T) csum[c] = csq[c] = 0.f;
+    __syncthreads();
+    const int nch = C0 / 8;
+    // ---- pass 1: per-channel sum and sum of squares of the raw conv output
+    for (int ch = warp; ch < nch; ch += STEM_T / 32) {
+        float wa[8][STEM_KMAX], wb[8][STEM_KMAX];  // taps of input channel 0 / 1 (zero past k)
+        stem_weights(wt, ch, k, wa, wb);
+        float sm8[8], sq8[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sm8[c] = sq8[c] = 0.f;
+        for (int t = lane; t < L0; t += 32) {
+            float acc[8];
+            stem_conv8(xs, Wp, t * s, k, wa, wb, acc);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                sm8[c] += acc[c];
+                sq8[c] = fmaf(acc[c], acc[c], sq8[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sm8[c] += __shfl_xor_sync(0xffffffffu, sm8[c], o);
+                sq8[c] += __shfl_xor_sync(0xffffffffu, sq8[c], o);
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                csum[ch * 8 + c] = sm8[c];
+                csq[ch * 8 + c] = sq8[c];
+            }
+    }
+    __syncthreads();
+    // ---- GroupNorm affine map per channel
+    const int cg = C0 / G;
+    for (int c = tid; c < C0; c += STEM_T) {
+        const int g0 = (c / cg) * cg;
+        float a = 0.f, b = 0.f;
+        for (int j = g0; j < g0 + cg; ++j) {
+            a += csum[j];
+            b += csq[j];
+        }
+        const float cnt = (float)L0 * (float)cg;
+        const float mean = a / cnt;
+        const float var = fmaxf(b / cnt - mean * mean, 0.f);
+        const float sc = rsqrtf(var + eps) * gamma[c];
+        scl[c] = sc;
+        shf[c] = beta[c] - mean * sc;
+    }
+    __syncthreads();
+    // ---- pass 2: normalise + ReLU (+ max-pool) -> BF16 chunk-major
+    const int Lo = pool ? (L0 + 2 - 3) / 2 + 1 : L0;
+    const size_t cstride = (size_t)(Lo + 2) * 8;
+    __nv_bfloat16 *ow = out + (size_t)blockIdx.x * nch * cstride;
+    for (int ch = warp; ch < nch; ch += STEM_T / 32) {
+        float wa[8][STEM_KMAX], wb[8][STEM_KMAX], sc8[8], sh8[8];
+        stem_weights(wt, ch, k, wa, wb);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            sc8[c] = scl[ch * 8 + c];
+            sh8[c] = shf[ch * 8 + c];
+        }
+        __nv_bfloat16 *oc = ow + (size_t)ch * cstride;
+        // lanes take 32 consecutive conv positions; a pooled output u (window t = 2u-1..2u+1)
+        // is formed by the even lane t = 2u from its neighbours' values (shuffles), the value
+        // of t = 2u-1 at a warp boundary carried over from the previous pass
+        float carry[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) carry[c] = -INFINITY;
+        for (int t0 = 0; t0 < L0; t0 += 32) {
+            const int t = t0 + lane;
+            float z[8];
+            if (t < L0) {
+                float acc[8];
+                stem_conv8(xs, Wp, t * s, k, wa, wb, acc);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) z[c] = fmaxf(fmaf(acc[c], sc8[c], sh8[c]), 0.f);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) z[c] = -INFINITY;
+            }
+            float m[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float lo = __shfl_up_sync(0xffffffffu, z[c], 1);
+                const float hi = __shfl_down_sync(0xffffffffu, z[c], 1);
+                if (lane == 0) lo = carry[c];
+                m[c] = pool ? fmaxf(fmaxf(lo, z[c]), lane < 31 ? hi : -INFINITY) : z[c];
+                carry[c] = __shfl_sync(0xffffffffu, z[c], 31);
+            }
+            const int u = pool ? t >> 1 : t;
+            if (t < L0 && (!pool || !(lane & 1)) && u < Lo) {
+                __nv_bfloat162 b0 = __floats2bfloat162_rn(m[0], m[1]), b1 = __floats2bfloat162_rn(m[2], m[3]);
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(m[4], m[5]), b3 = __floats2bfloat162_rn(m[6], m[7]);
+                *reinterpret_cast<uint4 *>(oc + (size_t)(u + 1) * 8) =
+                    make_uint4(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1),
+                               *reinterpret_cast<uint32_t *>(&b2), *reinterpret_cast<uint32_t *>(&b3));
+            }
+        }
+        if (lane == 0) *reinterpret_cast<uint4 *>(oc) = make_uint4(0, 0, 0, 0);
+        if (lane == 1) *reinterpret_cast<uint4 *>(oc + (size_t)(Lo + 1) * 8) = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -1180,34 +1402,28 @@ int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_
     const NetPlan &P = ctx->plan;
     const TcPlan &TP = *ctx->tcplan;
     const ConvLayer &S = P.convs[0];
-    const int64_t per_win32 = P.max_act_per_window * (int64_t)sizeof(float);
     const int64_t per_win16 = P.max_act_per_window * 2;
-    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_win, ((int64_t)2 << 30) / per_win32));
-    chunk = std::min<int64_t>(chunk, 8192);
-    // fp32 stem buffers (reused as two bf16 activation buffers once converted) + two bf16 buffers
-    float *f0 = nullptr, *f1 = nullptr;
-    __nv_bfloat16 *bA = nullptr, *bC = nullptr;
-    int rc = afg_ws_reserve(ctx, WS_ACT0, (size_t)(chunk * per_win32), (void **)&f0);
-    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT1, (size_t)(chunk * per_win32), (void **)&f1);
-    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT2, (size_t)(chunk * per_win16), (void **)&bA);
-    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT3, (size_t)(chunk * per_win16), (void **)&bC);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_win, 8192));
+    __nv_bfloat16 *bA = nullptr, *bB = nullptr, *bC = nullptr, *bD = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_ACT0, (size_t)(chunk * per_win16), (void **)&bA);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT1, (size_t)(chunk * per_win16), (void **)&bB);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT2, (size_t)(chunk * per_win16), (void **)&bC);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_ACT3, (size_t)(chunk * per_win16), (void **)&bD);
     if (rc) return rc;
-    __nv_bfloat16 *bB = reinterpret_cast<__nv_bfloat16 *>(f0);
-    __nv_bfloat16 *bD = reinterpret_cast<__nv_bfloat16 *>(f1);
+    const int W = ctx->cfg.win_len;
+    const int pad = S.k / 2;
+    const size_t stem_smem = (size_t)(2 * (W + 2 * pad) + 4 * S.cout) * sizeof(float);
     for (int64_t w0 = 0; w0 < n_win; w0 += chunk) {
         const int nw = (int)std::min<int64_t>(chunk, n_win - w0);
-        int rc2 = launch_stem_gn_fp32(ctx, y, n_y, y_stride, first, stride, shift, w0, nw, f0, f1, st);
-        if (rc2) return rc2;
-        const float *stem_out = P.net.stem_pool ? f1 : f0;
-        const int L0 = P.l_after_stem, C0 = S.cout;
-        const int64_t n_el = (int64_t)nw * (L0 + 2) * C0;
         {
-            KScope ks(ctx, st, KK_CONVERT, 0.0, (double)n_el * 6.0);
-            const int64_t n_thr = n_el / 8;
-            k_to_bf16_chunked<<<(unsigned)std::min<int64_t>((n_thr + 255) / 256, 152 * 64), 256, 0, st>>>(
-                stem_out, bA, L0 + 2, C0, nw);
+            const double fl = 2.0 * nw * (double)S.lout * S.cout * 2.0 * S.k;
+            const double by = (double)nw * (2.0 * W * 4.0 + 2.0 * (P.l_after_stem + 2) * S.cout);
+            KScope ks(ctx, st, KK_STEM, fl, by);
+            k_stem_bf16<<<nw, STEM_T, stem_smem, st>>>(y, n_y, y_stride, first, stride, shift, w0, S.wt, S.gamma,
+                                                       S.beta, S.cout, S.k, S.stride, W, S.lout, P.net.stem_pool,
+                                                       P.net.groups, P.net.eps, bA);
         }
-        AFG_LAUNCH_CHECK(ctx, "k_to_bf16");
+        AFG_LAUNCH_CHECK(ctx, "k_stem_bf16");
         __nv_bfloat16 *A = bA, *Cb = bC, *B = bB, *D = bD;
         for (const BlockPlan &bp : P.blocks) {
             const ConvLayer &c1 = P.convs[bp.c1], &c2 = P.convs[bp.c2];
