@@ -2,20 +2,23 @@
 // ResNet34 with GroupNorm of Sec. II): BF16 activations in HBM, chunk-major:
 // per window, C/8 chunks of 8 channels, each (L + 2) rows of 16 bytes with a
 // zero row before and after ([W][C/8][L + 2][8]).  A chunk is the no-swizzle
-// K-major core-matrix layout the tensor core reads, so one TMA box of
-// 8 channels x rows x chunks is one contiguous run in HBM and lands in shared
-// memory unchanged.
+// K-major core-matrix layout the tensor core reads, so the chunks of one
+// K-block of a window are one contiguous run in HBM, copied to shared memory
+// unchanged by one bulk copy.  An activation that feeds a stride-2
+// convolution is written parity-split instead: each chunk holds the even rows,
+// then the odd rows ([W][C/8][2][(L + 2)/2][8]), so that stride-2 taps are
+// contiguous too.
 //
 // One kernel per convolution, persistent over tiles, warp-specialised:
-//   warp 0  producer: TMA boxes into shared memory [chunk][row][16 B]
-//           (plus, for channel-major tiles, a bulk copy of the weight block)
+//   warp 0  producer: bulk copies of the K-block's activation chunks into
+//           shared memory [chunk][row][16 B] (plus, for channel-major tiles,
+//           the weight block)
 //   warp 1  MMA issuer: tcgen05.mma kind::f16, FP32 accumulators in TMEM
 //   warps 4..11 epilogue: GroupNorm statistics from TMEM, normalise,
 //           optional residual, optional ReLU, BF16 store (+ zero pad rows)
 // Taps are 16-byte row shifts of the activation descriptor; stride-2 convs
-// read each chunk as pairs of rows (a 5-D view [W][C/8][(L+2)/2][2][8]),
-// where tap 0/1/2 are the even rows / odd rows / even rows one pair down
-// (the 1x1 stride-2 shortcut reads the odd rows).
+// read parity-split chunks, where tap 0/1/2 are the even rows / odd rows /
+// even rows one row down (the 1x1 stride-2 shortcut loads only the odd rows).
 //
 // Orientations:
 //   POS  M = 128 output positions per MMA, N = C_out; a tile is one window;
@@ -32,7 +35,6 @@
 // Weight image of a layer (BF16, K-major core matrices): slices of
 // Ms = min(C_out, 128) output channels, [slice][C_in/8][tap][Ms][8], so one
 // K-block of any KB is a contiguous run and one image serves every knob.
-#include <cuda.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -56,11 +58,11 @@ struct LayerArgs {
     int orient;          // 0 POS, 1 CH
     int n_win;
     int Lout, Cout, Cin, stride, taps;
-    int rows_pad;        // rows per chunk in shared memory (box_rows * n_box)
-    int box_rows, n_box;
-    int KB;              // real input channels per K-block
-    int halves;          // 1: view chunks of one half; 2: even + odd halves (stride-2 k3)
-    int half0;           // first half loaded (1 for the stride-2 1x1 shortcut)
+    int rows;            // 16-byte rows per chunk in shared memory
+    int in_rows;         // rows per chunk of the input in HBM (L_in + 2)
+    int KB;              // input channels per K-block
+    int odd_only;        // 1: load only the odd half of parity-split chunks (1x1 stride-2 shortcut)
+    int out_split;       // 1: write the output parity-split (it feeds a stride-2 convolution)
     int n_kb;            // K-blocks per tile
     int wpc, slices;     // CH tiling
     int nsplit;          // CH: MMAs per window along N (L_out / nsplit <= 256 positions each)
@@ -74,6 +76,7 @@ struct LayerArgs {
     uint32_t w_block_bytes;    // CH: weight bytes per K-block; POS: whole image
     const unsigned char *wimg;
     const float *gamma, *beta;
+    const __nv_bfloat16 *in;
     const __nv_bfloat16 *res;
     __nv_bfloat16 *out;
     int *err;
@@ -97,18 +100,18 @@ __host__ __device__ inline LSmem layer_smem(const LayerArgs &a) {
     return s;
 }
 
-// shared-memory chunk (of the K-block's view chunks) and row offset of tap r
-__device__ __forceinline__ void tap_offsets(const LayerArgs &a, int r, int &chunk, int &row) {
-    if (a.stride == 1) {
-        chunk = 0;
-        row = a.taps == 1 ? 1 : r;
-    } else if (a.taps == 1) {
-        chunk = 0;  // only the odd half was loaded
-        row = 0;
-    } else {
-        chunk = (r == 1) ? a.KB / 8 : 0;
-        row = (r == 2) ? 1 : 0;
-    }
+// row offset of tap r inside a shared-memory chunk (16-byte units): stride 1 reads rows
+// p + r; stride 2 reads padded rows 2p, 2p + 1, 2p + 2 = even p, odd p, even p + 1 of a
+// parity-split chunk (odd rows start at (L_in + 2) / 2); the 1x1 shortcut's odd rows alone
+__host__ __device__ inline uint32_t tap_row(const LayerArgs &a, int r) {
+    if (a.stride == 1) return (uint32_t)r;
+    if (a.odd_only) return 0u;
+    return r == 1 ? (uint32_t)(a.in_rows / 2) : (uint32_t)(r == 2 ? 1 : 0);
+}
+
+// padded output row R of a chunk in HBM, plain or parity-split (L + 2 even)
+__device__ __forceinline__ size_t out_row(int R, int split, int Lout) {
+    return split ? (size_t)((R & 1) * ((Lout + 2) >> 1) + (R >> 1)) : (size_t)R;
 }
 
 __device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
@@ -299,7 +302,7 @@ __device__ __forceinline__ void transpose8_b16(uint32_t (&P)[4], int lane) {
 template <int NQ>
 __device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, float sh,
                                          const __nv_bfloat16 *__restrict__ rw8, __nv_bfloat16 *__restrict__ ow8,
-                                         int relu, int lane) {
+                                         int relu, int lane, int split, int Lout) {
     const int e = lane & 7;
     uint4 rr[2 * NQ];
     if (rw8) {
@@ -337,12 +340,13 @@ __device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, 
             P[j] = *reinterpret_cast<uint32_t *>(&b2);
         }
         transpose8_b16(P, lane);  // now: the octet's 8 channels at position p_first + 8 b + e
-        *reinterpret_cast<uint4 *>(ow8 + (size_t)(p_first + 8 * b + e + 1) * 8) = make_uint4(P[0], P[1], P[2], P[3]);
+        *reinterpret_cast<uint4 *>(ow8 + out_row(p_first + 8 * b + e + 1, split, Lout) * 8) =
+            make_uint4(P[0], P[1], P[2], P[3]);
     }
 }
 
 template <int ORIENT>
-__global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const LayerArgs a) {
+__global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
     // ORIENT (= a.orient) is compile-time: each instantiation keeps only its own path
     extern __shared__ __align__(1024) unsigned char sm[];
     const LSmem L = layer_smem(a);
@@ -360,9 +364,8 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_tiles = ORIENT == 0 ? a.n_win : ((a.n_win + a.wpc - 1) / a.wpc) * a.slices;
-    const uint32_t chunk_bytes = (uint32_t)a.rows_pad * 16;
-    const int view_chunks = a.halves * a.KB / 8;                  // chunks per window per K-block
-    const uint32_t win_bytes = (uint32_t)view_chunks * chunk_bytes;  // one window's K-block activations
+    const uint32_t chunk_bytes = (uint32_t)a.rows * 16;
+    const uint32_t win_bytes = (uint32_t)(a.KB / 8) * chunk_bytes;  // one window's K-block activations
     const int Nw = ORIENT == 0 ? a.Cout : 128;                  // rows of the weight tile
 
     if (tid == 0) {
@@ -405,29 +408,27 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     if (k >= (uint32_t)a.NB && !bounded_wait(&empty[s], ((k / a.NB) - 1) & 1, abort_flag, a.err))
                         break;
                     const uint32_t wb = ORIENT == 1 ? a.w_block_bytes : 0;
-                    tc::mbar_expect_tx(&full[s], a.act_stage_bytes + wb);
+                    const int n_here = min(nwt, a.n_win - w0);  // absent windows: stale data, never stored
+                    tc::mbar_expect_tx(&full[s], (uint32_t)n_here * win_bytes + wb);
                     if (ORIENT == 1) {
                         const unsigned char *src = a.wimg + ((size_t)slice * a.n_kb + kb) * a.w_block_bytes;  // [slice][C_in/8][tap][128][8]
                         unsigned char *dst = wsm + (size_t)s * a.w_block_bytes;
-                        for (uint32_t o = 0; o + 1 <= wb; o += 32768)
-                            tc::bulk_load(dst + o, src + o, min(32768u, wb - o), &full[s]);
+                        for (uint32_t o = 0; o < a.w_block_bytes; o += 32768)
+                            tc::bulk_load(dst + o, src + o, min(32768u, a.w_block_bytes - o), &full[s]);
                     }
-                    // view coordinates {channel, row parity, row (pair), chunk, window}; with one box
-                    // per chunk column (n_box == 1) a box carries all KB/8 chunks of the K-block
                     unsigned char *ab = act + (size_t)s * a.act_stage_bytes;
-                    const int c0 = kb * (a.KB / 8);
-                    for (int i = 0; i < nwt; ++i) {
-                        for (int h = 0; h < a.halves; ++h) {
-                            unsigned char *d = ab + (size_t)i * win_bytes + (size_t)h * (a.KB / 8) * chunk_bytes;
-                            if (a.n_box == 1) {
-                                tc::tma_load_5d(d, &tmap, &full[s], 0, a.half0 + h, 0, c0, w0 + i);
-                            } else {
-                                for (int c = 0; c < a.KB / 8; ++c)
-                                    for (int b = 0; b < a.n_box; ++b)
-                                        tc::tma_load_5d(d + (size_t)c * chunk_bytes + (size_t)b * a.box_rows * 16,
-                                                        &tmap, &full[s], 0, a.half0 + h, b * a.box_rows, c0 + c,
-                                                        w0 + i);
-                            }
+                    const size_t in_chunk = (size_t)a.in_rows * 16;  // bytes of one input chunk in HBM
+                    for (int i = 0; i < n_here; ++i) {
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.in) +
+                                                   ((size_t)(w0 + i) * (a.Cin / 8) + (size_t)kb * (a.KB / 8)) * in_chunk;
+                        unsigned char *d = ab + (size_t)i * win_bytes;
+                        if (!a.odd_only) {
+                            for (uint32_t o = 0; o < win_bytes; o += 32768)
+                                tc::bulk_load(d + o, src + o, min(32768u, win_bytes - o), &full[s]);
+                        } else {
+                            for (int c = 0; c < a.KB / 8; ++c)
+                                tc::bulk_load(d + (size_t)c * chunk_bytes, src + (size_t)c * in_chunk + chunk_bytes,
+                                              chunk_bytes, &full[s]);
                         }
                     }
                 }
@@ -440,18 +441,7 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
             const uint32_t idesc =
                 ORIENT == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.Lout / a.nsplit);
             const uint32_t wlbo = (uint32_t)(a.taps * Nw * 16);  // next 8-channel chunk of a weight tile
-            uint32_t toff0 = 0, toff1 = 0, toff2 = 0;  // activation offset of each tap (16-byte units)
-            {
-                int coff, roff;
-                tap_offsets(a, 0, coff, roff);
-                toff0 = (uint32_t)(coff * (chunk_bytes / 16) + roff);
-                if (a.taps > 1) {
-                    tap_offsets(a, 1, coff, roff);
-                    toff1 = (uint32_t)(coff * (chunk_bytes / 16) + roff);
-                    tap_offsets(a, 2, coff, roff);
-                    toff2 = (uint32_t)(coff * (chunk_bytes / 16) + roff);
-                }
-            }
+            const uint32_t toff0 = tap_row(a, 0), toff1 = tap_row(a, 1), toff2 = tap_row(a, 2);
             uint32_t k = 0, tiles = 0;
             for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x, ++tiles) {
                 const int buf = (int)(tiles % (uint32_t)a.nacc);
@@ -591,6 +581,7 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     const int row = 128 * j + 32 * q + lane + 1;
                     for (int c0 = 0; c0 < a.Cout; c0 += 32) {
                         const size_t o0 = (size_t)(c0 / 8) * cs + (size_t)row * 8;  // chunk c0/8 + i at o0 + i cs
+                        const size_t s0 = (size_t)(c0 / 8) * cs + out_row(row, a.out_split, a.Lout) * 8;
                         uint4 rr[4];
                         if (rw) {
 #pragma unroll
@@ -620,11 +611,11 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                         }
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            *reinterpret_cast<uint4 *>(ow + o0 + i * cs) =
+                            *reinterpret_cast<uint4 *>(ow + s0 + i * cs) =
                                 make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
                     }
                     if (row == 1 || row == a.Lout) {  // zero pad rows
-                        const size_t pr = (size_t)(row == 1 ? 0 : a.Lout + 1) * 8;
+                        const size_t pr = out_row(row == 1 ? 0 : a.Lout + 1, a.out_split, a.Lout) * 8;
                         for (int c = 0; c < a.Cout / 8; ++c)
                             *reinterpret_cast<uint4 *>(ow + (size_t)c * cs + pr) = make_uint4(0, 0, 0, 0);
                     }
@@ -691,10 +682,12 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const __grid_constant__ CUten
                     __nv_bfloat16 *__restrict__ ow = a.out + co;
                     const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + co : nullptr;
                     for (p0 = 0; p0 + 32 <= Lh; p0 += 32)
-                        ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane);
-                    if (p0 < Lh) ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane);
+                        ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane, a.out_split, a.Lout);
+                    if (p0 < Lh)
+                        ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane, a.out_split, a.Lout);
                     if ((lane & 7) == 0)  // zero pad row of the chunk
-                        *reinterpret_cast<uint4 *>(ow + (hsel ? (size_t)(a.Lout + 1) * 8 : 0)) = make_uint4(0, 0, 0, 0);
+                        *reinterpret_cast<uint4 *>(ow + out_row(hsel ? a.Lout + 1 : 0, a.out_split, a.Lout) * 8) =
+                            make_uint4(0, 0, 0, 0);
                 }
             }
             tc::fence_before_sync();
@@ -923,23 +916,6 @@ __global__ void k_head_bf16(const __nv_bfloat16 *__restrict__ x, int L, int C, c
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
 }  // namespace
 
 // Tile knobs of one convolution (see the header comment).
@@ -955,8 +931,8 @@ struct TcLayer {
     LayerArgs a;                 // everything but pointers and n_win
     TileKnobs knobs;
     unsigned char *wimg = nullptr;
-    int view_c, view_rows;       // tensor map of the input view: channels, rows per window
     int residual = 0, relu = 1;  // epilogue of this layer in the network
+    int out_split = 0;           // output feeds a stride-2 convolution: written parity-split
     int tuned = 0, n_cand = 0;
     float us_chosen = 0.f, us_default = 0.f;
 };
@@ -967,8 +943,7 @@ struct TcPlan {
 };
 
 // Geometry of a layer under the given knobs; false if the knobs do not fit the layer.
-static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs &k, LayerArgs &a, int &view_c,
-                           int &view_rows) {
+static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs &k, LayerArgs &a) {
     memset(&a, 0, sizeof a);
     a.Lout = C.lout;
     a.Cout = C.cout;
@@ -983,28 +958,14 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
     if (k.nacc != 1 && k.nacc != 2) return false;
     if (k.NB < 1 || k.NB > NB_MAX) return false;
     if (C.cin % 32 || C.cout % 16 || G < 1 || C.cout % G) return false;
-    if (!(C.k == 3 || (C.k == 1 && C.stride == 2))) return false;
+    if (!((C.k == 3 && C.stride <= 2) || (C.k == 1 && C.stride == 2))) return false;
+    if (C.stride == 2 && (C.lin % 2 || C.lout != C.lin / 2)) return false;
     const int cg = C.cout / G;
     if (cg & (cg - 1)) return false;
     const int acc_cols = k.nacc == 2 ? 256 : 512;
-    view_c = C.stride * C.cin;
-    view_rows = (C.lin + 2) / C.stride;
-    // TMA boxes of 8 channels x box_rows rows: a tiled TMA destination must be 128-byte aligned,
-    // so box_rows is a multiple of 8 (16 B rows); the box count minimises the padded rows
-    const int R = view_rows;
-    a.n_box = 0;
-    for (int nb = 1; nb <= 32; ++nb) {
-        const int br = ((R + nb - 1) / nb + 7) / 8 * 8;
-        if (br > 256) continue;
-        if (a.n_box == 0 || br * nb < a.rows_pad) {
-            a.n_box = nb;
-            a.box_rows = br;
-            a.rows_pad = br * nb;
-        }
-    }
-    if (a.n_box == 0) return false;
-    a.halves = (C.stride == 2 && C.k == 3) ? 2 : 1;
-    a.half0 = (C.stride == 2 && C.k == 1) ? 1 : 0;
+    a.in_rows = C.lin + 2;
+    a.odd_only = (C.stride == 2 && C.k == 1) ? 1 : 0;
+    a.rows = a.odd_only ? a.in_rows / 2 : a.in_rows;
     if (k.orient == 0) {
         // position-major: one window per tile, all input channels one K-block, weights resident
         if (C.cout > 128 || C.lout % 128 || (C.lout / 128) * C.cout > acc_cols) return false;
@@ -1028,8 +989,7 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
         a.n_kb = C.cin / k.KB;
         a.w_block_bytes = (uint32_t)(C.k * a.KB * 128 * 2);
     }
-    const uint32_t chunk_bytes = (uint32_t)a.rows_pad * 16;
-    a.act_stage_bytes = (uint32_t)a.wpc * a.halves * (a.KB / 8) * chunk_bytes;
+    a.act_stage_bytes = (uint32_t)a.wpc * (a.KB / 8) * (uint32_t)a.rows * 16;
     a.shape = stage_shape(a.orient, a.taps, a.KB / 16, a.orient == 0 ? a.Lout / 128 : a.wpc, a.nsplit);
     return layer_smem(a).total <= SMEM_LIMIT;
 }
@@ -1037,10 +997,9 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
 // deepest ring that fits (0 if none)
 static int deepest_ring(const ConvLayer &C, int G, float eps, TileKnobs k) {
     LayerArgs a;
-    int vc, vr;
     for (int nb = NB_MAX; nb >= 1; --nb) {
         k.NB = nb;
-        if (layer_geometry(C, G, eps, k, a, vc, vr)) return nb;
+        if (layer_geometry(C, G, eps, k, a)) return nb;
     }
     return 0;
 }
@@ -1077,12 +1036,9 @@ static void tile_candidates(const ConvLayer &C, int G, float eps, std::vector<Ti
 
 static bool build_layer(const ConvLayer &C, int G, float eps, const TileKnobs &k, TcLayer &T) {
     LayerArgs a;
-    int vc, vr;
-    if (!layer_geometry(C, G, eps, k, a, vc, vr)) return false;
+    if (!layer_geometry(C, G, eps, k, a)) return false;
     T.a = a;
     T.knobs = k;
-    T.view_c = vc;
-    T.view_rows = vr;
     return true;
 }
 
@@ -1106,6 +1062,9 @@ static void pack_weights(const ConvLayer &C, const float *wt_host /* [(r*cin+ci)
 
 static bool full_net_supported(const afg_ctx *ctx) {
     const NetPlan &P = ctx->plan;
+    if (P.blocks.empty() || P.convs[P.blocks[0].c1].stride != 1) return false;  // the stem output is not split
+    for (const BlockPlan &bp : P.blocks)
+        if (P.convs[bp.c2].lout % 2) return false;  // parity-split outputs need L + 2 even
     for (size_t i = 1; i < P.convs.size(); ++i) {
         const ConvLayer &C = P.convs[i];
         if (C.cin % 64 || C.cout % 64 || C.cout > 512) return false;
@@ -1120,12 +1079,14 @@ static bool full_net_supported(const afg_ctx *ctx) {
 int net_tc_layers_prepare(afg_ctx *ctx) {
     NetPlan &P = ctx->plan;
     if (P.convs.size() < 2 || !full_net_supported(ctx)) return AFG_OK;
-    if (!encode_fn()) return AFG_OK;  // no tensor-map encoder: the path stays unavailable
     TcPlan *tp = new TcPlan();
     tp->layers.resize(P.convs.size());
-    for (const BlockPlan &bp : P.blocks) {
+    for (size_t b = 0; b < P.blocks.size(); ++b) {
+        const BlockPlan &bp = P.blocks[b];
         tp->layers[bp.c2].residual = 1;
         if (bp.sc >= 0) tp->layers[bp.sc].relu = 0;
+        // the block's output feeds the next block's stride-2 convolutions
+        if (b + 1 < P.blocks.size() && P.convs[P.blocks[b + 1].c1].stride == 2) tp->layers[bp.c2].out_split = 1;
     }
     std::vector<float> all(ctx->d_params_bytes / sizeof(float));
     AFG_CUDA(ctx, cudaMemcpy(all.data(), ctx->d_params, ctx->d_params_bytes, cudaMemcpyDeviceToHost));
@@ -1166,27 +1127,18 @@ void net_tc_layers_release(afg_ctx *ctx) {
 
 bool net_tc_layers_available(const afg_ctx *ctx) { return ctx->tcplan != nullptr; }
 
-// encode the input view's tensor map and launch one layer (no accounting)
+// launch one layer (no accounting)
 static int conv_tc_raw(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, const __nv_bfloat16 *res, int relu,
                        __nv_bfloat16 *out, int nw, const ConvLayer &C, cudaStream_t st) {
-    // chunk-major input [nw][C_in/8][L_in + 2][8] viewed as {channel, row parity, row (pair), chunk, window}
-    CUtensorMap map;
-    const int s = C.stride;
-    const cuuint64_t rows = (cuuint64_t)(C.lin + 2);
-    const cuuint64_t dims[5] = {8, (cuuint64_t)s, rows / s, (cuuint64_t)(C.cin / 8), (cuuint64_t)nw};
-    const cuuint64_t strides[4] = {16, 16 * (cuuint64_t)s, rows * 16, rows * 16 * (cuuint64_t)(C.cin / 8)};
-    const cuuint32_t box[5] = {8, 1, (cuuint32_t)T.a.box_rows, (cuuint32_t)(T.a.n_box == 1 ? T.a.KB / 8 : 1), 1};
-    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(in), dims, strides,
-                             box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return afg_fail(ctx, AFG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    (void)C;
     LayerArgs a = T.a;
     a.n_win = nw;
     a.relu = relu;
+    a.out_split = T.out_split;
     a.wimg = T.wimg;
     a.gamma = C.gamma;
     a.beta = C.beta;
+    a.in = in;
     a.res = res;
     a.out = out;
     a.err = ctx->d_err;
@@ -1194,8 +1146,8 @@ static int conv_tc_raw(afg_ctx *ctx, const TcLayer &T, const __nv_bfloat16 *in, 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const unsigned grid = (unsigned)std::max(1, std::min(n_tiles, sms));
-    if (a.orient == 0) k_conv_tc<0><<<grid, LT, layer_smem(a).total, st>>>(map, a);
-    else k_conv_tc<1><<<grid, LT, layer_smem(a).total, st>>>(map, a);
+    if (a.orient == 0) k_conv_tc<0><<<grid, LT, layer_smem(a).total, st>>>(a);
+    else k_conv_tc<1><<<grid, LT, layer_smem(a).total, st>>>(a);
     AFG_LAUNCH_CHECK(ctx, "k_conv_tc");
     return AFG_OK;
 }
