@@ -295,21 +295,25 @@ __device__ __forceinline__ void transpose8_b16(uint32_t (&P)[4], int lane) {
     }
 }
 
-// Channel-major epilogue of 16 * NQ consecutive positions of one channel per lane: normalise
-// the accumulators (one TMEM wait), add the residual, ReLU, BF16.  Blocks of 8 positions are
-// transposed inside each lane octet (8 channels = one chunk), so every lane loads and stores
-// one 16-byte row: position p_first + 8 b + e of its octet's chunk at ow8 + (row) * 8.
+// Residual rows of a channel-major epilogue unit (16 * NQ positions from p_first): lane e of
+// each octet loads rows p_first + 8 b + e + 1 of the octet's chunk (issued one unit ahead).
 template <int NQ>
-__device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, float sh,
-                                         const __nv_bfloat16 *__restrict__ rw8, __nv_bfloat16 *__restrict__ ow8,
-                                         int relu, int lane, int split, int Lout) {
-    const int e = lane & 7;
-    uint4 rr[2 * NQ];
-    if (rw8) {
+__device__ __forceinline__ void ch_res_load(const __nv_bfloat16 *__restrict__ rw8, int p_first, int lane,
+                                            uint4 (&rr)[4]) {
 #pragma unroll
-        for (int b = 0; b < 2 * NQ; ++b)
-            rr[b] = __ldg(reinterpret_cast<const uint4 *>(rw8 + (size_t)(p_first + 8 * b + e + 1) * 8));
-    }
+    for (int b = 0; b < 2 * NQ; ++b)
+        rr[b] = __ldg(reinterpret_cast<const uint4 *>(rw8 + (size_t)(p_first + 8 * b + (lane & 7) + 1) * 8));
+}
+
+// Channel-major epilogue of 16 * NQ consecutive positions of one channel per lane: normalise
+// the accumulators (one TMEM wait), add the residual (rr, already loaded), ReLU, BF16.  Blocks
+// of 8 positions are transposed inside each lane octet (8 channels = one chunk), so every lane
+// stores one 16-byte row: position p_first + 8 b + e of its octet's chunk.
+template <int NQ>
+__device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, float sh, bool has_res,
+                                         const uint4 (&rr)[4], __nv_bfloat16 *__restrict__ ow8, int relu, int lane,
+                                         int split, int Lout) {
+    const int e = lane & 7;
     uint32_t r[NQ][16];
 #pragma unroll
     for (int g = 0; g < NQ; ++g) tc::tmem_ld16_nowait(taddr + (uint32_t)(16 * g), r[g]);
@@ -319,7 +323,7 @@ __device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, 
         float x[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) x[j] = fmaf(__uint_as_float(r[b >> 1][(b & 1) * 8 + j]), sc, sh);
-        if (rw8) {
+        if (has_res) {
             uint32_t R[4] = {rr[b].x, rr[b].y, rr[b].z, rr[b].w};
             transpose8_b16(R, lane);  // now: this lane's channel at the block's 8 positions
 #pragma unroll
@@ -522,6 +526,17 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                 const int w = t;
                 const int MT = a.Lout / 128;
                 const int cg = a.Cout / a.G;
+                const size_t ld = (size_t)(a.Lout + 2) * a.Cout;  // elements per window
+                const size_t cs = (size_t)(a.Lout + 2) * 8;       // elements per chunk
+                const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + (size_t)w * ld : nullptr;
+                // residual units (subtile j, 32 channels from c0) are loaded one unit ahead; the
+                // first is issued before the statistics pass
+                uint4 cur[4], nxt[4];
+                if (rw && hsel < MT) {
+                    const size_t o0 = (size_t)(128 * hsel + 32 * q + lane + 1) * 8;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) cur[i] = __ldg(reinterpret_cast<const uint4 *>(rw + o0 + i * cs));
+                }
                 // per-warp group partials in red[e][g] (sum) and red[e][16 + g] (sum of squares)
                 if (lane < 32) red[e * 32 + lane] = 0.f;
                 __syncwarp();
@@ -573,20 +588,26 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     shift[et] = a.beta[et] - mean * sc;
                 }
                 epi_sync();
-                const size_t ld = (size_t)(a.Lout + 2) * a.Cout;  // elements per window
-                const size_t cs = (size_t)(a.Lout + 2) * 8;       // elements per chunk
                 __nv_bfloat16 *__restrict__ ow = a.out + (size_t)w * ld;
-                const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + (size_t)w * ld : nullptr;
                 for (int j = hsel; j < MT; j += 2) {
                     const int row = 128 * j + 32 * q + lane + 1;
                     for (int c0 = 0; c0 < a.Cout; c0 += 32) {
-                        const size_t o0 = (size_t)(c0 / 8) * cs + (size_t)row * 8;  // chunk c0/8 + i at o0 + i cs
                         const size_t s0 = (size_t)(c0 / 8) * cs + out_row(row, a.out_split, a.Lout) * 8;
-                        uint4 rr[4];
-                        if (rw) {
+                        if (rw) {  // prefetch the next unit: (j, c0 + 32) or (j + 2, 0)
+                            const int cn = c0 + 32 < a.Cout ? c0 + 32 : 0;
+                            const int jn = c0 + 32 < a.Cout ? j : j + 2;
+                            if (jn < MT) {
+                                const size_t on = (size_t)(cn / 8) * cs + (size_t)(128 * jn + 32 * q + lane + 1) * 8;
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) rr[i] = __ldg(reinterpret_cast<const uint4 *>(rw + o0 + i * cs));
+                                for (int i = 0; i < 4; ++i)
+                                    nxt[i] = __ldg(reinterpret_cast<const uint4 *>(rw + on + i * cs));
+                            }
                         }
+                        uint4 rr[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) rr[i] = cur[i];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
                         float v[32];
                         tc::tmem_ld32(tb + (uint32_t)(j * a.Cout + c0), v);
                         uint32_t pk[16];
@@ -633,9 +654,18 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                 const int pb = hsel * Lh;
                 float *xch = scale;  // [window parity][half][128 channels][sum, sum of squares]
                 const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
+                const int n32 = Lh / 32, tail16 = Lh % 32;
                 for (int i = 0; i < a.wpc; ++i) {
                     const int w = w0 + i;
                     const uint32_t tw = tb + (uint32_t)(i * a.Lout + pb);
+                    const size_t co = (size_t)w * ld + (size_t)(c >> 3) * (a.Lout + 2) * 8;  // row 0 of c's chunk
+                    const bool has_res = a.res != nullptr && w < a.n_win;
+                    const __nv_bfloat16 *__restrict__ rw = has_res ? a.res + co : nullptr;
+                    uint4 cur[4], nxt[4];  // residual of the current / next unit (loads in flight meanwhile)
+                    if (has_res) {
+                        if (n32 > 0) ch_res_load<2>(rw, pb, lane, cur);
+                        else ch_res_load<1>(rw, pb, lane, cur);
+                    }
                     float s = 0.f, qq = 0.f;
                     int p0 = 0;
                     for (; p0 + 32 <= Lh; p0 += 32) {
@@ -678,13 +708,21 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     const float sc = rsqrtf(var + a.eps) * gam;
                     const float sh = bet - mean * sc;
                     if (w >= a.n_win) continue;
-                    const size_t co = (size_t)w * ld + (size_t)(c >> 3) * (a.Lout + 2) * 8;  // row 0 of c's chunk
                     __nv_bfloat16 *__restrict__ ow = a.out + co;
-                    const __nv_bfloat16 *__restrict__ rw = a.res ? a.res + co : nullptr;
-                    for (p0 = 0; p0 + 32 <= Lh; p0 += 32)
-                        ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane, a.out_split, a.Lout);
-                    if (p0 < Lh)
-                        ch_store<1>(tw + (uint32_t)p0, pb + p0, sc, sh, rw, ow, a.relu, lane, a.out_split, a.Lout);
+                    for (int u = 0; u < n32; ++u) {
+                        p0 = 32 * u;
+                        if (has_res) {
+                            if (u + 1 < n32) ch_res_load<2>(rw, pb + p0 + 32, lane, nxt);
+                            else if (tail16) ch_res_load<1>(rw, pb + p0 + 32, lane, nxt);
+                        }
+                        ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, has_res, cur, ow, a.relu, lane, a.out_split,
+                                    a.Lout);
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) cur[b] = nxt[b];
+                    }
+                    if (tail16)
+                        ch_store<1>(tw + (uint32_t)(32 * n32), pb + 32 * n32, sc, sh, has_res, cur, ow, a.relu, lane,
+                                    a.out_split, a.Lout);
                     if ((lane & 7) == 0)  // zero pad row of the chunk
                         *reinterpret_cast<uint4 *>(ow + out_row(hsel ? a.Lout + 1 : 0, a.out_split, a.Lout) * 8) =
                             make_uint4(0, 0, 0, 0);
