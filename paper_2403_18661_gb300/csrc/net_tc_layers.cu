@@ -746,11 +746,12 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
 // layer's input: conv (k taps, stride s, 2 -> C0 channels) read from the whitened stream,
 // GroupNorm, ReLU, optional max-pool (k3, s2, p1), BF16 chunk-major [C0/8][L + 2][8].
 // grid (n_win), block STEM_T; warp w owns the 8-channel chunks w, w + 8, ... (their 16 k
-// weights in registers), lanes own positions.  Pass 1 computes the conv for the GroupNorm
-// sums (sum and sum of squares per channel); pass 2 recomputes it, normalises, and pools
-// across neighbouring lanes before writing.
+// weights in registers), lanes own positions.  Pass 1 gets the GroupNorm sums (sum and sum of
+// squares per channel) from the first and second moments of the conv inputs; pass 2 computes
+// the conv, normalises, and pools across neighbouring lanes before writing.
 constexpr int STEM_T = 256;
 constexpr int STEM_KMAX = 7;
+constexpr int STEM_NMOM = 2 * STEM_KMAX + STEM_KMAX * (2 * STEM_KMAX + 1);  // S and the upper triangle of M
 
 // weights [c][ci][r] of the 8 channels of chunk ch, zero past k taps
 __device__ __forceinline__ void stem_weights(const float *__restrict__ wt, int ch, int k, float (&wa)[8][STEM_KMAX],
@@ -791,9 +792,10 @@ __global__ void __launch_bounds__(STEM_T) k_stem_bf16(const float *__restrict__ 
                                                       const float *__restrict__ beta, int C0, int k, int s, int W,
                                                       int L0, int pool, int G, float eps,
                                                       __nv_bfloat16 *__restrict__ out) {
-    extern __shared__ float xs[];  // [2][W + 2 pad], then per-channel sums [2][C0], scale/shift [2][C0]
+    extern __shared__ float xs[];  // [2][W + 2 pad], per-channel sums [2][C0], scale/shift [2][C0], moments
     const int pad = k / 2, Wp = W + 2 * pad;
     float *csum = xs + 2 * Wp, *csq = csum + C0, *scl = csq + C0, *shf = scl + C0;
+    float *red = shf + C0, *mom = red + (STEM_T / 32) * STEM_NMOM;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t win = w0 + blockIdx.x;
     const int64_t start = first + win * stride;
@@ -810,38 +812,79 @@ __global__ void __launch_bounds__(STEM_T) k_stem_bf16(const float *__restrict__ 
         xs[t] = a;
         xs[Wp + t] = b;
     }
-    for (int c = tid; c < C0; c += STEM_T) csum[c] = csq[c] = 0.f;
     __syncthreads();
     const int nch = C0 / 8;
-    // ---- pass 1: per-channel sum and sum of squares of the raw conv output
-    for (int ch = warp; ch < nch; ch += STEM_T / 32) {
-        float wa[8][STEM_KMAX], wb[8][STEM_KMAX];  // taps of input channel 0 / 1 (zero past k)
-        stem_weights(wt, ch, k, wa, wb);
-        float sm8[8], sq8[8];
+    // ---- pass 1: per-channel sum and sum of squares of the raw conv output from the moments
+    // of its inputs u_t = (x0[t s + r], x1[t s + r]), r < k:  sum_t y_c = w_c . S and
+    // sum_t y_c^2 = w_c^T M w_c with S = sum_t u_t, M = sum_t u_t u_t^T (upper triangle)
+    {
+        constexpr int D = 2 * STEM_KMAX, NM = D * (D + 1) / 2;
+        float S[D], M[NM];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) sm8[c] = sq8[c] = 0.f;
-        for (int t = lane; t < L0; t += 32) {
-            float acc[8];
-            stem_conv8(xs, Wp, t * s, k, wa, wb, acc);
+        for (int i = 0; i < D; ++i) S[i] = 0.f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                sm8[c] += acc[c];
-                sq8[c] = fmaf(acc[c], acc[c], sq8[c]);
+        for (int i = 0; i < NM; ++i) M[i] = 0.f;
+        for (int t = tid; t < L0; t += STEM_T) {
+            float u[D];
+#pragma unroll
+            for (int r = 0; r < STEM_KMAX; ++r) {
+                u[r] = r < k ? xs[t * s + r] : 0.f;
+                u[STEM_KMAX + r] = r < k ? xs[Wp + t * s + r] : 0.f;
+            }
+            int m = 0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                S[i] += u[i];
+#pragma unroll
+                for (int j = i; j < D; ++j) {
+                    M[m] = fmaf(u[i], u[j], M[m]);
+                    ++m;
+                }
             }
         }
+        // block reduction in a fixed order: warp butterflies, then the warps' rows in order
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+        for (int i = 0; i < D; ++i)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sm8[c] += __shfl_xor_sync(0xffffffffu, sm8[c], o);
-                sq8[c] += __shfl_xor_sync(0xffffffffu, sq8[c], o);
+            for (int o = 16; o > 0; o >>= 1) S[i] += __shfl_xor_sync(0xffffffffu, S[i], o);
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) M[i] += __shfl_xor_sync(0xffffffffu, M[i], o);
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) red[warp * STEM_NMOM + i] = S[i];
+#pragma unroll
+            for (int i = 0; i < NM; ++i) red[warp * STEM_NMOM + D + i] = M[i];
+        }
+        __syncthreads();
+        for (int i = tid; i < STEM_NMOM; i += STEM_T) {
+            float v = 0.f;
+            for (int w8 = 0; w8 < STEM_T / 32; ++w8) v += red[w8 * STEM_NMOM + i];
+            mom[i] = v;
+        }
+        __syncthreads();
+        for (int c = tid; c < C0; c += STEM_T) {
+            float wv[D];
+#pragma unroll
+            for (int r = 0; r < STEM_KMAX; ++r) {
+                wv[r] = r < k ? wt[c * 2 * k + r] : 0.f;
+                wv[STEM_KMAX + r] = r < k ? wt[c * 2 * k + k + r] : 0.f;
             }
-        if (lane == 0)
+            float sm = 0.f, sq = 0.f;
+            int m = 0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                csum[ch * 8 + c] = sm8[c];
-                csq[ch * 8 + c] = sq8[c];
+            for (int i = 0; i < D; ++i) {
+                sm = fmaf(wv[i], mom[i], sm);
+#pragma unroll
+                for (int j = i; j < D; ++j) {
+                    const float v = wv[i] * wv[j] * mom[D + m++];
+                    sq += (j == i) ? v : 2.f * v;
+                }
             }
+            csum[c] = sm;
+            csq[c] = sq;
+        }
     }
     __syncthreads();
     // ---- GroupNorm affine map per channel
@@ -1402,7 +1445,7 @@ int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_
     if (rc) return rc;
     const int W = ctx->cfg.win_len;
     const int pad = S.k / 2;
-    const size_t stem_smem = (size_t)(2 * (W + 2 * pad) + 4 * S.cout) * sizeof(float);
+    const size_t stem_smem = (size_t)(2 * (W + 2 * pad) + 4 * S.cout + (STEM_T / 32 + 1) * STEM_NMOM) * sizeof(float);
     for (int64_t w0 = 0; w0 < n_win; w0 += chunk) {
         const int nw = (int)std::min<int64_t>(chunk, n_win - w0);
         {
