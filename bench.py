@@ -409,7 +409,9 @@ def run_timeslides(args):
     """One step = the whole timeslide background of ~1 day: whitening of every
     segment, every window of every (segment, timeslide) series through the
     network in one persistent launch, integration and clustering of every
-    series; replayed as one CUDA graph."""
+    series (replayed as one CUDA graph), then the false-alarm rates: the
+    background triggers sorted on the device and ranked against 1024
+    statistic samples."""
     import torch
     import torch.distributed as dist
 
@@ -440,13 +442,24 @@ def run_timeslides(args):
         torch.cuda.synchronize()
 
     out = None
+    trig_cap = 1 << 20
+    far_out = None
+
+    def far_step():
+        logits, stat, trig, n_trig = out
+        return ctx.far(stat, stat[:1024], livetime, bg_idx=trig, n_bg=n_trig, bg_cap=trig_cap, out=far_out,
+                       stream=stream)
+
     with torch.cuda.stream(stream):
-        # one uninstrumented direct call for the per-kernel shares, then the captured graph
+        # one direct call with per-kernel timing for the shares, then the captured graph
         ctx.profile_enable(True)
-        out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, out=out, stream=stream)
+        out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, trig_cap=trig_cap, out=out, stream=stream)
+        far_out = far_step()
         kstats = ctx.profile_read()
         for _ in range(args.warmup):
-            out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, use_graph=True, out=out, stream=stream)
+            out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, trig_cap=trig_cap, use_graph=True, out=out,
+                                stream=stream)
+            far_step()
     barrier()
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
@@ -460,13 +473,16 @@ def run_timeslides(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.batch_run(xd, segs, args.n_shift, wl.fs, use_graph=True, out=out, stream=stream)
+            ctx.batch_run(xd, segs, args.n_shift, wl.fs, trig_cap=trig_cap, use_graph=True, out=out, stream=stream)
+            far_step()
             e1.record(stream)
             evs.append((e0, e1))
     barrier()
     ctx.sync(stream)
     clocks = sampler.stop() if sampler else None
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    n_bg = int(out[3].item())
+    far_min = float(far_out[1][:1024].min().item()) if n_bg else 0.0
     value, _, job_s = pdist.job_throughput(livetime * args.steps, total_ms / 1000.0, world)
     total_ms = job_s * 1000.0
     if rank != 0:
@@ -484,7 +500,8 @@ def run_timeslides(args):
            "vs_baseline": None, "dtype": "bf16" if precision == abi.AFG_BF16 else "f32", "data": "synthetic",
            "config": {"workload": wl.name, "segments": len(segs), "strain_s": int(sum(lengths)),
                       "timeslides": args.n_shift, "windows": tw, "livetime_s": livetime,
-                      "graph": "one CUDA graph per step", "l2": "flushed between steps (512 MiB write)"},
+                      "graph": "one CUDA graph per step + the FAR sort", "l2": "flushed between steps (512 MiB write)",
+                      "background_triggers": n_bg, "far_min_per_s": far_min},
            "roofline": roofline, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
            "kernels_direct_call": kernels}
     print(json.dumps(res), flush=True)

@@ -262,6 +262,46 @@ int afg_batch_run(afg_ctx *ctx, const float *x, int64_t x_len, const afg_segment
                   int64_t *n_trig, void *stream);
 
 
+/* ---------------------------------------------------------------- false-alarm rates, trigger times */
+
+/* False-alarm rates from a timeslide background (Sec. IX: the FAR assigned to an
+ * event is the number of background events with a detection statistic greater
+ * than the event's, divided by the background livetime).
+ * Background events: bg_stat[bg_idx[i]] for i < n (bg_idx NULL: bg_stat[i]),
+ * where n = min(*n_bg_dev, bg_cap) is read on the device, so the trigger list
+ * and count that afg_batch_run writes can be passed directly (bg_stat = its
+ * stat, bg_idx = its trig_idx, n_bg_dev = its n_trig, bg_cap = its trig_cap).
+ * For each of the n_fg foreground statistics fg[j] (device f32):
+ *   n_above[j] = #{background statistics > fg[j]}  (device i64, may be NULL)
+ *   far[j]     = n_above[j] / livetime_s            (device f64, per second, may be NULL)
+ * bg_sorted (device f32 [bg_cap], may be NULL) receives the background
+ * statistics in decreasing order (the first n entries).  The sort runs on the
+ * device (radix sort of order-preserving keys); nothing synchronises, so the
+ * call can follow afg_batch_run on the same stream or inside a graph capture.
+ * NaN statistics give unspecified counts.  Errors: AFG_ERR_ARG for NULL
+ * inputs, bg_cap < 0, n_fg < 0 or livetime_s <= 0. */
+int afg_far(afg_ctx *ctx, const float *bg_stat, const int64_t *bg_idx, const int64_t *n_bg_dev, int64_t bg_cap,
+            double livetime_s, const float *fg, int64_t n_fg, int64_t *n_above, double *far, float *bg_sorted,
+            void *stream);
+
+/* Times of statistic samples (host only, no GPU work).  For indices idx[i]
+ * into the statistic of one span analysed with run parameters p (as in
+ * afg_analyze), with t0 the time of raw sample 0:
+ *   t_peak[i] = t0 + (base + (idx[i] + n_int - 1) * stride + W) / fs
+ * (Sec. II: the statistic is stamped at the right edge of the newest window
+ * it integrates; base = fir_len/2 in plain mode, psd_len in epoch mode), and
+ * the coalescence-time estimate (Sec. II: correct for the integration length,
+ * the whitening settle-in and where the coalescence sat in the training
+ * kernel; Fig. 1: full activation comes 0.75 s after coalescence)
+ *   t_c[i] = t_peak[i] - (n_int - 1) * stride / fs - gap_s,
+ * i.e. the time at which a response that switches on gap_s after coalescence
+ * and lasts at least the integration length first reaches the maximum of its
+ * causal average.  gap_s = 0.75 reproduces the paper's offsets.  t_peak or
+ * t_c may be NULL.  Errors: AFG_ERR_ARG for NULL ctx/p/idx, n < 0, or an index
+ * outside [0, n_win - n_int]. */
+int afg_trigger_times(const afg_ctx *ctx, const afg_run_params *p, const int64_t *idx, int64_t n, double t0,
+                      double gap_s, double *t_peak, double *t_c);
+
 /* ---------------------------------------------------------------- streaming */
 
 /* Streaming analysis with continuous batching (Sec. VI: clients send strain

@@ -240,3 +240,39 @@ def analyze_plain(x: np.ndarray, wl, weights: np.ndarray) -> dict:
     stat = integrate(logits, wl.n_int)
     trig = triggers(stat, wl.cluster_half)
     return dict(psd=psd, white=white, logits=logits, stat=stat, triggers=trig)
+
+
+# --------------------------------------------------------------------------
+# Triggers -> false-alarm rates and times
+# --------------------------------------------------------------------------
+
+
+def far(background: np.ndarray, events: np.ndarray, livetime_s: float):
+    """False-alarm rate of each event (Sec. IX): the number of background events
+    whose detection statistic is greater than the event's, divided by the
+    background livetime.  Returns (counts, rates per second)."""
+    bg = np.asarray(background, dtype=np.float64)
+    ev = np.asarray(events, dtype=np.float64)
+    counts = np.array([int(np.count_nonzero(bg > x)) for x in ev], dtype=np.int64)
+    return counts, counts / float(livetime_s)
+
+
+def trigger_times(wl, idx, t0: float, gap_s: float):
+    """Time stamp of statistic samples and the coalescence-time estimate.
+
+    Sec. II: statistic sample j averages windows j .. j + n_int - 1 and is
+    stamped at the right edge of the newest one; the coalescence time follows
+    by removing the integration length and the delay between coalescence and
+    full network activation (Fig. 1: 0.75 s, whitening settle-in plus the
+    placement of the coalescence in the training kernel).  With a response
+    that switches on gap_s after coalescence and stays on for at least the
+    integration length, the causal average first peaks n_int - 1 windows
+    after the switch-on window.  Window w starts at raw sample base + w*stride
+    (base = the 0.5 s crop in plain mode, the PSD look-back in epoch mode).
+    """
+    j = np.asarray(idx, dtype=np.int64)
+    base = wl.crop if wl.epoch_len == 0 else wl.psd_len
+    newest = j + wl.n_int - 1
+    t_peak = t0 + (base + newest * wl.stride + wl.win_len) / wl.fs
+    t_c = t_peak - (wl.n_int - 1) * wl.stride / wl.fs - gap_s
+    return t_peak, t_c

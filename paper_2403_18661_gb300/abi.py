@@ -127,6 +127,9 @@ SIGNATURES = {
     "afg_tiles_get": ([_vp, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_tile_candidates": ([_vp, _i32, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_tiles_set": ([_vp, ctypes.POINTER(AfgTile), _i32], ctypes.c_int),
+    "afg_far": ([_vp, _vp, _vp, _vp, _i64, ctypes.c_double, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "afg_trigger_times": ([_vp, ctypes.POINTER(AfgRunParams), _vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp],
+                          ctypes.c_int),
     "afg_psd_estimate_noalloc": ([_vp, _i64, _i32, _i64, _i64, _i64, _i32, _i32, _vp, _vp], ctypes.c_int),
 }
 
@@ -259,6 +262,40 @@ class Context:
         self._check(self._lib.afg_profile_read(self._h, arr, cap, ctypes.byref(n)))
         return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, total_ms=a.total_ms,
                      algo_flops=a.algo_flops, algo_bytes=a.algo_bytes) for a in arr[:min(n.value, cap)]]
+
+    # ---------------------------------------------------------------- false-alarm rates, trigger times
+    def far(self, bg_stat, fg, livetime_s: float, bg_idx=None, n_bg=None, bg_cap: Optional[int] = None,
+            out=None, stream=None):
+        """FAR of each foreground statistic from a background (device tensors).  n_bg: device int64
+        tensor holding the count (as afg_batch_run writes it) or a Python int; bg_cap: entries
+        the count may reach (default: len(bg_idx) or len(bg_stat)).  Returns (n_above, far, bg_sorted)."""
+        import torch
+        dev = bg_stat.device
+        if bg_cap is None:
+            bg_cap = int(bg_idx.numel() if bg_idx is not None else bg_stat.numel())
+        if n_bg is None:
+            n_bg = bg_cap
+        if not torch.is_tensor(n_bg):
+            n_bg = torch.tensor([int(n_bg)], dtype=torch.int64, device=dev)
+        n_fg = int(fg.numel())
+        if out is None:
+            out = (torch.empty(max(n_fg, 1), dtype=torch.int64, device=dev),
+                   torch.empty(max(n_fg, 1), dtype=torch.float64, device=dev),
+                   torch.empty(max(bg_cap, 1), dtype=torch.float32, device=dev))
+        n_above, far, bg_sorted = out
+        self._check(self._lib.afg_far(self._h, _ptr(bg_stat), _ptr(bg_idx), _ptr(n_bg), bg_cap, float(livetime_s),
+                                      _ptr(fg), n_fg, _ptr(n_above), _ptr(far), _ptr(bg_sorted), _stream(stream)))
+        return n_above[:n_fg], far[:n_fg], bg_sorted
+
+    def trigger_times(self, idx, n_raw: int, t0: float = 0.0, gap_s: float = 0.75, shift: int = 0):
+        """(t_peak, t_c) of statistic indices of a span analysed with this context's workload."""
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        tp = np.empty(len(idx))
+        tc = np.empty(len(idx))
+        p = self.run_params(n_raw, shift)
+        self._check(self._lib.afg_trigger_times(self._h, ctypes.byref(p), idx.ctypes.data, len(idx), float(t0),
+                                                float(gap_s), tp.ctypes.data, tc.ctypes.data))
+        return tp, tc
 
     # ---------------------------------------------------------------- conv tiles
     def autotune(self, n_win: int = 1024, stream=None):

@@ -106,6 +106,7 @@ enum KernelKind {
     KK_TINY_TC,
     KK_SCATTER,
     KK_CONVERT,
+    KK_FAR,
     KK_COUNT
 };
 extern const char *const kKernelNames[KK_COUNT];
@@ -165,6 +166,9 @@ enum {
     WS_SCAN,
     WS_BATCH_SEGS,
     WS_BATCH_SERIES,
+    WS_FAR_KEYS,
+    WS_FAR_HIST,
+    WS_FAR_SORTED,
 };
 
 struct KScope {
@@ -237,6 +241,10 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
 int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, cudaStream_t st);
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
+// far.cu
+int launch_far(afg_ctx *ctx, const float *bg_stat, const int64_t *bg_idx, const int64_t *n_bg_dev, int64_t bg_cap,
+               double livetime_s, const float *fg, int64_t n_fg, int64_t *n_above, double *far, float *bg_sorted,
+               cudaStream_t st);
 // integrate.cu
 int launch_integrate(afg_ctx *ctx, const float *logits, int64_t n_win, int n_int, int cluster_half,
                      float *stat, int64_t *trig_idx, int64_t trig_cap, int64_t *n_trig, cudaStream_t st);

@@ -387,4 +387,32 @@ int afg_tiles_set(afg_ctx *ctx, const afg_tile *tiles, int32_t n) {
     return net_tc_tiles_set(ctx, tiles, n);
 }
 
+int afg_far(afg_ctx *ctx, const float *bg_stat, const int64_t *bg_idx, const int64_t *n_bg_dev, int64_t bg_cap,
+            double livetime_s, const float *fg, int64_t n_fg, int64_t *n_above, double *far, float *bg_sorted,
+            void *stream) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (!bg_stat || !n_bg_dev || bg_cap < 0 || n_fg < 0 || (n_fg > 0 && !fg))
+        return afg_fail(ctx, AFG_ERR_ARG, "far: null input or negative size");
+    if (!(livetime_s > 0.0)) return afg_fail(ctx, AFG_ERR_ARG, "far: livetime_s must be > 0");
+    return launch_far(ctx, bg_stat, bg_idx, n_bg_dev, bg_cap, livetime_s, fg, n_fg, n_above, far, bg_sorted,
+                      S(stream));
+}
+
+int afg_trigger_times(const afg_ctx *ctx, const afg_run_params *p, const int64_t *idx, int64_t n, double t0,
+                      double gap_s, double *t_peak, double *t_c) {
+    if (!ctx || !p || n < 0 || (n > 0 && !idx)) return AFG_ERR_ARG;
+    const double fs = (double)ctx->cfg.fs;
+    const int64_t base = p->epoch_len == 0 ? ctx->cfg.fir_len / 2 : p->psd_len;
+    const int64_t n_stat = p->n_win - p->n_int + 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (idx[i] < 0 || idx[i] >= n_stat) return AFG_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        const double tp = t0 + (double)(base + (idx[i] + p->n_int - 1) * p->stride + ctx->cfg.win_len) / fs;
+        if (t_peak) t_peak[i] = tp;
+        if (t_c) t_c[i] = tp - (double)((int64_t)(p->n_int - 1) * p->stride) / fs - gap_s;
+    }
+    return AFG_OK;
+}
+
 }  // extern "C"

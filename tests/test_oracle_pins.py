@@ -383,3 +383,42 @@ def test_paper_window_arithmetic_golden():
     assert wl.n_win == 244
     h = inputs.HOUR_RESNET34
     assert h.n_win * h.stride == 3600 * fs and h.n_int == 16
+
+
+# ---------------------------------------------------------------- false-alarm rates and trigger times
+
+def test_far_closed_form_and_ties():
+    """Sec. IX: FAR = #(background > event) / livetime; strictly greater, so a
+    tie with a background event does not count it."""
+    N, T = 1000, 86400.0
+    bg = np.arange(1, N + 1, dtype=np.float64)
+    ev = np.array([0.5, 1.0, 1.5, 999.0, N, N + 1.0, -np.inf, np.inf, 500.25])
+    counts, rates = orc.far(bg, ev, T)
+    want = np.array([N, N - 1, N - 1, 1, 0, 0, N, 0, N - 500])
+    assert np.array_equal(counts, want)
+    assert np.array_equal(rates, want / T)
+    c2, _ = orc.far(np.array([3.0, 3.0, 3.0, 1.0]), np.array([2.0, 3.0, 0.0]), 1.0)
+    assert list(c2) == [3, 0, 4]
+    c3, r3 = orc.far(np.array([]), np.array([0.0, -1.0]), 10.0)
+    assert list(c3) == [0, 0] and list(r3) == [0.0, 0.0]
+
+
+def test_trigger_time_recovers_a_step_response():
+    """A response that switches on at the window whose right edge is t_c + 0.75 s
+    (Fig. 1) and stays on: integration (Sec. II) and clustering put the first
+    maximum n_int - 1 windows later, and the estimate returns exactly t_c."""
+    import dataclasses
+    for wl in (inputs.PLAIN_64S, dataclasses.replace(inputs.PLAIN_64S, stride=128)):  # 4 Hz and 16 Hz
+        n_win = 200
+        for w_on in (7, 40, 123):
+            z = np.zeros(n_win)
+            z[w_on:] = 1.0
+            stat = orc.integrate(z, wl.n_int)
+            trig = orc.triggers(stat, wl.cluster_half)
+            on = [int(j) for j in trig if stat[j] == 1.0]  # (the flat zero stretch before it may cluster too)
+            assert on == [w_on]  # earliest index of the plateau
+            t0 = 1234.5
+            t_c_true = t0 + (wl.crop + w_on * wl.stride + wl.win_len) / wl.fs - 0.75
+            t_peak, t_c = orc.trigger_times(wl, on, t0, 0.75)
+            assert abs(t_c[0] - t_c_true) < 1e-9
+            assert abs(t_peak[0] - (t_c_true + 0.75 + (wl.n_int - 1) * wl.stride / wl.fs)) < 1e-9
