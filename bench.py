@@ -264,6 +264,31 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
+    if args.workload == "resample":
+        from oracle import oracle as orc
+        fs_in, M, sec = 16384, 8, 20
+        rng = np.random.default_rng(99)
+        x = rng.standard_normal((2, sec * fs_in + 2 * 10 * M)) * 1e-21
+        vals, total = [], 0.0
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            orc.resample(x, M)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                vals.append(sec / dt)
+                total += dt
+        value = statistics.mean(vals)
+        samp = f"{sec} s of two-detector 16384 Hz strain decimated by 8 per step (FP64 oracle, numpy)"
+        print(json.dumps({"metric": "strain-seconds/s resampled 16384 -> 2048 Hz", "impl": "reference", "value": value,
+                          "unit": "strain-s/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "1h-2det-16384Hz-decimate8"},
+                          "cpu_baseline": {"value": value, "unit": "strain-s/s", "cores": 1, "kind": "oracle",
+                                           "sample": samp},
+                          "e2e": {"value": value, "unit": "strain-s/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
     wl = workload_by_name(args.workload, args.n_win)
     x, _ = inputs.make_strain(wl)
     w = inputs.make_weights(wl.net, wl.weight_seed)
@@ -608,13 +633,109 @@ def run_serving(args):
     return 0
 
 
+def run_resample(args):
+    """One step = decimation of 1 h of two-detector strain from 16384 Hz to 2048 Hz (Sec. IV.A),
+    device buffers resident; e2e adds the host copies of the raw strain and of the result."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_18661_gb300 import abi
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fs_in, M, dur = 16384, 8, 3600.0
+    n_in = int(fs_in * dur) + 2 * 10 * M  # the hour plus the filter's half-length at each end
+    rng = np.random.default_rng(pdist.rank_seed(99, rank))
+    x = (rng.standard_normal((2, n_in), dtype=np.float32) * np.float32(1e-21))
+    wl = inputs.PLAIN_64S
+    ctx = abi.Context(wl, inputs.make_weights(wl.net, wl.weight_seed))
+    xd = torch.from_numpy(x).to(dev)
+    n_out, first = abi.resample_size(n_in, M)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        y, _ = ctx.resample(xd, M)
+    barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ctx.profile_enable(True)
+    evs = []
+    barrier()
+    for _ in range(args.steps):  # inputs (472 MB) exceed the 129 MB L2: no flush needed
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y, _ = ctx.resample(xd, M)
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    ctx.profile_enable(False)
+    clocks = sampler.stop() if sampler else None
+    kstats = ctx.profile_read()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    value, _, job_s = pdist.job_throughput(dur * args.steps, total_ms / 1000.0, world)
+    e2e = None
+    if not args.no_e2e:
+        xp = torch.from_numpy(x).pin_memory()
+        yh = torch.empty((2, n_out), dtype=torch.float32).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xd.copy_(xp, non_blocking=True)
+            y, _ = ctx.resample(xd, M)
+            yh.copy_(y, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        barrier()
+        e2e_v, _, _ = pdist.job_throughput(dur * args.steps, time.perf_counter() - t0, world)
+        e2e = {"value": e2e_v, "unit": "strain-s/s", "h2d_bytes_per_step": int(x.nbytes),
+               "d2h_bytes_per_step": int(yh.numel() * 4)}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        from oracle import oracle as orc
+        sec = 60
+        t0 = time.perf_counter()
+        orc.resample(x[:, : sec * fs_in + 2 * 10 * M].astype(np.float64), M)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sec / dt, "unit": "strain-s/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sec} s of two-detector 16384 Hz strain decimated by the FP64 oracle (numpy)"}
+    peaks = load_peaks()
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    out = {"metric": "strain-seconds/s resampled 16384 -> 2048 Hz", "value": value, "unit": "strain-s/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": job_s * 1000.0 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "1h-2det-16384Hz-decimate8", "n_in": n_in, "n_out": n_out, "taps": 2 * 10 * M + 1,
+                      "l2": "inputs (472 MB) larger than L2"},
+           "roofline": roofline_for(dom, peaks, job_s * 1000.0), "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(sum(k["launches"] for k in kstats)), "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="hour", choices=["hour", "plain64", "timeslides", "serving"])
+    ap.add_argument("--workload", default="hour", choices=["hour", "plain64", "timeslides", "serving", "resample"])
     ap.add_argument("--n-streams", type=int, default=128, help="streams (serving workload)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="strain per stream in the throughput phase")
     ap.add_argument("--n-shift", type=int, default=100, help="timeslides per segment (timeslides workload)")
@@ -638,6 +759,8 @@ def main():
         return run_timeslides(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "resample":
+        return run_resample(args)
     return run_ours(args)
 
 

@@ -262,6 +262,28 @@ int afg_batch_run(afg_ctx *ctx, const float *x, int64_t x_len, const afg_segment
                   int64_t *n_trig, void *stream);
 
 
+/* ---------------------------------------------------------------- resampling */
+
+/* Decimation of raw strain by an integer factor M (Sec. IV.A: the strain is
+ * resampled to 2048 Hz, e.g. 16384 Hz with M = 8 or 4096 Hz with M = 2;
+ * Table III: the filter's edge costs latency).  Anti-aliasing filter: a
+ * Kaiser-windowed sinc (beta = 5), 2L + 1 taps with L = 10 M, cutoff at the
+ * output Nyquist frequency, normalised to unit gain at DC.  Valid mode:
+ * output j is the filter centred on input sample (j0 + j) * M with
+ * j0 = ceil(L / M), for every centre whose taps lie inside the input:
+ *   y[d][j] = sum_{k=-L..L} h_k x[d][(j0 + j) M + k].
+ * x: [n_det][x_stride] f32 (device; x_stride 0 = n_in); y: [n_det][y_stride]
+ * f32 (device; y_stride 0 = the output count).  *n_out (host, may be NULL)
+ * receives the output count.  The first call with a given factor builds the
+ * taps on this context and synchronises; later calls only launch.
+ * Errors: AFG_ERR_ARG for NULL pointers, n_det < 1, a factor outside 2..16,
+ * or strides smaller than the rows. */
+int afg_resample(afg_ctx *ctx, const float *x, int64_t n_in, int32_t n_det, int64_t x_stride, int32_t factor, float *y,
+                 int64_t y_stride, int64_t *n_out, void *stream);
+
+/* Output count of afg_resample and the input sample of output 0 (host only). */
+int afg_resample_size(int64_t n_in, int32_t factor, int64_t *n_out, int64_t *first_input);
+
 /* ---------------------------------------------------------------- false-alarm rates, trigger times */
 
 /* False-alarm rates from a timeslide background (Sec. IX: the FAR assigned to an

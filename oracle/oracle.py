@@ -276,3 +276,38 @@ def trigger_times(wl, idx, t0: float, gap_s: float):
     t_peak = t0 + (base + newest * wl.stride + wl.win_len) / wl.fs
     t_c = t_peak - (wl.n_int - 1) * wl.stride / wl.fs - gap_s
     return t_peak, t_c
+
+
+# --------------------------------------------------------------------------
+# Resampling
+# --------------------------------------------------------------------------
+
+
+def resample_taps(factor: int) -> np.ndarray:
+    """Decimation filter for factor M (Sec. IV.A: strain resampled to 2048 Hz;
+    the paper names no filter).  Reading: a Kaiser-windowed sinc (beta = 5),
+    2L + 1 taps with L = 10 M, cutoff at the output Nyquist frequency, unit
+    gain at DC: the design of the common polyphase resampler."""
+    M = int(factor)
+    L = 10 * M
+    k = np.arange(2 * L + 1) - L
+    h = np.sinc(k / M) / M * np.kaiser(2 * L + 1, 5.0)
+    return h / h.sum()
+
+
+def resample(x: np.ndarray, factor: int):
+    """Valid-mode decimation: output j is the filter centred on input sample
+    (j0 + j) M, j0 = ceil(L / M), for every centre whose taps lie inside x.
+    Returns (y, first input sample)."""
+    M = int(factor)
+    L = 10 * M
+    h = resample_taps(M)
+    x = np.asarray(x, dtype=np.float64)
+    n_in = x.shape[-1]
+    j0 = -(-L // M)
+    n_out = max(0, (n_in - 1 - L) // M - j0 + 1) if n_in - 1 - L >= j0 * M else 0
+    if n_out == 0:
+        return np.zeros(x.shape[:-1] + (0,)), j0 * M
+    win = np.lib.stride_tricks.sliding_window_view(x, 2 * L + 1, axis=-1)
+    sel = win[..., j0 * M - L: j0 * M - L + (n_out - 1) * M + 1: M, :]
+    return sel @ h, j0 * M

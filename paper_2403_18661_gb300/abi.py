@@ -127,6 +127,8 @@ SIGNATURES = {
     "afg_tiles_get": ([_vp, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_tile_candidates": ([_vp, _i32, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_tiles_set": ([_vp, ctypes.POINTER(AfgTile), _i32], ctypes.c_int),
+    "afg_resample": ([_vp, _vp, _i64, _i32, _i64, _i32, _vp, _i64, ctypes.POINTER(_i64), _vp], ctypes.c_int),
+    "afg_resample_size": ([_i64, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
     "afg_far": ([_vp, _vp, _vp, _vp, _i64, ctypes.c_double, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
     "afg_trigger_times": ([_vp, ctypes.POINTER(AfgRunParams), _vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp],
                           ctypes.c_int),
@@ -205,6 +207,15 @@ def psd_estimate_noalloc(x, n_psd: int = 1, psd_step: int = 0, psd_span: Optiona
     return out
 
 
+def resample_size(n_in: int, factor: int):
+    """(output count, input sample of output 0) of afg_resample."""
+    n, f = _i64(), _i64()
+    rc = load().afg_resample_size(int(n_in), int(factor), ctypes.byref(n), ctypes.byref(f))
+    if rc != AFG_OK:
+        raise AfgError(rc, "resample_size: bad arguments")
+    return n.value, f.value
+
+
 class Context:
     """One library context (weights, twiddles, workspaces) on the current CUDA device."""
 
@@ -262,6 +273,19 @@ class Context:
         self._check(self._lib.afg_profile_read(self._h, arr, cap, ctypes.byref(n)))
         return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, total_ms=a.total_ms,
                      algo_flops=a.algo_flops, algo_bytes=a.algo_bytes) for a in arr[:min(n.value, cap)]]
+
+    # ---------------------------------------------------------------- resampling
+    def resample(self, x, factor: int, stream=None):
+        """Decimate device strain x [n_det][n_in] by `factor`: returns (y [n_det][n_out], first input sample)."""
+        import torch
+        n_det, n_in = x.shape
+        n_out, first = resample_size(n_in, factor)
+        y = torch.empty((n_det, max(n_out, 1)), dtype=torch.float32, device=x.device)
+        got = _i64()
+        self._check(self._lib.afg_resample(self._h, _ptr(x), n_in, n_det, x.stride(0), factor, _ptr(y), y.stride(0),
+                                           ctypes.byref(got), _stream(stream)))
+        assert got.value == n_out
+        return y[:, :n_out], first
 
     # ---------------------------------------------------------------- false-alarm rates, trigger times
     def far(self, bg_stat, fg, livetime_s: float, bg_idx=None, n_bg=None, bg_cap: Optional[int] = None,

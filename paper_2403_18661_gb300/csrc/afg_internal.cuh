@@ -107,6 +107,7 @@ enum KernelKind {
     KK_SCATTER,
     KK_CONVERT,
     KK_FAR,
+    KK_RESAMPLE,
     KK_COUNT
 };
 extern const char *const kKernelNames[KK_COUNT];
@@ -146,6 +147,7 @@ struct afg_ctx {
     int64_t bytes_held = 0;
     int *d_err = nullptr;             // device-side failure record (bounded waits that gave up)
     Workspace ws[24];
+    float *rs_taps[17] = {};          // decimation filters by factor (resample.cu)
 };
 
 // workspace slots
@@ -241,6 +243,10 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
 int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, cudaStream_t st);
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
+// resample.cu
+int64_t resample_count(int64_t n_in, int M, int64_t *j0_out);
+int launch_resample(afg_ctx *ctx, const float *x, int64_t n_in, int n_det, int64_t x_stride, int M, float *y,
+                    int64_t y_stride, int64_t *n_out_host, cudaStream_t st);
 // far.cu
 int launch_far(afg_ctx *ctx, const float *bg_stat, const int64_t *bg_idx, const int64_t *n_bg_dev, int64_t bg_cap,
                double livetime_s, const float *fg, int64_t n_fg, int64_t *n_above, double *far, float *bg_sorted,

@@ -184,6 +184,8 @@ int afg_ctx_destroy(afg_ctx *ctx) {
     if (ctx->d_params) cudaFree(ctx->d_params);
     if (ctx->plan.tc_params) cudaFree(ctx->plan.tc_params);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    for (float *t : ctx->rs_taps)
+        if (t) cudaFree(t);
     if (ctx->tw32) cudaFree(ctx->tw32);
     if (ctx->tw64) cudaFree(ctx->tw64);
     delete ctx;
@@ -413,6 +415,27 @@ int afg_trigger_times(const afg_ctx *ctx, const afg_run_params *p, const int64_t
         if (t_c) t_c[i] = tp - (double)((int64_t)(p->n_int - 1) * p->stride) / fs - gap_s;
     }
     return AFG_OK;
+}
+
+int afg_resample_size(int64_t n_in, int32_t factor, int64_t *n_out, int64_t *first_input) {
+    if (!n_out || n_in < 0 || factor < 2 || factor > 16) return AFG_ERR_ARG;
+    int64_t j0 = 0;
+    *n_out = resample_count(n_in, factor, &j0);
+    if (first_input) *first_input = j0 * factor;
+    return AFG_OK;
+}
+
+int afg_resample(afg_ctx *ctx, const float *x, int64_t n_in, int32_t n_det, int64_t x_stride, int32_t factor, float *y,
+                 int64_t y_stride, int64_t *n_out, void *stream) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (!x || !y || n_in < 0 || n_det < 1 || factor < 2 || factor > 16)
+        return afg_fail(ctx, AFG_ERR_ARG, "resample: null pointer, n_in < 0, n_det < 1 or factor outside 2..16");
+    if (x_stride == 0) x_stride = n_in;
+    const int64_t cnt = resample_count(n_in, factor, nullptr);
+    if (y_stride == 0) y_stride = cnt;
+    if (x_stride < n_in || y_stride < cnt) return afg_fail(ctx, AFG_ERR_ARG, "resample: row strides too small");
+    return launch_resample(ctx, x, n_in, n_det, x_stride, factor, y, y_stride, n_out, S(stream));
 }
 
 }  // extern "C"

@@ -7,7 +7,7 @@ const char *const kKernelNames[KK_COUNT] = {
     "twiddles", "welch_periodogram", "welch_mean", "filter_build_fp64", "whiten_overlap_save",
     "stem_conv", "groupnorm", "conv_gemm_fp32_simt", "pool_linear_head", "integrate", "triggers",
     "conv_gemm_bf16_tcgen05", "resnet_tiny_fused_bf16_tcgen05", "stream_scatter", "to_bf16",
-    "far_sort_rank",
+    "far_sort_rank", "resample_decimate",
 };
 
 static cudaEvent_t take_event(Prof &p) {

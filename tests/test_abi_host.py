@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2403_18661_gb300 import abi, inputs
@@ -67,3 +68,15 @@ def test_null_context_is_refused(lib):
     assert lib.afg_ctx_destroy(None) == -1
     assert lib.afg_psd_estimate(None, None, 0, 0, 0, 0, 0, None, None) == -1
     assert lib.afg_analyze(None, None, None, None, None, None, 0, None, None) == -1
+
+
+def test_resample_size_matches_the_oracle():
+    """Host-only sizing of the decimator (no GPU): output count and first input sample."""
+    from oracle import oracle as orc
+    for M in (2, 4, 8, 16):
+        for n_in in (0, 10 * M * 2, 10 * M * 2 + 1, 10 * M * 2 + M, 12345, 16384 * 8 + 3):
+            n, first = abi.resample_size(n_in, M)
+            y, first_o = orc.resample(np.zeros(n_in), M)
+            assert n == y.shape[-1] and first == first_o
+    with pytest.raises(abi.AfgError):
+        abi.resample_size(100, 1)

@@ -422,3 +422,44 @@ def test_trigger_time_recovers_a_step_response():
             t_peak, t_c = orc.trigger_times(wl, on, t0, 0.75)
             assert abs(t_c[0] - t_c_true) < 1e-9
             assert abs(t_peak[0] - (t_c_true + 0.75 + (wl.n_int - 1) * wl.stride / wl.fs)) < 1e-9
+
+
+# ---------------------------------------------------------------- resampling
+
+@pytest.mark.parametrize("M", [2, 4, 8])
+def test_resample_matches_scipy_resample_poly(M):
+    """The oracle's decimator is the Kaiser-windowed design of scipy.signal.resample_poly
+    (library check on the valid outputs)."""
+    scipy_signal = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(M)
+    x = rng.standard_normal((2, 5000 + 37))
+    y, first = orc.resample(x, M)
+    ref = scipy_signal.resample_poly(x, 1, M, axis=-1, window=("kaiser", 5.0))
+    j0 = first // M
+    assert first % M == 0 and y.shape[1] > 0
+    assert np.max(np.abs(y - ref[:, j0:j0 + y.shape[1]])) < 1e-12
+
+
+def test_resample_closed_forms():
+    """DC passes exactly; a cosine comes out scaled by the filter's response
+    H(f) = sum_k h_k cos(2 pi f k / fs_in), which is ~1 in the band and small
+    above the new Nyquist frequency."""
+    M, fs = 8, 16384.0
+    h = orc.resample_taps(M)
+    assert abs(h.sum() - 1.0) < 1e-14 and np.allclose(h, h[::-1])
+    y, _ = orc.resample(np.full(4000, 3.25), M)
+    assert np.max(np.abs(y - 3.25)) < 1e-13
+    L = 10 * M
+    k = np.arange(-L, L + 1)
+    n = np.arange(40000)
+    for f in (100.0, 800.0, 1500.0):
+        H = float(np.sum(h * np.cos(2 * np.pi * f * k / fs)))
+        y, first = orc.resample(np.cos(2 * np.pi * f * n / fs), M)
+        t = first + M * np.arange(y.shape[-1])
+        assert np.max(np.abs(y - H * np.cos(2 * np.pi * f * t / fs))) < 1e-12
+        if f <= 800.0:
+            assert abs(H - 1.0) < 2e-3
+        else:
+            assert abs(H) < 0.02
+    y, _ = orc.resample(np.zeros(100), M)  # shorter than the filter
+    assert y.shape[-1] == 0
