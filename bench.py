@@ -729,13 +729,90 @@ def run_resample(args):
     return 0
 
 
+def run_rates(args):
+    """Inference-rate sweep (Sec. IX: throughput vs inference rate; the online mode evaluates a
+    window at every sample).  One step = the whole path (PSD epochs, whitening, every window through
+    the paper's 16-channel network on tcgen05, integration, clustering) over 1 h of strain at a given
+    rate; the line's value is the paper's 4 Hz rate, the sweep holds 1..64 Hz and 2048 Hz."""
+    import torch
+
+    from paper_2403_18661_gb300 import abi
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        raise SystemExit("the rate sweep runs on one GPU")
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = dataclasses.replace(inputs.HOUR_RESNET34, name="1h-tiny-rates", net=inputs.TINY_NET, stride=512,
+                               n_win=3600 * 4, n_chirps=200)
+    x, _ = inputs.make_strain(base)
+    xd = torch.from_numpy(x).to(dev)
+    w = inputs.make_weights(base.net, base.weight_seed)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    rates = [1, 2, 4, 8, 16, 32, 64, 2048]
+    sweep, kst4, clocks = {}, None, None
+    for r in rates:
+        wl = dataclasses.replace(base, name=f"1h-tiny-{r}Hz", stride=2048 // r, n_win=3600 * r)
+        assert wl.n_raw == base.n_raw
+        res = {}
+        for prec in (["bf16", "fp32"] if (r <= 64 and not args.no_fp32) else ["bf16"]):
+            ctx = abi.Context(wl, w, precision=abi.AFG_BF16 if prec == "bf16" else abi.AFG_FP32)
+            steps = args.steps if r < 2048 or prec == "bf16" else 1
+            out = None
+            for _ in range(args.warmup):
+                out = ctx.analyze(xd, trig_cap=1 << 16, out=out)
+            torch.cuda.synchronize()
+            sampler = ClockSampler(0) if (r == 4 and prec == "bf16") else None
+            if sampler:
+                sampler.start()
+                ctx.profile_enable(True)
+            evs = []
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.analyze(xd, trig_cap=1 << 16, out=out)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            if sampler:
+                ctx.profile_enable(False)
+                clocks = sampler.stop()
+                kst4 = ctx.profile_read()
+            ctx.sync()
+            ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+            res[prec] = {"strain_s_per_s": 3600.0 / (ms / 1000.0), "windows_per_s": wl.n_win / (ms / 1000.0),
+                         "ms_per_step": ms}
+            ctx.close()
+        if "fp32" in res:
+            res["bf16_over_fp32"] = res["bf16"]["strain_s_per_s"] / res["fp32"]["strain_s_per_s"]
+        sweep[f"{r}Hz"] = res
+    peaks = load_peaks()
+    dom = max(kst4, key=lambda k: k["total_ms"])
+    v4 = sweep["4Hz"]["bf16"]
+    out = {"metric": "strain-seconds/s whiten+ResNet vs inference rate (tiny network, BF16)",
+           "value": v4["strain_s_per_s"], "unit": "strain-s/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v4["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": "1h-tiny-rate-sweep", "rates_hz": rates, "value_at": "4 Hz",
+                      "l2": "flushed between steps (512 MiB write)"},
+           "roofline": roofline_for(dom, peaks, sum(k["total_ms"] for k in kst4)),
+           "gpu_launches": int(sum(k["launches"] for k in kst4)), "clocks": clocks, "sweep": sweep}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="hour", choices=["hour", "plain64", "timeslides", "serving", "resample"])
+    ap.add_argument("--workload", default="hour",
+                    choices=["hour", "plain64", "timeslides", "serving", "resample", "rates"])
+    ap.add_argument("--no-fp32", action="store_true", help="rates workload: BF16 only")
     ap.add_argument("--n-streams", type=int, default=128, help="streams (serving workload)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="strain per stream in the throughput phase")
     ap.add_argument("--n-shift", type=int, default=100, help="timeslides per segment (timeslides workload)")
@@ -761,6 +838,8 @@ def main():
         return run_serving(args)
     if args.workload == "resample":
         return run_resample(args)
+    if args.workload == "rates":
+        return run_rates(args)
     return run_ours(args)
 
 

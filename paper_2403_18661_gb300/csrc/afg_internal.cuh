@@ -146,7 +146,7 @@ struct afg_ctx {
     double2 *tw64 = nullptr;          // same in double
     int64_t bytes_held = 0;
     int *d_err = nullptr;             // device-side failure record (bounded waits that gave up)
-    Workspace ws[24];
+    Workspace ws[32];
     float *rs_taps[17] = {};          // decimation filters by factor (resample.cu)
 };
 
@@ -171,6 +171,10 @@ enum {
     WS_FAR_KEYS,
     WS_FAR_HIST,
     WS_FAR_SORTED,
+    WS_TRIG_A,
+    WS_TRIG_B,
+    WS_TRIG_FLAG,
+    WS_TRIG_COUNT,
 };
 
 struct KScope {

@@ -4,9 +4,13 @@
 // candidate).
 //
 //   k_integrate   stat[j] = (1/n_int) sum_{i<n_int} z[j+i], summed in index order
-//   k_triggers    one CTA: flags the cluster maxima (earliest index wins ties)
-//                 and compacts them in increasing index order with a
-//                 block-wide prefix sum over 1024-index chunks.
+//   triggers      the cluster maxima (earliest index wins ties) from windowed
+//                 maxima built by doubling, O(n log h), compacted in increasing
+//                 index order across blocks (counts, one scan, writes).
+#include <math.h>
+
+#include <algorithm>
+
 #include "afg_internal.cuh"
 
 namespace {
@@ -19,46 +23,93 @@ __global__ void k_integrate(const float *__restrict__ z, int64_t n_out, int n_in
     stat[j] = s / (float)n_int;
 }
 
-constexpr int TT = 1024;
+// ---- clustering: j is a trigger iff I[j] > max I[j-h .. j-1] and I[j] >= max I[j+1 .. j+h]
+// (earliest index wins ties).  The statistic is padded with -inf on both sides (h each), so
+// every window is full; M_k[i] = max P[i .. i + 2^k) is built by k doubling passes
+// (2^k <= h < 2^(k+1)), and each half-window is the union of two overlapping 2^k windows.
+constexpr int TB = 1024;  // indices per compaction block
 
-__global__ void __launch_bounds__(TT) k_triggers(const float *__restrict__ I, int64_t n, int half,
-                                                 int64_t *__restrict__ idx, int64_t cap, int64_t *__restrict__ n_trig) {
-    __shared__ int warp_tot[TT / 32];
-    __shared__ int64_t base_s;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) base_s = 0;
-    __syncthreads();
-    for (int64_t c0 = 0; c0 < n; c0 += TT) {
-        const int64_t j = c0 + tid;
-        int flag = 0;
-        if (j < n) {
+__global__ void k_trig_pad(const float *__restrict__ I, int64_t n, int h, float *__restrict__ P) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + 2 * (int64_t)h;
+         i += (int64_t)gridDim.x * blockDim.x)
+        P[i] = (i >= h && i < n + h) ? I[i - h] : -INFINITY;
+}
+
+__global__ void k_trig_double(const float *__restrict__ A, int64_t len, int64_t step, float *__restrict__ B) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        B[i] = fmaxf(A[i], A[i + step]);
+}
+
+// flags and per-block counts (M: level-k maxima of the padded statistic, or the statistic when h = 0)
+__global__ void __launch_bounds__(TB) k_trig_flag(const float *__restrict__ I, const float *__restrict__ M,
+                                                  int64_t n, int h, int64_t w, uint8_t *__restrict__ flag,
+                                                  int *__restrict__ counts) {
+    __shared__ int wc[TB / 32];
+    const int64_t j = (int64_t)blockIdx.x * TB + threadIdx.x;
+    int f = 0;
+    if (j < n) {
+        if (h == 0) {
+            f = 1;
+        } else {
+            const int64_t p = j + h;  // padded index of j
             const float v = I[j];
-            flag = 1;
-            int64_t lo = j - half < 0 ? 0 : j - half;
-            int64_t hi = j + half >= n ? n - 1 : j + half;
-            for (int64_t i = lo; i < j && flag; ++i) flag = v > I[i];
-            for (int64_t i = j + 1; i <= hi && flag; ++i) flag = v >= I[i];
+            const float left = fmaxf(M[p - h], M[p - w]);
+            const float right = fmaxf(M[p + 1], M[p + h - w + 1]);
+            f = (v > left) && (v >= right);
         }
-        unsigned m = __ballot_sync(0xffffffffu, flag);
-        int in_warp = __popc(m & ((1u << lane) - 1u));
-        if (lane == 0) warp_tot[wid] = __popc(m);
+        flag[j] = (uint8_t)f;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int i = 0; i < TB / 32; ++i) t += wc[i];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of the block counts (one block, fixed order) and the total
+__global__ void __launch_bounds__(1024) k_trig_scan(int *__restrict__ counts, int nb, int64_t *__restrict__ n_trig) {
+    __shared__ int64_t s[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nb; c0 += 1024) {
+        const int i = c0 + threadIdx.x;
+        const int64_t v = i < nb ? counts[i] : 0;
+        s[threadIdx.x] = v;
         __syncthreads();
-        int before = 0, total = 0;
-        for (int w = 0; w < TT / 32; ++w) {
-            int t = warp_tot[w];
-            if (w < wid) before += t;
-            total += t;
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int64_t t = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
         }
-        const int64_t base = base_s;
-        if (flag) {
-            int64_t pos = base + before + in_warp;
-            if (pos < cap) idx[pos] = j;
-        }
+        if (i < nb) counts[i] = (int)(carry + s[threadIdx.x] - v);
         __syncthreads();
-        if (tid == 0) base_s = base + total;
+        if (threadIdx.x == 1023) carry += s[1023];
         __syncthreads();
     }
-    if (tid == 0) *n_trig = base_s;
+    if (threadIdx.x == 0) *n_trig = carry;
+}
+
+__global__ void __launch_bounds__(TB) k_trig_write(const uint8_t *__restrict__ flag, int64_t n,
+                                                   const int *__restrict__ base, int64_t *__restrict__ idx,
+                                                   int64_t cap) {
+    __shared__ int wc[TB / 32];
+    const int64_t j = (int64_t)blockIdx.x * TB + threadIdx.x;
+    const int f = j < n ? flag[j] : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wc[wid] = __popc(m);
+    __syncthreads();
+    int before = 0;
+    for (int i = 0; i < wid; ++i) before += wc[i];
+    if (f) {
+        const int64_t pos = (int64_t)base[blockIdx.x] + before + __popc(m & ((1u << lane) - 1u));
+        if (pos < cap) idx[pos] = j;
+    }
 }
 
 }  // namespace
@@ -71,9 +122,43 @@ int launch_integrate(afg_ctx *ctx, const float *logits, int64_t n_win, int n_int
         k_integrate<<<(unsigned)((n_out + 255) / 256), 256, 0, st>>>(logits, n_out, n_int, stat);
     }
     AFG_LAUNCH_CHECK(ctx, "k_integrate");
+    if (n_out <= 0) {
+        AFG_CUDA(ctx, cudaMemsetAsync(n_trig, 0, sizeof(int64_t), st));
+        return AFG_OK;
+    }
+    const int h = cluster_half;
+    int k = 0;
+    while (h > 0 && ((int64_t)2 << k) <= h) ++k;  // 2^k <= h < 2^(k+1)
+    const int64_t w = h > 0 ? ((int64_t)1 << k) : 0;
+    const int64_t N = n_out + 2 * (int64_t)h;
+    const int nb = (int)((n_out + TB - 1) / TB);
+    void *pa = nullptr, *pb = nullptr, *pf = nullptr, *pc = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_TRIG_A, (size_t)N * sizeof(float), &pa);
+    if (!rc && h > 0) rc = afg_ws_reserve(ctx, WS_TRIG_B, (size_t)N * sizeof(float), &pb);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_TRIG_FLAG, (size_t)n_out, &pf);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_TRIG_COUNT, (size_t)nb * sizeof(int), &pc);
+    if (rc) return rc;
+    float *A = static_cast<float *>(pa), *B = static_cast<float *>(pb);
+    const unsigned g = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 32);
     {
-        KScope ks(ctx, st, KK_TRIGGERS, 0.0, (double)n_out * 4.0);
-        k_triggers<<<1, TT, 0, st>>>(stat, n_out, cluster_half, trig_idx, trig_cap, n_trig);
+        KScope ks(ctx, st, KK_TRIGGERS, 0.0, (double)n_out * 4.0 * (3 + 2 * k));
+        const float *M = stat;
+        if (h > 0) {
+            k_trig_pad<<<g, 256, 0, st>>>(stat, n_out, h, A);
+            int64_t len = N;
+            for (int l = 1; l <= k; ++l) {  // M_l[i] = max(M_{l-1}[i], M_{l-1}[i + 2^(l-1)])
+                const int64_t step = (int64_t)1 << (l - 1);
+                len -= step;
+                k_trig_double<<<g, 256, 0, st>>>(A, len, step, B);
+                std::swap(A, B);
+            }
+            M = A;
+        }
+        uint8_t *flag = static_cast<uint8_t *>(pf);
+        int *counts = static_cast<int *>(pc);
+        k_trig_flag<<<nb, TB, 0, st>>>(stat, M, n_out, h, w, flag, counts);
+        k_trig_scan<<<1, 1024, 0, st>>>(counts, nb, n_trig);
+        k_trig_write<<<nb, TB, 0, st>>>(flag, n_out, counts, trig_idx, trig_cap);
     }
     AFG_LAUNCH_CHECK(ctx, "k_triggers");
     return AFG_OK;

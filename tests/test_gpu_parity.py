@@ -117,6 +117,25 @@ def test_integrate_and_triggers_bit_exact(ctx_tiny):
     assert np.array_equal(trig.cpu().numpy()[:n], want)
 
 
+@pytest.mark.parametrize("half", [0, 1, 2, 7, 64, 1000, 2048, 8192])
+def test_triggers_any_half_width(ctx_tiny, half):
+    """Clustering at every half-width the inference rates need (8 s at 1..2048 Hz), on a
+    smooth series with plateaus and exact ties (n_int = 1 passes the series through
+    unchanged): triggers must equal the oracle's, index for index."""
+    rng = np.random.default_rng(half + 11)
+    n = 60_000
+    z = np.cumsum(rng.standard_normal(n))
+    z = np.convolve(z, np.ones(50) / 50, mode="same")
+    z = np.round(z, 1).astype(np.float32)  # plateaus and ties
+    stat, trig, n_trig = ctx_tiny.integrate(_dev(z), 1, half, trig_cap=n)
+    s = stat.cpu().numpy()
+    assert np.array_equal(s, z)
+    want = orc.triggers(s.astype(np.float64), half)
+    n_got = int(n_trig.item())
+    assert n_got == len(want)
+    assert np.array_equal(trig.cpu().numpy()[:n_got], want)
+
+
 def test_triggers_ties_and_capacity(ctx_tiny):
     z = np.zeros(40, dtype=np.float32)
     z[10:14] = 1.0  # plateau after integration with n_int = 1
