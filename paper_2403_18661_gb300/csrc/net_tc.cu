@@ -34,6 +34,7 @@ constexpr int TF_THREADS = 512;
 constexpr int TF_WARPS = TF_THREADS / 32;
 constexpr int TF_C = 16;                   // channels of the fused network
 constexpr int TF_WIMG = 3 * 2 * TF_C * 16;  // bytes of one conv's weight image (3 taps x 512 B)
+constexpr int TF_GROUPS = 3;                // MMA commit groups per conv (8 M subtiles each at W = 3072)
 
 struct TinyArgs {
     const float *y;
@@ -73,6 +74,26 @@ __host__ __device__ inline Smem tiny_smem(int W, int n_conv, int k_stem) {
 }
 
 
+// Sum NV per-lane values over the warp (NV a power of two <= 32) so that lane l ends with
+// the warp total of value l / (32 / NV) in v[0]: each butterfly stage keeps the half of the
+// values selected by the lane's bit and adds the partner's copy (NV - 1 shuffles in all,
+// instead of 5 per value), then plain butterflies finish the lanes that share a value.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[NV], int lane) {
+#pragma unroll
+    for (int off = 16, h = NV / 2; h >= 1; off >>= 1, h >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+#pragma unroll
+    for (int off = 16 / NV; off >= 1; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+}
+
 // Reduce per-thread group sums (s[g], q[g], g < G) over the block and write the
 // per-channel affine map of GroupNorm: scale[c] = rstd_g * gamma_c,
 // shift[c] = beta_c - mean_g * scale[c].  cnt = elements per group.
@@ -81,22 +102,15 @@ __device__ __forceinline__ void gn_reduce(float (&s)[TF_C], float (&q)[TF_C], fl
                                           const float *gamma, const float *beta, float *red, float *scale,
                                           float *shift) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NV = 2 * G;  // sums then sums of squares
+    float v[NV];
 #pragma unroll
-    for (int g = 0; g < TF_C; ++g) {
-        if (g < G) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s[g] += __shfl_xor_sync(0xffffffffu, s[g], o);
-                q[g] += __shfl_xor_sync(0xffffffffu, q[g], o);
-            }
-        }
+    for (int g = 0; g < G; ++g) {
+        v[g] = s[g];
+        v[G + g] = q[g];
     }
-    if (lane == 0) {
-        for (int g = 0; g < G; ++g) {
-            red[warp * 2 * TF_C + g] = s[g];
-            red[warp * 2 * TF_C + TF_C + g] = q[g];
-        }
-    }
+    warp_reduce_scatter<NV>(v, lane);
+    if ((lane & (32 / NV - 1)) == 0) red[warp * 2 * TF_C + lane / (32 / NV)] = v[0];  // [warp][s(G) q(G)]
     __syncthreads();
     if (threadIdx.x < TF_C) {
         const int c = threadIdx.x;
@@ -105,7 +119,7 @@ __device__ __forceinline__ void gn_reduce(float (&s)[TF_C], float (&q)[TF_C], fl
         float ts = 0.f, tq = 0.f;
         for (int w = 0; w < TF_WARPS; ++w) {
             ts += red[w * 2 * TF_C + g];
-            tq += red[w * 2 * TF_C + TF_C + g];
+            tq += red[w * 2 * TF_C + G + g];
         }
         const float mean = ts / cnt;
         const float var = fmaxf(tq / cnt - mean * mean, 0.f);
@@ -129,6 +143,80 @@ __device__ __forceinline__ void tiny_issue(uint32_t tmem, uint64_t ad00, uint64_
                          r > 0 ? 1u : 0u);
 }
 
+// Where window `win` lives: single series, (segment, timeslide, window) in batch mode, or an
+// explicit pointer pair in list mode.  start + t < n_y and l1_shift < n_y, so one conditional
+// subtraction wraps the shifted L1 index.
+struct WinLoc {
+    const float *y0, *y1;
+    float *out_ptr;
+    int64_t n_y, start, l1_shift, out;
+};
+
+__device__ __forceinline__ WinLoc locate_window(const TinyArgs &args, int64_t win) {
+    WinLoc w;
+    w.y0 = args.y;
+    w.y1 = nullptr;
+    w.out_ptr = nullptr;
+    w.n_y = args.n_y;
+    w.start = args.first + win * args.stride;
+    w.l1_shift = args.shift;
+    w.out = win;
+    if (win >= args.n_win) return w;
+    if (args.wins) {
+        const WinPtr wp = args.wins[win];
+        w.y0 = wp.y0;
+        w.y1 = wp.y1;
+        w.out_ptr = wp.out;
+        w.start = 0;
+        w.l1_shift = 0;
+        w.n_y = INT64_MAX / 4;
+    } else if (args.n_seg > 0) {
+        int lo = 0, hi = args.n_seg - 1;  // last segment with win_first <= win
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (args.segs[mid].win_first <= win) lo = mid;
+            else hi = mid - 1;
+        }
+        const SegDesc sd = args.segs[lo];
+        const int64_t local = win - sd.win_first;
+        const int64_t k = local / sd.n_win;  // timeslide index (0-based)
+        const int64_t j = local - k * sd.n_win;
+        w.y0 = args.y + sd.y_off;
+        w.n_y = sd.n_y;
+        w.start = j * args.stride;
+        w.l1_shift = ((sd.shift_first + k) * args.shift_step) % w.n_y;
+    }
+    if (!w.y1) w.y1 = w.y0 + args.y_stride;
+    return w;
+}
+
+// Stage the window (both detectors, zero padding) into xs [2][W + 2 pad]: plain loads, or
+// 4-byte cp.async copies (zero-filled at the padding) that the caller waits for.
+__device__ __forceinline__ void load_window(const TinyArgs &args, const WinLoc &w, float *xs, int W, int pad,
+                                            bool async) {
+    const int Wp = W + 2 * pad;
+    for (int p = threadIdx.x; p < Wp; p += TF_THREADS) {
+        const int tt = p - pad;
+        const bool in = tt >= 0 && tt < W;
+        const float *a = w.y0 + (in ? w.start + tt : 0);
+        int64_t i1 = w.start + w.l1_shift + (in ? tt : 0);
+        if (i1 >= w.n_y) i1 -= w.n_y;
+        const float *b = w.y1 + i1;
+        if (async) {
+            const uint32_t n = in ? 4u : 0u;  // 0: zero fill, nothing read
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(xs + p)), "l"(a), "r"(n)
+                         : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(xs + Wp + p)), "l"(b),
+                         "r"(n)
+                         : "memory");
+        } else {
+            xs[p] = in ? *a : 0.f;
+            xs[Wp + p] = in ? *b : 0.f;
+        }
+    }
+    if (async) asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <int G>
 __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs args) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -141,9 +229,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     float *scale = reinterpret_cast<float *>(sm + L.off_s);
     float *shift = scale + TF_C;
     float *red = reinterpret_cast<float *>(sm + L.off_r);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.off_misc);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + L.off_misc + 8);
-    int *abort_flag = reinterpret_cast<int *>(sm + L.off_misc + 12);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.off_misc);  // [TF_GROUPS]: MMA groups of a conv
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + L.off_misc + 8 * TF_GROUPS);
+    int *abort_flag = reinterpret_cast<int *>(sm + L.off_misc + 8 * TF_GROUPS + 4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t act_chunk = (size_t)(W + 2) * 16;  // bytes of one 8-channel chunk
     const int MT = W / 128;
@@ -159,7 +247,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         *reinterpret_cast<uint4 *>(buf + c * act_chunk + (size_t)row * 16) = make_uint4(0, 0, 0, 0);
     }
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        for (int g = 0; g < TF_GROUPS; ++g) tc::mbar_init(&bar[g], 1);
         tc::fence_mbar_init();
         *abort_flag = 0;
     }
@@ -185,52 +273,16 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     float *xs = reinterpret_cast<float *>(actB + 16);
     const int Wp = W + 2 * pad;
 
+    WinLoc cur = locate_window(args, blockIdx.x);
+    bool prefetched = false;  // the window's samples were copied asynchronously during the previous one
     for (int64_t win = blockIdx.x; win < args.n_win; win += gridDim.x) {
-        // ---- locate the window: single series, or (segment, timeslide, window) in batch mode
-        const float *y0 = args.y;
-        const float *y1 = nullptr;
-        float *out_ptr = nullptr;
-        int64_t n_y = args.n_y, start = args.first + win * args.stride, l1_shift = args.shift, out = win;
-        if (args.wins) {
-            const WinPtr wp = args.wins[win];
-            y0 = wp.y0;
-            y1 = wp.y1;
-            out_ptr = wp.out;
-            start = 0;
-            l1_shift = 0;
-            n_y = INT64_MAX / 4;
-        } else if (args.n_seg > 0) {
-            int lo = 0, hi = args.n_seg - 1;  // last segment with win_first <= win
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (args.segs[mid].win_first <= win) lo = mid;
-                else hi = mid - 1;
-            }
-            const SegDesc sd = args.segs[lo];
-            const int64_t local = win - sd.win_first;
-            const int64_t k = local / sd.n_win;  // timeslide index (0-based)
-            const int64_t j = local - k * sd.n_win;
-            y0 = args.y + sd.y_off;
-            n_y = sd.n_y;
-            start = j * args.stride;
-            l1_shift = ((sd.shift_first + k) * args.shift_step) % n_y;
-            out = win;
-        }
-        // start + t < n_y and l1_shift < n_y: one conditional subtraction wraps L1
-        if (!y1) y1 = y0 + args.y_stride;
-        for (int p = tid; p < Wp; p += TF_THREADS) {
-            const int tt = p - pad;
-            float a = 0.f, b = 0.f;
-            if (tt >= 0 && tt < W) {
-                a = y0[start + tt];
-                int64_t i1 = start + l1_shift + tt;
-                if (i1 >= n_y) i1 -= n_y;
-                b = y1[i1];
-            }
-            xs[p] = a;
-            xs[Wp + p] = b;
-        }
+        if (prefetched) asm volatile("cp.async.wait_all;" ::: "memory");
+        else load_window(args, cur, xs, W, pad, false);
         __syncthreads();
+        const int64_t out = cur.out;
+        float *out_ptr = cur.out_ptr;
+        const int64_t win_next = win + gridDim.x;
+        prefetched = false;
         // ---- stem pass 1: GroupNorm statistics of the k = 3 stem from the moments
         // of its six inputs u = (x0[t..t+2], x1[t..t+2]):  sum_t y_c = w_c . S and
         // sum_t y_c^2 = w_c^T M w_c, with S = sum_t u and M = sum_t u u^T
@@ -258,20 +310,17 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     }
                 }
             }
-            // block reduction of the 27 moments (fixed order)
+            // block reduction of the 27 moments (fixed order): warp reduce-scatter, then warps
+            {
+                float v[32];
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
+                for (int i = 0; i < 6; ++i) v[i] = S[i];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) S[i] += __shfl_xor_sync(0xffffffffu, S[i], o);
+                for (int i = 0; i < 21; ++i) v[6 + i] = M[i];
 #pragma unroll
-            for (int i = 0; i < 21; ++i)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) M[i] += __shfl_xor_sync(0xffffffffu, M[i], o);
-            if (lane == 0) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) red[warp * 32 + i] = S[i];
-#pragma unroll
-                for (int i = 0; i < 21; ++i) red[warp * 32 + 6 + i] = M[i];
+                for (int i = 27; i < 32; ++i) v[i] = 0.f;
+                warp_reduce_scatter<32>(v, lane);  // lane i holds the warp's moment i
+                if (lane < 27) red[warp * 32 + lane] = v[0];
             }
             __syncthreads();
             if (tid < 27) {
@@ -363,61 +412,78 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             unsigned char *src = second ? actB : actA;
             unsigned char *dst = second ? actA : actB;
             const bool last = l == n_conv - 1;
-            // ---- issue the conv as MT x 3 MMAs
+            // ---- issue the conv as MT x 3 MMAs in TF_GROUPS commit groups of M subtiles, so that
+            // the statistics of a group are read while the later groups still run
+            const int GS = (MT + TF_GROUPS - 1) / TF_GROUPS;
             if (tid == 0) {
                 tc::fence_after_sync();
                 const uint64_t ad00 = tc::desc_kmajor_noswizzle(tc::smem_addr(src), (uint32_t)act_chunk, 128);
                 const uint64_t bd00 = tc::desc_kmajor_noswizzle(tc::smem_addr(wimg + (size_t)l * TF_WIMG), 256, 128);
-                if (MT == 24) {
-                    tiny_issue<24>(tmem, ad00, bd00, idesc);  // 1.5 s windows at 2048 Hz
-                } else {
-                    for (int j = 0; j < MT; ++j)
-                        for (int r = 0; r < 3; ++r)
-                            tc::mma_bf16(tmem + (uint32_t)(j * TF_C), ad00 + (uint64_t)(128 * j + r), bd00 + (uint64_t)(32 * r),
-                                         idesc, r > 0 ? 1u : 0u);
+                for (int g = 0; g < TF_GROUPS; ++g) {
+                    const int j_lo = g * GS, j_hi = min(MT, j_lo + GS);
+                    if (MT == 24) {
+                        tiny_issue<8>(tmem + (uint32_t)(j_lo * TF_C), ad00 + (uint64_t)(128 * j_lo), bd00,
+                                      idesc);  // 1.5 s windows at 2048 Hz
+                    } else {
+                        for (int j = j_lo; j < j_hi; ++j)
+                            for (int r = 0; r < 3; ++r)
+                                tc::mma_bf16(tmem + (uint32_t)(j * TF_C), ad00 + (uint64_t)(128 * j + r),
+                                             bd00 + (uint64_t)(32 * r), idesc, r > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(&bar[g]);
                 }
-                tc::mma_commit(bar);
             }
-            const bool ok = tc::mbar_wait(bar, phase & 1, 1000000000ull);
-            phase++;
-            if (!ok) {
-                atomicExch(args.err, 1);
-                *abort_flag = 1;
-            }
-            __syncthreads();
-            if (*abort_flag) {
-                aborted = true;
-                break;
-            }
-            tc::fence_after_sync();
             const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-            // ---- epilogue pass 1: GroupNorm statistics
+            // ---- epilogue pass 1: GroupNorm statistics, group by group as the MMAs complete
             {
                 float s[TF_C], q[TF_C];
 #pragma unroll
                 for (int g = 0; g < TF_C; ++g) s[g] = q[g] = 0.f;
-                for (int j0 = warp >> 2; j0 < MT; j0 += 2 * (TF_WARPS / 4)) {
-                    const int j1 = j0 + TF_WARPS / 4;
-                    uint32_t r0[16], r1[16];
-                    tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
-                    if (j1 < MT) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
-                    tc::tmem_wait_ld();
-#pragma unroll
-                    for (int c = 0; c < TF_C; ++c) {
-                        const int g = c / (TF_C / G);
-                        const float v = __uint_as_float(r0[c]);
-                        s[g] += v;
-                        q[g] = fmaf(v, v, q[g]);
-                    }
-                    if (j1 < MT) {
+                bool ok = true;
+                for (int grp = 0; grp < TF_GROUPS; ++grp) {
+                    if (!tc::mbar_wait(&bar[grp], phase & 1, 1000000000ull)) ok = false;
+                    tc::fence_after_sync();
+                    const int j_lo = grp * GS, j_hi = min(MT, j_lo + GS);
+                    for (int j0 = j_lo + (warp >> 2); j0 < j_hi; j0 += 2 * (TF_WARPS / 4)) {
+                        const int j1 = j0 + TF_WARPS / 4;
+                        uint32_t r0[16], r1[16];
+                        tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
+                        if (j1 < j_hi) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
+                        tc::tmem_wait_ld();
 #pragma unroll
                         for (int c = 0; c < TF_C; ++c) {
                             const int g = c / (TF_C / G);
-                            const float v = __uint_as_float(r1[c]);
+                            const float v = __uint_as_float(r0[c]);
                             s[g] += v;
                             q[g] = fmaf(v, v, q[g]);
                         }
+                        if (j1 < j_hi) {
+#pragma unroll
+                            for (int c = 0; c < TF_C; ++c) {
+                                const int g = c / (TF_C / G);
+                                const float v = __uint_as_float(r1[c]);
+                                s[g] += v;
+                                q[g] = fmaf(v, v, q[g]);
+                            }
+                        }
                     }
+                }
+                phase++;
+                if (!ok) {
+                    atomicExch(args.err, 1);
+                    *abort_flag = 1;
+                }
+                __syncthreads();
+                if (*abort_flag) {
+                    aborted = true;
+                    break;
+                }
+                if (last && win_next < args.n_win) {
+                    // buffer B (the staging of the raw window) is free once the last conv's MMAs
+                    // have read it: copy the next window's samples meanwhile
+                    cur = locate_window(args, win_next);
+                    load_window(args, cur, xs, W, pad, true);
+                    prefetched = true;
                 }
                 const float *gb = conv_gb + l * 2 * TF_C;
                 gn_reduce<G>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift);
@@ -484,27 +550,27 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         }
         if (aborted) break;
         // ---- head: global mean pool of the last block's output, then linear
-#pragma unroll
-        for (int c = 0; c < TF_C; ++c) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) hs[c] += __shfl_xor_sync(0xffffffffu, hs[c], o);
-        }
-        if (lane == 0)
-            for (int c = 0; c < TF_C; ++c) red[warp * 2 * TF_C + c] = hs[c];
+        warp_reduce_scatter<TF_C>(hs, lane);  // lane 2c holds the warp's sum of channel c
+        if (!(lane & 1)) red[warp * 2 * TF_C + (lane >> 1)] = hs[0];
         __syncthreads();
-        if (tid == 0) {
-            float z = fc_b;
-            for (int c = 0; c < TF_C; ++c) {
-                float tot = 0.f;
-                for (int w = 0; w < TF_WARPS; ++w) tot += red[w * 2 * TF_C + c];
-                z += fc_w[c] * (tot / (float)W);
+        if (tid < 32) {
+            float part = 0.f;  // lanes 0..15: channel lane over all warps, times its weight
+            if (lane < TF_C) {
+                for (int w = 0; w < TF_WARPS; ++w) part += red[w * 2 * TF_C + lane];
+                part = fc_w[lane] * (part / (float)W);
             }
-            if (out_ptr) *out_ptr = z;
-            else args.logits[out] = z;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) {
+                const float z = fc_b + part;
+                if (out_ptr) *out_ptr = z;
+                else args.logits[out] = z;
+            }
         }
         __syncthreads();
     }
-    // ---- teardown
+    // ---- teardown (a prefetch may still be in flight after an abort)
+    asm volatile("cp.async.wait_all;" ::: "memory");
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
