@@ -4,9 +4,10 @@
 // candidate).
 //
 //   k_integrate   stat[j] = (1/n_int) sum_{i<n_int} z[j+i], summed in index order
-//   triggers      the cluster maxima (earliest index wins ties) from windowed
-//                 maxima built by doubling, O(n log h), compacted in increasing
-//                 index order across blocks (counts, one scan, writes).
+//   triggers      the cluster maxima (earliest index wins ties): short series by a
+//                 direct scan in one CTA; long ones from windowed maxima built by
+//                 doubling, O(n log h), compacted in increasing index order across
+//                 blocks (counts, one scan, writes).
 #include <math.h>
 
 #include <algorithm>
@@ -21,6 +22,51 @@ __global__ void k_integrate(const float *__restrict__ z, int64_t n_out, int n_in
     float s = 0.f;
     for (int i = 0; i < n_int; ++i) s += z[j + i];
     stat[j] = s / (float)n_int;
+}
+
+// Short series: one CTA scans each index's neighbourhood directly (early exit on the first
+// larger neighbour) and compacts in index order over 1024-index chunks.
+constexpr int TT = 1024;
+
+__global__ void __launch_bounds__(TT) k_triggers_small(const float *__restrict__ I, int64_t n, int half,
+                                                       int64_t *__restrict__ idx, int64_t cap,
+                                                       int64_t *__restrict__ n_trig) {
+    __shared__ int warp_tot[TT / 32];
+    __shared__ int64_t base_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < n; c0 += TT) {
+        const int64_t j = c0 + tid;
+        int flag = 0;
+        if (j < n) {
+            const float v = I[j];
+            flag = 1;
+            const int64_t lo = j - half < 0 ? 0 : j - half;
+            const int64_t hi = j + half >= n ? n - 1 : j + half;
+            for (int64_t i = lo; i < j && flag; ++i) flag = v > I[i];
+            for (int64_t i = j + 1; i <= hi && flag; ++i) flag = v >= I[i];
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        const int in_warp = __popc(m & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[wid] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < TT / 32; ++w) {
+            const int t = warp_tot[w];
+            if (w < wid) before += t;
+            total += t;
+        }
+        const int64_t base = base_s;
+        if (flag) {
+            const int64_t pos = base + before + in_warp;
+            if (pos < cap) idx[pos] = j;
+        }
+        __syncthreads();
+        if (tid == 0) base_s = base + total;
+        __syncthreads();
+    }
+    if (tid == 0) *n_trig = base_s;
 }
 
 // ---- clustering: j is a trigger iff I[j] > max I[j-h .. j-1] and I[j] >= max I[j+1 .. j+h]
@@ -127,6 +173,12 @@ int launch_integrate(afg_ctx *ctx, const float *logits, int64_t n_win, int n_int
         return AFG_OK;
     }
     const int h = cluster_half;
+    if (n_out <= 16384 && h <= 256) {  // short series: the direct scan needs one launch
+        KScope ks(ctx, st, KK_TRIGGERS, 0.0, (double)n_out * 4.0);
+        k_triggers_small<<<1, TT, 0, st>>>(stat, n_out, h, trig_idx, trig_cap, n_trig);
+        AFG_LAUNCH_CHECK(ctx, "k_triggers_small");
+        return AFG_OK;
+    }
     int k = 0;
     while (h > 0 && ((int64_t)2 << k) <= h) ++k;  // 2^k <= h < 2^(k+1)
     const int64_t w = h > 0 ? ((int64_t)1 << k) : 0;

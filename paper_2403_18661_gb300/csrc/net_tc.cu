@@ -190,28 +190,52 @@ __device__ __forceinline__ WinLoc locate_window(const TinyArgs &args, int64_t wi
     return w;
 }
 
-// Stage the window (both detectors, zero padding) into xs [2][W + 2 pad]: plain loads, or
-// 4-byte cp.async copies (zero-filled at the padding) that the caller waits for.
+// Stage the window into xs: detector d's sample s at xs[d * (W + 8) + 4 + s] (16-byte
+// aligned), zero pads just before and after each row.  Plain loads, or cp.async copies that
+// the caller waits for: 16 bytes at a time where both rows are 16-byte aligned and the
+// circular L1 index cannot wrap inside 4 samples, else 4 bytes.
 __device__ __forceinline__ void load_window(const TinyArgs &args, const WinLoc &w, float *xs, int W, int pad,
                                             bool async) {
-    const int Wp = W + 2 * pad;
-    for (int p = threadIdx.x; p < Wp; p += TF_THREADS) {
-        const int tt = p - pad;
-        const bool in = tt >= 0 && tt < W;
-        const float *a = w.y0 + (in ? w.start + tt : 0);
-        int64_t i1 = w.start + w.l1_shift + (in ? tt : 0);
-        if (i1 >= w.n_y) i1 -= w.n_y;
-        const float *b = w.y1 + i1;
-        if (async) {
-            const uint32_t n = in ? 4u : 0u;  // 0: zero fill, nothing read
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(xs + p)), "l"(a), "r"(n)
+    const int RP = W + 8;
+    if (threadIdx.x < 4 * pad) {  // zero pads (pad <= 3) of both rows
+        const int d = threadIdx.x & 1, i = threadIdx.x >> 1;  // i < pad: left; i >= pad: right
+        const int s = i < pad ? -1 - i : W + (i - pad);
+        if (s < W + pad) xs[d * RP + 4 + s] = 0.f;
+    }
+    const bool vec = async && ((w.start | w.l1_shift | w.n_y) & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(w.y0 + w.start) | reinterpret_cast<uintptr_t>(w.y1)) & 15) == 0;
+    if (vec) {
+        for (int c = threadIdx.x; c < 2 * (W / 4); c += TF_THREADS) {
+            const int d = c >= W / 4, s = 4 * (c - d * (W / 4));
+            const float *src;
+            if (d == 0) {
+                src = w.y0 + w.start + s;
+            } else {
+                int64_t i1 = w.start + w.l1_shift + s;
+                if (i1 >= w.n_y) i1 -= w.n_y;
+                src = w.y1 + i1;
+            }
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_addr(xs + d * RP + 4 + s)),
+                         "l"(src)
                          : "memory");
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(xs + Wp + p)), "l"(b),
-                         "r"(n)
-                         : "memory");
-        } else {
-            xs[p] = in ? *a : 0.f;
-            xs[Wp + p] = in ? *b : 0.f;
+        }
+    } else {
+        for (int c = threadIdx.x; c < 2 * W; c += TF_THREADS) {
+            const int d = c >= W, s = c - d * W;
+            const float *src;
+            if (d == 0) {
+                src = w.y0 + w.start + s;
+            } else {
+                int64_t i1 = w.start + w.l1_shift + s;
+                if (i1 >= w.n_y) i1 -= w.n_y;
+                src = w.y1 + i1;
+            }
+            if (async)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_addr(xs + d * RP + 4 + s)),
+                             "l"(src)
+                             : "memory");
+            else
+                xs[d * RP + 4 + s] = *src;
         }
     }
     if (async) asm volatile("cp.async.commit_group;" ::: "memory");
@@ -269,9 +293,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     const float cnt = (float)W * (float)(TF_C / G);
     uint32_t phase = 0;
 
-    // staging for the raw window (2 x (W + 2 pad) floats) inside buffer B, past its first pad row
+    // staging for the raw window (2 rows of W + 8 floats) inside buffer B, past its first pad row
     float *xs = reinterpret_cast<float *>(actB + 16);
-    const int Wp = W + 2 * pad;
+    const float *xs0 = xs + 4 - pad, *xs1 = xs + (W + 8) + 4 - pad;  // padded index p of each detector row
 
     WinLoc cur = locate_window(args, blockIdx.x);
     bool prefetched = false;  // the window's samples were copied asynchronously during the previous one
@@ -292,12 +316,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             for (int i = 0; i < 6; ++i) S[i] = 0.f;
 #pragma unroll
             for (int i = 0; i < 21; ++i) M[i] = 0.f;
+#pragma unroll 2
             for (int t = tid; t < W; t += TF_THREADS) {
                 float u[6];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    u[r] = xs[t + r];
-                    u[3 + r] = xs[Wp + t + r];
+                    u[r] = xs0[t + r];
+                    u[3 + r] = xs1[t + r];
                 }
                 int m = 0;
 #pragma unroll
@@ -376,12 +401,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 sh8[c] = shift[h * 8 + c];
             }
             unsigned char *dstc = actA + h * act_chunk;
+#pragma unroll 2
             for (int t = tid >> 1; t < W; t += TF_THREADS / 2) {
                 float u[6];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    u[r] = xs[t + r];
-                    u[3 + r] = xs[Wp + t + r];
+                    u[r] = xs0[t + r];
+                    u[3 + r] = xs1[t + r];
                 }
                 uint32_t pk[4];
 #pragma unroll
