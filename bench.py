@@ -600,7 +600,8 @@ def run_serving(args):
         r = ctx.stream_poll(sid)
         lat.append(r["t_done"] - r["t_push"])
     lat = np.concatenate(lat) * 1000.0
-    # phase 3: maximum offered load
+    # phase 3: maximum offered load (the engine is idle here: counters start clean)
+    ctx.profile_enable(True)
     stats0 = ctx.stream_stats()
     t1 = time.perf_counter()
     n_thr = int(thr_s * wl.fs)
@@ -613,9 +614,14 @@ def run_serving(args):
     wall = time.perf_counter() - t1
     clocks = sampler.stop()
     stats1 = ctx.stream_stats()
+    ctx.profile_enable(False)
+    kstats = ctx.profile_read()
     for sid in sids:
         ctx.stream_poll(sid)
     value = pushed_samples / wl.fs / wall
+    n_steps = max(1, int(stats1["steps"] - stats0["steps"]))
+    n_results = int(stats1["windows"] - stats0["windows"])
+    dom = max(kstats, key=lambda k: k["total_ms"]) if kstats else None
     out = {"metric": "strain-seconds/s whiten+ResNet (serving, continuous batching)", "value": value,
            "unit": "strain-s/s", "n_gpus": 1, "steps": int(stats1["steps"] - stats0["steps"]), "warmup": 0,
            "ms_per_step": 1000.0 * wall / max(1, stats1["steps"] - stats0["steps"]), "higher_is_better": True,
@@ -625,9 +631,15 @@ def run_serving(args):
                       "throughput_seconds_per_stream": thr_s},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                           "p99": float(np.percentile(lat, 99)), "results": int(lat.size)},
-           "windows_per_s": (stats1["windows"] - stats0["windows"]) / wall, "clocks": clocks,
-           "e2e": {"value": value, "unit": "strain-s/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
-                   "note": "wall time from the first host push to the last result on the host"}}
+           "windows_per_s": n_results / wall, "clocks": clocks,
+           "roofline": roofline_for(dom, load_peaks(), sum(k["total_ms"] for k in kstats)) if dom else None,
+           "gpu_launches": int(sum(k["launches"] for k in kstats)),
+           "kernels": {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3)} for k in kstats},
+           "e2e": {"value": value, "unit": "strain-s/s",
+                   "h2d_bytes_per_step": int(pushed_samples * 2 * 4 / n_steps),
+                   "d2h_bytes_per_step": int(n_results * 32 / n_steps),
+                   "note": "wall time from the first host push to the last result on the host (pinned staging "
+                           "copies in, 32-byte results out)"}}
     print(json.dumps(out), flush=True)
     ctx.close()
     return 0

@@ -175,6 +175,7 @@ enum {
     WS_TRIG_B,
     WS_TRIG_FLAG,
     WS_TRIG_COUNT,
+    WS_FB_SCRATCH,
 };
 
 struct KScope {

@@ -2,7 +2,8 @@
 // filter-build and whitening kernels.
 //
 // Complex FFT of NC = 8192 points as a Stockham auto-sort sequence of
-// radix-8 passes (8*8*8*8) plus one radix-2 pass.  Each pass reads R points
+// radix-8 passes (8*8*8*8) plus one radix-2 pass (and of 2048 points:
+// 8*8*8*4).  Each pass reads R points
 // at stride NC/R into registers, applies the twiddles, does an in-register
 // DFT of size R and writes the R results at stride Ns; in place, with a
 // barrier between the reads and the writes.  Twiddles come from a table
@@ -68,10 +69,10 @@ template <typename C, int SIGN> __device__ __forceinline__ void dft8(C *v) {
     v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
-// One Stockham pass of radix R over NC points held in shared memory `d`.
-template <typename C, int R, int SIGN, int NT>
+// One Stockham pass of radix R over LEN points held in shared memory `d`.
+template <typename C, int R, int SIGN, int NT, int LEN = NC>
 __device__ __forceinline__ void stockham_pass(C *d, int Ns, const C *tw) {
-    constexpr int NB = NC / R;          // butterflies in the pass
+    constexpr int NB = LEN / R;         // butterflies in the pass
     constexpr int BPT = (NB + NT - 1) / NT;
     C v[BPT][R];
     const int tid = threadIdx.x;
@@ -116,6 +117,16 @@ __device__ __forceinline__ void fft_nc(C *d, const C *tw) {
     stockham_pass<C, 8, SIGN, NT>(d, 64, tw);
     stockham_pass<C, 8, SIGN, NT>(d, 512, tw);
     stockham_pass<C, 2, SIGN, NT>(d, 4096, tw);
+}
+
+// Complex FFT of 2048 points in shared memory (radix 8, 8, 8, 4), natural order in and
+// out, unnormalised, twiddles from the same NFFT table.  Caller syncs before.
+template <typename C, int SIGN, int NT>
+__device__ __forceinline__ void fft_2048(C *d, const C *tw) {
+    stockham_pass<C, 8, SIGN, NT, 2048>(d, 1, tw);
+    stockham_pass<C, 8, SIGN, NT, 2048>(d, 8, tw);
+    stockham_pass<C, 8, SIGN, NT, 2048>(d, 64, tw);
+    stockham_pass<C, 4, SIGN, NT, 2048>(d, 512, tw);
 }
 
 // Real-FFT split after a forward complex FFT of z_j = x_{2j} + i x_{2j+1}:

@@ -119,6 +119,82 @@ __global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict_
     for (int k = threadIdx.x; k < NBIN; k += NT64) out[k] = (float)(d[k].x / (double)NC);
 }
 
+// ---- filter build spread over many CTAs (fir_len <= 2048).  With the 16384-point grid
+// N, P = 8 and L = N / P = 2048:
+//   inverse:  h_m = (1/N) sum_r e^{+2 pi i r m / N} Z_r[m mod L],
+//             Z_r = sum_j A_{P j + r} e^{+2 pi i j n / L}      (8 inverse FFTs of L points)
+//   taper:    g_m = sqrt(2/fs) taper(m) h_m,  m in [-L/2, L/2) (the F taps lie inside)
+//   forward:  G_{P j + r} = sum_n y_r[n] e^{-2 pi i j n / L},
+//             y_r[m mod L] = g_m e^{-2 pi i r m / N}         (8 forward FFTs of L points;
+//             the support of g is shorter than L, so the fold does not alias)
+// The same FP64 arithmetic as k_filter_build, on 2 P CTAs per filter instead of one.
+constexpr int FB_L = 2048;
+constexpr int FB_P = NFFT / FB_L;
+constexpr int FB_T = 256;
+
+// grid (FB_P, n_filters): Z_r of filter f = det * n_psd + e
+__global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ psd, double fs, double f_hp,
+                                                     const double2 *__restrict__ tw, double2 *__restrict__ Z) {
+    __shared__ double2 d[FB_L];
+    const int r = blockIdx.x;
+    const int64_t f = blockIdx.y;
+    const double *p = psd + f * NBIN;
+    for (int j = threadIdx.x; j < FB_L; j += FB_T) {
+        const int k = FB_P * j + r;
+        const int kk = k <= NFFT / 2 ? k : NFFT - k;  // the amplitude response is even in k
+        const double fr = (double)kk * fs / (double)NFFT;
+        const double pk = p[kk];
+        d[j] = make_double2((fr >= f_hp && pk > 0.0) ? 1.0 / sqrt(pk) : 0.0, 0.0);
+    }
+    __syncthreads();
+    fft_2048<double2, +1, FB_T>(d, tw);
+    double2 *z = Z + (f * FB_P + r) * FB_L;
+    for (int n = threadIdx.x; n < FB_L; n += FB_T) z[n] = d[n];
+}
+
+// grid (FB_L / FB_T, n_filters): one lag m per thread
+__global__ void __launch_bounds__(FB_T) k_fb_taper(const double2 *__restrict__ Z, double fs, int F,
+                                                   const double2 *__restrict__ tw, double2 *__restrict__ Y) {
+    const int64_t f = blockIdx.y;
+    const int m = blockIdx.x * FB_T + threadIdx.x - FB_L / 2;  // lag in [-L/2, L/2)
+    const int slot = m & (FB_L - 1);
+    const double2 *z = Z + f * FB_P * FB_L + slot;
+    double h = 0.0;
+#pragma unroll
+    for (int r = 0; r < FB_P; ++r) {
+        const double2 w = tw[(r * m) & (NFFT - 1)];  // e^{-2 pi i r m / N}; use its conjugate
+        const double2 v = z[(int64_t)r * FB_L];
+        h += w.x * v.x + w.y * v.y;  // Re(conj(w) v)
+    }
+    h /= (double)NFFT;
+    const int half = F / 2;
+    double g = 0.0;
+    if (m >= -half && m < half) g = h * sqrt(2.0 / fs) * (0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F));
+    double2 *y = Y + f * FB_P * FB_L + slot;
+#pragma unroll
+    for (int r = 0; r < FB_P; ++r) {
+        const double2 w = tw[(r * m) & (NFFT - 1)];
+        y[(int64_t)r * FB_L] = make_double2(g * w.x, g * w.y);
+    }
+}
+
+// grid (FB_P, n_filters): gains G_k / NC for k = P j + r <= NFFT / 2
+__global__ void __launch_bounds__(FB_T) k_fb_forward(const double2 *__restrict__ Y, const double2 *__restrict__ tw,
+                                                     float *__restrict__ gains) {
+    __shared__ double2 d[FB_L];
+    const int r = blockIdx.x;
+    const int64_t f = blockIdx.y;
+    const double2 *y = Y + (f * FB_P + r) * FB_L;
+    for (int n = threadIdx.x; n < FB_L; n += FB_T) d[n] = y[n];
+    __syncthreads();
+    fft_2048<double2, -1, FB_T>(d, tw);
+    float *out = gains + f * NBIN;
+    for (int j = threadIdx.x; j < FB_L; j += FB_T) {
+        const int k = FB_P * j + r;
+        if (k <= NFFT / 2) out[k] = (float)(d[j].x / (double)NC);
+    }
+}
+
 // One overlap-save block: the FIR of src[0 .. WB + F - 1) (samples past
 // `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value).
 // d: NC + 1 float2 of shared memory.
@@ -211,6 +287,31 @@ int set_attrs(afg_ctx *ctx) {
 
 }  // namespace
 
+// gains [n_det][n_psd][NBIN] from psd: the many-CTA FP64 build where fir_len <= 2048,
+// else one CTA per filter
+int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st) {
+    const int64_t nf = (int64_t)n_det * n_psd;
+    if (nf <= 0) return AFG_OK;
+    if (ctx->cfg.fir_len <= FB_L && nf <= 65535) {
+        void *scr = nullptr;
+        int rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, (size_t)2 * nf * FB_P * FB_L * sizeof(double2), &scr);
+        if (rc) return rc;
+        double2 *Z = static_cast<double2 *>(scr), *Y = Z + nf * FB_P * FB_L;
+        KScope ks(ctx, st, KK_FILTER, 0.0, (double)nf * NBIN * (8.0 + 4.0));
+        k_fb_inverse<<<dim3(FB_P, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass,
+                                                                ctx->tw64, Z);
+        k_fb_taper<<<dim3(FB_L / FB_T, (unsigned)nf), FB_T, 0, st>>>(Z, (double)ctx->cfg.fs, ctx->cfg.fir_len,
+                                                                     ctx->tw64, Y);
+        k_fb_forward<<<dim3(FB_P, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+    } else {
+        KScope ks(ctx, st, KK_FILTER, 0.0, (double)nf * NBIN * (8.0 + 4.0));
+        k_filter_build<<<dim3((unsigned)n_psd, n_det), NT64, (NC + 1) * sizeof(double2), st>>>(
+            psd, n_psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass, ctx->cfg.fir_len, ctx->tw64, gains);
+    }
+    AFG_LAUNCH_CHECK(ctx, "filter build");
+    return AFG_OK;
+}
+
 int afg_make_twiddles(afg_ctx *ctx) {
     {
         KScope ks(ctx, 0, KK_TWIDDLES, 0.0, (double)NFFT * (sizeof(float2) + sizeof(double2)));
@@ -256,12 +357,8 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
     float *gains = nullptr;
     int rc = afg_ws_reserve(ctx, WS_FILTER, (size_t)n_det * n_psd * NBIN * sizeof(float), (void **)&gains);
     if (rc) return rc;
-    {
-        KScope ks(ctx, st, KK_FILTER, 0.0, (double)n_det * n_psd * NBIN * (8.0 + 4.0));
-        k_filter_build<<<dim3((unsigned)n_psd, n_det), NT64, (NC + 1) * sizeof(double2), st>>>(
-            psd, n_psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass, ctx->cfg.fir_len, ctx->tw64, gains);
-    }
-    AFG_LAUNCH_CHECK(ctx, "k_filter_build");
+    rc = filter_build(ctx, psd, n_det, n_psd, gains, st);
+    if (rc) return rc;
     if (out_len <= 0) return AFG_OK;
     const int64_t nb = (out_len + WB - 1) / WB;
     {
@@ -277,11 +374,7 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
 
 // Filter build only: gains [n_det][n_psd][NBIN] from psd (FP64), on st.
 int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st) {
-    KScope ks(ctx, st, KK_FILTER, 0.0, (double)n_det * n_psd * NBIN * (8.0 + 4.0));
-    k_filter_build<<<dim3((unsigned)n_psd, n_det), NT64, (NC + 1) * sizeof(double2), st>>>(
-        psd, n_psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass, ctx->cfg.fir_len, ctx->tw64, gains);
-    AFG_LAUNCH_CHECK(ctx, "k_filter_build");
-    return AFG_OK;
+    return filter_build(ctx, psd, n_det, n_psd, gains, st);
 }
 
 int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,
