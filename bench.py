@@ -42,6 +42,7 @@ from paper_2403_18661_gb300 import inputs  # noqa: E402
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 N_SM = 152
 FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2  # GB300: 1.25 TFLOP/s FP64 nominal = 152 SMs x 2 FMA/clk x 2 x 2.07 GHz
 
 
 def load_peaks():
@@ -190,6 +191,11 @@ def roofline_for(dom: dict, peaks: dict, step_ms_total: float) -> dict:
         achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
         peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         src = f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x {sm_max:g} MHz"
+    elif name.startswith("filter_build_fp64"):
+        bound, unit = "alu", "TFLOP/s"
+        achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
+        peak = N_SM * FP64_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        src = f"derived: {N_SM} SMs x {FP64_LANES_PER_SM} FP64 FMA lanes x 2 x {sm_max:g} MHz"
     elif "bf16" in name:
         bound, unit = "tensor", "TFLOP/s"
         achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12

@@ -5,7 +5,8 @@
 // The background statistics are sorted in decreasing order on the device by an
 // LSD radix sort of order-preserving 32-bit keys (4 passes of 8 bits, each pass
 // stable: per-tile digit histograms, one exclusive scan over (digit, tile), and a
-// scatter that ranks equal digits in input order).  Each foreground statistic x
+// scatter that ranks equal digits in input order).  Launches are sized by the
+// capacity; only the tiles that hold keys do work.  Each foreground statistic x
 // then gets count = #{background > x} by binary search, and FAR = count / livetime.
 // The background count may live on the device (as afg_batch_run writes it), so
 // every kernel reads n = min(*n_dev, cap) itself and nothing synchronises.
@@ -47,11 +48,17 @@ __global__ void k_far_keys(const float *__restrict__ stat, const int64_t *__rest
         keys[i] = key_of(stat[idx ? idx[i] : i]);
 }
 
-// hist[d * n_tiles + tile] = keys of the tile whose digit (at `shift`) is d
+// tiles that hold keys
+__device__ __forceinline__ int occupied_tiles(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+
+// hist[d * n_eff + tile] = keys of the tile whose digit (at `shift`) is d, over the
+// n_eff = ceil(n / RS_TILE) tiles that hold keys (blocks past them return at once)
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint32_t *__restrict__ keys, const int64_t *n_dev,
-                                                  int64_t cap, int shift, uint32_t *__restrict__ hist, int n_tiles) {
+                                                  int64_t cap, int shift, uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[256];
     const int64_t n = dev_count(n_dev, cap);
+    const int n_eff = occupied_tiles(n);
+    if ((int)blockIdx.x >= n_eff) return;
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -60,30 +67,60 @@ __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint32_t *__restrict__ k
         if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+    hist[(size_t)threadIdx.x * n_eff + blockIdx.x] = h[threadIdx.x];
 }
 
-// in-place exclusive scan of m counts, one block (fixed order: chunks of 1024, then carry)
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ a, int64_t m) {
-    __shared__ uint32_t s[1024];
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t c0 = 0; c0 < m; c0 += 1024) {
-        const int64_t i = c0 + threadIdx.x;
-        const uint32_t v = i < m ? a[i] : 0u;
-        s[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
-            const uint32_t t = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0u;
-            __syncthreads();
-            s[threadIdx.x] += t;
-            __syncthreads();
+// In-place exclusive scan of the 256 n_eff histogram entries (digit-major, so the scan
+// order is (digit, tile)), one block walking chunks of 1024 with a running carry.  Each
+// chunk: a warp scan, the 32 warp totals through shared memory (double-buffered, so one
+// barrier per chunk), and every warp scans those totals itself.  Loads run SCAN_AHEAD
+// chunks ahead of the chunk being scanned.
+constexpr int SCAN_AHEAD = 4;
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ a, const int64_t *n_dev, int64_t cap) {
+    __shared__ uint32_t wsum[2][32];
+    const int64_t n = dev_count(n_dev, cap);
+    const int64_t m = (int64_t)256 * occupied_tiles(n);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t v[SCAN_AHEAD];
+#pragma unroll
+    for (int k = 0; k < SCAN_AHEAD; ++k) {
+        const int64_t i = (int64_t)k * 1024 + t;
+        v[k] = i < m ? a[i] : 0u;
+    }
+    uint32_t carry = 0;
+    int buf = 0;
+    for (int64_t c0 = 0; c0 < m; c0 += 1024 * SCAN_AHEAD) {
+        uint32_t nxt[SCAN_AHEAD];
+#pragma unroll
+        for (int k = 0; k < SCAN_AHEAD; ++k) {
+            const int64_t i = c0 + (int64_t)(SCAN_AHEAD + k) * 1024 + t;
+            nxt[k] = i < m ? a[i] : 0u;
         }
-        if (i < m) a[i] = carry + s[threadIdx.x] - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += s[1023];
-        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SCAN_AHEAD; ++k) {
+            uint32_t x = v[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[buf][warp] = x;
+            __syncthreads();
+            uint32_t w = wsum[buf][lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            const uint32_t before = __shfl_sync(0xffffffffu, w, (warp + 31) & 31);
+            const uint32_t total = __shfl_sync(0xffffffffu, w, 31);
+            const int64_t i = c0 + (int64_t)k * 1024 + t;
+            if (i < m) a[i] = carry + (warp ? before : 0u) + x - v[k];
+            carry += total;
+            buf ^= 1;
+        }
+#pragma unroll
+        for (int k = 0; k < SCAN_AHEAD; ++k) v[k] = nxt[k];
     }
 }
 
@@ -92,12 +129,14 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ a, int6
 // ranked by warp (lower warps first) and by lane (match_any peers with lower lanes).
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint32_t *__restrict__ kin, uint32_t *__restrict__ kout,
                                                      const int64_t *n_dev, int64_t cap, int shift,
-                                                     const uint32_t *__restrict__ hist, int n_tiles) {
+                                                     const uint32_t *__restrict__ hist) {
     __shared__ uint32_t running[256];          // keys of each digit placed by earlier rounds (+ tile base)
     __shared__ uint32_t wcnt[RS_WARPS][257];   // per-warp digit counts of the current round
     const int64_t n = dev_count(n_dev, cap);
+    const int n_eff = occupied_tiles(n);
+    if ((int)blockIdx.x >= n_eff) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    running[t] = hist[(size_t)t * n_tiles + blockIdx.x];
+    running[t] = hist[(size_t)t * n_eff + blockIdx.x];
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
     const uint32_t lt = (1u << lane) - 1u;
     for (int r = 0; r < RS_ROUNDS; ++r) {
@@ -169,9 +208,9 @@ int launch_far(afg_ctx *ctx, const float *bg_stat, const int64_t *bg_idx, const 
         KScope ks(ctx, st, KK_FAR, 0.0, (double)bg_cap * (4.0 + 8.0 + 4.0 * 4 * 4 + 4.0) + n_fg * 20.0);
         k_far_keys<<<g1, 256, 0, st>>>(bg_stat, bg_idx, n_bg_dev, bg_cap, ka);
         for (int pass = 0; pass < 4; ++pass) {
-            k_rs_hist<<<n_tiles, RS_T, 0, st>>>(ka, n_bg_dev, bg_cap, 8 * pass, hist, n_tiles);
-            k_rs_scan<<<1, 1024, 0, st>>>(hist, m);
-            k_rs_scatter<<<n_tiles, RS_T, 0, st>>>(ka, kb, n_bg_dev, bg_cap, 8 * pass, hist, n_tiles);
+            k_rs_hist<<<n_tiles, RS_T, 0, st>>>(ka, n_bg_dev, bg_cap, 8 * pass, hist);
+            k_rs_scan<<<1, 1024, 0, st>>>(hist, n_bg_dev, bg_cap);
+            k_rs_scatter<<<n_tiles, RS_T, 0, st>>>(ka, kb, n_bg_dev, bg_cap, 8 * pass, hist);
             std::swap(ka, kb);
         }
         k_far_values<<<g1, 256, 0, st>>>(ka, n_bg_dev, bg_cap, bg_sorted);

@@ -292,19 +292,23 @@ int set_attrs(afg_ctx *ctx) {
 int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st) {
     const int64_t nf = (int64_t)n_det * n_psd;
     if (nf <= 0) return AFG_OK;
+    // algorithmic FP64 work of one filter: an inverse and a forward real FFT of NFFT points,
+    // 2.5 N log2 N flops each
+    const double flops = (double)nf * 2.0 * 2.5 * NFFT * 14.0;
+    static_assert(NFFT == 1 << 14, "flop count assumes log2(NFFT) = 14");
     if (ctx->cfg.fir_len <= FB_L && nf <= 65535) {
         void *scr = nullptr;
         int rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, (size_t)2 * nf * FB_P * FB_L * sizeof(double2), &scr);
         if (rc) return rc;
         double2 *Z = static_cast<double2 *>(scr), *Y = Z + nf * FB_P * FB_L;
-        KScope ks(ctx, st, KK_FILTER, 0.0, (double)nf * NBIN * (8.0 + 4.0));
+        KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
         k_fb_inverse<<<dim3(FB_P, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass,
                                                                 ctx->tw64, Z);
         k_fb_taper<<<dim3(FB_L / FB_T, (unsigned)nf), FB_T, 0, st>>>(Z, (double)ctx->cfg.fs, ctx->cfg.fir_len,
                                                                      ctx->tw64, Y);
         k_fb_forward<<<dim3(FB_P, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
     } else {
-        KScope ks(ctx, st, KK_FILTER, 0.0, (double)nf * NBIN * (8.0 + 4.0));
+        KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
         k_filter_build<<<dim3((unsigned)n_psd, n_det), NT64, (NC + 1) * sizeof(double2), st>>>(
             psd, n_psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass, ctx->cfg.fir_len, ctx->tw64, gains);
     }
