@@ -27,53 +27,19 @@ namespace {
 __constant__ float c_taps[604];
 __host__ __device__ constexpr int c_taps_off(int M) { return M == 2 ? 0 : M == 4 ? 41 : M == 8 ? 122 : 283; }
 
-constexpr int RSMP_T = 128;
-constexpr int RSMP_PER = 8;                    // consecutive outputs per thread
-constexpr int RSMP_OUT = RSMP_PER * RSMP_T;    // outputs per block
-constexpr int RSMP_Q = 21;                     // taps per phase at L = 10 M (phase 0: 21, others 20)
-constexpr int RSMP_WIN = RSMP_PER + 20;        // samples of one phase row a thread reads: its outputs + 20
+constexpr int RSMP_T = 256;
+constexpr int RSMP_OUT = 4 * RSMP_T;  // outputs per block
+constexpr int RSMP_Q = 21;            // taps per phase at L = 10 M (phase 0: 21, others 20)
+constexpr int RSMP_WIN = 24;          // window of one thread per phase: 4 outputs + 20, rounded to float4
 // words per phase row: a multiple of 4 (16-byte rows) that is 4 mod 8, so the rows p and p + 4
 // written from one 16-byte load of a warp fall in different shared-memory banks
-constexpr int RSMP_PITCH = RSMP_OUT + RSMP_WIN;
-static_assert(RSMP_WIN % 4 == 0 && RSMP_PITCH % 8 == 4, "phase-row layout");
-constexpr int RSMP_BATCH = 8;                  // 16-byte staging loads in flight per thread
+constexpr int RSMP_PITCH = RSMP_OUT + RSMP_WIN + 4;
+static_assert(RSMP_PITCH % 8 == 4, "phase-row layout");
 
-// y[base + r] += h[q M + p] x-row_p[base + q + r] over the taps of phase p, the row window in
-// registers (RSMP_WIN / 4 16-byte shared loads)
-template <int MF>
-__device__ __forceinline__ void phase_fma(const float *__restrict__ row, int p, int M, int ntap,
-                                          const float *__restrict__ h, float (&acc)[RSMP_PER]) {
-    float win[RSMP_WIN];
-    const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-    for (int v = 0; v < RSMP_WIN / 4; ++v) {
-        const float4 u = r4[v];
-        win[4 * v] = u.x;
-        win[4 * v + 1] = u.y;
-        win[4 * v + 2] = u.z;
-        win[4 * v + 3] = u.w;
-    }
-#pragma unroll
-    for (int q = 0; q < RSMP_Q; ++q) {
-        const int k = q * (MF ? MF : M) + p;
-        if (MF) {  // a compile-time constant-bank operand
-            if (k < 20 * (MF ? MF : 1) + 1) {
-                const float hk = c_taps[c_taps_off(MF) + k];
-#pragma unroll
-                for (int r = 0; r < RSMP_PER; ++r) acc[r] = fmaf(hk, win[q + r], acc[r]);
-            }
-        } else {
-            const float hk = k < ntap ? h[k] : 0.f;
-#pragma unroll
-            for (int r = 0; r < RSMP_PER; ++r) acc[r] = fmaf(hk, win[q + r], acc[r]);
-        }
-    }
-}
-
-// MF: the factor at compile time (0: runtime M).  Thread t computes the RSMP_PER consecutive
-// outputs of its block's tile from RSMP_PER t.  For each phase p it holds a window of
-// RSMP_WIN consecutive samples of that phase's row in registers, and the tap h[q M + p]
-// multiplies window entries q .. q + RSMP_PER - 1.
+// MF: the factor at compile time (0: runtime M).  Thread t computes the 4 consecutive
+// outputs 4t .. 4t + 3 of its block's tile.  For each phase p it holds a sliding window of
+// 4 + 20 consecutive samples of that phase's row in registers (six 16-byte shared loads),
+// and the tap h[q M + p] multiplies window entries q .. q + 3.
 template <int MF>
 __global__ void __launch_bounds__(RSMP_T) k_decimate(const float *__restrict__ x, int64_t x_stride, int64_t n_in,
                                                      const float *__restrict__ taps, int M_rt, int L, int64_t j0,
@@ -94,27 +60,25 @@ __global__ void __launch_bounds__(RSMP_T) k_decimate(const float *__restrict__ x
         for (int k = threadIdx.x; k < ntap; k += RSMP_T) h[k] = taps[k];
     // stage the span de-interleaved by phase: local sample li at [li % M][li / M]
     if (MF >= 4 && vec_load && first + span <= n_in) {
-        // 16-byte loads (first is a multiple of 4: x rows 16-byte aligned), 4 phases per load,
-        // RSMP_BATCH loads of a thread issued before their shared stores
+        // 16-byte loads (first is a multiple of 4: x rows 16-byte aligned), 4 phases per load;
+        // all of a thread's loads are issued before the first shared store
+        constexpr int NV = ((MF ? MF : 1) * RSMP_PITCH / 4 + RSMP_T - 1) / RSMP_T;
         const float4 *x4 = reinterpret_cast<const float4 *>(xd + first);
-        const int nv = span / 4;
-        for (int b0 = 0; b0 < nv; b0 += RSMP_BATCH * RSMP_T) {
-            float4 u[RSMP_BATCH];
+        float4 u[NV];
 #pragma unroll
-            for (int k = 0; k < RSMP_BATCH; ++k) {
-                const int v = b0 + k * RSMP_T + threadIdx.x;
-                u[k] = v < nv ? __ldg(x4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+        for (int k = 0; k < NV; ++k) {
+            const int v = threadIdx.x + k * RSMP_T;
+            u[k] = v < span / 4 ? __ldg(x4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-            for (int k = 0; k < RSMP_BATCH; ++k) {
-                const int v = b0 + k * RSMP_T + threadIdx.x;
-                if (v < nv) {
-                    const int li = 4 * v, p = li & ((MF ? MF : 1) - 1), m = li / (MF ? MF : 1);
-                    xs[p * pitch + m] = u[k].x;
-                    xs[(p + 1) * pitch + m] = u[k].y;
-                    xs[(p + 2) * pitch + m] = u[k].z;
-                    xs[(p + 3) * pitch + m] = u[k].w;
-                }
+        for (int k = 0; k < NV; ++k) {
+            const int v = threadIdx.x + k * RSMP_T;
+            if (v < span / 4) {
+                const int li = 4 * v, p = li & ((MF ? MF : 1) - 1), m = li / (MF ? MF : 1);
+                xs[p * pitch + m] = u[k].x;
+                xs[(p + 1) * pitch + m] = u[k].y;
+                xs[(p + 2) * pitch + m] = u[k].z;
+                xs[(p + 3) * pitch + m] = u[k].w;
             }
         }
     } else {
@@ -126,25 +90,58 @@ __global__ void __launch_bounds__(RSMP_T) k_decimate(const float *__restrict__ x
         }
     }
     __syncthreads();
-    float acc[RSMP_PER];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int base = 4 * threadIdx.x;
+    if (MF) {  // every tap a compile-time constant-bank operand
 #pragma unroll
-    for (int r = 0; r < RSMP_PER; ++r) acc[r] = 0.f;
-    const int base = RSMP_PER * threadIdx.x;
-    if (MF) {
+        for (int p = 0; p < (MF ? MF : 1); ++p) {
+            float win[RSMP_WIN];
+            const float4 *row = reinterpret_cast<const float4 *>(xs + p * pitch + base);
 #pragma unroll
-        for (int p = 0; p < (MF ? MF : 1); ++p) phase_fma<MF>(xs + p * pitch + base, p, M, ntap, h, acc);
-    } else {
+            for (int v = 0; v < RSMP_WIN / 4; ++v) {
+                const float4 u = row[v];
+                win[4 * v] = u.x;
+                win[4 * v + 1] = u.y;
+                win[4 * v + 2] = u.z;
+                win[4 * v + 3] = u.w;
+            }
+#pragma unroll
+            for (int q = 0; q < RSMP_Q; ++q) {
+                const int k = q * (MF ? MF : 1) + p;
+                if (k < 20 * (MF ? MF : 1) + 1) {
+                    const float hk = c_taps[c_taps_off(MF) + k];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r] = fmaf(hk, win[q + r], acc[r]);
+                }
+            }
+        }
+    } else
 #pragma unroll 1
-        for (int p = 0; p < M; ++p) phase_fma<0>(xs + p * pitch + base, p, M, ntap, h, acc);
+    for (int p = 0; p < M; ++p) {
+        float win[RSMP_WIN];
+        const float4 *row = reinterpret_cast<const float4 *>(xs + p * pitch + base);
+#pragma unroll
+        for (int v = 0; v < RSMP_WIN / 4; ++v) {
+            const float4 u = row[v];
+            win[4 * v] = u.x;
+            win[4 * v + 1] = u.y;
+            win[4 * v + 2] = u.z;
+            win[4 * v + 3] = u.w;
+        }
+#pragma unroll
+        for (int q = 0; q < RSMP_Q; ++q) {
+            const int k = q * M + p;
+            const float hk = k < ntap ? h[k] : 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r] = fmaf(hk, win[q + r], acc[r]);
+        }
     }
     const int64_t o = o0 + base;
-    if (vec_store && o + RSMP_PER - 1 < n_out) {  // rows 16-byte aligned (checked on the host), o a multiple of 4
-#pragma unroll
-        for (int r = 0; r < RSMP_PER; r += 4)
-            *reinterpret_cast<float4 *>(yd + o + r) = make_float4(acc[r], acc[r + 1], acc[r + 2], acc[r + 3]);
+    if (vec_store && o + 3 < n_out) {  // rows 16-byte aligned (checked on the host), o a multiple of 4
+        *reinterpret_cast<float4 *>(yd + o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
     } else {
 #pragma unroll
-        for (int r = 0; r < RSMP_PER; ++r)
+        for (int r = 0; r < 4; ++r)
             if (o + r < n_out) yd[o + r] = acc[r];
     }
 }
