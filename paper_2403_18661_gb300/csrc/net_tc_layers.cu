@@ -46,10 +46,13 @@
 
 namespace {
 
-constexpr int LT = 384;            // threads: 12 warps
-constexpr int EPI_W0 = 4;          // first epilogue warp
-constexpr int EPI_WARPS = 8;
+constexpr int LT = 448;            // threads: 14 warps
+constexpr int EPI_W0 = 2;          // first epilogue warp
+constexpr int EPI_WARPS = 12;      // three per TMEM lane quarter
 constexpr int EPI_T = EPI_WARPS * 32;
+constexpr int EPI_PARTS = EPI_WARPS / 4;  // the epilogue splits positions (subtiles) into this many parts
+constexpr int XCH_FLOATS = 2 * EPI_PARTS * 128 * 2;  // channel-major GroupNorm exchange
+static_assert(XCH_FLOATS >= 2 * 512, "scale and shift share the exchange region");
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int NB_MAX = 8;          // deepest shared-memory ring
 constexpr uint32_t SMEM_LIMIT = 227 * 1024;
@@ -69,6 +72,7 @@ struct LayerArgs {
     int NB;              // pipeline stages (<= NB_MAX)
     int shape;           // index of the unrolled MMA sequence of one stage (-1: generic loops)
     int nacc;            // TMEM accumulator buffers (1, or 2 with buffer b at column 256 b)
+    int nparts;          // CH: parts the epilogue splits each window's positions into (2 or 3)
     int G;
     float eps;
     int relu;
@@ -95,7 +99,7 @@ __host__ __device__ inline LSmem layer_smem(const LayerArgs &a) {
     s.off_act = align_up(wbytes, 1024);
     s.off_red = align_up(s.off_act + a.act_stage_bytes * a.NB, 16);
     s.off_sc = s.off_red + EPI_WARPS * 32 * 4;
-    s.off_bar = align_up(s.off_sc + 2 * 512 * 4, 16);
+    s.off_bar = align_up(s.off_sc + XCH_FLOATS * 4, 16);
     s.total = s.off_bar + 8 * (2 * NB_MAX + 5) + 16;  // full, empty, acc_full[2], acc_empty[2], wbar; slot, flag
     return s;
 }
@@ -508,10 +512,10 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
         }
     } else if (warp >= EPI_W0) {
         // ------------------------------------------------------------ epilogue
-        const int e = warp - EPI_W0;        // 0..7
-        const int q = warp & 3;             // TMEM lane quarter
-        const int hsel = e >> 2;            // which half of the subtiles / windows
-        const int et = tid - EPI_W0 * 32;   // 0..255
+        const int e = warp - EPI_W0;        // 0 .. EPI_WARPS - 1
+        const int q = warp & 3;             // TMEM lane quarter (warp w reaches lanes 32 (w % 4) ..)
+        const int hsel = e >> 2;            // which part of the subtiles / positions
+        const int et = tid - EPI_W0 * 32;   // 0 .. EPI_T - 1
         const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
         uint32_t tiles = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tiles) {
@@ -542,19 +546,20 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                 __syncwarp();
                 for (int c0 = 0; c0 < a.Cout; c0 += 16) {
                     // per-channel sums of this 16-channel chunk over the thread's subtiles
-                    // (up to 4 TMEM loads in flight, one wait) ...
+                    // (up to 2 TMEM loads in flight, one wait) ...
                     float cs[16], cq[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) cs[c] = cq[c] = 0.f;
-                    for (int j0 = hsel; j0 < MT; j0 += 8) {
-                        uint32_t r[4][16];
-                        const int nj = min(4, (MT - j0 + 1) / 2);
+                    for (int j0 = hsel; j0 < MT; j0 += 2 * EPI_PARTS) {
+                        uint32_t r[2][16];
+                        const int nj = min(2, (MT - j0 + EPI_PARTS - 1) / EPI_PARTS);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (u < nj) tc::tmem_ld16_nowait(tb + (uint32_t)((j0 + 2 * u) * a.Cout + c0), r[u]);
+                        for (int u = 0; u < 2; ++u)
+                            if (u < nj)
+                                tc::tmem_ld16_nowait(tb + (uint32_t)((j0 + EPI_PARTS * u) * a.Cout + c0), r[u]);
                         tc::tmem_wait_ld();
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
+                        for (int u = 0; u < 2; ++u)
                             if (u < nj) {
 #pragma unroll
                                 for (int c = 0; c < 16; ++c) {
@@ -589,13 +594,13 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                 }
                 epi_sync();
                 __nv_bfloat16 *__restrict__ ow = a.out + (size_t)w * ld;
-                for (int j = hsel; j < MT; j += 2) {
+                for (int j = hsel; j < MT; j += EPI_PARTS) {
                     const int row = 128 * j + 32 * q + lane + 1;
                     for (int c0 = 0; c0 < a.Cout; c0 += 32) {
                         const size_t s0 = (size_t)(c0 / 8) * cs + out_row(row, a.out_split, a.Lout) * 8;
-                        if (rw) {  // prefetch the next unit: (j, c0 + 32) or (j + 2, 0)
+                        if (rw) {  // prefetch the next unit: (j, c0 + 32) or (j + EPI_PARTS, 0)
                             const int cn = c0 + 32 < a.Cout ? c0 + 32 : 0;
-                            const int jn = c0 + 32 < a.Cout ? j : j + 2;
+                            const int jn = c0 + 32 < a.Cout ? j : j + EPI_PARTS;
                             if (jn < MT) {
                                 const size_t on = (size_t)(cn / 8) * cs + (size_t)(128 * jn + 32 * q + lane + 1) * 8;
 #pragma unroll
@@ -642,24 +647,26 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     }
                 }
             } else {
-                // rows = channels of the slice; thread: channel 32q + lane; the two warp halves
-                // take the two halves of every window's positions and exchange GroupNorm partials
+                // rows = channels of the slice; thread: channel 32q + lane; the warps of a lane quarter
+                // take the parts of every window's positions and exchange GroupNorm partials
                 const int slice = t % a.slices;
                 const int w0 = (t / a.slices) * a.wpc;
                 const int cl = 32 * q + lane;
                 const int c = slice * 128 + cl;
                 const int cg = a.Cout / a.G;  // <= 32: lanes of one group are contiguous
                 const float gam = a.gamma[c], bet = a.beta[c];
-                const int Lh = a.Lout >> 1;
+                const int np = a.nparts;       // 2 or 3; warps of an unused part only keep the barriers
+                const bool active = hsel < np;
+                const int Lh = a.Lout / np;
                 const int pb = hsel * Lh;
-                float *xch = scale;  // [window parity][half][128 channels][sum, sum of squares]
+                float *xch = scale;  // [window parity][part][128 channels][sum, sum of squares]
                 const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
                 const int n32 = Lh / 32, tail16 = Lh % 32;
                 for (int i = 0; i < a.wpc; ++i) {
                     const int w = w0 + i;
                     const uint32_t tw = tb + (uint32_t)(i * a.Lout + pb);
                     const size_t co = (size_t)w * ld + (size_t)(c >> 3) * (a.Lout + 2) * 8;  // row 0 of c's chunk
-                    const bool has_res = a.res != nullptr && w < a.n_win;
+                    const bool has_res = active && a.res != nullptr && w < a.n_win;
                     const __nv_bfloat16 *__restrict__ rw = has_res ? a.res + co : nullptr;
                     uint4 cur[4], nxt[4];  // residual of the current / next unit (loads in flight meanwhile)
                     if (has_res) {
@@ -667,50 +674,57 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                         else ch_res_load<1>(rw, pb, lane, cur);
                     }
                     float s = 0.f, qq = 0.f;
-                    int p0 = 0;
-                    for (; p0 + 32 <= Lh; p0 += 32) {
-                        uint32_t r0[16], r1[16];
-                        tc::tmem_ld16_nowait(tw + (uint32_t)p0, r0);
-                        tc::tmem_ld16_nowait(tw + (uint32_t)(p0 + 16), r1);
-                        tc::tmem_wait_ld();
+                    if (active) {
+                        int p0 = 0;
+                        for (; p0 + 32 <= Lh; p0 += 32) {
+                            uint32_t r0[16], r1[16];
+                            tc::tmem_ld16_nowait(tw + (uint32_t)p0, r0);
+                            tc::tmem_ld16_nowait(tw + (uint32_t)(p0 + 16), r1);
+                            tc::tmem_wait_ld();
 #pragma unroll
-                        for (int p = 0; p < 16; ++p) {
-                            const float v0 = __uint_as_float(r0[p]), v1 = __uint_as_float(r1[p]);
-                            s += v0 + v1;
-                            qq = fmaf(v0, v0, fmaf(v1, v1, qq));
+                            for (int p = 0; p < 16; ++p) {
+                                const float v0 = __uint_as_float(r0[p]), v1 = __uint_as_float(r1[p]);
+                                s += v0 + v1;
+                                qq = fmaf(v0, v0, fmaf(v1, v1, qq));
+                            }
                         }
-                    }
-                    if (p0 < Lh) {
-                        uint32_t r0[16];
-                        tc::tmem_ld16_nowait(tw + (uint32_t)p0, r0);
-                        tc::tmem_wait_ld();
+                        if (p0 < Lh) {
+                            uint32_t r0[16];
+                            tc::tmem_ld16_nowait(tw + (uint32_t)p0, r0);
+                            tc::tmem_wait_ld();
 #pragma unroll
-                        for (int p = 0; p < 16; ++p) {
-                            const float v0 = __uint_as_float(r0[p]);
-                            s += v0;
-                            qq = fmaf(v0, v0, qq);
+                            for (int p = 0; p < 16; ++p) {
+                                const float v0 = __uint_as_float(r0[p]);
+                                s += v0;
+                                qq = fmaf(v0, v0, qq);
+                            }
                         }
+                        for (int o = cg / 2; o > 0; o >>= 1) {
+                            s += __shfl_xor_sync(0xffffffffu, s, o);
+                            qq += __shfl_xor_sync(0xffffffffu, qq, o);
+                        }
+                        float *mine = xch + (((i & 1) * EPI_PARTS + hsel) * 128 + cl) * 2;
+                        mine[0] = s;
+                        mine[1] = qq;
                     }
-                    for (int o = cg / 2; o > 0; o >>= 1) {
-                        s += __shfl_xor_sync(0xffffffffu, s, o);
-                        qq += __shfl_xor_sync(0xffffffffu, qq, o);
-                    }
-                    float *mine = xch + (((i & 1) * 2 + hsel) * 128 + cl) * 2;
-                    const float *other = xch + (((i & 1) * 2 + (hsel ^ 1)) * 128 + cl) * 2;
-                    mine[0] = s;
-                    mine[1] = qq;
                     epi_sync();
-                    s += other[0];
-                    qq += other[1];
+                    if (!active || w >= a.n_win) continue;
+                    // every part sums the parts in the same order, so all get the same statistics
+                    s = 0.f;
+                    qq = 0.f;
+                    for (int k = 0; k < np; ++k) {
+                        const float *pk = xch + (((i & 1) * EPI_PARTS + k) * 128 + cl) * 2;
+                        s += pk[0];
+                        qq += pk[1];
+                    }
                     const float cnt = (float)a.Lout * (float)cg;
                     const float mean = s / cnt;
                     const float var = fmaxf(qq / cnt - mean * mean, 0.f);
                     const float sc = rsqrtf(var + a.eps) * gam;
                     const float sh = bet - mean * sc;
-                    if (w >= a.n_win) continue;
                     __nv_bfloat16 *__restrict__ ow = a.out + co;
                     for (int u = 0; u < n32; ++u) {
-                        p0 = 32 * u;
+                        const int p0 = 32 * u;
                         if (has_res) {
                             if (u + 1 < n32) ch_res_load<2>(rw, pb + p0 + 32, lane, nxt);
                             else if (tail16) ch_res_load<1>(rw, pb + p0 + 32, lane, nxt);
@@ -723,9 +737,13 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     if (tail16)
                         ch_store<1>(tw + (uint32_t)(32 * n32), pb + 32 * n32, sc, sh, has_res, cur, ow, a.relu, lane,
                                     a.out_split, a.Lout);
-                    if ((lane & 7) == 0)  // zero pad row of the chunk
-                        *reinterpret_cast<uint4 *>(ow + out_row(hsel ? a.Lout + 1 : 0, a.out_split, a.Lout) * 8) =
-                            make_uint4(0, 0, 0, 0);
+                    if ((lane & 7) == 0) {  // zero pad rows of the chunk
+                        if (hsel == 0)
+                            *reinterpret_cast<uint4 *>(ow + out_row(0, a.out_split, a.Lout) * 8) = make_uint4(0, 0, 0, 0);
+                        if (hsel == np - 1)
+                            *reinterpret_cast<uint4 *>(ow + out_row(a.Lout + 1, a.out_split, a.Lout) * 8) =
+                                make_uint4(0, 0, 0, 0);
+                    }
                 }
             }
             tc::fence_before_sync();
@@ -1057,12 +1075,14 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
         a.wpc = 1;
         a.slices = 1;
         a.nsplit = 1;
+        a.nparts = EPI_PARTS;
         a.w_block_bytes = (uint32_t)(C.k * C.cin * C.cout * 2);
     } else {
         if (C.cout % 128 || cg > 32) return false;
         if (!(k.KB == 32 || k.KB == 64 || k.KB == 128) || C.cin % k.KB) return false;
         a.nsplit = (C.lout + 255) / 256;
         if (C.lout % 32 || C.lout % a.nsplit || (C.lout / a.nsplit) % 16) return false;
+        a.nparts = C.lout % (16 * EPI_PARTS) == 0 ? EPI_PARTS : 2;
         if (k.wpc < 1 || k.wpc * C.lout > acc_cols) return false;
         a.wpc = k.wpc;
         a.slices = C.cout / 128;
