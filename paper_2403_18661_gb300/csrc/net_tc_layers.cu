@@ -52,7 +52,11 @@ constexpr int EPI_WARPS = 12;      // three per TMEM lane quarter
 constexpr int EPI_T = EPI_WARPS * 32;
 constexpr int EPI_PARTS = EPI_WARPS / 4;  // the epilogue splits positions (subtiles) into this many parts
 constexpr int XCH_FLOATS = 2 * EPI_PARTS * 128 * 2;  // channel-major GroupNorm exchange
-static_assert(XCH_FLOATS >= 2 * 512, "scale and shift share the exchange region");
+constexpr int CH_SCR_BYTES = 256;                     // channel-major transpose scratch per epilogue warp
+// epilogue region: position-major [red][scale][shift] or channel-major [exchange][scratch]
+constexpr int POS_EPI_BYTES = EPI_WARPS * 32 * 4 + 2 * 512 * 4;
+constexpr int CH_EPI_BYTES = XCH_FLOATS * 4 + EPI_WARPS * CH_SCR_BYTES;
+constexpr int EPI_BYTES = POS_EPI_BYTES > CH_EPI_BYTES ? POS_EPI_BYTES : CH_EPI_BYTES;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int NB_MAX = 8;          // deepest shared-memory ring
 constexpr uint32_t SMEM_LIMIT = 227 * 1024;
@@ -98,8 +102,8 @@ __host__ __device__ inline LSmem layer_smem(const LayerArgs &a) {
     s.off_w = 0;
     s.off_act = align_up(wbytes, 1024);
     s.off_red = align_up(s.off_act + a.act_stage_bytes * a.NB, 16);
-    s.off_sc = s.off_red + EPI_WARPS * 32 * 4;
-    s.off_bar = align_up(s.off_sc + XCH_FLOATS * 4, 16);
+    s.off_sc = s.off_red + EPI_WARPS * 32 * 4;  // position-major scale, shift
+    s.off_bar = align_up(s.off_red + EPI_BYTES, 16);
     s.total = s.off_bar + 8 * (2 * NB_MAX + 5) + 16;  // full, empty, acc_full[2], acc_empty[2], wbar; slot, flag
     return s;
 }
@@ -253,52 +257,6 @@ __device__ __forceinline__ bool issue_stage(int shape, const StageGeo &g) {
     }
 }
 
-// 8 x 8 transpose of 16-bit values inside each octet of lanes (lanes 8g .. 8g + 7): on entry
-// lane e holds row e (columns 0..7 as four packed pairs), on exit column e.  Three butterfly
-// stages swap the off-diagonal 4 x 4, 2 x 2 and 1 x 1 blocks.
-__device__ __forceinline__ void transpose8_b16(uint32_t (&P)[4], int lane) {
-    {
-        const bool hi = lane & 4;
-        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, hi ? P[0] : P[2], 4);
-        const uint32_t y1 = __shfl_xor_sync(0xffffffffu, hi ? P[1] : P[3], 4);
-        if (hi) {
-            P[0] = y0;
-            P[1] = y1;
-        } else {
-            P[2] = y0;
-            P[3] = y1;
-        }
-    }
-    {
-        const bool hi = lane & 2;
-        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, hi ? P[0] : P[1], 2);
-        const uint32_t y1 = __shfl_xor_sync(0xffffffffu, hi ? P[2] : P[3], 2);
-        if (hi) {
-            P[0] = y0;
-            P[2] = y1;
-        } else {
-            P[1] = y0;
-            P[3] = y1;
-        }
-    }
-    {
-        const bool hi = lane & 1;  // even lanes send their odd columns, odd lanes their even ones
-        const uint32_t y0 = __shfl_xor_sync(0xffffffffu, __byte_perm(P[0], P[1], hi ? 0x5410 : 0x7632), 1);
-        const uint32_t y1 = __shfl_xor_sync(0xffffffffu, __byte_perm(P[2], P[3], hi ? 0x5410 : 0x7632), 1);
-        if (hi) {
-            P[0] = __byte_perm(P[0], y0, 0x3254);
-            P[1] = __byte_perm(P[1], y0, 0x3276);
-            P[2] = __byte_perm(P[2], y1, 0x3254);
-            P[3] = __byte_perm(P[3], y1, 0x3276);
-        } else {
-            P[0] = __byte_perm(P[0], y0, 0x5410);
-            P[1] = __byte_perm(P[1], y0, 0x7610);
-            P[2] = __byte_perm(P[2], y1, 0x5410);
-            P[3] = __byte_perm(P[3], y1, 0x7610);
-        }
-    }
-}
-
 // Residual rows of a channel-major epilogue unit (16 * NQ positions from p_first): lane e of
 // each octet loads rows p_first + 8 b + e + 1 of the octet's chunk (issued one unit ahead).
 template <int NQ>
@@ -309,47 +267,74 @@ __device__ __forceinline__ void ch_res_load(const __nv_bfloat16 *__restrict__ rw
         rr[b] = __ldg(reinterpret_cast<const uint4 *>(rw8 + (size_t)(p_first + 8 * b + (lane & 7) + 1) * 8));
 }
 
-// Channel-major epilogue of 16 * NQ consecutive positions of one channel per lane: normalise
-// the accumulators (one TMEM wait), add the residual (rr, already loaded), ReLU, BF16.  Blocks
-// of 8 positions are transposed inside each lane octet (8 channels = one chunk), so every lane
-// stores one 16-byte row: position p_first + 8 b + e of its octet's chunk.
+// Channel-major epilogue of 16 * NQ consecutive positions of the warp's 32 channels: the
+// accumulators are read in the MMA fragment layout (lane t: channels t/4, 8 + t/4, 16 + t/4,
+// 24 + t/4 of the warp at positions 2 (t % 4) and 2 (t % 4) + 1 of each group of 8), normalised
+// (sc4[k], sh4[k]: channel 8 k + t/4), the residual added, ReLU'd and packed to BF16.  Per
+// group, stmatrix.trans turns the four 8 x 8 fragments (one per 8-channel chunk) into chunk
+// rows in the warp's 256-byte scratch (two chunks at a time), and every lane stores one
+// 16-byte row: position p_first + 8 g + lane % 8 of chunk lane / 8.  The residual rows
+// (rr[g], loaded by ch_res_load) come in through ldmatrix.trans the same way.
 template <int NQ>
-__device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, float sc, float sh, bool has_res,
-                                         const uint4 (&rr)[4], __nv_bfloat16 *__restrict__ ow8, int relu, int lane,
-                                         int split, int Lout) {
-    const int e = lane & 7;
-    uint32_t r[NQ][16];
-#pragma unroll
-    for (int g = 0; g < NQ; ++g) tc::tmem_ld16_nowait(taddr + (uint32_t)(16 * g), r[g]);
+__device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, const float (&sc4)[4], const float (&sh4)[4],
+                                         bool has_res, const uint4 (&rr)[4], __nv_bfloat16 *__restrict__ ow8,
+                                         int relu, int lane, int split, int Lout, uint32_t scr) {
+    constexpr int NG = 2 * NQ;
+    uint32_t A[4 * NG], B[4 * NG];  // TMEM lanes 0..15 and 16..31 of the warp's quarter
+    if constexpr (NG == 4) {
+        tc::tmem_ld16x256b_x4_nowait(taddr, A);
+        tc::tmem_ld16x256b_x4_nowait(taddr + (16u << 16), B);
+    } else {
+        tc::tmem_ld16x256b_x2_nowait(taddr, A);
+        tc::tmem_ld16x256b_x2_nowait(taddr + (16u << 16), B);
+    }
     tc::tmem_wait_ld();
+    const uint32_t my_row = scr + (uint32_t)(lane & 15) * 16;  // row address this thread gives stmatrix
+    const int half = lane >> 4;                                  // which pass stores this lane's chunk
 #pragma unroll
-    for (int b = 0; b < 2 * NQ; ++b) {
+    for (int g = 0; g < NG; ++g) {
         float x[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = fmaf(__uint_as_float(r[b >> 1][(b & 1) * 8 + j]), sc, sh);
-        if (has_res) {
-            uint32_t R[4] = {rr[b].x, rr[b].y, rr[b].z, rr[b].w};
-            transpose8_b16(R, lane);  // now: this lane's channel at the block's 8 positions
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                x[2 * j] += __uint_as_float(R[j] << 16);
-                x[2 * j + 1] += __uint_as_float(R[j] & 0xffff0000u);
-            }
-        }
-        uint32_t P[4];
-#pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float x0 = x[2 * j], x1 = x[2 * j + 1];
-            if (relu) {
-                x0 = fmaxf(x0, 0.f);
-                x1 = fmaxf(x1, 0.f);
-            }
-            __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
-            P[j] = *reinterpret_cast<uint32_t *>(&b2);
+            x[j] = fmaf(__uint_as_float(A[4 * g + j]), sc4[j >> 1], sh4[j >> 1]);
+            x[4 + j] = fmaf(__uint_as_float(B[4 * g + j]), sc4[2 + (j >> 1)], sh4[2 + (j >> 1)]);
         }
-        transpose8_b16(P, lane);  // now: the octet's 8 channels at position p_first + 8 b + e
-        *reinterpret_cast<uint4 *>(ow8 + out_row(p_first + 8 * b + e + 1, split, Lout) * 8) =
-            make_uint4(P[0], P[1], P[2], P[3]);
+        if (has_res) {
+            uint32_t Q[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // rows of chunks 2h, 2h + 1 -> their fragments
+                if (half == h)
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(my_row), "r"(rr[g].x), "r"(rr[g].y),
+                                 "r"(rr[g].z), "r"(rr[g].w)
+                                 : "memory");
+                __syncwarp();
+                tc::ldmatrix_x2_trans(my_row, Q[2 * h], Q[2 * h + 1]);
+                __syncwarp();
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                x[2 * k] += __uint_as_float(Q[k] << 16);
+                x[2 * k + 1] += __uint_as_float(Q[k] & 0xffff0000u);
+            }
+        }
+        uint32_t R[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            R[k] = relu ? tc::pack_bf16x2_relu(x[2 * k], x[2 * k + 1]) : tc::pack_bf16x2(x[2 * k], x[2 * k + 1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // fragments of chunks 2h, 2h + 1 -> their rows
+            tc::stmatrix_x2_trans(my_row, R[2 * h], R[2 * h + 1]);
+            __syncwarp();
+            if (half == h) {
+                uint4 v;
+                asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                             : "r"(my_row)
+                             : "memory");
+                *reinterpret_cast<uint4 *>(ow8 + out_row(p_first + 8 * g + (lane & 7) + 1, split, Lout) * 8) = v;
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -659,7 +644,9 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                 const bool active = hsel < np;
                 const int Lh = a.Lout / np;
                 const int pb = hsel * Lh;
-                float *xch = scale;  // [window parity][part][128 channels][sum, sum of squares]
+                float *xch = red;  // [window parity][part][128 channels][sum, sum of squares]
+                const uint32_t scr = tc::smem_addr(reinterpret_cast<unsigned char *>(red) + XCH_FLOATS * 4 +
+                                                   e * CH_SCR_BYTES);
                 const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
                 const int n32 = Lh / 32, tail16 = Lh % 32;
                 for (int i = 0; i < a.wpc; ++i) {
@@ -722,6 +709,12 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     const float var = fmaxf(qq / cnt - mean * mean, 0.f);
                     const float sc = rsqrtf(var + a.eps) * gam;
                     const float sh = bet - mean * sc;
+                    float sc4[4], sh4[4];  // of the channels this lane holds in the fragment layout
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        sc4[k] = __shfl_sync(0xffffffffu, sc, 8 * k + (lane >> 2));
+                        sh4[k] = __shfl_sync(0xffffffffu, sh, 8 * k + (lane >> 2));
+                    }
                     __nv_bfloat16 *__restrict__ ow = a.out + co;
                     for (int u = 0; u < n32; ++u) {
                         const int p0 = 32 * u;
@@ -729,14 +722,14 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                             if (u + 1 < n32) ch_res_load<2>(rw, pb + p0 + 32, lane, nxt);
                             else if (tail16) ch_res_load<1>(rw, pb + p0 + 32, lane, nxt);
                         }
-                        ch_store<2>(tw + (uint32_t)p0, pb + p0, sc, sh, has_res, cur, ow, a.relu, lane, a.out_split,
-                                    a.Lout);
+                        ch_store<2>(tw + (uint32_t)p0, pb + p0, sc4, sh4, has_res, cur, ow, a.relu, lane, a.out_split,
+                                    a.Lout, scr);
 #pragma unroll
                         for (int b = 0; b < 4; ++b) cur[b] = nxt[b];
                     }
                     if (tail16)
-                        ch_store<1>(tw + (uint32_t)(32 * n32), pb + 32 * n32, sc, sh, has_res, cur, ow, a.relu, lane,
-                                    a.out_split, a.Lout);
+                        ch_store<1>(tw + (uint32_t)(32 * n32), pb + 32 * n32, sc4, sh4, has_res, cur, ow, a.relu, lane,
+                                    a.out_split, a.Lout, scr);
                     if ((lane & 7) == 0) {  // zero pad rows of the chunk
                         if (hsel == 0)
                             *reinterpret_cast<uint4 *>(ow + out_row(0, a.out_split, a.Lout) * 8) = make_uint4(0, 0, 0, 0);
