@@ -51,7 +51,7 @@ constexpr int EPI_W0 = 2;          // first epilogue warp
 constexpr int EPI_WARPS = 12;      // three per TMEM lane quarter
 constexpr int EPI_T = EPI_WARPS * 32;
 constexpr int EPI_PARTS = EPI_WARPS / 4;  // the epilogue splits positions (subtiles) into this many parts
-constexpr int XCH_FLOATS = 2 * EPI_PARTS * 128 * 2;  // channel-major GroupNorm exchange
+constexpr int XCH_FLOATS = EPI_PARTS * 128 * 2;  // channel-major GroupNorm exchange (one window at a time)
 constexpr int CH_SCR_BYTES = 256;                     // channel-major transpose scratch per epilogue warp
 // epilogue region: position-major [red][scale][shift] or channel-major [exchange][scratch]
 constexpr int POS_EPI_BYTES = EPI_WARPS * 32 * 4 + 2 * 512 * 4;
@@ -77,6 +77,10 @@ struct LayerArgs {
     int shape;           // index of the unrolled MMA sequence of one stage (-1: generic loops)
     int nacc;            // TMEM accumulator buffers (1, or 2 with buffer b at column 256 b)
     int nparts;          // CH: parts the epilogue splits each window's positions into (2 or 3)
+    int pair;            // CH: the two windows of a tile share each MMA along N: per chunk, window 0's rows
+                         // in a slot of win_cols rows (rows rounded up to 8), then window 1's rows
+    int mma_n;           // CH: N of one MMA (L_out / nsplit, or win_cols + L_out rounded up to 16 for a pair)
+    int win_cols;        // CH: TMEM columns from one window of the tile to the next (L_out, or the pair slot)
     int G;
     float eps;
     int relu;
@@ -131,31 +135,48 @@ __device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, int
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(EPI_T) : "memory"); }
 
-// Fold the per-channel partial sums of a 16-channel chunk into GroupNorm groups of
-// CG channels, reduce them over the warp, and let lane 0 add them to its warp's row.
-template <int CG>
-__device__ __forceinline__ void fold_chunk(const float (&cs)[16], const float (&cq)[16], int c0, int lane,
-                                           float *red_row) {
-    constexpr int W = CG < 16 ? CG : 16;  // channels of one group inside the chunk
+// Sum 32 per-lane values over the warp so that lane l ends with the total of value l
+// (butterfly reduce-scatter: 16 + 8 + 4 + 2 + 1 shuffles).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
 #pragma unroll
-    for (int gl = 0; gl < 16 / W; ++gl) {
-        float a = 0.f, b = 0.f;
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = (lane & o) != 0;
 #pragma unroll
-        for (int c = gl * W; c < (gl + 1) * W; ++c) {
-            a += cs[c];
-            b += cq[c];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) {
-            const int g = (c0 + gl * W) / CG;
-            red_row[g] += a;
-            red_row[16 + g] += b;
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
+    return v[0];
+}
+
+// Position-major GroupNorm partials of one warp: the thread's rows (positions) of its
+// subtiles j = hsel, hsel + EPI_PARTS, ... folded into the CO / CG groups (value g: sum,
+// value 16 + g: sum of squares), 16 channels per TMEM wait; lane l returns the warp's total
+// of value l.
+template <int CO, int CG>
+__device__ __forceinline__ float pos_group_partials(uint32_t tb, int hsel, int MT, int lane) {
+    static_assert(CO / CG <= 16 && CO % 32 == 0, "at most 16 groups");
+    float gp[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) gp[i] = 0.f;
+    for (int j = hsel; j < MT; j += EPI_PARTS) {
+#pragma unroll
+        for (int c0 = 0; c0 < CO; c0 += 16) {
+            uint32_t r[16];
+            tc::tmem_ld16_nowait(tb + (uint32_t)(j * CO + c0), r);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const float v = __uint_as_float(r[c]);
+                const int g = (c0 + c) / CG;
+                gp[g] += v;
+                gp[16 + g] = fmaf(v, v, gp[16 + g]);
+            }
+        }
+    }
+    return warp_reduce_scatter32(gp, lane);
 }
 
 // Stage shapes with a fully unrolled MMA sequence.  A loop around single tcgen05.mma
@@ -385,32 +406,55 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            if (ORIENT == 0) {
-                tc::mbar_expect_tx(wbar, a.w_block_bytes);
-                for (uint32_t o = 0; o < a.w_block_bytes; o += 32768)
-                    tc::bulk_load(wsm + o, a.wimg + o, min(32768u, a.w_block_bytes - o), wbar);
-            }
-            uint32_t k = 0;  // stage uses
-            for (int t = blockIdx.x; t < n_tiles && !*(volatile int *)abort_flag; t += gridDim.x) {
-                const int slice = ORIENT == 0 ? 0 : t % a.slices;
-                const int w0 = ORIENT == 0 ? t : (t / a.slices) * a.wpc;
-                const int nwt = ORIENT == 0 ? 1 : a.wpc;
-                for (int kb = 0; kb < a.n_kb; ++kb, ++k) {
-                    const int s = k % a.NB;
-                    if (k >= (uint32_t)a.NB && !bounded_wait(&empty[s], ((k / a.NB) - 1) & 1, abort_flag, a.err))
-                        break;
-                    const uint32_t wb = ORIENT == 1 ? a.w_block_bytes : 0;
-                    const int n_here = min(nwt, a.n_win - w0);  // absent windows: stale data, never stored
-                    tc::mbar_expect_tx(&full[s], (uint32_t)n_here * win_bytes + wb);
-                    if (ORIENT == 1) {
-                        const unsigned char *src = a.wimg + ((size_t)slice * a.n_kb + kb) * a.w_block_bytes;  // [slice][C_in/8][tap][128][8]
-                        unsigned char *dst = wsm + (size_t)s * a.w_block_bytes;
-                        for (uint32_t o = 0; o < a.w_block_bytes; o += 32768)
-                            tc::bulk_load(dst + o, src + o, min(32768u, a.w_block_bytes - o), &full[s]);
+        // the whole warp walks the stages: lane 0 waits for the slot and arms its barrier (and
+        // copies the weights), then the lanes issue the activation copies, in parallel where a
+        // window pair needs one small copy per (chunk, window)
+        if (ORIENT == 0 && lane == 0) {
+            tc::mbar_expect_tx(wbar, a.w_block_bytes);
+            for (uint32_t o = 0; o < a.w_block_bytes; o += 32768)
+                tc::bulk_load(wsm + o, a.wimg + o, min(32768u, a.w_block_bytes - o), wbar);
+        }
+        uint32_t k = 0;  // stage uses
+        bool stop = false;
+        for (int t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
+            if (__shfl_sync(0xffffffffu, lane == 0 ? *(volatile int *)abort_flag : 0, 0)) break;
+            const int slice = ORIENT == 0 ? 0 : t % a.slices;
+            const int w0 = ORIENT == 0 ? t : (t / a.slices) * a.wpc;
+            const int nwt = ORIENT == 0 ? 1 : a.wpc;
+            const int n_here = min(nwt, a.n_win - w0);  // absent windows: stale data, never stored
+            for (int kb = 0; kb < a.n_kb; ++kb, ++k) {
+                const int s = k % a.NB;
+                int ok = 1;
+                if (lane == 0) {
+                    if (k >= (uint32_t)a.NB && !bounded_wait(&empty[s], ((k / a.NB) - 1) & 1, abort_flag, a.err)) {
+                        ok = 0;
+                    } else {
+                        const uint32_t wb = ORIENT == 1 ? a.w_block_bytes : 0;
+                        tc::mbar_expect_tx(&full[s], (uint32_t)n_here * win_bytes + wb);
+                        if (ORIENT == 1) {
+                            const unsigned char *src = a.wimg + ((size_t)slice * a.n_kb + kb) * a.w_block_bytes;  // [slice][C_in/8][tap][128][8]
+                            unsigned char *dst = wsm + (size_t)s * a.w_block_bytes;
+                            for (uint32_t o = 0; o < a.w_block_bytes; o += 32768)
+                                tc::bulk_load(dst + o, src + o, min(32768u, a.w_block_bytes - o), &full[s]);
+                        }
                     }
-                    unsigned char *ab = act + (size_t)s * a.act_stage_bytes;
-                    const size_t in_chunk = (size_t)a.in_rows * 16;  // bytes of one input chunk in HBM
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    stop = true;
+                    break;
+                }
+                unsigned char *ab = act + (size_t)s * a.act_stage_bytes;
+                const size_t in_chunk = (size_t)a.in_rows * 16;  // bytes of one input chunk in HBM
+                if (ORIENT == 1 && a.pair) {
+                    // lane 2 c + i: chunk c of window i, at row (win_cols + rows) c + win_cols i
+                    const int c = lane >> 1, i = lane & 1;
+                    if (c < a.KB / 8 && i < n_here) {
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.in) +
+                                                   ((size_t)(w0 + i) * (a.Cin / 8) + (size_t)kb * (a.KB / 8) + c) * in_chunk;
+                        tc::bulk_load(ab + ((size_t)c * (a.win_cols + a.rows) + (size_t)i * a.win_cols) * 16, src,
+                                      chunk_bytes, &full[s]);
+                    }
+                } else if (lane == 0) {
                     for (int i = 0; i < n_here; ++i) {
                         const unsigned char *src = reinterpret_cast<const unsigned char *>(a.in) +
                                                    ((size_t)(w0 + i) * (a.Cin / 8) + (size_t)kb * (a.KB / 8)) * in_chunk;
@@ -432,7 +476,10 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
         if (lane == 0) {
             if (ORIENT == 0) bounded_wait(wbar, 0, abort_flag, a.err);
             const uint32_t idesc =
-                ORIENT == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.Lout / a.nsplit);
+                ORIENT == 0 ? tc::idesc_bf16_f32(128, a.Cout) : tc::idesc_bf16_f32(128, a.mma_n);
+            // activation chunk stride along K: one chunk, or a pair of window chunks
+            const uint32_t a_lbo = (ORIENT == 1 && a.pair) ? (uint32_t)(a.win_cols + a.rows) * 16 : chunk_bytes;
+            const int wpc_mma = (ORIENT == 1 && a.pair) ? 1 : a.wpc;
             const uint32_t wlbo = (uint32_t)(a.taps * Nw * 16);  // next 8-channel chunk of a weight tile
             const uint32_t toff0 = tap_row(a, 0), toff1 = tap_row(a, 1), toff2 = tap_row(a, 2);
             uint32_t k = 0, tiles = 0;
@@ -458,16 +505,16 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     StageGeo g;
                     g.dt = dt;
                     g.wd00 = tc::desc_kmajor_noswizzle(wb, wlbo, 128);
-                    g.ad00 = tc::desc_kmajor_noswizzle(ab, chunk_bytes, 128);
+                    g.ad00 = tc::desc_kmajor_noswizzle(ab, a_lbo, 128);
                     g.w_tap = (uint64_t)Nw;                // (Nw * 16) >> 4
                     g.w_kk = (uint64_t)(2 * a.taps * Nw);  // two chunks
-                    g.a_kk = (uint64_t)(2 * chunk_bytes / 16);
+                    g.a_kk = (uint64_t)(2 * a_lbo / 16);
                     g.a_win = (uint64_t)(win_bytes / 16);
                     g.toff0 = toff0;
                     g.toff1 = toff1;
                     g.toff2 = toff2;
                     g.n_step = ORIENT == 1 ? (uint32_t)(a.Lout / a.nsplit) : 0u;
-                    g.win_cols = ORIENT == 1 ? (uint32_t)a.Lout : (uint32_t)a.Cout;
+                    g.win_cols = ORIENT == 1 ? (uint32_t)a.win_cols : (uint32_t)a.Cout;
                     g.idesc = idesc;
                     g.first = kb == 0 ? 1u : 0u;
                     if (!issue_stage<ORIENT>(a.shape, g)) {
@@ -482,7 +529,7 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                                     for (int j = 0; j < MT; ++j)
                                         tc::mma_bf16(dt + (uint32_t)(j * a.Cout), adk + (uint64_t)(128 * j), wd, idesc, acc);
                                 } else {
-                                    for (int i = 0; i < a.wpc; ++i)
+                                    for (int i = 0; i < wpc_mma; ++i)
                                         for (int h = 0; h < a.nsplit; ++h)
                                             tc::mma_bf16(dt + (uint32_t)(i * a.Lout) + (uint32_t)h * g.n_step, wd,
                                                          adk + (uint64_t)i * g.a_win + (uint64_t)(h * g.n_step), idesc, acc);
@@ -526,42 +573,11 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) cur[i] = __ldg(reinterpret_cast<const uint4 *>(rw + o0 + i * cs));
                 }
-                // per-warp group partials in red[e][g] (sum) and red[e][16 + g] (sum of squares)
-                if (lane < 32) red[e * 32 + lane] = 0.f;
-                __syncwarp();
-                for (int c0 = 0; c0 < a.Cout; c0 += 16) {
-                    // per-channel sums of this 16-channel chunk over the thread's subtiles
-                    // (up to 2 TMEM loads in flight, one wait) ...
-                    float cs[16], cq[16];
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) cs[c] = cq[c] = 0.f;
-                    for (int j0 = hsel; j0 < MT; j0 += 2 * EPI_PARTS) {
-                        uint32_t r[2][16];
-                        const int nj = min(2, (MT - j0 + EPI_PARTS - 1) / EPI_PARTS);
-#pragma unroll
-                        for (int u = 0; u < 2; ++u)
-                            if (u < nj)
-                                tc::tmem_ld16_nowait(tb + (uint32_t)((j0 + EPI_PARTS * u) * a.Cout + c0), r[u]);
-                        tc::tmem_wait_ld();
-#pragma unroll
-                        for (int u = 0; u < 2; ++u)
-                            if (u < nj) {
-#pragma unroll
-                                for (int c = 0; c < 16; ++c) {
-                                    const float v = __uint_as_float(r[u][c]);
-                                    cs[c] += v;
-                                    cq[c] = fmaf(v, v, cq[c]);
-                                }
-                            }
-                    }
-                    // ... folded into the chunk's groups and reduced over the warp
-                    switch (cg) {
-                        case 4: fold_chunk<4>(cs, cq, c0, lane, red + e * 32); break;
-                        case 8: fold_chunk<8>(cs, cq, c0, lane, red + e * 32); break;
-                        case 16: fold_chunk<16>(cs, cq, c0, lane, red + e * 32); break;
-                        default: fold_chunk<32>(cs, cq, c0, lane, red + e * 32); break;
-                    }
-                }
+                // per-warp group partials: red[e][g] (sum) and red[e][16 + g] (sum of squares)
+                float part;
+                if (a.Cout == 64) part = pos_group_partials<64, 4>(tb, hsel, MT, lane);
+                else part = pos_group_partials<128, 8>(tb, hsel, MT, lane);  // the two geometries the host admits
+                red[e * 32 + lane] = part;
                 epi_sync();
                 if (et < a.Cout) {
                     const int g = et / cg;
@@ -644,14 +660,14 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                 const bool active = hsel < np;
                 const int Lh = a.Lout / np;
                 const int pb = hsel * Lh;
-                float *xch = red;  // [window parity][part][128 channels][sum, sum of squares]
+                float *xch = red;  // [part][128 channels][sum, sum of squares] of the current window
                 const uint32_t scr = tc::smem_addr(reinterpret_cast<unsigned char *>(red) + XCH_FLOATS * 4 +
                                                    e * CH_SCR_BYTES);
                 const size_t ld = (size_t)(a.Lout + 2) * a.Cout;
                 const int n32 = Lh / 32, tail16 = Lh % 32;
                 for (int i = 0; i < a.wpc; ++i) {
                     const int w = w0 + i;
-                    const uint32_t tw = tb + (uint32_t)(i * a.Lout + pb);
+                    const uint32_t tw = tb + (uint32_t)(i * a.win_cols + pb);
                     const size_t co = (size_t)w * ld + (size_t)(c >> 3) * (a.Lout + 2) * 8;  // row 0 of c's chunk
                     const bool has_res = active && a.res != nullptr && w < a.n_win;
                     const __nv_bfloat16 *__restrict__ rw = has_res ? a.res + co : nullptr;
@@ -690,20 +706,22 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                             s += __shfl_xor_sync(0xffffffffu, s, o);
                             qq += __shfl_xor_sync(0xffffffffu, qq, o);
                         }
-                        float *mine = xch + (((i & 1) * EPI_PARTS + hsel) * 128 + cl) * 2;
+                        float *mine = xch + (hsel * 128 + cl) * 2;
                         mine[0] = s;
                         mine[1] = qq;
                     }
-                    epi_sync();
-                    if (!active || w >= a.n_win) continue;
+                    epi_sync();  // the partials are written
                     // every part sums the parts in the same order, so all get the same statistics
                     s = 0.f;
                     qq = 0.f;
-                    for (int k = 0; k < np; ++k) {
-                        const float *pk = xch + (((i & 1) * EPI_PARTS + k) * 128 + cl) * 2;
-                        s += pk[0];
-                        qq += pk[1];
-                    }
+                    if (active)
+                        for (int k = 0; k < np; ++k) {
+                            const float *pk = xch + (k * 128 + cl) * 2;
+                            s += pk[0];
+                            qq += pk[1];
+                        }
+                    epi_sync();  // ... and read: the next window may overwrite them
+                    if (!active || w >= a.n_win) continue;
                     const float cnt = (float)a.Lout * (float)cg;
                     const float mean = s / cnt;
                     const float var = fmaxf(qq / cnt - mean * mean, 0.f);
@@ -1061,7 +1079,8 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
     if (k.orient == 0) {
         // position-major: one window per tile, all input channels one K-block, weights resident
         if (C.cout > 128 || C.lout % 128 || (C.lout / 128) * C.cout > acc_cols) return false;
-        if (!(cg == 4 || cg == 8 || cg == 16 || cg == 32) || G > 16) return false;
+        // the statistics pass is unrolled for 16 groups of 64 or 128 channels
+        if (G != 16 || (C.cout != 64 && C.cout != 128)) return false;
         if (k.wpc != 1) return false;
         a.KB = C.cin;
         a.n_kb = 1;
@@ -1069,6 +1088,9 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
         a.slices = 1;
         a.nsplit = 1;
         a.nparts = EPI_PARTS;
+        a.pair = 0;
+        a.mma_n = C.cout;
+        a.win_cols = C.cout;
         a.w_block_bytes = (uint32_t)(C.k * C.cin * C.cout * 2);
     } else {
         if (C.cout % 128 || cg > 32) return false;
@@ -1080,11 +1102,27 @@ static bool layer_geometry(const ConvLayer &C, int G, float eps, const TileKnobs
         a.wpc = k.wpc;
         a.slices = C.cout / 128;
         a.KB = k.KB;
+        // two windows per MMA where their rows fit one N <= 256 (stride 1: every row is read); window
+        // 1 starts at an 8-aligned row (and TMEM column) so the epilogue reads whole 8-column groups
+        const int pslot = (a.rows + 7) / 8 * 8;
+        const int pair_n = (pslot + C.lout + 15) / 16 * 16;
+        a.pair = (k.wpc == 2 && C.stride == 1 && a.nsplit == 1 && pair_n <= acc_cols && pair_n <= 256) ? 1 : 0;
+        a.mma_n = a.pair ? pair_n : C.lout / a.nsplit;
+        a.win_cols = a.pair ? pslot : C.lout;
         a.n_kb = C.cin / k.KB;
         a.w_block_bytes = (uint32_t)(C.k * a.KB * 128 * 2);
     }
     a.act_stage_bytes = (uint32_t)a.wpc * (a.KB / 8) * (uint32_t)a.rows * 16;
-    a.shape = stage_shape(a.orient, a.taps, a.KB / 16, a.orient == 0 ? a.Lout / 128 : a.wpc, a.nsplit);
+    if (a.pair) {
+        a.act_stage_bytes = (uint32_t)(a.KB / 8) * (uint32_t)(a.win_cols + a.rows) * 16;
+        if (layer_smem(a).total > SMEM_LIMIT) {  // the padded pair does not fit: one MMA per window
+            a.pair = 0;
+            a.mma_n = C.lout / a.nsplit;
+            a.win_cols = C.lout;
+            a.act_stage_bytes = (uint32_t)a.wpc * (a.KB / 8) * (uint32_t)a.rows * 16;
+        }
+    }
+    a.shape = stage_shape(a.orient, a.taps, a.KB / 16, a.orient == 0 ? a.Lout / 128 : (a.pair ? 1 : a.wpc), a.nsplit);
     return layer_smem(a).total <= SMEM_LIMIT;
 }
 
