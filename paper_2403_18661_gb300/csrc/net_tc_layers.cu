@@ -158,9 +158,9 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
 template <int CO, int CG>
 __device__ __forceinline__ float pos_group_partials(uint32_t tb, int hsel, int MT, int lane) {
     static_assert(CO / CG <= 16 && CO % 32 == 0, "at most 16 groups");
-    float gp[32];
+    float2 acc[16];  // per group: (sum, sum of squares), one packed FMA per value
 #pragma unroll
-    for (int i = 0; i < 32; ++i) gp[i] = 0.f;
+    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
     for (int j = hsel; j < MT; j += EPI_PARTS) {
 #pragma unroll
         for (int c0 = 0; c0 < CO; c0 += 16) {
@@ -171,10 +171,15 @@ __device__ __forceinline__ float pos_group_partials(uint32_t tb, int hsel, int M
             for (int c = 0; c < 16; ++c) {
                 const float v = __uint_as_float(r[c]);
                 const int g = (c0 + c) / CG;
-                gp[g] += v;
-                gp[16 + g] = fmaf(v, v, gp[16 + g]);
+                acc[g] = __ffma2_rn(make_float2(v, v), make_float2(1.f, v), acc[g]);
             }
         }
+    }
+    float gp[32];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        gp[i] = acc[i].x;
+        gp[16 + i] = acc[i].y;
     }
     return warp_reduce_scatter32(gp, lane);
 }
@@ -314,11 +319,12 @@ __device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, const floa
     const int half = lane >> 4;                                  // which pass stores this lane's chunk
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
-        float x[8];
+        float2 x[4];  // x[k]: chunk k's channel at the lane's two positions
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            x[j] = fmaf(__uint_as_float(A[4 * g + j]), sc4[j >> 1], sh4[j >> 1]);
-            x[4 + j] = fmaf(__uint_as_float(B[4 * g + j]), sc4[2 + (j >> 1)], sh4[2 + (j >> 1)]);
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t *src = k < 2 ? &A[4 * g + 2 * k] : &B[4 * g + 2 * (k - 2)];
+            x[k] = __ffma2_rn(make_float2(__uint_as_float(src[0]), __uint_as_float(src[1])),
+                              make_float2(sc4[k], sc4[k]), make_float2(sh4[k], sh4[k]));
         }
         if (has_res) {
             uint32_t Q[4];
@@ -333,15 +339,13 @@ __device__ __forceinline__ void ch_store(uint32_t taddr, int p_first, const floa
                 __syncwarp();
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                x[2 * k] += __uint_as_float(Q[k] << 16);
-                x[2 * k + 1] += __uint_as_float(Q[k] & 0xffff0000u);
-            }
+            for (int k = 0; k < 4; ++k)
+                x[k] = __fadd2_rn(x[k], make_float2(__uint_as_float(Q[k] << 16), __uint_as_float(Q[k] & 0xffff0000u)));
         }
         uint32_t R[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            R[k] = relu ? tc::pack_bf16x2_relu(x[2 * k], x[2 * k + 1]) : tc::pack_bf16x2(x[2 * k], x[2 * k + 1]);
+            R[k] = relu ? tc::pack_bf16x2_relu(x[k].x, x[k].y) : tc::pack_bf16x2(x[k].x, x[k].y);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // fragments of chunks 2h, 2h + 1 -> their rows
             tc::stmatrix_x2_trans(my_row, R[2 * h], R[2 * h + 1]);
@@ -618,23 +622,18 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                         tc::tmem_ld32(tb + (uint32_t)(j * a.Cout + c0), v);
                         uint32_t pk[16];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            float x0 = fmaf(v[2 * i], scale[c0 + 2 * i], shift[c0 + 2 * i]);
-                            float x1 = fmaf(v[2 * i + 1], scale[c0 + 2 * i + 1], shift[c0 + 2 * i + 1]);
+                        for (int i = 0; i < 16; ++i) {  // channels c0 + 2i, c0 + 2i + 1 as one packed pair
+                            float2 x = __ffma2_rn(make_float2(v[2 * i], v[2 * i + 1]),
+                                                  *reinterpret_cast<const float2 *>(scale + c0 + 2 * i),
+                                                  *reinterpret_cast<const float2 *>(shift + c0 + 2 * i));
                             if (rw) {
                                 const uint32_t u = (i & 3) == 0 ? rr[i >> 2].x
                                                    : (i & 3) == 1 ? rr[i >> 2].y
                                                    : (i & 3) == 2 ? rr[i >> 2].z
                                                                   : rr[i >> 2].w;
-                                x0 += __uint_as_float(u << 16);
-                                x1 += __uint_as_float(u & 0xffff0000u);
+                                x = __fadd2_rn(x, make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u)));
                             }
-                            if (a.relu) {
-                                x0 = fmaxf(x0, 0.f);
-                                x1 = fmaxf(x1, 0.f);
-                            }
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
-                            pk[i] = *reinterpret_cast<uint32_t *>(&b2);
+                            pk[i] = a.relu ? tc::pack_bf16x2_relu(x.x, x.y) : tc::pack_bf16x2(x.x, x.y);
                         }
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
@@ -678,6 +677,8 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     }
                     float s = 0.f, qq = 0.f;
                     if (active) {
+                        // (sum, sum of squares) in two packed accumulators, one packed FMA per value
+                        float2 m0 = make_float2(0.f, 0.f), m1 = make_float2(0.f, 0.f);
                         int p0 = 0;
                         for (; p0 + 32 <= Lh; p0 += 32) {
                             uint32_t r0[16], r1[16];
@@ -687,8 +688,8 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
 #pragma unroll
                             for (int p = 0; p < 16; ++p) {
                                 const float v0 = __uint_as_float(r0[p]), v1 = __uint_as_float(r1[p]);
-                                s += v0 + v1;
-                                qq = fmaf(v0, v0, fmaf(v1, v1, qq));
+                                m0 = __ffma2_rn(make_float2(v0, v0), make_float2(1.f, v0), m0);
+                                m1 = __ffma2_rn(make_float2(v1, v1), make_float2(1.f, v1), m1);
                             }
                         }
                         if (p0 < Lh) {
@@ -698,10 +699,11 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
 #pragma unroll
                             for (int p = 0; p < 16; ++p) {
                                 const float v0 = __uint_as_float(r0[p]);
-                                s += v0;
-                                qq = fmaf(v0, v0, qq);
+                                m0 = __ffma2_rn(make_float2(v0, v0), make_float2(1.f, v0), m0);
                             }
                         }
+                        s = m0.x + m1.x;
+                        qq = m0.y + m1.y;
                         for (int o = cg / 2; o > 0; o >>= 1) {
                             s += __shfl_xor_sync(0xffffffffu, s, o);
                             qq += __shfl_xor_sync(0xffffffffu, qq, o);
