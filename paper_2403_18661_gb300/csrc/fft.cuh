@@ -129,6 +129,14 @@ __device__ __forceinline__ void fft_2048(C *d, const C *tw) {
     stockham_pass<C, 4, SIGN, NT, 2048>(d, 512, tw);
 }
 
+// Complex FFT of 512 points in shared memory (radix 8, 8, 8), as fft_2048.
+template <typename C, int SIGN, int NT>
+__device__ __forceinline__ void fft_512(C *d, const C *tw) {
+    stockham_pass<C, 8, SIGN, NT, 512>(d, 1, tw);
+    stockham_pass<C, 8, SIGN, NT, 512>(d, 8, tw);
+    stockham_pass<C, 8, SIGN, NT, 512>(d, 64, tw);
+}
+
 // Real-FFT split after a forward complex FFT of z_j = x_{2j} + i x_{2j+1}:
 // d[0..NC) holds Z on entry; on exit d[0..NC] holds X_k, k in [0, NC], the
 // first half of the DFT of the NFFT real samples.  d must have NC+1 slots.

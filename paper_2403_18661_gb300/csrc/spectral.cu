@@ -120,77 +120,127 @@ __global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict_
 }
 
 // ---- filter build spread over many CTAs (fir_len <= 2048).  With the 16384-point grid
-// N, P = 8 and L = N / P = 2048:
+// N, P sub-transforms of L = N / P points (L = 2048, or 512 when few filters are built):
 //   inverse:  h_m = (1/N) sum_r e^{+2 pi i r m / N} Z_r[m mod L],
-//             Z_r = sum_j A_{P j + r} e^{+2 pi i j n / L}      (8 inverse FFTs of L points)
-//   taper:    g_m = sqrt(2/fs) taper(m) h_m,  m in [-L/2, L/2) (the F taps lie inside)
+//             Z_r = sum_j A_{P j + r} e^{+2 pi i j n / L}      (P inverse FFTs of L points)
+//   taper:    g_m = sqrt(2/fs) taper(m) h_m,  m in [-1024, 1024) (the F <= 2048 taps lie inside)
 //   forward:  G_{P j + r} = sum_n y_r[n] e^{-2 pi i j n / L},
-//             y_r[m mod L] = g_m e^{-2 pi i r m / N}         (8 forward FFTs of L points;
-//             the support of g is shorter than L, so the fold does not alias)
+//             y_r[n] = sum_{m = n mod L} g_m e^{-2 pi i r m / N}   (P forward FFTs of L points;
+//             at L = 2048 each slot n holds one lag, at L = 512 it folds four)
 // The same FP64 arithmetic as k_filter_build, on 2 P CTAs per filter instead of one.
-constexpr int FB_L = 2048;
-constexpr int FB_P = NFFT / FB_L;
+constexpr int FB_LAGS = 2048;  // lags m in [-FB_LAGS / 2, FB_LAGS / 2)
 constexpr int FB_T = 256;
 
-// grid (FB_P, n_filters): Z_r of filter f = det * n_psd + e
+template <int L>
+__device__ __forceinline__ void fb_fft(double2 *d, const double2 *tw, bool inverse) {
+    if (L == 2048) {
+        if (inverse) fft_2048<double2, +1, FB_T>(d, tw);
+        else fft_2048<double2, -1, FB_T>(d, tw);
+    } else {
+        if (inverse) fft_512<double2, +1, FB_T>(d, tw);
+        else fft_512<double2, -1, FB_T>(d, tw);
+    }
+}
+
+// grid (P, n_filters): Z_r of filter f = det * n_psd + e
+template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ psd, double fs, double f_hp,
                                                      const double2 *__restrict__ tw, double2 *__restrict__ Z) {
-    __shared__ double2 d[FB_L];
+    constexpr int P = NFFT / L;
+    __shared__ double2 d[L];
     const int r = blockIdx.x;
     const int64_t f = blockIdx.y;
     const double *p = psd + f * NBIN;
-    for (int j = threadIdx.x; j < FB_L; j += FB_T) {
-        const int k = FB_P * j + r;
+    for (int j = threadIdx.x; j < L; j += FB_T) {
+        const int k = P * j + r;
         const int kk = k <= NFFT / 2 ? k : NFFT - k;  // the amplitude response is even in k
         const double fr = (double)kk * fs / (double)NFFT;
         const double pk = p[kk];
         d[j] = make_double2((fr >= f_hp && pk > 0.0) ? 1.0 / sqrt(pk) : 0.0, 0.0);
     }
     __syncthreads();
-    fft_2048<double2, +1, FB_T>(d, tw);
-    double2 *z = Z + (f * FB_P + r) * FB_L;
-    for (int n = threadIdx.x; n < FB_L; n += FB_T) z[n] = d[n];
+    fb_fft<L>(d, tw, true);
+    double2 *z = Z + (f * P + r) * L;
+    for (int n = threadIdx.x; n < L; n += FB_T) z[n] = d[n];
 }
 
-// grid (FB_L / FB_T, n_filters): one lag m per thread
-__global__ void __launch_bounds__(FB_T) k_fb_taper(const double2 *__restrict__ Z, double fs, int F,
-                                                   const double2 *__restrict__ tw, double2 *__restrict__ Y) {
-    const int64_t f = blockIdx.y;
-    const int m = blockIdx.x * FB_T + threadIdx.x - FB_L / 2;  // lag in [-L/2, L/2)
-    const int slot = m & (FB_L - 1);
-    const double2 *z = Z + f * FB_P * FB_L + slot;
+// g_m of lag m from the P partial transforms (slot m mod L)
+template <int P, int L>
+__device__ __forceinline__ double fb_tap(const double2 *__restrict__ Zf, int m, double fs, int F,
+                                         const double2 *__restrict__ tw) {
+    const int slot = m & (L - 1);
     double h = 0.0;
-#pragma unroll
-    for (int r = 0; r < FB_P; ++r) {
+#pragma unroll 8
+    for (int r = 0; r < P; ++r) {
         const double2 w = tw[(r * m) & (NFFT - 1)];  // e^{-2 pi i r m / N}; use its conjugate
-        const double2 v = z[(int64_t)r * FB_L];
+        const double2 v = Zf[(int64_t)r * L + slot];
         h += w.x * v.x + w.y * v.y;  // Re(conj(w) v)
     }
     h /= (double)NFFT;
     const int half = F / 2;
-    double g = 0.0;
-    if (m >= -half && m < half) g = h * sqrt(2.0 / fs) * (0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F));
-    double2 *y = Y + f * FB_P * FB_L + slot;
+    return (m >= -half && m < half) ? h * sqrt(2.0 / fs) * (0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F))
+                                    : 0.0;
+}
+
+// L = 2048: grid (FB_LAGS / FB_T, n_filters), one lag per thread, one lag per slot
+__global__ void __launch_bounds__(FB_T) k_fb_taper(const double2 *__restrict__ Z, double fs, int F,
+                                                   const double2 *__restrict__ tw, double2 *__restrict__ Y) {
+    constexpr int L = 2048, P = NFFT / L;
+    const int64_t f = blockIdx.y;
+    const int m = blockIdx.x * FB_T + threadIdx.x - FB_LAGS / 2;  // lag in [-1024, 1024)
+    const double g = fb_tap<P, L>(Z + f * P * L, m, fs, F, tw);
+    double2 *y = Y + f * P * L + (m & (L - 1));
 #pragma unroll
-    for (int r = 0; r < FB_P; ++r) {
+    for (int r = 0; r < P; ++r) {
         const double2 w = tw[(r * m) & (NFFT - 1)];
-        y[(int64_t)r * FB_L] = make_double2(g * w.x, g * w.y);
+        y[(int64_t)r * L] = make_double2(g * w.x, g * w.y);
     }
 }
 
-// grid (FB_P, n_filters): gains G_k / NC for k = P j + r <= NFFT / 2
+// L = 512: grid (L / FB_FS, n_filters), FB_FS slots x 4 lags per CTA.  Thread (slot n, lag t)
+// forms g_m of m = n + L t - 1024, then y_r[n] for its quarter of the P = 32 r, summed over
+// the slot's four lags.
+constexpr int FB_FS = 32;
+__global__ void __launch_bounds__(FB_FS * 4) k_fb_taper_fold(const double2 *__restrict__ Z, double fs, int F,
+                                                             const double2 *__restrict__ tw,
+                                                             double2 *__restrict__ Y) {
+    constexpr int L = 512, P = NFFT / L, FOLD = FB_LAGS / L;
+    static_assert(FOLD == 4, "four lags per slot");
+    __shared__ double gs[FOLD][FB_FS];
+    const int64_t f = blockIdx.y;
+    const int nl = threadIdx.x % FB_FS, t = threadIdx.x / FB_FS;
+    const int n = blockIdx.x * FB_FS + nl;
+    gs[t][nl] = fb_tap<P, L>(Z + f * P * L, n + L * t - FB_LAGS / 2, fs, F, tw);
+    __syncthreads();
+    double2 *y = Y + f * P * L + n;
+    for (int r = t * (P / FOLD); r < (t + 1) * (P / FOLD); ++r) {
+        double ax = 0.0, ay = 0.0;
+#pragma unroll
+        for (int u = 0; u < FOLD; ++u) {
+            const int m = n + L * u - FB_LAGS / 2;
+            const double2 w = tw[(r * m) & (NFFT - 1)];
+            ax += gs[u][nl] * w.x;
+            ay += gs[u][nl] * w.y;
+        }
+        y[(int64_t)r * L] = make_double2(ax, ay);
+    }
+}
+
+// grid (P, n_filters): gains G_k / NC for k = P j + r <= NFFT / 2
+template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_forward(const double2 *__restrict__ Y, const double2 *__restrict__ tw,
                                                      float *__restrict__ gains) {
-    __shared__ double2 d[FB_L];
+    constexpr int P = NFFT / L;
+    __shared__ double2 d[L];
     const int r = blockIdx.x;
     const int64_t f = blockIdx.y;
-    const double2 *y = Y + (f * FB_P + r) * FB_L;
-    for (int n = threadIdx.x; n < FB_L; n += FB_T) d[n] = y[n];
+    const double2 *y = Y + (f * P + r) * L;
+    for (int n = threadIdx.x; n < L; n += FB_T) d[n] = y[n];
     __syncthreads();
-    fft_2048<double2, -1, FB_T>(d, tw);
+    fb_fft<L>(d, tw, false);
     float *out = gains + f * NBIN;
-    for (int j = threadIdx.x; j < FB_L; j += FB_T) {
-        const int k = FB_P * j + r;
+    for (int j = threadIdx.x; j < L; j += FB_T) {
+        const int k = P * j + r;
         if (k <= NFFT / 2) out[k] = (float)(d[j].x / (double)NC);
     }
 }
@@ -296,17 +346,27 @@ int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, floa
     // 2.5 N log2 N flops each
     const double flops = (double)nf * 2.0 * 2.5 * NFFT * 14.0;
     static_assert(NFFT == 1 << 14, "flop count assumes log2(NFFT) = 14");
-    if (ctx->cfg.fir_len <= FB_L && nf <= 65535) {
+    if (ctx->cfg.fir_len <= FB_LAGS && nf <= 65535) {
         void *scr = nullptr;
-        int rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, (size_t)2 * nf * FB_P * FB_L * sizeof(double2), &scr);
+        int rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, (size_t)2 * nf * NFFT * sizeof(double2), &scr);
         if (rc) return rc;
-        double2 *Z = static_cast<double2 *>(scr), *Y = Z + nf * FB_P * FB_L;
+        double2 *Z = static_cast<double2 *>(scr), *Y = Z + nf * NFFT;
         KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
-        k_fb_inverse<<<dim3(FB_P, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass,
-                                                                ctx->tw64, Z);
-        k_fb_taper<<<dim3(FB_L / FB_T, (unsigned)nf), FB_T, 0, st>>>(Z, (double)ctx->cfg.fs, ctx->cfg.fir_len,
-                                                                     ctx->tw64, Y);
-        k_fb_forward<<<dim3(FB_P, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+        if (nf * (NFFT / 2048) >= 152) {  // enough filters to fill the GPU with 2048-point transforms
+            constexpr int L = 2048, P = NFFT / L;
+            k_fb_inverse<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass,
+                                                                    ctx->tw64, Z);
+            k_fb_taper<<<dim3(FB_LAGS / FB_T, (unsigned)nf), FB_T, 0, st>>>(Z, (double)ctx->cfg.fs,
+                                                                            ctx->cfg.fir_len, ctx->tw64, Y);
+            k_fb_forward<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+        } else {  // few filters: 32 transforms of 512 points each, four times the CTAs
+            constexpr int L = 512, P = NFFT / L;
+            k_fb_inverse<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass,
+                                                                    ctx->tw64, Z);
+            k_fb_taper_fold<<<dim3(L / FB_FS, (unsigned)nf), FB_FS * 4, 0, st>>>(Z, (double)ctx->cfg.fs,
+                                                                                 ctx->cfg.fir_len, ctx->tw64, Y);
+            k_fb_forward<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+        }
     } else {
         KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
         k_filter_build<<<dim3((unsigned)n_psd, n_det), NT64, (NC + 1) * sizeof(double2), st>>>(
