@@ -295,6 +295,27 @@ def run_reference(args):
                           "e2e": {"value": value, "unit": "strain-s/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return 0
+    if args.workload == "whiten":
+        wl = whiten_workload(args.n_win)
+        wl_s = dataclasses.replace(wl, n_win=(160 * wl.epoch_len) // wl.stride)
+        x, _ = inputs.make_strain(wl_s)
+        vals, total = [], 0.0
+        for i in range(args.warmup + args.steps):
+            r = oracle_whiten_sample(wl_s, x, n_epochs=128, seed=i)
+            if i >= args.warmup:
+                vals.append(r["value"])
+                total += r["seconds"]
+        value = statistics.mean(vals)
+        print(json.dumps({"metric": "strain-seconds/s Welch+filter+whitening", "impl": "reference", "value": value,
+                          "unit": "strain-s/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": wl.name, "analysed_s": wl.n_white / wl.fs},
+                          "cpu_baseline": {"value": value, "unit": "strain-s/s", "cores": r["cores"],
+                                           "kind": "oracle", "sample": r["sample"]},
+                          "e2e": {"value": value, "unit": "strain-s/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
     wl = workload_by_name(args.workload, args.n_win)
     x, _ = inputs.make_strain(wl)
     w = inputs.make_weights(wl.net, wl.weight_seed)
@@ -651,6 +672,139 @@ def run_serving(args):
     return 0
 
 
+def whiten_workload(n_win: int = 0):
+    """Six hours of seeded two-detector coloured noise in epoch mode: the Welch PSD of the
+    64 s before every 8 s epoch, its FP64 filter and the overlap-save whitening (Sec. IV.B,
+    Sec. VI).  Windows only size the whitened span (16 Hz, as the 1 h workload)."""
+    base = inputs.HOUR_RESNET34
+    n = n_win or 6 * base.n_win
+    return dataclasses.replace(base, name=f"{n * base.stride // base.fs // 3600}h-2det-welch-filter-whiten"
+                               if not n_win else f"welch-filter-whiten-{n}win", n_win=n,
+                               duration_s=n * base.stride / base.fs, n_chirps=0, seed=9876)
+
+
+def oracle_whiten_sample(wl, x: np.ndarray, n_epochs: int, seed: int = 0):
+    """The FP64 oracle's Welch + filter + direct-FIR whitening on n_epochs consecutive epochs of
+    both detectors, starting at a seeded random epoch, extrapolated to strain-seconds per second."""
+    from oracle import oracle as orc
+    e0 = int(np.random.default_rng(seed).integers(0, max(wl.n_epochs - n_epochs, 0) + 1))
+    lo = e0 * wl.epoch_len
+    xs = x[:, lo:lo + wl.psd_len + n_epochs * wl.epoch_len + wl.crop].astype(np.float64)
+    eps = list(range(n_epochs))  # epochs e0.. of x are epochs 0.. of xs
+    t0 = time.perf_counter()
+    psd = orc.psd_epochs(xs, wl, eps)
+    orc.whiten(xs, wl, psd, eps)
+    dt = time.perf_counter() - t0
+    return {"value": n_epochs * wl.epoch_len / wl.fs / dt, "unit": "strain-s/s", "cores": orc.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{n_epochs} consecutive epochs of 8 s (Welch of the 64 s before each, FP64 filter, direct "
+                      f"2047-tap FIR, 2 detectors), extrapolated per analysed second"}
+
+
+def run_whiten(args):
+    """One step = steps a1-a3 over six hours: Welch periodograms and epoch means, FP64 filter
+    build, overlap-save whitening of both detectors, device buffers resident (inputs and
+    outputs, 355 MB each, exceed the 129 MB L2); e2e adds the host copies of the raw strain and
+    of the whitened result."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_18661_gb300 import abi
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = whiten_workload(args.n_win)
+    wl_r = dataclasses.replace(wl, seed=pdist.rank_seed(wl.seed, rank)) if rank else wl
+    x, _ = inputs.make_strain(wl_r)
+    ctx = abi.Context(wl, inputs.make_weights(wl.net, wl.weight_seed))
+    xd = torch.from_numpy(x).to(dev)
+    n_psd, n_out = wl.n_epochs, wl.n_white
+    psd = torch.empty((2, n_psd, wl.nfft // 2 + 1), dtype=torch.float64, device=dev)
+    y = torch.empty((2, n_out), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.psd_estimate(xd, n_psd=n_psd, psd_step=wl.epoch_len, psd_span=wl.psd_len, out=psd)
+        ctx.whiten(xd, psd, wl.psd_len, n_out, epoch_len=wl.epoch_len, out=y)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    big = x.nbytes > (129 << 20)
+    flush = None if big else torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ctx.profile_enable(True)
+    evs = []
+    barrier()
+    for _ in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    ctx.profile_enable(False)
+    clocks = sampler.stop() if sampler else None
+    kstats = ctx.profile_read()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    sec = n_out / wl.fs
+    value, _, job_s = pdist.job_throughput(sec * args.steps, total_ms / 1000.0, world)
+    e2e = None
+    if not args.no_e2e:
+        xp = torch.from_numpy(x).pin_memory()
+        yh = torch.empty((2, n_out), dtype=torch.float32).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xd.copy_(xp, non_blocking=True)
+            step()
+            yh.copy_(y, non_blocking=True)
+            stream.synchronize()
+        barrier()
+        e2e_v, _, _ = pdist.job_throughput(sec * args.steps, time.perf_counter() - t0, world)
+        e2e = {"value": e2e_v, "unit": "strain-s/s", "h2d_bytes_per_step": int(x.nbytes),
+               "d2h_bytes_per_step": int(yh.numel() * 4)}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_whiten_sample(wl, x, n_epochs=128)
+        cpu.pop("seconds")
+    peaks = load_peaks()
+    hbm = [k for k in kstats if k["name"] in ("whiten_overlap_save", "welch_periodogram", "welch_mean")]
+    dom = max(hbm, key=lambda k: k["total_ms"])
+    per_kernel = {k["name"]: roofline_for(k, peaks, job_s * 1000.0) for k in kstats if k["launches"]}
+    out = {"metric": "strain-seconds/s Welch+filter+whitening", "value": value, "unit": "strain-s/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": job_s * 1000.0 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl.name, "analysed_s": sec, "epochs": n_psd, "n_raw": wl.n_raw,
+                      "l2": "inputs larger than L2" if big else "flushed between steps (512 MiB write)"},
+           "roofline": roofline_for(dom, peaks, job_s * 1000.0), "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(sum(k["launches"] for k in kstats)), "clocks": clocks, "kernels": per_kernel}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_resample(args):
     """One step = decimation of 1 h of two-detector strain from 16384 Hz to 2048 Hz (Sec. IV.A),
     device buffers resident; e2e adds the host copies of the raw strain and of the result."""
@@ -829,7 +983,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="hour",
-                    choices=["hour", "plain64", "timeslides", "serving", "resample", "rates"])
+                    choices=["hour", "plain64", "timeslides", "serving", "resample", "rates", "whiten"])
     ap.add_argument("--no-fp32", action="store_true", help="rates workload: BF16 only")
     ap.add_argument("--n-streams", type=int, default=128, help="streams (serving workload)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="strain per stream in the throughput phase")
@@ -858,6 +1012,8 @@ def main():
         return run_resample(args)
     if args.workload == "rates":
         return run_rates(args)
+    if args.workload == "whiten":
+        return run_whiten(args)
     return run_ours(args)
 
 

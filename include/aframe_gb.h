@@ -478,17 +478,17 @@ int afg_tiles_set(afg_ctx *ctx, const afg_tile *tiles, int32_t n);
  * x: [n_det][n] float32 (device); psd: [n_det][n_psd][8193] float64 (device).
  *
  * Memory: the periodogram scratch (AFG_NOALLOC_MAX_PERIODOGRAMS x 8193
- * doubles, 4.2 MB) and a 128 KiB twiddle table are static __device__ arrays
- * that every GPU which loads the library holds until the process exits.
+ * doubles, 4.2 MB) is a static __device__ array that every GPU which loads
+ * the library holds until the process exits.
  * This call allocates and frees nothing.  It refuses with AFG_ERR_BUDGET
  * when n_det * ((n_psd-1)*psd_step/hop + (psd_span-nfft)/hop + 1) exceeds
  * AFG_NOALLOC_MAX_PERIODOGRAMS, and with AFG_ERR_ARG on the requirements of
  * afg_psd_estimate.  AFG_ERR_CUDA if a launch or the set-up fails.
  *
  * Set-up: the first call on each device (made with that device current)
- * resolves the arrays' device addresses, configures the kernel and fills the
- * twiddle table, synchronising `stream`; make that first call before any
- * stream capture.  Later calls only launch kernels on `stream`.
+ * resolves the array's device address and configures the kernel, both
+ * synchronous runtime calls; make that first call before any stream
+ * capture.  Later calls only launch kernels on `stream`.
  *
  * Sharing: all calls on a device use the same scratch, which keeps the last
  * call's contents (every value a call reads is written earlier in that same

@@ -142,8 +142,7 @@ struct afg_ctx {
     NetPlan plan;
     float *d_params = nullptr;        // all network parameters (device)
     size_t d_params_bytes = 0;
-    float2 *tw32 = nullptr;           // exp(-2 pi i k / NFFT), k < NFFT, float
-    double2 *tw64 = nullptr;          // same in double
+    double2 *tw64 = nullptr;          // exp(-2 pi i k / NFFT), k < NFFT, double (filter build)
     int64_t bytes_held = 0;
     int *d_err = nullptr;             // device-side failure record (bounded waits that gave up)
     Workspace ws[32];
@@ -220,7 +219,7 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
                   int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, int64_t y_stride,
                   cudaStream_t st, int64_t x_stride = 0);
 cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step, int64_t psd_span,
-                          int hop, int fs, const float2 *tw, double *P, double *psd, cudaStream_t st);
+                          int hop, int fs, double *P, double *psd, cudaStream_t st);
 cudaError_t prepare_psd_kernels();
 int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st);
 int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,

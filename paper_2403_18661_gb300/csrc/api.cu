@@ -144,9 +144,8 @@ int afg_ctx_create(const afg_config *cfg, const float *weights_host, int64_t n_w
     afg_ctx *ctx = new afg_ctx();
     ctx->cfg = *cfg;
     cudaGetDevice(&ctx->device);
-    size_t tw_bytes = NFFT * (sizeof(float2) + sizeof(double2));
+    size_t tw_bytes = NFFT * sizeof(double2);
     cudaError_t e = cudaMalloc(&ctx->tw64, NFFT * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->tw32, NFFT * sizeof(float2));
     if (e != cudaSuccess) {
         cudaGetLastError();
         afg_ctx_destroy(ctx);
@@ -186,7 +185,6 @@ int afg_ctx_destroy(afg_ctx *ctx) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     for (float *t : ctx->rs_taps)
         if (t) cudaFree(t);
-    if (ctx->tw32) cudaFree(ctx->tw32);
     if (ctx->tw64) cudaFree(ctx->tw64);
     delete ctx;
     return AFG_OK;

@@ -1,14 +1,13 @@
 // Allocation-free Welch PSD entry point (afg_psd_estimate_noalloc).
 //
 // For callers that must not call cudaMalloc (see the header for who and
-// why): the periodogram scratch the Welch kernels need, and their FFT
-// twiddle table, live in file-scope __device__ arrays of fixed size that
-// every GPU loading this library holds until the process exits.  No call
-// here allocates or frees device memory.
+// why): the periodogram scratch the Welch kernels need lives in a file-scope
+// __device__ array of fixed size that every GPU loading this library holds
+// until the process exits.  No call here allocates or frees device memory.
 //
-// Host code must not use the arrays' names as device addresses (on the host
-// they are stand-in symbols); the addresses are looked up once per device
-// with cudaGetSymbolAddress in setup() and passed to the kernels.
+// Host code must not use the array's name as a device address (on the host
+// it is a stand-in symbol); the address is looked up once per device with
+// cudaGetSymbolAddress in setup() and passed to the kernels.
 #include <mutex>
 
 #include "afg_internal.cuh"
@@ -20,42 +19,26 @@ constexpr int kMaxDevices = 64;
 
 // periodogram scratch: [n_det][n_seg][NBIN] doubles, n_det * n_seg <= kMaxPeriodograms (4.2 MB)
 static __device__ __align__(256) double g_noalloc_periodograms[kMaxPeriodograms * NBIN];
-// exp(-2 pi i k / NFFT), k < NFFT, float (128 KiB)
-static __device__ __align__(256) float2 g_noalloc_twiddles[NFFT];
-
-__global__ void k_noalloc_twiddles() {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= NFFT) return;
-    double s, c;
-    sincospi(2.0 * (double)k / (double)NFFT, &s, &c);
-    g_noalloc_twiddles[k] = make_float2((float)c, (float)-s);
-}
 
 struct DeviceState {
     bool ready = false;
     double *scratch = nullptr;
-    float2 *twiddles = nullptr;
 };
 
 DeviceState g_dev[kMaxDevices];
 std::mutex g_mu;
 
-// Once per device, with that device current: resolve the arrays' device
-// addresses, opt the periodogram kernel into its shared memory and fill the
-// twiddle table (synchronising `st`, so this must not run under stream capture).
-int setup(int dev, cudaStream_t st, DeviceState **out) {
+// Once per device, with that device current: resolve the array's device
+// address and opt the periodogram kernel into its shared memory (both
+// synchronous runtime calls, so this must not run under stream capture).
+int setup(int dev, DeviceState **out) {
     std::lock_guard<std::mutex> lock(g_mu);
     DeviceState &s = g_dev[dev];
     if (!s.ready) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_periodograms) != cudaSuccess) return AFG_ERR_CUDA;
         s.scratch = static_cast<double *>(p);
-        if (cudaGetSymbolAddress(&p, g_noalloc_twiddles) != cudaSuccess) return AFG_ERR_CUDA;
-        s.twiddles = static_cast<float2 *>(p);
         if (prepare_psd_kernels() != cudaSuccess) return AFG_ERR_CUDA;
-        k_noalloc_twiddles<<<NFFT / 256, 256, 0, st>>>();
-        if (cudaGetLastError() != cudaSuccess) return AFG_ERR_CUDA;
-        if (cudaStreamSynchronize(st) != cudaSuccess) return AFG_ERR_CUDA;
         s.ready = true;
     }
     *out = &s;
@@ -78,11 +61,11 @@ extern "C" int afg_psd_estimate_noalloc(const float *x, int64_t n, int32_t n_det
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AFG_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     DeviceState *s = nullptr;
-    int rc = setup(dev, st, &s);
+    int rc = setup(dev, &s);
     if (rc != AFG_OK) return rc;
     // every periodogram the mean reads is written earlier in the same call,
     // so the scratch needs no clearing between calls
-    if (launch_psd_on(x, n, n_det, n_psd, psd_step, psd_span, hop, fs, s->twiddles, s->scratch, psd, st) !=
+    if (launch_psd_on(x, n, n_det, n_psd, psd_step, psd_span, hop, fs, s->scratch, psd, st) !=
         cudaSuccess)
         return AFG_ERR_CUDA;
     return AFG_OK;

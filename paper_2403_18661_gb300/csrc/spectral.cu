@@ -3,11 +3,13 @@
 // 0.5 s crop at each edge; Sec. VI: PSD from the first 64 s of state).
 //
 // Kernels
-//   k_twiddles        exp(-2 pi i k / NFFT) tables in double and float
+//   k_twiddles        exp(-2 pi i k / NFFT) table in double (filter build)
 //   k_periodogram     one Hann-windowed segment per CTA: FP32 real FFT in
-//                     shared memory, |X_k|^2 formed and stored in FP64
-//   k_psd_mean        FP64 mean over the K segments of each epoch, density
-//                     scaling and one-sided doubling
+//                     shared memory (radix-16 passes, fft16.cuh), |X_k|^2
+//                     formed and stored in FP64
+//   k_psd_mean        FP64 mean over the K segments of each epoch (a sliding
+//                     sum over a run of epochs per thread), density scaling
+//                     and one-sided doubling
 //   k_filter_build    one (detector, epoch) per CTA, all FP64: amplitude
 //                     response psd^-1/2 above the highpass, zero-phase
 //                     inverse real FFT, Hann taper of F taps, sqrt(2/fs),
@@ -15,65 +17,115 @@
 //   k_whiten          one 8192-output overlap-save block per CTA: FP32 real
 //                     FFT of 8192 + F - 1 samples (zero padded to NFFT),
 //                     multiply by the epoch's gains, inverse FFT, keep the
-//                     outputs whose support lies inside the block.
+//                     outputs whose support lies inside the block.  The
+//                     forward transform's last pass, the split, the gains,
+//                     the inverse split and the inverse transform's first
+//                     pass are one fused shared-memory pass.
 #include <math.h>
 #include <stdio.h>
 
 #include "afg_internal.cuh"
 #include "fft.cuh"
+#include "fft16.cuh"
 
 namespace {
 
-constexpr int NT32 = 512;   // threads of the FP32 FFT kernels
 constexpr int NT64 = 1024;  // threads of the FP64 filter kernel
 
-__global__ void k_twiddles(float2 *tw32, double2 *tw64) {
+__global__ void k_twiddles(double2 *tw64) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= NFFT) return;
     double s, c;
     sincospi(2.0 * (double)k / (double)NFFT, &s, &c);
     tw64[k] = make_double2(c, -s);
-    tw32[k] = make_float2((float)c, (float)-s);
 }
 
-// grid (n_seg, n_det); segment g of detector d covers x[d][g*hop, g*hop + NFFT)
-__global__ void __launch_bounds__(NT32) k_periodogram(const float *__restrict__ x, int64_t x_stride, int hop,
-                                                       const float2 *__restrict__ tw, double *__restrict__ P,
-                                                       int64_t n_seg) {
+// Forward radix-2 pass (Ns = 4096) and real-FFT split for task j of the
+// Welch kernel, 1 <= j <= 2048: the butterflies j and 4096 - j give Z at
+// j, j + 4096, 4096 - j and 8192 - j, i.e. the split pairs (j, NC - j) and
+// (j + 4096, 4096 - j); |X_k|^2 of those four bins goes to P in FP64.
+// (At j = 2048 the two butterflies coincide and only the first pair is kept.)
+__device__ __forceinline__ void welch_mid_task(const float2 *d, int j, double *P) {
+    using namespace r16;
+    const float2 a = d[pad(j)], b = d[pad(j + 4096)], c = d[pad(4096 - j)], e = d[pad(8192 - j)];
+    const float2 w = cis<-1>((float)j / 8192.0f);  // W^j
+    const float2 u = cis<-1>((float)j / 4096.0f);  // radix-2 twiddle of butterfly j
+    const float2 u2 = make_float2(-u.x, u.y);      // of butterfly 4096 - j: -conj(u)
+    const float2 ub = cmul(u, b), ue = cmul(u2, e);
+    const float2 zj = cadd(a, ub), zj4 = csub(a, ub), zc = cadd(c, ue), zc4 = csub(c, ue);
+    float2 x1, x1n, x2, x2n;
+    split_fwd(zj, zc4, w, x1, x1n);             // bins j, 8192 - j
+    split_fwd(zj4, zc, mul_i<-1>(w), x2, x2n);  // bins j + 4096, 4096 - j (W^{j+4096} = -i W^j)
+    auto p2 = [](float2 x) { return (double)x.x * (double)x.x + (double)x.y * (double)x.y; };
+    P[j] = p2(x1);
+    P[8192 - j] = p2(x1n);
+    if (j < 2048) {
+        P[j + 4096] = p2(x2);
+        P[4096 - j] = p2(x2n);
+    }
+}
+
+// grid (n_seg, n_det), r16::NT threads; segment g of detector d covers x[d][g*hop, g*hop + NFFT)
+__global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restrict__ x, int64_t x_stride, int hop,
+                                                             double *__restrict__ P, int64_t n_seg) {
+    using namespace r16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *d = reinterpret_cast<float2 *>(smem_raw);
     const int64_t g = blockIdx.x;
     const int det = blockIdx.y;
+    const int t = threadIdx.x;
     const float *src = x + det * x_stride + g * (int64_t)hop;
-    for (int j = threadIdx.x; j < NC; j += NT32) {
-        int i0 = 2 * j, i1 = 2 * j + 1;
-        // periodic Hann window w_i = 1/2 - 1/2 cos(2 pi i / NFFT)
-        float w0 = 0.5f - 0.5f * cospif(2.0f * (float)i0 / (float)NFFT);
-        float w1 = 0.5f - 0.5f * cospif(2.0f * (float)i1 / (float)NFFT);
-        d[j] = make_float2(src[i0] * w0, src[i1] * w1);
+    // z_n = w_2n x_2n + i w_2n+1 x_2n+1 with the periodic Hann window
+    // w_i = 1/2 - 1/2 cos(2 pi i / NFFT), n = t + 512 r (the first pass's inputs)
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int i0 = 2 * (t + NT * r), i1 = i0 + 1;
+        const float w0 = 0.5f - 0.5f * cospif(2.0f * (float)i0 / (float)NFFT);
+        const float w1 = 0.5f - 0.5f * cospif(2.0f * (float)i1 / (float)NFFT);
+        v[r] = make_float2(src[i0] * w0, src[i1] * w1);
     }
-    __syncthreads();
-    fft_nc<float2, -1, NT32>(d, tw);
-    real_split_forward<float2, NT32>(d, tw);
+    forward_r16(d, v);
     double *out = P + ((int64_t)det * n_seg + g) * NBIN;
-    for (int k = threadIdx.x; k < NBIN; k += NT32) {
-        double re = (double)d[k].x, im = (double)d[k].y;
-        out[k] = re * re + im * im;
+    if (t == 0) {
+        // butterfly 0: Z_0, Z_4096; bins 0, NC (from the self-pair k = 0) and 4096
+        const float2 a = d[pad(0)], b = d[pad(4096)];
+        float2 x0, xn, x4, x4d;
+        split_fwd(cadd(a, b), cadd(a, b), make_float2(1.0f, 0.0f), x0, xn);
+        split_fwd(csub(a, b), csub(a, b), make_float2(0.0f, -1.0f), x4, x4d);
+        out[0] = (double)x0.x * x0.x + (double)x0.y * x0.y;
+        out[NC] = (double)xn.x * xn.x + (double)xn.y * xn.y;
+        out[4096] = (double)x4.x * x4.x + (double)x4.y * x4.y;
+    } else {
+        welch_mid_task(d, t, out);
     }
+#pragma unroll
+    for (int m = 1; m < 4; ++m) welch_mid_task(d, t + NT * m, out);
+    if (t == NT - 1) welch_mid_task(d, 2048, out);
 }
 
-// grid (ceil(NBIN/256), n_psd, n_det)
+constexpr int PSD_EPT = 16;  // epochs per thread of k_psd_mean
+
+// grid (ceil(NBIN/256), ceil(n_psd/PSD_EPT), n_det): bin k of epochs
+// [e0, e0 + PSD_EPT) as a sliding FP64 sum over the periodograms (epoch e
+// averages segments [e seg_step, e seg_step + K))
 __global__ void k_psd_mean(const double *__restrict__ P, int64_t n_seg, int seg_step, int K, double scale,
                            double *__restrict__ psd, int64_t n_psd) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= NBIN) return;
-    int64_t e = blockIdx.y;
-    int det = blockIdx.z;
-    const double *src = P + ((int64_t)det * n_seg + e * seg_step) * NBIN + k;
+    const int64_t e0 = (int64_t)blockIdx.y * PSD_EPT;
+    const int det = blockIdx.z;
+    const double *src = P + (int64_t)det * n_seg * NBIN + k;
+    double *dst = psd + (int64_t)det * n_psd * NBIN + k;
+    const double onesided = (k == 0 || k == NFFT / 2) ? 1.0 : 2.0;
     double acc = 0.0;
-    for (int q = 0; q < K; ++q) acc += src[(int64_t)q * NBIN];
-    double onesided = (k == 0 || k == NFFT / 2) ? 1.0 : 2.0;
-    psd[((int64_t)det * n_psd + e) * NBIN + k] = onesided * acc * scale;
+    for (int q = 0; q < K; ++q) acc += src[(e0 * seg_step + q) * NBIN];
+    dst[e0 * NBIN] = onesided * acc * scale;
+    for (int64_t e = e0 + 1; e < e0 + PSD_EPT && e < n_psd; ++e) {
+        const int64_t s_old = (e - 1) * seg_step, s_new = s_old + K;
+        for (int q = 0; q < seg_step; ++q) acc += src[(s_new + q) * NBIN] - src[(s_old + q) * NBIN];
+        dst[e * NBIN] = onesided * acc * scale;
+    }
 }
 
 // grid (n_psd, n_det); builds the whitening gains of one (detector, epoch)
@@ -245,43 +297,125 @@ __global__ void __launch_bounds__(FB_T) k_fb_forward(const double2 *__restrict__
     }
 }
 
+// 4-byte asynchronous copy global -> shared (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// Fused mid pass of the whitening kernel for task j, 1 <= j <= 2048: the
+// forward radix-2 butterflies j and 4096 - j (Ns = 4096) give Z at j,
+// j + 4096, 4096 - j, 8192 - j; the split pairs (j, NC - j) and
+// (j + 4096, 4096 - j) are multiplied by the gains g and split back; the
+// inverse radix-2 butterflies j and 4096 - j (Ns = 1) produce o[0..1] for
+// d[2j], d[2j + 1] and o[2..3] for d[2(4096 - j)], d[2(4096 - j) + 1].
+__device__ __forceinline__ void whiten_mid_task(const float2 *d, const float *g, int j, float2 (&o)[4]) {
+    using namespace r16;
+    const float2 a = d[pad(j)], b = d[pad(j + 4096)], c = d[pad(4096 - j)], e = d[pad(8192 - j)];
+    const float2 w = cis<-1>((float)j / 8192.0f);  // W^j
+    const float2 u = cis<-1>((float)j / 4096.0f);  // radix-2 twiddle of butterfly j
+    const float2 u2 = make_float2(-u.x, u.y);      // of butterfly 4096 - j
+    const float2 ub = cmul(u, b), ue = cmul(u2, e);
+    const float2 zj = cadd(a, ub), zj4 = csub(a, ub), zc = cadd(c, ue), zc4 = csub(c, ue);
+    const float2 w4 = mul_i<-1>(w);                // W^{j + 4096}
+    float2 x1, x1n, x2, x2n, p1, p1n, p2, p2n;
+    split_fwd(zj, zc4, w, x1, x1n);
+    split_fwd(zj4, zc, w4, x2, x2n);
+    split_inv(cscale(x1, g[j]), cscale(x1n, g[8192 - j]), w, p1, p1n);        // Z'_j, Z'_{8192-j}
+    split_inv(cscale(x2, g[j + 4096]), cscale(x2n, g[4096 - j]), w4, p2, p2n);  // Z'_{j+4096}, Z'_{4096-j}
+    o[0] = cadd(p1, p2);
+    o[1] = csub(p1, p2);
+    o[2] = cadd(p2n, p1n);
+    o[3] = csub(p2n, p1n);
+}
+
+// Task 0 of the mid pass: butterfly 0 gives Z_0 and Z_4096, each its own
+// split partner (bin 0 with the Nyquist bin NC, and bin 4096); o[0..1] go to d[0], d[1].
+__device__ __forceinline__ void whiten_mid_task0(const float2 *d, const float *g, float2 (&o)[4]) {
+    using namespace r16;
+    const float2 a = d[pad(0)], b = d[pad(4096)];
+    const float2 z0 = cadd(a, b), z4 = csub(a, b);
+    const float2 one = make_float2(1.0f, 0.0f), mi = make_float2(0.0f, -1.0f);  // W^0, W^4096
+    float2 x0, xn, x4, x4d, p0, pn, p4, p4d;
+    split_fwd(z0, z0, one, x0, xn);
+    split_inv(cscale(x0, g[0]), cscale(xn, g[NC]), one, p0, pn);
+    split_fwd(z4, z4, mi, x4, x4d);
+    split_inv(cscale(x4, g[4096]), cscale(x4d, g[4096]), mi, p4, p4d);
+    o[0] = cadd(p0, p4);
+    o[1] = csub(p0, p4);
+    o[2] = o[0];
+    o[3] = o[1];
+}
+
+constexpr int WHITEN_SMEM = r16::SLOTS * (int)sizeof(float2) + NBIN * (int)sizeof(float);
+constexpr int WELCH_SMEM = r16::SLOTS * (int)sizeof(float2);
+
 // One overlap-save block: the FIR of src[0 .. WB + F - 1) (samples past
 // `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value).
-// d: NC + 1 float2 of shared memory.
+// smem: r16::SLOTS float2 for the transform, then NBIN floats for the gains gk,
+// which are copied in asynchronously while the forward transform runs.
 template <typename Out>
-__device__ __forceinline__ void whiten_block(float2 *d, const float *__restrict__ src, int64_t avail,
-                                             const float *__restrict__ gk, int F, int64_t cnt,
-                                             const float2 *__restrict__ tw, Out out) {
+__device__ __forceinline__ void whiten_block(unsigned char *smem, const float *__restrict__ src, int64_t avail,
+                                             const float *__restrict__ gk, int F, int64_t cnt, Out out) {
+    using namespace r16;
+    float2 *d = reinterpret_cast<float2 *>(smem);
+    float *gs = reinterpret_cast<float *>(smem + SLOTS * sizeof(float2));
+    const int t = threadIdx.x;
+    for (int k = t; k < NBIN; k += NT) cp_async4(gs + k, gk + k);
     const int half = F / 2;
     const int64_t need = WB + F - 1;  // samples that reach a kept output
-    for (int j = threadIdx.x; j < NC; j += NT32) {
-        int64_t i0 = 2 * (int64_t)j, i1 = i0 + 1;
-        float a = (i0 < need && i0 < avail) ? src[i0] : 0.0f;
-        float b = (i1 < need && i1 < avail) ? src[i1] : 0.0f;
-        d[j] = make_float2(a, b);
+    const int64_t lim = need < avail ? need : avail;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int64_t i0 = 2 * (int64_t)(t + NT * r);
+        v[r] = make_float2(i0 < lim ? src[i0] : 0.0f, i0 + 1 < lim ? src[i0 + 1] : 0.0f);
+    }
+    forward_r16(d, v);
+    cp_async_wait_all();
+    __syncthreads();
+    float2 o[4][4], ox[4];
+    if (t == 0) whiten_mid_task0(d, gs, o[0]);
+    else whiten_mid_task(d, gs, t, o[0]);
+#pragma unroll
+    for (int m = 1; m < 4; ++m) whiten_mid_task(d, gs, t + NT * m, o[m]);
+    if (t == NT - 1) whiten_mid_task(d, gs, 2048, ox);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int j = t + NT * m, jc = 4096 - j;
+        d[pad(2 * j)] = o[m][0];
+        d[pad(2 * j + 1)] = o[m][1];
+        if (j != 0) {
+            d[pad(2 * jc)] = o[m][2];
+            d[pad(2 * jc + 1)] = o[m][3];
+        }
+    }
+    if (t == NT - 1) {
+        d[pad(4096)] = ox[0];
+        d[pad(4097)] = ox[1];
     }
     __syncthreads();
-    fft_nc<float2, -1, NT32>(d, tw);
-    real_split_forward<float2, NT32>(d, tw);
-    for (int k = threadIdx.x; k < NBIN; k += NT32) {
-        float gv = gk[k];
-        d[k] = make_float2(d[k].x * gv, d[k].y * gv);
+    inverse_r16(d, v);
+    // complex sample c = t + 512 q holds real samples 2c, 2c + 1; output q0 = 2c - F/2
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float2 y = v[out16(q)];
+        const int64_t q0 = 2 * (int64_t)(t + NT * q) - half;
+        if (q0 >= 0 && q0 < cnt) out(q0, y.x);
+        if (q0 + 1 >= 0 && q0 + 1 < cnt) out(q0 + 1, y.y);
     }
-    __syncthreads();
-    real_split_inverse<float2, NT32>(d, tw);
-    fft_nc<float2, +1, NT32>(d, tw);
-    const float *t = reinterpret_cast<const float *>(d);
-    for (int q = threadIdx.x; q < cnt; q += NT32) out(q, t[q + half]);
 }
 
 // grid (n_blocks, n_det); block b produces y[d][b*WB, min((b+1)*WB, out_len))
-__global__ void __launch_bounds__(NT32) k_whiten(const float *__restrict__ x, int64_t n, int64_t x_stride,
-                                                  const float *__restrict__ gains, int64_t n_psd,
-                                                  int64_t out_first, int64_t out_len, int64_t epoch_len, int F,
-                                                  const float2 *__restrict__ tw, float *__restrict__ y,
-                                                  int64_t y_stride) {
+__global__ void __launch_bounds__(r16::NT, 2) k_whiten(const float *__restrict__ x, int64_t n, int64_t x_stride,
+                                                        const float *__restrict__ gains, int64_t n_psd,
+                                                        int64_t out_first, int64_t out_len, int64_t epoch_len, int F,
+                                                        float *__restrict__ y, int64_t y_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *d = reinterpret_cast<float2 *>(smem_raw);
     const int64_t o = (int64_t)blockIdx.x * WB;
     const int det = blockIdx.y;
     int64_t e = 0;
@@ -293,7 +427,7 @@ __global__ void __launch_bounds__(NT32) k_whiten(const float *__restrict__ x, in
     int64_t cnt = out_len - o;
     if (cnt > WB) cnt = WB;
     float *dst = y + det * y_stride + o;
-    whiten_block(d, x + det * x_stride + s0, n - s0, gains + ((int64_t)det * n_psd + e) * NBIN, F, cnt, tw,
+    whiten_block(smem_raw, x + det * x_stride + s0, n - s0, gains + ((int64_t)det * n_psd + e) * NBIN, F, cnt,
                  [dst](int64_t q, float v) { dst[q] = v; });
 }
 
@@ -302,15 +436,13 @@ __global__ void __launch_bounds__(NT32) k_whiten(const float *__restrict__ x, in
 // gains desc.gains + d * NBIN into the mirrored ring desc.y (row stride
 // y_stride, ring length y_ring): output q goes to ring slots
 // (y_pos + q) mod y_ring and that + y_ring.
-__global__ void __launch_bounds__(NT32) k_whiten_multi(const WhitenPiece *__restrict__ pieces, int F,
-                                                        const float2 *__restrict__ tw) {
+__global__ void __launch_bounds__(r16::NT, 2) k_whiten_multi(const WhitenPiece *__restrict__ pieces, int F) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *d = reinterpret_cast<float2 *>(smem_raw);
     const WhitenPiece pc = pieces[blockIdx.x];
     const int det = blockIdx.y;
     float *yr = pc.y + det * pc.y_stride;
     const int64_t ring = pc.y_ring, pos = pc.y_pos;
-    whiten_block(d, pc.x + det * pc.x_stride, pc.cnt + F - 1, pc.gains + det * NBIN, F, pc.cnt, tw,
+    whiten_block(smem_raw, pc.x + det * pc.x_stride, pc.cnt + F - 1, pc.gains + det * NBIN, F, pc.cnt,
                  [yr, ring, pos](int64_t q, float v) {
                      int64_t m = pos + q;
                      if (m >= ring) m -= ring;
@@ -323,12 +455,9 @@ bool g_attrs_set = false;
 
 int set_attrs(afg_ctx *ctx) {
     if (g_attrs_set) return AFG_OK;
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((NC + 1) * sizeof(float2))));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((NC + 1) * sizeof(float2))));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((NC + 1) * sizeof(float2))));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize, WELCH_SMEM));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize, WHITEN_SMEM));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, WHITEN_SMEM));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_filter_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((NC + 1) * sizeof(double2))));
     g_attrs_set = true;
@@ -378,8 +507,8 @@ int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, floa
 
 int afg_make_twiddles(afg_ctx *ctx) {
     {
-        KScope ks(ctx, 0, KK_TWIDDLES, 0.0, (double)NFFT * (sizeof(float2) + sizeof(double2)));
-        k_twiddles<<<NFFT / 256, 256>>>(ctx->tw32, ctx->tw64);
+        KScope ks(ctx, 0, KK_TWIDDLES, 0.0, (double)NFFT * sizeof(double2));
+        k_twiddles<<<NFFT / 256, 256>>>(ctx->tw64);
     }
     AFG_LAUNCH_CHECK(ctx, "k_twiddles");
     return set_attrs(ctx);
@@ -399,16 +528,15 @@ int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd
     {
         // one read of every segment, one FP64 periodogram written per segment
         KScope ks(ctx, st, KK_PERIODOGRAM, 0.0, (double)n_det * n_seg * (NFFT * 4.0 + NBIN * 8.0));
-        k_periodogram<<<dim3((unsigned)n_seg, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(x, x_stride, hop,
-                                                                                              ctx->tw32, P, n_seg);
+        k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, x_stride, hop, P, n_seg);
     }
     AFG_LAUNCH_CHECK(ctx, "k_periodogram");
     // periodic Hann: sum w^2 = 3 NFFT / 8
     const double scale = 1.0 / ((double)K * (double)ctx->cfg.fs * (3.0 * NFFT / 8.0));
     {
         KScope ks(ctx, st, KK_PSD_MEAN, 0.0, (double)n_det * (n_seg + n_psd) * NBIN * 8.0);
-        k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)n_psd, n_det), 256, 0, st>>>(P, n_seg, (int)seg_step,
-                                                                                      (int)K, scale, psd, n_psd);
+        k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)((n_psd + PSD_EPT - 1) / PSD_EPT), n_det), 256, 0, st>>>(
+            P, n_seg, (int)seg_step, (int)K, scale, psd, n_psd);
     }
     AFG_LAUNCH_CHECK(ctx, "k_psd_mean");
     return AFG_OK;
@@ -429,8 +557,9 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
         // algorithmic: read the cropped span once, write the output once, read the gains
         const double F = ctx->cfg.fir_len;
         KScope ks(ctx, st, KK_WHITEN, 0.0, (double)n_det * ((2.0 * out_len + F - 1.0) * 4.0 + n_psd * NBIN * 4.0));
-        k_whiten<<<dim3((unsigned)nb, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(
-            x, n, x_stride, gains, n_psd, out_first, out_len, epoch_len, ctx->cfg.fir_len, ctx->tw32, y, y_stride);
+        k_whiten<<<dim3((unsigned)nb, n_det), r16::NT, WHITEN_SMEM, st>>>(x, n, x_stride, gains, n_psd, out_first,
+                                                                          out_len, epoch_len, ctx->cfg.fir_len, y,
+                                                                          y_stride);
     }
     AFG_LAUNCH_CHECK(ctx, "k_whiten");
     return AFG_OK;
@@ -446,8 +575,7 @@ int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_piece
     if (n_pieces <= 0) return AFG_OK;
     const double F = ctx->cfg.fir_len;
     KScope ks(ctx, st, KK_WHITEN, 0.0, 2.0 * ((2.0 * total_out + n_pieces * (F - 1.0)) * 4.0 + n_pieces * NBIN * 4.0));
-    k_whiten_multi<<<dim3((unsigned)n_pieces, 2), NT32, (NC + 1) * sizeof(float2), st>>>(pieces_dev, ctx->cfg.fir_len,
-                                                                                        ctx->tw32);
+    k_whiten_multi<<<dim3((unsigned)n_pieces, 2), r16::NT, WHITEN_SMEM, st>>>(pieces_dev, ctx->cfg.fir_len);
     AFG_LAUNCH_CHECK(ctx, "k_whiten_multi");
     return AFG_OK;
 }
@@ -455,21 +583,20 @@ int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_piece
 // The Welch kernels on caller-provided scratch and twiddles (no workspace,
 // no context, no accounting).  P must hold n_det * n_seg * NBIN doubles.
 cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, int64_t psd_step, int64_t psd_span,
-                          int hop, int fs, const float2 *tw, double *P, double *psd, cudaStream_t st) {
+                          int hop, int fs, double *P, double *psd, cudaStream_t st) {
     const int64_t K = (psd_span - NFFT) / hop + 1;
     const int64_t seg_step = n_psd > 1 ? psd_step / hop : 0;
     const int64_t n_seg = (n_psd - 1) * seg_step + K;
-    k_periodogram<<<dim3((unsigned)n_seg, n_det), NT32, (NC + 1) * sizeof(float2), st>>>(x, n, hop, tw, P, n_seg);
+    k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, n, hop, P, n_seg);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const double scale = 1.0 / ((double)K * (double)fs * (3.0 * NFFT / 8.0));
-    k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)n_psd, n_det), 256, 0, st>>>(P, n_seg, (int)seg_step, (int)K,
-                                                                                  scale, psd, n_psd);
+    k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)((n_psd + PSD_EPT - 1) / PSD_EPT), n_det), 256, 0, st>>>(
+        P, n_seg, (int)seg_step, (int)K, scale, psd, n_psd);
     return cudaGetLastError();
 }
 
-// Opt the periodogram kernel into its 64 KiB of dynamic shared memory on the current device.
+// Opt the periodogram kernel into its 68 KiB of dynamic shared memory on the current device.
 cudaError_t prepare_psd_kernels() {
-    return cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((NC + 1) * sizeof(float2)));
+    return cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize, WELCH_SMEM);
 }

@@ -68,6 +68,20 @@ def test_psd_epochs_share_segments(c1, ctx_tiny):
             assert np.max(np.abs(got[d, e] - ref) / ref) < PSD_RTOL
 
 
+def test_psd_many_epochs(ctx_tiny):
+    # 40 epochs every 4 s, each the mean of 15 segments (64 s, as in the epoch workloads): the
+    # per-thread runs of epochs of the averaging kernel end at epochs 16 and 32 and leave a
+    # partial last run
+    n_psd, step, span = 40, 8192, 131072
+    x = np.stack([inputs.coloured_noise(step * (n_psd - 1) + span, 31 + d, inputs.NoiseModel(), 2048)
+                  for d in range(2)]).astype(np.float32)
+    got = ctx_tiny.psd_estimate(_dev(x), n_psd=n_psd, psd_step=step, psd_span=span).cpu().numpy()
+    for d in range(2):
+        for e in range(n_psd):
+            ref = orc.welch(x[d, e * step: e * step + span].astype(np.float64), 16384, 8192, 2048.0)
+            assert np.max(np.abs(got[d, e] - ref) / ref) < PSD_RTOL, (d, e)
+
+
 def test_whiten_with_oracle_psd(c1, ctx_tiny):
     wl, x, w, ref = c1
     psd = _dev(ref["psd"])
