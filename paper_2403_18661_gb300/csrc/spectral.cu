@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict_
 //   forward:  G_{P j + r} = sum_n y_r[n] e^{-2 pi i j n / L},
 //             y_r[n] = sum_{m = n mod L} g_m e^{-2 pi i r m / N}   (P forward FFTs of L points;
 //             at L = 2048 each slot n holds one lag, at L = 512 it folds four)
-// The same FP64 arithmetic as k_filter_build, on 2 P CTAs per filter instead of one.
+// The same FP64 arithmetic as k_filter_build (up to rounding order), on many CTAs per filter
+// instead of one; the inverse and forward stages each pair two sub-transforms into one
+// complex FFT (real amplitude response; Hermitian folded taps), P / 2 CTAs per stage.
 constexpr int FB_LAGS = 2048;  // lags m in [-FB_LAGS / 2, FB_LAGS / 2)
 constexpr int FB_T = 256;
 
@@ -194,26 +196,33 @@ __device__ __forceinline__ void fb_fft(double2 *d, const double2 *tw, bool inver
     }
 }
 
-// grid (P, n_filters): Z_r of filter f = det * n_psd + e
+// grid (P / 2, n_filters): Z_r and Z_{r + P/2} of filter f = det * n_psd + e from one
+// complex transform.  Both inputs A_{P j + r} are real, so each Z is Hermitian and
+// C = IFFT(A_r + i A_{r'}) splits as Z_r[n] = (C[n] + conj C[-n]) / 2,
+// Z_{r'}[n] = (C[n] - conj C[-n]) / 2i.
 template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ psd, double fs, double f_hp,
                                                      const double2 *__restrict__ tw, double2 *__restrict__ Z) {
     constexpr int P = NFFT / L;
     __shared__ double2 d[L];
-    const int r = blockIdx.x;
+    const int r1 = blockIdx.x, r2 = r1 + P / 2;
     const int64_t f = blockIdx.y;
     const double *p = psd + f * NBIN;
-    for (int j = threadIdx.x; j < L; j += FB_T) {
-        const int k = P * j + r;
+    auto amp = [&](int k) {
         const int kk = k <= NFFT / 2 ? k : NFFT - k;  // the amplitude response is even in k
         const double fr = (double)kk * fs / (double)NFFT;
         const double pk = p[kk];
-        d[j] = make_double2((fr >= f_hp && pk > 0.0) ? 1.0 / sqrt(pk) : 0.0, 0.0);
-    }
+        return (fr >= f_hp && pk > 0.0) ? 1.0 / sqrt(pk) : 0.0;
+    };
+    for (int j = threadIdx.x; j < L; j += FB_T) d[j] = make_double2(amp(P * j + r1), amp(P * j + r2));
     __syncthreads();
     fb_fft<L>(d, tw, true);
-    double2 *z = Z + (f * P + r) * L;
-    for (int n = threadIdx.x; n < L; n += FB_T) z[n] = d[n];
+    double2 *z1 = Z + (f * P + r1) * L, *z2 = Z + (f * P + r2) * L;
+    for (int n = threadIdx.x; n < L; n += FB_T) {
+        const double2 c = d[n], cm = d[(L - n) & (L - 1)];
+        z1[n] = make_double2(0.5 * (c.x + cm.x), 0.5 * (c.y - cm.y));
+        z2[n] = make_double2(0.5 * (c.y + cm.y), -0.5 * (c.x - cm.x));
+    }
 }
 
 // g_m of lag m from the P partial transforms (slot m mod L)
@@ -278,22 +287,28 @@ __global__ void __launch_bounds__(FB_FS * 4) k_fb_taper_fold(const double2 *__re
     }
 }
 
-// grid (P, n_filters): gains G_k / NC for k = P j + r <= NFFT / 2
+// grid (P / 2, n_filters): gains G_k / NC for k = P j + r <= NFFT / 2, r and r + P/2 from
+// one complex transform.  The taps are even, so each y_r is Hermitian and its transform
+// real: FFT(y_r + i y_{r'}) = G_{P j + r} + i G_{P j + r'}.
 template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_forward(const double2 *__restrict__ Y, const double2 *__restrict__ tw,
                                                      float *__restrict__ gains) {
     constexpr int P = NFFT / L;
     __shared__ double2 d[L];
-    const int r = blockIdx.x;
+    const int r1 = blockIdx.x, r2 = r1 + P / 2;
     const int64_t f = blockIdx.y;
-    const double2 *y = Y + (f * P + r) * L;
-    for (int n = threadIdx.x; n < L; n += FB_T) d[n] = y[n];
+    const double2 *y1 = Y + (f * P + r1) * L, *y2 = Y + (f * P + r2) * L;
+    for (int n = threadIdx.x; n < L; n += FB_T) {
+        const double2 a = y1[n], b = y2[n];
+        d[n] = make_double2(a.x - b.y, a.y + b.x);
+    }
     __syncthreads();
     fb_fft<L>(d, tw, false);
     float *out = gains + f * NBIN;
     for (int j = threadIdx.x; j < L; j += FB_T) {
-        const int k = P * j + r;
-        if (k <= NFFT / 2) out[k] = (float)(d[j].x / (double)NC);
+        const int k1 = P * j + r1, k2 = P * j + r2;
+        if (k1 <= NFFT / 2) out[k1] = (float)(d[j].x / (double)NC);
+        if (k2 <= NFFT / 2) out[k2] = (float)(d[j].y / (double)NC);
     }
 }
 
@@ -483,18 +498,18 @@ int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, floa
         KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
         if (nf * (NFFT / 2048) >= 152) {  // enough filters to fill the GPU with 2048-point transforms
             constexpr int L = 2048, P = NFFT / L;
-            k_fb_inverse<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass,
-                                                                    ctx->tw64, Z);
+            k_fb_inverse<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs,
+                                                                        ctx->cfg.f_highpass, ctx->tw64, Z);
             k_fb_taper<<<dim3(FB_LAGS / FB_T, (unsigned)nf), FB_T, 0, st>>>(Z, (double)ctx->cfg.fs,
                                                                             ctx->cfg.fir_len, ctx->tw64, Y);
-            k_fb_forward<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
-        } else {  // few filters: 32 transforms of 512 points each, four times the CTAs
+            k_fb_forward<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+        } else {  // few filters: 32 sub-transforms of 512 points each (16 paired transforms per stage)
             constexpr int L = 512, P = NFFT / L;
-            k_fb_inverse<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs, ctx->cfg.f_highpass,
-                                                                    ctx->tw64, Z);
+            k_fb_inverse<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs,
+                                                                        ctx->cfg.f_highpass, ctx->tw64, Z);
             k_fb_taper_fold<<<dim3(L / FB_FS, (unsigned)nf), FB_FS * 4, 0, st>>>(Z, (double)ctx->cfg.fs,
                                                                                  ctx->cfg.fir_len, ctx->tw64, Y);
-            k_fb_forward<L><<<dim3(P, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+            k_fb_forward<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
         }
     } else {
         KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
