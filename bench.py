@@ -604,29 +604,44 @@ def run_serving(args):
         ctx.stream_poll(sid)
     # phase 2: Poisson arrivals, real time
     rng = np.random.default_rng(11)
-    t0 = time.perf_counter()
-    heap = [(float(rng.exponential(0.25)), i) for i in range(n_streams)]
-    heapq.heapify(heap)
-    pushes = 0
+
+    def poisson_phase(min_pushes, min_s):
+        t0 = time.perf_counter()
+        heap = [(float(rng.exponential(0.25)), i) for i in range(n_streams)]
+        heapq.heapify(heap)
+        n = 0
+        while n < min_pushes or heap[0][0] < min_s:
+            t_next, i = heapq.heappop(heap)
+            dt = t0 + t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ctx.stream_push(sids[i], xs[i][:, pos[i]:pos[i] + chunk])
+            pos[i] += chunk
+            n += 1
+            heapq.heappush(heap, (t_next + float(rng.exponential(0.25)), i))
+            if pos[i] + chunk > n_tot - int(thr_s * wl.fs):
+                break
+        ctx.stream_flush(120.0)
+        out = []
+        for sid in sids:
+            r = ctx.stream_poll(sid)
+            out.append(r["t_done"] - r["t_push"])
+        return n, np.concatenate(out) * 1000.0
+
     sampler = ClockSampler(local)
     sampler.start()
-    while pushes < 9191 or heap[0][0] < lat_s:
-        t_next, i = heapq.heappop(heap)
-        dt = t0 + t_next - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        ctx.stream_push(sids[i], xs[i][:, pos[i]:pos[i] + chunk])
-        pos[i] += chunk
-        pushes += 1
-        heapq.heappush(heap, (t_next + float(rng.exponential(0.25)), i))
-        if pos[i] + chunk > n_tot - int(thr_s * wl.fs):
-            break
-    ctx.stream_flush(120.0)
-    lat = []
-    for sid in sids:
-        r = ctx.stream_poll(sid)
-        lat.append(r["t_done"] - r["t_push"])
-    lat = np.concatenate(lat) * 1000.0
+    pushes, lat = poisson_phase(9191, lat_s)
+    # a short profiled Poisson phase (events around every launch; not used for the percentiles):
+    # what one latency-phase step is made of
+    ctx.profile_enable(True)
+    st0 = ctx.stream_stats()
+    n_prof, _ = poisson_phase(1024, 0.0)
+    st1 = ctx.stream_stats()
+    ctx.profile_enable(False)
+    prof_steps = max(1, int(st1["steps"] - st0["steps"]))
+    lat_kernels = {k["name"]: {"launches_per_step": round(k["launches"] / prof_steps, 3),
+                               "us_per_launch": round(1000.0 * k["total_ms"] / max(k["timed"], 1), 2)}
+                   for k in ctx.profile_read()}
     # phase 3: maximum offered load (the engine is idle here: counters start clean)
     ctx.profile_enable(True)
     stats0 = ctx.stream_stats()
@@ -658,6 +673,7 @@ def run_serving(args):
                       "throughput_seconds_per_stream": thr_s},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                           "p99": float(np.percentile(lat, 99)), "results": int(lat.size)},
+           "latency_step_kernels": {"pushes": n_prof, "steps": prof_steps, "kernels": lat_kernels},
            "windows_per_s": n_results / wall, "clocks": clocks,
            "roofline": roofline_for(dom, load_peaks(), sum(k["total_ms"] for k in kstats)) if dom else None,
            "gpu_launches": int(sum(k["launches"] for k in kstats)),

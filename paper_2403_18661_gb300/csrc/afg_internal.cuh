@@ -68,7 +68,7 @@ struct WinPtr {
     float *out;
 };
 
-// One piece of a multi-stream whitening launch (at most WB outputs, one epoch's gains)
+// One piece of a multi-stream whitening launch (at most whiten_multi_piece_max outputs, one epoch's gains)
 struct WhitenPiece {
     const float *x;     // raw sample of output 0 minus F/2, detector row 0
     int64_t x_stride;   // samples between detector rows of x
@@ -187,6 +187,33 @@ struct KScope {
 };
 
 // ----------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// (and run its set-up) while the previous kernel on the stream finishes; it
+// calls pdl_wait() before it touches anything that kernel writes, which
+// returns once that kernel has completed and its writes are visible.
+// pdl_trigger() in the earlier kernel lets the dependent launch start early.
+// Both are no-ops for kernels launched without the attribute.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// ----------------------------------------------------------------------------
 // Error plumbing
 // ----------------------------------------------------------------------------
 int afg_fail(afg_ctx *ctx, int code, const char *fmt, ...);
@@ -224,6 +251,7 @@ cudaError_t prepare_psd_kernels();
 int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st);
 int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,
                         cudaStream_t st);
+int whiten_multi_piece_max(const afg_ctx *ctx);  // outputs per piece of launch_whiten_multi
 // net_fp32.cu
 int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights);
 int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,

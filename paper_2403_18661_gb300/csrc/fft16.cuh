@@ -20,6 +20,9 @@
 // Real transforms of NFFT = 16384 samples use z_n = x_2n + i x_2n+1 and the
 // split X_k = E_k + W^k O_k, E_k = (Z_k + conj Z_{NC-k}) / 2,
 // O_k = (Z_k - conj Z_{NC-k}) / 2i, W = exp(-2 pi i / NFFT).
+//
+// A 2048-point variant (real transforms of 4096 samples, 128 threads, radix
+// 16, 16, 4 and the fused radix 2) serves short whitening pieces of streams.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -129,16 +132,18 @@ template <int Ns> __device__ __forceinline__ void store16(float2 *d, const float
     for (int q = 0; q < 16; ++q) d[pad(base + q * Ns)] = v[out16(q)];
 }
 
-__device__ __forceinline__ void load16(float2 (&v)[16], const float2 *d, int j) {
+// the 16 inputs of butterfly j of a radix-16 pass over LEN = 16 NTX points
+template <int NTX = NT> __device__ __forceinline__ void load16(float2 (&v)[16], const float2 *d, int j) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = d[pad(j + NT * r)];
+    for (int r = 0; r < 16; ++r) v[r] = d[pad(j + NTX * r)];
 }
 
-// One in-place Stockham radix-16 pass at stride Ns (reads, barrier, writes, barrier).
-template <int S, int Ns> __device__ __forceinline__ void pass16(float2 *d) {
+// One in-place Stockham radix-16 pass at stride Ns over 16 NTX points (NTX threads;
+// reads, barrier, writes, barrier).
+template <int S, int Ns, int NTX = NT> __device__ __forceinline__ void pass16(float2 *d) {
     const int j = threadIdx.x;
     float2 v[16];
-    load16(v, d, j);
+    load16<NTX>(v, d, j);
     butterfly16<S, Ns>(v, j);
     __syncthreads();
     store16<Ns>(d, v, j);
@@ -191,6 +196,68 @@ __device__ __forceinline__ void split_inv(float2 yk, float2 ynk, float2 w, float
     const float2 io = mul_i<+1>(o);
     zk = cadd(e, io);
     znk = conj(csub(e, io));
+}
+
+// ---- 2048-point variant (real transforms of 4096 samples) on NT_S = 128 threads:
+// forward radix 16, 16, 4 at Ns = 1, 16, 256, then the fused radix-2 pass at 1024;
+// inverse (after the fused pass) radix 16, 16 at Ns = 2, 32 and radix 4 at Ns = 512.
+// Every thread still holds 16 points per pass (four radix-4 butterflies).
+constexpr int NC_S = 2048;
+constexpr int NT_S = NC_S / 16;
+constexpr int SLOTS_S = NC_S + NC_S / 16;
+
+// four radix-4 butterflies b = t + 128 q of a pass at stride Ns: inputs b + 512 r, twiddles,
+// DFT; v[q][r] holds output r of butterfly q
+template <int S, int Ns> __device__ __forceinline__ void butterflies4_s(const float2 *d, float2 (&v)[4][4]) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int b = t + NT_S * q;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[q][r] = d[pad(b + (NC_S / 4) * r)];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = (t + NT_S * q) & (Ns - 1);
+        const float x = (float)k / (float)(2 * Ns);  // exp(S 2 pi i r k / (4 Ns)) = exp(S i pi x r)
+        const float2 w1 = cis<S>(x), w2 = cis<S>(2.0f * x);
+        v[q][1] = cmul(v[q][1], w1);
+        v[q][2] = cmul(v[q][2], w2);
+        v[q][3] = cmul(v[q][3], cmul(w1, w2));
+        dft4<S>(v[q][0], v[q][1], v[q][2], v[q][3]);
+    }
+}
+
+template <int S, int Ns> __device__ __forceinline__ void pass4_s(float2 *d) {
+    float2 v[4][4];
+    butterflies4_s<S, Ns>(d, v);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int b = threadIdx.x + NT_S * q, k = b & (Ns - 1);
+        const int base = (b - k) * 4 + k;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) d[pad(base + r * Ns)] = v[q][r];
+    }
+    __syncthreads();
+}
+
+// forward passes before the fused one: v holds z[t + 128 r] on entry
+__device__ __forceinline__ void forward_s(float2 *d, float2 (&v)[16]) {
+    const int j = threadIdx.x;
+    dft16<-1>(v);
+    store16<1>(d, v, j);
+    __syncthreads();
+    pass16<-1, 16, NT_S>(d);
+    pass4_s<-1, 256>(d);
+}
+
+// inverse passes after the fused one; output r of butterfly q is complex sample
+// t + 128 q + 512 r, returned in v[q][r]
+__device__ __forceinline__ void inverse_s(float2 *d, float2 (&v)[4][4]) {
+    pass16<+1, 2, NT_S>(d);
+    pass16<+1, 32, NT_S>(d);
+    butterflies4_s<+1, NC_S / 4>(d, v);
 }
 
 }  // namespace r16

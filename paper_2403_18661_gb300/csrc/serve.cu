@@ -12,11 +12,13 @@
 // before its epoch); window w covers whitened [w * stride, w * stride + W).
 //
 // The engine (one host thread per context) forms a step from every chunk
-// pushed so far: one H2D copy and a scatter kernel into the raw rings, PSD
-// and filter refreshes of streams entering a new epoch, one whitening launch
-// for every stream's new samples, one network launch for every new window,
-// one integration launch and one D2H copy.  Chunks pushed while a step runs
-// join the next one; two steps may be in flight.
+// pushed so far: one H2D copy and a scatter kernel into the raw rings, one
+// whitening launch for every stream's new samples, one network launch for
+// every new window, one integration launch and one D2H copy.  PSD and filter
+// refreshes are enqueued after a step's result event, as soon as a stream's
+// raw strain covers the 64 s before an epoch, ahead of that epoch's first
+// whitened sample.  Chunks pushed while a step runs join the next one; two
+// steps may be in flight.
 #include <string.h>
 
 #include <algorithm>
@@ -53,6 +55,7 @@ struct IntegDesc {
 
 // grid (n_desc): copy each staged chunk into its stream's mirrored raw ring
 __global__ void k_scatter(const ScatterDesc *__restrict__ d, const float *__restrict__ stage) {
+    pdl_trigger();
     const ScatterDesc s = d[blockIdx.x];
     for (int64_t i = threadIdx.x; i < 2 * s.n; i += blockDim.x) {
         const int det = i >= s.n;
@@ -67,10 +70,12 @@ __global__ void k_scatter(const ScatterDesc *__restrict__ d, const float *__rest
 }
 
 // one thread per new window: stat = mean of the last n_int logits (oldest first)
+// (Launched as a programmatic dependent of the network launch before it.)
 __global__ void k_stream_integrate(const IntegDesc *__restrict__ d, int n, int n_int) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const IntegDesc s = d[i < n ? i : 0];
+    pdl_wait();  // logits of the network launch before
     if (i >= n) return;
-    const IntegDesc s = d[i];
     float acc = 0.f;
     for (int64_t j = s.w - n_int + 1; j <= s.w; ++j) acc += s.ring[j % LR];
     s.out[0] = acc / (float)n_int;
@@ -105,12 +110,14 @@ struct PendingResult {
 
 struct StepBuf {
     bool busy = false;
+    // one pinned host block and its device copy per step: the staged chunks, then the
+    // step's scatter, whitening, window and integration descriptors (one H2D copy)
     float *h_stage = nullptr, *d_stage = nullptr;
-    size_t stage_cap = 0;
-    ScatterDesc *h_sc = nullptr, *d_sc = nullptr;
-    WhitenPiece *h_wp = nullptr, *d_wp = nullptr;
-    WinPtr *h_win = nullptr, *d_win = nullptr;
-    IntegDesc *h_int = nullptr, *d_int = nullptr;
+    size_t stage_cap = 0, blk_bytes = 0;
+    ScatterDesc *h_sc = nullptr;
+    WhitenPiece *h_wp = nullptr;
+    WinPtr *h_win = nullptr;
+    IntegDesc *h_int = nullptr;
     float *d_out = nullptr, *h_out = nullptr;
     int cap_sc = 0, cap_wp = 0, cap_win = 0;
     cudaEvent_t ev = nullptr;
@@ -137,35 +144,35 @@ struct ServeEngine {
 
 namespace {
 
+size_t align16(size_t n) { return (n + 15) & ~(size_t)15; }
+
 int alloc_step(afg_ctx *ctx, StepBuf &b, int max_streams, int64_t per_stream_new, int64_t stride) {
     b.stage_cap = (size_t)max_streams * 2 * per_stream_new;
     b.cap_sc = max_streams;
-    b.cap_wp = max_streams * 4;
+    b.cap_wp = max_streams * (int)(per_stream_new / 512 + 3);  // pieces of >= 512 outputs, one epoch break
     b.cap_win = (int)(max_streams * (per_stream_new / stride + 2));
-    AFG_CUDA(ctx, cudaHostAlloc(&b.h_stage, b.stage_cap * sizeof(float), cudaHostAllocDefault));
-    AFG_CUDA(ctx, cudaMalloc(&b.d_stage, b.stage_cap * sizeof(float)));
+    b.blk_bytes = align16(b.stage_cap * sizeof(float)) + align16(b.cap_sc * sizeof(ScatterDesc)) +
+                  align16(b.cap_wp * sizeof(WhitenPiece)) + align16(b.cap_win * sizeof(WinPtr)) +
+                  align16(b.cap_win * sizeof(IntegDesc));
+    AFG_CUDA(ctx, cudaHostAlloc(&b.h_stage, b.blk_bytes, cudaHostAllocDefault));
+    AFG_CUDA(ctx, cudaMalloc(&b.d_stage, b.blk_bytes));
     AFG_CUDA(ctx, cudaHostAlloc(&b.h_sc, b.cap_sc * sizeof(ScatterDesc), cudaHostAllocDefault));
-    AFG_CUDA(ctx, cudaMalloc(&b.d_sc, b.cap_sc * sizeof(ScatterDesc)));
     AFG_CUDA(ctx, cudaHostAlloc(&b.h_wp, b.cap_wp * sizeof(WhitenPiece), cudaHostAllocDefault));
-    AFG_CUDA(ctx, cudaMalloc(&b.d_wp, b.cap_wp * sizeof(WhitenPiece)));
     AFG_CUDA(ctx, cudaHostAlloc(&b.h_win, b.cap_win * sizeof(WinPtr), cudaHostAllocDefault));
-    AFG_CUDA(ctx, cudaMalloc(&b.d_win, b.cap_win * sizeof(WinPtr)));
     AFG_CUDA(ctx, cudaHostAlloc(&b.h_int, b.cap_win * sizeof(IntegDesc), cudaHostAllocDefault));
-    AFG_CUDA(ctx, cudaMalloc(&b.d_int, b.cap_win * sizeof(IntegDesc)));
     AFG_CUDA(ctx, cudaHostAlloc(&b.h_out, b.cap_win * 2 * sizeof(float), cudaHostAllocDefault));
     AFG_CUDA(ctx, cudaMalloc(&b.d_out, b.cap_win * 2 * sizeof(float)));
     AFG_CUDA(ctx, cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming));
-    ctx->bytes_held += (int64_t)(b.stage_cap * 4 + b.cap_sc * sizeof(ScatterDesc) + b.cap_wp * sizeof(WhitenPiece) +
-                                 b.cap_win * (sizeof(WinPtr) + sizeof(IntegDesc) + 8));
+    ctx->bytes_held += (int64_t)(b.blk_bytes + b.cap_win * 8);
     return AFG_OK;
 }
 
 void free_step(StepBuf &b) {
     cudaFreeHost(b.h_stage); cudaFree(b.d_stage);
-    cudaFreeHost(b.h_sc); cudaFree(b.d_sc);
-    cudaFreeHost(b.h_wp); cudaFree(b.d_wp);
-    cudaFreeHost(b.h_win); cudaFree(b.d_win);
-    cudaFreeHost(b.h_int); cudaFree(b.d_int);
+    cudaFreeHost(b.h_sc);
+    cudaFreeHost(b.h_wp);
+    cudaFreeHost(b.h_win);
+    cudaFreeHost(b.h_int);
     cudaFreeHost(b.h_out); cudaFree(b.d_out);
     if (b.ev) cudaEventDestroy(b.ev);
     b = StepBuf();
@@ -194,6 +201,20 @@ int complete(ServeEngine &E, StepBuf &b) {
     b.res.clear();
     b.slots.clear();
     E.cv_done.notify_all();
+    return AFG_OK;
+}
+
+// PSD of raw [e * epoch_len, e * epoch_len + psd_len) and the two detectors' gains of
+// epoch e into the stream's gains slot e & 1, on st.
+int refresh_gains(ServeEngine &E, Slot &sl, int64_t e, cudaStream_t st) {
+    afg_ctx *ctx = E.ctx;
+    const afg_stream_params &p = E.p;
+    const int slot_g = (int)(e & 1);
+    const float *xr = sl.raw + (e * p.epoch_len) % E.R;
+    int rc = launch_psd(ctx, xr, p.psd_len, 2, 1, 0, p.psd_len, sl.psd, st, 2 * E.R);
+    if (!rc) rc = launch_filter(ctx, sl.psd, 2, 1, sl.gains + (int64_t)slot_g * 2 * NBIN, st);
+    if (rc) return rc;
+    sl.gains_epoch[slot_g] = e;
     return AFG_OK;
 }
 
@@ -256,14 +277,9 @@ int launch_step(ServeEngine &E, StepBuf &b) {
         sl.P += n;
         b.slots.push_back(t.slot);
     }
-    AFG_CUDA(ctx, cudaMemcpyAsync(b.d_stage, b.h_stage, stage_off * sizeof(float), cudaMemcpyHostToDevice, st));
-    AFG_CUDA(ctx, cudaMemcpyAsync(b.d_sc, b.h_sc, n_sc * sizeof(ScatterDesc), cudaMemcpyHostToDevice, st));
-    {
-        KScope ks(ctx, st, KK_SCATTER, 0.0, (double)stage_off * 12.0);
-        k_scatter<<<n_sc, 256, 0, st>>>(b.d_sc, b.d_stage);
-    }
-    AFG_LAUNCH_CHECK(ctx, "k_scatter");
-    // 2) epochs: refresh PSD + gains; 3) whitening pieces; 4) windows
+    // 2) whitening pieces (and the gains refreshes they still need); 3) windows
+    std::vector<std::pair<int, int64_t>> refresh;  // (slot, epoch) built after the scatter, before the pieces
+    const int64_t piece_max = whiten_multi_piece_max(ctx);
     for (Taken &t : taken) {
         Slot &sl = E.slots[t.slot];
         const double t_push = t.chunks.back().t_push;
@@ -271,14 +287,11 @@ int launch_step(ServeEngine &E, StepBuf &b) {
         int64_t j = sl.Q;
         while (j < q_new) {
             const int64_t e = j / p.epoch_len;
-            const int64_t end = std::min({q_new, (e + 1) * p.epoch_len, j + (int64_t)WB});
+            const int64_t end = std::min({q_new, (e + 1) * p.epoch_len, j + piece_max});
             const int slot_g = (int)(e & 1);
-            if (sl.gains_epoch[slot_g] != e) {
-                const float *xr = sl.raw + (e * p.epoch_len) % E.R;
-                int rc = launch_psd(ctx, xr, p.psd_len, 2, 1, 0, p.psd_len, sl.psd, st, 2 * E.R);
-                if (!rc) rc = launch_filter(ctx, sl.psd, 2, 1, sl.gains + (int64_t)slot_g * 2 * NBIN, st);
-                if (rc) return -1;
+            if (sl.gains_epoch[slot_g] != e) {  // not built ahead (chunks longer than F/2)
                 sl.gains_epoch[slot_g] = e;
+                refresh.emplace_back(t.slot, e);
             }
             WhitenPiece wp;
             wp.x = sl.raw + (p.psd_len + j - F / 2) % E.R;
@@ -311,25 +324,54 @@ int launch_step(ServeEngine &E, StepBuf &b) {
             b.h_win[n_win++] = wptr;
         }
     }
-    if (n_wp) {
-        AFG_CUDA(ctx, cudaMemcpyAsync(b.d_wp, b.h_wp, n_wp * sizeof(WhitenPiece), cudaMemcpyHostToDevice, st));
-        if (launch_whiten_multi(ctx, b.d_wp, n_wp, total_white, st)) return -1;
-    }
-    if (n_win) {
-        AFG_CUDA(ctx, cudaMemcpyAsync(b.d_win, b.h_win, n_win * sizeof(WinPtr), cudaMemcpyHostToDevice, st));
-        if (launch_infer_bf16_list(ctx, b.d_win, n_win, st)) return -1;
-    }
+    // one H2D copy: chunks, then the descriptors
     const int n_res = (int)b.res.size();
+    char *hb = reinterpret_cast<char *>(b.h_stage), *db = reinterpret_cast<char *>(b.d_stage);
+    size_t off = align16(stage_off * sizeof(float));
+    const size_t o_sc = off;
+    off += align16(n_sc * sizeof(ScatterDesc));
+    const size_t o_wp = off;
+    off += align16(n_wp * sizeof(WhitenPiece));
+    const size_t o_win = off;
+    off += align16(n_win * sizeof(WinPtr));
+    const size_t o_int = off;
+    off += align16(n_res * sizeof(IntegDesc));
+    memcpy(hb + o_sc, b.h_sc, n_sc * sizeof(ScatterDesc));
+    memcpy(hb + o_wp, b.h_wp, n_wp * sizeof(WhitenPiece));
+    memcpy(hb + o_win, b.h_win, n_win * sizeof(WinPtr));
+    memcpy(hb + o_int, b.h_int, n_res * sizeof(IntegDesc));
+    AFG_CUDA(ctx, cudaMemcpyAsync(db, hb, off, cudaMemcpyHostToDevice, st));
+    {
+        KScope ks(ctx, st, KK_SCATTER, 0.0, (double)stage_off * 12.0);
+        k_scatter<<<n_sc, 256, 0, st>>>(reinterpret_cast<const ScatterDesc *>(db + o_sc), b.d_stage);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_scatter");
+    for (const auto &r : refresh)
+        if (refresh_gains(E, E.slots[r.first], r.second, st)) return -1;
+    if (n_wp && launch_whiten_multi(ctx, reinterpret_cast<const WhitenPiece *>(db + o_wp), n_wp, total_white, st))
+        return -1;
+    if (n_win && launch_infer_bf16_list(ctx, reinterpret_cast<const WinPtr *>(db + o_win), n_win, st)) return -1;
     if (n_res) {
-        AFG_CUDA(ctx, cudaMemcpyAsync(b.d_int, b.h_int, n_res * sizeof(IntegDesc), cudaMemcpyHostToDevice, st));
         {
             KScope ks(ctx, st, KK_INTEGRATE, (double)n_res * p.n_int, (double)n_res * (p.n_int + 2) * 4.0);
-            k_stream_integrate<<<(n_res + 127) / 128, 128, 0, st>>>(b.d_int, n_res, p.n_int);
+            AFG_CUDA(ctx, launch_pdl(k_stream_integrate, dim3((unsigned)((n_res + 127) / 128)), dim3(128), 0, st,
+                                     reinterpret_cast<const IntegDesc *>(db + o_int), n_res, (int)p.n_int));
         }
-        AFG_LAUNCH_CHECK(ctx, "k_stream_integrate");
         AFG_CUDA(ctx, cudaMemcpyAsync(b.h_out, b.d_out, n_res * 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
     }
     AFG_CUDA(ctx, cudaEventRecord(b.ev, st));
+    // Refreshes ahead of need: a stream whose raw strain now covers the 64 s before its
+    // current or next epoch gets that epoch's PSD and gains here, after this step's result
+    // event, so no push waits for them.  The data is complete F/2 samples before the epoch's
+    // first output can be whitened, so a later step (same CUDA stream) finds the gains
+    // built; the gains slot they take held the epoch before the previous one, which no
+    // pending or later piece reads.
+    for (Taken &t : taken) {
+        Slot &sl = E.slots[t.slot];
+        for (int64_t e = sl.Q / p.epoch_len; e <= sl.Q / p.epoch_len + 1; ++e)
+            if (sl.gains_epoch[e & 1] != e && sl.P >= e * p.epoch_len + p.psd_len && refresh_gains(E, sl, e, st))
+                return -1;
+    }
     b.busy = true;
     E.steps++;
     E.windows += n_win;

@@ -321,44 +321,48 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
-// Fused mid pass of the whitening kernel for task j, 1 <= j <= 2048: the
-// forward radix-2 butterflies j and 4096 - j (Ns = 4096) give Z at j,
-// j + 4096, 4096 - j, 8192 - j; the split pairs (j, NC - j) and
-// (j + 4096, 4096 - j) are multiplied by the gains g and split back; the
-// inverse radix-2 butterflies j and 4096 - j (Ns = 1) produce o[0..1] for
-// d[2j], d[2j + 1] and o[2..3] for d[2(4096 - j)], d[2(4096 - j) + 1].
+// Fused mid pass of the whitening kernel for task j, 1 <= j <= NCX / 4, of a
+// transform of NCX complex points (H = NCX / 2): the forward radix-2 butterflies j
+// and H - j (Ns = H) give Z at j, j + H, H - j, NCX - j; the split pairs (j, NCX - j)
+// and (j + H, H - j) are multiplied by the gains g (on the transform's own grid) and
+// split back; the inverse radix-2 butterflies j and H - j (Ns = 1) produce o[0..1]
+// for d[2j], d[2j + 1] and o[2..3] for d[2(H - j)], d[2(H - j) + 1].
+template <int NCX>
 __device__ __forceinline__ void whiten_mid_task(const float2 *d, const float *g, int j, float2 (&o)[4]) {
     using namespace r16;
-    const float2 a = d[pad(j)], b = d[pad(j + 4096)], c = d[pad(4096 - j)], e = d[pad(8192 - j)];
-    const float2 w = cis<-1>((float)j / 8192.0f);  // W^j
-    const float2 u = cis<-1>((float)j / 4096.0f);  // radix-2 twiddle of butterfly j
-    const float2 u2 = make_float2(-u.x, u.y);      // of butterfly 4096 - j
+    constexpr int H = NCX / 2;
+    const float2 a = d[pad(j)], b = d[pad(j + H)], c = d[pad(H - j)], e = d[pad(NCX - j)];
+    const float2 w = cis<-1>((float)j / (float)NCX);        // W^j, W = exp(-2 pi i / 2 NCX)
+    const float2 u = cis<-1>((float)j / (float)(NCX / 2));  // radix-2 twiddle of butterfly j
+    const float2 u2 = make_float2(-u.x, u.y);               // of butterfly H - j
     const float2 ub = cmul(u, b), ue = cmul(u2, e);
     const float2 zj = cadd(a, ub), zj4 = csub(a, ub), zc = cadd(c, ue), zc4 = csub(c, ue);
-    const float2 w4 = mul_i<-1>(w);                // W^{j + 4096}
+    const float2 w4 = mul_i<-1>(w);                         // W^{j + H}
     float2 x1, x1n, x2, x2n, p1, p1n, p2, p2n;
     split_fwd(zj, zc4, w, x1, x1n);
     split_fwd(zj4, zc, w4, x2, x2n);
-    split_inv(cscale(x1, g[j]), cscale(x1n, g[8192 - j]), w, p1, p1n);        // Z'_j, Z'_{8192-j}
-    split_inv(cscale(x2, g[j + 4096]), cscale(x2n, g[4096 - j]), w4, p2, p2n);  // Z'_{j+4096}, Z'_{4096-j}
+    split_inv(cscale(x1, g[j]), cscale(x1n, g[NCX - j]), w, p1, p1n);     // Z'_j, Z'_{NCX-j}
+    split_inv(cscale(x2, g[j + H]), cscale(x2n, g[H - j]), w4, p2, p2n);  // Z'_{j+H}, Z'_{H-j}
     o[0] = cadd(p1, p2);
     o[1] = csub(p1, p2);
     o[2] = cadd(p2n, p1n);
     o[3] = csub(p2n, p1n);
 }
 
-// Task 0 of the mid pass: butterfly 0 gives Z_0 and Z_4096, each its own
-// split partner (bin 0 with the Nyquist bin NC, and bin 4096); o[0..1] go to d[0], d[1].
+// Task 0 of the mid pass: butterfly 0 gives Z_0 and Z_H, each its own split partner
+// (bin 0 with the Nyquist bin NCX, and bin H); o[0..1] go to d[0], d[1].
+template <int NCX>
 __device__ __forceinline__ void whiten_mid_task0(const float2 *d, const float *g, float2 (&o)[4]) {
     using namespace r16;
-    const float2 a = d[pad(0)], b = d[pad(4096)];
+    constexpr int H = NCX / 2;
+    const float2 a = d[pad(0)], b = d[pad(H)];
     const float2 z0 = cadd(a, b), z4 = csub(a, b);
-    const float2 one = make_float2(1.0f, 0.0f), mi = make_float2(0.0f, -1.0f);  // W^0, W^4096
+    const float2 one = make_float2(1.0f, 0.0f), mi = make_float2(0.0f, -1.0f);  // W^0, W^H
     float2 x0, xn, x4, x4d, p0, pn, p4, p4d;
     split_fwd(z0, z0, one, x0, xn);
-    split_inv(cscale(x0, g[0]), cscale(xn, g[NC]), one, p0, pn);
+    split_inv(cscale(x0, g[0]), cscale(xn, g[NCX]), one, p0, pn);
     split_fwd(z4, z4, mi, x4, x4d);
-    split_inv(cscale(x4, g[4096]), cscale(x4d, g[4096]), mi, p4, p4d);
+    split_inv(cscale(x4, g[H]), cscale(x4d, g[H]), mi, p4, p4d);
     o[0] = cadd(p0, p4);
     o[1] = csub(p0, p4);
     o[2] = o[0];
@@ -393,11 +397,11 @@ __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *_
     cp_async_wait_all();
     __syncthreads();
     float2 o[4][4], ox[4];
-    if (t == 0) whiten_mid_task0(d, gs, o[0]);
-    else whiten_mid_task(d, gs, t, o[0]);
+    if (t == 0) whiten_mid_task0<NC>(d, gs, o[0]);
+    else whiten_mid_task<NC>(d, gs, t, o[0]);
 #pragma unroll
-    for (int m = 1; m < 4; ++m) whiten_mid_task(d, gs, t + NT * m, o[m]);
-    if (t == NT - 1) whiten_mid_task(d, gs, 2048, ox);
+    for (int m = 1; m < 4; ++m) whiten_mid_task<NC>(d, gs, t + NT * m, o[m]);
+    if (t == NT - 1) whiten_mid_task<NC>(d, gs, 2048, ox);
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -451,9 +455,12 @@ __global__ void __launch_bounds__(r16::NT, 2) k_whiten(const float *__restrict__
 // gains desc.gains + d * NBIN into the mirrored ring desc.y (row stride
 // y_stride, ring length y_ring): output q goes to ring slots
 // (y_pos + q) mod y_ring and that + y_ring.
+// (Launched as a programmatic dependent of the scatter or gains refresh before it.)
 __global__ void __launch_bounds__(r16::NT, 2) k_whiten_multi(const WhitenPiece *__restrict__ pieces, int F) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     const WhitenPiece pc = pieces[blockIdx.x];
+    pdl_wait();  // raw rings (scatter) and gains (refresh) come from the kernels before
     const int det = blockIdx.y;
     float *yr = pc.y + det * pc.y_stride;
     const int64_t ring = pc.y_ring, pos = pc.y_pos;
@@ -466,6 +473,95 @@ __global__ void __launch_bounds__(r16::NT, 2) k_whiten_multi(const WhitenPiece *
                  });
 }
 
+constexpr int WHITEN_SMEM_S = r16::SLOTS_S * (int)sizeof(float2) + (r16::NC_S + 1) * (int)sizeof(float);
+
+// Largest piece of the 4096-point block for a filter of F taps (0 if F leaves too few).
+int whiten_piece_max_s(int F) {
+    const int m = 2 * r16::NC_S - F + 1;
+    return m >= 512 ? m : 0;
+}
+
+// One overlap-save block of the 4096-point transform: the FIR of src[0 .. cnt + F - 1)
+// (cnt <= 4097 - F, samples past `avail` read as zero) -> outputs q in [0, cnt) written as
+// out(q, value).  The taps span fewer than 4096 lags, so the gains of this grid are those
+// of the 16384-point grid at every 4th bin; they are rescaled by 4 for the shorter
+// transform's 1 / 2048 normalisation (exact in FP32).
+template <typename Out>
+__device__ __forceinline__ void whiten_block_s(unsigned char *smem, const float *__restrict__ src, int64_t avail,
+                                               const float *__restrict__ gk, int F, int64_t cnt, Out out) {
+    using namespace r16;
+    constexpr int GS = NC / NC_S;  // bins of the 16384-point grid per bin of this one
+    float2 *d = reinterpret_cast<float2 *>(smem);
+    float *gs = reinterpret_cast<float *>(smem + SLOTS_S * sizeof(float2));
+    const int t = threadIdx.x;
+    for (int k = t; k <= NC_S; k += NT_S) cp_async4(gs + k, gk + GS * k);
+    const int half = F / 2;
+    const int64_t need = cnt + F - 1;
+    const int64_t lim = need < avail ? need : avail;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int64_t i0 = 2 * (int64_t)(t + NT_S * r);
+        v[r] = make_float2(i0 < lim ? src[i0] : 0.0f, i0 + 1 < lim ? src[i0 + 1] : 0.0f);
+    }
+    forward_s(d, v);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int k = t; k <= NC_S; k += NT_S) gs[k] *= (float)GS;
+    __syncthreads();
+    float2 o[4][4], ox[4];
+    if (t == 0) whiten_mid_task0<NC_S>(d, gs, o[0]);
+    else whiten_mid_task<NC_S>(d, gs, t, o[0]);
+#pragma unroll
+    for (int m = 1; m < 4; ++m) whiten_mid_task<NC_S>(d, gs, t + NT_S * m, o[m]);
+    if (t == NT_S - 1) whiten_mid_task<NC_S>(d, gs, NC_S / 4, ox);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int j = t + NT_S * m, jc = NC_S / 2 - j;
+        d[pad(2 * j)] = o[m][0];
+        d[pad(2 * j + 1)] = o[m][1];
+        if (j != 0) {
+            d[pad(2 * jc)] = o[m][2];
+            d[pad(2 * jc + 1)] = o[m][3];
+        }
+    }
+    if (t == NT_S - 1) {
+        d[pad(NC_S / 2)] = ox[0];
+        d[pad(NC_S / 2 + 1)] = ox[1];
+    }
+    __syncthreads();
+    float2 y[4][4];
+    inverse_s(d, y);
+    // complex sample c = t + 128 q + 512 r holds real samples 2c, 2c + 1; output q0 = 2c - F/2
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t q0 = 2 * (int64_t)(t + NT_S * q + (NC_S / 4) * r) - half;
+            if (q0 >= 0 && q0 < cnt) out(q0, y[q][r].x);
+            if (q0 + 1 >= 0 && q0 + 1 < cnt) out(q0 + 1, y[q][r].y);
+        }
+}
+
+// k_whiten_multi with the 4096-point block: pieces of at most 4097 - F outputs.
+__global__ void __launch_bounds__(r16::NT_S) k_whiten_multi_s(const WhitenPiece *__restrict__ pieces, int F) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    const WhitenPiece pc = pieces[blockIdx.x];
+    pdl_wait();  // raw rings (scatter) and gains (refresh) come from the kernels before
+    const int det = blockIdx.y;
+    float *yr = pc.y + det * pc.y_stride;
+    const int64_t ring = pc.y_ring, pos = pc.y_pos;
+    whiten_block_s(smem_raw, pc.x + det * pc.x_stride, pc.cnt + F - 1, pc.gains + det * NBIN, F, pc.cnt,
+                   [yr, ring, pos](int64_t q, float v) {
+                       int64_t m = pos + q;
+                       if (m >= ring) m -= ring;
+                       yr[m] = v;
+                       yr[m + ring] = v;
+                   });
+}
+
 bool g_attrs_set = false;
 
 int set_attrs(afg_ctx *ctx) {
@@ -473,6 +569,7 @@ int set_attrs(afg_ctx *ctx) {
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize, WELCH_SMEM));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize, WHITEN_SMEM));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, WHITEN_SMEM));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_whiten_multi_s, cudaFuncAttributeMaxDynamicSharedMemorySize, WHITEN_SMEM_S));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_filter_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)((NC + 1) * sizeof(double2))));
     g_attrs_set = true;
@@ -580,6 +677,12 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
     return AFG_OK;
 }
 
+// Most outputs one piece of launch_whiten_multi may hold.
+int whiten_multi_piece_max(const afg_ctx *ctx) {
+    const int m = whiten_piece_max_s(ctx->cfg.fir_len);
+    return m ? m : WB;
+}
+
 // Filter build only: gains [n_det][n_psd][NBIN] from psd (FP64), on st.
 int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st) {
     return filter_build(ctx, psd, n_det, n_psd, gains, st);
@@ -590,8 +693,12 @@ int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_piece
     if (n_pieces <= 0) return AFG_OK;
     const double F = ctx->cfg.fir_len;
     KScope ks(ctx, st, KK_WHITEN, 0.0, 2.0 * ((2.0 * total_out + n_pieces * (F - 1.0)) * 4.0 + n_pieces * NBIN * 4.0));
-    k_whiten_multi<<<dim3((unsigned)n_pieces, 2), r16::NT, WHITEN_SMEM, st>>>(pieces_dev, ctx->cfg.fir_len);
-    AFG_LAUNCH_CHECK(ctx, "k_whiten_multi");
+    if (whiten_piece_max_s(ctx->cfg.fir_len))  // pieces were cut to the 4096-point block
+        AFG_CUDA(ctx, launch_pdl(k_whiten_multi_s, dim3((unsigned)n_pieces, 2), dim3(r16::NT_S), WHITEN_SMEM_S, st,
+                                 pieces_dev, ctx->cfg.fir_len));
+    else
+        AFG_CUDA(ctx, launch_pdl(k_whiten_multi, dim3((unsigned)n_pieces, 2), dim3(r16::NT), WHITEN_SMEM, st,
+                                 pieces_dev, ctx->cfg.fir_len));
     return AFG_OK;
 }
 
