@@ -35,6 +35,8 @@ constexpr int TF_WARPS = TF_THREADS / 32;
 constexpr int TF_C = 16;                   // channels of the fused network
 constexpr int TF_WIMG = 3 * 2 * TF_C * 16;  // bytes of one conv's weight image (3 taps x 512 B)
 constexpr int TF_GROUPS = 3;                // MMA commit groups per conv (8 M subtiles each at W = 3072)
+constexpr int TF_CLUSTER = 4;               // list mode, few windows: CTAs sharing one window
+constexpr int TF_XCH = 64 * 4;              // bytes of the cluster exchange area after the shared-memory layout
 
 struct TinyArgs {
     const float *y;
@@ -127,6 +129,98 @@ __device__ __forceinline__ void gn_reduce(float (&s)[TF_C], float (&q)[TF_C], fl
         scale[c] = a;
         shift[c] = beta[c] - mean * a;
     }
+    __syncthreads();
+}
+
+// ---- clusters of CTAs sharing one window (list mode with few windows): barrier over all
+// threads of the cluster (release/acquire orders shared-memory writes before it with reads
+// after it in every CTA) and loads from another CTA's shared memory
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// address of shared variable p in the shared memory of cluster CTA `rank`
+__device__ __forceinline__ uint32_t dsmem_addr(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_addr(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float dsmem_ld(const float *p, uint32_t rank) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(dsmem_addr(p, rank)) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint4 dsmem_ld16(const void *p, uint32_t rank) {
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(dsmem_addr(p, rank))
+                 : "memory");
+    return v;
+}
+// sum of x[i] over the CL CTAs of the cluster, in rank order (the same total in every CTA)
+template <int CL> __device__ __forceinline__ float cluster_sum(const float *x) {
+    float t = 0.f;
+#pragma unroll
+    for (int r = 0; r < CL; ++r) t += dsmem_ld(x, (uint32_t)r);
+    return t;
+}
+
+// gn_reduce for a window split over a cluster of CL CTAs: the block totals of the
+// 2 G group sums go through xch (shared memory, 2 G floats) to every CTA of the cluster
+template <int G, int CL>
+__device__ __forceinline__ void gn_reduce_cluster(float (&s)[TF_C], float (&q)[TF_C], float cnt, float eps,
+                                                  const float *gamma, const float *beta, float *red, float *scale,
+                                                  float *shift, float *xch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NV = 2 * G;
+    float v[NV];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        v[g] = s[g];
+        v[G + g] = q[g];
+    }
+    warp_reduce_scatter<NV>(v, lane);
+    if ((lane & (32 / NV - 1)) == 0) red[warp * 2 * TF_C + lane / (32 / NV)] = v[0];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float t = 0.f;
+        for (int w = 0; w < TF_WARPS; ++w) t += red[w * 2 * TF_C + threadIdx.x];
+        xch[threadIdx.x] = t;
+    }
+    cluster_sync_all();
+    if (threadIdx.x < TF_C) {
+        const int c = threadIdx.x, g = c / (TF_C / G);
+        const float mean = cluster_sum<CL>(xch + g) / cnt;
+        const float var = fmaxf(cluster_sum<CL>(xch + G + g) / cnt - mean * mean, 0.f);
+        const float a = rsqrtf(var + eps) * gamma[c];
+        scale[c] = a;
+        shift[c] = beta[c] - mean * a;
+    }
+    __syncthreads();
+}
+
+// Halo rows of a split window: row 0 of `buf` takes the left neighbour's last position
+// (its row Wl), row Wl + 1 the right neighbour's first (its row 1); the window's own
+// edges keep their zero rows.  After a cluster barrier that orders the neighbours' writes.
+template <int CL>
+__device__ __forceinline__ void halo_exchange(unsigned char *buf, size_t act_chunk, int Wl, uint32_t rank) {
+    cluster_sync_all();
+    if (threadIdx.x < 4) {
+        const int side = threadIdx.x >> 1, c = threadIdx.x & 1;
+        const bool has = side ? rank + 1 < (uint32_t)CL : rank > 0;
+        if (has) {
+            const uint32_t nb = side ? rank + 1 : rank - 1;
+            const int src_row = side ? 1 : Wl, dst_row = side ? Wl + 1 : 0;
+            const uint4 v = dsmem_ld16(buf + c * act_chunk + (size_t)src_row * 16, nb);
+            *reinterpret_cast<uint4 *>(buf + c * act_chunk + (size_t)dst_row * 16) = v;
+        }
+    }
+    tc::fence_proxy_async_smem();
     __syncthreads();
 }
 
@@ -241,12 +335,19 @@ __device__ __forceinline__ void load_window(const TinyArgs &args, const WinLoc &
     if (async) asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-template <int G>
+// CL > 1 (list mode only): a cluster of CL CTAs shares each window, CTA rank q taking
+// positions [q W / CL, (q + 1) W / CL); GroupNorm statistics, the stem moments and the
+// pooled head sums are summed over the cluster, and after every layer that writes an
+// activation each CTA fetches its neighbours' boundary rows.  Every CTA of a cluster
+// runs the same sequence of cluster barriers whatever happens, so none can wait alone.
+template <int G, int CL = 1>
 __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs args) {
     extern __shared__ __align__(1024) unsigned char sm[];
     pdl_trigger();
-    const int W = args.W, k = args.k_stem, pad = k / 2, n_conv = args.n_conv;
-    const Smem L = tiny_smem(W, n_conv, k);
+    const int W = args.W, Wl = W / CL, k = args.k_stem, pad = k / 2, n_conv = args.n_conv;
+    const Smem L = tiny_smem(Wl, n_conv, k);
+    const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
+    float *xch = reinterpret_cast<float *>(sm + L.total);  // CL > 1: [0, 32) moments, [32, 48) GN, [48, 64) head
     unsigned char *actA = sm + L.off_a;
     unsigned char *actB = sm + L.off_b;
     unsigned char *wimg = sm + L.off_w;
@@ -258,8 +359,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + L.off_misc + 8 * TF_GROUPS);
     int *abort_flag = reinterpret_cast<int *>(sm + L.off_misc + 8 * TF_GROUPS + 4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const size_t act_chunk = (size_t)(W + 2) * 16;  // bytes of one 8-channel chunk
-    const int MT = W / 128;
+    const size_t act_chunk = (size_t)(Wl + 2) * 16;  // bytes of one 8-channel chunk
+    const int MT = Wl / 128;
 
     // ---- one-time set-up: parameters, weight image, zero pad rows, barrier, TMEM
     const int n_prm = tiny_param_count(k, n_conv);
@@ -268,7 +369,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         reinterpret_cast<uint4 *>(wimg)[i] = reinterpret_cast<const uint4 *>(args.wimg)[i];
     if (tid < 8) {
         unsigned char *buf = (tid & 4) ? actB : actA;
-        const int c = (tid >> 1) & 1, row = (tid & 1) ? W + 1 : 0;
+        const int c = (tid >> 1) & 1, row = (tid & 1) ? Wl + 1 : 0;
         *reinterpret_cast<uint4 *>(buf + c * act_chunk + (size_t)row * 16) = make_uint4(0, 0, 0, 0);
     }
     if (tid == 0) {
@@ -276,8 +377,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         tc::fence_mbar_init();
         *abort_flag = 0;
     }
+    // a split window needs 96 columns: 128 leaves room for CTAs of one cluster that share an SM
     if (warp == 0) {
-        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_alloc(tmem_slot, CL > 1 ? 128 : 512);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -294,20 +396,32 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     const float cnt = (float)W * (float)(TF_C / G);
     uint32_t phase = 0;
 
-    // staging for the raw window (2 rows of W + 8 floats) inside buffer B, past its first pad row
+    // staging for the raw window (2 rows of Wl + 8 floats) inside buffer B, past its first pad row
     float *xs = reinterpret_cast<float *>(actB + 16);
-    const float *xs0 = xs + 4 - pad, *xs1 = xs + (W + 8) + 4 - pad;  // padded index p of each detector row
+    const float *xs0 = xs + 4 - pad, *xs1 = xs + (Wl + 8) + 4 - pad;  // padded index p of each detector row
 
-    WinLoc cur = locate_window(args, blockIdx.x);
+    const int64_t win0 = blockIdx.x / CL, win_step = gridDim.x / CL;
+    WinLoc cur = locate_window(args, win0);
     bool prefetched = false;  // the window's samples were copied asynchronously during the previous one
     pdl_wait();  // list mode: the whitened rings come from the whitening launch before (set-up above overlaps it)
-    for (int64_t win = blockIdx.x; win < args.n_win; win += gridDim.x) {
-        if (prefetched) asm volatile("cp.async.wait_all;" ::: "memory");
-        else load_window(args, cur, xs, W, pad, false);
+    for (int64_t win = win0; win < args.n_win; win += win_step) {
+        if (CL > 1) {
+            // this CTA's slice of the window with pad samples each side (zero beyond the window)
+            cur = locate_window(args, win);
+            const int q0 = (int)rank * Wl, n = Wl + 2 * pad, RP = Wl + 8;
+            for (int c = tid; c < 2 * n; c += TF_THREADS) {
+                const int d = c >= n, sl = c - d * n - pad, g = q0 + sl;
+                xs[d * RP + 4 + sl] = (g >= 0 && g < W) ? (d ? cur.y1 : cur.y0)[g] : 0.f;
+            }
+        } else if (prefetched) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        } else {
+            load_window(args, cur, xs, W, pad, false);
+        }
         __syncthreads();
         const int64_t out = cur.out;
         float *out_ptr = cur.out_ptr;
-        const int64_t win_next = win + gridDim.x;
+        const int64_t win_next = win + win_step;
         prefetched = false;
         // ---- stem pass 1: GroupNorm statistics of the k = 3 stem from the moments
         // of its six inputs u = (x0[t..t+2], x1[t..t+2]):  sum_t y_c = w_c . S and
@@ -319,7 +433,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
 #pragma unroll
             for (int i = 0; i < 21; ++i) M[i] = 0.f;
 #pragma unroll 2
-            for (int t = tid; t < W; t += TF_THREADS) {
+            for (int t = tid; t < Wl; t += TF_THREADS) {
                 float u[6];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
@@ -353,7 +467,12 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             if (tid < 27) {
                 float tot = 0.f;
                 for (int w = 0; w < TF_WARPS; ++w) tot += red[w * 32 + tid];
-                red[TF_WARPS * 32 + tid] = tot;
+                if (CL > 1) xch[tid] = tot;
+                else red[TF_WARPS * 32 + tid] = tot;
+            }
+            if (CL > 1) {
+                cluster_sync_all();
+                if (tid < 27) red[TF_WARPS * 32 + tid] = cluster_sum<CL>(xch + tid);
             }
             __syncthreads();
             if (tid < TF_C) {
@@ -404,7 +523,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             }
             unsigned char *dstc = actA + h * act_chunk;
 #pragma unroll 2
-            for (int t = tid >> 1; t < W; t += TF_THREADS / 2) {
+            for (int t = tid >> 1; t < Wl; t += TF_THREADS / 2) {
                 float u[6];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
@@ -430,6 +549,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         }
         tc::fence_proxy_async_smem();
         __syncthreads();
+        if (CL > 1) halo_exchange<CL>(actA, act_chunk, Wl, rank);
 
         float hs[TF_C];
 #pragma unroll
@@ -452,6 +572,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     if (MT == 24) {
                         tiny_issue<8>(tmem + (uint32_t)(j_lo * TF_C), ad00 + (uint64_t)(128 * j_lo), bd00,
                                       idesc);  // 1.5 s windows at 2048 Hz
+                    } else if (MT == 6) {
+                        tiny_issue<2>(tmem + (uint32_t)(j_lo * TF_C), ad00 + (uint64_t)(128 * j_lo), bd00,
+                                      idesc);  // a quarter of such a window (cluster of 4)
                     } else {
                         for (int j = j_lo; j < j_hi; ++j)
                             for (int r = 0; r < 3; ++r)
@@ -502,11 +625,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     *abort_flag = 1;
                 }
                 __syncthreads();
-                if (*abort_flag) {
+                if (*abort_flag && CL == 1) {  // (a cluster CTA carries on: its partners wait at barriers)
                     aborted = true;
                     break;
                 }
-                if (last && win_next < args.n_win) {
+                if (CL == 1 && last && win_next < args.n_win) {
                     // buffer B (the staging of the raw window) is free once the last conv's MMAs
                     // have read it: copy the next window's samples meanwhile
                     cur = locate_window(args, win_next);
@@ -514,7 +637,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     prefetched = true;
                 }
                 const float *gb = conv_gb + l * 2 * TF_C;
-                gn_reduce<G>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift);
+                if (CL > 1) gn_reduce_cluster<G, CL>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift, xch + 32);
+                else gn_reduce<G>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift);
             }
             // ---- epilogue pass 2: normalise (+ residual) + ReLU -> BF16 (two subtiles per TMEM wait)
             {
@@ -575,16 +699,29 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             tc::fence_before_sync();
             tc::fence_proxy_async_smem();
             __syncthreads();
+            if (CL > 1 && !last) halo_exchange<CL>(dst, act_chunk, Wl, rank);
         }
         if (aborted) break;
         // ---- head: global mean pool of the last block's output, then linear
         warp_reduce_scatter<TF_C>(hs, lane);  // lane 2c holds the warp's sum of channel c
         if (!(lane & 1)) red[warp * 2 * TF_C + (lane >> 1)] = hs[0];
         __syncthreads();
-        if (tid < 32) {
+        if (CL > 1) {  // channel sums of the cluster: each CTA's block totals through xch
+            if (tid < TF_C) {
+                float t = 0.f;
+                for (int w = 0; w < TF_WARPS; ++w) t += red[w * 2 * TF_C + tid];
+                xch[48 + tid] = t;
+            }
+            cluster_sync_all();
+        }
+        if (tid < 32 && (CL == 1 || rank == 0)) {
             float part = 0.f;  // lanes 0..15: channel lane over all warps, times its weight
             if (lane < TF_C) {
-                for (int w = 0; w < TF_WARPS; ++w) part += red[w * 2 * TF_C + lane];
+                if (CL > 1) {
+                    part = cluster_sum<CL>(xch + 48 + lane);
+                } else {
+                    for (int w = 0; w < TF_WARPS; ++w) part += red[w * 2 * TF_C + lane];
+                }
                 part = fc_w[lane] * (part / (float)W);
             }
 #pragma unroll
@@ -597,11 +734,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         }
         __syncthreads();
     }
-    // ---- teardown (a prefetch may still be in flight after an abort)
+    // ---- teardown (a prefetch may still be in flight after an abort); a cluster CTA waits
+    // until every partner has finished reading its shared memory
     asm volatile("cp.async.wait_all;" ::: "memory");
+    if (CL > 1) cluster_sync_all();
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, CL > 1 ? 128 : 512);
 }
 
 bool tiny_compatible(const afg_ctx *ctx) {
@@ -668,6 +807,19 @@ int net_tc_prepare(afg_ctx *ctx) {
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (ctx->cfg.win_len % (128 * TF_CLUSTER) == 0) {  // list mode on clusters: a quarter window per CTA
+        const int smem_c = (int)tiny_smem(ctx->cfg.win_len / TF_CLUSTER, n_conv, k).total + TF_XCH;
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<1, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem_c));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<2, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem_c));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<4, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem_c));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<8, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem_c));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<16, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem_c));
+    }
     return AFG_OK;
 }
 
@@ -744,6 +896,20 @@ int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, 
     KScope ks(ctx, st, KK_TINY_TC, flops, (double)n_win * (2.0 * W * 4.0 + 4.0));
     // a programmatic dependent of the whitening launch: set-up overlaps its tail
     cudaError_t e;
+    if (W % (128 * TF_CLUSTER) == 0 && n_win * TF_CLUSTER <= sms) {
+        // few windows (a latency-bound step): one cluster of TF_CLUSTER CTAs per window
+        const size_t smem_c = tiny_smem(W / TF_CLUSTER, n_conv, a.k_stem).total + TF_XCH;
+        const dim3 gc((unsigned)(n_win * TF_CLUSTER));
+        switch (a.G) {
+            case 1: e = launch_pdl_cluster(k_tiny_fused<1, TF_CLUSTER>, gc, dim3(TF_THREADS), smem_c, st, TF_CLUSTER, a); break;
+            case 2: e = launch_pdl_cluster(k_tiny_fused<2, TF_CLUSTER>, gc, dim3(TF_THREADS), smem_c, st, TF_CLUSTER, a); break;
+            case 4: e = launch_pdl_cluster(k_tiny_fused<4, TF_CLUSTER>, gc, dim3(TF_THREADS), smem_c, st, TF_CLUSTER, a); break;
+            case 8: e = launch_pdl_cluster(k_tiny_fused<8, TF_CLUSTER>, gc, dim3(TF_THREADS), smem_c, st, TF_CLUSTER, a); break;
+            default: e = launch_pdl_cluster(k_tiny_fused<16, TF_CLUSTER>, gc, dim3(TF_THREADS), smem_c, st, TF_CLUSTER, a); break;
+        }
+        AFG_CUDA(ctx, e);
+        return AFG_OK;
+    }
     switch (a.G) {
         case 1: e = launch_pdl(k_tiny_fused<1>, dim3(grid), dim3(TF_THREADS), L.total, st, a); break;
         case 2: e = launch_pdl(k_tiny_fused<2>, dim3(grid), dim3(TF_THREADS), L.total, st, a); break;

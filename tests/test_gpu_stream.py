@@ -42,7 +42,7 @@ def _oracle_stream(x, w):
             white[d, lo:hi] = orc.fir(x64[d], taps, WL.psd_len + lo, hi - lo)
     n_win = (q - WL.win_len) // WL.stride + 1
     z = orc.infer_windows(WL.net, w, white, WL.win_len, 0, WL.stride, n_win)
-    return z, orc.integrate(z, WL.n_int)
+    return z, orc.integrate(z, WL.n_int), white
 
 
 @pytest.fixture(scope="module")
@@ -58,13 +58,20 @@ def test_stream_matches_oracle(weights, capsys):
     _push_all(ctx, sid, x)
     ctx.stream_flush()
     r = ctx.stream_poll(sid)
-    z, st = _oracle_stream(x, weights)
+    z, st, white = _oracle_stream(x, weights)
     assert len(r) == len(st) and np.array_equal(r["window"], np.arange(WL.n_int - 1, len(z)))
     err_z = np.abs(r["logit"] - z[WL.n_int - 1:]) / (1 + np.abs(z[WL.n_int - 1:]))
     err_s = np.abs(r["stat"] - st) / (1 + np.abs(st))
+    # the same BF16 network over the oracle's whitened strain: only the stream's FP32
+    # whitening (rounding ~1e-6 of unit variance) separates the two, so a tolerance ten
+    # times the alone-vs-mix one catches any misplaced or mis-scaled whitened sample
+    zb = ctx.infer_windows(torch.from_numpy(white.astype(np.float32)).cuda(), 0, WL.stride, len(z)).cpu().numpy()
+    err_w = np.abs(r["logit"] - zb[WL.n_int - 1:]) / (1 + np.abs(zb[WL.n_int - 1:]))
     with capsys.disabled():
-        print(f"\nstream: {len(r)} results, max |dz|/(1+|z|) = {err_z.max():.3e}, stat {err_s.max():.3e}")
+        print(f"\nstream: {len(r)} results, max |dz|/(1+|z|) = {err_z.max():.3e}, stat {err_s.max():.3e}, "
+              f"vs BF16 network on oracle-whitened strain {err_w.max():.3e}")
     assert err_z.max() < BF16_LOGIT_TOL and err_s.max() < BF16_LOGIT_TOL
+    assert err_w.max() < 10 * MIX_TOL
     assert np.all(r["t_done"] >= r["t_push"])
     ctx.close()
 
