@@ -35,14 +35,22 @@ constexpr int TF_WARPS = TF_THREADS / 32;
 constexpr int TF_C = 16;                   // channels of the fused network
 constexpr int TF_WIMG = 3 * 2 * TF_C * 16;  // bytes of one conv's weight image (3 taps x 512 B)
 constexpr int TF_GROUPS = 3;                // MMA commit groups per conv (8 M subtiles each at W = 3072)
-constexpr int TF_CLUSTER = 4;               // list mode, few windows: CTAs sharing one window
+constexpr int TF_CLUSTER = 8;               // list mode, few windows: CTAs sharing one window
 constexpr int TF_XCH = 64 * 4;              // bytes of the cluster exchange area after the shared-memory layout
+constexpr int TF_SMEM_MAX = 227 * 1024;     // opt-in shared memory per CTA
+
+// segment descriptors a batch launch keeps in shared memory (after the layout of total bytes)
+__host__ inline int tiny_seg_cache_cap(size_t total) {
+    const int64_t room = ((int64_t)TF_SMEM_MAX - (int64_t)total) / (int64_t)sizeof(SegDesc);
+    return (int)std::max<int64_t>(0, std::min<int64_t>(room, 256));
+}
 
 struct TinyArgs {
     const float *y;
     int64_t n_y, y_stride, first, stride, shift, n_win;
     const SegDesc *segs;            // batch mode (n_seg > 0): per-segment window descriptors
     int n_seg;
+    int seg_cache;                  // batch mode: n_seg if the descriptors are copied to shared memory, else 0
     const WinPtr *wins;             // list mode (non-null): window i reads wins[i].y0 / y1, writes *wins[i].out
     int64_t shift_step;
     const float *params;            // stem w [16][2][k], stem gamma/beta, per conv gamma/beta, fc w [16], fc b
@@ -246,7 +254,8 @@ struct WinLoc {
     int64_t n_y, start, l1_shift, out;
 };
 
-__device__ __forceinline__ WinLoc locate_window(const TinyArgs &args, int64_t win) {
+// segs: the segment descriptors (the kernel's shared-memory copy where it made one)
+__device__ __forceinline__ WinLoc locate_window(const TinyArgs &args, int64_t win, const SegDesc *segs) {
     WinLoc w;
     w.y0 = args.y;
     w.y1 = nullptr;
@@ -268,10 +277,10 @@ __device__ __forceinline__ WinLoc locate_window(const TinyArgs &args, int64_t wi
         int lo = 0, hi = args.n_seg - 1;  // last segment with win_first <= win
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (args.segs[mid].win_first <= win) lo = mid;
+            if (segs[mid].win_first <= win) lo = mid;
             else hi = mid - 1;
         }
-        const SegDesc sd = args.segs[lo];
+        const SegDesc sd = segs[lo];
         const int64_t local = win - sd.win_first;
         const int64_t k = local / sd.n_win;  // timeslide index (0-based)
         const int64_t j = local - k * sd.n_win;
@@ -372,12 +381,23 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         const int c = (tid >> 1) & 1, row = (tid & 1) ? Wl + 1 : 0;
         *reinterpret_cast<uint4 *>(buf + c * act_chunk + (size_t)row * 16) = make_uint4(0, 0, 0, 0);
     }
+    // batch mode: the segment descriptors in shared memory (after the layout), so that locating a
+    // window (a binary search per window, on every window's critical path) reads no global memory
+    if (CL == 1 && args.seg_cache > 0) {
+        SegDesc *seg_sm = reinterpret_cast<SegDesc *>(sm + L.total);
+        for (int i = tid; i < args.seg_cache; i += TF_THREADS) seg_sm[i] = args.segs[i];
+    }
+    // (recomputed where used: keeping the pointer live across the window loop costs a register)
+    auto segs_at = [&]() -> const SegDesc * {
+        return (CL == 1 && args.seg_cache > 0) ? reinterpret_cast<const SegDesc *>(sm + tiny_smem(Wl, n_conv, k).total)
+                                               : args.segs;
+    };
     if (tid == 0) {
         for (int g = 0; g < TF_GROUPS; ++g) tc::mbar_init(&bar[g], 1);
         tc::fence_mbar_init();
         *abort_flag = 0;
     }
-    // a split window needs 96 columns: 128 leaves room for CTAs of one cluster that share an SM
+    // a split window needs at most 96 columns: 128 leaves room for CTAs of one cluster that share an SM
     if (warp == 0) {
         tc::tmem_alloc(tmem_slot, CL > 1 ? 128 : 512);
         tc::tmem_relinquish();
@@ -401,13 +421,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     const float *xs0 = xs + 4 - pad, *xs1 = xs + (Wl + 8) + 4 - pad;  // padded index p of each detector row
 
     const int64_t win0 = blockIdx.x / CL, win_step = gridDim.x / CL;
-    WinLoc cur = locate_window(args, win0);
+    WinLoc cur = locate_window(args, win0, segs_at());
     bool prefetched = false;  // the window's samples were copied asynchronously during the previous one
     pdl_wait();  // list mode: the whitened rings come from the whitening launch before (set-up above overlaps it)
     for (int64_t win = win0; win < args.n_win; win += win_step) {
         if (CL > 1) {
             // this CTA's slice of the window with pad samples each side (zero beyond the window)
-            cur = locate_window(args, win);
+            cur = locate_window(args, win, segs_at());
             const int q0 = (int)rank * Wl, n = Wl + 2 * pad, RP = Wl + 8;
             for (int c = tid; c < 2 * n; c += TF_THREADS) {
                 const int d = c >= n, sl = c - d * n - pad, g = q0 + sl;
@@ -440,14 +460,23 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     u[r] = xs0[t + r];
                     u[3 + r] = xs1[t + r];
                 }
+                // upper triangle row by row; two entries of a row per packed FP32x2 FMA
                 int m = 0;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
                     S[i] += u[i];
 #pragma unroll
-                    for (int jj = i; jj < 6; ++jj) {
-                        M[m] = fmaf(u[i], u[jj], M[m]);
-                        ++m;
+                    for (int jj = i; jj < 6; jj += 2) {
+                        if (jj + 1 < 6) {
+                            const float2 r2 = __ffma2_rn(make_float2(u[jj], u[jj + 1]), make_float2(u[i], u[i]),
+                                                         make_float2(M[m], M[m + 1]));
+                            M[m] = r2.x;
+                            M[m + 1] = r2.y;
+                            m += 2;
+                        } else {
+                            M[m] = fmaf(u[i], u[jj], M[m]);
+                            ++m;
+                        }
                     }
                 }
             }
@@ -539,10 +568,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                         a0 = fmaf(wr[c][i], u[i], a0);
                         a1 = fmaf(wr[c + 1][i], u[i], a1);
                     }
-                    a0 = fmaxf(fmaf(a0, sc8[c], sh8[c]), 0.f);
-                    a1 = fmaxf(fmaf(a1, sc8[c + 1], sh8[c + 1]), 0.f);
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(a0, a1);
-                    pk[c / 2] = *reinterpret_cast<uint32_t *>(&b2);
+                    pk[c / 2] = tc::pack_bf16x2_relu(fmaf(a0, sc8[c], sh8[c]), fmaf(a1, sc8[c + 1], sh8[c + 1]));
                 }
                 *reinterpret_cast<uint4 *>(dstc + (size_t)(t + 1) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
@@ -575,6 +601,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     } else if (MT == 6) {
                         tiny_issue<2>(tmem + (uint32_t)(j_lo * TF_C), ad00 + (uint64_t)(128 * j_lo), bd00,
                                       idesc);  // a quarter of such a window (cluster of 4)
+                    } else if (MT == 3) {
+                        tiny_issue<1>(tmem + (uint32_t)(j_lo * TF_C), ad00 + (uint64_t)(128 * j_lo), bd00,
+                                      idesc);  // an eighth of such a window (cluster of 8)
                     } else {
                         for (int j = j_lo; j < j_hi; ++j)
                             for (int r = 0; r < 3; ++r)
@@ -585,11 +614,12 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 }
             }
             const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-            // ---- epilogue pass 1: GroupNorm statistics, group by group as the MMAs complete
+            // ---- epilogue pass 1: GroupNorm statistics, group by group as the MMAs complete;
+            // (sum, sum of squares) of a group as one packed FP32x2 FMA per value
             {
-                float s[TF_C], q[TF_C];
+                float2 sq[G];
 #pragma unroll
-                for (int g = 0; g < TF_C; ++g) s[g] = q[g] = 0.f;
+                for (int g = 0; g < G; ++g) sq[g] = make_float2(0.f, 0.f);
                 bool ok = true;
                 for (int grp = 0; grp < TF_GROUPS; ++grp) {
                     if (!tc::mbar_wait(&bar[grp], phase & 1, 1000000000ull)) ok = false;
@@ -603,18 +633,15 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                         tc::tmem_wait_ld();
 #pragma unroll
                         for (int c = 0; c < TF_C; ++c) {
-                            const int g = c / (TF_C / G);
                             const float v = __uint_as_float(r0[c]);
-                            s[g] += v;
-                            q[g] = fmaf(v, v, q[g]);
+                            sq[c / (TF_C / G)] = __ffma2_rn(make_float2(v, v), make_float2(1.f, v), sq[c / (TF_C / G)]);
                         }
                         if (j1 < j_hi) {
 #pragma unroll
                             for (int c = 0; c < TF_C; ++c) {
-                                const int g = c / (TF_C / G);
                                 const float v = __uint_as_float(r1[c]);
-                                s[g] += v;
-                                q[g] = fmaf(v, v, q[g]);
+                                sq[c / (TF_C / G)] =
+                                    __ffma2_rn(make_float2(v, v), make_float2(1.f, v), sq[c / (TF_C / G)]);
                             }
                         }
                     }
@@ -632,9 +659,15 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 if (CL == 1 && last && win_next < args.n_win) {
                     // buffer B (the staging of the raw window) is free once the last conv's MMAs
                     // have read it: copy the next window's samples meanwhile
-                    cur = locate_window(args, win_next);
+                    cur = locate_window(args, win_next, segs_at());
                     load_window(args, cur, xs, W, pad, true);
                     prefetched = true;
+                }
+                float s[TF_C], q[TF_C];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    s[g] = sq[g].x;
+                    q[g] = sq[g].y;
                 }
                 const float *gb = conv_gb + l * 2 * TF_C;
                 if (CL > 1) gn_reduce_cluster<G, CL>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift, xch + 32);
@@ -663,32 +696,34 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                         const int row = 128 * j + 32 * (warp & 3) + lane + 1;
 #pragma unroll
                         for (int ch = 0; ch < 2; ++ch) {
-                            float val[8];
+                            // normalise, residual add, ReLU two channels per instruction (packed FP32x2);
+                            // the ReLU of stored values is folded into the BF16 conversion
+                            float2 val[4];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                val[e] = fmaf(__uint_as_float(rr[ch * 8 + e]), sc[ch * 8 + e], sh[ch * 8 + e]);
+                            for (int e = 0; e < 4; ++e)
+                                val[e] = __ffma2_rn(make_float2(__uint_as_float(rr[ch * 8 + 2 * e]),
+                                                                __uint_as_float(rr[ch * 8 + 2 * e + 1])),
+                                                    make_float2(sc[ch * 8 + 2 * e], sc[ch * 8 + 2 * e + 1]),
+                                                    make_float2(sh[ch * 8 + 2 * e], sh[ch * 8 + 2 * e + 1]));
                             if (second) {
                                 const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk +
                                                                                  (size_t)row * 16);
                                 const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    val[2 * e] += __uint_as_float(w4[e] << 16);
-                                    val[2 * e + 1] += __uint_as_float(w4[e] & 0xffff0000u);
-                                }
+                                for (int e = 0; e < 4; ++e)
+                                    val[e] = __fadd2_rn(val[e], make_float2(__uint_as_float(w4[e] << 16),
+                                                                            __uint_as_float(w4[e] & 0xffff0000u)));
                             }
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) val[e] = fmaxf(val[e], 0.f);
                             if (last) {
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) hs[ch * 8 + e] += val[e];
+                                for (int e = 0; e < 4; ++e) {
+                                    hs[ch * 8 + 2 * e] += fmaxf(val[e].x, 0.f);
+                                    hs[ch * 8 + 2 * e + 1] += fmaxf(val[e].y, 0.f);
+                                }
                             } else {
                                 uint32_t pk[4];
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    __nv_bfloat162 b2 = __floats2bfloat162_rn(val[2 * e], val[2 * e + 1]);
-                                    pk[e] = *reinterpret_cast<uint32_t *>(&b2);
-                                }
+                                for (int e = 0; e < 4; ++e) pk[e] = tc::pack_bf16x2_relu(val[e].x, val[e].y);
                                 *reinterpret_cast<uint4 *>(dst + ch * act_chunk + (size_t)row * 16) =
                                     make_uint4(pk[0], pk[1], pk[2], pk[3]);
                             }
@@ -801,7 +836,8 @@ int net_tc_prepare(afg_ctx *ctx) {
     P.tc_wimg = static_cast<unsigned char *>(d) + ((pbytes + 255) / 256) * 256;
     AFG_CUDA(ctx, cudaMemcpy(P.tc_params, prm.data(), pbytes, cudaMemcpyHostToDevice));
     AFG_CUDA(ctx, cudaMemcpy(P.tc_wimg, img.data(), ibytes, cudaMemcpyHostToDevice));
-    const int smem = (int)tiny_smem(ctx->cfg.win_len, n_conv, k).total;
+    const size_t base = tiny_smem(ctx->cfg.win_len, n_conv, k).total;
+    const int smem = (int)(base + tiny_seg_cache_cap(base) * sizeof(SegDesc));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -831,6 +867,7 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     const int n_conv = (int)P.convs.size() - 1;
     const int W = ctx->cfg.win_len;
     TinyArgs a;
+    memset(&a, 0, sizeof a);
     a.y = white;
     a.n_y = 0;
     a.y_stride = y_stride;
@@ -852,17 +889,19 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     a.G = P.net.groups;
     a.eps = P.net.eps;
     const Smem L = tiny_smem(W, n_conv, a.k_stem);
+    a.seg_cache = n_seg <= tiny_seg_cache_cap(L.total) ? n_seg : 0;
+    const size_t smem = L.total + (size_t)a.seg_cache * sizeof(SegDesc);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const unsigned grid = (unsigned)std::min<int64_t>(total_win, std::max(sms, 1));
     const double flops = 2.0 * total_win * W * TF_C * ((3.0 * TF_C) * n_conv + 2.0 * a.k_stem);
     KScope ks(ctx, st, KK_TINY_TC, flops, (double)total_win * (2.0 * W * 4.0 + 4.0));
     switch (a.G) {
-        case 1: k_tiny_fused<1><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        case 2: k_tiny_fused<2><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        case 4: k_tiny_fused<4><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        case 8: k_tiny_fused<8><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        default: k_tiny_fused<16><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 1: k_tiny_fused<1><<<grid, TF_THREADS, smem, st>>>(a); break;
+        case 2: k_tiny_fused<2><<<grid, TF_THREADS, smem, st>>>(a); break;
+        case 4: k_tiny_fused<4><<<grid, TF_THREADS, smem, st>>>(a); break;
+        case 8: k_tiny_fused<8><<<grid, TF_THREADS, smem, st>>>(a); break;
+        default: k_tiny_fused<16><<<grid, TF_THREADS, smem, st>>>(a); break;
     }
     AFG_LAUNCH_CHECK(ctx, "k_tiny_fused(batch)");
     return AFG_OK;
@@ -933,6 +972,7 @@ int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
     const int n_conv = (int)P.convs.size() - 1;
     const int W = ctx->cfg.win_len;
     TinyArgs a;
+    memset(&a, 0, sizeof a);
     a.segs = nullptr;
     a.n_seg = 0;
     a.wins = nullptr;
