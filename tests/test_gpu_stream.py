@@ -76,6 +76,40 @@ def test_stream_matches_oracle(weights, capsys):
     ctx.close()
 
 
+def test_stream_small_steps_on_clusters(weights):
+    """Steps of one 0.25 s push each (4 new windows): the latency-bound network launch, where
+    each window is split over a cluster of CTAs that exchange GroupNorm statistics and halo
+    rows through distributed shared memory.  The warm-up runs in large steps (one CTA per
+    window); every result of both kinds is checked against the oracle and against the same
+    BF16 network run on the oracle's whitened strain."""
+    x = _strain(74.0, 5)
+    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
+    ctx.stream_start(max_streams=4)
+    sid = ctx.stream_open()
+    warm = 67 * WL.fs
+    _push_all(ctx, sid, x[:, :warm], chunk=4096)
+    ctx.stream_flush()
+    steps0 = ctx.stream_stats()["steps"]
+    n_small = 0
+    for a in range(warm, x.shape[1], 512):
+        ctx.stream_push(sid, x[:, a:a + 512])
+        ctx.stream_flush()  # one push per step
+        n_small += 1
+    assert ctx.stream_stats()["steps"] - steps0 == n_small
+    r = ctx.stream_poll(sid)
+    z, st, white = _oracle_stream(x, weights)
+    assert len(r) == len(st) and np.array_equal(r["window"], np.arange(WL.n_int - 1, len(z)))
+    n_late = int(np.sum(r["window"] >= (warm - WL.psd_len - WL.crop - WL.win_len) // WL.stride))
+    assert n_late >= 4 * (n_small - 1)  # results produced by the small steps
+    err_z = np.abs(r["logit"] - z[WL.n_int - 1:]) / (1 + np.abs(z[WL.n_int - 1:]))
+    err_s = np.abs(r["stat"] - st) / (1 + np.abs(st))
+    zb = ctx.infer_windows(torch.from_numpy(white.astype(np.float32)).cuda(), 0, WL.stride, len(z)).cpu().numpy()
+    err_w = np.abs(r["logit"] - zb[WL.n_int - 1:]) / (1 + np.abs(zb[WL.n_int - 1:]))
+    assert err_z.max() < BF16_LOGIT_TOL and err_s.max() < BF16_LOGIT_TOL
+    assert err_w.max() < 10 * MIX_TOL, err_w.max()
+    ctx.close()
+
+
 def test_stream_same_alone_and_in_the_mix(weights):
     xa = _strain(80.0, 7)
     ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
