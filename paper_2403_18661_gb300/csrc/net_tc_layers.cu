@@ -989,6 +989,234 @@ __global__ void __launch_bounds__(STEM_T) k_stem_bf16(const float *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------- stem on the tensor cores
+// The stem conv (C0 = 64 outputs, 2 inputs, k <= 8 taps, stride s) as an implicit GEMM per
+// window: M = the L0 output positions in subtiles of 128, N = 64, K = 2k zero-padded to 16,
+// one tcgen05.mma per subtile.  A is an im2col tile built in shared memory from the window's
+// samples (row t = x0[s t - pad + r], r < k, then x1[...], BF16, K-major without swizzle:
+// element (t, kk) at (kk / 8) * L0 * 16 + t * 16 + (kk % 8) * 2), B the 64 x 16 weight tile.
+// Rounds of 4 subtiles (256 TMEM columns, so two CTAs share an SM) run twice: first for the
+// GroupNorm sums (read from TMEM), then to normalise, apply ReLU and max-pool (neighbouring
+// positions are neighbouring lanes; the position before each 32-lane block comes through a
+// shared edge table) and store BF16 chunk-major rows.
+constexpr int STC_T = 256;      // threads: 8 warps, two per TMEM lane quarter (32 columns each)
+constexpr int STC_C = 64;       // output channels
+constexpr int STC_RS = 4;       // subtiles per round
+constexpr int STC_COLS = 256;   // TMEM columns per CTA (STC_RS x 64)
+
+struct StemTcSmem {
+    size_t xs, a, b, edge, red, scl, bar, total;
+};
+__host__ __device__ inline StemTcSmem stem_tc_smem(int W, int k, int L0) {
+    StemTcSmem m;
+    const int pad = k / 2, Wp = W + 2 * pad;
+    m.xs = 0;
+    m.a = ((size_t)2 * Wp * 4 + 127) / 128 * 128;
+    m.b = m.a + (size_t)2 * L0 * 16;
+    m.edge = m.b + (size_t)2 * STC_C * 16;
+    m.red = m.edge + (size_t)(L0 / 32) * STC_C * 4;
+    m.scl = m.red + (size_t)(STC_T / 32) * 32 * 4;
+    m.bar = m.scl + (size_t)2 * STC_C * 4;
+    m.total = m.bar + 16;
+    return m;
+}
+
+// CG: channels per GroupNorm group (a divisor of 32)
+template <int CG>
+__global__ void __launch_bounds__(STC_T, 2) k_stem_tc(const float *__restrict__ y, int64_t n_y, int64_t y_stride,
+                                                      int64_t first, int64_t stride, int64_t shift, int64_t w0,
+                                                      const float *__restrict__ wt, const float *__restrict__ gamma,
+                                                      const float *__restrict__ beta, int k, int s, int W, int L0,
+                                                      int pool, float eps, int *err, __nv_bfloat16 *__restrict__ out) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int NLG = 32 / CG;  // groups in a warp's 32 channels
+    const StemTcSmem L = stem_tc_smem(W, k, L0);
+    float *xs = reinterpret_cast<float *>(sm + L.xs);
+    unsigned char *As = sm + L.a, *Bs = sm + L.b;
+    float *edge = reinterpret_cast<float *>(sm + L.edge);
+    float *red = reinterpret_cast<float *>(sm + L.red);
+    float *scl = reinterpret_cast<float *>(sm + L.scl), *shf = scl + STC_C;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + L.bar + 8);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = warp & 3, ch = warp >> 2;  // TMEM lane quarter, column half
+    const int pad = k / 2, Wp = W + 2 * pad;
+    const int64_t win = w0 + blockIdx.x;
+    const int64_t start = first + win * stride;
+
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, STC_COLS);
+        tc::tmem_relinquish();
+    }
+    // the window's samples (zero outside it), FP32
+    for (int t = tid; t < Wp; t += STC_T) {
+        const int tt = t - pad;
+        float a = 0.f, b = 0.f;
+        if (tt >= 0 && tt < W) {
+            a = y[start + tt];
+            int64_t i1 = start + shift + tt;
+            if (i1 >= n_y) i1 -= n_y;
+            b = y[y_stride + i1];
+        }
+        xs[t] = a;
+        xs[Wp + t] = b;
+    }
+    // weight tile: element (c, kk), kk = ci * k + r, from wt[c][ci][r]
+    for (int i = tid; i < STC_C * 16; i += STC_T) {
+        const int c = i >> 4, kk = i & 15;
+        const float v = kk < 2 * k ? wt[c * 2 * k + kk] : 0.f;
+        reinterpret_cast<__nv_bfloat16 *>(Bs + (kk >> 3) * STC_C * 16 + c * 16)[kk & 7] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+    // im2col rows, 16 bytes per K half
+    for (int t = tid; t < L0; t += STC_T) {
+        uint32_t pk[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            float v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int kk = 2 * h + e, ci = kk >= k ? 1 : 0, r = kk - ci * k;
+                v[e] = kk < 2 * k ? xs[ci * Wp + t * s + r] : 0.f;
+            }
+            pk[h] = tc::pack_bf16x2(v[0], v[1]);
+        }
+        *reinterpret_cast<uint4 *>(As + (size_t)t * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4 *>(As + (size_t)L0 * 16 + (size_t)t * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * ch);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, STC_C);
+    const uint64_t ad0 = tc::desc_kmajor_noswizzle(tc::smem_addr(As), (uint32_t)(L0 * 16), 128);
+    const uint64_t bd0 = tc::desc_kmajor_noswizzle(tc::smem_addr(Bs), STC_C * 16, 128);
+    const int MT = L0 / 128, rounds = MT / STC_RS;
+    uint32_t phase = 0;
+    bool ok = true;
+    // one round: MMAs of subtiles RS*rd .. + RS into columns 64 m, then wait for them
+    auto mma_round = [&](int rd) {
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int m = 0; m < STC_RS; ++m)
+                tc::mma_bf16(tmem + (uint32_t)(64 * m), ad0 + (uint64_t)((128 * (STC_RS * rd + m) * 16) >> 4), bd0,
+                             idesc, 0u);
+            tc::mma_commit(bar);
+        }
+        if (!tc::mbar_wait(bar, phase & 1, 1000000000ull)) ok = false;
+        phase++;
+        tc::fence_after_sync();
+    };
+
+    // ---- pass 1: GroupNorm sums (sum, sum of squares) of the warp's NLG groups
+    float2 gs[NLG];
+#pragma unroll
+    for (int g = 0; g < NLG; ++g) gs[g] = make_float2(0.f, 0.f);
+    for (int rd = 0; rd < rounds; ++rd) {
+        mma_round(rd);
+#pragma unroll 1
+        for (int m = 0; m < STC_RS; ++m) {
+            float v[32];
+            tc::tmem_ld32(tq + (uint32_t)(64 * m), v);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) gs[c / CG] = __ffma2_rn(make_float2(v[c], v[c]), make_float2(1.f, v[c]), gs[c / CG]);
+        }
+        tc::fence_before_sync();
+        __syncthreads();  // every TMEM read of the round is done before the next round's MMAs
+    }
+#pragma unroll
+    for (int g = 0; g < NLG; ++g)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gs[g].x += __shfl_xor_sync(0xffffffffu, gs[g].x, o);
+            gs[g].y += __shfl_xor_sync(0xffffffffu, gs[g].y, o);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int g = 0; g < NLG; ++g) {
+            red[warp * 32 + 2 * g] = gs[g].x;
+            red[warp * 32 + 2 * g + 1] = gs[g].y;
+        }
+    __syncthreads();
+    if (tid < STC_C) {
+        const int c = tid, h = c >> 5, g = (c & 31) / CG;
+        float a = 0.f, b = 0.f;
+        for (int qq = 0; qq < 4; ++qq) {  // the four warps of column half h
+            a += red[(h * 4 + qq) * 32 + 2 * g];
+            b += red[(h * 4 + qq) * 32 + 2 * g + 1];
+        }
+        const float cnt = (float)L0 * (float)CG;
+        const float mean = a / cnt;
+        const float var = fmaxf(b / cnt - mean * mean, 0.f);
+        const float sc = rsqrtf(var + eps) * gamma[c];
+        scl[c] = sc;
+        shf[c] = beta[c] - mean * sc;
+    }
+    __syncthreads();
+
+    // ---- pass 2: normalise + ReLU (+ max-pool) -> BF16 chunk-major rows
+    const int Lo = pool ? (L0 + 2 - 3) / 2 + 1 : L0;
+    const size_t cstride = (size_t)(Lo + 2) * 8;
+    __nv_bfloat16 *ow = out + (size_t)blockIdx.x * (STC_C / 8) * cstride;
+    const float *sc = scl + 32 * ch, *sh = shf + 32 * ch;  // (warp-uniform shared reads)
+    for (int rd = 0; rd < rounds; ++rd) {
+        mma_round(rd);
+#pragma unroll 1
+        for (int m = 0; m < STC_RS; ++m) {
+            const int j = STC_RS * rd + m, blk = 4 * j + q, t = 32 * blk + lane;
+            float z[32];
+            tc::tmem_ld32(tq + (uint32_t)(64 * m), z);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) z[c] = fmaxf(fmaf(z[c], sc[c], sh[c]), 0.f);
+            if (pool && lane == 31)
+#pragma unroll
+                for (int c = 0; c < 32; ++c) edge[blk * STC_C + 32 * ch + c] = z[c];
+            __syncthreads();  // the edge of the block before this one is written
+            uint32_t pk[16];
+            if (pool) {
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    float lo0 = __shfl_up_sync(0xffffffffu, z[c], 1), lo1 = __shfl_up_sync(0xffffffffu, z[c + 1], 1);
+                    const float hi0 = __shfl_down_sync(0xffffffffu, z[c], 1);
+                    const float hi1 = __shfl_down_sync(0xffffffffu, z[c + 1], 1);
+                    if (lane == 0) {
+                        lo0 = blk > 0 ? edge[(blk - 1) * STC_C + 32 * ch + c] : -INFINITY;
+                        lo1 = blk > 0 ? edge[(blk - 1) * STC_C + 32 * ch + c + 1] : -INFINITY;
+                    }
+                    pk[c / 2] = tc::pack_bf16x2(fmaxf(fmaxf(lo0, z[c]), hi0), fmaxf(fmaxf(lo1, z[c + 1]), hi1));
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) pk[c / 2] = tc::pack_bf16x2(z[c], z[c + 1]);
+            }
+            const int u = pool ? t >> 1 : t;
+            if ((!pool || !(lane & 1)) && u < Lo) {
+#pragma unroll
+                for (int c8 = 0; c8 < 4; ++c8)  // chunks 4 ch .. 4 ch + 3, row u + 1
+                    *reinterpret_cast<uint4 *>(ow + (size_t)(4 * ch + c8) * cstride + (size_t)(u + 1) * 8) =
+                        make_uint4(pk[4 * c8], pk[4 * c8 + 1], pk[4 * c8 + 2], pk[4 * c8 + 3]);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    // zero pad rows of the 8 chunks
+    if (tid < 16) {
+        const int c8 = tid >> 1, row = (tid & 1) ? Lo + 1 : 0;
+        *reinterpret_cast<uint4 *>(ow + (size_t)c8 * cstride + (size_t)row * 8) = make_uint4(0, 0, 0, 0);
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, STC_COLS);
+}
+
 // grid (n_win), block 256: logit = fc_b + sum_c fc_w[c] * mean_t x[t][c] (bf16 chunk-major input,
 // C / 8 <= 256 chunks); each thread sums 8 channels of one chunk over a subset of rows
 __global__ void k_head_bf16(const __nv_bfloat16 *__restrict__ x, int L, int C, const float *__restrict__ fc_w,
@@ -1248,8 +1476,28 @@ int net_tc_layers_prepare(afg_ctx *ctx) {
     }
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT));
+    {
+        const ConvLayer &S = P.convs[0];
+        const int smem = (int)stem_tc_smem(ctx->cfg.win_len, S.k, S.lout).total;
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_stem_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_stem_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_stem_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_stem_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        AFG_CUDA(ctx, cudaFuncSetAttribute(k_stem_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    }
     ctx->tcplan = tp;
     return AFG_OK;
+}
+
+// The stem runs on the tensor cores where its shape fits k_stem_tc: 64 outputs, 2 k <= 16,
+// whole rounds of 4 subtiles of 128 positions, groups of 2..32 channels.
+static bool stem_tc_fits(const afg_ctx *ctx) {
+    const ConvLayer &S = ctx->plan.convs[0];
+    const int G = ctx->plan.net.groups;
+    if (S.cout != STC_C || S.cin != 2 || 2 * S.k > 16 || S.lout % (128 * STC_RS) || G < 2 || STC_C % G) return false;
+    const int cg = STC_C / G;
+    return cg >= 2 && cg <= 32 && !(cg & (cg - 1)) &&
+           stem_tc_smem(ctx->cfg.win_len, S.k, S.lout).total <= (size_t)SMEM_LIMIT;
 }
 
 void net_tc_layers_release(afg_ctx *ctx) {
@@ -1505,11 +1753,27 @@ int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_
             const double fl = 2.0 * nw * (double)S.lout * S.cout * 2.0 * S.k;
             const double by = (double)nw * (2.0 * W * 4.0 + 2.0 * (P.l_after_stem + 2) * S.cout);
             KScope ks(ctx, st, KK_STEM, fl, by);
-            k_stem_bf16<<<nw, STEM_T, stem_smem, st>>>(y, n_y, y_stride, first, stride, shift, w0, S.wt, S.gamma,
-                                                       S.beta, S.cout, S.k, S.stride, W, S.lout, P.net.stem_pool,
-                                                       P.net.groups, P.net.eps, bA);
+            if (stem_tc_fits(ctx)) {
+                const size_t sm_tc = stem_tc_smem(W, S.k, S.lout).total;
+                const int cg = S.cout / P.net.groups;
+#define AFG_STEM_TC(CGV)                                                                                         \
+    k_stem_tc<CGV><<<nw, STC_T, sm_tc, st>>>(y, n_y, y_stride, first, stride, shift, w0, S.wt, S.gamma, S.beta, \
+                                             S.k, S.stride, W, S.lout, P.net.stem_pool, P.net.eps, ctx->d_err, bA)
+                switch (cg) {
+                    case 2: AFG_STEM_TC(2); break;
+                    case 4: AFG_STEM_TC(4); break;
+                    case 8: AFG_STEM_TC(8); break;
+                    case 16: AFG_STEM_TC(16); break;
+                    default: AFG_STEM_TC(32); break;
+                }
+#undef AFG_STEM_TC
+            } else {
+                k_stem_bf16<<<nw, STEM_T, stem_smem, st>>>(y, n_y, y_stride, first, stride, shift, w0, S.wt, S.gamma,
+                                                           S.beta, S.cout, S.k, S.stride, W, S.lout, P.net.stem_pool,
+                                                           P.net.groups, P.net.eps, bA);
+            }
         }
-        AFG_LAUNCH_CHECK(ctx, "k_stem_bf16");
+        AFG_LAUNCH_CHECK(ctx, "stem");
         __nv_bfloat16 *A = bA, *Cb = bC, *B = bB, *D = bD;
         for (const BlockPlan &bp : P.blocks) {
             const ConvLayer &c1 = P.convs[bp.c1], &c2 = P.convs[bp.c2];
