@@ -78,6 +78,23 @@ struct WhitenPiece {
     int64_t y_ring;     // ring length (each row holds 2 * y_ring samples)
     int64_t y_pos;      // ring slot of output 0 (< y_ring)
     int64_t cnt;        // outputs of the piece (<= WB)
+    // Samples not yet in the raw ring (4096-point kernel only): input i >= i_new is
+    // stg[i - i_new] (detector row d at stg + d * stg_stride) instead of x[i]; stg null: all from x.
+    const float *stg;
+    int64_t stg_stride, i_new;
+    // If sc_ring is set, this piece's CTAs also write those sc_n samples into the stream's mirrored
+    // raw ring (row stride 2 sc_R) at slot sc_pos: one piece per stream, so no separate scatter.
+    float *sc_ring;
+    int64_t sc_R, sc_pos, sc_n;
+};
+
+// One new window of a stream whose 1 s statistic a serving step produces: the mean of the
+// logits of windows w - n_int + 1 .. w, read from the stream's logit ring (STREAM_LR slots).
+constexpr int STREAM_LR = 64;
+struct IntegDesc {
+    const float *ring;  // logits ring of the stream
+    int64_t w;          // window index
+    float *out;         // (stat, logit) pair
 };
 
 struct Workspace {
@@ -266,6 +283,7 @@ int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, flo
 int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,
                         cudaStream_t st);
 int whiten_multi_piece_max(const afg_ctx *ctx);  // outputs per piece of launch_whiten_multi
+bool whiten_multi_takes_staging(const afg_ctx *ctx);  // pieces may carry stg / sc_ring
 // net_fp32.cu
 int net_plan_build(afg_ctx *ctx, const float *weights_host, int64_t n_weights);
 int launch_infer_fp32(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
@@ -286,7 +304,10 @@ int net_tc_tiles_set(afg_ctx *ctx, const afg_tile *in, int n);
 int net_tc_prepare(afg_ctx *ctx);
 int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, const SegDesc *segs_dev, int n_seg,
                             int64_t total_win, int64_t stride, int64_t shift_step, float *logits, cudaStream_t st);
-int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, cudaStream_t st);
+// integ (n_integ entries, may be 0): statistics the launch computes once all its windows are
+// done (the last CTA to finish, counted in *done, which must be 0 on entry and is left at 0)
+int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, const IntegDesc *integ,
+                           int n_integ, int n_int, unsigned *done, cudaStream_t st);
 int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                       int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 // resample.cu

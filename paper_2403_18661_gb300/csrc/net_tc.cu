@@ -52,6 +52,9 @@ struct TinyArgs {
     int n_seg;
     int seg_cache;                  // batch mode: n_seg if the descriptors are copied to shared memory, else 0
     const WinPtr *wins;             // list mode (non-null): window i reads wins[i].y0 / y1, writes *wins[i].out
+    const IntegDesc *integ;         // list mode: statistics to form once every window is done (or null)
+    int n_integ, n_int;
+    unsigned *done;                 // windows completed (integ only); the last CTA integrates and resets it
     int64_t shift_step;
     const float *params;            // stem w [16][2][k], stem gamma/beta, per conv gamma/beta, fc w [16], fc b
     const unsigned char *wimg;      // n_conv x TF_WIMG bytes, BF16, shared-memory image order
@@ -761,10 +764,47 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            bool last_win = false;
             if (lane == 0) {
                 const float z = fc_b + part;
                 if (out_ptr) *out_ptr = z;
                 else args.logits[out] = z;
+                if (args.integ) {  // publish the logit, then count the window
+                    __threadfence();
+                    last_win = atomicAdd(args.done, 1u) == (unsigned)(args.n_win - 1);
+                }
+            }
+            if (__shfl_sync(0xffffffffu, last_win, 0)) {
+                // every logit of the launch is written: the statistics of the new windows, lane l
+                // loading logit w - n_int + 1 + l (+ 32 ...) of 8 statistics at a time, then a warp sum
+                // in a fixed order (the loads of a batch are all in flight together)
+                __threadfence();
+                for (int i0 = 0; i0 < args.n_integ; i0 += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        v[b] = 0.f;
+                        if (i0 + b < args.n_integ) {
+                            const IntegDesc d = args.integ[i0 + b];
+                            for (int l = lane; l < args.n_int; l += 32)
+                                v[b] += __ldcg(d.ring + (d.w - args.n_int + 1 + l) % STREAM_LR);
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < 8; ++b)
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v[b] += __shfl_xor_sync(0xffffffffu, v[b], o);
+                    if (lane < 8 && i0 + lane < args.n_integ) {
+                        float tot = v[0];
+#pragma unroll
+                        for (int b = 1; b < 8; ++b)
+                            if (lane == b) tot = v[b];
+                        const IntegDesc d = args.integ[i0 + lane];
+                        d.out[0] = tot / (float)args.n_int;
+                        d.out[1] = __ldcg(d.ring + d.w % STREAM_LR);
+                    }
+                }
+                if (lane == 0) *args.done = 0u;
             }
         }
         __syncthreads();
@@ -907,7 +947,8 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     return AFG_OK;
 }
 
-int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, cudaStream_t st) {
+int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, const IntegDesc *integ,
+                           int n_integ, int n_int, unsigned *done, cudaStream_t st) {
     const NetPlan &P = ctx->plan;
     if (!tiny_compatible(ctx) || !P.tc_params)
         return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "streams: the BF16 path covers one-stage 16-channel networks");
@@ -918,6 +959,12 @@ int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, 
     memset(&a, 0, sizeof a);
     a.wins = wins_dev;
     a.n_win = n_win;
+    if (n_integ > 0) {
+        a.integ = integ;
+        a.n_integ = n_integ;
+        a.n_int = n_int;
+        a.done = done;
+    }
     a.stride = 1;
     a.params = P.tc_params;
     a.wimg = P.tc_wimg;

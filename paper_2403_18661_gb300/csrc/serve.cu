@@ -14,7 +14,8 @@
 // The engine (one host thread per context) forms a step from every chunk
 // pushed so far: one H2D copy and a scatter kernel into the raw rings, one
 // whitening launch for every stream's new samples, one network launch for
-// every new window, one integration launch and one D2H copy.  PSD and filter
+// every new window (whose last CTA also integrates them in small steps; an
+// integration launch in large ones) and one D2H copy.  PSD and filter
 // refreshes are enqueued after a step's result event, as soon as a stream's
 // raw strain covers the 64 s before an epoch, ahead of that epoch's first
 // whitened sample.  Chunks pushed while a step runs join the next one; two
@@ -22,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -33,7 +35,9 @@
 
 namespace {
 
-constexpr int LR = 64;  // logits ring per stream
+constexpr int LR = STREAM_LR;  // logits ring per stream
+constexpr double kPollS = 20e-3;  // the idle engine polls for pushes this long before it sleeps
+constexpr int kFuseInteg = 64;   // steps with at most this many new statistics integrate in the network launch
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -45,12 +49,6 @@ struct ScatterDesc {
     int64_t pos;      // slot of the first new sample (< R)
     int64_t n;        // new samples per detector
     int64_t src;      // offset of the chunk in the staging buffer ([2][n] per chunk)
-};
-
-struct IntegDesc {
-    const float *ring;  // logits ring of the stream
-    int64_t w;          // window index
-    float *out;         // (stat, logit) pair
 };
 
 // grid (n_desc): copy each staged chunk into its stream's mirrored raw ring
@@ -69,8 +67,9 @@ __global__ void k_scatter(const ScatterDesc *__restrict__ d, const float *__rest
     }
 }
 
-// one thread per new window: stat = mean of the last n_int logits (oldest first)
-// (Launched as a programmatic dependent of the network launch before it.)
+// one thread per new window: stat = mean of the last n_int logits (oldest first); for large
+// steps, where the network launch's last CTA would integrate them one warp at a time
+// (launched as a programmatic dependent of the network launch)
 __global__ void k_stream_integrate(const IntegDesc *__restrict__ d, int n, int n_int) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const IntegDesc s = d[i < n ? i : 0];
@@ -134,9 +133,11 @@ struct ServeEngine {
     std::vector<Slot> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
+    std::atomic<uint64_t> pushes{0};  // chunks pushed so far (polled by the idle engine without the lock)
     bool stop = false;
     std::thread th;
     cudaStream_t st = nullptr;
+    unsigned *d_done = nullptr;  // completion counter of the network launch (integration by its last CTA)
     StepBuf buf[2];
     int err = AFG_OK;
     int64_t steps = 0, windows = 0, samples = 0;
@@ -254,8 +255,11 @@ int launch_step(ServeEngine &E, StepBuf &b) {
     int64_t total_white = 0;
     b.res.clear();
     b.slots.clear();
-    // 1) stage the chunks and describe the scatter into the raw rings
-    for (Taken &t : taken) {
+    // 1) stage the chunks and describe their scatter into the raw rings
+    std::vector<ScatterDesc> scs(taken.size());
+    std::vector<int64_t> p_old(taken.size());
+    for (size_t ti = 0; ti < taken.size(); ++ti) {
+        Taken &t = taken[ti];
         Slot &sl = E.slots[t.slot];
         int64_t n = 0;
         for (Chunk &c : t.chunks) n += c.n;
@@ -272,7 +276,8 @@ int launch_step(ServeEngine &E, StepBuf &b) {
         d.pos = sl.P % E.R;
         d.n = n;
         d.src = (int64_t)stage_off;
-        b.h_sc[n_sc++] = d;
+        scs[ti] = d;
+        p_old[ti] = sl.P;
         stage_off += 2 * n;
         sl.P += n;
         b.slots.push_back(t.slot);
@@ -280,7 +285,10 @@ int launch_step(ServeEngine &E, StepBuf &b) {
     // 2) whitening pieces (and the gains refreshes they still need); 3) windows
     std::vector<std::pair<int, int64_t>> refresh;  // (slot, epoch) built after the scatter, before the pieces
     const int64_t piece_max = whiten_multi_piece_max(ctx);
-    for (Taken &t : taken) {
+    const bool staged = whiten_multi_takes_staging(ctx);
+    std::vector<int> first_piece(taken.size(), -1);  // a stream's first piece also scatters its chunk
+    for (size_t ti = 0; ti < taken.size(); ++ti) {
+        Taken &t = taken[ti];
         Slot &sl = E.slots[t.slot];
         const double t_push = t.chunks.back().t_push;
         const int64_t q_new = std::max(sl.Q, sl.P - p.psd_len - F / 2 + 1);
@@ -302,6 +310,15 @@ int launch_step(ServeEngine &E, StepBuf &b) {
             wp.y_ring = E.Wr;
             wp.y_pos = j % E.Wr;
             wp.cnt = end - j;
+            // samples from the step's chunks come straight from the staging copy
+            wp.stg = staged ? b.d_stage + scs[ti].src : nullptr;
+            wp.stg_stride = scs[ti].n;
+            wp.i_new = p_old[ti] - (p.psd_len + j - F / 2);
+            wp.sc_ring = nullptr;
+            wp.sc_R = E.R;
+            wp.sc_pos = scs[ti].pos;
+            wp.sc_n = scs[ti].n;
+            if (first_piece[ti] < 0) first_piece[ti] = n_wp;
             b.h_wp[n_wp++] = wp;
             total_white += end - j;
             j = end;
@@ -324,6 +341,16 @@ int launch_step(ServeEngine &E, StepBuf &b) {
             b.h_win[n_win++] = wptr;
         }
     }
+    // Scatter: inside the whitening launch (a stream's first piece) unless a gains refresh must read
+    // the new samples from the ring first, or the stream has no piece this step, or the whitening
+    // kernel reads only the ring; those go through k_scatter.
+    const bool fuse = staged && refresh.empty();
+    for (size_t ti = 0; ti < taken.size(); ++ti) {
+        if (fuse && first_piece[ti] >= 0) b.h_wp[first_piece[ti]].sc_ring = scs[ti].ring;
+        else b.h_sc[n_sc++] = scs[ti];
+    }
+    if (!fuse)
+        for (int i = 0; i < n_wp; ++i) b.h_wp[i].stg = nullptr;
     // one H2D copy: chunks, then the descriptors
     const int n_res = (int)b.res.size();
     char *hb = reinterpret_cast<char *>(b.h_stage), *db = reinterpret_cast<char *>(b.d_stage);
@@ -341,24 +368,30 @@ int launch_step(ServeEngine &E, StepBuf &b) {
     memcpy(hb + o_win, b.h_win, n_win * sizeof(WinPtr));
     memcpy(hb + o_int, b.h_int, n_res * sizeof(IntegDesc));
     AFG_CUDA(ctx, cudaMemcpyAsync(db, hb, off, cudaMemcpyHostToDevice, st));
-    {
-        KScope ks(ctx, st, KK_SCATTER, 0.0, (double)stage_off * 12.0);
-        k_scatter<<<n_sc, 256, 0, st>>>(reinterpret_cast<const ScatterDesc *>(db + o_sc), b.d_stage);
+    if (n_sc) {
+        {
+            KScope ks(ctx, st, KK_SCATTER, 0.0, (double)stage_off * 12.0);
+            k_scatter<<<n_sc, 256, 0, st>>>(reinterpret_cast<const ScatterDesc *>(db + o_sc), b.d_stage);
+        }
+        AFG_LAUNCH_CHECK(ctx, "k_scatter");
     }
-    AFG_LAUNCH_CHECK(ctx, "k_scatter");
     for (const auto &r : refresh)
         if (refresh_gains(E, E.slots[r.first], r.second, st)) return -1;
     if (n_wp && launch_whiten_multi(ctx, reinterpret_cast<const WhitenPiece *>(db + o_wp), n_wp, total_white, st))
         return -1;
-    if (n_win && launch_infer_bf16_list(ctx, reinterpret_cast<const WinPtr *>(db + o_win), n_win, st)) return -1;
-    if (n_res) {
-        {
-            KScope ks(ctx, st, KK_INTEGRATE, (double)n_res * p.n_int, (double)n_res * (p.n_int + 2) * 4.0);
-            AFG_CUDA(ctx, launch_pdl(k_stream_integrate, dim3((unsigned)((n_res + 127) / 128)), dim3(128), 0, st,
-                                     reinterpret_cast<const IntegDesc *>(db + o_int), n_res, (int)p.n_int));
-        }
-        AFG_CUDA(ctx, cudaMemcpyAsync(b.h_out, b.d_out, n_res * 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    // small steps: the network launch also integrates the new windows (its last CTA, after every
+    // logit); large ones use one thread per statistic in a launch of their own
+    const IntegDesc *integ = reinterpret_cast<const IntegDesc *>(db + o_int);
+    const bool fuse_integ = n_res <= kFuseInteg;
+    if (n_win && launch_infer_bf16_list(ctx, reinterpret_cast<const WinPtr *>(db + o_win), n_win, integ,
+                                        fuse_integ ? n_res : 0, (int)p.n_int, E.d_done, st))
+        return -1;
+    if (n_res && !fuse_integ) {
+        KScope ks(ctx, st, KK_INTEGRATE, (double)n_res * p.n_int, (double)n_res * (p.n_int + 2) * 4.0);
+        AFG_CUDA(ctx, launch_pdl(k_stream_integrate, dim3((unsigned)((n_res + 127) / 128)), dim3(128), 0, st, integ,
+                                 n_res, (int)p.n_int));
     }
+    if (n_res) AFG_CUDA(ctx, cudaMemcpyAsync(b.h_out, b.d_out, n_res * 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
     AFG_CUDA(ctx, cudaEventRecord(b.ev, st));
     // Refreshes ahead of need: a stream whose raw strain now covers the 64 s before its
     // current or next epoch gets that epoch's PSD and gains here, after this step's result
@@ -396,7 +429,26 @@ void engine_main(ServeEngine *E) {
             for (const Slot &s : E->slots) any = any || (s.open && !s.pending.empty());
             if (!any && !E->buf[0].busy && !E->buf[1].busy) {
                 if (E->stop) break;
-                E->cv_work.wait_for(lock, std::chrono::milliseconds(50));
+                // Idle: poll for the next push for up to kPollS before sleeping, since a thread woken
+                // from a condition variable starts tens of microseconds late (one busy core while
+                // pushes keep coming; arrivals further apart pay the wake-up).
+                const uint64_t seen = E->pushes.load(std::memory_order_acquire);
+                lock.unlock();
+                const double t0 = now_s();
+                bool got = false;
+                while (now_s() - t0 < kPollS)
+                    if (E->pushes.load(std::memory_order_acquire) != seen) {
+                        got = true;
+                        break;
+                    }
+                if (got) continue;
+                lock.lock();
+                E->cv_work.wait_for(lock, std::chrono::milliseconds(50), [&] {
+                    if (E->stop) return true;
+                    for (const Slot &s : E->slots)
+                        if (s.open && !s.pending.empty()) return true;
+                    return false;
+                });
                 continue;
             }
         }
@@ -441,6 +493,7 @@ void serve_release(afg_ctx *ctx) {
     free_step(E->buf[0]);
     free_step(E->buf[1]);
     if (E->st) cudaStreamDestroy(E->st);
+    if (E->d_done) cudaFree(E->d_done);
     delete E;
     ctx->serve = nullptr;
 }
@@ -470,6 +523,8 @@ extern "C" int afg_stream_start(afg_ctx *ctx, const afg_stream_params *p) {
     int rc = alloc_step(ctx, E->buf[0], p->max_streams, E->per_stream_new, p->stride);
     if (!rc) rc = alloc_step(ctx, E->buf[1], p->max_streams, E->per_stream_new, p->stride);
     if (!rc && cudaStreamCreateWithFlags(&E->st, cudaStreamNonBlocking) != cudaSuccess) rc = AFG_ERR_CUDA;
+    if (!rc && (cudaMalloc(&E->d_done, 16) != cudaSuccess || cudaMemset(E->d_done, 0, 16) != cudaSuccess))
+        rc = AFG_ERR_CUDA;
     // the Welch scratch at its per-refresh size (no allocation inside steps)
     void *tmp = nullptr;
     const int64_t K = (p->psd_len - NFFT) / hop + 1;
@@ -555,6 +610,7 @@ extern "C" int afg_stream_push(afg_ctx *ctx, int64_t id, const float *chunk_host
         sl.pushed++;
         sl.pending.push_back(std::move(c));
     }
+    E->pushes.fetch_add(1, std::memory_order_release);
     E->cv_work.notify_one();
     return AFG_OK;
 }

@@ -486,8 +486,10 @@ int whiten_piece_max_s(int F) {
 // out(q, value).  The taps span fewer than 4096 lags, so the gains of this grid are those
 // of the 16384-point grid at every 4th bin; they are rescaled by 4 for the shorter
 // transform's 1 / 2048 normalisation (exact in FP32).
+// stg (may be null): input i >= i_new comes from stg[i - i_new] instead of src[i].
 template <typename Out>
 __device__ __forceinline__ void whiten_block_s(unsigned char *smem, const float *__restrict__ src, int64_t avail,
+                                               const float *__restrict__ stg, int64_t i_new,
                                                const float *__restrict__ gk, int F, int64_t cnt, Out out) {
     using namespace r16;
     constexpr int GS = NC / NC_S;  // bins of the 16384-point grid per bin of this one
@@ -498,11 +500,15 @@ __device__ __forceinline__ void whiten_block_s(unsigned char *smem, const float 
     const int half = F / 2;
     const int64_t need = cnt + F - 1;
     const int64_t lim = need < avail ? need : avail;
+    auto sample = [&](int64_t i) -> float {
+        if (i >= lim) return 0.0f;
+        return (stg && i >= i_new) ? stg[i - i_new] : src[i];
+    };
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int64_t i0 = 2 * (int64_t)(t + NT_S * r);
-        v[r] = make_float2(i0 < lim ? src[i0] : 0.0f, i0 + 1 < lim ? src[i0 + 1] : 0.0f);
+        v[r] = make_float2(sample(i0), sample(i0 + 1));
     }
     forward_s(d, v);
     cp_async_wait_all();
@@ -551,9 +557,21 @@ __global__ void __launch_bounds__(r16::NT_S) k_whiten_multi_s(const WhitenPiece 
     const WhitenPiece pc = pieces[blockIdx.x];
     pdl_wait();  // raw rings (scatter) and gains (refresh) come from the kernels before
     const int det = blockIdx.y;
+    const float *stg = pc.stg ? pc.stg + det * pc.stg_stride : nullptr;
+    if (pc.sc_ring) {  // the stream's new samples into its mirrored raw ring (read by later steps)
+        float *row = pc.sc_ring + det * 2 * pc.sc_R;
+        for (int64_t k = threadIdx.x; k < pc.sc_n; k += r16::NT_S) {
+            int64_t m = pc.sc_pos + k;
+            if (m >= pc.sc_R) m -= pc.sc_R;
+            const float v = stg[k];
+            row[m] = v;
+            row[m + pc.sc_R] = v;
+        }
+    }
     float *yr = pc.y + det * pc.y_stride;
     const int64_t ring = pc.y_ring, pos = pc.y_pos;
-    whiten_block_s(smem_raw, pc.x + det * pc.x_stride, pc.cnt + F - 1, pc.gains + det * NBIN, F, pc.cnt,
+    whiten_block_s(smem_raw, pc.x + det * pc.x_stride, pc.cnt + F - 1, stg, pc.i_new, pc.gains + det * NBIN, F,
+                   pc.cnt,
                    [yr, ring, pos](int64_t q, float v) {
                        int64_t m = pos + q;
                        if (m >= ring) m -= ring;
@@ -676,6 +694,8 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
     AFG_LAUNCH_CHECK(ctx, "k_whiten");
     return AFG_OK;
 }
+
+bool whiten_multi_takes_staging(const afg_ctx *ctx) { return whiten_piece_max_s(ctx->cfg.fir_len) != 0; }
 
 // Most outputs one piece of launch_whiten_multi may hold.
 int whiten_multi_piece_max(const afg_ctx *ctx) {
