@@ -21,8 +21,8 @@
 // split X_k = E_k + W^k O_k, E_k = (Z_k + conj Z_{NC-k}) / 2,
 // O_k = (Z_k - conj Z_{NC-k}) / 2i, W = exp(-2 pi i / NFFT).
 //
-// A 2048-point variant (real transforms of 4096 samples, 128 threads, radix
-// 16, 16, 4 and the fused radix 2) serves short whitening pieces of streams.
+// A 2048-point variant (real transforms of 4096 samples, 512 threads, radix-4
+// passes and the fused radix 2) serves short whitening pieces of streams.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -198,66 +198,67 @@ __device__ __forceinline__ void split_inv(float2 yk, float2 ynk, float2 w, float
     znk = conj(csub(e, io));
 }
 
-// ---- 2048-point variant (real transforms of 4096 samples) on NT_S = 128 threads:
-// forward radix 16, 16, 4 at Ns = 1, 16, 256, then the fused radix-2 pass at 1024;
-// inverse (after the fused pass) radix 16, 16 at Ns = 2, 32 and radix 4 at Ns = 512.
-// Every thread still holds 16 points per pass (four radix-4 butterflies).
+// ---- 2048-point variant (real transforms of 4096 samples) on NT_S = 512 threads, one
+// radix-4 butterfly per thread per pass: forward radix 4 at Ns = 1, 4, 16, 64, 256, then the
+// fused radix-2 pass at 1024; inverse (after the fused pass) radix 4 at Ns = 2, 8, 32, 128, 512.
+// (Short pieces are latency-bound: four points per thread and more threads beat sixteen.)
 constexpr int NC_S = 2048;
-constexpr int NT_S = NC_S / 16;
+constexpr int NT_S = NC_S / 4;
 constexpr int SLOTS_S = NC_S + NC_S / 16;
 
-// four radix-4 butterflies b = t + 128 q of a pass at stride Ns: inputs b + 512 r, twiddles,
-// DFT; v[q][r] holds output r of butterfly q
-template <int S, int Ns> __device__ __forceinline__ void butterflies4_s(const float2 *d, float2 (&v)[4][4]) {
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int b = t + NT_S * q;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) v[q][r] = d[pad(b + (NC_S / 4) * r)];
+// radix-4 butterfly of thread j at stride Ns: twiddles exp(S 2 pi i r k / 4 Ns), k = j mod Ns, DFT
+template <int S, int Ns> __device__ __forceinline__ void butterfly4_s(float2 (&v)[4], int j) {
+    if (Ns > 1) {
+        const float2 w1 = cis<S>((float)(j & (Ns - 1)) / (float)(2 * Ns));
+        const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
     }
+    dft4<S>(v[0], v[1], v[2], v[3]);
+}
+
+template <int Ns> __device__ __forceinline__ void store4_s(float2 *d, const float2 (&v)[4], int j) {
+    const int k = j & (Ns - 1), base = (j - k) * 4 + k;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int k = (t + NT_S * q) & (Ns - 1);
-        const float x = (float)k / (float)(2 * Ns);  // exp(S 2 pi i r k / (4 Ns)) = exp(S i pi x r)
-        const float2 w1 = cis<S>(x), w2 = cis<S>(2.0f * x);
-        v[q][1] = cmul(v[q][1], w1);
-        v[q][2] = cmul(v[q][2], w2);
-        v[q][3] = cmul(v[q][3], cmul(w1, w2));
-        dft4<S>(v[q][0], v[q][1], v[q][2], v[q][3]);
-    }
+    for (int r = 0; r < 4; ++r) d[pad(base + r * Ns)] = v[r];
+}
+
+__device__ __forceinline__ void load4_s(float2 (&v)[4], const float2 *d, int j) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) v[r] = d[pad(j + NT_S * r)];
 }
 
 template <int S, int Ns> __device__ __forceinline__ void pass4_s(float2 *d) {
-    float2 v[4][4];
-    butterflies4_s<S, Ns>(d, v);
+    const int j = threadIdx.x;
+    float2 v[4];
+    load4_s(v, d, j);
+    butterfly4_s<S, Ns>(v, j);
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int b = threadIdx.x + NT_S * q, k = b & (Ns - 1);
-        const int base = (b - k) * 4 + k;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) d[pad(base + r * Ns)] = v[q][r];
-    }
+    store4_s<Ns>(d, v, j);
     __syncthreads();
 }
 
-// forward passes before the fused one: v holds z[t + 128 r] on entry
-__device__ __forceinline__ void forward_s(float2 *d, float2 (&v)[16]) {
+// forward passes before the fused one: v holds z[t + 512 r] on entry
+__device__ __forceinline__ void forward_s(float2 *d, float2 (&v)[4]) {
     const int j = threadIdx.x;
-    dft16<-1>(v);
-    store16<1>(d, v, j);
+    butterfly4_s<-1, 1>(v, j);
+    store4_s<1>(d, v, j);
     __syncthreads();
-    pass16<-1, 16, NT_S>(d);
+    pass4_s<-1, 4>(d);
+    pass4_s<-1, 16>(d);
+    pass4_s<-1, 64>(d);
     pass4_s<-1, 256>(d);
 }
 
-// inverse passes after the fused one; output r of butterfly q is complex sample
-// t + 128 q + 512 r, returned in v[q][r]
-__device__ __forceinline__ void inverse_s(float2 *d, float2 (&v)[4][4]) {
-    pass16<+1, 2, NT_S>(d);
-    pass16<+1, 32, NT_S>(d);
-    butterflies4_s<+1, NC_S / 4>(d, v);
+// inverse passes after the fused one; output r of thread t is complex sample t + 512 r, in v[r]
+__device__ __forceinline__ void inverse_s(float2 *d, float2 (&v)[4]) {
+    pass4_s<+1, 2>(d);
+    pass4_s<+1, 8>(d);
+    pass4_s<+1, 32>(d);
+    pass4_s<+1, 128>(d);
+    load4_s(v, d, threadIdx.x);
+    butterfly4_s<+1, NC_S / 4>(v, threadIdx.x);
 }
 
 }  // namespace r16

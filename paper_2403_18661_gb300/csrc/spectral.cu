@@ -504,9 +504,9 @@ __device__ __forceinline__ void whiten_block_s(unsigned char *smem, const float 
         if (i >= lim) return 0.0f;
         return (stg && i >= i_new) ? stg[i - i_new] : src[i];
     };
-    float2 v[16];
+    float2 v[4];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < 4; ++r) {
         const int64_t i0 = 2 * (int64_t)(t + NT_S * r);
         v[r] = make_float2(sample(i0), sample(i0 + 1));
     }
@@ -515,21 +515,20 @@ __device__ __forceinline__ void whiten_block_s(unsigned char *smem, const float 
     __syncthreads();
     for (int k = t; k <= NC_S; k += NT_S) gs[k] *= (float)GS;
     __syncthreads();
-    float2 o[4][4], ox[4];
-    if (t == 0) whiten_mid_task0<NC_S>(d, gs, o[0]);
-    else whiten_mid_task<NC_S>(d, gs, t, o[0]);
-#pragma unroll
-    for (int m = 1; m < 4; ++m) whiten_mid_task<NC_S>(d, gs, t + NT_S * m, o[m]);
+    // one task per thread (tasks 0 .. NC_S / 4 - 1), the last thread also task NC_S / 4
+    static_assert(NT_S == NC_S / 4, "one mid-pass task per thread");
+    float2 o[4], ox[4];
+    if (t == 0) whiten_mid_task0<NC_S>(d, gs, o);
+    else whiten_mid_task<NC_S>(d, gs, t, o);
     if (t == NT_S - 1) whiten_mid_task<NC_S>(d, gs, NC_S / 4, ox);
     __syncthreads();
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int j = t + NT_S * m, jc = NC_S / 2 - j;
-        d[pad(2 * j)] = o[m][0];
-        d[pad(2 * j + 1)] = o[m][1];
+    {
+        const int j = t, jc = NC_S / 2 - j;
+        d[pad(2 * j)] = o[0];
+        d[pad(2 * j + 1)] = o[1];
         if (j != 0) {
-            d[pad(2 * jc)] = o[m][2];
-            d[pad(2 * jc + 1)] = o[m][3];
+            d[pad(2 * jc)] = o[2];
+            d[pad(2 * jc + 1)] = o[3];
         }
     }
     if (t == NT_S - 1) {
@@ -537,20 +536,18 @@ __device__ __forceinline__ void whiten_block_s(unsigned char *smem, const float 
         d[pad(NC_S / 2 + 1)] = ox[1];
     }
     __syncthreads();
-    float2 y[4][4];
+    float2 y[4];
     inverse_s(d, y);
-    // complex sample c = t + 128 q + 512 r holds real samples 2c, 2c + 1; output q0 = 2c - F/2
+    // complex sample c = t + 512 r holds real samples 2c, 2c + 1; output q0 = 2c - F/2
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int64_t q0 = 2 * (int64_t)(t + NT_S * q + (NC_S / 4) * r) - half;
-            if (q0 >= 0 && q0 < cnt) out(q0, y[q][r].x);
-            if (q0 + 1 >= 0 && q0 + 1 < cnt) out(q0 + 1, y[q][r].y);
-        }
+    for (int r = 0; r < 4; ++r) {
+        const int64_t q0 = 2 * (int64_t)(t + NT_S * r) - half;
+        if (q0 >= 0 && q0 < cnt) out(q0, y[r].x);
+        if (q0 + 1 >= 0 && q0 + 1 < cnt) out(q0 + 1, y[r].y);
+    }
 }
 
-// k_whiten_multi with the 4096-point block: pieces of at most 4097 - F outputs.
+// k_whiten_multi with the 4096-point block (512 threads): pieces of at most 4097 - F outputs.
 __global__ void __launch_bounds__(r16::NT_S) k_whiten_multi_s(const WhitenPiece *__restrict__ pieces, int F) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_trigger();
