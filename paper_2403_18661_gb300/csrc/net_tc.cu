@@ -36,7 +36,11 @@ constexpr int TF_C = 16;                   // channels of the fused network
 constexpr int TF_WIMG = 3 * 2 * TF_C * 16;  // bytes of one conv's weight image (3 taps x 512 B)
 constexpr int TF_GROUPS = 3;                // MMA commit groups per conv (8 M subtiles each at W = 3072)
 constexpr int TF_CLUSTER = 8;               // list mode, few windows: CTAs sharing one window
-constexpr int TF_XCH = 64 * 4;              // bytes of the cluster exchange area after the shared-memory layout
+// cluster exchange area after the shared-memory layout (floats): [0, 32) stem moments, [32, 48)
+// GroupNorm partials, [48, 64) head sums, then per layer parity p the raw accumulators of the
+// CTA's first and last positions at 64 + 48 p + 16 side and their residual rows (BF16 pairs) at
+// 64 + 48 p + 32 + 8 side
+constexpr int TF_XCH = (64 + 2 * 48) * 4;
 constexpr int TF_SMEM_MAX = 227 * 1024;     // opt-in shared memory per CTA
 
 // segment descriptors a batch launch keeps in shared memory (after the layout of total bytes)
@@ -165,14 +169,6 @@ __device__ __forceinline__ float dsmem_ld(const float *p, uint32_t rank) {
     asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(dsmem_addr(p, rank)) : "memory");
     return v;
 }
-__device__ __forceinline__ uint4 dsmem_ld16(const void *p, uint32_t rank) {
-    uint4 v;
-    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "r"(dsmem_addr(p, rank))
-                 : "memory");
-    return v;
-}
 // sum of x[i] over the CL CTAs of the cluster, in rank order (the same total in every CTA)
 template <int CL> __device__ __forceinline__ float cluster_sum(const float *x) {
     float t = 0.f;
@@ -212,26 +208,6 @@ __device__ __forceinline__ void gn_reduce_cluster(float (&s)[TF_C], float (&q)[T
         scale[c] = a;
         shift[c] = beta[c] - mean * a;
     }
-    __syncthreads();
-}
-
-// Halo rows of a split window: row 0 of `buf` takes the left neighbour's last position
-// (its row Wl), row Wl + 1 the right neighbour's first (its row 1); the window's own
-// edges keep their zero rows.  After a cluster barrier that orders the neighbours' writes.
-template <int CL>
-__device__ __forceinline__ void halo_exchange(unsigned char *buf, size_t act_chunk, int Wl, uint32_t rank) {
-    cluster_sync_all();
-    if (threadIdx.x < 4) {
-        const int side = threadIdx.x >> 1, c = threadIdx.x & 1;
-        const bool has = side ? rank + 1 < (uint32_t)CL : rank > 0;
-        if (has) {
-            const uint32_t nb = side ? rank + 1 : rank - 1;
-            const int src_row = side ? 1 : Wl, dst_row = side ? Wl + 1 : 0;
-            const uint4 v = dsmem_ld16(buf + c * act_chunk + (size_t)src_row * 16, nb);
-            *reinterpret_cast<uint4 *>(buf + c * act_chunk + (size_t)dst_row * 16) = v;
-        }
-    }
-    tc::fence_proxy_async_smem();
     __syncthreads();
 }
 
@@ -349,8 +325,10 @@ __device__ __forceinline__ void load_window(const TinyArgs &args, const WinLoc &
 
 // CL > 1 (list mode only): a cluster of CL CTAs shares each window, CTA rank q taking
 // positions [q W / CL, (q + 1) W / CL); GroupNorm statistics, the stem moments and the
-// pooled head sums are summed over the cluster, and after every layer that writes an
-// activation each CTA fetches its neighbours' boundary rows.  Every CTA of a cluster
+// pooled head sums are summed over the cluster.  The halo rows (one neighbour position per
+// side) are built locally: the stem's from one more input sample per side, a conv's from
+// the neighbours' raw boundary accumulators and residuals, published with the GroupNorm
+// partials, so each layer costs one cluster barrier.  Every CTA of a cluster
 // runs the same sequence of cluster barriers whatever happens, so none can wait alone.
 template <int G, int CL = 1>
 __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs args) {
@@ -359,7 +337,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     const int W = args.W, Wl = W / CL, k = args.k_stem, pad = k / 2, n_conv = args.n_conv;
     const Smem L = tiny_smem(Wl, n_conv, k);
     const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
-    float *xch = reinterpret_cast<float *>(sm + L.total);  // CL > 1: [0, 32) moments, [32, 48) GN, [48, 64) head
+    float *xch = reinterpret_cast<float *>(sm + L.total);  // CL > 1: exchange area (TF_XCH)
     unsigned char *actA = sm + L.off_a;
     unsigned char *actB = sm + L.off_b;
     unsigned char *wimg = sm + L.off_w;
@@ -431,9 +409,10 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
         if (CL > 1) {
             // this CTA's slice of the window with pad samples each side (zero beyond the window)
             cur = locate_window(args, win, segs_at());
-            const int q0 = (int)rank * Wl, n = Wl + 2 * pad, RP = Wl + 8;
+            // pad + 1 samples each side: the stem of the halo positions -1 and Wl is computed here too
+            const int q0 = (int)rank * Wl, mg = pad + 1, n = Wl + 2 * mg, RP = Wl + 8;
             for (int c = tid; c < 2 * n; c += TF_THREADS) {
-                const int d = c >= n, sl = c - d * n - pad, g = q0 + sl;
+                const int d = c >= n, sl = c - d * n - mg, g = q0 + sl;
                 xs[d * RP + 4 + sl] = (g >= 0 && g < W) ? (d ? cur.y1 : cur.y0)[g] : 0.f;
             }
         } else if (prefetched) {
@@ -575,10 +554,34 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 }
                 *reinterpret_cast<uint4 *>(dstc + (size_t)(t + 1) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
+            if (CL > 1 && tid < 4) {
+                // halo rows 0 and Wl + 1: the stem at local positions -1 and Wl, the neighbours' edge
+                // positions, from the same samples, weights and cluster statistics (zero outside the window)
+                const int t = (tid >> 1) ? Wl : -1, g = (int)rank * Wl + t;
+                uint32_t pk[4] = {0u, 0u, 0u, 0u};
+                if (g >= 0 && g < W) {
+                    float u[6];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        u[r] = xs0[t + r];
+                        u[3 + r] = xs1[t + r];
+                    }
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) {
+                            a0 = fmaf(wr[c][i], u[i], a0);
+                            a1 = fmaf(wr[c + 1][i], u[i], a1);
+                        }
+                        pk[c / 2] = tc::pack_bf16x2_relu(fmaf(a0, sc8[c], sh8[c]), fmaf(a1, sc8[c + 1], sh8[c + 1]));
+                    }
+                }
+                *reinterpret_cast<uint4 *>(dstc + (size_t)(t + 1) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
         }
         tc::fence_proxy_async_smem();
         __syncthreads();
-        if (CL > 1) halo_exchange<CL>(actA, act_chunk, Wl, rank);
 
         float hs[TF_C];
 #pragma unroll
@@ -634,6 +637,23 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                         tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
                         if (j1 < j_hi) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
                         tc::tmem_wait_ld();
+                        if (CL > 1 && !last) {
+                            // raw accumulators of the CTA's first position (subtile 0, lane 0) and last
+                            // (subtile MT - 1, lane 127): the neighbours build their halo rows from them
+                            float *bnd = xch + 64 + 48 * (l & 1);
+                            if ((warp & 3) == 0 && lane == 0 && j0 == 0)
+#pragma unroll
+                                for (int c = 0; c < TF_C; ++c) bnd[c] = __uint_as_float(r0[c]);
+                            if ((warp & 3) == 3 && lane == 31) {
+                                if (j0 == MT - 1) {
+#pragma unroll
+                                    for (int c = 0; c < TF_C; ++c) bnd[16 + c] = __uint_as_float(r0[c]);
+                                } else if (j1 == MT - 1 && j1 < j_hi) {
+#pragma unroll
+                                    for (int c = 0; c < TF_C; ++c) bnd[16 + c] = __uint_as_float(r1[c]);
+                                }
+                            }
+                        }
 #pragma unroll
                         for (int c = 0; c < TF_C; ++c) {
                             const float v = __uint_as_float(r0[c]);
@@ -673,8 +693,38 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     q[g] = sq[g].y;
                 }
                 const float *gb = conv_gb + l * 2 * TF_C;
+                if (CL > 1 && !last && second && tid < 4) {
+                    // the residual (block input) of the first and last positions, before pass 2 overwrites it
+                    const int side = tid >> 1, ch = tid & 1;
+                    *reinterpret_cast<uint4 *>(xch + 64 + 48 * (l & 1) + 32 + 8 * side + 4 * ch) =
+                        *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + (size_t)(side ? Wl : 1) * 16);
+                }
                 if (CL > 1) gn_reduce_cluster<G, CL>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift, xch + 32);
                 else gn_reduce<G>(s, q, cnt, args.eps, gb, gb + TF_C, red, scale, shift);
+                if (CL > 1 && !last && tid < 4) {
+                    // halo rows of dst: the neighbours' edge outputs, computed here with the same arithmetic
+                    // as pass 2 (normalise, residual, ReLU in the BF16 conversion) from their raw accumulators
+                    const int side = tid >> 1, ch = tid & 1;
+                    if (side ? rank + 1 < (uint32_t)CL : rank > 0) {
+                        const uint32_t nb = side ? rank + 1 : rank - 1;
+                        const float *bnd = xch + 64 + 48 * (l & 1);
+                        const int from = side ? 0 : 16;  // right neighbour's first position, left's last
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int c = ch * 8 + 2 * e;
+                            float2 v = __ffma2_rn(make_float2(dsmem_ld(bnd + from + c, nb), dsmem_ld(bnd + from + c + 1, nb)),
+                                                  make_float2(scale[c], scale[c + 1]), make_float2(shift[c], shift[c + 1]));
+                            if (second) {
+                                const uint32_t w = __float_as_uint(dsmem_ld(bnd + 32 + 8 * (side ? 0 : 1) + 4 * ch + e, nb));
+                                v = __fadd2_rn(v, make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u)));
+                            }
+                            pk[e] = tc::pack_bf16x2_relu(v.x, v.y);
+                        }
+                        *reinterpret_cast<uint4 *>(dst + ch * act_chunk + (size_t)(side ? Wl + 1 : 0) * 16) =
+                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                }
             }
             // ---- epilogue pass 2: normalise (+ residual) + ReLU -> BF16 (two subtiles per TMEM wait)
             {
@@ -737,7 +787,6 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             tc::fence_before_sync();
             tc::fence_proxy_async_smem();
             __syncthreads();
-            if (CL > 1 && !last) halo_exchange<CL>(dst, act_chunk, Wl, rank);
         }
         if (aborted) break;
         // ---- head: global mean pool of the last block's output, then linear

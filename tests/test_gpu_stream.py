@@ -106,7 +106,9 @@ def test_stream_small_steps_on_clusters(weights):
     zb = ctx.infer_windows(torch.from_numpy(white.astype(np.float32)).cuda(), 0, WL.stride, len(z)).cpu().numpy()
     err_w = np.abs(r["logit"] - zb[WL.n_int - 1:]) / (1 + np.abs(zb[WL.n_int - 1:]))
     assert err_z.max() < BF16_LOGIT_TOL and err_s.max() < BF16_LOGIT_TOL
-    assert err_w.max() < 10 * MIX_TOL, err_w.max()
+    # the clustered network differs from one CTA per window only in its summation order (the
+    # same FP32 and BF16 arithmetic per element): the alone-vs-mix bound applies
+    assert err_w.max() < MIX_TOL, err_w.max()
     ctx.close()
 
 
