@@ -340,7 +340,11 @@ int afg_trigger_times(const afg_ctx *ctx, const afg_run_params *p, const int64_t
  * including the 0.5 s whitening crop after it, has been pushed.
  * A host engine thread per context forms one GPU step from every chunk
  * pushed so far (all streams, one launch per stage); chunks pushed while a
- * step runs join the next step.  Streams run the BF16 tensor-core network
+ * step runs join the next step.  When idle, the engine polls for the next push
+ * for 20 ms before it sleeps (a sleeping thread wakes tens of microseconds
+ * late), so it keeps one host core busy while pushes keep arriving.  PSD
+ * refreshes are built after a step's results, ahead of the epoch that needs
+ * them.  Streams run the BF16 tensor-core network
  * (precision AFG_BF16, a 16-channel one-stage network).  While streams are
  * active, make no other calls on the same context except the stream calls. */
 typedef struct afg_stream_params {
