@@ -112,6 +112,37 @@ def test_stream_small_steps_on_clusters(weights):
     ctx.close()
 
 
+def test_stream_round_robin_steps_match_alone(weights):
+    """Three streams pushed round-robin one 0.25 s chunk at a time, without waiting: the
+    engine forms steps of one or a few pushes of different streams, two of them in flight.
+    Each stream's results must equal the same stream analysed alone with the same chunking."""
+    xs = [_strain(72.0, 40 + i) for i in range(3)]
+    warm = 67 * WL.fs
+
+    def run(streams):
+        ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
+        ctx.stream_start(max_streams=4)
+        sids = [ctx.stream_open() for _ in streams]
+        for sid, x in zip(sids, streams):
+            _push_all(ctx, sid, x[:, :warm], chunk=4096)
+        ctx.stream_flush()
+        for a in range(warm, streams[0].shape[1], 512):
+            for sid, x in zip(sids, streams):
+                ctx.stream_push(sid, x[:, a:a + 512])
+        ctx.stream_flush()
+        out = [ctx.stream_poll(sid) for sid in sids]
+        ctx.close()
+        return out
+
+    mixed = run(xs)
+    for i, x in enumerate(xs):
+        alone = run([x])[0]
+        assert np.array_equal(mixed[i]["window"], alone["window"])
+        for key in ("logit", "stat"):
+            d = np.abs(mixed[i][key] - alone[key]) / (1 + np.abs(alone[key]))
+            assert d.max() <= MIX_TOL, (i, key, d.max())
+
+
 def test_stream_same_alone_and_in_the_mix(weights):
     xa = _strain(80.0, 7)
     ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
