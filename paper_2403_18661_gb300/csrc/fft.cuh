@@ -1,9 +1,10 @@
-// Shared-memory FFT building blocks (float and double), used by the Welch,
-// filter-build and whitening kernels.
+// Shared-memory FFT building blocks, templated on the complex type; the FP64
+// filter build uses them (the FP32 Welch and whitening transforms are in
+// fft16.cuh).
 //
 // Complex FFT of NC = 8192 points as a Stockham auto-sort sequence of
 // radix-8 passes (8*8*8*8) plus one radix-2 pass (and of 2048 points:
-// 8*8*8*4).  Each pass reads R points
+// 8*8*8*4, and of 512: 8*8*8).  Each pass reads R points
 // at stride NC/R into registers, applies the twiddles, does an in-register
 // DFT of size R and writes the R results at stride Ns; in place, with a
 // barrier between the reads and the writes.  Twiddles come from a table
