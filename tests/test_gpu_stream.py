@@ -28,7 +28,7 @@ def _push_all(ctx, sid, x, chunk=512):
         ctx.stream_push(sid, x[:, a:a + chunk])
 
 
-def _oracle_stream(x, w):
+def _oracle_stream(x, w, WL=WL):
     """Epoch-mode whitening of everything pushed, windows at the stream stride, 1 s integration."""
     x64 = x.astype(np.float64)
     P = x.shape[1]
@@ -109,6 +109,29 @@ def test_stream_small_steps_on_clusters(weights):
     # the clustered network differs from one CTA per window only in its summation order (the
     # same FP32 and BF16 arithmetic per element): the alone-vs-mix bound applies
     assert err_w.max() < MIX_TOL, err_w.max()
+    ctx.close()
+
+
+def test_stream_long_filter(weights):
+    """A 2 s (4096-tap) whitening filter: stream pieces are too long for the 4096-point block, so
+    the steps use the 16384-point multi-stream kernel and the separate scatter launch, and the
+    filters come from the one-CTA FP64 build (more than 2048 lags)."""
+    import dataclasses
+    wl = dataclasses.replace(WL, fir_len=4096)
+    x = _strain(86.0, 9)
+    ctx = abi.Context(wl, weights, precision=abi.AFG_BF16)
+    ctx.stream_start(max_streams=4)
+    sid = ctx.stream_open()
+    _push_all(ctx, sid, x)
+    ctx.stream_flush()
+    r = ctx.stream_poll(sid)
+    z, st, white = _oracle_stream(x, weights, wl)
+    assert len(r) == len(st) and len(r) > 100
+    err_s = np.abs(r["stat"] - st) / (1 + np.abs(st))
+    zb = ctx.infer_windows(torch.from_numpy(white.astype(np.float32)).cuda(), 0, wl.stride, len(z)).cpu().numpy()
+    err_w = np.abs(r["logit"] - zb[wl.n_int - 1:]) / (1 + np.abs(zb[wl.n_int - 1:]))
+    assert err_s.max() < BF16_LOGIT_TOL
+    assert err_w.max() < 10 * MIX_TOL, err_w.max()
     ctx.close()
 
 
