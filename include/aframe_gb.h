@@ -166,7 +166,8 @@ int afg_psd_estimate(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, int
  * x: [n_det][n] float32; psd: [n_det][n_psd][nfft/2+1] float64 (device);
  * y: [n_det][out_len] float32.
  * Requirements: out_first >= F/2 and out_first + out_len + F/2 - 1 <= n
- * (the crop), epoch_len % 8192 == 0 when epoch_len > 0. */
+ * (the crop), epoch_len % 8192 == 0 when epoch_len > 0.
+ * out_len = 0 writes nothing (y may then be NULL). */
 int afg_whiten(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, const double *psd, int64_t n_psd,
                int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, void *stream);
 
@@ -177,7 +178,8 @@ int afg_whiten(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, const dou
  * t in [0, W).  Windows are never materialised: the first convolution reads
  * them from y.  logits[j] = network(window j), float32.
  * y: [2][n_y] float32 whitened.  logits: [n_win] float32.
- * Requirements: first >= 0, first + (n_win-1)*stride + W <= n_y, 0 <= shift < n_y. */
+ * Requirements: first >= 0, first + (n_win-1)*stride + W <= n_y, 0 <= shift < n_y.
+ * n_win = 0 launches nothing (logits may then be NULL). */
 int afg_infer_windows(afg_ctx *ctx, const float *y, int64_t n_y, int64_t first, int64_t stride, int64_t n_win,
                       int64_t shift, float *logits, void *stream);
 

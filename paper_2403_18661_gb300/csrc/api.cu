@@ -242,7 +242,8 @@ int afg_whiten(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, const dou
                int64_t out_first, int64_t out_len, int64_t epoch_len, float *y, void *stream) {
     if (!ctx) return AFG_ERR_ARG;
     ctx->err.clear();
-    if (!x || !psd || !y || n_det < 1) return afg_fail(ctx, AFG_ERR_ARG, "whiten: null pointer or n_det < 1");
+    if (!x || !psd || (!y && out_len > 0) || n_det < 1)
+        return afg_fail(ctx, AFG_ERR_ARG, "whiten: null pointer or n_det < 1");
     int rc = check_whiten(ctx, n, n_psd, out_first, out_len, epoch_len);
     if (rc) return rc;
     return launch_whiten(ctx, x, n, n_det, psd, n_psd, out_first, out_len, epoch_len, y, out_len, S(stream));
@@ -261,7 +262,7 @@ int afg_infer_windows(afg_ctx *ctx, const float *y, int64_t n_y, int64_t first, 
     if (!ctx) return AFG_ERR_ARG;
     ctx->err.clear();
     const int W = ctx->cfg.win_len;
-    if (!y || !logits || n_win < 0 || stride < 1 || first < 0)
+    if (!y || (!logits && n_win > 0) || n_win < 0 || stride < 1 || first < 0)
         return afg_fail(ctx, AFG_ERR_ARG, "infer_windows: bad pointer, n_win, stride or first");
     if (n_win > 0 && first + (n_win - 1) * stride + W > n_y)
         return afg_fail(ctx, AFG_ERR_ARG, "infer_windows: last window reaches past n_y");

@@ -321,3 +321,38 @@ def test_bf16_resnet34_tensor_core_layers(capsys):
     assert d.max() < BF16_LOGIT_TOL and worst < BF16_LOGIT_TOL
     c16.close()
     c32.close()
+
+
+@pytest.mark.parametrize("precision", [abi.AFG_FP32, abi.AFG_BF16])
+def test_empty_and_degenerate_requests(c1, precision):
+    """Zero-size requests are no-ops; the smallest valid ones reduce to their definitions:
+    one Welch segment is one periodogram, and n_win = n_int integrates to a single mean."""
+    wl, x, w, ref = c1
+    ctx = abi.Context(wl, w, precision=precision)
+    xd = _dev(x)
+    # no windows, no whitened samples: nothing launched, nothing written
+    assert ctx.infer_windows(_dev(ref["white"].astype(np.float32)), 0, 512, 0).numel() == 0
+    psd = _dev(ref["psd"])
+    assert ctx.whiten(xd, psd, wl.crop, 0).numel() == 0
+    # one 8 s segment: the Welch mean of a single periodogram.  Its bins scatter exponentially
+    # about the spectrum, so a few sit far below it, where FP32 rounding (set by the spectrum,
+    # not by the bin) is a large fraction of the bin: bound the error by the local level, the
+    # mean of the reference over +-16 bins
+    got = ctx.psd_estimate(xd[:, :16384].contiguous()).cpu().numpy()
+    for d in range(2):
+        want = orc.welch(x[d, :16384].astype(np.float64), 16384, 8192, 2048.0)
+        level = np.convolve(want, np.ones(33) / 33, mode="same")
+        assert np.max(np.abs(got[d, 0] - want) / level) < PSD_RTOL
+    # n_win = n_int: one statistic, the mean of all logits; fewer windows are refused
+    z = np.random.default_rng(5).standard_normal(16).astype(np.float32)
+    stat, trig, n_trig = ctx.integrate(_dev(z), 16, 4)
+    assert stat.numel() == 1 and abs(float(stat.item()) - float(np.mean(z.astype(np.float64)))) < 1e-6
+    assert int(n_trig.item()) == 1 and int(trig[0].item()) == 0
+    # fewer windows than the integration length: refused by the library (called directly, with
+    # valid buffers, since the binding could not size the output)
+    zd, one = _dev(z[:8]), torch.zeros(1, dtype=torch.float32, device="cuda")
+    idx, cnt = torch.zeros(1, dtype=torch.int64, device="cuda"), torch.zeros(1, dtype=torch.int64, device="cuda")
+    rc = ctx._lib.afg_integrate(ctx._h, abi._ptr(zd), 8, 16, 4, abi._ptr(one), abi._ptr(idx), 1, abi._ptr(cnt),
+                                abi._stream(None))
+    assert rc == abi.AFG_ERR_ARG
+    ctx.close()
