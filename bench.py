@@ -40,9 +40,14 @@ from paper_2403_18661_gb300 import dist as pdist  # noqa: E402
 from paper_2403_18661_gb300 import inputs  # noqa: E402
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
-N_SM = 152
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2  # GB300: 1.25 TFLOP/s FP64 nominal = 152 SMs x 2 FMA/clk x 2 x 2.07 GHz
+
+
+def n_sm() -> int:
+    """Streaming multiprocessors of the current device (read from the device)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
 def load_peaks():
@@ -51,9 +56,10 @@ def load_peaks():
         with open(p) as f:
             d = json.load(f)
         d["_source"] = "measured"
-        return d
-    d = dict(FALLBACK_PEAKS)
-    d["_source"] = "fallback"
+    else:
+        d = dict(FALLBACK_PEAKS)
+        d["_source"] = "fallback"
+    d["n_sm"] = n_sm()
     return d
 
 
@@ -185,17 +191,18 @@ def dist_setup():
 def roofline_for(dom: dict, peaks: dict, step_ms_total: float) -> dict:
     """Roofline of the dominant kernel from its live CUDA-event time and algorithmic work."""
     sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sms = peaks["n_sm"]
     name = dom["name"]
     if name.startswith("conv_gemm_fp32"):
         bound, unit = "alu", "TFLOP/s"
         achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
-        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        src = f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x {sm_max:g} MHz"
+        peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        src = f"derived: {sms} SMs (read from the device) x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x {sm_max:g} MHz"
     elif name.startswith("filter_build_fp64"):
         bound, unit = "alu", "TFLOP/s"
         achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
-        peak = N_SM * FP64_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        src = f"derived: {N_SM} SMs x {FP64_LANES_PER_SM} FP64 FMA lanes x 2 x {sm_max:g} MHz"
+        peak = sms * FP64_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        src = f"derived: {sms} SMs (read from the device) x {FP64_LANES_PER_SM} FP64 FMA lanes x 2 x {sm_max:g} MHz"
     elif "bf16" in name:
         bound, unit = "tensor", "TFLOP/s"
         achieved = dom["algo_flops"] / (dom["total_ms"] / 1000.0) / 1e12
@@ -423,6 +430,17 @@ def run_ours(args):
     if precision == abi.AFG_FP32 and not args.no_bf16 and wl.net == inputs.RESNET34_NET:
         bf16 = time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world)
         bf16["ratio_vs_fp32"] = bf16["value"] / value
+    nested = args.workload == "hour" and not args.n_win
+    del xd, flush
+    torch.cuda.empty_cache()
+    # the batching workload (every rank analyses its own day: weak scaling) and the serving workload
+    # (one GPU), each with its own timing, nested in this line
+    batched = bf16_batched_subresult(world, rank, local, peaks) if nested and not args.no_batched else None
+    serving = None
+    if nested and not args.no_serving and world == 1:
+        serving = serving_measure(args.n_streams, 20.0, local)
+        serving = {k: serving[k] for k in ("value", "unit", "latency_ms", "config", "windows_per_s", "roofline",
+                                           "gpu_launches", "clocks", "e2e")}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -448,13 +466,123 @@ def run_ours(args):
                       "net": "resnet34-1d-gn16" if wl.net == inputs.RESNET34_NET else "tiny-1d-gn8",
                       "precision": args.precision, "l2": "flushed between steps (512 MiB write)"},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-           "bf16": bf16, "tiles": tiles,
+           "bf16": bf16, "bf16_batched": batched, "serving": serving, "tiles": tiles,
            "clocks": clocks, "kernels": kernels}
+    out["config"]["n_sm"] = peaks["n_sm"]
     print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def timeslide_measure(precision, n_seg, n_shift, steps, warmup, world, rank, local, with_far=True, clocks=True):
+    """Time `steps` steps of the timeslide background (segments x timeslides through
+    afg_batch_run, replayed as one CUDA graph, then the FAR of the background triggers)
+    after `warmup` untimed steps.  Returns the measurement (every rank) and, on rank 0, the
+    per-kernel shares of one direct (profiled) call."""
+    import torch
+
+    from paper_2403_18661_gb300 import abi
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = inputs.TIMESLIDE_DAY
+    lengths = inputs.segment_lengths(n_seg=40, total_s=86400)[:n_seg]
+    x, segs = inputs.make_segments(lengths, seed=pdist.rank_seed(wl.seed, rank), chirp_every_s=300.0,
+                                   workers=min(16, os.cpu_count() or 1))
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    ctx = abi.Context(wl, w, precision=precision)
+    xd = torch.from_numpy(x).to(dev)
+    del x
+    n_win, tw, ts = ctx.batch_layout(segs, n_shift, wl.fs)
+    livetime = tw * wl.stride / wl.fs  # background seconds analysed per step
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = None
+    trig_cap = 1 << 20
+    far_out = None
+
+    def far_step():
+        logits, stat, trig, n_trig = out
+        return ctx.far(stat, stat[:1024], livetime, bg_idx=trig, n_bg=n_trig, bg_cap=trig_cap, out=far_out,
+                       stream=stream)
+
+    with torch.cuda.stream(stream):
+        # one direct call with per-kernel timing for the shares, then the captured graph
+        ctx.profile_enable(True)
+        out = ctx.batch_run(xd, segs, n_shift, wl.fs, trig_cap=trig_cap, out=out, stream=stream)
+        if with_far:
+            far_out = far_step()
+        kstats = ctx.profile_read()
+        for _ in range(warmup):
+            out = ctx.batch_run(xd, segs, n_shift, wl.fs, trig_cap=trig_cap, use_graph=True, out=out, stream=stream)
+            if with_far:
+                far_step()
+    pdist.barrier(world)
+    sampler = ClockSampler(local) if (rank == 0 and clocks) else None
+    if sampler:
+        sampler.start()
+    ctx.profile_enable(False)
+    evs = []
+    pdist.barrier(world)
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.batch_run(xd, segs, n_shift, wl.fs, trig_cap=trig_cap, use_graph=True, out=out, stream=stream)
+            if with_far:
+                far_step()
+            e1.record(stream)
+            evs.append((e0, e1))
+    pdist.barrier(world)
+    ctx.sync(stream)
+    clk = sampler.stop() if sampler else None
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    n_bg = int(out[3].item())
+    far_min = float(far_out[1][:1024].min().item()) if (with_far and n_bg) else None
+    value, _, job_s = pdist.job_throughput(livetime * steps, total_ms / 1000.0, world)
+    ctx.close()
+    del xd, flush
+    return {"value": value, "ms_per_step": job_s * 1000.0 / steps, "livetime_s": livetime, "windows": tw,
+            "segments": len(segs), "strain_s": int(sum(lengths)), "timeslides": n_shift, "background_triggers": n_bg,
+            "far_min_per_s": far_min, "kstats": kstats, "clocks": clk, "steps": steps, "warmup": warmup}
+
+
+def timeslide_summary(m, peaks, precision):
+    """Roofline and kernel shares of a timeslide measurement (rank 0)."""
+    kstats = m["kstats"]
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    launches_per_step = int(sum(k["launches"] for k in kstats))
+    return {"value": m["value"], "unit": "strain-s/s", "ms_per_step": m["ms_per_step"], "steps": m["steps"],
+            "warmup": m["warmup"], "dtype": "bf16" if precision else "f32",
+            "config": {"workload": inputs.TIMESLIDE_DAY.name if m["segments"] == 40 and m["timeslides"] == 100
+                       else f"timeslides-{m['segments']}seg-{m['timeslides']}shifts-tiny-4Hz",
+                       "segments": m["segments"], "strain_s": m["strain_s"], "timeslides": m["timeslides"],
+                       "windows": m["windows"], "livetime_s": m["livetime_s"],
+                       "graph": "one CUDA graph per step + the FAR sort", "l2": "flushed between steps (512 MiB write)",
+                       "background_triggers": m["background_triggers"], "far_min_per_s": m["far_min_per_s"]},
+            "roofline": roofline_for(dom, peaks, sum(k["total_ms"] for k in kstats)),
+            "gpu_launches": launches_per_step * m["steps"], "clocks": m["clocks"],
+            "kernels_direct_call": {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3)}
+                                    for k in kstats}}
+
+
+def bf16_batched_subresult(world, rank, local, peaks):
+    """The batching workload (40 uneven segments, about 1 day, 100 timeslides, the 16-channel
+    network in BF16, one graph per step), plus the BF16 / FP32 ratio measured on a subset
+    (4 segments x 10 timeslides) that the FP32 path finishes in well under a second per step."""
+    from paper_2403_18661_gb300 import abi
+    full = timeslide_measure(abi.AFG_BF16, 40, 100, 3, 3, world, rank, local)
+    sub16 = timeslide_measure(abi.AFG_BF16, 4, 10, 5, 3, world, rank, local, clocks=False)
+    sub32 = timeslide_measure(abi.AFG_FP32, 4, 10, 5, 3, world, rank, local, clocks=False)
+    if rank != 0:
+        return None
+    r = timeslide_summary(full, peaks, abi.AFG_BF16)
+    r["vs_fp32_subset"] = {"segments": 4, "timeslides": 10, "windows": sub16["windows"],
+                           "bf16": sub16["value"], "fp32": sub32["value"], "ratio": sub16["value"] / sub32["value"]}
+    return r
 
 
 def run_timeslides(args):
@@ -475,96 +603,27 @@ def run_timeslides(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    wl = inputs.TIMESLIDE_DAY
-    lengths = inputs.segment_lengths(n_seg=40, total_s=86400)[: args.n_seg]
-    x, segs = inputs.make_segments(lengths, seed=pdist.rank_seed(wl.seed, rank), chirp_every_s=300.0)
-    w = inputs.make_weights(wl.net, wl.weight_seed)
     precision = abi.AFG_BF16 if args.precision == "bf16" else abi.AFG_FP32
-    ctx = abi.Context(wl, w, precision=precision)
-    xd = torch.from_numpy(x).to(dev)
-    n_win, tw, ts = ctx.batch_layout(segs, args.n_shift, wl.fs)
-    livetime = tw * wl.stride / wl.fs  # background seconds analysed per step
-    stream = torch.cuda.Stream()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    out = None
-    trig_cap = 1 << 20
-    far_out = None
-
-    def far_step():
-        logits, stat, trig, n_trig = out
-        return ctx.far(stat, stat[:1024], livetime, bg_idx=trig, n_bg=n_trig, bg_cap=trig_cap, out=far_out,
-                       stream=stream)
-
-    with torch.cuda.stream(stream):
-        # one direct call with per-kernel timing for the shares, then the captured graph
-        ctx.profile_enable(True)
-        out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, trig_cap=trig_cap, out=out, stream=stream)
-        far_out = far_step()
-        kstats = ctx.profile_read()
-        for _ in range(args.warmup):
-            out = ctx.batch_run(xd, segs, args.n_shift, wl.fs, trig_cap=trig_cap, use_graph=True, out=out,
-                                stream=stream)
-            far_step()
-    barrier()
-    sampler = ClockSampler(local) if rank == 0 else None
-    if sampler:
-        sampler.start()
-    ctx.profile_enable(False)
-    evs = []
-    barrier()
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.batch_run(xd, segs, args.n_shift, wl.fs, trig_cap=trig_cap, use_graph=True, out=out, stream=stream)
-            far_step()
-            e1.record(stream)
-            evs.append((e0, e1))
-    barrier()
-    ctx.sync(stream)
-    clocks = sampler.stop() if sampler else None
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    n_bg = int(out[3].item())
-    far_min = float(far_out[1][:1024].min().item()) if n_bg else 0.0
-    value, _, job_s = pdist.job_throughput(livetime * args.steps, total_ms / 1000.0, world)
-    total_ms = job_s * 1000.0
+    m = timeslide_measure(precision, args.n_seg, args.n_shift, args.steps, args.warmup, world, rank, local)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
-    peaks = load_peaks()
-    dom = max(kstats, key=lambda k: k["total_ms"])
-    launches_per_step = int(sum(k["launches"] for k in kstats))
-    roofline = roofline_for(dom, peaks, sum(k["total_ms"] for k in kstats))
-    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3)} for k in kstats}
-    res = {"metric": "strain-seconds/s whiten+ResNet (timeslide background livetime)", "value": value,
+    r = timeslide_summary(m, load_peaks(), precision)
+    res = {"metric": "strain-seconds/s whiten+ResNet (timeslide background livetime)", "value": r["value"],
            "unit": "strain-s/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "bf16" if precision == abi.AFG_BF16 else "f32", "data": "synthetic",
-           "config": {"workload": wl.name, "segments": len(segs), "strain_s": int(sum(lengths)),
-                      "timeslides": args.n_shift, "windows": tw, "livetime_s": livetime,
-                      "graph": "one CUDA graph per step + the FAR sort", "l2": "flushed between steps (512 MiB write)",
-                      "background_triggers": n_bg, "far_min_per_s": far_min},
-           "roofline": roofline, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-           "kernels_direct_call": kernels}
+           "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic", "config": r["config"],
+           "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+           "kernels_direct_call": r["kernels_direct_call"]}
     print(json.dumps(res), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def run_serving(args):
-    """Continuous-batching serving of n streams of 0.25 s chunks.
+def serving_measure(n_streams, serve_seconds, local):
+    """Continuous-batching serving of n streams of 0.25 s chunks (rank 0 only; returns the result).
 
     Phase 1 (not timed) fills every stream past its 64 s PSD look-back.
     Phase 2 (latency) pushes chunks with Poisson arrivals at 4 per second per
@@ -577,18 +636,15 @@ def run_serving(args):
 
     from paper_2403_18661_gb300 import abi
 
-    world, rank, local = dist_setup()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(0)
     wl = inputs.SERVING_128
-    n_streams = args.n_streams
     chunk = 512
-    warm_s, lat_s, thr_s = 66.0, max(1.0, 9300 / (4.0 * n_streams)), args.serve_seconds
+    warm_s, lat_s, thr_s = 66.0, max(1.0, 9300 / (4.0 * n_streams)), serve_seconds
     total_s = warm_s + lat_s * 1.6 + thr_s + 2.0
     n_tot = int(total_s * wl.fs)
-    xs = [np.stack([inputs.coloured_noise(n_tot, wl.seed * 1000 + 2 * i + d) for d in range(2)]).astype(np.float32)
-          for i in range(n_streams)]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        xs = list(ex.map(lambda i: np.stack([inputs.coloured_noise(n_tot, wl.seed * 1000 + 2 * i + d)
+                                             for d in range(2)]).astype(np.float32), range(n_streams)))
     w = inputs.make_weights(wl.net, wl.weight_seed)
     ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
     ctx.stream_start(max_streams=n_streams, max_chunk=4096)
@@ -683,14 +739,23 @@ def run_serving(args):
                    "d2h_bytes_per_step": int(n_results * 32 / n_steps),
                    "note": "wall time from the first host push to the last result on the host (pinned staging "
                            "copies in, 32-byte results out)"}}
-    print(json.dumps(out), flush=True)
     ctx.close()
+    return out
+
+
+def run_serving(args):
+    import torch
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    print(json.dumps(serving_measure(args.n_streams, args.serve_seconds, local)), flush=True)
     return 0
 
 
 def whiten_workload(n_win: int = 0):
     """Six hours of seeded two-detector coloured noise in epoch mode: the Welch PSD of the
-    64 s before every 8 s epoch, its FP64 filter and the overlap-save whitening (Sec. IV.B,
+    64 s before every 8 s epoch, its FP64 filter and the overlap-save whitening (Sec. IV ("Noise sampling"),
     Sec. VI).  Windows only size the whitened span (16 Hz, as the 1 h workload)."""
     base = inputs.HOUR_RESNET34
     n = n_win or 6 * base.n_win
@@ -1013,6 +1078,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 comparison of the FP32 workload")
     ap.add_argument("--no-tune", action="store_true", help="keep the default conv tiles (no autotuning)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: skip the nested timeslide-batch (BF16 batched) measurement")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default workload: skip the nested serving (p50/p99 latency) measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -3,7 +3,7 @@
  * (Marx et al., "A machine-learning pipeline for real-time detection of
  * gravitational waves from compact binary coalescences", arXiv 2403.18661).
  *
- * The path (Sec. II, Sec. IV.B "Noise sampling", Sec. VI "Inference"):
+ * The path (Sec. II, Sec. IV, "Noise sampling" paragraph, Sec. VI "Inference"):
  *   two-detector strain --Welch PSD--> inverse-ASD whitening filter -->
  *   FFT-domain whitening with 0.5 s crop --> overlapping 1.5 s windows -->
  *   1D ResNet with GroupNorm (one logit per window) --> 1 s top-hat
@@ -135,9 +135,24 @@ int afg_ctx_bytes(const afg_ctx *ctx, int64_t *bytes);
  * outputs are unspecified).  Clears the record. */
 int afg_sync(afg_ctx *ctx, void *stream);
 
+/* Check of the bounded device-side waits (failure detection; the paper has no
+ * counterpart: it concerns this library's kernels, not the method).  The
+ * tensor-core kernels wait on mbarriers for their MMAs and bulk copies, each
+ * wait limited in time; when one gives up, the kernel records it, returns
+ * early (its outputs are then unspecified) and afg_sync reports
+ * AFG_ERR_TIMEOUT.  This call exercises that path without a fault: n_blocks
+ * CTAs each wait, through the same bounded wait and the same record, on an
+ * mbarrier that nothing arrives on, so every wait ends by its limit
+ * (limit_ns, at most 1e10) with nothing in flight, and the kernel exits
+ * normally.  waited_ns: device int64 [n_blocks], the time each CTA waited.
+ * Asynchronous on `stream`; call afg_sync(ctx, stream) to read the result
+ * (AFG_ERR_TIMEOUT, which also clears the record).  The context stays
+ * usable.  Errors: AFG_ERR_ARG for out-of-range arguments. */
+int afg_wait_check(afg_ctx *ctx, int64_t limit_ns, int32_t n_blocks, int64_t *waited_ns, void *stream);
+
 /* ---------------------------------------------------------------- hot path */
 
-/* Welch PSD (Sec. IV.B: the first 8 s of a window estimate the PSD; Sec. VI:
+/* Welch PSD (Sec. IV ("Noise sampling"): the first 8 s of a window estimate the PSD; Sec. VI:
  * the first 64 s of the stream state).  For detector d and epoch e in
  * [0, n_psd): one-sided density of x[d][e*psd_step, e*psd_step + psd_span),
  * averaged (mean) over K = (psd_span - nfft)/hop + 1 segments of nfft
@@ -153,7 +168,7 @@ int afg_sync(afg_ctx *ctx, void *stream);
 int afg_psd_estimate(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, int64_t n_psd, int64_t psd_step,
                      int64_t psd_span, double *psd, void *stream);
 
-/* Whitening (Sec. IV.B: whitened in the frequency domain, transformed back,
+/* Whitening (Sec. IV ("Noise sampling"): whitened in the frequency domain, transformed back,
  * 0.5 s corrupted at each end removed; Sec. VI).  For each detector d and
  * output j in [0, out_len):
  *   y[d][j] = sum_{m=-F/2}^{F/2-1} g^{(e)}_m x[d][out_first + j - m],

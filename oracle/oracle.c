@@ -8,7 +8,7 @@
  * header, table or constant with the CUDA library.
  *
  * Every routine follows a definition of the paper (arXiv 2403.18661):
- *   Welch PSD + whitening filter + whitening, 0.5 s crop .. Sec. IV.B "Noise
+ *   Welch PSD + whitening filter + whitening, 0.5 s crop .. Sec. IV, "Noise
  *                                                           sampling", Sec. VI
  *   1D ResNet34 with GroupNorm, scalar output ............. Sec. II, Sec. IX
  *   1 s top-hat integration, 8 s max clustering ........... Sec. II
@@ -83,7 +83,7 @@ int orc_fft(double *re, double *im, int64_t n, int sign) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Welch one-sided PSD density (Sec. IV.B: "the first 8 s is used to        */
+/* Welch one-sided PSD density (Sec. IV ("Noise sampling"): "the first 8 s is used to        */
 /* estimate the power spectral density"; Sec. VI: "the first 64 seconds").  */
 /* Readings: segments of nfft samples every hop samples (K = (n-nfft)/hop+1),*/
 /* periodic Hann window w_j = 1/2 - 1/2 cos(2 pi j / nfft), no detrending,   */
@@ -121,7 +121,7 @@ int orc_welch(const double *x, int64_t n, int nfft, int hop, double fs, double *
 }
 
 /* ------------------------------------------------------------------------ */
-/* Inverse-ASD whitening filter (Sec. IV.B "filter construction"; 1 s FIR,  */
+/* Inverse-ASD whitening filter (Sec. IV, "Noise sampling": "filter construction"; 1 s FIR,  */
 /* 32 Hz highpass).  Readings:                                              */
 /*   A_k = psd_k^{-1/2} for k*fs/nfft >= f_hp, else 0 (hard highpass);      */
 /*   h_m = (1/nfft) sum_k A_k e^{+2 pi i k m / nfft}  (real, even: the      */
@@ -159,7 +159,7 @@ int orc_whitening_taps(const double *psd, int nfft, double fs, double f_hp, int 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Whitening as a direct linear FIR (Sec. IV.B: whitened, transformed back, */
+/* Whitening as a direct linear FIR (Sec. IV ("Noise sampling"): whitened, transformed back, */
 /* 0.5 s corrupted on both ends and removed).                                */
 /* y_j = sum_{i=0}^{F-1} taps[i] * x[first + j - (i - F/2)],  j in [0,len). */
 /* Requires first >= F/2 and first + len - 1 + F/2 - 1 < n, so that the      */

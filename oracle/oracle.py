@@ -88,7 +88,7 @@ def fft(x: np.ndarray, inverse: bool = False) -> np.ndarray:
 
 
 def welch(x: np.ndarray, nfft: int, hop: int, fs: float) -> np.ndarray:
-    """One-sided Welch PSD density (periodic Hann, mean, no detrend); Sec. IV.B, Sec. VI."""
+    """One-sided Welch PSD density (periodic Hann, mean, no detrend); Sec. IV ("Noise sampling"), Sec. VI."""
     x = _d(x)
     out = np.empty(nfft // 2 + 1)
     if _load().orc_welch(_ptr(x), len(x), nfft, hop, fs, _ptr(out)) < 1:
@@ -97,7 +97,7 @@ def welch(x: np.ndarray, nfft: int, hop: int, fs: float) -> np.ndarray:
 
 
 def whitening_taps(psd: np.ndarray, nfft: int, fs: float, f_hp: float, fir_len: int) -> np.ndarray:
-    """FIR taps g_m, m in [-F/2, F/2): tapered zero-phase inverse ASD with highpass (Sec. IV.B)."""
+    """FIR taps g_m, m in [-F/2, F/2): tapered zero-phase inverse ASD with highpass (Sec. IV ("Noise sampling"))."""
     psd = _d(psd)
     taps = np.empty(fir_len)
     if _load().orc_whitening_taps(_ptr(psd), nfft, fs, f_hp, fir_len, _ptr(taps)) != 0:

@@ -104,6 +104,7 @@ SIGNATURES = {
     "afg_last_error": ([_vp], ctypes.c_char_p),
     "afg_ctx_bytes": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
     "afg_sync": ([_vp, _vp], ctypes.c_int),
+    "afg_wait_check": ([_vp, _i64, _i32, _vp, _vp], ctypes.c_int),
     "afg_psd_estimate": ([_vp, _vp, _i64, _i32, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
     "afg_whiten": ([_vp, _vp, _i64, _i32, _vp, _i64, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
     "afg_infer_windows": ([_vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp], ctypes.c_int),
@@ -260,6 +261,14 @@ class Context:
     def sync(self, stream=None):
         """Wait for queued work; raise AfgError(AFG_ERR_TIMEOUT) if a kernel's bounded wait gave up."""
         self._check(self._lib.afg_sync(self._h, _stream(stream)))
+
+    def wait_check(self, limit_ns: int, n_blocks: int = 1, stream=None):
+        """Launch afg_wait_check (CTAs whose bounded waits must run out) and return the device
+        tensor of per-CTA waited nanoseconds; call sync() to read the timeout record."""
+        import torch
+        waited = torch.zeros(n_blocks, dtype=torch.int64, device="cuda")
+        self._check(self._lib.afg_wait_check(self._h, int(limit_ns), int(n_blocks), _ptr(waited), _stream(stream)))
+        return waited
 
     # ---------------------------------------------------------------- profiling
     def profile_enable(self, on: bool = True):

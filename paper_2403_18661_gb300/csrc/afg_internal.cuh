@@ -22,6 +22,32 @@ constexpr int NC = NFFT / 2;
 constexpr int NBIN = NFFT / 2 + 1;
 constexpr int WB = 8192;
 
+// Epochs per thread of the Welch averaging kernel; its grid's y extent is
+// ceil(n_psd / PSD_EPT), which must stay within 65535.
+constexpr int PSD_EPT = 16;
+
+// Validate the layout of a Welch request (x: [n_det][n], n_psd epochs of
+// psd_span samples every psd_step, segments of NFFT every hop) without
+// forming any product that could overflow: every product is bounded by a
+// division first.  On success returns true and the number of distinct
+// segments each detector needs (every epoch's segments, shared ones once).
+inline bool psd_request_ok(int64_t n, int n_det, int64_t n_psd, int64_t psd_step, int64_t psd_span, int hop,
+                           int64_t *n_seg_out) {
+    if (n_det < 1 || n_det > 65535 || n_psd < 1 || hop < 1 || NFFT % hop) return false;
+    if (psd_span < NFFT || psd_span > n || (psd_span - NFFT) % hop) return false;
+    int64_t seg_step = 0;
+    if (n_psd > 1) {
+        if (psd_step <= 0 || psd_step % hop || psd_step > n) return false;
+        if (n_psd - 1 > (n - psd_span) / psd_step) return false;  // (n_psd - 1) psd_step + psd_span <= n
+        seg_step = psd_step / hop;
+    }
+    if ((n_psd + PSD_EPT - 1) / PSD_EPT > 65535) return false;
+    const int64_t n_seg = (n_psd - 1) * seg_step + (psd_span - NFFT) / hop + 1;  // <= n / hop + 1
+    if (n_seg > 0x7fffffff) return false;
+    *n_seg_out = n_seg;
+    return true;
+}
+
 // ----------------------------------------------------------------------------
 // Network plan: one entry per convolution, in execution order.
 // ----------------------------------------------------------------------------
@@ -249,6 +275,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // ----------------------------------------------------------------------------
 int afg_fail(afg_ctx *ctx, int code, const char *fmt, ...);
 int afg_cuda_fail(afg_ctx *ctx, cudaError_t e, const char *what);
+size_t filter_build_scratch_bytes(const afg_ctx *ctx, int64_t nf);
 int afg_ws_reserve(afg_ctx *ctx, int slot, size_t bytes, void **out);
 void batch_cache_release(afg_ctx *ctx);
 void serve_release(afg_ctx *ctx);

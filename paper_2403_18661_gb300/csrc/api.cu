@@ -221,8 +221,9 @@ int afg_psd_estimate(afg_ctx *ctx, const float *x, int64_t n, int32_t n_det, int
         return afg_fail(ctx, AFG_ERR_ARG, "psd_estimate: psd_span must be nfft + a multiple of hop");
     if (n_psd > 1 && (psd_step <= 0 || psd_step % hop))
         return afg_fail(ctx, AFG_ERR_ARG, "psd_estimate: psd_step must be a positive multiple of hop");
-    if ((n_psd - 1) * (n_psd > 1 ? psd_step : 0) + psd_span > n)
-        return afg_fail(ctx, AFG_ERR_ARG, "psd_estimate: epochs reach past the end of x");
+    int64_t n_seg = 0;
+    if (!psd_request_ok(n, n_det, n_psd, psd_step, psd_span, hop, &n_seg))
+        return afg_fail(ctx, AFG_ERR_ARG, "psd_estimate: epochs reach past the end of x (or too many epochs)");
     return launch_psd(ctx, x, n, n_det, n_psd, psd_step, psd_span, psd, S(stream));
 }
 

@@ -1,5 +1,5 @@
 // Radix-16 FP32 transforms of NC = 8192 complex points for the Welch and
-// whitening kernels (Sec. IV.B: the PSD and the frequency-domain whitening
+// whitening kernels (Sec. IV ("Noise sampling"): the PSD and the frequency-domain whitening
 // are FFTs of the strain).
 //
 // Layout: 512 threads, one radix-16 butterfly per thread per pass; the 8192

@@ -49,14 +49,10 @@ int setup(int dev, DeviceState **out) {
 
 extern "C" int afg_psd_estimate_noalloc(const float *x, int64_t n, int32_t n_det, int64_t n_psd, int64_t psd_step,
                                         int64_t psd_span, int32_t fs, int32_t hop, double *psd, void *stream) {
-    if (!x || !psd || n_det < 1 || n_psd < 1 || fs < 1) return AFG_ERR_ARG;
-    if (hop < 1 || NFFT % hop) return AFG_ERR_ARG;
-    if (psd_span < NFFT || (psd_span - NFFT) % hop) return AFG_ERR_ARG;
-    if (n_psd > 1 && (psd_step <= 0 || psd_step % hop)) return AFG_ERR_ARG;
-    if ((n_psd - 1) * (n_psd > 1 ? psd_step : 0) + psd_span > n) return AFG_ERR_ARG;
-    const int64_t K = (psd_span - NFFT) / hop + 1;
-    const int64_t n_seg = (n_psd - 1) * (n_psd > 1 ? psd_step / hop : 0) + K;
-    if ((int64_t)n_det * n_seg > kMaxPeriodograms) return AFG_ERR_BUDGET;
+    if (!x || !psd || fs < 1) return AFG_ERR_ARG;
+    int64_t n_seg = 0;
+    if (!psd_request_ok(n, n_det, n_psd, psd_step, psd_span, hop, &n_seg)) return AFG_ERR_ARG;
+    if (n_seg > kMaxPeriodograms / n_det) return AFG_ERR_BUDGET;  // n_det * n_seg > the scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AFG_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

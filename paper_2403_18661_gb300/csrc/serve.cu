@@ -525,10 +525,14 @@ extern "C" int afg_stream_start(afg_ctx *ctx, const afg_stream_params *p) {
     if (!rc && cudaStreamCreateWithFlags(&E->st, cudaStreamNonBlocking) != cudaSuccess) rc = AFG_ERR_CUDA;
     if (!rc && (cudaMalloc(&E->d_done, 16) != cudaSuccess || cudaMemset(E->d_done, 0, 16) != cudaSuccess))
         rc = AFG_ERR_CUDA;
-    // the Welch scratch at its per-refresh size (no allocation inside steps)
+    // the scratch of a gains refresh at its per-refresh size (the Welch periodograms of one stream
+    // and the FP64 transforms of its 2 filters), reserved and counted against the HBM budget here,
+    // before any stream is admitted: steps never allocate, and the engine thread never changes
+    // bytes_held outside E->mu
     void *tmp = nullptr;
     const int64_t K = (p->psd_len - NFFT) / hop + 1;
     if (!rc) rc = afg_ws_reserve(ctx, WS_PERIODOGRAM, (size_t)2 * K * NBIN * sizeof(double), &tmp);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, filter_build_scratch_bytes(ctx, 2), &tmp);
     if (rc) {
         ctx->serve = E;
         serve_release(ctx);

@@ -1,5 +1,5 @@
 // Welch PSD, whitening-filter build and FFT-domain whitening
-// (Sec. IV.B "Noise sampling": PSD from 8 s, frequency-domain whitening,
+// (Sec. IV, "Noise sampling" paragraph: PSD from 8 s, frequency-domain whitening,
 // 0.5 s crop at each edge; Sec. VI: PSD from the first 64 s of state).
 //
 // Kernels
@@ -104,7 +104,6 @@ __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restr
     if (t == NT - 1) welch_mid_task(d, 2048, out);
 }
 
-constexpr int PSD_EPT = 16;  // epochs per thread of k_psd_mean
 
 // grid (ceil(NBIN/256), ceil(n_psd/PSD_EPT), n_det): bin k of epochs
 // [e0, e0 + PSD_EPT) as a sliding FP64 sum over the periodograms (epoch e
@@ -593,6 +592,13 @@ int set_attrs(afg_ctx *ctx) {
 
 }  // namespace
 
+// device scratch of building nf filters at once: two FP64 complex transforms of NFFT points per
+// filter for the many-CTA build (fir_len <= 2048), none for the one-CTA build
+size_t filter_build_scratch_bytes(const afg_ctx *ctx, int64_t nf) {
+    if (ctx->cfg.fir_len > FB_LAGS || nf > 65535) return 0;
+    return (size_t)2 * nf * NFFT * sizeof(double2);
+}
+
 // gains [n_det][n_psd][NBIN] from psd: the many-CTA FP64 build where fir_len <= 2048,
 // else one CTA per filter
 int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st) {
@@ -604,7 +610,7 @@ int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, floa
     static_assert(NFFT == 1 << 14, "flop count assumes log2(NFFT) = 14");
     if (ctx->cfg.fir_len <= FB_LAGS && nf <= 65535) {
         void *scr = nullptr;
-        int rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, (size_t)2 * nf * NFFT * sizeof(double2), &scr);
+        int rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, filter_build_scratch_bytes(ctx, nf), &scr);
         if (rc) return rc;
         double2 *Z = static_cast<double2 *>(scr), *Y = Z + nf * NFFT;
         KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));

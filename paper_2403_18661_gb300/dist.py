@@ -36,3 +36,13 @@ def job_throughput(local_units: float, local_seconds: float, world: int = 1) -> 
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     return float(u.item()) / float(t.item()), float(u.item()), float(t.item())
+
+
+def barrier(world: int = 1) -> None:
+    """All ranks meet (when world > 1), then this rank's device is idle."""
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()

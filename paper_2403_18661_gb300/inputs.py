@@ -388,23 +388,40 @@ TIMESLIDE_DAY = Workload(name="timeslides-40seg-1day-tiny-4Hz-100shifts", durati
 
 
 def make_segments(lengths_s: Sequence[int], seed: int, model: NoiseModel = NoiseModel(), fs: int = FS,
-                  chirp_every_s: float = 0.0) -> Tuple[np.ndarray, List[Tuple[int, int]]]:
+                  chirp_every_s: float = 0.0, workers: int = 0) -> Tuple[np.ndarray, List[Tuple[int, int]]]:
     """Concatenated two-detector float32 strain [2][sum n] of independent coloured-noise
-    segments, plus [(offset, n_raw)] per segment; optional chirps every chirp_every_s."""
+    segments, plus [(offset, n_raw)] per segment; optional chirps every chirp_every_s.
+    workers > 1 generates segments on that many threads (every segment has its own seeds and
+    its chirps are drawn first, in order, so the result does not depend on the thread count)."""
     ns = [int(l) * fs for l in lengths_s]
     x = np.empty((2, sum(ns)), dtype=np.float32)
     segs, off = [], 0
     rng = _rng(seed + 5)
+    plan = []
     for i, n in enumerate(ns):
-        seg = np.stack([coloured_noise(n, seed * 1000 + 2 * i + d, model, fs) for d in range(2)])
+        chirps = []
         if chirp_every_s > 0:
             for j in range(int(n / fs // chirp_every_s)):
                 t_c = (j + 0.5) * chirp_every_s + rng.uniform(-1, 1)
-                inject_chirp(seg, t_c, float(rng.uniform(10, 60)), float(rng.uniform(4, 20)),
-                             seed=seed * 7919 + i * 131 + j, model=model, fs=fs)
-        x[:, off:off + n] = seg
+                chirps.append((t_c, float(rng.uniform(10, 60)), float(rng.uniform(4, 20)), seed * 7919 + i * 131 + j))
+        plan.append((i, n, off, chirps))
         segs.append((off, n))
         off += n
+
+    def one(item):
+        i, n, o, chirps = item
+        seg = np.stack([coloured_noise(n, seed * 1000 + 2 * i + d, model, fs) for d in range(2)])
+        for t_c, mc, snr, cs in chirps:
+            inject_chirp(seg, t_c, mc, snr, seed=cs, model=model, fs=fs)
+        x[:, o:o + n] = seg
+
+    if workers > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(one, plan))
+    else:
+        for item in plan:
+            one(item)
     return x, segs
 
 

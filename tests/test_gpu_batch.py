@@ -10,13 +10,14 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import trigger_match  # noqa: E402
 from oracle import oracle as orc  # noqa: E402
 from paper_2403_18661_gb300 import abi, inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
 LOGIT_TOL = 1e-4
-BF16_LOGIT_TOL = 5e-2
+BF16_LOGIT_TOL = 2e-3  # three times the measured 6.1e-4 of this batch
 N_SHIFT = 3
 SHIFT_STEP = 2048
 
@@ -47,8 +48,10 @@ def batch_case():
 def _check(wl, segs, ref, logits, stat, trig, n_trig, tol):
     lg, st = logits.cpu().numpy(), stat.cpu().numpy()
     tr = trig.cpu().numpy()[: int(n_trig.item())]
+    assert np.all(np.diff(tr) > 0)
     lo = so = 0
     worst = 0.0
+    tot = dict(oracle=0, gpu=0, decisive=0, near_tie=0, near_tie_same=0, near_tie_moved=0, near_ties=[])
     for per in ref:
         for z, s_ref, t_ref in per:
             got = lg[lo:lo + len(z)]
@@ -56,20 +59,15 @@ def _check(wl, segs, ref, logits, stat, trig, n_trig, tol):
             worst = max(worst, float(err.max()))
             assert err.max() < tol
             s_got = st[so:so + len(s_ref)]
-            assert np.max(np.abs(s_got - s_ref) / (1 + np.abs(s_ref))) < tol
-            # triggers of this series (global statistic indices) must be the oracle's,
-            # except near-ties, which may move by one sample
-            mine = set(int(t) - so for t in tr if so <= t < so + len(s_ref))
-            for j in t_ref:
-                lo_j, hi_j = max(0, j - wl.cluster_half), min(len(s_ref), j + wl.cluster_half + 1)
-                nb = np.delete(s_ref[lo_j:hi_j], j - lo_j)
-                margin = s_ref[j] - (nb.max() if len(nb) else -np.inf)
-                if margin > 2 * tol * (1 + abs(s_ref[j])):
-                    assert j in mine or (j - 1) in mine or (j + 1) in mine
+            # this series' triggers (global statistic indices) against the oracle's, both directions
+            mine = np.array([int(t) - so for t in tr if so <= t < so + len(s_ref)], dtype=np.int64)
+            c = trigger_match.compare(s_got, s_ref, mine, t_ref, wl.cluster_half, tol)
+            for k in tot:
+                tot[k] += c[k]
             lo += len(z)
             so += len(s_ref)
     assert lo == len(lg) and so == len(st)
-    return worst
+    return worst, tot
 
 
 @pytest.mark.parametrize("precision,tol", [(abi.AFG_FP32, LOGIT_TOL), (abi.AFG_BF16, BF16_LOGIT_TOL)])
@@ -80,9 +78,11 @@ def test_batch_matches_oracle(batch_case, precision, tol, capsys):
     assert n_win == [len(per[0][0]) for per in ref]
     out = ctx.batch_run(torch.from_numpy(x).cuda(), segs, N_SHIFT, SHIFT_STEP)
     ctx.sync()
-    worst = _check(wl, segs, ref, *out, tol)
+    worst, c = _check(wl, segs, ref, *out, tol)
     with capsys.disabled():
-        print(f"\nbatch precision {precision}: {tw} windows, max |dz|/(1+|z|) = {worst:.3e}")
+        print(f"\nbatch precision {precision}: {tw} windows, max |dz|/(1+|z|) = {worst:.3e}; "
+              f"{trigger_match.summary(c)}")
+    assert c["decisive"] > 0
     ctx.close()
 
 

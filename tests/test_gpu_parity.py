@@ -9,9 +9,14 @@ inputs):
                the input spread over the band and multiplied by the largest
                filter gain (~1e1 above the RMS gain)
   logits FP32  |dz| <= 1e-4 (1 + |z|)
-  statistic    |dI| <= 1e-4 (1 + |I|); trigger lists equal except where the
-               oracle's maximum beats its runner-up by < 2 x the logit
-               tolerance, and then within +-1 sample
+  statistic    |dI| <= 1e-4 (1 + |I|); trigger lists compared in both
+               directions (trigger_match.compare): every maximum that beats
+               its +-4 s neighbourhood by more than 2 x the tolerance must be
+               at the same index on both sides; near-ties are counted, listed
+               and must resolve to a tied neighbour
+  BF16 logits  |dz| <= 2e-3 (1 + |z|) for the 16-channel network (three times
+               the measured 5.6e-4 / 6.1e-4), 2e-2 (1 + |z|) for the
+               ResNet34-GN (three times the measured 5.8e-3 / 6.8e-3)
   triggers of a given statistic: bit-exact (index work).
 """
 import numpy as np
@@ -19,6 +24,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import trigger_match  # noqa: E402
 from oracle import oracle as orc  # noqa: E402
 from paper_2403_18661_gb300 import abi, inputs  # noqa: E402
 
@@ -118,6 +124,27 @@ def test_infer_windows_tiny_with_shift(c1, ctx_tiny):
         assert err.max() < LOGIT_TOL, (shift, err.max())
 
 
+@pytest.mark.parametrize("stride,n_win", [(1, 96), (32, 80), (128, 60), (2048, 40)])
+def test_infer_windows_inference_rates(c1, ctx_tiny, ctx_tiny_bf16, stride, n_win, capsys):
+    """The inference-rate sweep (Sec. VI: 1 s to 1/2048 s between windows; 2048 Hz is the online
+    rate of Sec. VIII): windows every `stride` samples, from an odd first sample and with an L1
+    shift, through the FP32 and the BF16 networks, against the oracle window by window."""
+    wl, x, w, ref = c1
+    white = ref["white"].astype(np.float32)
+    yd = _dev(white)
+    first, shift = 37, 2048 * 3 + 5
+    n_win = min(n_win, (white.shape[1] - wl.win_len - first) // stride + 1)
+    want = orc.infer_windows(wl.net, w, white.astype(np.float64), wl.win_len, first, stride, n_win, shift)
+    for ctx, tol in ((ctx_tiny, LOGIT_TOL), (ctx_tiny_bf16, BF16_LOGIT_TOL)):
+        got = ctx.infer_windows(yd, first, stride, n_win, shift).cpu().numpy()
+        ctx.sync()
+        err = np.abs(got - want) / (1 + np.abs(want))
+        with capsys.disabled():
+            print(f"\nstride {stride}: {n_win} windows, {'FP32' if ctx is ctx_tiny else 'BF16'} "
+                  f"max |dz|/(1+|z|) = {err.max():.3e}")
+        assert err.max() < tol, (stride, err.max())
+
+
 def test_integrate_and_triggers_bit_exact(ctx_tiny):
     rng = np.random.default_rng(3)
     z = rng.standard_normal(5000).astype(np.float32)
@@ -159,19 +186,7 @@ def test_triggers_ties_and_capacity(ctx_tiny):
     assert trig.cpu().numpy()[0] == want[0]
 
 
-def _trigger_match(stat_gpu, stat_ref, trig_gpu, trig_ref, half, tol):
-    gpu = set(int(t) for t in trig_gpu)
-    for j in trig_ref:
-        lo, hi = max(0, j - half), min(len(stat_ref), j + half + 1)
-        nb = np.delete(stat_ref[lo:hi], j - lo)
-        margin = stat_ref[j] - (nb.max() if len(nb) else -np.inf)
-        if margin > 2 * tol * (1 + abs(stat_ref[j])):
-            assert j in gpu, f"oracle trigger {j} (margin {margin:.3g}) missing on the GPU"
-        else:
-            assert any(abs(j - g) <= 1 for g in gpu) or margin <= 2 * tol * (1 + abs(stat_ref[j]))
-
-
-def test_analyze_plain_c1_end_to_end(c1, ctx_tiny):
+def test_analyze_plain_c1_end_to_end(c1, ctx_tiny, capsys):
     wl, x, w, ref = c1
     logits, stat, trig, n_trig = ctx_tiny.analyze(_dev(x))
     lg = logits.cpu().numpy()
@@ -180,7 +195,10 @@ def test_analyze_plain_c1_end_to_end(c1, ctx_tiny):
     st = stat.cpu().numpy()
     assert np.max(np.abs(st - ref["stat"]) / (1 + np.abs(ref["stat"]))) < LOGIT_TOL
     n = int(n_trig.item())
-    _trigger_match(st, ref["stat"], trig.cpu().numpy()[:n], ref["triggers"], wl.cluster_half, LOGIT_TOL)
+    c = trigger_match.compare(st, ref["stat"], trig.cpu().numpy()[:n], ref["triggers"], wl.cluster_half, LOGIT_TOL)
+    with capsys.disabled():
+        print(f"\nC1 FP32 {trigger_match.summary(c)}")
+    assert c["decisive"] > 0
 
 
 def test_analyze_host_matches_device(c1, ctx_tiny):
@@ -253,9 +271,12 @@ def test_resnet34_hour_sampled_windows():
 
 # ---------------------------------------------------------------- BF16 tensor-core network
 # BF16 operands (8-bit mantissa, relative rounding 2^-9 per operand) through
-# four GroupNorm'd convolutions: the logit error is bounded here by
-# 5e-2 (1 + |z|); the measured maximum is printed.
-BF16_LOGIT_TOL = 5e-2
+# GroupNorm'd convolutions.  The bounds are three times the largest error
+# measured on these workloads (16-channel network 5.6e-4 on the 64 s span and
+# 6.1e-4 on the timeslide batch; ResNet34-GN 5.8e-3 against the oracle and
+# 6.8e-3 against the FP32 path); the measured maxima are printed.
+BF16_LOGIT_TOL = 2e-3
+BF16_RESNET34_TOL = 2e-2
 
 
 @pytest.fixture(scope="module")
@@ -281,13 +302,21 @@ def test_bf16_tiny_logits_against_oracle(c1, ctx_tiny_bf16, capsys):
         assert err.max() < BF16_LOGIT_TOL, err.max()
 
 
-def test_bf16_precision_c1_peaks_within_one_sample(c1, ctx_tiny_bf16):
+def test_bf16_precision_c1_trigger_list(c1, ctx_tiny_bf16, capsys):
+    """Precision workload: the 64 s span through the BF16 network; the statistic within the
+    BF16 tolerance and the trigger lists compared in both directions."""
     wl, x, w, ref = c1
     logits, stat, trig, n_trig = ctx_tiny_bf16.analyze(_dev(x))
     ctx_tiny_bf16.sync()
-    st = stat.cpu().numpy()
+    lg, st = logits.cpu().numpy(), stat.cpu().numpy()
+    err = np.abs(lg - ref["logits"]) / (1 + np.abs(ref["logits"]))
     n = int(n_trig.item())
-    _trigger_match(st, ref["stat"], trig.cpu().numpy()[:n], ref["triggers"], wl.cluster_half, BF16_LOGIT_TOL)
+    c = trigger_match.compare(st, ref["stat"], trig.cpu().numpy()[:n], ref["triggers"], wl.cluster_half,
+                              BF16_LOGIT_TOL)
+    with capsys.disabled():
+        print(f"\nC1 BF16 logits max |dz|/(1+|z|) = {err.max():.3e}; {trigger_match.summary(c)}")
+    assert err.max() < BF16_LOGIT_TOL
+    assert c["decisive"] > 0
 
 
 def test_bf16_resnet34_tensor_core_layers(capsys):
@@ -318,7 +347,7 @@ def test_bf16_resnet34_tensor_core_layers(capsys):
     with capsys.disabled():
         print(f"\nBF16 ResNet34: vs FP32 max {d.max():.3e}, vs oracle (6 windows) max {worst:.3e}")
     assert np.all(np.isfinite(z16))
-    assert d.max() < BF16_LOGIT_TOL and worst < BF16_LOGIT_TOL
+    assert d.max() < BF16_RESNET34_TOL and worst < BF16_RESNET34_TOL
     c16.close()
     c32.close()
 

@@ -10,7 +10,8 @@ from paper_2403_18661_gb300 import abi, inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-BF16_LOGIT_TOL = 5e-2
+# BF16 16-channel network against the FP64 oracle: three times the measured 5.6e-4
+BF16_LOGIT_TOL = 2e-3
 # alone vs in the mix: the only difference is the overlap-save block alignment of
 # the whitening (FP32 rounding order), so the FP32 logit tolerance applies
 MIX_TOL = 1e-4
@@ -202,14 +203,19 @@ def test_stream_same_alone_and_in_the_mix(weights):
 
 
 def test_stream_admission_by_hbm_budget(weights):
+    """Admission by HBM budget, with no headroom beyond two streams: everything a step and a
+    gains refresh need (the Welch periodograms and the FP64 filter-build transforms) is reserved
+    and counted when the engine starts, so the admitted streams then run through several PSD
+    refreshes without any allocation, and their results match the oracle."""
     probe = abi.Context(WL, weights, precision=abi.AFG_BF16)
     probe.stream_start(max_streams=8)
     base = probe.bytes_held
     s0 = probe.stream_open()
     per_stream = probe.bytes_held - base
     probe.close()
-    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16, hbm_budget=base + int(2.5 * per_stream))
+    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16, hbm_budget=base + 2 * per_stream + 4096)
     ctx.stream_start(max_streams=8)
+    assert ctx.bytes_held == base
     s1, s2 = ctx.stream_open(), ctx.stream_open()
     with pytest.raises(abi.AfgError) as e:
         ctx.stream_open()
@@ -225,6 +231,18 @@ def test_stream_admission_by_hbm_budget(weights):
         except abi.AfgError:
             assert time.time() < deadline
             time.sleep(0.05)
+    # 72 s into each admitted stream: the first gains and the refreshes every 8 s after them
+    xs = {s2: _strain(72.0, 21), s3: _strain(72.0, 22)}
+    for a in range(0, 72 * WL.fs, 2048):
+        for sid, x in xs.items():
+            ctx.stream_push(sid, x[:, a:a + 2048])
+    ctx.stream_flush()
+    assert ctx.bytes_held <= base + 2 * per_stream + 4096
+    for sid, x in xs.items():
+        r = ctx.stream_poll(sid)
+        z, st, _ = _oracle_stream(x, weights)
+        assert len(r) == len(st) > 0
+        assert np.max(np.abs(r["stat"] - st) / (1 + np.abs(st))) < BF16_LOGIT_TOL
     ctx.close()
 
 

@@ -2,10 +2,11 @@
 
 Every tile the tuner may pick must compute the same network: each candidate
 of each layer geometry is applied and the logits are compared with the FP32
-path (the BF16 logit tolerance, 5e-2 (1 + |z|): BF16 operand rounding of
-2^-9 through the GroupNorm'd convolutions) and with the default tiles (tiles
-differ only in the FP32 accumulation order inside a layer, which moves a
-BF16 rounding now and then).  37 windows leave partial tiles for every
+path (the ResNet34-GN BF16 logit tolerance, 2e-2 (1 + |z|): three times the
+measured 5.9e-3 of BF16 operand rounding through 36 GroupNorm'd convolutions)
+and with the default tiles, within 8e-3 (1 + |z|): three times the measured
+2.5e-3 (tiles differ only in the FP32 accumulation order inside a layer,
+which moves a BF16 rounding of an activation now and then).  37 windows leave partial tiles for every
 windows-per-tile count from 2 to 5.
 """
 import dataclasses
@@ -19,8 +20,8 @@ from paper_2403_18661_gb300 import abi, inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-BF16_LOGIT_TOL = 5e-2
-TILE_TOL = 2e-2
+BF16_LOGIT_TOL = 2e-2
+TILE_TOL = 8e-3
 
 
 @pytest.fixture(scope="module")

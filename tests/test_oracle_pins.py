@@ -192,6 +192,70 @@ def test_whitened_coloured_noise_is_flat_and_unit_variance():
 
 # ---------------------------------------------------------------- network layers
 
+# ---------------------------------------------------------------- epoch composition (Sec. VI)
+
+def test_epoch_psd_and_whitening_follow_the_64s_lookback():
+    """Sec. VI: the first 64 s of state estimate the PSD and the rest is whitened.  In epoch mode
+    whitened sample j (raw sample psd_len + j) belongs to epoch e = j // epoch_len, whose PSD is the
+    Welch estimate of raw [e epoch_len, e epoch_len + psd_len), the 64 s just before it.
+
+    Input: white Gaussian noise whose variance steps per 8 s block (block b has variance v_b,
+    neighbours differing by at least 1.8x).  For independent samples E|X_k|^2 = sum_n w_n^2 v(n) at
+    every bin, so each 8 s Welch segment has the flat expected level 2 v / fs, and a segment that
+    straddles two blocks averages them (the periodic Hann's squares sum to the same value over
+    either half).  Over the 15 segments of epoch e's look-back (blocks e .. e+7) the expected
+    level is therefore (2 / fs) (1.5 v_e + 2 (v_{e+1} + .. + v_{e+6}) + 1.5 v_{e+7}) / 15.
+    The whitened samples of epoch e come from raw block e + 8, so away from the block edges their
+    variance is v_{e+8} sum_m g_m^2 with g the epoch's own taps (white input).  A look-back or an
+    epoch-to-block mapping off by one epoch moves either figure by far more than its tolerance."""
+    fs, blk = 2048, 16384
+    wl = inputs.Workload(name="epoch-pin", duration_s=0.0, net=inputs.TINY_NET, stride=512, n_win=1,
+                         epoch_len=blk, n_chirps=0)
+    n_ep = 4
+    n_blocks = 8 + n_ep
+    rng = np.random.default_rng(2403)
+    # per detector: variances on a rising trend (x1.35 per block, so a look-back shifted by one
+    # epoch changes the level by about that factor) that alternate low/high (x2.5, so neighbouring
+    # blocks differ by >= 1.8x), with +-10 % random factors
+    b = np.arange(n_blocks)
+    v = np.stack([1.35 ** b * np.where((b + d) % 2 == 0, 1.0, 2.5) * rng.uniform(0.9, 1.1, n_blocks)
+                  for d in range(2)])
+    n = n_blocks * blk + wl.crop
+    x = np.empty((2, n))
+    for d in range(2):
+        z = rng.standard_normal(n)
+        sig = np.sqrt(np.repeat(v[d], blk))
+        x[d, : n_blocks * blk] = z[: n_blocks * blk] * sig
+        x[d, n_blocks * blk:] = z[n_blocks * blk:] * math.sqrt(v[d, -1])
+    eps = list(range(n_ep))
+    psd = orc.psd_epochs(x, wl, eps)
+    white = orc.whiten(x, wl, psd, eps)
+    assert psd.shape == (2, n_ep, 8193) and white.shape == (2, n_ep * blk)
+    wts = np.array([1.5] + [2.0] * 6 + [1.5]) / 15.0
+    # standard error of the bin-averaged level: each bin of a 15-segment Welch mean scatters by
+    # about 1/sqrt(15 / 1.2) of its level; bins are nearly independent, 8191 of them are averaged
+    se_level = math.sqrt(1.2 / 15 / 8191)
+    for d in range(2):
+        for e in eps:
+            level = psd[d, e, 1:8192].mean() * fs / 2.0
+            want = float(wts @ v[d, e:e + 8])
+            assert abs(level / want - 1.0) < 6 * se_level, (d, e, level, want)
+            for wrong in (e - 1, e + 1):  # a one-epoch slip of the look-back is far outside
+                if 0 <= wrong <= n_blocks - 8:
+                    assert abs(float(wts @ v[d, wrong:wrong + 8]) / want - 1.0) > 30 * se_level
+            taps = orc.whitening_taps(psd[d, e], wl.nfft, wl.fs, wl.f_highpass, wl.fir_len)
+            seg = white[d, e * blk + wl.crop:(e + 1) * blk - wl.crop]  # away from block edges
+            var = float(np.mean(seg ** 2))
+            want_var = v[d, e + 8] * float(np.sum(taps ** 2))
+            # the highpassed output is correlated over a few samples: allow 6 standard errors of
+            # sqrt(2 / (n / 2))
+            se_var = math.sqrt(2.0 / (len(seg) / 2))
+            assert abs(var / want_var - 1.0) < 6 * se_var, (d, e, var, want_var)
+            for nb in (e + 7, e + 9):  # the neighbouring raw blocks differ by >= 1.8x
+                if nb < n_blocks:
+                    assert abs(v[d, nb] / v[d, e + 8] - 1.0) > 0.44
+
+
 def _conv_brute(x, w, stride, pad):
     cin, L = x.shape
     cout, _, k = w.shape
