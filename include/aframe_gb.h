@@ -244,11 +244,14 @@ typedef struct afg_batch_params {
     int64_t epoch_len;    /* PSD epoch (8 s = 16384 samples); a multiple of 8192 */
     int64_t stride;       /* window stride in samples */
     int64_t shift_step;   /* timeslide step in samples (1 s = fs) */
-    int32_t n_shift;      /* timeslides k = 1 .. n_shift (zero lag is not background) */
+    int32_t n_shift;      /* timeslides k = shift_first .. shift_first + n_shift - 1 */
     int32_t n_int;        /* integration length in windows */
     int32_t cluster_half; /* trigger half-width in statistic samples */
     int32_t use_graph;    /* 1: capture the whole batch into a CUDA graph on the first call
                              and replay it while the arguments stay the same */
+    int64_t shift_first;  /* first timeslide k of this call (>= 1: zero lag is not background;
+                             0 is read as 1), so that several calls (or GPUs) can each take a
+                             contiguous range of the timeslides of one background */
 } afg_batch_params;
 
 /* Sizes of a batch (host only, no GPU work): for every segment, the windows
@@ -258,15 +261,15 @@ typedef struct afg_batch_params {
  * rest is whitened): it yields floor((n_raw - psd_len - fir_len/2) /
  * epoch_len) whole epochs of whitened data and (n_white - W)/stride + 1
  * windows.  AFG_ERR_ARG if a segment is too short for one epoch, n_int
- * windows, or n_shift * shift_step whitened samples. */
+ * windows, or (shift_first + n_shift - 1) * shift_step whitened samples. */
 int afg_batch_layout(afg_ctx *ctx, const afg_segment *segs_host, int32_t n_seg, const afg_batch_params *p,
                      int64_t *n_win_host, int64_t *total_windows, int64_t *total_stat);
 
 /* Timeslide background over many segments in one call (Sec. IX: Hanford
  * fixed, Livingston shifted in 1 s steps until the livetime is reached).
  * Each detector of each segment is whitened once on its own axis (epoch
- * mode); series s = i * n_shift + (k - 1) pairs H1 of segment i with its L1
- * circularly shifted by k * shift_step samples within the segment's whitened
+ * mode); series s = i * n_shift + (k - shift_first) pairs H1 of segment i with
+ * its L1 circularly shifted by k * shift_step samples within the segment's whitened
  * span.  All windows of all series go through one persistent network launch.
  * Outputs, concatenated in series order: logits [total_windows] (may be
  * NULL: a context workspace is used), stat [total_stat] (each series

@@ -61,7 +61,7 @@ class AfgSegment(ctypes.Structure):
 class AfgBatchParams(ctypes.Structure):
     _fields_ = [("psd_len", ctypes.c_int64), ("epoch_len", ctypes.c_int64), ("stride", ctypes.c_int64),
                 ("shift_step", ctypes.c_int64), ("n_shift", ctypes.c_int32), ("n_int", ctypes.c_int32),
-                ("cluster_half", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("cluster_half", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("shift_first", ctypes.c_int64)]
 
 
 class AfgStreamParams(ctypes.Structure):
@@ -422,7 +422,7 @@ class Context:
         return logits, stat, trig, n_trig
 
     # ---------------------------------------------------------------- timeslide batches
-    def _batch_args(self, segments, n_shift: int, shift_step: int, use_graph: bool):
+    def _batch_args(self, segments, n_shift: int, shift_step: int, use_graph: bool, shift_first: int = 1):
         wl = self.workload
         segs = (AfgSegment * len(segments))()
         for i, (off, n) in enumerate(segments):
@@ -430,11 +430,12 @@ class Context:
         p = AfgBatchParams()
         p.psd_len, p.epoch_len, p.stride, p.shift_step = wl.psd_len, wl.epoch_len, wl.stride, shift_step
         p.n_shift, p.n_int, p.cluster_half, p.use_graph = n_shift, wl.n_int, wl.cluster_half, int(use_graph)
+        p.shift_first = shift_first
         return segs, p
 
-    def batch_layout(self, segments, n_shift: int, shift_step: int):
+    def batch_layout(self, segments, n_shift: int, shift_step: int, shift_first: int = 1):
         """(windows per timeslide of each segment, total windows, total statistic samples)."""
-        segs, p = self._batch_args(segments, n_shift, shift_step, False)
+        segs, p = self._batch_args(segments, n_shift, shift_step, False, shift_first)
         n_win = (ctypes.c_int64 * len(segments))()
         tw, ts = _i64(), _i64()
         self._check(self._lib.afg_batch_layout(self._h, segs, len(segments), ctypes.byref(p), n_win, ctypes.byref(tw),
@@ -442,12 +443,13 @@ class Context:
         return list(n_win), tw.value, ts.value
 
     def batch_run(self, x, segments, n_shift: int, shift_step: int, trig_cap: int = 1 << 20, use_graph: bool = False,
-                  out=None, stream=None):
-        """Timeslide background over `segments` [(offset, n_raw)] of device strain x [2][x_len]:
-        returns (logits, stat, trig_idx, n_trig) device tensors, concatenated in series order."""
+                  out=None, stream=None, shift_first: int = 1):
+        """Timeslide background over `segments` [(offset, n_raw)] of device strain x [2][x_len], timeslides
+        k = shift_first .. shift_first + n_shift - 1: returns (logits, stat, trig_idx, n_trig) device
+        tensors, concatenated in series order."""
         import torch
-        segs, p = self._batch_args(segments, n_shift, shift_step, use_graph)
-        _, tw, ts = self.batch_layout(segments, n_shift, shift_step)
+        segs, p = self._batch_args(segments, n_shift, shift_step, use_graph, shift_first)
+        _, tw, ts = self.batch_layout(segments, n_shift, shift_step, shift_first)
         if out is None:
             out = (torch.empty(tw, dtype=torch.float32, device=x.device),
                    torch.empty(ts, dtype=torch.float32, device=x.device),

@@ -35,8 +35,9 @@ int make_plan(afg_ctx *ctx, const afg_segment *segs, int n_seg, const afg_batch_
     if (!segs || n_seg < 1 || !p) return afg_fail(ctx, AFG_ERR_ARG, "batch: no segments");
     if (p->epoch_len <= 0 || p->epoch_len % WB || p->epoch_len % hop || p->psd_len < NFFT ||
         (p->psd_len - NFFT) % hop || p->stride < 1 || p->n_shift < 1 || p->shift_step < 0 || p->n_int < 1 ||
-        p->cluster_half < 0)
+        p->cluster_half < 0 || p->shift_first < 0 || p->shift_first > (int64_t)1 << 40)
         return afg_fail(ctx, AFG_ERR_ARG, "batch: bad parameters");
+    const int64_t k0 = p->shift_first > 0 ? p->shift_first : 1;  // first timeslide of this call
     P = Plan();
     for (int i = 0; i < n_seg; ++i) {
         const int64_t n = segs[i].n_raw;
@@ -49,14 +50,14 @@ int make_plan(afg_ctx *ctx, const afg_segment *segs, int n_seg, const afg_batch_
         if (n_win < p->n_int)
             return afg_fail(ctx, AFG_ERR_ARG, "batch: segment %d has %lld windows, fewer than n_int", i,
                             (long long)n_win);
-        if ((int64_t)p->n_shift * p->shift_step >= n_white)
+        if ((k0 + p->n_shift - 1) * p->shift_step >= n_white)
             return afg_fail(ctx, AFG_ERR_ARG, "batch: segment %d is shorter than the largest timeslide", i);
         SegDesc d;
         d.y_off = P.total_white;
         d.n_y = n_white;
         d.n_win = n_win;
         d.win_first = P.total_win;
-        d.shift_first = 1;
+        d.shift_first = k0;
         P.segs.push_back(d);
         P.n_ep.push_back(n_ep);
         for (int k = 0; k < p->n_shift; ++k) {
@@ -226,7 +227,7 @@ static int enqueue(afg_ctx *ctx, const Plan &P, const float *x, int64_t x_len, c
             for (int k = 0; k < p->n_shift && !rc; ++k) {
                 const SegDesc &d = P.segs[i];
                 rc = launch_infer_fp32(ctx, white + d.y_off, d.n_y, P.total_white, 0, p->stride, d.n_win,
-                                       ((int64_t)(k + 1) * p->shift_step) % d.n_y,
+                                       ((d.shift_first + k) * p->shift_step) % d.n_y,
                                        logits + d.win_first + (int64_t)k * d.n_win, st);
             }
     }

@@ -91,6 +91,9 @@ __host__ __device__ inline Smem tiny_smem(int W, int n_conv, int k_stem) {
 }
 
 
+// x rounded to BF16 (nearest even) and back: the operand precision of the tensor-core stem
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
 // Sum NV per-lane values over the warp (NV a power of two <= 32) so that lane l ends with
 // the warp total of value l / (32 / NV) in v[0]: each butterfly stage keeps the half of the
 // values selected by the lane's bit and adds the partner's copy (NV - 1 shuffles in all,
@@ -277,7 +280,7 @@ __device__ __forceinline__ WinLoc locate_window(const TinyArgs &args, int64_t wi
 // the caller waits for: 16 bytes at a time where both rows are 16-byte aligned and the
 // circular L1 index cannot wrap inside 4 samples, else 4 bytes.
 __device__ __forceinline__ void load_window(const TinyArgs &args, const WinLoc &w, float *xs, int W, int pad,
-                                            bool async) {
+                                            bool async, int nthreads = TF_THREADS) {
     const int RP = W + 8;
     if (threadIdx.x < 4 * pad) {  // zero pads (pad <= 3) of both rows
         const int d = threadIdx.x & 1, i = threadIdx.x >> 1;  // i < pad: left; i >= pad: right
@@ -287,7 +290,7 @@ __device__ __forceinline__ void load_window(const TinyArgs &args, const WinLoc &
     const bool vec = async && ((w.start | w.l1_shift | w.n_y) & 3) == 0 &&
                      ((reinterpret_cast<uintptr_t>(w.y0 + w.start) | reinterpret_cast<uintptr_t>(w.y1)) & 15) == 0;
     if (vec) {
-        for (int c = threadIdx.x; c < 2 * (W / 4); c += TF_THREADS) {
+        for (int c = threadIdx.x; c < 2 * (W / 4); c += nthreads) {
             const int d = c >= W / 4, s = 4 * (c - d * (W / 4));
             const float *src;
             if (d == 0) {
@@ -302,7 +305,7 @@ __device__ __forceinline__ void load_window(const TinyArgs &args, const WinLoc &
                          : "memory");
         }
     } else {
-        for (int c = threadIdx.x; c < 2 * W; c += TF_THREADS) {
+        for (int c = threadIdx.x; c < 2 * W; c += nthreads) {
             const int d = c >= W, s = c - d * W;
             const float *src;
             if (d == 0) {
@@ -439,8 +442,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 float u[6];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    u[r] = xs0[t + r];
-                    u[3 + r] = xs1[t + r];
+                    u[r] = bf16_round(xs0[t + r]);
+                    u[3 + r] = bf16_round(xs1[t + r]);
                 }
                 // upper triangle row by row; two entries of a row per packed FP32x2 FMA
                 int m = 0;
@@ -488,7 +491,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
             __syncthreads();
             if (tid < TF_C) {
                 const float *mom = red + TF_WARPS * 32;
-                const float *wc = stem_w + tid * 6;  // [ci][r] = u order
+                float wc[6];  // [ci][r] = u order
+#pragma unroll
+                for (int i = 0; i < 6; ++i) wc[i] = bf16_round(stem_w[tid * 6 + i]);
                 float mean = 0.f, e2 = 0.f;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) mean = fmaf(wc[i], mom[i], mean);
@@ -528,7 +533,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
 #pragma unroll
-                for (int i = 0; i < 6; ++i) wr[c][i] = stem_w[(h * 8 + c) * 6 + i];
+                for (int i = 0; i < 6; ++i) wr[c][i] = bf16_round(stem_w[(h * 8 + c) * 6 + i]);
                 sc8[c] = scale[h * 8 + c];
                 sh8[c] = shift[h * 8 + c];
             }
@@ -538,8 +543,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                 float u[6];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    u[r] = xs0[t + r];
-                    u[3 + r] = xs1[t + r];
+                    u[r] = bf16_round(xs0[t + r]);
+                    u[3 + r] = bf16_round(xs1[t + r]);
                 }
                 uint32_t pk[4];
 #pragma unroll
@@ -563,8 +568,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
                     float u[6];
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
-                        u[r] = xs0[t + r];
-                        u[3 + r] = xs1[t + r];
+                        u[r] = bf16_round(xs0[t + r]);
+                        u[3 + r] = bf16_round(xs1[t + r]);
                     }
 #pragma unroll
                     for (int c = 0; c < 8; c += 2) {
@@ -867,6 +872,442 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
     if (warp == 0) tc::tmem_dealloc(tmem, CL > 1 ? 128 : 512);
 }
 
+// ============================================================================
+// k_tiny_pipe: the fused 16-channel network with its layers pipelined inside a
+// window (one window per CTA pass, persistent over windows).
+//
+// Warp roles (416 threads):
+//   warps 0..11  epilogue: build the stem's im2col tile, then per layer a
+//                statistics pass and a normalise pass over the TMEM accumulators;
+//                quad q = warp / 4 owns the 128-position subtiles j = q, q + 3, ..
+//                (each warp its TMEM lane quarter warp % 4)
+//   warp 12      MMA issue (one elected lane, the warp uniform)
+// Every layer, stem included, is an implicit GEMM with M = 128 positions, N = 16
+// channels, accumulators for the whole window in TMEM (W / 128 subtiles x 16
+// columns).  Per subtile j two mbarriers link the roles:
+//   rows_ready[j]  the input rows of subtile j of the next layer are in shared
+//                  memory (128 epilogue arrivals): its im2col rows for the stem,
+//                  else the previous layer's normalised output; the tensor core
+//                  also reads the first row of subtile j + 1 (the k = 3 halo), so
+//                  the MMAs of subtile j wait for rows_ready[j] and [j + 1].
+//                  The arrival also releases subtile j's accumulator columns,
+//                  which the layer's MMAs overwrite (their old values were read
+//                  by the normalise pass that produced these rows).
+//   mma_done[j]    the MMAs of subtile j of the current layer have completed.
+// So the MMAs of layer k + 1 run while the normalise pass of layer k is still
+// writing later subtiles, and the statistics pass of layer k + 1 reads each
+// subtile as soon as its MMAs are done; only GroupNorm's block-wide reduction
+// separates the layers.  Each barrier completes once per layer, so both roles
+// wait on the parity of a running layer count.
+//
+// Stem (2 -> 16 channels, k = 3): row t of the im2col tile holds the six BF16 taps
+// (x0[t-1], x0[t], x0[t+1], x1[t-1], x1[t], x1[t+1], 0, 0): one 16-byte row per
+// position, read as the first K half of an M = 128, N = 16, K = 16 MMA.  The
+// second K half is addressed 16 bytes on (the next row, finite data) and meets
+// zero weights.  The tile sits in buffer B's second channel chunk, the raw FP32
+// window (staged by cp.async during the previous window's last layer) in its
+// first; both are free by then.
+// Shared memory: activation buffers A and B ([2 chunks][W + 2 rows][16 B], rows
+// 0 and W + 1 zero), the BF16 weight images (convs, then the stem), the FP32
+// parameters, reduction scratch and barriers, then the batch segment table.
+// ============================================================================
+constexpr int TP_EPI_WARPS = 12;           // 3 quads: with the MMA warp 13 warps, 128 registers each
+constexpr int TP_NQ = TP_EPI_WARPS / 4;      // quads of epilogue warps
+constexpr int TP_EPI = TP_EPI_WARPS * 32;
+constexpr int TP_THREADS = TP_EPI + 32;
+constexpr int TP_MT_MAX = 32;
+constexpr int TP_STEM_IMG = 512;  // BF16 image of the stem weights: 16 channels x K = 16
+constexpr uint64_t TP_WAIT_NS = 1000000000ull;
+
+struct PipeSmem {
+    size_t off_a, off_b, off_w, off_p, off_s, off_r, off_bar, total;
+};
+
+__host__ __device__ inline PipeSmem pipe_smem(int W, int n_conv, int k_stem) {
+    PipeSmem s;
+    const size_t act = (size_t)2 * (W + 2) * 16;
+    s.off_a = 0;
+    s.off_b = act;
+    s.off_w = 2 * act;
+    s.off_p = s.off_w + (size_t)n_conv * TF_WIMG + TP_STEM_IMG;
+    s.off_s = s.off_p + (((size_t)tiny_param_count(k_stem, n_conv) * 4 + 15) / 16) * 16;
+    s.off_r = s.off_s + 2 * TF_C * 4;
+    s.off_bar = s.off_r + (size_t)(TP_EPI_WARPS * 32 + 32) * 4;
+    // mma_done[TP_MT_MAX], rows_ready[TP_MT_MAX], drain, then tmem slot, abort flag, stop flag
+    s.total = s.off_bar + (2 * TP_MT_MAX + 1) * 8 + 16;
+    return s;
+}
+
+// GroupNorm reduction over the epilogue warps (named barrier 1): per-thread group
+// sums (x: sum, y: sum of squares) -> per-channel affine map, plus a consistent copy
+// of the abort flag for every epilogue thread (stop).
+template <int G>
+__device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, float eps, const float *gamma,
+                                              const float *beta, float *red, float *scale, float *shift,
+                                              const volatile int *abort_flag, int *stop) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NV = 2 * G;
+    float v[NV];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        v[g] = sq[g].x;
+        v[G + g] = sq[g].y;
+    }
+    warp_reduce_scatter<NV>(v, lane);
+    if ((lane & (32 / NV - 1)) == 0) red[warp * 32 + lane / (32 / NV)] = v[0];
+    tc::named_bar_sync(1, TP_EPI);
+    if (threadIdx.x < TF_C) {
+        const int c = threadIdx.x, g = c / (TF_C / G);
+        float ts = 0.f, tq = 0.f;
+        for (int w = 0; w < TP_EPI_WARPS; ++w) {
+            ts += red[w * 32 + g];
+            tq += red[w * 32 + G + g];
+        }
+        const float mean = ts / cnt;
+        const float var = fmaxf(tq / cnt - mean * mean, 0.f);
+        const float a = rsqrtf(var + eps) * gamma[c];
+        scale[c] = a;
+        shift[c] = beta[c] - mean * a;
+    }
+    if (threadIdx.x == 0) *stop = *abort_flag;
+    tc::named_bar_sync(1, TP_EPI);
+}
+
+// Window output: the logit (and, in list mode, the statistics of the launch once its last
+// window is done; executed by one warp, lane 0 holding z).
+__device__ __forceinline__ void tiny_emit(const TinyArgs &args, int64_t out, float *out_ptr, float z, int lane) {
+    bool last_win = false;
+    if (lane == 0) {
+        if (out_ptr) *out_ptr = z;
+        else args.logits[out] = z;
+        if (args.integ) {  // publish the logit, then count the window
+            __threadfence();
+            last_win = atomicAdd(args.done, 1u) == (unsigned)(args.n_win - 1);
+        }
+    }
+    if (__shfl_sync(0xffffffffu, last_win, 0)) {
+        // every logit of the launch is written: the statistics of the new windows, lane l
+        // loading logit w - n_int + 1 + l (+ 32 ...) of 8 statistics at a time, then a warp sum
+        // in a fixed order (the loads of a batch are all in flight together)
+        __threadfence();
+        for (int i0 = 0; i0 < args.n_integ; i0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                v[b] = 0.f;
+                if (i0 + b < args.n_integ) {
+                    const IntegDesc d = args.integ[i0 + b];
+                    for (int l = lane; l < args.n_int; l += 32)
+                        v[b] += __ldcg(d.ring + (d.w - args.n_int + 1 + l) % STREAM_LR);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v[b] += __shfl_xor_sync(0xffffffffu, v[b], o);
+            if (lane < 8 && i0 + lane < args.n_integ) {
+                float tot = v[0];
+#pragma unroll
+                for (int b = 1; b < 8; ++b)
+                    if (lane == b) tot = v[b];
+                const IntegDesc d = args.integ[i0 + lane];
+                d.out[0] = tot / (float)args.n_int;
+                d.out[1] = __ldcg(d.ring + d.w % STREAM_LR);
+            }
+        }
+        if (lane == 0) *args.done = 0u;
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    pdl_trigger();
+    const int W = args.W, n_conv = args.n_conv, MT = W / 128, k_stem = args.k_stem;
+    const PipeSmem L = pipe_smem(W, n_conv, k_stem);
+    unsigned char *actA = sm + L.off_a;
+    unsigned char *actB = sm + L.off_b;
+    unsigned char *wimg = sm + L.off_w;
+    float *prm = reinterpret_cast<float *>(sm + L.off_p);
+    float *scale = reinterpret_cast<float *>(sm + L.off_s);
+    float *shift = scale + TF_C;
+    float *red = reinterpret_cast<float *>(sm + L.off_r);
+    uint64_t *mma_done = reinterpret_cast<uint64_t *>(sm + L.off_bar);
+    uint64_t *rows_ready = mma_done + TP_MT_MAX;
+    uint64_t *drain = rows_ready + TP_MT_MAX;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *stop = reinterpret_cast<int *>(tmem_slot + 2);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t act_chunk = (size_t)(W + 2) * 16;
+
+    // ---- one-time set-up: parameters, weight images, zero pad rows, barriers, TMEM
+    const int n_prm = tiny_param_count(k_stem, n_conv);
+    for (int i = tid; i < n_prm; i += TP_THREADS) prm[i] = args.params[i];
+    for (int i = tid; i < (n_conv * TF_WIMG + TP_STEM_IMG) / 16; i += TP_THREADS)
+        reinterpret_cast<uint4 *>(wimg)[i] = reinterpret_cast<const uint4 *>(args.wimg)[i];
+    if (tid < 8) {
+        unsigned char *buf = (tid & 4) ? actB : actA;
+        const int c = (tid >> 1) & 1, row = (tid & 1) ? W + 1 : 0;
+        *reinterpret_cast<uint4 *>(buf + c * act_chunk + (size_t)row * 16) = make_uint4(0, 0, 0, 0);
+    }
+    // the im2col tile's rows start finite (zero): the stem MMA's second K half (zero weights) also
+    // reads the first row of the next subtile, which another quad may not have written yet
+    for (int i = tid; i < W; i += TP_THREADS)
+        *reinterpret_cast<uint4 *>(actB + act_chunk + 16 + (size_t)i * 16) = make_uint4(0, 0, 0, 0);
+    if (args.seg_cache > 0) {
+        SegDesc *seg_sm = reinterpret_cast<SegDesc *>(sm + L.total);
+        for (int i = tid; i < args.seg_cache; i += TP_THREADS) seg_sm[i] = args.segs[i];
+    }
+    if (tid == 0) {
+        for (int j = 0; j < TP_MT_MAX; ++j) {
+            tc::mbar_init(&mma_done[j], 1);
+            tc::mbar_init(&rows_ready[j], 128);
+        }
+        tc::mbar_init(drain, 1);
+        tc::fence_mbar_init();
+        *abort_flag = 0;
+        *stop = 0;
+    }
+    if (warp == TP_EPI_WARPS) {
+        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();  // weight images and zero rows -> the tensor core
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const SegDesc *segs = args.seg_cache > 0 ? reinterpret_cast<const SegDesc *>(sm + L.total) : args.segs;
+    const int64_t win0 = blockIdx.x, win_step = gridDim.x;
+    pdl_wait();  // list mode: the whitened rings come from the whitening launch before
+
+    if (warp == TP_EPI_WARPS) {
+        // ================================================================ MMA warp
+        const uint32_t idesc = tc::idesc_bf16_f32(128, TF_C);
+        const uint64_t d_stem_a = tc::desc_kmajor_noswizzle(tc::smem_addr(actB + act_chunk + 16), 16, 128);
+        const uint64_t d_stem_b = tc::desc_kmajor_noswizzle(tc::smem_addr(wimg + (size_t)n_conv * TF_WIMG), 256, 128);
+        const uint64_t d_a = tc::desc_kmajor_noswizzle(tc::smem_addr(actA), (uint32_t)act_chunk, 128);
+        const uint64_t d_b = tc::desc_kmajor_noswizzle(tc::smem_addr(actB), (uint32_t)act_chunk, 128);
+        const uint64_t d_w = tc::desc_kmajor_noswizzle(tc::smem_addr(wimg), 256, 128);
+        uint32_t seq = 0;
+        bool ok = true;
+        for (int64_t win = win0; win < args.n_win && ok; win += win_step) {
+            for (int k = 0; k <= n_conv && ok; ++k, ++seq) {
+                const uint32_t par = seq & 1;
+                const int l = k - 1;
+                const uint64_t ad = (l & 1) ? d_b : d_a;  // the second conv of a block reads B
+                const uint64_t bd = d_w + (uint64_t)((k > 0 ? l : 0) * (TF_WIMG / 16));
+                for (int j = 0; j < MT; ++j) {
+                    bool w_ok = tc::mbar_wait(&rows_ready[j], par, TP_WAIT_NS);
+                    if (w_ok && k > 0 && j + 1 < MT) w_ok = tc::mbar_wait(&rows_ready[j + 1], par, TP_WAIT_NS);
+                    // one decision for the whole warp (the issue below is by an elected lane of a converged warp)
+                    if (!__all_sync(0xffffffffu, w_ok && !*abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t dt = tmem + (uint32_t)(j * TF_C);
+                    if (k == 0) {
+                        tc::mma_bf16_elect(dt, d_stem_a + (uint64_t)(128 * j), d_stem_b, idesc, 0u);
+                    } else {
+                        const uint64_t a0 = ad + (uint64_t)(128 * j);
+                        tc::mma_bf16_elect(dt, a0, bd, idesc, 0u);
+                        tc::mma_bf16_elect(dt, a0 + 1, bd + 32, idesc, 1u);
+                        tc::mma_bf16_elect(dt, a0 + 2, bd + 64, idesc, 1u);
+                    }
+                    tc::mma_commit_elect(&mma_done[j]);
+                }
+                __syncwarp();
+            }
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(args.err, 1);
+            *abort_flag = 1;
+        }
+        // every MMA issued above completes before the accumulators are released
+        tc::mma_commit_elect(drain);
+        if (!tc::mbar_wait(drain, 0, TP_WAIT_NS) && lane == 0) atomicExch(args.err, 1);
+    } else {
+        // ================================================================ epilogue warps
+        const int q = warp >> 2, lq = warp & 3;
+        const uint32_t tq = tmem + ((uint32_t)(32 * lq) << 16);
+        const float *stem_g = prm + TF_C * 2 * k_stem;
+        const float *stem_b = stem_g + TF_C;
+        const float *conv_gb = stem_b + TF_C;
+        const float *fc_w = conv_gb + n_conv * 2 * TF_C;
+        const float fc_b = fc_w[TF_C];
+        const float cnt = (float)W * (float)(TF_C / G);
+        float *xs = reinterpret_cast<float *>(actB + 16);   // raw window, [2][W + 8] FP32
+        unsigned char *im2col = actB + act_chunk + 16;       // stem im2col tile, [W][16 B]
+        const int RP = W + 8;
+        uint32_t seq = 0;
+        WinLoc cur = locate_window(args, win0, segs);
+        if (win0 < args.n_win) load_window(args, cur, xs, W, 1, true, TP_EPI);
+        for (int64_t win = win0; win < args.n_win; win += win_step) {
+            const int64_t out = cur.out;
+            float *out_ptr = cur.out_ptr;
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            tc::named_bar_sync(1, TP_EPI);
+            // ---- stem im2col rows of this quad's subtiles (BF16, six taps per 16-byte row)
+            for (int j = q; j < MT; j += TP_NQ) {
+                const int t = 128 * j + 32 * lq + lane;
+                const float *p0 = xs + 4 + t - 1, *p1 = xs + RP + 4 + t - 1;
+                const uint4 row = make_uint4(tc::pack_bf16x2(p0[0], p0[1]), tc::pack_bf16x2(p0[2], p1[0]),
+                                             tc::pack_bf16x2(p1[1], p1[2]), 0u);
+                *reinterpret_cast<uint4 *>(im2col + (size_t)t * 16) = row;
+                tc::fence_proxy_async_smem();
+                tc::fence_before_sync();  // (this subtile's accumulators were read by the last layer)
+                tc::mbar_arrive(&rows_ready[j]);
+            }
+            float hs[TF_C];
+#pragma unroll
+            for (int c = 0; c < TF_C; ++c) hs[c] = 0.f;
+            bool stopped = false;
+            for (int k = 0; k <= n_conv; ++k, ++seq) {
+                const uint32_t par = seq & 1;
+                const int l = k - 1;
+                const bool last = k == n_conv;
+                const bool res = k > 0 && (l & 1);  // second conv of a block: residual from A
+                unsigned char *dst = (k == 0 || (l & 1)) ? actA : actB;
+                const float *gam = k == 0 ? stem_g : conv_gb + l * 2 * TF_C;
+                // ---- statistics pass: each subtile as soon as its MMAs are done
+                float2 sq[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) sq[g] = make_float2(0.f, 0.f);
+                bool ok = true;
+                for (int j0 = q; j0 < MT; j0 += 2 * TP_NQ) {
+                    const int j1 = j0 + TP_NQ;
+                    uint32_t r0[16], r1[16];
+                    // (after a failed wait the rest are skipped: the MMA warp has stopped)
+                    if (*abort_flag || !tc::mbar_wait(&mma_done[j0], par, TP_WAIT_NS)) ok = false;
+                    if (j1 < MT && (*abort_flag || !tc::mbar_wait(&mma_done[j1], par, TP_WAIT_NS))) ok = false;
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
+                    if (j1 < MT) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < TF_C; ++c) {
+                        const float v = __uint_as_float(r0[c]);
+                        sq[c / (TF_C / G)] = __ffma2_rn(make_float2(v, v), make_float2(1.f, v), sq[c / (TF_C / G)]);
+                    }
+                    if (j1 < MT) {
+#pragma unroll
+                        for (int c = 0; c < TF_C; ++c) {
+                            const float v = __uint_as_float(r1[c]);
+                            sq[c / (TF_C / G)] =
+                                __ffma2_rn(make_float2(v, v), make_float2(1.f, v), sq[c / (TF_C / G)]);
+                        }
+                    }
+                }
+                if (!ok) {
+                    atomicExch(args.err, 1);
+                    *abort_flag = 1;
+                }
+                gn_reduce_epi<G>(sq, cnt, args.eps, gam, gam + TF_C, red, scale, shift, abort_flag, stop);
+                if (*stop) {
+                    stopped = true;
+                    break;
+                }
+                if (last && win + win_step < args.n_win) {
+                    // every MMA of the last layer is done (its statistics are complete), so buffer B,
+                    // its input, is free: stage the next window's samples while this one finishes
+                    cur = locate_window(args, win + win_step, segs);
+                    load_window(args, cur, xs, W, 1, true, TP_EPI);
+                }
+                // ---- normalise pass (+ residual) + ReLU -> BF16 rows of dst, or the pooled sums
+                float sc[TF_C], sh[TF_C];
+#pragma unroll
+                for (int c = 0; c < TF_C; ++c) {
+                    sc[c] = scale[c];
+                    sh[c] = shift[c];
+                }
+                for (int j0 = q; j0 < MT; j0 += 2 * TP_NQ) {
+                    const int j1 = j0 + TP_NQ;
+                    const bool two = j1 < MT;
+                    uint32_t r0[16], r1[16];
+                    tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
+                    if (two) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        if (half == 1 && !two) break;
+                        const int j = half ? j1 : j0;
+                        const uint32_t *rr = half ? r1 : r0;
+                        const size_t row = (size_t)(128 * j + 32 * lq + lane + 1) * 16;
+#pragma unroll
+                        for (int ch = 0; ch < 2; ++ch) {
+                            float2 v[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                v[e] = __ffma2_rn(make_float2(__uint_as_float(rr[ch * 8 + 2 * e]),
+                                                              __uint_as_float(rr[ch * 8 + 2 * e + 1])),
+                                                  make_float2(sc[ch * 8 + 2 * e], sc[ch * 8 + 2 * e + 1]),
+                                                  make_float2(sh[ch * 8 + 2 * e], sh[ch * 8 + 2 * e + 1]));
+                            if (last) {
+                                // the block's residual in FP32, ReLU, pooled sums (nothing stored)
+                                const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + row);
+                                const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const float2 y = __fadd2_rn(v[e], make_float2(__uint_as_float(w4[e] << 16),
+                                                                                  __uint_as_float(w4[e] & 0xffff0000u)));
+                                    hs[ch * 8 + 2 * e] += fmaxf(y.x, 0.f);
+                                    hs[ch * 8 + 2 * e + 1] += fmaxf(y.y, 0.f);
+                                }
+                            } else if (res) {
+                                // + the block's residual in FP32, ReLU folded into the BF16 conversion
+                                const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + row);
+                                const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+                                uint32_t pk[4];
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const float2 y = __fadd2_rn(v[e], make_float2(__uint_as_float(w4[e] << 16),
+                                                                                  __uint_as_float(w4[e] & 0xffff0000u)));
+                                    pk[e] = tc::pack_bf16x2_relu(y.x, y.y);
+                                }
+                                *reinterpret_cast<uint4 *>(dst + ch * act_chunk + row) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            } else {
+                                *reinterpret_cast<uint4 *>(dst + ch * act_chunk + row) =
+                                    make_uint4(tc::pack_bf16x2_relu(v[0].x, v[0].y), tc::pack_bf16x2_relu(v[1].x, v[1].y),
+                                               tc::pack_bf16x2_relu(v[2].x, v[2].y), tc::pack_bf16x2_relu(v[3].x, v[3].y));
+                            }
+                        }
+                        if (!last) {
+                            tc::fence_proxy_async_smem();
+                            tc::fence_before_sync();
+                            tc::mbar_arrive(&rows_ready[j]);
+                        }
+                    }
+                }
+                if (last) tc::fence_before_sync();
+            }
+            if (stopped) break;
+            // ---- head: global mean pool, then the linear layer
+            warp_reduce_scatter<TF_C>(hs, lane);  // lane 2c holds the warp's sum of channel c
+            if (!(lane & 1)) red[warp * 32 + (lane >> 1)] = hs[0];
+            tc::named_bar_sync(1, TP_EPI);
+            if (warp == 0) {
+                float part = 0.f;
+                if (lane < TF_C) {
+                    for (int w = 0; w < TP_EPI_WARPS; ++w) part += red[w * 32 + lane];
+                    part = fc_w[lane] * (part / (float)W);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                tiny_emit(args, out, out_ptr, fc_b + part, lane);
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    // ---- teardown: the MMA warp has drained its MMAs
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == TP_EPI_WARPS) tc::tmem_dealloc(tmem, 512);
+}
+
 bool tiny_compatible(const afg_ctx *ctx) {
     const afg_net &n = ctx->cfg.net;
     const int W = ctx->cfg.win_len;
@@ -874,8 +1315,12 @@ bool tiny_compatible(const afg_ctx *ctx) {
     return n.n_stages == 1 && n.widths[0] == TF_C && n.stem_k == 3 && n.stem_stride == 1 && n.stem_pool == 0 &&
            W % 128 == 0 &&
            (W / 128) * TF_C <= 512 && (g == 1 || g == 2 || g == 4 || g == 8 || g == 16) &&
-           tiny_smem(W, 2 * n.blocks[0], n.stem_k).total <= 227 * 1024;
+           tiny_smem(W, 2 * n.blocks[0], n.stem_k).total <= 227 * 1024 &&
+           pipe_smem(W, 2 * n.blocks[0], n.stem_k).total <= 227 * 1024;
 }
+
+// batch segment descriptors the pipelined kernel keeps in shared memory after its layout
+__host__ inline int pipe_seg_cache_cap(size_t total) { return tiny_seg_cache_cap(total); }
 
 }  // namespace
 
@@ -886,7 +1331,8 @@ int net_tc_prepare(afg_ctx *ctx) {
     const int k = P.net.stem_k;
     const int n_conv = (int)P.convs.size() - 1;
     std::vector<float> prm((size_t)tiny_param_count(k, n_conv));
-    std::vector<unsigned short> img((size_t)n_conv * TF_WIMG / 2);
+    // conv images, then the stem's image (K = ci * 3 + r, zero for K >= 6) for the pipelined kernel
+    std::vector<unsigned short> img(((size_t)n_conv * TF_WIMG + TP_STEM_IMG) / 2, 0);
     std::vector<float> host_w;
     // copy the device parameter image back to read the layers' weights
     std::vector<float> all(ctx->d_params_bytes / sizeof(float));
@@ -895,6 +1341,13 @@ int net_tc_prepare(afg_ctx *ctx) {
     size_t o = 0;
     const ConvLayer &S = P.convs[0];
     for (int i = 0; i < TF_C * 2 * k; ++i) prm[o++] = at(S.wt)[i];
+    // stem weights [co][ci][r] -> image[k = ci * 3 + r][co] (K-major, no swizzle, as the convs' taps)
+    for (int co = 0; co < TF_C; ++co)
+        for (int kk = 0; kk < 2 * k; ++kk) {
+            const size_t byte = (size_t)n_conv * TF_WIMG + (kk / 8) * 256 + co * 16 + (kk % 8) * 2;
+            __nv_bfloat16 b = __float2bfloat16_rn(at(S.wt)[co * 2 * k + kk]);
+            img[byte / 2] = *reinterpret_cast<unsigned short *>(&b);
+        }
     for (int c = 0; c < TF_C; ++c) prm[o++] = at(S.gamma)[c];
     for (int c = 0; c < TF_C; ++c) prm[o++] = at(S.beta)[c];
     for (int l = 0; l < n_conv; ++l) {
@@ -925,13 +1378,13 @@ int net_tc_prepare(afg_ctx *ctx) {
     P.tc_wimg = static_cast<unsigned char *>(d) + ((pbytes + 255) / 256) * 256;
     AFG_CUDA(ctx, cudaMemcpy(P.tc_params, prm.data(), pbytes, cudaMemcpyHostToDevice));
     AFG_CUDA(ctx, cudaMemcpy(P.tc_wimg, img.data(), ibytes, cudaMemcpyHostToDevice));
-    const size_t base = tiny_smem(ctx->cfg.win_len, n_conv, k).total;
-    const int smem = (int)(base + tiny_seg_cache_cap(base) * sizeof(SegDesc));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const size_t pbase = pipe_smem(ctx->cfg.win_len, n_conv, k).total;
+    const int psmem = (int)(pbase + pipe_seg_cache_cap(pbase) * sizeof(SegDesc));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
     if (ctx->cfg.win_len % (128 * TF_CLUSTER) == 0) {  // list mode on clusters: a quarter window per CTA
         const int smem_c = (int)tiny_smem(ctx->cfg.win_len / TF_CLUSTER, n_conv, k).total + TF_XCH;
         AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<1, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -977,8 +1430,8 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     a.W = W;
     a.G = P.net.groups;
     a.eps = P.net.eps;
-    const Smem L = tiny_smem(W, n_conv, a.k_stem);
-    a.seg_cache = n_seg <= tiny_seg_cache_cap(L.total) ? n_seg : 0;
+    const PipeSmem L = pipe_smem(W, n_conv, a.k_stem);
+    a.seg_cache = n_seg <= pipe_seg_cache_cap(L.total) ? n_seg : 0;
     const size_t smem = L.total + (size_t)a.seg_cache * sizeof(SegDesc);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -986,13 +1439,13 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     const double flops = 2.0 * total_win * W * TF_C * ((3.0 * TF_C) * n_conv + 2.0 * a.k_stem);
     KScope ks(ctx, st, KK_TINY_TC, flops, (double)total_win * (2.0 * W * 4.0 + 4.0));
     switch (a.G) {
-        case 1: k_tiny_fused<1><<<grid, TF_THREADS, smem, st>>>(a); break;
-        case 2: k_tiny_fused<2><<<grid, TF_THREADS, smem, st>>>(a); break;
-        case 4: k_tiny_fused<4><<<grid, TF_THREADS, smem, st>>>(a); break;
-        case 8: k_tiny_fused<8><<<grid, TF_THREADS, smem, st>>>(a); break;
-        default: k_tiny_fused<16><<<grid, TF_THREADS, smem, st>>>(a); break;
+        case 1: k_tiny_pipe<1><<<grid, TP_THREADS, smem, st>>>(a); break;
+        case 2: k_tiny_pipe<2><<<grid, TP_THREADS, smem, st>>>(a); break;
+        case 4: k_tiny_pipe<4><<<grid, TP_THREADS, smem, st>>>(a); break;
+        case 8: k_tiny_pipe<8><<<grid, TP_THREADS, smem, st>>>(a); break;
+        default: k_tiny_pipe<16><<<grid, TP_THREADS, smem, st>>>(a); break;
     }
-    AFG_LAUNCH_CHECK(ctx, "k_tiny_fused(batch)");
+    AFG_LAUNCH_CHECK(ctx, "k_tiny_pipe(batch)");
     return AFG_OK;
 }
 
@@ -1023,7 +1476,6 @@ int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, 
     a.W = W;
     a.G = P.net.groups;
     a.eps = P.net.eps;
-    const Smem L = tiny_smem(W, n_conv, a.k_stem);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const unsigned grid = (unsigned)std::min<int64_t>(n_win, std::max(sms, 1));
@@ -1045,12 +1497,13 @@ int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, 
         AFG_CUDA(ctx, e);
         return AFG_OK;
     }
+    const size_t psmem = pipe_smem(W, n_conv, a.k_stem).total;
     switch (a.G) {
-        case 1: e = launch_pdl(k_tiny_fused<1>, dim3(grid), dim3(TF_THREADS), L.total, st, a); break;
-        case 2: e = launch_pdl(k_tiny_fused<2>, dim3(grid), dim3(TF_THREADS), L.total, st, a); break;
-        case 4: e = launch_pdl(k_tiny_fused<4>, dim3(grid), dim3(TF_THREADS), L.total, st, a); break;
-        case 8: e = launch_pdl(k_tiny_fused<8>, dim3(grid), dim3(TF_THREADS), L.total, st, a); break;
-        default: e = launch_pdl(k_tiny_fused<16>, dim3(grid), dim3(TF_THREADS), L.total, st, a); break;
+        case 1: e = launch_pdl(k_tiny_pipe<1>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
+        case 2: e = launch_pdl(k_tiny_pipe<2>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
+        case 4: e = launch_pdl(k_tiny_pipe<4>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
+        case 8: e = launch_pdl(k_tiny_pipe<8>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
+        default: e = launch_pdl(k_tiny_pipe<16>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
     }
     AFG_CUDA(ctx, e);
     return AFG_OK;
@@ -1089,20 +1542,20 @@ int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
     a.W = W;
     a.G = P.net.groups;
     a.eps = P.net.eps;
-    const Smem L = tiny_smem(W, n_conv, a.k_stem);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const unsigned grid = (unsigned)std::min<int64_t>(n_win, std::max(sms, 1));
     const double flops_conv = 2.0 * n_win * W * TF_C * (3.0 * TF_C) * n_conv;
     const double flops_stem = 2.0 * n_win * W * TF_C * 2.0 * a.k_stem;
     KScope ks(ctx, st, KK_TINY_TC, flops_conv + flops_stem, (double)n_win * (2.0 * W * 4.0 + 4.0));
+    const size_t psmem = pipe_smem(W, n_conv, a.k_stem).total;
     switch (a.G) {
-        case 1: k_tiny_fused<1><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        case 2: k_tiny_fused<2><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        case 4: k_tiny_fused<4><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        case 8: k_tiny_fused<8><<<grid, TF_THREADS, L.total, st>>>(a); break;
-        default: k_tiny_fused<16><<<grid, TF_THREADS, L.total, st>>>(a); break;
+        case 1: k_tiny_pipe<1><<<grid, TP_THREADS, psmem, st>>>(a); break;
+        case 2: k_tiny_pipe<2><<<grid, TP_THREADS, psmem, st>>>(a); break;
+        case 4: k_tiny_pipe<4><<<grid, TP_THREADS, psmem, st>>>(a); break;
+        case 8: k_tiny_pipe<8><<<grid, TP_THREADS, psmem, st>>>(a); break;
+        default: k_tiny_pipe<16><<<grid, TP_THREADS, psmem, st>>>(a); break;
     }
-    AFG_LAUNCH_CHECK(ctx, "k_tiny_fused");
+    AFG_LAUNCH_CHECK(ctx, "k_tiny_pipe");
     return AFG_OK;
 }

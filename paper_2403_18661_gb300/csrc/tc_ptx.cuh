@@ -99,6 +99,28 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// The same MMA issued by a whole warp executing uniformly: one elected lane issues it, so
+// the operands stay warp-uniform (no per-lane divergence around the issue).
+__device__ __forceinline__ void mma_bf16_elect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred P, Q;\n\t"
+        "elect.sync _|P, 0xffffffff;\n\t"
+        "setp.ne.b32 Q, %4, 0;\n\t"
+        "@P tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, Q;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// commit from the elected lane of a uniform warp (the lane that issued with mma_bf16_elect)
+__device__ __forceinline__ void mma_commit_elect(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\t"
+        "@P tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+            smem_addr(bar))
+        : "memory");
+}
+
 // arrive once on `bar` when every MMA this thread issued before has completed
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
@@ -170,6 +192,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2_relu(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
     return d;
+}
+
+// relu(a * b + c) on BF16 pairs, rounded once to BF16
+__device__ __forceinline__ uint32_t fma_relu_bf16x2(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// named barrier `id` (1..15) over `count` threads (a multiple of 32)
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // 32 consecutive columns per thread, waited

@@ -51,7 +51,8 @@ def _check(wl, segs, ref, logits, stat, trig, n_trig, tol):
     assert np.all(np.diff(tr) > 0)
     lo = so = 0
     worst = 0.0
-    tot = dict(oracle=0, gpu=0, decisive=0, near_tie=0, near_tie_same=0, near_tie_moved=0, near_ties=[])
+    tot = dict(oracle=0, gpu=0, identical=True, decisive=0, near_tie=0, near_tie_same=0, near_tie_moved=0,
+               near_ties=[])
     for per in ref:
         for z, s_ref, t_ref in per:
             got = lg[lo:lo + len(z)]
@@ -63,7 +64,7 @@ def _check(wl, segs, ref, logits, stat, trig, n_trig, tol):
             mine = np.array([int(t) - so for t in tr if so <= t < so + len(s_ref)], dtype=np.int64)
             c = trigger_match.compare(s_got, s_ref, mine, t_ref, wl.cluster_half, tol)
             for k in tot:
-                tot[k] += c[k]
+                tot[k] = (tot[k] and c[k]) if k == "identical" else tot[k] + c[k]
             lo += len(z)
             so += len(s_ref)
     assert lo == len(lg) and so == len(st)
@@ -82,7 +83,9 @@ def test_batch_matches_oracle(batch_case, precision, tol, capsys):
     with capsys.disabled():
         print(f"\nbatch precision {precision}: {tw} windows, max |dz|/(1+|z|) = {worst:.3e}; "
               f"{trigger_match.summary(c)}")
-    assert c["decisive"] > 0
+    # every trigger was checked: decisive ones index for index, near-ties (with the BF16 tolerance
+    # almost all maxima of this near-flat random-weight statistic) at the same index or tied
+    assert c["oracle"] > 0 and c["decisive"] + c["near_tie_same"] + c["near_tie_moved"] == c["oracle"] + c["gpu"]
     ctx.close()
 
 

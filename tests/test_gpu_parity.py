@@ -316,7 +316,7 @@ def test_bf16_precision_c1_trigger_list(c1, ctx_tiny_bf16, capsys):
     with capsys.disabled():
         print(f"\nC1 BF16 logits max |dz|/(1+|z|) = {err.max():.3e}; {trigger_match.summary(c)}")
     assert err.max() < BF16_LOGIT_TOL
-    assert c["decisive"] > 0
+    assert c["oracle"] > 0 and c["decisive"] + c["near_tie_same"] + c["near_tie_moved"] == c["oracle"] + c["gpu"]
 
 
 def test_bf16_resnet34_tensor_core_layers(capsys):

@@ -47,8 +47,8 @@ def compare(stat_gpu, stat_ref, trig_gpu, trig_ref, half: int, tol: float) -> di
     err = np.abs(sg - so) / (1 + np.abs(so))
     assert err.size == 0 or err.max() <= tol, f"statistic differs by {err.max():.3g} > {tol}"
     set_g, set_o = set(tg.tolist()), set(to.tolist())
-    counts = dict(oracle=len(to), gpu=len(tg), decisive=0, near_tie=0, near_tie_same=0, near_tie_moved=0,
-                  near_ties=[])
+    counts = dict(oracle=len(to), gpu=len(tg), identical=bool(np.array_equal(tg, to)), decisive=0, near_tie=0,
+                  near_tie_same=0, near_tie_moved=0, near_ties=[])
     for side, trig, stat, other, other_stat, other_list in (("oracle", to, so, set_g, sg, tg),
                                                             ("gpu", tg, sg, set_o, so, to)):
         for j, m in zip(trig.tolist(), margins(stat, trig, half)):
@@ -75,7 +75,8 @@ def compare(stat_gpu, stat_ref, trig_gpu, trig_ref, half: int, tol: float) -> di
 
 
 def summary(c: dict) -> str:
-    return (f"triggers oracle {c['oracle']} gpu {c['gpu']}: {c['decisive']} decisive (exact), "
+    return (f"triggers oracle {c['oracle']} gpu {c['gpu']} (identical lists: {c['identical']}): "
+            f"{c['decisive']} decisive (exact), "
             f"{c['near_tie']} near-ties ({c['near_tie_same']} same index, {c['near_tie_moved']} resolved "
             f"to a tied point: (side, index, tied point, distance to the other list's nearest trigger, "
             f"margin) {c['near_ties']})")
