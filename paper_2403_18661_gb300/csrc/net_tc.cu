@@ -876,24 +876,33 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
 // k_tiny_pipe: the fused 16-channel network with its layers pipelined inside a
 // window (one window per CTA pass, persistent over windows).
 //
-// Warp roles (416 threads):
+// Warp roles (448 threads):
 //   warps 0..11  epilogue: build the stem's im2col tile, then per layer a
 //                statistics pass and a normalise pass over the TMEM accumulators;
-//                quad q = warp / 4 owns the 128-position subtiles j = q, q + 3, ..
-//                (each warp its TMEM lane quarter warp % 4)
-//   warp 12      MMA issue (one elected lane, the warp uniform)
+//                quad q = warp / 4 owns the units u = q, q + 3, .. (a unit is two
+//                128-position subtiles, 2u and 2u + 1; each warp reads its TMEM
+//                lane quarter warp % 4)
+//   warps 12, 13 MMA issue, warp 12 + m for the units u = m, m + 2, .. (one elected
+//                lane issues, the warp uniform; two issuing warps because the issue
+//                latency of these small MMAs, not the tensor core, bounds one warp)
 // Every layer, stem included, is an implicit GEMM with M = 128 positions, N = 16
 // channels, accumulators for the whole window in TMEM (W / 128 subtiles x 16
-// columns).  Per subtile j two mbarriers link the roles:
-//   rows_ready[j]  the input rows of subtile j of the next layer are in shared
-//                  memory (128 epilogue arrivals): its im2col rows for the stem,
+// columns).  Per unit u two mbarriers link the roles:
+//   rows_ready[u]  the input rows of unit u of the next layer are in shared
+//                  memory (one arrival per warp of the owning quad, after the
+//                  warp's writes and proxy fences): its im2col rows for the stem,
 //                  else the previous layer's normalised output; the tensor core
-//                  also reads the first row of subtile j + 1 (the k = 3 halo), so
-//                  the MMAs of subtile j wait for rows_ready[j] and [j + 1].
-//                  The arrival also releases subtile j's accumulator columns,
+//                  also reads the first row of unit u + 1 (the k = 3 halo), so
+//                  the MMAs of unit u need rows_ready[u] and [u + 1].
+//                  The arrival also releases unit u's accumulator columns,
 //                  which the layer's MMAs overwrite (their old values were read
 //                  by the normalise pass that produced these rows).
-//   mma_done[j]    the MMAs of subtile j of the current layer have completed.
+//   mma_done[u]    the MMAs of unit u of the current layer have completed.
+// Issue latency, not the tensor core, bounds an issue loop at this size (an M = 128,
+// N = 16, K = 16 MMA issues in about 40 cycles when its operands are warp-uniform,
+// several times slower when they come from per-lane registers; a wait on a barrier,
+// even a completed one, costs about 235): an MMA warp polls every unit's barrier at
+// once (lane i tests unit i, then a ballot) and issues its units that are ready.
 // So the MMAs of layer k + 1 run while the normalise pass of layer k is still
 // writing later subtiles, and the statistics pass of layer k + 1 reads each
 // subtile as soon as its MMAs are done; only GroupNorm's block-wide reduction
@@ -911,13 +920,15 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
 // 0 and W + 1 zero), the BF16 weight images (convs, then the stem), the FP32
 // parameters, reduction scratch and barriers, then the batch segment table.
 // ============================================================================
-constexpr int TP_EPI_WARPS = 12;           // 3 quads: with the MMA warp 13 warps, 128 registers each
-constexpr int TP_NQ = TP_EPI_WARPS / 4;      // quads of epilogue warps
+constexpr int TP_EPI_WARPS = 12;           // 3 quads of epilogue warps
+constexpr int TP_NQ = TP_EPI_WARPS / 4;
+constexpr int TP_MMA_WARPS = 2;             // issue warps (even and odd units): 14 warps, 144 registers each
 constexpr int TP_EPI = TP_EPI_WARPS * 32;
-constexpr int TP_THREADS = TP_EPI + 32;
+constexpr int TP_THREADS = TP_EPI + 32 * TP_MMA_WARPS;
 constexpr int TP_MT_MAX = 32;
 constexpr int TP_STEM_IMG = 512;  // BF16 image of the stem weights: 16 channels x K = 16
 constexpr uint64_t TP_WAIT_NS = 1000000000ull;
+constexpr int TP_EPI_RED = TP_EPI_WARPS * 32 + 32;  // floats of one reduction scratch
 
 struct PipeSmem {
     size_t off_a, off_b, off_w, off_p, off_s, off_r, off_bar, total;
@@ -932,19 +943,23 @@ __host__ __device__ inline PipeSmem pipe_smem(int W, int n_conv, int k_stem) {
     s.off_p = s.off_w + (size_t)n_conv * TF_WIMG + TP_STEM_IMG;
     s.off_s = s.off_p + (((size_t)tiny_param_count(k_stem, n_conv) * 4 + 15) / 16) * 16;
     s.off_r = s.off_s + 2 * TF_C * 4;
-    s.off_bar = s.off_r + (size_t)(TP_EPI_WARPS * 32 + 32) * 4;
-    // mma_done[TP_MT_MAX], rows_ready[TP_MT_MAX], drain, then tmem slot, abort flag, stop flag
+    // reduction scratch: two halves (layer parity) of [TP_EPI_WARPS][32] floats + a stop flag, then the head's
+    s.off_bar = s.off_r + (size_t)(3 * TP_EPI_RED) * 4;
+    // mma_done[TP_MT_MAX], rows_ready[TP_MT_MAX] (per unit; the first MT / 2 used), drain, then the
+    // tmem slot, abort flag, stop flag
     s.total = s.off_bar + (2 * TP_MT_MAX + 1) * 8 + 16;
     return s;
 }
 
-// GroupNorm reduction over the epilogue warps (named barrier 1): per-thread group
-// sums (x: sum, y: sum of squares) -> per-channel affine map, plus a consistent copy
-// of the abort flag for every epilogue thread (stop).
+// GroupNorm reduction over the epilogue warps, one named barrier (id 1): per-thread group sums
+// (x: sum, y: sum of squares) -> every warp's lanes hold the per-channel affine map
+// (sc[c] = rstd_g gamma_c, sh[c] = beta_c - mean_g sc[c]) and a consistent copy of the abort
+// flag (stop).  red is this layer's half of a double buffer: a warp that runs ahead writes the
+// next layer's sums into the other half, and cannot get two layers ahead past the barrier.
 template <int G>
 __device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, float eps, const float *gamma,
-                                              const float *beta, float *red, float *scale, float *shift,
-                                              const volatile int *abort_flag, int *stop) {
+                                              const float *beta, float *red, float (&sc)[TF_C], float (&sh)[TF_C],
+                                              const volatile int *abort_flag, bool &stop) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NV = 2 * G;
     float v[NV];
@@ -955,22 +970,26 @@ __device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, 
     }
     warp_reduce_scatter<NV>(v, lane);
     if ((lane & (32 / NV - 1)) == 0) red[warp * 32 + lane / (32 / NV)] = v[0];
+    int *stop_slot = reinterpret_cast<int *>(red + TP_EPI_WARPS * 32);
+    if (threadIdx.x == 0) *stop_slot = *abort_flag;
     tc::named_bar_sync(1, TP_EPI);
-    if (threadIdx.x < TF_C) {
-        const int c = threadIdx.x, g = c / (TF_C / G);
-        float ts = 0.f, tq = 0.f;
-        for (int w = 0; w < TP_EPI_WARPS; ++w) {
-            ts += red[w * 32 + g];
-            tq += red[w * 32 + G + g];
-        }
-        const float mean = ts / cnt;
-        const float var = fmaxf(tq / cnt - mean * mean, 0.f);
-        const float a = rsqrtf(var + eps) * gamma[c];
-        scale[c] = a;
-        shift[c] = beta[c] - mean * a;
+    // lane i < 2G: total i over the warps (sums, then sums of squares); lane c (mod 16) then forms
+    // channel c's affine map, and the 16 maps are broadcast to every lane
+    float t = 0.f;
+    if (lane < NV)
+#pragma unroll
+        for (int w = 0; w < TP_EPI_WARPS; ++w) t += red[w * 32 + lane];
+    const int c = lane & (TF_C - 1), g = c / (TF_C / G);
+    const float s_g = __shfl_sync(0xffffffffu, t, g), q_g = __shfl_sync(0xffffffffu, t, G + g);
+    const float mean = s_g / cnt;
+    const float a = rsqrtf(fmaxf(q_g / cnt - mean * mean, 0.f) + eps) * gamma[c];
+    const float b = beta[c] - mean * a;
+#pragma unroll
+    for (int i = 0; i < TF_C; ++i) {
+        sc[i] = __shfl_sync(0xffffffffu, a, i);
+        sh[i] = __shfl_sync(0xffffffffu, b, i);
     }
-    if (threadIdx.x == 0) *stop = *abort_flag;
-    tc::named_bar_sync(1, TP_EPI);
+    stop = *stop_slot != 0;
 }
 
 // Window output: the logit (and, in list mode, the statistics of the launch once its last
@@ -1029,15 +1048,12 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
     unsigned char *actB = sm + L.off_b;
     unsigned char *wimg = sm + L.off_w;
     float *prm = reinterpret_cast<float *>(sm + L.off_p);
-    float *scale = reinterpret_cast<float *>(sm + L.off_s);
-    float *shift = scale + TF_C;
     float *red = reinterpret_cast<float *>(sm + L.off_r);
     uint64_t *mma_done = reinterpret_cast<uint64_t *>(sm + L.off_bar);
     uint64_t *rows_ready = mma_done + TP_MT_MAX;
     uint64_t *drain = rows_ready + TP_MT_MAX;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    int *stop = reinterpret_cast<int *>(tmem_slot + 2);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t act_chunk = (size_t)(W + 2) * 16;
 
@@ -1062,12 +1078,11 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
     if (tid == 0) {
         for (int j = 0; j < TP_MT_MAX; ++j) {
             tc::mbar_init(&mma_done[j], 1);
-            tc::mbar_init(&rows_ready[j], 128);
+            tc::mbar_init(&rows_ready[j], 4);
         }
-        tc::mbar_init(drain, 1);
+        tc::mbar_init(drain, TP_MMA_WARPS);
         tc::fence_mbar_init();
         *abort_flag = 0;
-        *stop = 0;
     }
     if (warp == TP_EPI_WARPS) {
         tc::tmem_alloc(tmem_slot, 512);
@@ -1082,44 +1097,73 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
     const int64_t win0 = blockIdx.x, win_step = gridDim.x;
     pdl_wait();  // list mode: the whitened rings come from the whitening launch before
 
-    if (warp == TP_EPI_WARPS) {
-        // ================================================================ MMA warp
+    if (warp >= TP_EPI_WARPS) {
+        // ================================================================ MMA warps
+        const int mw = warp - TP_EPI_WARPS;  // this warp issues the units u = mw, mw + TP_MMA_WARPS, ..
         const uint32_t idesc = tc::idesc_bf16_f32(128, TF_C);
         const uint64_t d_stem_a = tc::desc_kmajor_noswizzle(tc::smem_addr(actB + act_chunk + 16), 16, 128);
         const uint64_t d_stem_b = tc::desc_kmajor_noswizzle(tc::smem_addr(wimg + (size_t)n_conv * TF_WIMG), 256, 128);
         const uint64_t d_a = tc::desc_kmajor_noswizzle(tc::smem_addr(actA), (uint32_t)act_chunk, 128);
         const uint64_t d_b = tc::desc_kmajor_noswizzle(tc::smem_addr(actB), (uint32_t)act_chunk, 128);
         const uint64_t d_w = tc::desc_kmajor_noswizzle(tc::smem_addr(wimg), 256, 128);
+        const int NU = (MT + 1) / 2;  // units of two subtiles
+        // The issue loops have warp-uniform trip counts and no early exit, so their counters, and the
+        // descriptors derived from them, stay warp-uniform.  After a failed wait `ok` turns false and the
+        // remaining waits are skipped (the MMAs still issue: they only read shared memory and write
+        // accumulators that nothing reads any more).
         uint32_t seq = 0;
         bool ok = true;
-        for (int64_t win = win0; win < args.n_win && ok; win += win_step) {
-            for (int k = 0; k <= n_conv && ok; ++k, ++seq) {
-                const uint32_t par = seq & 1;
-                const int l = k - 1;
-                const uint64_t ad = (l & 1) ? d_b : d_a;  // the second conv of a block reads B
-                const uint64_t bd = d_w + (uint64_t)((k > 0 ? l : 0) * (TF_WIMG / 16));
-                for (int j = 0; j < MT; ++j) {
-                    bool w_ok = tc::mbar_wait(&rows_ready[j], par, TP_WAIT_NS);
-                    if (w_ok && k > 0 && j + 1 < MT) w_ok = tc::mbar_wait(&rows_ready[j + 1], par, TP_WAIT_NS);
-                    // one decision for the whole warp (the issue below is by an elected lane of a converged warp)
-                    if (!__all_sync(0xffffffffu, w_ok && !*abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    const uint32_t dt = tmem + (uint32_t)(j * TF_C);
-                    if (k == 0) {
-                        tc::mma_bf16_elect(dt, d_stem_a + (uint64_t)(128 * j), d_stem_b, idesc, 0u);
-                    } else {
-                        const uint64_t a0 = ad + (uint64_t)(128 * j);
-                        tc::mma_bf16_elect(dt, a0, bd, idesc, 0u);
-                        tc::mma_bf16_elect(dt, a0 + 1, bd + 32, idesc, 1u);
-                        tc::mma_bf16_elect(dt, a0 + 2, bd + 64, idesc, 1u);
-                    }
-                    tc::mma_commit_elect(&mma_done[j]);
+        // wait until the leading `need` units have their rows: one poll tests every unit (lane i unit i)
+        auto wait_rows = [&](int &ready, int need, uint32_t par) {
+            while (ready < need) {
+                const bool rdy = lane >= NU || tc::mbar_test_wait(&rows_ready[lane], par);
+                const unsigned m = __ballot_sync(0xffffffffu, rdy);
+                ready = m == 0xffffffffu ? 32 : __ffs(~m) - 1;
+                if (ready < need && !tc::mbar_wait_warp(&rows_ready[ready], par, TP_WAIT_NS, 0u)) {
+                    ok = false;
+                    ready = NU;
                 }
-                __syncwarp();
             }
+            tc::fence_after_sync();
+        };
+        for (int64_t win = win0; win < args.n_win; win += win_step) {
+            {   // stem: one K = 16 MMA per subtile over the im2col tile
+                const uint32_t par = seq & 1;
+                int ready = ok ? 0 : NU;
+                for (int u = mw; u < NU; u += TP_MMA_WARPS) {
+                    wait_rows(ready, u + 1, par);
+                    const int j0 = 2 * u;
+                    tc::mma_bf16_elect(tmem + (uint32_t)(j0 * TF_C), d_stem_a + (uint64_t)(128 * j0), d_stem_b, idesc, 0u);
+                    if (j0 + 1 < MT)
+                        tc::mma_bf16_elect(tmem + (uint32_t)((j0 + 1) * TF_C), d_stem_a + (uint64_t)(128 * (j0 + 1)),
+                                           d_stem_b, idesc, 0u);
+                    tc::mma_commit_elect(&mma_done[u]);
+                }
+                ++seq;
+            }
+            for (int l = 0; l < n_conv; ++l, ++seq) {  // convs: three taps, a conv also reads the next unit's first row
+                const uint32_t par = seq & 1;
+                const uint64_t ad = (l & 1) ? d_b : d_a;  // the second conv of a block reads B
+                const uint64_t bd = d_w + (uint64_t)(l * (TF_WIMG / 16));
+                int ready = ok ? 0 : NU;
+                for (int u = mw; u < NU; u += TP_MMA_WARPS) {
+                    wait_rows(ready, min(u + 2, NU), par);
+                    const int j0 = 2 * u;
+                    const uint64_t a0 = ad + (uint64_t)(128 * j0);
+                    const uint32_t t0 = tmem + (uint32_t)(j0 * TF_C);
+                    tc::mma_bf16_elect(t0, a0, bd, idesc, 0u);
+                    tc::mma_bf16_elect(t0, a0 + 1, bd + 32, idesc, 1u);
+                    tc::mma_bf16_elect(t0, a0 + 2, bd + 64, idesc, 1u);
+                    if (j0 + 1 < MT) {
+                        tc::mma_bf16_elect(t0 + TF_C, a0 + 128, bd, idesc, 0u);
+                        tc::mma_bf16_elect(t0 + TF_C, a0 + 129, bd + 32, idesc, 1u);
+                        tc::mma_bf16_elect(t0 + TF_C, a0 + 130, bd + 64, idesc, 1u);
+                    }
+                    tc::mma_commit_elect(&mma_done[u]);
+                }
+            }
+            if (*abort_flag) ok = false;  // the epilogue gave up: skip the waits from now on
+            ok = __all_sync(0xffffffffu, ok);
         }
         if (!ok) {
             if (lane == 0) atomicExch(args.err, 1);
@@ -1149,16 +1193,19 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
             float *out_ptr = cur.out_ptr;
             asm volatile("cp.async.wait_all;" ::: "memory");
             tc::named_bar_sync(1, TP_EPI);
-            // ---- stem im2col rows of this quad's subtiles (BF16, six taps per 16-byte row)
-            for (int j = q; j < MT; j += TP_NQ) {
-                const int t = 128 * j + 32 * lq + lane;
-                const float *p0 = xs + 4 + t - 1, *p1 = xs + RP + 4 + t - 1;
-                const uint4 row = make_uint4(tc::pack_bf16x2(p0[0], p0[1]), tc::pack_bf16x2(p0[2], p1[0]),
-                                             tc::pack_bf16x2(p1[1], p1[2]), 0u);
-                *reinterpret_cast<uint4 *>(im2col + (size_t)t * 16) = row;
+            // ---- stem im2col rows of this quad's units (BF16, six taps per 16-byte row)
+            for (int u = q; 2 * u < MT; u += TP_NQ) {
+                for (int j = 2 * u; j < min(2 * u + 2, MT); ++j) {
+                    const int t = 128 * j + 32 * lq + lane;
+                    const float *p0 = xs + 4 + t - 1, *p1 = xs + RP + 4 + t - 1;
+                    const uint4 row = make_uint4(tc::pack_bf16x2(p0[0], p0[1]), tc::pack_bf16x2(p0[2], p1[0]),
+                                                 tc::pack_bf16x2(p1[1], p1[2]), 0u);
+                    *reinterpret_cast<uint4 *>(im2col + (size_t)t * 16) = row;
+                }
                 tc::fence_proxy_async_smem();
-                tc::fence_before_sync();  // (this subtile's accumulators were read by the last layer)
-                tc::mbar_arrive(&rows_ready[j]);
+                tc::fence_before_sync();  // (this unit's accumulators were read by the last layer)
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&rows_ready[u]);
             }
             float hs[TF_C];
 #pragma unroll
@@ -1176,17 +1223,17 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
 #pragma unroll
                 for (int g = 0; g < G; ++g) sq[g] = make_float2(0.f, 0.f);
                 bool ok = true;
-                for (int j0 = q; j0 < MT; j0 += 2 * TP_NQ) {
-                    const int j1 = j0 + TP_NQ;
+                for (int u = q; 2 * u < MT; u += TP_NQ) {
+                    const int j0 = 2 * u, j1 = j0 + 1;
                     uint32_t r0[16], r1[16];
                     // (after a failed wait the rest are skipped: the MMA warp has stopped)
-                    if (*abort_flag || !tc::mbar_wait(&mma_done[j0], par, TP_WAIT_NS)) ok = false;
-                    if (j1 < MT && (*abort_flag || !tc::mbar_wait(&mma_done[j1], par, TP_WAIT_NS))) ok = false;
-                    __syncwarp();
+                    if (ok) ok = tc::mbar_wait_warp(&mma_done[u], par, TP_WAIT_NS);
                     tc::fence_after_sync();
                     tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
                     if (j1 < MT) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
                     tc::tmem_wait_ld();
+                    tc::tmem_regs_ready(r0);
+                    tc::tmem_regs_ready(r1);
 #pragma unroll
                     for (int c = 0; c < TF_C; ++c) {
                         const float v = __uint_as_float(r0[c]);
@@ -1205,8 +1252,11 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                     atomicExch(args.err, 1);
                     *abort_flag = 1;
                 }
-                gn_reduce_epi<G>(sq, cnt, args.eps, gam, gam + TF_C, red, scale, shift, abort_flag, stop);
-                if (*stop) {
+                float sc[TF_C], sh[TF_C];
+                bool stop_now = false;
+                gn_reduce_epi<G>(sq, cnt, args.eps, gam, gam + TF_C, red + (seq & 1) * TP_EPI_RED, sc, sh, abort_flag,
+                                 stop_now);
+                if (stop_now) {
                     stopped = true;
                     break;
                 }
@@ -1217,24 +1267,20 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                     load_window(args, cur, xs, W, 1, true, TP_EPI);
                 }
                 // ---- normalise pass (+ residual) + ReLU -> BF16 rows of dst, or the pooled sums
-                float sc[TF_C], sh[TF_C];
-#pragma unroll
-                for (int c = 0; c < TF_C; ++c) {
-                    sc[c] = scale[c];
-                    sh[c] = shift[c];
-                }
-                for (int j0 = q; j0 < MT; j0 += 2 * TP_NQ) {
-                    const int j1 = j0 + TP_NQ;
+                for (int u = q; 2 * u < MT; u += TP_NQ) {
+                    const int j0 = 2 * u, j1 = j0 + 1;
                     const bool two = j1 < MT;
-                    uint32_t r0[16], r1[16];
-                    tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
-                    if (two) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
+                    uint32_t ra[16], rb[16];
+                    tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), ra);
+                    if (two) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), rb);
                     tc::tmem_wait_ld();
+                    tc::tmem_regs_ready(ra);
+                    tc::tmem_regs_ready(rb);
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         if (half == 1 && !two) break;
                         const int j = half ? j1 : j0;
-                        const uint32_t *rr = half ? r1 : r0;
+                        const uint32_t *rr = half ? rb : ra;
                         const size_t row = (size_t)(128 * j + 32 * lq + lane + 1) * 16;
 #pragma unroll
                         for (int ch = 0; ch < 2; ++ch) {
@@ -1247,8 +1293,8 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                                                   make_float2(sh[ch * 8 + 2 * e], sh[ch * 8 + 2 * e + 1]));
                             if (last) {
                                 // the block's residual in FP32, ReLU, pooled sums (nothing stored)
-                                const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + row);
-                                const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+                                const uint4 rv = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + row);
+                                const uint32_t w4[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
                                     const float2 y = __fadd2_rn(v[e], make_float2(__uint_as_float(w4[e] << 16),
@@ -1258,8 +1304,8 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                                 }
                             } else if (res) {
                                 // + the block's residual in FP32, ReLU folded into the BF16 conversion
-                                const uint4 u = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + row);
-                                const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+                                const uint4 rv = *reinterpret_cast<const uint4 *>(actA + ch * act_chunk + row);
+                                const uint32_t w4[4] = {rv.x, rv.y, rv.z, rv.w};
                                 uint32_t pk[4];
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
@@ -1274,24 +1320,26 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                                                tc::pack_bf16x2_relu(v[2].x, v[2].y), tc::pack_bf16x2_relu(v[3].x, v[3].y));
                             }
                         }
-                        if (!last) {
-                            tc::fence_proxy_async_smem();
-                            tc::fence_before_sync();
-                            tc::mbar_arrive(&rows_ready[j]);
-                        }
+                    }
+                    if (!last) {
+                        tc::fence_proxy_async_smem();
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&rows_ready[u]);
                     }
                 }
                 if (last) tc::fence_before_sync();
             }
             if (stopped) break;
             // ---- head: global mean pool, then the linear layer
+            float *hred = red + 2 * TP_EPI_RED;
             warp_reduce_scatter<TF_C>(hs, lane);  // lane 2c holds the warp's sum of channel c
-            if (!(lane & 1)) red[warp * 32 + (lane >> 1)] = hs[0];
+            if (!(lane & 1)) hred[warp * 32 + (lane >> 1)] = hs[0];
             tc::named_bar_sync(1, TP_EPI);
             if (warp == 0) {
                 float part = 0.f;
                 if (lane < TF_C) {
-                    for (int w = 0; w < TP_EPI_WARPS; ++w) part += red[w * 32 + lane];
+                    for (int w = 0; w < TP_EPI_WARPS; ++w) part += hred[w * 32 + lane];
                     part = fc_w[lane] * (part / (float)W);
                 }
 #pragma unroll

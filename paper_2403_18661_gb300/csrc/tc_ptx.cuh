@@ -50,6 +50,51 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     }
 }
 
+// non-blocking test of the phase (never suspends the thread)
+__device__ __forceinline__ uint32_t mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+// try_wait that may suspend the thread for up to hint_ns while the phase is incomplete (it
+// resumes when the phase completes), so that a waiting warp does not compete for issue slots
+__device__ __forceinline__ uint32_t mbar_try_wait_suspend(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok;
+}
+
+// A warp waits for the phase: lane 0 polls, suspending for at most hint_ns between polls (0: a
+// spin on the non-blocking test, for latency-critical waits), the other lanes wait at the warp
+// barrier; the result (false: gave up after timeout_ns) is the same in every lane and the warp is
+// converged afterwards.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, uint64_t timeout_ns,
+                                               uint32_t hint_ns = 200u) {
+    uint32_t ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        auto poll = [&]() { return hint_ns ? mbar_try_wait_suspend(bar, parity, hint_ns) : mbar_test_wait(bar, parity); };
+        if (!poll()) {
+            const uint64_t t0 = globaltimer_ns();
+            while (!(ok = poll()))
+                if (globaltimer_ns() - t0 > timeout_ns) break;
+        }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
@@ -112,6 +157,29 @@ __device__ __forceinline__ void mma_bf16_elect(uint32_t d_tmem, uint64_t adesc, 
         : "memory");
 }
 
+// mma_bf16_elect issued only if `live` (a warp-uniform value): the skip is a predicate, not a
+// branch, so the surrounding loop stays uniform
+__device__ __forceinline__ void mma_bf16_elect_if(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                  uint32_t accumulate, uint32_t live) {
+    asm volatile(
+        "{\n\t.reg .pred P, Q, R;\n\t"
+        "elect.sync _|P, 0xffffffff;\n\t"
+        "setp.ne.b32 Q, %4, 0;\n\t"
+        "setp.ne.and.b32 R, %5, 0, P;\n\t"
+        "@R tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, Q;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(live)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_elect_if(uint64_t *bar, uint32_t live) {
+    asm volatile(
+        "{\n\t.reg .pred P, R;\n\telect.sync _|P, 0xffffffff;\n\t"
+        "setp.ne.and.b32 R, %1, 0, P;\n\t"
+        "@R tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+            smem_addr(bar)), "r"(live)
+        : "memory");
+}
+
 // commit from the elected lane of a uniform warp (the lane that issued with mma_bf16_elect)
 __device__ __forceinline__ void mma_commit_elect(uint64_t *bar) {
     asm volatile(
@@ -153,6 +221,16 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Mark 16 registers filled by earlier *_nowait loads as (re)defined here, so that the compiler
+// cannot move their uses above the wait that precedes this call.
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[16]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
 
 // 16 lanes x 8 columns per repetition (the MMA accumulator fragment): thread t receives
 // (lane t/4, columns 2(t%4) and 2(t%4)+1) and (lane 8 + t/4, the same columns) of each

@@ -113,3 +113,40 @@ def test_batch_rejects_short_segments(batch_case):
         ctx.batch_layout([(0, 60 * 2048)], N_SHIFT, SHIFT_STEP)  # shorter than the 64 s look-back
     assert e.value.status == -1
     ctx.close()
+
+
+def test_batch_shift_ranges_concatenate(batch_case):
+    """A background split into timeslide ranges (shift_first, as the ranks of a multi-GPU job take
+    them) gives, series by series, exactly the logits, statistics and triggers of the whole batch."""
+    wl, x, segs, w, ref = batch_case
+    ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
+    xd = torch.from_numpy(x).cuda()
+    n_win, _, _ = ctx.batch_layout(segs, N_SHIFT, SHIFT_STEP)
+    full = [t.cpu().numpy() for t in ctx.batch_run(xd, segs, N_SHIFT, SHIFT_STEP)]
+    parts = [(1, 1), (2, N_SHIFT - 1)]
+    got = {}
+    for k_first, n_k in parts:
+        lg, st, tr, nt = [t.cpu().numpy() for t in ctx.batch_run(xd, segs, n_k, SHIFT_STEP, shift_first=k_first)]
+        tr = tr[: int(nt[0])]
+        lo = so = 0
+        for i, nw in enumerate(n_win):
+            for k in range(k_first, k_first + n_k):
+                ns = nw - wl.n_int + 1
+                got[(i, k)] = (lg[lo:lo + nw], st[so:so + ns], tr[(tr >= so) & (tr < so + ns)] - so)
+                lo += nw
+                so += ns
+    ctx.sync()
+    lg, st, tr, nt = full
+    tr = tr[: int(nt[0])]
+    lo = so = 0
+    for i, nw in enumerate(n_win):
+        for k in range(1, N_SHIFT + 1):
+            ns = nw - wl.n_int + 1
+            a_lg, a_st, a_tr = got[(i, k)]
+            assert np.array_equal(a_lg, lg[lo:lo + nw]) and np.array_equal(a_st, st[so:so + ns])
+            assert np.array_equal(a_tr, tr[(tr >= so) & (tr < so + ns)] - so)
+            lo += nw
+            so += ns
+    with pytest.raises(abi.AfgError):  # the largest timeslide must fit the shortest segment
+        ctx.batch_layout(segs, 1, SHIFT_STEP, shift_first=10 ** 6)
+    ctx.close()
