@@ -276,7 +276,6 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 int afg_fail(afg_ctx *ctx, int code, const char *fmt, ...);
 int afg_cuda_fail(afg_ctx *ctx, cudaError_t e, const char *what);
 size_t filter_build_scratch_bytes(const afg_ctx *ctx, int64_t nf);
-cudaError_t fft16_tables_init();
 int afg_ws_reserve(afg_ctx *ctx, int slot, size_t bytes, void **out);
 void batch_cache_release(afg_ctx *ctx);
 void serve_release(afg_ctx *ctx);

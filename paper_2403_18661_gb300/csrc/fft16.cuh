@@ -96,42 +96,6 @@ template <int S> __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 }
 __device__ __forceinline__ int out16(int q) { return 4 * (q & 3) + (q >> 2); }
 
-// ---- twiddle tables (device memory of the including translation unit, the spectral kernels';
-// filled once per device by fft16_tables_init)
-// Radix-16 passes: row k of the pass at stride Ns holds exp(-2 pi i r k / (16 Ns)), r = 0..15
-// (16 float2 per row, so that a row is eight aligned 16-byte loads); the inverse uses the
-// conjugates.  Rows of Ns = 16, 256 (forward) and 2, 32, 512 (inverse) follow each other.
-// Mid passes: W^j = exp(-2 pi i j / NFFT), j = 0 .. NC.
-// Each value is sincospif of its own angle (no products of rounded twiddles).
-template <int Ns> __host__ __device__ constexpr int tw_row0() {
-    return Ns == 16 ? 0 : Ns == 256 ? 16 : Ns == 2 ? 272 : Ns == 32 ? 274 : 306;
-}
-constexpr int TW_ROWS = 306 + 512;
-static __device__ float2 g_tw16[TW_ROWS * 16];
-static __device__ float2 g_wnfft[NC + 1];
-// the periodic Hann window of the Welch segments, w_i = 1/2 - 1/2 cos(2 pi i / NFFT)
-static __device__ float g_hann[NFFT];
-
-// v[r] *= (table twiddle r of butterfly offset k at stride Ns), conjugated for S = +1
-template <int S, int Ns> __device__ __forceinline__ void twiddle16_tab(float2 (&v)[16], int k) {
-    const float4 *row = reinterpret_cast<const float4 *>(g_tw16 + (tw_row0<Ns>() + k) * 16);
-    float4 t[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) t[i] = __ldg(row + i);
-#pragma unroll
-    for (int r = 1; r < 16; ++r) {
-        const float4 q = t[r >> 1];
-        const float2 w = (r & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
-        v[r] = cmul(v[r], S < 0 ? w : conj(w));
-    }
-}
-
-// W^j (j <= NC) and its conjugate for the mid passes
-template <int S> __device__ __forceinline__ float2 wtab(int j) {
-    const float2 w = __ldg(g_wnfft + j);
-    return S < 0 ? w : conj(w);
-}
-
 // v[r] *= exp(S i pi x r), r = 1..15 (x = 2 k / (16 Ns) for butterfly offset k)
 template <int S> __device__ __forceinline__ void twiddle16(float2 (&v)[16], float x) {
     const float2 w1 = cis<S>(x), w4 = cis<S>(4.0f * x), w8 = cis<S>(8.0f * x);
@@ -156,7 +120,7 @@ template <int S> __device__ __forceinline__ void twiddle16(float2 (&v)[16], floa
 // Radix-16 butterfly of thread j at stride Ns on inputs already in v (read
 // from positions j + 512 r): twiddles, DFT; outputs stay in v (out16 order).
 template <int S, int Ns> __device__ __forceinline__ void butterfly16(float2 (&v)[16], int j) {
-    if (Ns > 1) twiddle16_tab<S, Ns>(v, j & (Ns - 1));
+    if (Ns > 1) twiddle16<S>(v, (float)(j & (Ns - 1)) / (float)(8 * Ns));
     dft16<S>(v);
 }
 

@@ -22,8 +22,6 @@
 //                     the inverse split and the inverse transform's first
 //                     pass are one fused shared-memory pass.
 #include <math.h>
-
-#include <mutex>
 #include <stdio.h>
 
 #include "afg_internal.cuh"
@@ -33,30 +31,6 @@
 namespace {
 
 constexpr int NT64 = 1024;  // threads of the FP64 filter kernel
-
-// the tables of fft16.cuh: radix-16 pass twiddles, W^j for the mid passes, the Hann window
-__global__ void k_fft16_tables() {
-    using namespace r16;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < TW_ROWS * 16) {
-        const int row = i / 16, r = i % 16;
-        int Ns, k;
-        if (row < tw_row0<256>()) Ns = 16, k = row;
-        else if (row < tw_row0<2>()) Ns = 256, k = row - tw_row0<256>();
-        else if (row < tw_row0<32>()) Ns = 2, k = row - tw_row0<2>();
-        else if (row < tw_row0<512>()) Ns = 32, k = row - tw_row0<32>();
-        else Ns = 512, k = row - tw_row0<512>();
-        float sn, cs;
-        sincospif((float)(r * k) / (float)(8 * Ns), &sn, &cs);  // exp(-2 pi i r k / (16 Ns))
-        g_tw16[i] = make_float2(cs, -sn);
-    }
-    if (i <= NC) {
-        float sn, cs;
-        sincospif((float)i / (float)NC, &sn, &cs);  // W^i = exp(-2 pi i i / NFFT)
-        g_wnfft[i] = make_float2(cs, -sn);
-    }
-    if (i < NFFT) g_hann[i] = 0.5f - 0.5f * cospif(2.0f * (float)i / (float)NFFT);
-}
 
 __global__ void k_twiddles(double2 *tw64) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,8 +48,8 @@ __global__ void k_twiddles(double2 *tw64) {
 __device__ __forceinline__ void welch_mid_task(const float2 *d, int j, double *P) {
     using namespace r16;
     const float2 a = d[pad(j)], b = d[pad(j + 4096)], c = d[pad(4096 - j)], e = d[pad(8192 - j)];
-    const float2 w = wtab<-1>(j);      // W^j
-    const float2 u = wtab<-1>(2 * j);  // radix-2 twiddle of butterfly j (W^{2j})
+    const float2 w = cis<-1>((float)j / 8192.0f);  // W^j
+    const float2 u = cis<-1>((float)j / 4096.0f);  // radix-2 twiddle of butterfly j
     const float2 u2 = make_float2(-u.x, u.y);      // of butterfly 4096 - j: -conj(u)
     const float2 ub = cmul(u, b), ue = cmul(u2, e);
     const float2 zj = cadd(a, ub), zj4 = csub(a, ub), zc = cadd(c, ue), zc4 = csub(c, ue);
@@ -106,9 +80,10 @@ __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restr
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const int i0 = 2 * (t + NT * r);
-        const float2 w = __ldg(reinterpret_cast<const float2 *>(g_hann + i0));
-        v[r] = make_float2(src[i0] * w.x, src[i0 + 1] * w.y);
+        const int i0 = 2 * (t + NT * r), i1 = i0 + 1;
+        const float w0 = 0.5f - 0.5f * cospif(2.0f * (float)i0 / (float)NFFT);
+        const float w1 = 0.5f - 0.5f * cospif(2.0f * (float)i1 / (float)NFFT);
+        v[r] = make_float2(src[i0] * w0, src[i1] * w1);
     }
     forward_r16(d, v);
     double *out = P + ((int64_t)det * n_seg + g) * NBIN;
@@ -142,35 +117,13 @@ __global__ void k_psd_mean(const double *__restrict__ P, int64_t n_seg, int seg_
     const double *src = P + (int64_t)det * n_seg * NBIN + k;
     double *dst = psd + (int64_t)det * n_psd * NBIN + k;
     const double onesided = (k == 0 || k == NFFT / 2) ? 1.0 : 2.0;
-    // the first epoch's K segments with four independent partial sums (four loads in flight)
-    const double *s0 = src + e0 * seg_step * NBIN;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int q = 0;
-    for (; q + 4 <= K; q += 4) {
-        a0 += s0[(int64_t)q * NBIN];
-        a1 += s0[(int64_t)(q + 1) * NBIN];
-        a2 += s0[(int64_t)(q + 2) * NBIN];
-        a3 += s0[(int64_t)(q + 3) * NBIN];
-    }
-    for (; q < K; ++q) a0 += s0[(int64_t)q * NBIN];
-    double acc = (a0 + a1) + (a2 + a3);
+    double acc = 0.0;
+    for (int q = 0; q < K; ++q) acc += src[(e0 * seg_step + q) * NBIN];
     dst[e0 * NBIN] = onesided * acc * scale;
-    const int64_t e_end = min(e0 + (int64_t)PSD_EPT, n_psd);
-    if (seg_step == 2) {
-        // epochs every two segments (the epoch workloads): two segments enter and two leave the
-        // sum per epoch; unrolled so that the loads of several epochs are in flight together
-#pragma unroll 4
-        for (int64_t e = e0 + 1; e < e_end; ++e) {
-            const double *o = src + (e - 1) * 2 * NBIN, *n = o + (int64_t)K * NBIN;
-            acc += (n[0] + n[NBIN]) - (o[0] + o[NBIN]);
-            dst[e * NBIN] = onesided * acc * scale;
-        }
-    } else {
-        for (int64_t e = e0 + 1; e < e_end; ++e) {
-            const int64_t s_old = (e - 1) * seg_step, s_new = s_old + K;
-            for (int qq = 0; qq < seg_step; ++qq) acc += src[(s_new + qq) * NBIN] - src[(s_old + qq) * NBIN];
-            dst[e * NBIN] = onesided * acc * scale;
-        }
+    for (int64_t e = e0 + 1; e < e0 + PSD_EPT && e < n_psd; ++e) {
+        const int64_t s_old = (e - 1) * seg_step, s_new = s_old + K;
+        for (int q = 0; q < seg_step; ++q) acc += src[(s_new + q) * NBIN] - src[(s_old + q) * NBIN];
+        dst[e * NBIN] = onesided * acc * scale;
     }
 }
 
@@ -378,8 +331,8 @@ __device__ __forceinline__ void whiten_mid_task(const float2 *d, const float *g,
     using namespace r16;
     constexpr int H = NCX / 2;
     const float2 a = d[pad(j)], b = d[pad(j + H)], c = d[pad(H - j)], e = d[pad(NCX - j)];
-    const float2 w = wtab<-1>(j * (NC / NCX));      // W^j, W = exp(-2 pi i / 2 NCX)
-    const float2 u = wtab<-1>(2 * j * (NC / NCX));  // radix-2 twiddle of butterfly j
+    const float2 w = cis<-1>((float)j / (float)NCX);        // W^j, W = exp(-2 pi i / 2 NCX)
+    const float2 u = cis<-1>((float)j / (float)(NCX / 2));  // radix-2 twiddle of butterfly j
     const float2 u2 = make_float2(-u.x, u.y);               // of butterfly H - j
     const float2 ub = cmul(u, b), ue = cmul(u2, e);
     const float2 zj = cadd(a, ub), zj4 = csub(a, ub), zc = cadd(c, ue), zc4 = csub(c, ue);
@@ -686,7 +639,6 @@ int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, floa
 }
 
 int afg_make_twiddles(afg_ctx *ctx) {
-    AFG_CUDA(ctx, fft16_tables_init());
     {
         KScope ks(ctx, 0, KK_TWIDDLES, 0.0, (double)NFFT * sizeof(double2));
         k_twiddles<<<NFFT / 256, 256>>>(ctx->tw64);
@@ -789,28 +741,7 @@ cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, i
     return cudaGetLastError();
 }
 
-// Fill the FP32 transform tables of fft16.cuh on the current device, once per device (a
-// synchronous kernel; callers run it at set-up, outside any stream capture).
-cudaError_t fft16_tables_init() {
-    static std::mutex mu;
-    static bool ready[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (ready[dev]) return cudaSuccess;
-    k_fft16_tables<<<NFFT / 256, 256>>>();
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) ready[dev] = true;
-    return e;
-}
-
-// Opt the periodogram kernel into its 68 KiB of dynamic shared memory on the current device and
-// fill the transform tables.
+// Opt the periodogram kernel into its 68 KiB of dynamic shared memory on the current device.
 cudaError_t prepare_psd_kernels() {
-    cudaError_t e = fft16_tables_init();
-    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize, WELCH_SMEM);
 }
