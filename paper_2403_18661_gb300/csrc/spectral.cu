@@ -5,8 +5,9 @@
 // Kernels
 //   k_twiddles        exp(-2 pi i k / NFFT) table in double (filter build)
 //   k_periodogram     one Hann-windowed segment per CTA: FP32 real FFT in
-//                     shared memory (radix-16 passes, fft16.cuh), |X_k|^2
-//                     formed and stored in FP64
+//                     shared memory (radix-16 passes, fft16.cuh), the window
+//                     applied to the spectrum (a three-bin convolution),
+//                     |X_k|^2 formed and stored in FP64
 //   k_psd_mean        FP64 mean over the K segments of each epoch (a sliding
 //                     sum over a run of epochs per thread), density scaling
 //                     and one-sided doubling
@@ -43,9 +44,11 @@ __global__ void k_twiddles(double2 *tw64) {
 // Forward radix-2 pass (Ns = 4096) and real-FFT split for task j of the
 // Welch kernel, 1 <= j <= 2048: the butterflies j and 4096 - j give Z at
 // j, j + 4096, 4096 - j and 8192 - j, i.e. the split pairs (j, NC - j) and
-// (j + 4096, 4096 - j); |X_k|^2 of those four bins goes to P in FP64.
-// (At j = 2048 the two butterflies coincide and only the first pair is kept.)
-__device__ __forceinline__ void welch_mid_task(const float2 *d, int j, double *P) {
+// (j + 4096, 4096 - j).  The four spectrum values U at bins j, 8192 - j, j + 4096
+// and 4096 - j replace the four Z values they came from (the same slots: tasks
+// touch disjoint slot sets).  (At j = 2048 the two butterflies coincide and only
+// the first pair is written.)
+__device__ __forceinline__ void welch_mid_task(float2 *d, int j) {
     using namespace r16;
     const float2 a = d[pad(j)], b = d[pad(j + 4096)], c = d[pad(4096 - j)], e = d[pad(8192 - j)];
     const float2 w = cis<-1>((float)j / 8192.0f);  // W^j
@@ -56,54 +59,73 @@ __device__ __forceinline__ void welch_mid_task(const float2 *d, int j, double *P
     float2 x1, x1n, x2, x2n;
     split_fwd(zj, zc4, w, x1, x1n);             // bins j, 8192 - j
     split_fwd(zj4, zc, mul_i<-1>(w), x2, x2n);  // bins j + 4096, 4096 - j (W^{j+4096} = -i W^j)
-    auto p2 = [](float2 x) { return (double)x.x * (double)x.x + (double)x.y * (double)x.y; };
-    P[j] = p2(x1);
-    P[8192 - j] = p2(x1n);
+    d[pad(j)] = x1;
+    d[pad(8192 - j)] = x1n;
     if (j < 2048) {
-        P[j + 4096] = p2(x2);
-        P[4096 - j] = p2(x2n);
+        d[pad(j + 4096)] = x2;
+        d[pad(4096 - j)] = x2n;
     }
 }
 
-// grid (n_seg, n_det), r16::NT threads; segment g of detector d covers x[d][g*hop, g*hop + NFFT)
+// grid (n_seg, n_det), r16::NT threads; segment g of detector d covers x[d][g*hop, g*hop + NFFT).
+// The periodic Hann window is applied in the frequency domain: its DFT has three non-zero bins,
+// so the windowed spectrum is X_k = U_k / 2 - (U_{k-1} + U_{k+1}) / 4 with U the spectrum of the
+// unwindowed segment (U_{-1} = conj U_1, U_{NC+1} = conj U_{NC-1} for a real segment).
 __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restrict__ x, int64_t x_stride, int hop,
                                                              double *__restrict__ P, int64_t n_seg) {
     using namespace r16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *d = reinterpret_cast<float2 *>(smem_raw);
+    float2 *u_nyq = d + SLOTS;  // U_NC (real)
     const int64_t g = blockIdx.x;
     const int det = blockIdx.y;
     const int t = threadIdx.x;
     const float *src = x + det * x_stride + g * (int64_t)hop;
-    // z_n = w_2n x_2n + i w_2n+1 x_2n+1 with the periodic Hann window
-    // w_i = 1/2 - 1/2 cos(2 pi i / NFFT), n = t + 512 r (the first pass's inputs)
+    // z_n = x_2n + i x_2n+1, n = t + 512 r (the first pass's inputs)
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const int i0 = 2 * (t + NT * r), i1 = i0 + 1;
-        const float w0 = 0.5f - 0.5f * cospif(2.0f * (float)i0 / (float)NFFT);
-        const float w1 = 0.5f - 0.5f * cospif(2.0f * (float)i1 / (float)NFFT);
-        v[r] = make_float2(src[i0] * w0, src[i1] * w1);
+        const int i0 = 2 * (t + NT * r);
+        v[r] = make_float2(src[i0], src[i0 + 1]);
     }
     forward_r16(d, v);
-    double *out = P + ((int64_t)det * n_seg + g) * NBIN;
+    // the unwindowed spectrum U_0 .. U_NC into the transform's slots
     if (t == 0) {
         // butterfly 0: Z_0, Z_4096; bins 0, NC (from the self-pair k = 0) and 4096
         const float2 a = d[pad(0)], b = d[pad(4096)];
         float2 x0, xn, x4, x4d;
         split_fwd(cadd(a, b), cadd(a, b), make_float2(1.0f, 0.0f), x0, xn);
         split_fwd(csub(a, b), csub(a, b), make_float2(0.0f, -1.0f), x4, x4d);
-        out[0] = (double)x0.x * x0.x + (double)x0.y * x0.y;
-        out[NC] = (double)xn.x * xn.x + (double)xn.y * xn.y;
-        out[4096] = (double)x4.x * x4.x + (double)x4.y * x4.y;
+        d[pad(0)] = x0;
+        *u_nyq = xn;
+        d[pad(4096)] = x4;
     } else {
-        welch_mid_task(d, t, out);
+        welch_mid_task(d, t);
     }
 #pragma unroll
-    for (int m = 1; m < 4; ++m) welch_mid_task(d, t + NT * m, out);
-    if (t == NT - 1) welch_mid_task(d, 2048, out);
+    for (int m = 1; m < 4; ++m) welch_mid_task(d, t + NT * m);
+    if (t == NT - 1) welch_mid_task(d, 2048);
+    __syncthreads();
+    // windowed bins k = t + 512 m (and NC), |X_k|^2 in FP64
+    double *out = P + ((int64_t)det * n_seg + g) * NBIN;
+    auto U = [&](int k) -> float2 {
+        if (k < 0) return conj(d[pad(-k)]);
+        if (k == NC) return *u_nyq;
+        if (k > NC) return conj(d[pad(2 * NC - k)]);
+        return d[pad(k)];
+    };
+    auto p2 = [](float2 q) { return (double)q.x * (double)q.x + (double)q.y * (double)q.y; };
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int k = t + NT * m;
+        const float2 l = U(k - 1), c = U(k), r = U(k + 1);
+        out[k] = p2(make_float2(0.5f * c.x - 0.25f * (l.x + r.x), 0.5f * c.y - 0.25f * (l.y + r.y)));
+    }
+    if (t == NT - 1) {
+        const float2 l = U(NC - 1), c = U(NC), r = U(NC + 1);
+        out[NC] = p2(make_float2(0.5f * c.x - 0.25f * (l.x + r.x), 0.5f * c.y - 0.25f * (l.y + r.y)));
+    }
 }
-
 
 // grid (ceil(NBIN/256), ceil(n_psd/PSD_EPT), n_det): bin k of epochs
 // [e0, e0 + PSD_EPT) as a sliding FP64 sum over the periodograms (epoch e
@@ -369,7 +391,7 @@ __device__ __forceinline__ void whiten_mid_task0(const float2 *d, const float *g
 }
 
 constexpr int WHITEN_SMEM = r16::SLOTS * (int)sizeof(float2) + NBIN * (int)sizeof(float);
-constexpr int WELCH_SMEM = r16::SLOTS * (int)sizeof(float2);
+constexpr int WELCH_SMEM = (r16::SLOTS + 1) * (int)sizeof(float2);
 
 // One overlap-save block: the FIR of src[0 .. WB + F - 1) (samples past
 // `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value).
