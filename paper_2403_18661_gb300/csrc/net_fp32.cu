@@ -188,122 +188,150 @@ __global__ void __launch_bounds__(GN_T) k_groupnorm(float *__restrict__ x, int L
 // ---------------------------------------------------------------- conv GEMM
 // out[w][t+1][n] = sum_kk A[w,t][kk] * Wt[kk][n],  A[w,t][kk] = in[w][t*s + off][kk]
 // (kk runs over k*Cin contiguous floats).  M = n_win * Lout rows.
-// Tiles of BM x BN per CTA (256 threads, TM x TN outputs each), K in steps of
-// BK: the next step's A/B tiles are loaded into registers while the current
-// step is multiplied out of shared memory (double-buffered, one barrier per step).
-template <int BM, int BN, int TM, int TN>
+// Tiles of BM x BN per CTA (256 threads, TM x TN outputs each), K in steps of BK,
+// double-buffered in shared memory with one barrier per step: the next step's A
+// and B tiles are copied by cp.async while the current step is multiplied (A into
+// a staging area; after the copies land, each thread rewrites the A values it
+// copied itself into the layout below, so no extra barrier is needed).
+//
+// The products are packed FP32x2 FMAs (fma.rn.f32x2: two independent FMAs, each
+// rounded once like fmaf), so every output is accumulated in exactly the order
+// k = 0 .. K-1 with one rounding per step.  Each pair is (a_m, a_m) x (b_n, b_n+1),
+// the (a, a) pair built in registers from the transposed A tile.
+// A thread's TM rows and TN columns are runs of 4 spaced BM / (TM/4) and BN / (TN/4)
+// apart, so the 16-byte B loads of a warp touch consecutive addresses.
+template <int BM, int BN, int BK>
+struct ConvSmem {
+    static constexpr int A_LD = BM + 4;  // +4 floats spreads the transposed stores over the banks
+    static constexpr size_t bytes = sizeof(float) * (2 * BK * (A_LD + BN) + BM * BK);
+};
+
+template <int BM, int BN, int TM, int TN, int BK>
 __global__ void __launch_bounds__(256, 2) k_conv_fp32(const float *__restrict__ in, const float *__restrict__ wt,
                                                    float *__restrict__ out, int M, int Lout, int Lp_in, int Lp_out,
                                                    int Cin, int Cout, int K, int s, int off) {
-    constexpr int BK = 16;
-    constexpr int TX = BN / TN;
+    constexpr int TX = BN / TN, TY = BM / TM;
+    static_assert(TX * TY == 256 && TM % 4 == 0 && TN % 4 == 0, "tile shape");
+    constexpr int A_LD = ConvSmem<BM, BN, BK>::A_LD;
     constexpr int A_F4 = BM * BK / 4;  // float4 loads per A tile
-    constexpr int B_F4 = BK * BN / 4;
+    constexpr int B_F4 = BK * BN / 4;  // 16-byte copies per B tile
     constexpr int A_PER = (A_F4 + 255) / 256;
     constexpr int B_PER = (B_F4 + 255) / 256;
-    __shared__ __align__(16) float As[2][BK][BM + 4];
-    __shared__ __align__(16) float Bs[2][BK][BN];
+    extern __shared__ __align__(16) float conv_smem[];
+    float *As = conv_smem;                     // [2][BK][A_LD]
+    float *Bs = conv_smem + 2 * BK * A_LD;     // [2][BK][BN]
+    float *Ast = Bs + 2 * BK * BN;             // [BM][BK] staging of the next A tile
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
 
     const float *arow[A_PER];
-    int acol[A_PER], amrow[A_PER];
 #pragma unroll
     for (int i = 0; i < A_PER; ++i) {
-        int f = tid + i * 256;
-        int r = f / (BK / 4);
-        amrow[i] = r;
-        acol[i] = (f % (BK / 4)) * 4;
-        int m = m0 + r;
+        const int f = tid + i * 256;
+        const int m = m0 + f / (BK / 4);
         if (f < A_F4 && m < M) {
-            int w = m / Lout, t = m - w * Lout;
-            arow[i] = in + ((int64_t)w * Lp_in + (int64_t)t * s + off) * Cin;
+            const int w = m / Lout, t = m - w * Lout;
+            arow[i] = in + ((int64_t)w * Lp_in + (int64_t)t * s + off) * Cin + (f % (BK / 4)) * 4;
         } else {
             arow[i] = nullptr;
         }
     }
-    float4 ra[A_PER], rb[B_PER];
-    auto load_tiles = [&](int k0) {
+    auto copy_tiles = [&](int k0, int buf) {
 #pragma unroll
         for (int i = 0; i < A_PER; ++i) {
             const int f = tid + i * 256;
-            ra[i] = (f < A_F4 && arow[i]) ? __ldg(reinterpret_cast<const float4 *>(arow[i] + k0 + acol[i]))
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (f < A_F4) {  // rows past M are zero-filled (source size 0)
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ast + f * 4);
+                const float *src = arow[i] ? arow[i] + k0 : in;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                             "r"(arow[i] ? 16 : 0)
+                             : "memory");
+            }
         }
 #pragma unroll
         for (int i = 0; i < B_PER; ++i) {
             const int f = tid + i * 256;
             if (f < B_F4) {
                 const int r = f / (BN / 4), c = (f % (BN / 4)) * 4;
-                rb[i] = __ldg(reinterpret_cast<const float4 *>(wt + (int64_t)(k0 + r) * Cout + n0 + c));
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Bs + (buf * BK + r) * BN + c);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                             "l"(wt + (int64_t)(k0 + r) * Cout + n0 + c)
+                             : "memory");
             }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    auto store_tiles = [&](int buf) {
+    // after cp.async.wait_all: the thread's own staged A values -> the transposed A tile
+    auto store_a = [&](int buf) {
 #pragma unroll
         for (int i = 0; i < A_PER; ++i) {
             const int f = tid + i * 256;
             if (f < A_F4) {
-                As[buf][acol[i] + 0][amrow[i]] = ra[i].x;
-                As[buf][acol[i] + 1][amrow[i]] = ra[i].y;
-                As[buf][acol[i] + 2][amrow[i]] = ra[i].z;
-                As[buf][acol[i] + 3][amrow[i]] = ra[i].w;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < B_PER; ++i) {
-            const int f = tid + i * 256;
-            if (f < B_F4) {
-                const int r = f / (BN / 4), c = (f % (BN / 4)) * 4;
-                *reinterpret_cast<float4 *>(&Bs[buf][r][c]) = rb[i];
+                const float4 v = *reinterpret_cast<const float4 *>(Ast + f * 4);
+                float *d = As + (buf * BK + (f % (BK / 4)) * 4) * A_LD + (f / (BK / 4));
+                d[0] = v.x;
+                d[A_LD] = v.y;
+                d[2 * A_LD] = v.z;
+                d[3 * A_LD] = v.w;
             }
         }
     };
-    float acc[TM][TN];
+    float2 acc[TM][TN / 2];  // acc[i][j] = columns (2j, 2j+1) of the thread's row i
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < TN / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-    load_tiles(0);
-    store_tiles(0);
+    copy_tiles(0, 0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    store_a(0);
     __syncthreads();
     int cur = 0;
     for (int k0 = 0; k0 < K; k0 += BK) {
         const bool more = k0 + BK < K;
-        if (more) load_tiles(k0 + BK);  // global loads in flight during the math below
+        if (more) copy_tiles(k0 + BK, cur ^ 1);  // copies in flight during the math below
+        const float *Ac = As + cur * BK * A_LD;
+        const float *Bc = Bs + cur * BK * BN;
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            float a[TM], b[TN];
+            float4 ap[TM / 4];
+            float4 bq[TN / 4];
 #pragma unroll
-            for (int i = 0; i < TM; i += 4) {
-                float4 v = *reinterpret_cast<const float4 *>(&As[cur][kk][ty * TM + i]);
-                a[i] = v.x; a[i + 1] = v.y; a[i + 2] = v.z; a[i + 3] = v.w;
+            for (int h = 0; h < TM / 4; ++h) {
+                ap[h] = *reinterpret_cast<const float4 *>(Ac + kk * A_LD + h * TY * 4 + ty * 4);
             }
 #pragma unroll
-            for (int j = 0; j < TN; j += 4) {
-                float4 v = *reinterpret_cast<const float4 *>(&Bs[cur][kk][tx * TN + j]);
-                b[j] = v.x; b[j + 1] = v.y; b[j + 2] = v.z; b[j + 3] = v.w;
+            for (int h = 0; h < TN / 4; ++h)
+                bq[h] = *reinterpret_cast<const float4 *>(Bc + kk * BN + h * TX * 4 + tx * 4);
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                const float4 &a4 = ap[i / 4];
+                const float av = (i % 4 == 0) ? a4.x : (i % 4 == 1) ? a4.y : (i % 4 == 2) ? a4.z : a4.w;
+                const float2 a2 = make_float2(av, av);
+#pragma unroll
+                for (int j = 0; j < TN / 2; ++j) {
+                    const float2 b2 = (j & 1) ? make_float2(bq[j / 2].z, bq[j / 2].w)
+                                              : make_float2(bq[j / 2].x, bq[j / 2].y);
+                    acc[i][j] = __ffma2_rn(a2, b2, acc[i][j]);
+                }
             }
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
-        if (more) store_tiles(cur ^ 1);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (more) store_a(cur ^ 1);
         __syncthreads();
         cur ^= 1;
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        int m = m0 + ty * TM + i;
+        const int m = m0 + (i / 4) * TY * 4 + ty * 4 + (i % 4);
         if (m >= M) continue;
-        int w = m / Lout, t = m - w * Lout;
-        float *o = out + ((int64_t)w * Lp_out + t + 1) * Cout + n0 + tx * TN;
+        const int w = m / Lout, t = m - w * Lout;
+        float *o = out + ((int64_t)w * Lp_out + t + 1) * Cout + n0 + tx * 4;
 #pragma unroll
-        for (int j = 0; j < TN; j += 4)
-            *reinterpret_cast<float4 *>(o + j) = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+        for (int h = 0; h < TN / 4; ++h)
+            *reinterpret_cast<float4 *>(o + h * TX * 4) =
+                make_float4(acc[i][2 * h].x, acc[i][2 * h].y, acc[i][2 * h + 1].x, acc[i][2 * h + 1].y);
     }
 }
 
@@ -342,7 +370,7 @@ __global__ void k_head(const float *__restrict__ x, int L, int C, const float *_
     }
 }
 
-template <int BM, int BN, int TM, int TN>
+template <int BM, int BN, int TM, int TN, int BK>
 void conv_launch(afg_ctx *ctx, const float *in, const float *wt, float *out, int nw, const ConvLayer &L,
                  cudaStream_t st) {
     const int M = nw * L.lout;
@@ -352,14 +380,21 @@ void conv_launch(afg_ctx *ctx, const float *in, const float *wt, float *out, int
     // algorithmic: 2 M N K FLOPs; one read of the input activations and weights, one write of the output
     KScope ks(ctx, st, KK_CONV_FP32, 2.0 * M * L.cout * K,
               4.0 * ((double)nw * L.lin * L.cin + (double)K * L.cout + (double)M * L.cout));
-    k_conv_fp32<BM, BN, TM, TN><<<grid, 256, 0, st>>>(in, wt, out, M, L.lout, L.lin + 2, L.lout + 2, L.cin, L.cout,
-                                                      K, L.stride, off);
+    constexpr size_t smem = ConvSmem<BM, BN, BK>::bytes;
+    static bool attr_set = false;  // per instantiation; one device per process
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_conv_fp32<BM, BN, TM, TN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    k_conv_fp32<BM, BN, TM, TN, BK><<<grid, 256, smem, st>>>(in, wt, out, M, L.lout, L.lin + 2, L.lout + 2, L.cin,
+                                                             L.cout, K, L.stride, off);
 }
 
+// K = k * Cin is a multiple of 16 for every convolution of the networks (Cin >= 16)
 void conv_dispatch(afg_ctx *ctx, const float *in, float *out, int nw, const ConvLayer &L, cudaStream_t st) {
-    if (L.cout % 128 == 0) conv_launch<128, 128, 8, 8>(ctx, in, L.wt, out, nw, L, st);
-    else if (L.cout % 64 == 0) conv_launch<128, 64, 8, 4>(ctx, in, L.wt, out, nw, L, st);
-    else conv_launch<256, 16, 4, 4>(ctx, in, L.wt, out, nw, L, st);
+    if (L.cout % 128 == 0) conv_launch<128, 128, 8, 8, 16>(ctx, in, L.wt, out, nw, L, st);
+    else if (L.cout % 64 == 0) conv_launch<128, 64, 8, 4, 16>(ctx, in, L.wt, out, nw, L, st);
+    else conv_launch<256, 16, 4, 4, 16>(ctx, in, L.wt, out, nw, L, st);
 }
 
 // GroupNorm launch with its accounting: one read (+ residual read) and one write of the tile
