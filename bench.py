@@ -237,6 +237,29 @@ def tune_tiles(ctx, stream, n_win: int = 1024):
             "chosen": sorted({(t["orient"], t["wpc"], t["kb"], t["stages"], t["acc_bufs"]) for t in tiles})}
 
 
+def layer_roofline(tiles: list, n_win: int, conv_ms: float, peaks: dict) -> dict:
+    """Per-layer roofline of the tensor-core convolutions: each layer's time bound is the larger of
+    its algorithmic FLOPs at the sustained BF16 rate and its algorithmic bytes (input, residual and
+    output once, plus weights) at the measured HBM rate; the network's bound is their sum.  frac =
+    bound / measured conv time per step.  Layers whose FLOP/byte is below the ridge point are HBM-bound."""
+    tf = peaks.get("bf16_tflops_sustained", 1700.0) * 1e12
+    bw = peaks.get("hbm_gbs", 6800.0) * 1e9
+    t_bound, t_hbm, n_hbm = 0.0, 0.0, 0
+    for t in tiles:
+        flops = 2.0 * n_win * t["lout"] * t["cout"] * t["taps"] * t["cin"]
+        nbytes = 2.0 * n_win * ((t["lin"] + 2) * t["cin"] + (t["lout"] + 2) * t["cout"] * (2 if t["residual"] else 1)) \
+            + 2.0 * t["taps"] * t["cin"] * t["cout"]
+        tc, tm = flops / tf, nbytes / bw
+        t_bound += max(tc, tm)
+        if tm > tc:
+            t_hbm += tm
+            n_hbm += 1
+    return {"bound_ms": t_bound * 1e3, "conv_ms": conv_ms, "frac": t_bound * 1e3 / max(conv_ms, 1e-9),
+            "layers": len(tiles), "hbm_bound_layers": n_hbm, "hbm_bound_share_of_bound": t_hbm / max(t_bound, 1e-12),
+            "ridge_flop_per_byte": tf / bw,
+            "peaks": "measured bf16_tflops_sustained and hbm_gbs" if peaks.get("_source") != "fallback" else "fallback"}
+
+
 def time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world):
     """The same workload through the BF16 tensor-core network (context of its own),
     timed like the FP32 value; returned as a sub-result with the ratio to FP32."""
@@ -267,9 +290,16 @@ def time_bf16_same_workload(wl, w, xd, args, stream, flush, peaks, world):
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
     value, _, job_s = pdist.job_throughput(wl.n_win * wl.stride / wl.fs * args.steps, total_ms / 1000.0, world)
     dom = max(kstats, key=lambda k: k["total_ms"])
+    lroof = None
+    try:
+        geo = ctx.tiles()
+    except abi.AfgError:
+        geo = []
+    if geo and dom["name"].startswith("conv_gemm_bf16"):
+        lroof = layer_roofline(geo, wl.n_win, dom["total_ms"] / args.steps, peaks)
     ctx.close()
     return {"value": value, "unit": "strain-s/s", "ms_per_step": job_s * 1000.0 / args.steps, "dtype": "bf16",
-            "roofline": roofline_for(dom, peaks, job_s * 1000.0),
+            "roofline": roofline_for(dom, peaks, job_s * 1000.0), "layer_roofline": lroof,
             "gpu_launches": int(sum(k["launches"] for k in kstats)), "tiles": tiles}
 
 
