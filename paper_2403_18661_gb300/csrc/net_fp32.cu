@@ -185,6 +185,115 @@ __global__ void __launch_bounds__(GN_T) k_groupnorm(float *__restrict__ x, int L
     }
 }
 
+// GroupNorm with the window's tile staged in shared memory (every tile of the 16-channel and
+// ResNet34-GN networks has L * C = 49,152 floats, 192 KB): thread t copies float4 chunks t, t + GN_ST,
+// ... of the window with cp.async (all copies in flight together, no registers held), and after its
+// own copies have landed reads only those chunks back, so the tile is read from HBM once.  The mean
+// and the centred variance come from shared memory (the same two-pass definition, partial sums
+// reduced in a fixed order), and the normalised tile (+ residual, ReLU) is written once.  C/4
+// divides GN_ST, so a thread's 4 channels are fixed.
+constexpr int GN_ST = 512;
+constexpr int GN_ST_MAX4 = 12288;  // float4 chunks of the largest staged tile (192 KB)
+
+__device__ __forceinline__ void gn_channel_reduce_st(float (&a)[4], float *red, float *chs, int C) {
+    const int tid = threadIdx.x;
+    for (int e = 0; e < 4; ++e) red[tid * 4 + e] = a[e];
+    __syncthreads();
+    const int q = C / 4;
+    for (int c = tid; c < C; c += GN_ST) {
+        const int quad = c / 4, e = c % 4;
+        float s = 0.f;
+        for (int t = quad; t < GN_ST; t += q) s += red[t * 4 + e];
+        chs[c] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(GN_ST, 1) k_groupnorm_st(float *__restrict__ x, int L, int C, int G,
+                                                          const float *__restrict__ gamma,
+                                                          const float *__restrict__ beta, float eps,
+                                                          const float *__restrict__ res, int relu) {
+    extern __shared__ __align__(16) float4 gn_tile[];  // [L * C / 4]
+    __shared__ float red[GN_ST * 4];
+    __shared__ float chs[512];
+    __shared__ float gmean[32], grstd[32];
+    const int tid = threadIdx.x;
+    const int cg = C / G;
+    const int n4 = L * C / 4;
+    const int64_t tile = (int64_t)(L + 2) * C;
+    float *xt = x + (int64_t)blockIdx.x * tile + C;  // row 0 of data
+    const int c0 = (tid % (C / 4)) * 4;
+    const float4 *x4 = reinterpret_cast<const float4 *>(xt);
+    for (int i = tid; i < n4; i += GN_ST)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(gn_tile + i)),
+                     "l"(x4 + i)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = tid; i < n4; i += GN_ST) {
+        const float4 v = gn_tile[i];
+        a[0] += v.x; a[1] += v.y; a[2] += v.z; a[3] += v.w;
+    }
+    gn_channel_reduce_st(a, red, chs, C);
+    if (tid < G) {
+        float s = 0.f;
+        for (int c = tid * cg; c < (tid + 1) * cg; ++c) s += chs[c];
+        gmean[tid] = s / (float)(L * cg);
+    }
+    __syncthreads();
+    float mu[4];
+    for (int e = 0; e < 4; ++e) mu[e] = gmean[(c0 + e) / cg];
+    for (int e = 0; e < 4; ++e) a[e] = 0.f;
+    for (int i = tid; i < n4; i += GN_ST) {
+        const float4 v = gn_tile[i];
+        float d;
+        d = v.x - mu[0]; a[0] = fmaf(d, d, a[0]);
+        d = v.y - mu[1]; a[1] = fmaf(d, d, a[1]);
+        d = v.z - mu[2]; a[2] = fmaf(d, d, a[2]);
+        d = v.w - mu[3]; a[3] = fmaf(d, d, a[3]);
+    }
+    gn_channel_reduce_st(a, red, chs, C);
+    if (tid < G) {
+        float s = 0.f;
+        for (int c = tid * cg; c < (tid + 1) * cg; ++c) s += chs[c];
+        grstd[tid] = rsqrtf(s / (float)(L * cg) + eps);
+    }
+    __syncthreads();
+    float sc[4], sh[4];
+    for (int e = 0; e < 4; ++e) {
+        const int c = c0 + e, g = c / cg;
+        sc[e] = grstd[g] * gamma[c];
+        sh[e] = beta[c] - gmean[g] * sc[e];
+    }
+    const float4 *r4 = res ? reinterpret_cast<const float4 *>(res + (int64_t)blockIdx.x * tile + C) : nullptr;
+    float4 *w4 = reinterpret_cast<float4 *>(xt);
+    constexpr int RB = 8;  // residual loads in flight per thread
+    for (int i0 = tid; i0 < n4; i0 += RB * GN_ST) {
+        float4 r[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            const int i = i0 + k * GN_ST;
+            r[k] = (r4 && i < n4) ? r4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            const int i = i0 + k * GN_ST;
+            if (i >= n4) break;
+            const float4 u = gn_tile[i];
+            float o[4] = {fmaf(u.x, sc[0], sh[0]) + r[k].x, fmaf(u.y, sc[1], sh[1]) + r[k].y,
+                          fmaf(u.z, sc[2], sh[2]) + r[k].z, fmaf(u.w, sc[3], sh[3]) + r[k].w};
+            if (relu)
+                for (int e = 0; e < 4; ++e) o[e] = fmaxf(o[e], 0.f);
+            w4[i] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+    for (int c = tid; c < C; c += GN_ST) {
+        xt[-C + c] = 0.f;
+        xt[(int64_t)L * C + c] = 0.f;
+    }
+}
+
 // ---------------------------------------------------------------- conv GEMM
 // out[w][t+1][n] = sum_kk A[w,t][kk] * Wt[kk][n],  A[w,t][kk] = in[w][t*s + off][kk]
 // (kk runs over k*Cin contiguous floats).  M = n_win * Lout rows.
@@ -404,7 +513,17 @@ void gn_launch(afg_ctx *ctx, float *x, int nw, int L, int C, int G, const float 
     double bytes = tile * (res ? 3.0 : 2.0);
     if (pool_out) bytes = tile * 1.5;
     KScope ks(ctx, st, KK_GROUPNORM, 0.0, bytes);
-    k_groupnorm<<<nw, GN_T, 0, st>>>(x, L, C, G, gamma, beta, eps, res, relu, pool_out);
+    const int64_t n4 = (int64_t)L * C / 4;
+    if (!pool_out && C % 4 == 0 && C <= 512 && GN_ST % (C / 4) == 0 && n4 >= GN_ST && n4 <= GN_ST_MAX4) {
+        static bool attr_set = false;  // one device per process
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_groupnorm_st, cudaFuncAttributeMaxDynamicSharedMemorySize, GN_ST_MAX4 * 16);
+            attr_set = true;
+        }
+        k_groupnorm_st<<<nw, GN_ST, (size_t)n4 * 16, st>>>(x, L, C, G, gamma, beta, eps, res, relu);
+    } else {
+        k_groupnorm<<<nw, GN_T, 0, st>>>(x, L, C, G, gamma, beta, eps, res, relu, pool_out);
+    }
 }
 
 }  // namespace
