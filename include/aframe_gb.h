@@ -397,6 +397,17 @@ int afg_stream_open(afg_ctx *ctx, int64_t *stream_id);
  * non-finite sample, AFG_ERR_STATE for a stream that is not open. */
 int afg_stream_push(afg_ctx *ctx, int64_t id, const float *chunk_host, int64_t n, int64_t *ticket);
 
+/* Push n_push chunks of n samples per detector at once (a burst of arrivals):
+ * chunk k goes to stream ids[k] and is chunks_host[k][2][n] (host memory,
+ * row-major, copied before returning); the same as n_push calls of
+ * afg_stream_push in order, under one lock, with one push time.  tickets
+ * (NULL or n_push entries) receives each push's sequence number within its
+ * stream.  Every chunk and id is checked first: AFG_ERR_NAN (a non-finite
+ * sample) or AFG_ERR_STATE (a stream that is not open) pushes nothing.
+ * AFG_ERR_ARG for n outside 1..max_chunk or missing arrays. */
+int afg_stream_push_many(afg_ctx *ctx, int64_t n_push, const int64_t *ids, const float *chunks_host, int64_t n,
+                         int64_t *tickets);
+
 /* Move up to cap available results of the stream (oldest first) to out;
  * waits up to wait_s seconds if none is available yet. */
 int afg_stream_poll(afg_ctx *ctx, int64_t id, afg_stream_result *out, int64_t cap, int64_t *n_out, double wait_s);

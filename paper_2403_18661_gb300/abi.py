@@ -118,6 +118,7 @@ SIGNATURES = {
     "afg_stream_start": ([_vp, ctypes.POINTER(AfgStreamParams)], ctypes.c_int),
     "afg_stream_open": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
     "afg_stream_push": ([_vp, _i64, _vp, _i64, ctypes.POINTER(_i64)], ctypes.c_int),
+    "afg_stream_push_many": ([_vp, _i64, _vp, _vp, _i64, _vp], ctypes.c_int),
     "afg_stream_poll": ([_vp, _i64, _vp, _i64, ctypes.POINTER(_i64), ctypes.c_double], ctypes.c_int),
     "afg_stream_flush": ([_vp, ctypes.c_double], ctypes.c_int),
     "afg_stream_close": ([_vp, _i64], ctypes.c_int),
@@ -479,6 +480,16 @@ class Context:
         t = _i64()
         self._check(self._lib.afg_stream_push(self._h, sid, c.ctypes.data, c.shape[1], ctypes.byref(t)))
         return t.value
+
+    def stream_push_many(self, sids, chunks: np.ndarray) -> np.ndarray:
+        """Push chunks[k] ([2][n]) to stream sids[k] for every k in one call; returns the tickets."""
+        ids = np.ascontiguousarray(np.asarray(sids, dtype=np.int64))
+        c = np.ascontiguousarray(chunks, dtype=np.float32)
+        assert c.ndim == 3 and c.shape[0] == ids.size and c.shape[1] == 2
+        t = np.empty(ids.size, dtype=np.int64)
+        self._check(self._lib.afg_stream_push_many(self._h, ids.size, ids.ctypes.data, c.ctypes.data, c.shape[2],
+                                                   t.ctypes.data))
+        return t
 
     def stream_poll(self, sid: int, cap: int = 65536, wait_s: float = 0.0) -> np.ndarray:
         out = np.empty(cap, dtype=STREAM_RESULT_DTYPE)

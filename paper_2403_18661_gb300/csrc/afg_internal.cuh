@@ -307,6 +307,9 @@ cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, i
                           int hop, int fs, double *P, double *psd, cudaStream_t st);
 cudaError_t prepare_psd_kernels();
 int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st);
+int launch_psd_rows(afg_ctx *ctx, const float *const *rows_dev, int n_rows, int64_t psd_span, double *psd,
+                    cudaStream_t st);
+int launch_scatter_rows(afg_ctx *ctx, const float *src, float *const *dst_dev, int n_rows, int len, cudaStream_t st);
 int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,
                         cudaStream_t st);
 int whiten_multi_piece_max(const afg_ctx *ctx);  // outputs per piece of launch_whiten_multi

@@ -6,7 +6,7 @@
 //
 // Per stream, on the device: a mirrored ring of raw strain (every span of up
 // to R samples is contiguous), a mirrored ring of whitened strain, the
-// whitening gains of two epochs, the PSD, and a ring of logits.  Whitened
+// whitening gains of two epochs, and a ring of logits.  Whitened
 // sample j of a stream is raw sample psd_len + j, whitened with the PSD of
 // raw [e * epoch_len, e * epoch_len + psd_len), e = j / epoch_len (the 64 s
 // before its epoch); window w covers whitened [w * stride, w * stride + W).
@@ -18,8 +18,10 @@
 // integration launch in large ones) and one D2H copy.  PSD and filter
 // refreshes are enqueued after a step's result event, as soon as a stream's
 // raw strain covers the 64 s before an epoch, ahead of that epoch's first
-// whitened sample.  Chunks pushed while a step runs join the next one; two
-// steps may be in flight.
+// whitened sample; all of a step's refreshes are batched (per 16 streams: one
+// periodogram launch, one mean launch, one filter build over every detector,
+// one launch that copies the gains to the streams' slots).  Chunks pushed
+// while a step runs join the next one; two steps may be in flight.
 #include <string.h>
 
 #include <algorithm>
@@ -90,7 +92,6 @@ struct Chunk {
 struct Slot {
     bool open = false, closing = false;
     float *raw = nullptr, *white = nullptr, *gains = nullptr, *logits = nullptr;
-    double *psd = nullptr;
     void *mem = nullptr;
     int64_t bytes = 0;
     int64_t P = 0, Q = 0, n_win = 0;      // raw committed, whitened produced, windows evaluated
@@ -119,6 +120,7 @@ struct StepBuf {
     IntegDesc *h_int = nullptr;
     float *d_out = nullptr, *h_out = nullptr;
     int cap_sc = 0, cap_wp = 0, cap_win = 0;
+    int cap_rf = 0;  // gains-refresh rows per list (two detectors per refresh)
     cudaEvent_t ev = nullptr;
     std::vector<PendingResult> res;
     std::vector<int> slots;  // streams with chunks in this step
@@ -139,6 +141,9 @@ struct ServeEngine {
     cudaStream_t st = nullptr;
     unsigned *d_done = nullptr;  // completion counter of the network launch (integration by its last CTA)
     StepBuf buf[2];
+    int rb_rows = 0;                // rows (detector PSDs) per batched gains refresh
+    double *d_rf_psd = nullptr;     // [rb_rows][NBIN] PSDs of a refresh batch
+    float *d_rf_gains = nullptr;    // [rb_rows][NBIN] their gains, before the scatter to the streams' slots
     int err = AFG_OK;
     int64_t steps = 0, windows = 0, samples = 0;
 };
@@ -152,9 +157,10 @@ int alloc_step(afg_ctx *ctx, StepBuf &b, int max_streams, int64_t per_stream_new
     b.cap_sc = max_streams;
     b.cap_wp = max_streams * (int)(per_stream_new / 512 + 3);  // pieces of >= 512 outputs, one epoch break
     b.cap_win = (int)(max_streams * (per_stream_new / stride + 2));
+    b.cap_rf = 4 * max_streams;  // two epochs of two detectors per stream
     b.blk_bytes = align16(b.stage_cap * sizeof(float)) + align16(b.cap_sc * sizeof(ScatterDesc)) +
                   align16(b.cap_wp * sizeof(WhitenPiece)) + align16(b.cap_win * sizeof(WinPtr)) +
-                  align16(b.cap_win * sizeof(IntegDesc));
+                  align16(b.cap_win * sizeof(IntegDesc)) + 2 * align16((size_t)b.cap_rf * 2 * sizeof(void *));
     AFG_CUDA(ctx, cudaHostAlloc(&b.h_stage, b.blk_bytes, cudaHostAllocDefault));
     AFG_CUDA(ctx, cudaMalloc(&b.d_stage, b.blk_bytes));
     AFG_CUDA(ctx, cudaHostAlloc(&b.h_sc, b.cap_sc * sizeof(ScatterDesc), cudaHostAllocDefault));
@@ -205,17 +211,47 @@ int complete(ServeEngine &E, StepBuf &b) {
     return AFG_OK;
 }
 
-// PSD of raw [e * epoch_len, e * epoch_len + psd_len) and the two detectors' gains of
-// epoch e into the stream's gains slot e & 1, on st.
-int refresh_gains(ServeEngine &E, Slot &sl, int64_t e, cudaStream_t st) {
-    afg_ctx *ctx = E.ctx;
+// Gains refreshes of one list, batched: for every (slot, epoch) the PSD of raw [e * epoch_len,
+// e * epoch_len + psd_len) of both detectors and their gains into the stream's gains slot e & 1.
+// The host writes, into the step's staging block, the list's source rows (each detector's raw
+// samples) followed by its destination rows (gains slots); per batch of rb_rows rows one
+// periodogram launch, one mean launch and one filter build cover every row, and one launch
+// copies the gains to their slots.
+struct RefreshList {
+    size_t off = 0;  // byte offset of the pointer rows in the staging block
+    int n = 0;       // refreshes
+};
+
+void refresh_plan(ServeEngine &E, StepBuf &b, char *hb, RefreshList &L,
+                  const std::vector<std::pair<int, int64_t>> &list) {
     const afg_stream_params &p = E.p;
-    const int slot_g = (int)(e & 1);
-    const float *xr = sl.raw + (e * p.epoch_len) % E.R;
-    int rc = launch_psd(ctx, xr, p.psd_len, 2, 1, 0, p.psd_len, sl.psd, st, 2 * E.R);
-    if (!rc) rc = launch_filter(ctx, sl.psd, 2, 1, sl.gains + (int64_t)slot_g * 2 * NBIN, st);
-    if (rc) return rc;
-    sl.gains_epoch[slot_g] = e;
+    L.n = (int)list.size();
+    const float **src = reinterpret_cast<const float **>(hb + L.off);
+    float **dst = reinterpret_cast<float **>(hb + L.off) + b.cap_rf;
+    for (int i = 0; i < L.n; ++i) {
+        Slot &sl = E.slots[list[i].first];
+        const int64_t e = list[i].second;
+        const float *xr = sl.raw + (e * p.epoch_len) % E.R;
+        float *g = sl.gains + (int64_t)(e & 1) * 2 * NBIN;
+        src[2 * i] = xr;
+        src[2 * i + 1] = xr + 2 * E.R;
+        dst[2 * i] = g;
+        dst[2 * i + 1] = g + NBIN;
+        sl.gains_epoch[e & 1] = e;
+    }
+}
+
+int refresh_run(ServeEngine &E, StepBuf &b, char *db, const RefreshList &L, cudaStream_t st) {
+    afg_ctx *ctx = E.ctx;
+    const float *const *src = reinterpret_cast<const float *const *>(db + L.off);
+    float *const *dst = reinterpret_cast<float *const *>(db + L.off) + b.cap_rf;
+    for (int r0 = 0; r0 < 2 * L.n; r0 += E.rb_rows) {
+        const int nr = std::min(E.rb_rows, 2 * L.n - r0);
+        int rc = launch_psd_rows(ctx, src + r0, nr, E.p.psd_len, E.d_rf_psd, st);
+        if (!rc) rc = launch_filter(ctx, E.d_rf_psd, nr, 1, E.d_rf_gains, st);
+        if (!rc) rc = launch_scatter_rows(ctx, E.d_rf_gains, dst + r0, nr, NBIN, st);
+        if (rc) return rc;
+    }
     return AFG_OK;
 }
 
@@ -341,6 +377,20 @@ int launch_step(ServeEngine &E, StepBuf &b) {
             b.h_win[n_win++] = wptr;
         }
     }
+    // Refreshes ahead of need: a stream whose raw strain now covers the 64 s before its current or
+    // next epoch gets that epoch's PSD and gains, enqueued after this step's result event so that
+    // no push waits for them.  The data is complete F/2 samples before the epoch's first output can
+    // be whitened, so a later step (same CUDA stream) finds the gains built; the gains slot they
+    // take held the epoch before the previous one, which no pending or later piece reads.
+    std::vector<std::pair<int, int64_t>> ahead;
+    for (Taken &t : taken) {
+        Slot &sl = E.slots[t.slot];
+        for (int64_t e = sl.Q / p.epoch_len; e <= sl.Q / p.epoch_len + 1; ++e)
+            if (sl.gains_epoch[e & 1] != e && sl.P >= e * p.epoch_len + p.psd_len) {
+                sl.gains_epoch[e & 1] = e;  // (set again by refresh_plan)
+                ahead.emplace_back(t.slot, e);
+            }
+    }
     // Scatter: inside the whitening launch (a stream's first piece) unless a gains refresh must read
     // the new samples from the ring first, or the stream has no piece this step, or the whitening
     // kernel reads only the ring; those go through k_scatter.
@@ -363,6 +413,23 @@ int launch_step(ServeEngine &E, StepBuf &b) {
     off += align16(n_win * sizeof(WinPtr));
     const size_t o_int = off;
     off += align16(n_res * sizeof(IntegDesc));
+    // the refresh pointer rows: in-step refreshes, then refreshes ahead of need
+    RefreshList rf_in, rf_ahead;
+    if ((int)(2 * refresh.size()) > b.cap_rf || (int)(2 * ahead.size()) > b.cap_rf)
+    {
+        afg_fail(ctx, AFG_ERR_STATE, "stream step: more gains refreshes than planned for");
+        return -1;
+    }
+    if (!refresh.empty()) {
+        rf_in.off = off;
+        off += 2 * align16((size_t)b.cap_rf * sizeof(void *));
+        refresh_plan(E, b, hb, rf_in, refresh);
+    }
+    if (!ahead.empty()) {
+        rf_ahead.off = off;
+        off += 2 * align16((size_t)b.cap_rf * sizeof(void *));
+        refresh_plan(E, b, hb, rf_ahead, ahead);
+    }
     memcpy(hb + o_sc, b.h_sc, n_sc * sizeof(ScatterDesc));
     memcpy(hb + o_wp, b.h_wp, n_wp * sizeof(WhitenPiece));
     memcpy(hb + o_win, b.h_win, n_win * sizeof(WinPtr));
@@ -375,8 +442,7 @@ int launch_step(ServeEngine &E, StepBuf &b) {
         }
         AFG_LAUNCH_CHECK(ctx, "k_scatter");
     }
-    for (const auto &r : refresh)
-        if (refresh_gains(E, E.slots[r.first], r.second, st)) return -1;
+    if (rf_in.n && refresh_run(E, b, db, rf_in, st)) return -1;
     if (n_wp && launch_whiten_multi(ctx, reinterpret_cast<const WhitenPiece *>(db + o_wp), n_wp, total_white, st))
         return -1;
     // small steps: the network launch also integrates the new windows (its last CTA, after every
@@ -393,18 +459,8 @@ int launch_step(ServeEngine &E, StepBuf &b) {
     }
     if (n_res) AFG_CUDA(ctx, cudaMemcpyAsync(b.h_out, b.d_out, n_res * 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
     AFG_CUDA(ctx, cudaEventRecord(b.ev, st));
-    // Refreshes ahead of need: a stream whose raw strain now covers the 64 s before its
-    // current or next epoch gets that epoch's PSD and gains here, after this step's result
-    // event, so no push waits for them.  The data is complete F/2 samples before the epoch's
-    // first output can be whitened, so a later step (same CUDA stream) finds the gains
-    // built; the gains slot they take held the epoch before the previous one, which no
-    // pending or later piece reads.
-    for (Taken &t : taken) {
-        Slot &sl = E.slots[t.slot];
-        for (int64_t e = sl.Q / p.epoch_len; e <= sl.Q / p.epoch_len + 1; ++e)
-            if (sl.gains_epoch[e & 1] != e && sl.P >= e * p.epoch_len + p.psd_len && refresh_gains(E, sl, e, st))
-                return -1;
-    }
+    // the refreshes ahead of need (planned above), after the step's result event
+    if (rf_ahead.n && refresh_run(E, b, db, rf_ahead, st)) return -1;
     b.busy = true;
     E.steps++;
     E.windows += n_win;
@@ -473,7 +529,7 @@ void engine_main(ServeEngine *E) {
 }
 
 int64_t slot_bytes(const ServeEngine &E) {
-    return (int64_t)(2 * 2 * E.R + 2 * 2 * E.Wr + 2 * 2 * NBIN + LR) * 4 + 2 * NBIN * 8 + 1024;
+    return (int64_t)(2 * 2 * E.R + 2 * 2 * E.Wr + 2 * 2 * NBIN + LR) * 4 + 1024;
 }
 
 }  // namespace
@@ -494,6 +550,8 @@ void serve_release(afg_ctx *ctx) {
     free_step(E->buf[1]);
     if (E->st) cudaStreamDestroy(E->st);
     if (E->d_done) cudaFree(E->d_done);
+    if (E->d_rf_psd) cudaFree(E->d_rf_psd);
+    if (E->d_rf_gains) cudaFree(E->d_rf_gains);
     delete E;
     ctx->serve = nullptr;
 }
@@ -525,14 +583,21 @@ extern "C" int afg_stream_start(afg_ctx *ctx, const afg_stream_params *p) {
     if (!rc && cudaStreamCreateWithFlags(&E->st, cudaStreamNonBlocking) != cudaSuccess) rc = AFG_ERR_CUDA;
     if (!rc && (cudaMalloc(&E->d_done, 16) != cudaSuccess || cudaMemset(E->d_done, 0, 16) != cudaSuccess))
         rc = AFG_ERR_CUDA;
-    // the scratch of a gains refresh at its per-refresh size (the Welch periodograms of one stream
-    // and the FP64 transforms of its 2 filters), reserved and counted against the HBM budget here,
-    // before any stream is admitted: steps never allocate, and the engine thread never changes
-    // bytes_held outside E->mu
+    // the scratch of a batch of gains refreshes (up to 16 streams: the Welch periodograms of their
+    // detectors, the FP64 transforms of their filters, their PSDs and gains), reserved and counted
+    // against the HBM budget here, before any stream is admitted: steps never allocate, and the
+    // engine thread never changes bytes_held outside E->mu
     void *tmp = nullptr;
     const int64_t K = (p->psd_len - NFFT) / hop + 1;
-    if (!rc) rc = afg_ws_reserve(ctx, WS_PERIODOGRAM, (size_t)2 * K * NBIN * sizeof(double), &tmp);
-    if (!rc) rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, filter_build_scratch_bytes(ctx, 2), &tmp);
+    E->rb_rows = 2 * std::min(p->max_streams, 16);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_PERIODOGRAM, (size_t)E->rb_rows * K * NBIN * sizeof(double), &tmp);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_FB_SCRATCH, filter_build_scratch_bytes(ctx, E->rb_rows), &tmp);
+    if (!rc && (cudaMalloc(&E->d_rf_psd, (size_t)E->rb_rows * NBIN * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&E->d_rf_gains, (size_t)E->rb_rows * NBIN * sizeof(float)) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = afg_fail(ctx, AFG_ERR_OOM, "stream_start: refresh buffers");
+    }
+    if (!rc) ctx->bytes_held += (int64_t)E->rb_rows * NBIN * (sizeof(double) + sizeof(float));
     if (rc) {
         ctx->serve = E;
         serve_release(ctx);
@@ -583,9 +648,6 @@ extern "C" int afg_stream_open(afg_ctx *ctx, int64_t *stream_id) {
     sl.gains = reinterpret_cast<float *>(c);
     c += 2 * 2 * NBIN * 4;
     sl.logits = reinterpret_cast<float *>(c);
-    c += LR * 4;
-    c = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(c) + 255) & ~uintptr_t(255));
-    sl.psd = reinterpret_cast<double *>(c);
     sl.open = true;
     ctx->bytes_held += bytes;
     *stream_id = s;
@@ -615,6 +677,44 @@ extern "C" int afg_stream_push(afg_ctx *ctx, int64_t id, const float *chunk_host
         sl.pending.push_back(std::move(c));
     }
     E->pushes.fetch_add(1, std::memory_order_release);
+    E->cv_work.notify_one();
+    return AFG_OK;
+}
+
+extern "C" int afg_stream_push_many(afg_ctx *ctx, int64_t n_push, const int64_t *ids, const float *chunks_host,
+                                    int64_t n, int64_t *tickets) {
+    if (!ctx) return AFG_ERR_ARG;
+    ServeEngine *E = ctx->serve;
+    if (!E) return afg_fail(ctx, AFG_ERR_STATE, "stream_push_many: no engine");
+    if (n_push < 0 || (n_push > 0 && (!ids || !chunks_host)) || n < 1 || n > E->p.max_chunk)
+        return afg_fail(ctx, AFG_ERR_ARG, "stream_push_many: bad arguments");
+    if (n_push == 0) return AFG_OK;
+    // every check before anything is queued: a refused call pushes nothing
+    for (int64_t i = 0; i < 2 * n * n_push; ++i)
+        if (!(chunks_host[i] == chunks_host[i]) || chunks_host[i] - chunks_host[i] != 0.0f)
+            return afg_fail(ctx, AFG_ERR_NAN, "stream_push_many: non-finite sample in push %lld",
+                            (long long)(i / (2 * n)));
+    std::vector<Chunk> cs((size_t)n_push);
+    const double t = now_s();
+    for (int64_t k = 0; k < n_push; ++k) {
+        cs[k].data.assign(chunks_host + 2 * n * k, chunks_host + 2 * n * (k + 1));
+        cs[k].n = n;
+        cs[k].t_push = t;
+    }
+    {
+        std::lock_guard<std::mutex> lock(E->mu);
+        if (E->err) return afg_fail(ctx, E->err, "stream_push_many: the engine stopped after an error");
+        for (int64_t k = 0; k < n_push; ++k)
+            if (ids[k] < 0 || ids[k] >= (int64_t)E->slots.size() || !E->slots[ids[k]].open)
+                return afg_fail(ctx, AFG_ERR_STATE, "stream_push_many: stream %lld is not open", (long long)ids[k]);
+        for (int64_t k = 0; k < n_push; ++k) {
+            Slot &sl = E->slots[ids[k]];
+            if (tickets) tickets[k] = sl.pushed;
+            sl.pushed++;
+            sl.pending.push_back(std::move(cs[k]));
+        }
+    }
+    E->pushes.fetch_add((uint64_t)n_push, std::memory_order_release);
     E->cv_work.notify_one();
     return AFG_OK;
 }

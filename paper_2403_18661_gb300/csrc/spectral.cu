@@ -72,7 +72,8 @@ __device__ __forceinline__ void welch_mid_task(float2 *d, int j) {
 // so the windowed spectrum is X_k = U_k / 2 - (U_{k-1} + U_{k+1}) / 4 with U the spectrum of the
 // unwindowed segment (U_{-1} = conj U_1, U_{NC+1} = conj U_{NC-1} for a real segment).
 __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restrict__ x, int64_t x_stride, int hop,
-                                                             double *__restrict__ P, int64_t n_seg) {
+                                                             double *__restrict__ P, int64_t n_seg,
+                                                             const float *const *__restrict__ rows) {
     using namespace r16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *d = reinterpret_cast<float2 *>(smem_raw);
@@ -80,7 +81,8 @@ __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restr
     const int64_t g = blockIdx.x;
     const int det = blockIdx.y;
     const int t = threadIdx.x;
-    const float *src = x + det * x_stride + g * (int64_t)hop;
+    // row det starts at x + det * x_stride, or at rows[det] (rows of unrelated buffers)
+    const float *src = (rows ? rows[det] : x + det * x_stride) + g * (int64_t)hop;
     // z_n = x_2n + i x_2n+1, n = t + 512 r (the first pass's inputs)
     float2 v[16];
 #pragma unroll
@@ -683,7 +685,7 @@ int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd
     {
         // one read of every segment, one FP64 periodogram written per segment
         KScope ks(ctx, st, KK_PERIODOGRAM, 0.0, (double)n_det * n_seg * (NFFT * 4.0 + NBIN * 8.0));
-        k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, x_stride, hop, P, n_seg);
+        k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, x_stride, hop, P, n_seg, nullptr);
     }
     AFG_LAUNCH_CHECK(ctx, "k_periodogram");
     // periodic Hann: sum w^2 = 3 NFFT / 8
@@ -733,6 +735,46 @@ int launch_filter(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, flo
     return filter_build(ctx, psd, n_det, n_psd, gains, st);
 }
 
+// One PSD per row of psd_span samples, row r starting at rows_dev[r] (device array of n_rows
+// pointers): the Welch periodograms of all rows in one launch and their means in another, into
+// psd [n_rows][NBIN].  The same kernels and arithmetic as launch_psd with n_psd = 1.
+int launch_psd_rows(afg_ctx *ctx, const float *const *rows_dev, int n_rows, int64_t psd_span, double *psd,
+                    cudaStream_t st) {
+    if (n_rows <= 0) return AFG_OK;
+    const int hop = ctx->cfg.hop;
+    const int64_t K = (psd_span - NFFT) / hop + 1;
+    double *P = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_PERIODOGRAM, (size_t)n_rows * K * NBIN * sizeof(double), (void **)&P);
+    if (rc) return rc;
+    {
+        KScope ks(ctx, st, KK_PERIODOGRAM, 0.0, (double)n_rows * K * (NFFT * 4.0 + NBIN * 8.0));
+        k_periodogram<<<dim3((unsigned)K, (unsigned)n_rows), r16::NT, WELCH_SMEM, st>>>(nullptr, 0, hop, P, K,
+                                                                                        rows_dev);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_periodogram");
+    const double scale = 1.0 / ((double)K * (double)ctx->cfg.fs * (3.0 * NFFT / 8.0));
+    {
+        KScope ks(ctx, st, KK_PSD_MEAN, 0.0, (double)n_rows * (K + 1) * NBIN * 8.0);
+        k_psd_mean<<<dim3((NBIN + 255) / 256, 1, (unsigned)n_rows), 256, 0, st>>>(P, K, 0, (int)K, scale, psd, 1);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_psd_mean");
+    return AFG_OK;
+}
+
+// grid (n_rows): row r of src [n_rows][len] to dst_dev[r] (device array of n_rows pointers)
+__global__ void k_scatter_rows(const float *__restrict__ src, float *const *__restrict__ dst, int len) {
+    const float *s = src + (int64_t)blockIdx.x * len;
+    float *d = dst[blockIdx.x];
+    for (int i = threadIdx.x; i < len; i += blockDim.x) d[i] = s[i];
+}
+
+int launch_scatter_rows(afg_ctx *ctx, const float *src, float *const *dst_dev, int n_rows, int len, cudaStream_t st) {
+    if (n_rows <= 0) return AFG_OK;
+    k_scatter_rows<<<n_rows, 256, 0, st>>>(src, dst_dev, len);
+    AFG_LAUNCH_CHECK(ctx, "k_scatter_rows");
+    return AFG_OK;
+}
+
 int launch_whiten_multi(afg_ctx *ctx, const WhitenPiece *pieces_dev, int n_pieces, int64_t total_out,
                         cudaStream_t st) {
     if (n_pieces <= 0) return AFG_OK;
@@ -754,7 +796,7 @@ cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, i
     const int64_t K = (psd_span - NFFT) / hop + 1;
     const int64_t seg_step = n_psd > 1 ? psd_step / hop : 0;
     const int64_t n_seg = (n_psd - 1) * seg_step + K;
-    k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, n, hop, P, n_seg);
+    k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, n, hop, P, n_seg, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const double scale = 1.0 / ((double)K * (double)fs * (3.0 * NFFT / 8.0));

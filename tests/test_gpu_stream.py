@@ -260,3 +260,54 @@ def test_stream_refuses_nan_and_closed_streams(weights):
         ctx.stream_push(sid, np.zeros((2, 64), dtype=np.float32))
     assert e.value.status == -6
     ctx.close()
+
+
+def test_stream_push_many_matches_single_pushes(weights):
+    """afg_stream_push_many (a burst of arrivals in one call) queues the same chunks as single
+    pushes in the same order: three streams pushed one round of 0.25 s chunks per call give the
+    same windows, and logits and statistics within the mix tolerance, as single round-robin pushes;
+    the tickets count each stream's pushes.  A burst with a non-finite sample or a closed stream is
+    refused whole: nothing of it is queued (the next ticket continues the count)."""
+    xs = [_strain(72.0, 60 + i) for i in range(3)]
+    warm = 67 * WL.fs
+
+    def run(many):
+        ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
+        ctx.stream_start(max_streams=4)
+        sids = [ctx.stream_open() for _ in xs]
+        for sid, x in zip(sids, xs):
+            _push_all(ctx, sid, x[:, :warm], chunk=4096)
+        ctx.stream_flush()
+        first = warm // 4096 + (1 if warm % 4096 else 0)
+        for r, a in enumerate(range(warm, xs[0].shape[1], 512)):
+            if many:
+                t = ctx.stream_push_many(sids, np.stack([x[:, a:a + 512] for x in xs]))
+                assert t.tolist() == [first + r] * len(sids)
+            else:
+                for sid, x in zip(sids, xs):
+                    ctx.stream_push(sid, x[:, a:a + 512])
+        ctx.stream_flush()
+        out = [ctx.stream_poll(sid) for sid in sids]
+        if many:
+            nxt = first + len(range(warm, xs[0].shape[1], 512))
+            bad = np.zeros((3, 2, 64), dtype=np.float32)
+            bad[2, 1, 7] = np.inf
+            with pytest.raises(abi.AfgError) as e:
+                ctx.stream_push_many(sids, bad)
+            assert e.value.status == -7
+            ctx.stream_close(sids[1])
+            with pytest.raises(abi.AfgError) as e:
+                ctx.stream_push_many(sids, np.zeros((3, 2, 64), dtype=np.float32))
+            assert e.value.status == -6
+            # nothing of either refused burst was queued
+            assert ctx.stream_push(sids[0], np.zeros((2, 64), dtype=np.float32)) == nxt
+        ctx.close()
+        return out
+
+    single, many = run(False), run(True)
+    for i in range(len(xs)):
+        assert len(many[i]) == len(single[i]) > 0
+        assert np.array_equal(many[i]["window"], single[i]["window"])
+        for key in ("logit", "stat"):
+            d = np.abs(many[i][key] - single[i][key]) / (1 + np.abs(single[i][key]))
+            assert d.max() <= MIX_TOL, (i, key, d.max())
