@@ -502,7 +502,7 @@ void conv_launch(afg_ctx *ctx, const float *in, const float *wt, float *out, int
 // K = k * Cin is a multiple of 16 for every convolution of the networks (Cin >= 16)
 void conv_dispatch(afg_ctx *ctx, const float *in, float *out, int nw, const ConvLayer &L, cudaStream_t st) {
     if (L.cout % 128 == 0) conv_launch<128, 128, 8, 8, 16>(ctx, in, L.wt, out, nw, L, st);
-    else if (L.cout % 64 == 0) conv_launch<128, 64, 8, 4, 16>(ctx, in, L.wt, out, nw, L, st);
+    else if (L.cout % 64 == 0) conv_launch<256, 64, 8, 8, 16>(ctx, in, L.wt, out, nw, L, st);  // 8 x 8 per thread too
     else conv_launch<256, 16, 4, 4, 16>(ctx, in, L.wt, out, nw, L, st);
 }
 
