@@ -150,3 +150,80 @@ def test_batch_shift_ranges_concatenate(batch_case):
     with pytest.raises(abi.AfgError):  # the largest timeslide must fit the shortest segment
         ctx.batch_layout(segs, 1, SHIFT_STEP, shift_first=10 ** 6)
     ctx.close()
+
+
+def _series_slices(n_win, n_shift, n_int):
+    """(logit, statistic) start offsets of every (segment, timeslide) series, in series order."""
+    lo = so = 0
+    out = {}
+    for i, nw in enumerate(n_win):
+        for k in range(n_shift):
+            out[(i, k)] = (lo, so, nw, nw - n_int + 1)
+            lo += nw
+            so += nw - n_int + 1
+    return out
+
+
+def test_batch_full_day_sampled(capsys):
+    """The batching workload at its full size, in the configuration the bench times: 40 uneven
+    segments (about 1 day) x 100 timeslides of 1 s in one persistent launch, BF16.  At this size
+    the oracle checks samples and the rest is checked by properties that hold at any size:
+    * series of the two shortest segments at timeslides 1, 2, 50 and 100, recomputed as small
+      batches (shift_first ranges), are bit-identical to the same series of the full launch;
+    * 16 windows of each of those series, spread over the series, match the oracle's logits
+      (whitening of the segment on its own, then the network) within the BF16 tolerance;
+    * each sampled series' statistic is the 1 s moving average of its logits, and its triggers
+      are exactly the clustering of its own statistic."""
+    wl = inputs.TIMESLIDE_DAY
+    n_shift, step = 100, wl.fs
+    lengths = inputs.segment_lengths(n_seg=40, total_s=86400)
+    x, segs = inputs.make_segments(lengths, seed=wl.seed, chirp_every_s=300.0, workers=16)
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
+    xd = torch.from_numpy(x).cuda()
+    n_win, tw, ts = ctx.batch_layout(segs, n_shift, step)
+    lg, st, tr, nt = [t.cpu().numpy() for t in ctx.batch_run(xd, segs, n_shift, step)]
+    ctx.sync()
+    assert len(lg) == tw == sum(n_win) * n_shift and len(st) == ts
+    tr = tr[: int(nt[0])]
+    assert np.all(np.diff(tr) > 0)
+    sl = _series_slices(n_win, n_shift, wl.n_int)
+    picks = sorted(range(len(segs)), key=lambda i: segs[i][1])[:2]
+    sub_segs = [segs[i] for i in picks]
+    sub_n_win, _, _ = ctx.batch_layout(sub_segs, 1, step)
+    worst, checked = 0.0, 0
+    rng = np.random.default_rng(5)
+    for j, i in enumerate(picks):
+        off, n = segs[i]
+        xs = x[:, off:off + n].astype(np.float64)
+        eps = list(range((n - wl.psd_len - wl.crop) // wl.epoch_len))
+        white = orc.whiten(xs, wl, orc.psd_epochs(xs, wl, eps), eps)
+        for k_first, n_k in ((1, 2), (50, 1), (100, 1)):
+            s_lg, s_st, s_tr, s_nt = [t.cpu().numpy() for t in
+                                      ctx.batch_run(xd, sub_segs, n_k, step, shift_first=k_first)]
+            s_tr = s_tr[: int(s_nt[0])]
+            s_sl = _series_slices(sub_n_win, n_k, wl.n_int)
+            for kk in range(n_k):
+                k = k_first + kk
+                lo, so, nw, ns = sl[(i, k - 1)]
+                a_lo, a_so, a_nw, a_ns = s_sl[(j, kk)]
+                assert (a_nw, a_ns) == (nw, ns) == (n_win[i], n_win[i] - wl.n_int + 1)
+                z, s = lg[lo:lo + nw], st[so:so + ns]
+                assert np.array_equal(z, s_lg[a_lo:a_lo + nw]) and np.array_equal(s, s_st[a_so:a_so + ns])
+                mine = tr[(tr >= so) & (tr < so + ns)] - so
+                assert np.array_equal(mine, s_tr[(s_tr >= a_so) & (s_tr < a_so + ns)] - a_so)
+                # properties: the statistic is the moving average of the logits; the triggers cluster it
+                ma = np.convolve(z.astype(np.float64), np.ones(wl.n_int) / wl.n_int, mode="valid")
+                assert np.max(np.abs(s - ma) / (1 + np.abs(ma))) < 1e-5
+                assert np.array_equal(orc.triggers(s.astype(np.float64), wl.cluster_half), mine)
+                # sampled windows against the oracle
+                for w0 in sorted(rng.choice(nw, size=16, replace=False).tolist()):
+                    ref = orc.infer_windows(wl.net, w, white, wl.win_len, w0 * wl.stride, wl.stride, 1, k * step)
+                    e = abs(float(z[w0]) - float(ref[0])) / (1 + abs(float(ref[0])))
+                    worst = max(worst, e)
+                    checked += 1
+                    assert e < BF16_LOGIT_TOL, (i, k, w0, e)
+    with capsys.disabled():
+        print(f"\nfull-day batch: {tw} windows, {len(tr)} triggers; {checked} sampled windows of "
+              f"{len(picks)} segments x 4 timeslides vs the oracle, max |dz|/(1+|z|) = {worst:.3e}")
+    ctx.close()
