@@ -311,3 +311,44 @@ def test_stream_push_many_matches_single_pushes(weights):
         for key in ("logit", "stat"):
             d = np.abs(many[i][key] - single[i][key]) / (1 + np.abs(single[i][key]))
             assert d.max() <= MIX_TOL, (i, key, d.max())
+
+
+def test_stream_128_streams_sampled(weights, capsys):
+    """The serving configuration at its full size: 128 streams (max_streams = 128), staggered so that
+    their PSD refreshes fall in different steps and several share one batched refresh, then 0.25 s
+    chunks of every stream per afg_stream_push_many burst.  Every stream delivers exactly its windows'
+    statistics (windows n_int - 1 .. n_win - 1, finite), and four sampled streams match the oracle's
+    streaming analysis within the BF16 tolerance."""
+    n_streams = 128
+    rng = np.random.default_rng(7)
+    lead = [64.0 + 0.25 * int(rng.integers(0, 32)) for _ in range(n_streams)]  # staggered warm-up
+    tail_s = 12.0
+    xs = [_strain(lead[i] + tail_s, 300 + i) for i in range(n_streams)]
+    ctx = abi.Context(WL, weights, precision=abi.AFG_BF16)
+    ctx.stream_start(max_streams=n_streams, max_chunk=4096)
+    sids = [ctx.stream_open() for _ in range(n_streams)]
+    for sid, x, l in zip(sids, xs, lead):
+        _push_all(ctx, sid, x[:, :int(l * WL.fs)], chunk=4096)
+    for a in range(0, int(tail_s * WL.fs), 512):
+        ctx.stream_push_many(sids, np.stack([x[:, int(l * WL.fs) + a:int(l * WL.fs) + a + 512]
+                                             for x, l in zip(xs, lead)]))
+    ctx.stream_flush(120.0)
+    res = [ctx.stream_poll(sid) for sid in sids]
+    for x, r in zip(xs, res):
+        q = x.shape[1] - WL.psd_len - WL.crop + 1
+        n_win = (q - WL.win_len) // WL.stride + 1
+        assert np.array_equal(r["window"], np.arange(WL.n_int - 1, n_win))
+        assert np.all(np.isfinite(r["stat"])) and np.all(np.isfinite(r["logit"]))
+    worst = 0.0
+    for i in (0, 37, 85, 127):
+        z, st, _ = _oracle_stream(xs[i], weights)
+        r = res[i]
+        err = max(float(np.max(np.abs(r["logit"] - z[WL.n_int - 1:]) / (1 + np.abs(z[WL.n_int - 1:])))),
+                  float(np.max(np.abs(r["stat"] - st) / (1 + np.abs(st)))))
+        worst = max(worst, err)
+        assert err < BF16_LOGIT_TOL, (i, err)
+    stats = ctx.stream_stats()
+    with capsys.disabled():
+        print(f"\n128 streams: {sum(len(r) for r in res)} results in {stats['steps']} steps; "
+              f"4 sampled streams vs the oracle, max |dz|/(1+|z|) = {worst:.3e}")
+    ctx.close()
