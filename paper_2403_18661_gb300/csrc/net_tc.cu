@@ -943,12 +943,25 @@ __host__ __device__ inline PipeSmem pipe_smem(int W, int n_conv, int k_stem) {
     s.off_p = s.off_w + (size_t)n_conv * TF_WIMG + TP_STEM_IMG;
     s.off_s = s.off_p + (((size_t)tiny_param_count(k_stem, n_conv) * 4 + 15) / 16) * 16;
     s.off_r = s.off_s + 2 * TF_C * 4;
-    // reduction scratch: two halves (layer parity) of [TP_EPI_WARPS][32] floats + a stop flag, then the head's
-    s.off_bar = s.off_r + (size_t)(3 * TP_EPI_RED) * 4;
+    // reduction scratch: two halves (layer parity) of [TP_EPI_WARPS][32] floats + a stop flag, then the head's,
+    // then per epilogue warp the 16 scales and 16 shifts of the current GroupNorm
+    s.off_bar = s.off_r + (size_t)(3 * TP_EPI_RED + TP_EPI_WARPS * 32) * 4;
     // mma_done[TP_MT_MAX], rows_ready[TP_MT_MAX] (per unit; the first MT / 2 used), drain, then the
     // tmem slot, abort flag, stop flag
     s.total = s.off_bar + (2 * TP_MT_MAX + 1) * 8 + 16;
     return s;
+}
+
+// Per-channel (sum, sum of squares) of one position's 16 accumulators, adjacent channels as packed pairs
+// (the loaded registers are the FP32x2 operands as they are: no register moves).
+__device__ __forceinline__ void acc_channel_pairs(const uint32_t (&r)[16], float2 (&s2)[TF_C / 2],
+                                                  float2 (&q2)[TF_C / 2]) {
+#pragma unroll
+    for (int i = 0; i < TF_C / 2; ++i) {
+        const float2 v = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        s2[i] = __fadd2_rn(s2[i], v);
+        q2[i] = __ffma2_rn(v, v, q2[i]);
+    }
 }
 
 // GroupNorm reduction over the epilogue warps, one named barrier (id 1): per-thread group sums
@@ -958,8 +971,8 @@ __host__ __device__ inline PipeSmem pipe_smem(int W, int n_conv, int k_stem) {
 // next layer's sums into the other half, and cannot get two layers ahead past the barrier.
 template <int G>
 __device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, float eps, const float *gamma,
-                                              const float *beta, float *red, float (&sc)[TF_C], float (&sh)[TF_C],
-                                              const volatile int *abort_flag, bool &stop) {
+                                              const float *beta, float *red, float *maps, float (&sc)[TF_C],
+                                              float (&sh)[TF_C], const volatile int *abort_flag, bool &stop) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NV = 2 * G;
     float v[NV];
@@ -984,11 +997,22 @@ __device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, 
     const float mean = s_g / cnt;
     const float a = rsqrtf(fmaxf(q_g / cnt - mean * mean, 0.f) + eps) * gamma[c];
     const float b = beta[c] - mean * a;
-#pragma unroll
-    for (int i = 0; i < TF_C; ++i) {
-        sc[i] = __shfl_sync(0xffffffffu, a, i);
-        sh[i] = __shfl_sync(0xffffffffu, b, i);
+    // the 16 maps to every lane through the warp's own slot (broadcast loads, adjacent pairs aligned for
+    // the packed normalisation)
+    float *mw = maps + warp * 32;
+    if (lane < TF_C) {
+        mw[lane] = a;
+        mw[TF_C + lane] = b;
     }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < TF_C; i += 4) {
+        const float4 va = *reinterpret_cast<const float4 *>(mw + i);
+        const float4 vb = *reinterpret_cast<const float4 *>(mw + TF_C + i);
+        sc[i] = va.x; sc[i + 1] = va.y; sc[i + 2] = va.z; sc[i + 3] = va.w;
+        sh[i] = vb.x; sh[i + 1] = vb.y; sh[i + 2] = vb.z; sh[i + 3] = vb.w;
+    }
+    __syncwarp();  // (the slot is rewritten at the next layer only after every lane has read it)
     stop = *stop_slot != 0;
 }
 
@@ -1119,7 +1143,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 const bool rdy = lane >= NU || tc::mbar_test_wait(&rows_ready[lane], par);
                 const unsigned m = __ballot_sync(0xffffffffu, rdy);
                 ready = m == 0xffffffffu ? 32 : __ffs(~m) - 1;
-                if (ready < need && !tc::mbar_wait_warp(&rows_ready[ready], par, TP_WAIT_NS, 0u)) {
+                if (ready < need && !tc::mbar_spin_warp(&rows_ready[ready], par, TP_WAIT_NS)) {
                     ok = false;
                     ready = NU;
                 }
@@ -1218,35 +1242,36 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 const bool res = k > 0 && (l & 1);  // second conv of a block: residual from A
                 unsigned char *dst = (k == 0 || (l & 1)) ? actA : actB;
                 const float *gam = k == 0 ? stem_g : conv_gb + l * 2 * TF_C;
-                // ---- statistics pass: each subtile as soon as its MMAs are done
-                float2 sq[G];
+                // ---- statistics pass: each subtile as soon as its MMAs are done; per-channel sums and sums
+                // of squares of adjacent channel pairs as packed FP32x2 adds and FMAs on the loaded registers
+                float2 s2[TF_C / 2], q2[TF_C / 2];
 #pragma unroll
-                for (int g = 0; g < G; ++g) sq[g] = make_float2(0.f, 0.f);
+                for (int i = 0; i < TF_C / 2; ++i) s2[i] = q2[i] = make_float2(0.f, 0.f);
                 bool ok = true;
                 for (int u = q; 2 * u < MT; u += TP_NQ) {
                     const int j0 = 2 * u, j1 = j0 + 1;
                     uint32_t r0[16], r1[16];
                     // (after a failed wait the rest are skipped: the MMA warp has stopped)
-                    if (ok) ok = tc::mbar_wait_warp(&mma_done[u], par, TP_WAIT_NS);
+                    if (ok) ok = tc::mbar_wait_warp_tested(&mma_done[u], par, TP_WAIT_NS);
                     tc::fence_after_sync();
                     tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
                     if (j1 < MT) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
                     tc::tmem_wait_ld();
                     tc::tmem_regs_ready(r0);
                     tc::tmem_regs_ready(r1);
+                    acc_channel_pairs(r0, s2, q2);
+                    if (j1 < MT) acc_channel_pairs(r1, s2, q2);
+                }
+                float2 sq[G];  // (sum, sum of squares) per group
 #pragma unroll
-                    for (int c = 0; c < TF_C; ++c) {
-                        const float v = __uint_as_float(r0[c]);
-                        sq[c / (TF_C / G)] = __ffma2_rn(make_float2(v, v), make_float2(1.f, v), sq[c / (TF_C / G)]);
-                    }
-                    if (j1 < MT) {
+                for (int g = 0; g < G; ++g) {
+                    float s = 0.f, qq = 0.f;
 #pragma unroll
-                        for (int c = 0; c < TF_C; ++c) {
-                            const float v = __uint_as_float(r1[c]);
-                            sq[c / (TF_C / G)] =
-                                __ffma2_rn(make_float2(v, v), make_float2(1.f, v), sq[c / (TF_C / G)]);
-                        }
+                    for (int c = g * (TF_C / G); c < (g + 1) * (TF_C / G); ++c) {
+                        s += (c & 1) ? s2[c >> 1].y : s2[c >> 1].x;
+                        qq += (c & 1) ? q2[c >> 1].y : q2[c >> 1].x;
                     }
+                    sq[g] = make_float2(s, qq);
                 }
                 if (!ok) {
                     atomicExch(args.err, 1);
@@ -1254,8 +1279,8 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 }
                 float sc[TF_C], sh[TF_C];
                 bool stop_now = false;
-                gn_reduce_epi<G>(sq, cnt, args.eps, gam, gam + TF_C, red + (seq & 1) * TP_EPI_RED, sc, sh, abort_flag,
-                                 stop_now);
+                gn_reduce_epi<G>(sq, cnt, args.eps, gam, gam + TF_C, red + (seq & 1) * TP_EPI_RED, red + 3 * TP_EPI_RED,
+                                 sc, sh, abort_flag, stop_now);
                 if (stop_now) {
                     stopped = true;
                     break;

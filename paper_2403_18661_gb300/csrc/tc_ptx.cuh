@@ -95,6 +95,33 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, u
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+// mbar_wait_warp for waits that have usually completed already: lane 0 first tests the phase without
+// blocking (a blocking try_wait costs its latency even on a completed phase), then polls with
+// try_wait, suspending up to 200 ns per poll, until timeout_ns.
+__device__ __forceinline__ bool mbar_wait_warp_tested(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
+    uint32_t ok = 1;
+    if ((threadIdx.x & 31) == 0 && !mbar_test_wait(bar, parity) && !mbar_try_wait_suspend(bar, parity, 200u)) {
+        const uint64_t t0 = globaltimer_ns();
+        while (!(ok = mbar_try_wait_suspend(bar, parity, 200u)))
+            if (globaltimer_ns() - t0 > timeout_ns) break;
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// A warp spins on the non-blocking test until the phase completes (latency-critical waits):
+// lane 0 polls, reading the clock for the timeout only every 64 polls; same result in every lane.
+__device__ __forceinline__ bool mbar_spin_warp(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
+    uint32_t ok = 1;
+    if ((threadIdx.x & 31) == 0 && !mbar_test_wait(bar, parity)) {
+        const uint64_t t0 = globaltimer_ns();
+        for (uint32_t i = 1;; ++i) {
+            if ((ok = mbar_test_wait(bar, parity))) break;
+            if ((i & 63) == 0 && globaltimer_ns() - t0 > timeout_ns) break;
+        }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
