@@ -928,6 +928,7 @@ constexpr int TP_THREADS = TP_EPI + 32 * TP_MMA_WARPS;
 constexpr int TP_MT_MAX = 32;
 constexpr int TP_STEM_IMG = 512;  // BF16 image of the stem weights: 16 channels x K = 16
 constexpr uint64_t TP_WAIT_NS = 1000000000ull;
+constexpr uint32_t TP_SPIN_NS = 32;  // issue warps: sleep between polls of an incomplete barrier
 constexpr int TP_EPI_RED = TP_EPI_WARPS * 32 + 32;  // floats of one reduction scratch
 
 struct PipeSmem {
@@ -1062,11 +1063,15 @@ __device__ __forceinline__ void tiny_emit(const TinyArgs &args, int64_t out, flo
     }
 }
 
-template <int G>
+// MTS: the window's subtiles as a compile-time constant (0: from args.W); with a constant that is even
+// and whose units divide evenly among the quads and issue warps, every loop over units has a fixed
+// trip count and no partial unit
+template <int G, int MTS = 0>
 __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args) {
     extern __shared__ __align__(1024) unsigned char sm[];
     pdl_trigger();
-    const int W = args.W, n_conv = args.n_conv, MT = W / 128, k_stem = args.k_stem;
+    constexpr bool FIXED = MTS > 0 && MTS % 2 == 0 && (MTS / 2) % TP_NQ == 0 && (MTS / 2) % TP_MMA_WARPS == 0;
+    const int W = MTS > 0 ? 128 * MTS : args.W, n_conv = args.n_conv, MT = W / 128, k_stem = args.k_stem;
     const PipeSmem L = pipe_smem(W, n_conv, k_stem);
     unsigned char *actA = sm + L.off_a;
     unsigned char *actB = sm + L.off_b;
@@ -1143,22 +1148,25 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 const bool rdy = lane >= NU || tc::mbar_test_wait(&rows_ready[lane], par);
                 const unsigned m = __ballot_sync(0xffffffffu, rdy);
                 ready = m == 0xffffffffu ? 32 : __ffs(~m) - 1;
-                if (ready < need && !tc::mbar_spin_warp(&rows_ready[ready], par, TP_WAIT_NS)) {
+                if (ready < need && !tc::mbar_spin_warp(&rows_ready[ready], par, TP_WAIT_NS, TP_SPIN_NS)) {
                     ok = false;
                     ready = NU;
                 }
             }
             tc::fence_after_sync();
         };
+        // this warp's i-th unit of a layer, and its count
+        const int n_mu = FIXED ? NU / TP_MMA_WARPS : (NU - mw + TP_MMA_WARPS - 1) / TP_MMA_WARPS;
         for (int64_t win = win0; win < args.n_win; win += win_step) {
             {   // stem: one K = 16 MMA per subtile over the im2col tile
                 const uint32_t par = seq & 1;
                 int ready = ok ? 0 : NU;
-                for (int u = mw; u < NU; u += TP_MMA_WARPS) {
+                for (int i = 0; i < n_mu; ++i) {
+                    const int u = mw + TP_MMA_WARPS * i;
                     wait_rows(ready, u + 1, par);
                     const int j0 = 2 * u;
                     tc::mma_bf16_elect(tmem + (uint32_t)(j0 * TF_C), d_stem_a + (uint64_t)(128 * j0), d_stem_b, idesc, 0u);
-                    if (j0 + 1 < MT)
+                    if (FIXED || j0 + 1 < MT)
                         tc::mma_bf16_elect(tmem + (uint32_t)((j0 + 1) * TF_C), d_stem_a + (uint64_t)(128 * (j0 + 1)),
                                            d_stem_b, idesc, 0u);
                     tc::mma_commit_elect(&mma_done[u]);
@@ -1170,7 +1178,8 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 const uint64_t ad = (l & 1) ? d_b : d_a;  // the second conv of a block reads B
                 const uint64_t bd = d_w + (uint64_t)(l * (TF_WIMG / 16));
                 int ready = ok ? 0 : NU;
-                for (int u = mw; u < NU; u += TP_MMA_WARPS) {
+                for (int i = 0; i < n_mu; ++i) {
+                    const int u = mw + TP_MMA_WARPS * i;
                     wait_rows(ready, min(u + 2, NU), par);
                     const int j0 = 2 * u;
                     const uint64_t a0 = ad + (uint64_t)(128 * j0);
@@ -1178,7 +1187,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                     tc::mma_bf16_elect(t0, a0, bd, idesc, 0u);
                     tc::mma_bf16_elect(t0, a0 + 1, bd + 32, idesc, 1u);
                     tc::mma_bf16_elect(t0, a0 + 2, bd + 64, idesc, 1u);
-                    if (j0 + 1 < MT) {
+                    if (FIXED || j0 + 1 < MT) {
                         tc::mma_bf16_elect(t0 + TF_C, a0 + 128, bd, idesc, 0u);
                         tc::mma_bf16_elect(t0 + TF_C, a0 + 129, bd + 32, idesc, 1u);
                         tc::mma_bf16_elect(t0 + TF_C, a0 + 130, bd + 64, idesc, 1u);
@@ -1210,6 +1219,8 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
         unsigned char *im2col = actB + act_chunk + 16;       // stem im2col tile, [W][16 B]
         const int RP = W + 8;
         uint32_t seq = 0;
+        // this quad's i-th unit is u = q + TP_NQ i, i < n_qu
+        const int n_qu = FIXED ? (MT / 2) / TP_NQ : ((MT + 1) / 2 - q + TP_NQ - 1) / TP_NQ;
         WinLoc cur = locate_window(args, win0, segs);
         if (win0 < args.n_win) load_window(args, cur, xs, W, 1, true, TP_EPI);
         for (int64_t win = win0; win < args.n_win; win += win_step) {
@@ -1218,8 +1229,9 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
             asm volatile("cp.async.wait_all;" ::: "memory");
             tc::named_bar_sync(1, TP_EPI);
             // ---- stem im2col rows of this quad's units (BF16, six taps per 16-byte row)
-            for (int u = q; 2 * u < MT; u += TP_NQ) {
-                for (int j = 2 * u; j < min(2 * u + 2, MT); ++j) {
+            for (int i = 0; i < n_qu; ++i) {
+                const int u = q + TP_NQ * i;
+                for (int j = 2 * u; j < (FIXED ? 2 * u + 2 : min(2 * u + 2, MT)); ++j) {
                     const int t = 128 * j + 32 * lq + lane;
                     const float *p0 = xs + 4 + t - 1, *p1 = xs + RP + 4 + t - 1;
                     const uint4 row = make_uint4(tc::pack_bf16x2(p0[0], p0[1]), tc::pack_bf16x2(p0[2], p1[0]),
@@ -1248,19 +1260,21 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
 #pragma unroll
                 for (int i = 0; i < TF_C / 2; ++i) s2[i] = q2[i] = make_float2(0.f, 0.f);
                 bool ok = true;
-                for (int u = q; 2 * u < MT; u += TP_NQ) {
+                for (int i = 0; i < n_qu; ++i) {
+                    const int u = q + TP_NQ * i;
                     const int j0 = 2 * u, j1 = j0 + 1;
+                    const bool two = FIXED || j1 < MT;
                     uint32_t r0[16], r1[16];
                     // (after a failed wait the rest are skipped: the MMA warp has stopped)
                     if (ok) ok = tc::mbar_wait_warp_tested(&mma_done[u], par, TP_WAIT_NS);
                     tc::fence_after_sync();
                     tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), r0);
-                    if (j1 < MT) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
+                    if (two) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), r1);
                     tc::tmem_wait_ld();
                     tc::tmem_regs_ready(r0);
                     tc::tmem_regs_ready(r1);
                     acc_channel_pairs(r0, s2, q2);
-                    if (j1 < MT) acc_channel_pairs(r1, s2, q2);
+                    if (two) acc_channel_pairs(r1, s2, q2);
                 }
                 float2 sq[G];  // (sum, sum of squares) per group
 #pragma unroll
@@ -1292,9 +1306,10 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                     load_window(args, cur, xs, W, 1, true, TP_EPI);
                 }
                 // ---- normalise pass (+ residual) + ReLU -> BF16 rows of dst, or the pooled sums
-                for (int u = q; 2 * u < MT; u += TP_NQ) {
+                for (int i = 0; i < n_qu; ++i) {
+                    const int u = q + TP_NQ * i;
                     const int j0 = 2 * u, j1 = j0 + 1;
-                    const bool two = j1 < MT;
+                    const bool two = FIXED || j1 < MT;
                     uint32_t ra[16], rb[16];
                     tc::tmem_ld16_nowait(tq + (uint32_t)(j0 * TF_C), ra);
                     if (two) tc::tmem_ld16_nowait(tq + (uint32_t)(j1 * TF_C), rb);
@@ -1395,6 +1410,29 @@ bool tiny_compatible(const afg_ctx *ctx) {
 // batch segment descriptors the pipelined kernel keeps in shared memory after its layout
 __host__ inline int pipe_seg_cache_cap(size_t total) { return tiny_seg_cache_cap(total); }
 
+// subtiles of the 1.5 s window at 2048 Hz (3072 positions): compiled with a fixed geometry
+constexpr int TP_MT_FIXED = 24;
+
+template <int G, int MTS>
+cudaError_t launch_pipe_t(const TinyArgs &a, unsigned grid, size_t smem, cudaStream_t st, bool pdl) {
+    if (pdl) return launch_pdl(k_tiny_pipe<G, MTS>, dim3(grid), dim3(TP_THREADS), smem, st, a);
+    k_tiny_pipe<G, MTS><<<grid, TP_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// The pipelined network over a.n_win windows; the fixed-geometry build for 8 groups and 3072 positions
+cudaError_t launch_pipe(const TinyArgs &a, unsigned grid, size_t smem, cudaStream_t st, bool pdl) {
+    switch (a.G) {
+        case 1: return launch_pipe_t<1, 0>(a, grid, smem, st, pdl);
+        case 2: return launch_pipe_t<2, 0>(a, grid, smem, st, pdl);
+        case 4: return launch_pipe_t<4, 0>(a, grid, smem, st, pdl);
+        case 8:
+            return a.W == 128 * TP_MT_FIXED ? launch_pipe_t<8, TP_MT_FIXED>(a, grid, smem, st, pdl)
+                                            : launch_pipe_t<8, 0>(a, grid, smem, st, pdl);
+        default: return launch_pipe_t<16, 0>(a, grid, smem, st, pdl);
+    }
+}
+
 }  // namespace
 
 // Build the fused kernel's parameter block and BF16 weight image (device).
@@ -1458,6 +1496,7 @@ int net_tc_prepare(afg_ctx *ctx) {
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8, TP_MT_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
     if (ctx->cfg.win_len % (128 * TF_CLUSTER) == 0) {  // list mode on clusters: a quarter window per CTA
         const int smem_c = (int)tiny_smem(ctx->cfg.win_len / TF_CLUSTER, n_conv, k).total + TF_XCH;
         AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<1, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1511,14 +1550,8 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     const unsigned grid = (unsigned)std::min<int64_t>(total_win, std::max(sms, 1));
     const double flops = 2.0 * total_win * W * TF_C * ((3.0 * TF_C) * n_conv + 2.0 * a.k_stem);
     KScope ks(ctx, st, KK_TINY_TC, flops, (double)total_win * (2.0 * W * 4.0 + 4.0));
-    switch (a.G) {
-        case 1: k_tiny_pipe<1><<<grid, TP_THREADS, smem, st>>>(a); break;
-        case 2: k_tiny_pipe<2><<<grid, TP_THREADS, smem, st>>>(a); break;
-        case 4: k_tiny_pipe<4><<<grid, TP_THREADS, smem, st>>>(a); break;
-        case 8: k_tiny_pipe<8><<<grid, TP_THREADS, smem, st>>>(a); break;
-        default: k_tiny_pipe<16><<<grid, TP_THREADS, smem, st>>>(a); break;
-    }
-    AFG_LAUNCH_CHECK(ctx, "k_tiny_pipe(batch)");
+    cudaError_t e = launch_pipe(a, grid, smem, st, false);
+    if (e != cudaSuccess) return afg_cuda_fail(ctx, e, "k_tiny_pipe(batch)");
     return AFG_OK;
 }
 
@@ -1571,14 +1604,7 @@ int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, 
         return AFG_OK;
     }
     const size_t psmem = pipe_smem(W, n_conv, a.k_stem).total;
-    switch (a.G) {
-        case 1: e = launch_pdl(k_tiny_pipe<1>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
-        case 2: e = launch_pdl(k_tiny_pipe<2>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
-        case 4: e = launch_pdl(k_tiny_pipe<4>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
-        case 8: e = launch_pdl(k_tiny_pipe<8>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
-        default: e = launch_pdl(k_tiny_pipe<16>, dim3(grid), dim3(TP_THREADS), psmem, st, a); break;
-    }
-    AFG_CUDA(ctx, e);
+    AFG_CUDA(ctx, launch_pipe(a, grid, psmem, st, true));
     return AFG_OK;
 }
 
@@ -1622,13 +1648,7 @@ int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
     const double flops_stem = 2.0 * n_win * W * TF_C * 2.0 * a.k_stem;
     KScope ks(ctx, st, KK_TINY_TC, flops_conv + flops_stem, (double)n_win * (2.0 * W * 4.0 + 4.0));
     const size_t psmem = pipe_smem(W, n_conv, a.k_stem).total;
-    switch (a.G) {
-        case 1: k_tiny_pipe<1><<<grid, TP_THREADS, psmem, st>>>(a); break;
-        case 2: k_tiny_pipe<2><<<grid, TP_THREADS, psmem, st>>>(a); break;
-        case 4: k_tiny_pipe<4><<<grid, TP_THREADS, psmem, st>>>(a); break;
-        case 8: k_tiny_pipe<8><<<grid, TP_THREADS, psmem, st>>>(a); break;
-        default: k_tiny_pipe<16><<<grid, TP_THREADS, psmem, st>>>(a); break;
-    }
-    AFG_LAUNCH_CHECK(ctx, "k_tiny_pipe");
+    cudaError_t e = launch_pipe(a, grid, psmem, st, false);
+    if (e != cudaSuccess) return afg_cuda_fail(ctx, e, "k_tiny_pipe");
     return AFG_OK;
 }

@@ -108,13 +108,16 @@ __device__ __forceinline__ bool mbar_wait_warp_tested(uint64_t *bar, uint32_t pa
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// A warp spins on the non-blocking test until the phase completes (latency-critical waits):
-// lane 0 polls, reading the clock for the timeout only every 64 polls; same result in every lane.
-__device__ __forceinline__ bool mbar_spin_warp(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
+// A warp polls the non-blocking test until the phase completes (latency-critical waits): lane 0
+// polls, sleeping about sleep_ns between polls (0: a pure spin) so that the waiting warp takes few
+// issue slots, and reads the clock for the timeout only every 64 polls; same result in every lane.
+__device__ __forceinline__ bool mbar_spin_warp(uint64_t *bar, uint32_t parity, uint64_t timeout_ns,
+                                               uint32_t sleep_ns = 0) {
     uint32_t ok = 1;
     if ((threadIdx.x & 31) == 0 && !mbar_test_wait(bar, parity)) {
         const uint64_t t0 = globaltimer_ns();
         for (uint32_t i = 1;; ++i) {
+            if (sleep_ns) __nanosleep(sleep_ns);
             if ((ok = mbar_test_wait(bar, parity))) break;
             if ((i & 63) == 0 && globaltimer_ns() - t0 > timeout_ns) break;
         }

@@ -302,6 +302,30 @@ def test_bf16_tiny_logits_against_oracle(c1, ctx_tiny_bf16, capsys):
         assert err.max() < BF16_LOGIT_TOL, err.max()
 
 
+@pytest.mark.parametrize("win_len,groups", [(1664, 8), (2048, 8), (3072, 4), (3072, 16)])
+def test_bf16_tiny_other_windows_and_groups(c1, win_len, groups, capsys):
+    """The fused 16-channel network away from the 1.5 s / 8-group configuration that has a compiled
+    fixed geometry: an odd number of 128-position subtiles (1664), 2048 positions, and 4 or 16
+    GroupNorm groups, against the oracle window by window (shifted L1, odd first sample)."""
+    import dataclasses
+    wl, x, _, ref = c1
+    net = dataclasses.replace(wl.net, groups=groups)
+    wv = dataclasses.replace(wl, win_len=win_len, net=net)
+    w = inputs.make_weights(net, 11)
+    ctx = abi.Context(wv, w, precision=abi.AFG_BF16)
+    white = ref["white"]
+    first, stride, shift = 3, 389, 2048 * 2 + 7
+    n_win = min(300, (white.shape[1] - win_len - first) // stride + 1)
+    got = ctx.infer_windows(_dev(white.astype(np.float32)), first, stride, n_win, shift).cpu().numpy()
+    ctx.sync()
+    ctx.close()
+    want = orc.infer_windows(net, w, white, win_len, first, stride, n_win, shift)
+    err = np.abs(got - want) / (1 + np.abs(want))
+    with capsys.disabled():
+        print(f"\nBF16 tiny net W {win_len} G {groups}: {n_win} windows, max |dz|/(1+|z|) = {err.max():.3e}")
+    assert err.max() < BF16_LOGIT_TOL, err.max()
+
+
 def test_bf16_precision_c1_trigger_list(c1, ctx_tiny_bf16, capsys):
     """Precision workload: the 64 s span through the BF16 network; the statistic within the
     BF16 tolerance and the trigger lists compared in both directions."""
