@@ -928,7 +928,7 @@ constexpr int TP_THREADS = TP_EPI + 32 * TP_MMA_WARPS;
 constexpr int TP_MT_MAX = 32;
 constexpr int TP_STEM_IMG = 512;  // BF16 image of the stem weights: 16 channels x K = 16
 constexpr uint64_t TP_WAIT_NS = 1000000000ull;
-constexpr uint32_t TP_SPIN_NS = 32;  // issue warps: sleep between polls of an incomplete barrier
+constexpr uint32_t TP_SPIN_NS = 64;  // issue warps: sleep between polls of an incomplete barrier
 constexpr int TP_EPI_RED = TP_EPI_WARPS * 32 + 32;  // floats of one reduction scratch
 
 struct PipeSmem {
@@ -1243,9 +1243,9 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&rows_ready[u]);
             }
-            float hs[TF_C];
+            float2 hs2[TF_C / 2];  // pooled sums of adjacent channel pairs (last layer)
 #pragma unroll
-            for (int c = 0; c < TF_C; ++c) hs[c] = 0.f;
+            for (int c = 0; c < TF_C / 2; ++c) hs2[c] = make_float2(0.f, 0.f);
             bool stopped = false;
             for (int k = 0; k <= n_conv; ++k, ++seq) {
                 const uint32_t par = seq & 1;
@@ -1339,8 +1339,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                                 for (int e = 0; e < 4; ++e) {
                                     const float2 y = __fadd2_rn(v[e], make_float2(__uint_as_float(w4[e] << 16),
                                                                                   __uint_as_float(w4[e] & 0xffff0000u)));
-                                    hs[ch * 8 + 2 * e] += fmaxf(y.x, 0.f);
-                                    hs[ch * 8 + 2 * e + 1] += fmaxf(y.y, 0.f);
+                                    hs2[ch * 4 + e] = __fadd2_rn(hs2[ch * 4 + e], make_float2(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f)));
                                 }
                             } else if (res) {
                                 // + the block's residual in FP32, ReLU folded into the BF16 conversion
@@ -1373,6 +1372,12 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
             if (stopped) break;
             // ---- head: global mean pool, then the linear layer
             float *hred = red + 2 * TP_EPI_RED;
+            float hs[TF_C];
+#pragma unroll
+            for (int c = 0; c < TF_C / 2; ++c) {
+                hs[2 * c] = hs2[c].x;
+                hs[2 * c + 1] = hs2[c].y;
+            }
             warp_reduce_scatter<TF_C>(hs, lane);  // lane 2c holds the warp's sum of channel c
             if (!(lane & 1)) hred[warp * 32 + (lane >> 1)] = hs[0];
             tc::named_bar_sync(1, TP_EPI);

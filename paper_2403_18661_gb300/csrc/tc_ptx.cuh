@@ -97,13 +97,15 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, u
 
 // mbar_wait_warp for waits that have usually completed already: lane 0 first tests the phase without
 // blocking (a blocking try_wait costs its latency even on a completed phase), then polls with
-// try_wait, suspending up to 200 ns per poll, until timeout_ns.
+// try_wait, suspending up to 200 ns per poll, and reads the clock for timeout_ns every 16 polls.
 __device__ __forceinline__ bool mbar_wait_warp_tested(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
     uint32_t ok = 1;
     if ((threadIdx.x & 31) == 0 && !mbar_test_wait(bar, parity) && !mbar_try_wait_suspend(bar, parity, 200u)) {
         const uint64_t t0 = globaltimer_ns();
-        while (!(ok = mbar_try_wait_suspend(bar, parity, 200u)))
-            if (globaltimer_ns() - t0 > timeout_ns) break;
+        for (uint32_t i = 1;; ++i) {
+            if ((ok = mbar_try_wait_suspend(bar, parity, 200u))) break;
+            if ((i & 15) == 0 && globaltimer_ns() - t0 > timeout_ns) break;
+        }
     }
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
