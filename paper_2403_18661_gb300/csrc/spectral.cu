@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restr
     for (int m = 1; m < 4; ++m) welch_mid_task(d, t + NT * m);
     if (t == NT - 1) welch_mid_task(d, 2048);
     __syncthreads();
-    // windowed bins k = t + 512 m (and NC), |X_k|^2 in FP64
+    // windowed bins k = t + 512 m (and NC) in registers, and the largest component magnitude of the block
     double *out = P + ((int64_t)det * n_seg + g) * NBIN;
     auto U = [&](int k) -> float2 {
         if (k < 0) return conj(d[pad(-k)]);
@@ -116,17 +116,51 @@ __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restr
         if (k > NC) return conj(d[pad(2 * NC - k)]);
         return d[pad(k)];
     };
-    auto p2 = [](float2 q) { return (double)q.x * (double)q.x + (double)q.y * (double)q.y; };
+    auto windowed = [&](int k) {
+        const float2 l = U(k - 1), c = U(k), r = U(k + 1);
+        return make_float2(0.5f * c.x - 0.25f * (l.x + r.x), 0.5f * c.y - 0.25f * (l.y + r.y));
+    };
+    float2 X[16];
+    float mx = 0.f;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        const int k = t + NT * m;
-        const float2 l = U(k - 1), c = U(k), r = U(k + 1);
-        out[k] = p2(make_float2(0.5f * c.x - 0.25f * (l.x + r.x), 0.5f * c.y - 0.25f * (l.y + r.y)));
+        X[m] = windowed(t + NT * m);
+        mx = fmaxf(mx, fmaxf(fabsf(X[m].x), fabsf(X[m].y)));
     }
+    float2 Xn = make_float2(0.f, 0.f);
     if (t == NT - 1) {
-        const float2 l = U(NC - 1), c = U(NC), r = U(NC + 1);
-        out[NC] = p2(make_float2(0.5f * c.x - 0.25f * (l.x + r.x), 0.5f * c.y - 0.25f * (l.y + r.y)));
+        Xn = windowed(NC);
+        mx = fmaxf(mx, fmaxf(fabsf(Xn.x), fabsf(Xn.y)));
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float *wmax = reinterpret_cast<float *>(u_nyq + 1);  // [NT / 32]
+    if ((t & 31) == 0) wmax[t >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) mx = fmaxf(mx, wmax[w]);
+    // |X_k|^2 = 2^-2s ((2^s X.re)^2 + (2^s X.im)^2): the power-of-two scale is exact and brings the largest
+    // component near 2^40, so the FP32 squares neither overflow nor underflow (strain spectra sit near
+    // 1e-19, whose squares are below FP32's range); the sum is rounded once in FP32 (relative 1.2e-7, far
+    // below the FP32 transform's own error) and rebuilt as the double with the exponent lowered by 2s, bit
+    // by bit, so no FP64 instruction runs here (the mean over segments is FP64).  NaN and infinity pass through.
+    int e = 0;
+    frexpf(mx, &e);
+    const int sc = min(40 - e, 120);
+    const float s2 = __int_as_float((127 + sc) << 23);  // 2^sc (sc >= -88)
+    const int ebias = 896 - 2 * sc;
+    auto p2 = [&](float2 q) -> double {
+        const float a = q.x * s2, b = q.y * s2;
+        const uint32_t u = __float_as_uint(fmaf(b, b, a * a));
+        const uint32_t E = u >> 23, m23 = u & 0x7FFFFFu;
+        if (E == 0) return 0.0;  // zero (or below 2^-126 of the scaled range)
+        if (E == 255) return __hiloint2double((int)(0x7FF00000u | (m23 ? 0x80000u : 0u)), 0);
+        return __hiloint2double((int)((uint32_t)((int)E + ebias) << 20 | (m23 >> 3)), (int)((m23 & 7u) << 29));
+    };
+#pragma unroll
+    for (int m = 0; m < 16; ++m) out[t + NT * m] = p2(X[m]);
+    if (t == NT - 1) out[NC] = p2(Xn);
 }
 
 // grid (ceil(NBIN/256), ceil(n_psd/PSD_EPT), n_det): bin k of epochs
@@ -140,14 +174,14 @@ __global__ void k_psd_mean(const double *__restrict__ P, int64_t n_seg, int seg_
     const int det = blockIdx.z;
     const double *src = P + (int64_t)det * n_seg * NBIN + k;
     double *dst = psd + (int64_t)det * n_psd * NBIN + k;
-    const double onesided = (k == 0 || k == NFFT / 2) ? 1.0 : 2.0;
+    const double f = (k == 0 || k == NFFT / 2) ? scale : 2.0 * scale;  // one-sided doubling and density scale
     double acc = 0.0;
     for (int q = 0; q < K; ++q) acc += src[(e0 * seg_step + q) * NBIN];
-    dst[e0 * NBIN] = onesided * acc * scale;
+    dst[e0 * NBIN] = acc * f;
     for (int64_t e = e0 + 1; e < e0 + PSD_EPT && e < n_psd; ++e) {
         const int64_t s_old = (e - 1) * seg_step, s_new = s_old + K;
         for (int q = 0; q < seg_step; ++q) acc += src[(s_new + q) * NBIN] - src[(s_old + q) * NBIN];
-        dst[e * NBIN] = onesided * acc * scale;
+        dst[e * NBIN] = acc * f;
     }
 }
 
@@ -393,7 +427,7 @@ __device__ __forceinline__ void whiten_mid_task0(const float2 *d, const float *g
 }
 
 constexpr int WHITEN_SMEM = r16::SLOTS * (int)sizeof(float2) + NBIN * (int)sizeof(float);
-constexpr int WELCH_SMEM = (r16::SLOTS + 1) * (int)sizeof(float2);
+constexpr int WELCH_SMEM = (r16::SLOTS + 1) * (int)sizeof(float2) + (r16::NT / 32) * (int)sizeof(float);
 
 // One overlap-save block: the FIR of src[0 .. WB + F - 1) (samples past
 // `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value).
