@@ -157,7 +157,9 @@ int afg_wait_check(afg_ctx *ctx, int64_t limit_ns, int32_t n_blocks, int64_t *wa
  * [0, n_psd): one-sided density of x[d][e*psd_step, e*psd_step + psd_span),
  * averaged (mean) over K = (psd_span - nfft)/hop + 1 segments of nfft
  * samples every hop samples, each multiplied by the periodic Hann window,
- * transformed with a real FFT in FP32 and squared and summed in FP64:
+ * transformed with a real FFT in FP32, squared in FP32 after an exact
+ * power-of-two scaling of the segment's spectrum (so that no square under- or
+ * overflows; relative rounding 1.2e-7) and summed in FP64:
  *   psd[d][e][k] = c_k / (K fs sum w^2) sum_s |X_s(k)|^2, k in [0, nfft/2],
  *   c_k = 1 for k = 0 and k = nfft/2, else 2.
  * x: [n_det][n] float32.  psd: [n_det][n_psd][nfft/2+1] float64.

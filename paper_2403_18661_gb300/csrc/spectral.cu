@@ -7,7 +7,8 @@
 //   k_periodogram     one Hann-windowed segment per CTA: FP32 real FFT in
 //                     shared memory (radix-16 passes, fft16.cuh), the window
 //                     applied to the spectrum (a three-bin convolution),
-//                     |X_k|^2 formed and stored in FP64
+//                     |X_k|^2 formed in FP32 after an exact power-of-two
+//                     scaling of the segment's spectrum, stored in FP64
 //   k_psd_mean        FP64 mean over the K segments of each epoch (a sliding
 //                     sum over a run of epochs per thread), density scaling
 //                     and one-sided doubling
@@ -73,7 +74,7 @@ __device__ __forceinline__ void welch_mid_task(float2 *d, int j) {
 // unwindowed segment (U_{-1} = conj U_1, U_{NC+1} = conj U_{NC-1} for a real segment).
 __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restrict__ x, int64_t x_stride, int hop,
                                                              double *__restrict__ P, int64_t n_seg,
-                                                             const float *const *__restrict__ rows) {
+                                                             const float *const *__restrict__ rows, float scale) {
     using namespace r16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *d = reinterpret_cast<float2 *>(smem_raw);
@@ -150,23 +151,46 @@ __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restr
     const int sc = min(40 - e, 120);
     const float s2 = __int_as_float((127 + sc) << 23);  // 2^sc (sc >= -88)
     const int ebias = 896 - 2 * sc;
-    auto p2 = [&](float2 q) -> double {
+    // c_k scale |X_k|^2 (the density scale and one-sided doubling of the mean, applied here in FP32 so
+    // that the mean over segments is a plain FP64 sum)
+    auto p2 = [&](float2 q, float f) -> double {
         const float a = q.x * s2, b = q.y * s2;
-        const uint32_t u = __float_as_uint(fmaf(b, b, a * a));
+        const uint32_t u = __float_as_uint(fmaf(b, b, a * a) * f);
         const uint32_t E = u >> 23, m23 = u & 0x7FFFFFu;
         if (E == 0) return 0.0;  // zero (or below 2^-126 of the scaled range)
         if (E == 255) return __hiloint2double((int)(0x7FF00000u | (m23 ? 0x80000u : 0u)), 0);
         return __hiloint2double((int)((uint32_t)((int)E + ebias) << 20 | (m23 >> 3)), (int)((m23 & 7u) << 29));
     };
+    const float f2 = 2.0f * scale;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) out[t + NT * m] = p2(X[m]);
-    if (t == NT - 1) out[NC] = p2(Xn);
+    for (int m = 0; m < 16; ++m) out[t + NT * m] = p2(X[m], (t | m) ? f2 : scale);
+    if (t == NT - 1) out[NC] = p2(Xn, scale);
 }
 
-// grid (ceil(NBIN/256), ceil(n_psd/PSD_EPT), n_det): bin k of epochs
-// [e0, e0 + PSD_EPT) as a sliding FP64 sum over the periodograms (epoch e
-// averages segments [e seg_step, e seg_step + K))
-__global__ void k_psd_mean(const double *__restrict__ P, int64_t n_seg, int seg_step, int K, double scale,
+// Epochs e0 .. e0 + PSD_EPT - 1 (those below n_psd) of one bin for a fixed segment step SS and count KK:
+// with the running prefix Q[n] of the run's segments (Q[0] = 0), epoch e0 + i is Q[i SS + KK] - Q[i SS];
+// the prefix passes Q[i SS] before it reaches Q[i SS + KK], so those values wait in registers.  One FP64
+// add per segment and one per epoch, every periodogram value of the run loaded once.
+template <int SS, int KK>
+__device__ __forceinline__ void psd_run_fixed(const double *src, double *dst, int64_t e0, int64_t n_psd) {
+    constexpr int E = PSD_EPT, NMAX = (E - 1) * SS + KK;
+    const int n_e = (int)min((int64_t)E, n_psd - e0);
+    const int n_used = (n_e - 1) * SS + KK;
+    const double *s0 = src + e0 * SS * NBIN;
+    double trail[E];
+    double q = 0.0;
+#pragma unroll
+    for (int n = 0; n <= NMAX; ++n) {
+        if (n % SS == 0 && n / SS < E) trail[n / SS] = q;
+        if (n >= KK && (n - KK) % SS == 0 && (n - KK) / SS < n_e) dst[(e0 + (n - KK) / SS) * NBIN] = q - trail[(n - KK) / SS];
+        if (n < NMAX && n < n_used) q += s0[(int64_t)n * NBIN];
+    }
+}
+
+// grid (ceil(NBIN/256), ceil(n_psd/PSD_EPT), n_det): bin k of epochs [e0, e0 + PSD_EPT) as FP64 sums of the
+// periodograms (already scaled by the density factor; epoch e sums segments [e seg_step, e seg_step + K)):
+// a running prefix for the 8 s epochs of 64 s PSDs at 50 % overlap (step 2, 15 segments), else a sliding sum
+__global__ void k_psd_mean(const double *__restrict__ P, int64_t n_seg, int seg_step, int K,
                            double *__restrict__ psd, int64_t n_psd) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= NBIN) return;
@@ -174,14 +198,17 @@ __global__ void k_psd_mean(const double *__restrict__ P, int64_t n_seg, int seg_
     const int det = blockIdx.z;
     const double *src = P + (int64_t)det * n_seg * NBIN + k;
     double *dst = psd + (int64_t)det * n_psd * NBIN + k;
-    const double f = (k == 0 || k == NFFT / 2) ? scale : 2.0 * scale;  // one-sided doubling and density scale
+    if (seg_step == 2 && K == 15) {
+        psd_run_fixed<2, 15>(src, dst, e0, n_psd);
+        return;
+    }
     double acc = 0.0;
     for (int q = 0; q < K; ++q) acc += src[(e0 * seg_step + q) * NBIN];
-    dst[e0 * NBIN] = acc * f;
+    dst[e0 * NBIN] = acc;
     for (int64_t e = e0 + 1; e < e0 + PSD_EPT && e < n_psd; ++e) {
         const int64_t s_old = (e - 1) * seg_step, s_new = s_old + K;
         for (int q = 0; q < seg_step; ++q) acc += src[(s_new + q) * NBIN] - src[(s_old + q) * NBIN];
-        dst[e * NBIN] = acc * f;
+        dst[e * NBIN] = acc;
     }
 }
 
@@ -427,6 +454,9 @@ __device__ __forceinline__ void whiten_mid_task0(const float2 *d, const float *g
 }
 
 constexpr int WHITEN_SMEM = r16::SLOTS * (int)sizeof(float2) + NBIN * (int)sizeof(float);
+// density factor of the mean of K periodograms (periodic Hann: sum w^2 = 3 NFFT / 8), applied per segment
+inline float psd_scale(int64_t K, int fs) { return (float)(1.0 / ((double)K * (double)fs * (3.0 * NFFT / 8.0))); }
+
 constexpr int WELCH_SMEM = (r16::SLOTS + 1) * (int)sizeof(float2) + (r16::NT / 32) * (int)sizeof(float);
 
 // One overlap-save block: the FIR of src[0 .. WB + F - 1) (samples past
@@ -719,15 +749,14 @@ int launch_psd(afg_ctx *ctx, const float *x, int64_t n, int n_det, int64_t n_psd
     {
         // one read of every segment, one FP64 periodogram written per segment
         KScope ks(ctx, st, KK_PERIODOGRAM, 0.0, (double)n_det * n_seg * (NFFT * 4.0 + NBIN * 8.0));
-        k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, x_stride, hop, P, n_seg, nullptr);
+        k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, x_stride, hop, P, n_seg, nullptr,
+                                                                                 psd_scale(K, ctx->cfg.fs));
     }
     AFG_LAUNCH_CHECK(ctx, "k_periodogram");
-    // periodic Hann: sum w^2 = 3 NFFT / 8
-    const double scale = 1.0 / ((double)K * (double)ctx->cfg.fs * (3.0 * NFFT / 8.0));
     {
         KScope ks(ctx, st, KK_PSD_MEAN, 0.0, (double)n_det * (n_seg + n_psd) * NBIN * 8.0);
         k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)((n_psd + PSD_EPT - 1) / PSD_EPT), n_det), 256, 0, st>>>(
-            P, n_seg, (int)seg_step, (int)K, scale, psd, n_psd);
+            P, n_seg, (int)seg_step, (int)K, psd, n_psd);
     }
     AFG_LAUNCH_CHECK(ctx, "k_psd_mean");
     return AFG_OK;
@@ -783,13 +812,12 @@ int launch_psd_rows(afg_ctx *ctx, const float *const *rows_dev, int n_rows, int6
     {
         KScope ks(ctx, st, KK_PERIODOGRAM, 0.0, (double)n_rows * K * (NFFT * 4.0 + NBIN * 8.0));
         k_periodogram<<<dim3((unsigned)K, (unsigned)n_rows), r16::NT, WELCH_SMEM, st>>>(nullptr, 0, hop, P, K,
-                                                                                        rows_dev);
+                                                                                        rows_dev, psd_scale(K, ctx->cfg.fs));
     }
     AFG_LAUNCH_CHECK(ctx, "k_periodogram");
-    const double scale = 1.0 / ((double)K * (double)ctx->cfg.fs * (3.0 * NFFT / 8.0));
     {
         KScope ks(ctx, st, KK_PSD_MEAN, 0.0, (double)n_rows * (K + 1) * NBIN * 8.0);
-        k_psd_mean<<<dim3((NBIN + 255) / 256, 1, (unsigned)n_rows), 256, 0, st>>>(P, K, 0, (int)K, scale, psd, 1);
+        k_psd_mean<<<dim3((NBIN + 255) / 256, 1, (unsigned)n_rows), 256, 0, st>>>(P, K, 0, (int)K, psd, 1);
     }
     AFG_LAUNCH_CHECK(ctx, "k_psd_mean");
     return AFG_OK;
@@ -830,12 +858,12 @@ cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, i
     const int64_t K = (psd_span - NFFT) / hop + 1;
     const int64_t seg_step = n_psd > 1 ? psd_step / hop : 0;
     const int64_t n_seg = (n_psd - 1) * seg_step + K;
-    k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, n, hop, P, n_seg, nullptr);
+    k_periodogram<<<dim3((unsigned)n_seg, n_det), r16::NT, WELCH_SMEM, st>>>(x, n, hop, P, n_seg, nullptr,
+                                                                             psd_scale(K, fs));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const double scale = 1.0 / ((double)K * (double)fs * (3.0 * NFFT / 8.0));
     k_psd_mean<<<dim3((NBIN + 255) / 256, (unsigned)((n_psd + PSD_EPT - 1) / PSD_EPT), n_det), 256, 0, st>>>(
-        P, n_seg, (int)seg_step, (int)K, scale, psd, n_psd);
+        P, n_seg, (int)seg_step, (int)K, psd, n_psd);
     return cudaGetLastError();
 }
 
