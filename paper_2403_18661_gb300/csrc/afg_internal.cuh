@@ -13,9 +13,10 @@
 // ----------------------------------------------------------------------------
 // Fixed transform geometry.  Welch segments and whitening blocks both use a
 // real FFT of NFFT = 16384 samples, computed as a complex FFT of NC = 8192
-// points in shared memory plus the even/odd split.  A whitening block
-// produces WB = 8192 outputs, so PSD epochs that are multiples of 8192
-// samples never straddle a block.
+// points in shared memory plus the even/odd split.  Whitening blocks are laid
+// out per PSD epoch (up to 16385 - F outputs on that transform, the epoch's
+// remainder on a 4096-point one), so no block straddles an epoch; epochs are
+// multiples of WB = 8192 samples, and a stream piece holds at most WB outputs.
 // ----------------------------------------------------------------------------
 constexpr int NFFT = 16384;
 constexpr int NC = NFFT / 2;

@@ -459,7 +459,7 @@ inline float psd_scale(int64_t K, int fs) { return (float)(1.0 / ((double)K * (d
 
 constexpr int WELCH_SMEM = (r16::SLOTS + 1) * (int)sizeof(float2) + (r16::NT / 32) * (int)sizeof(float);
 
-// One overlap-save block: the FIR of src[0 .. WB + F - 1) (samples past
+// One overlap-save block: the FIR of src[0 .. cnt + F - 1) (cnt <= 16385 - F; samples past
 // `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value).
 // smem: r16::SLOTS float2 for the transform, then NBIN floats for the gains gk,
 // which are copied in asynchronously while the forward transform runs.
@@ -472,7 +472,7 @@ __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *_
     const int t = threadIdx.x;
     for (int k = t; k < NBIN; k += NT) cp_async4(gs + k, gk + k);
     const int half = F / 2;
-    const int64_t need = WB + F - 1;  // samples that reach a kept output
+    const int64_t need = cnt + F - 1;  // samples that reach a kept output
     const int64_t lim = need < avail ? need : avail;
     float2 v[16];
 #pragma unroll
@@ -516,25 +516,57 @@ __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *_
     }
 }
 
-// grid (n_blocks, n_det); block b produces y[d][b*WB, min((b+1)*WB, out_len))
+template <typename Out>
+__device__ __forceinline__ void whiten_block_s(unsigned char *smem, const float *__restrict__ src, int64_t avail,
+                                               const float *__restrict__ stg, int64_t i_new,
+                                               const float *__restrict__ gk, int F, int64_t cnt, Out out);
+
+// Block layout of one whitening launch.  Every filter epoch (the whole span when epoch_len is 0) is covered by
+// blocks of bl = 16385 - F outputs (rounded down to 64) on the 16384-point transform, the most its circular
+// convolution keeps, and the epoch's remainder by one more block: on the 4096-point transform where it fits
+// (4097 - F outputs; 2048 of a 16384-sample epoch with F = 2048), else on the 16384-point one.  An 8192-output
+// block instead would keep half of every 16384-point transform.
+struct WhitenLayout {
+    int64_t span, bl, n_full, rem, bpe, n_blocks;
+    bool small_rem;
+};
+__host__ __device__ inline WhitenLayout whiten_layout(int64_t out_len, int64_t epoch_len, int F) {
+    WhitenLayout w;
+    w.span = epoch_len > 0 ? epoch_len : out_len;
+    w.bl = ((int64_t)(2 * r16::NT * 16 + 1 - F) / 64) * 64;
+    w.n_full = w.span / w.bl;
+    w.rem = w.span - w.n_full * w.bl;
+    w.bpe = w.n_full + (w.rem > 0 ? 1 : 0);
+    w.small_rem = w.rem > 0 && w.rem <= (int64_t)(2 * r16::NC_S + 1 - F);
+    const int64_t n_ep = epoch_len > 0 ? (out_len + epoch_len - 1) / epoch_len : 1;
+    w.n_blocks = out_len > 0 ? n_ep * w.bpe : 0;
+    return w;
+}
+
+// grid (whiten_layout().n_blocks, n_det); block (e, i) = (blockIdx.x / bpe, blockIdx.x % bpe) produces
+// y[d][e span + i bl, + its count) with the gains of epoch e
 __global__ void __launch_bounds__(r16::NT, 2) k_whiten(const float *__restrict__ x, int64_t n, int64_t x_stride,
                                                         const float *__restrict__ gains, int64_t n_psd,
                                                         int64_t out_first, int64_t out_len, int64_t epoch_len, int F,
                                                         float *__restrict__ y, int64_t y_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int64_t o = (int64_t)blockIdx.x * WB;
+    const WhitenLayout L = whiten_layout(out_len, epoch_len, F);
+    const int64_t e = (int64_t)blockIdx.x / L.bpe, i = (int64_t)blockIdx.x - e * L.bpe;
+    const int64_t o = e * L.span + i * L.bl;
+    int64_t cnt = i < L.n_full ? L.bl : L.rem;
+    if (cnt > out_len - o) cnt = out_len - o;
+    if (cnt <= 0) return;
     const int det = blockIdx.y;
-    int64_t e = 0;
-    if (epoch_len > 0) {
-        e = o / epoch_len;
-        if (e > n_psd - 1) e = n_psd - 1;
-    }
+    int64_t ep = epoch_len > 0 ? e : 0;
+    if (ep > n_psd - 1) ep = n_psd - 1;
     const int64_t s0 = out_first + o - F / 2;  // raw index of block sample 0
-    int64_t cnt = out_len - o;
-    if (cnt > WB) cnt = WB;
     float *dst = y + det * y_stride + o;
-    whiten_block(smem_raw, x + det * x_stride + s0, n - s0, gains + ((int64_t)det * n_psd + e) * NBIN, F, cnt,
-                 [dst](int64_t q, float v) { dst[q] = v; });
+    const float *gk = gains + ((int64_t)det * n_psd + ep) * NBIN;
+    auto out = [dst](int64_t q, float v) { dst[q] = v; };
+    if (i == L.n_full && L.small_rem)
+        whiten_block_s(smem_raw, x + det * x_stride + s0, n - s0, nullptr, 0, gk, F, cnt, out);
+    else
+        whiten_block(smem_raw, x + det * x_stride + s0, n - s0, gk, F, cnt, out);
 }
 
 // Whitening pieces of many streams in one launch: grid (n_desc, 2).  Piece i
@@ -772,7 +804,8 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
     rc = filter_build(ctx, psd, n_det, n_psd, gains, st);
     if (rc) return rc;
     if (out_len <= 0) return AFG_OK;
-    const int64_t nb = (out_len + WB - 1) / WB;
+    const int64_t nb = whiten_layout(out_len, epoch_len, ctx->cfg.fir_len).n_blocks;
+    if (nb > 0x7fffffff) return afg_fail(ctx, AFG_ERR_ARG, "whiten: too many blocks");
     {
         // algorithmic: read the cropped span once, write the output once, read the gains
         const double F = ctx->cfg.fir_len;
