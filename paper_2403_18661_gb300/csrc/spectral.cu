@@ -543,30 +543,56 @@ __host__ __device__ inline WhitenLayout whiten_layout(int64_t out_len, int64_t e
     return w;
 }
 
-// grid (whiten_layout().n_blocks, n_det); block (e, i) = (blockIdx.x / bpe, blockIdx.x % bpe) produces
-// y[d][e span + i bl, + its count) with the gains of epoch e
+// Block (e, i) of a whitening launch: y[d][e span + i bl, + cnt) with the gains of epoch e (cnt <= 0: none)
+struct WhitenBlock {
+    int64_t o, cnt, ep;
+};
+__device__ __forceinline__ WhitenBlock whiten_block_at(const WhitenLayout &L, int64_t e, int64_t i, int64_t out_len,
+                                                       int64_t epoch_len, int64_t n_psd) {
+    WhitenBlock b;
+    b.o = e * L.span + i * L.bl;
+    b.cnt = i < L.n_full ? L.bl : L.rem;
+    if (b.cnt > out_len - b.o) b.cnt = out_len - b.o;
+    b.ep = epoch_len > 0 ? e : 0;
+    if (b.ep > n_psd - 1) b.ep = n_psd - 1;
+    return b;
+}
+
+// grid (n_ep * n16, n_det): the blocks on the 16384-point transform, n16 per epoch (bpe, or n_full where the
+// remainder goes to k_whiten_rem); block (e, i) = (blockIdx.x / n16, blockIdx.x % n16)
 __global__ void __launch_bounds__(r16::NT, 2) k_whiten(const float *__restrict__ x, int64_t n, int64_t x_stride,
                                                         const float *__restrict__ gains, int64_t n_psd,
                                                         int64_t out_first, int64_t out_len, int64_t epoch_len, int F,
                                                         float *__restrict__ y, int64_t y_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const WhitenLayout L = whiten_layout(out_len, epoch_len, F);
-    const int64_t e = (int64_t)blockIdx.x / L.bpe, i = (int64_t)blockIdx.x - e * L.bpe;
-    const int64_t o = e * L.span + i * L.bl;
-    int64_t cnt = i < L.n_full ? L.bl : L.rem;
-    if (cnt > out_len - o) cnt = out_len - o;
-    if (cnt <= 0) return;
+    const int64_t n16 = L.small_rem ? L.n_full : L.bpe;
+    const int64_t e = (int64_t)blockIdx.x / n16;
+    const WhitenBlock b = whiten_block_at(L, e, (int64_t)blockIdx.x - e * n16, out_len, epoch_len, n_psd);
+    if (b.cnt <= 0) return;
     const int det = blockIdx.y;
-    int64_t ep = epoch_len > 0 ? e : 0;
-    if (ep > n_psd - 1) ep = n_psd - 1;
-    const int64_t s0 = out_first + o - F / 2;  // raw index of block sample 0
-    float *dst = y + det * y_stride + o;
-    const float *gk = gains + ((int64_t)det * n_psd + ep) * NBIN;
-    auto out = [dst](int64_t q, float v) { dst[q] = v; };
-    if (i == L.n_full && L.small_rem)
-        whiten_block_s(smem_raw, x + det * x_stride + s0, n - s0, nullptr, 0, gk, F, cnt, out);
-    else
-        whiten_block(smem_raw, x + det * x_stride + s0, n - s0, gk, F, cnt, out);
+    const int64_t s0 = out_first + b.o - F / 2;  // raw index of block sample 0
+    float *dst = y + det * y_stride + b.o;
+    whiten_block(smem_raw, x + det * x_stride + s0, n - s0, gains + ((int64_t)det * n_psd + b.ep) * NBIN, F, b.cnt,
+                 [dst](int64_t q, float v) { dst[q] = v; });
+}
+
+// grid (n_ep, n_det): each epoch's remainder block on the 4096-point transform (whiten_layout().small_rem).
+// A launch of its own: its 26 KB of shared memory lets several CTAs share an SM, which the short transform's
+// barrier-bound passes need.
+__global__ void __launch_bounds__(r16::NT_S) k_whiten_rem(const float *__restrict__ x, int64_t n, int64_t x_stride,
+                                                         const float *__restrict__ gains, int64_t n_psd,
+                                                         int64_t out_first, int64_t out_len, int64_t epoch_len, int F,
+                                                         float *__restrict__ y, int64_t y_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const WhitenLayout L = whiten_layout(out_len, epoch_len, F);
+    const WhitenBlock b = whiten_block_at(L, blockIdx.x, L.n_full, out_len, epoch_len, n_psd);
+    if (b.cnt <= 0) return;
+    const int det = blockIdx.y;
+    const int64_t s0 = out_first + b.o - F / 2;
+    float *dst = y + det * y_stride + b.o;
+    whiten_block_s(smem_raw, x + det * x_stride + s0, n - s0, nullptr, 0, gains + ((int64_t)det * n_psd + b.ep) * NBIN,
+                   F, b.cnt, [dst](int64_t q, float v) { dst[q] = v; });
 }
 
 // Whitening pieces of many streams in one launch: grid (n_desc, 2).  Piece i
@@ -804,17 +830,26 @@ int launch_whiten(afg_ctx *ctx, const float *x, int64_t n, int n_det, const doub
     rc = filter_build(ctx, psd, n_det, n_psd, gains, st);
     if (rc) return rc;
     if (out_len <= 0) return AFG_OK;
-    const int64_t nb = whiten_layout(out_len, epoch_len, ctx->cfg.fir_len).n_blocks;
+    const WhitenLayout wl = whiten_layout(out_len, epoch_len, ctx->cfg.fir_len);
+    const int64_t n_ep = wl.bpe > 0 ? wl.n_blocks / wl.bpe : 0;
+    const int64_t nb = n_ep * (wl.small_rem ? wl.n_full : wl.bpe);
     if (nb > 0x7fffffff) return afg_fail(ctx, AFG_ERR_ARG, "whiten: too many blocks");
     {
         // algorithmic: read the cropped span once, write the output once, read the gains
         const double F = ctx->cfg.fir_len;
         KScope ks(ctx, st, KK_WHITEN, 0.0, (double)n_det * ((2.0 * out_len + F - 1.0) * 4.0 + n_psd * NBIN * 4.0));
-        k_whiten<<<dim3((unsigned)nb, n_det), r16::NT, WHITEN_SMEM, st>>>(x, n, x_stride, gains, n_psd, out_first,
-                                                                          out_len, epoch_len, ctx->cfg.fir_len, y,
-                                                                          y_stride);
+        if (nb > 0)
+            k_whiten<<<dim3((unsigned)nb, n_det), r16::NT, WHITEN_SMEM, st>>>(x, n, x_stride, gains, n_psd, out_first,
+                                                                              out_len, epoch_len, ctx->cfg.fir_len, y,
+                                                                              y_stride);
     }
     AFG_LAUNCH_CHECK(ctx, "k_whiten");
+    if (wl.small_rem && n_ep > 0) {
+        KScope ks(ctx, st, KK_WHITEN, 0.0, 0.0);  // (the bytes are counted with the launch above)
+        k_whiten_rem<<<dim3((unsigned)n_ep, n_det), r16::NT_S, WHITEN_SMEM_S, st>>>(
+            x, n, x_stride, gains, n_psd, out_first, out_len, epoch_len, ctx->cfg.fir_len, y, y_stride);
+    }
+    AFG_LAUNCH_CHECK(ctx, "k_whiten_rem");
     return AFG_OK;
 }
 
