@@ -473,14 +473,21 @@ typedef struct afg_tile {
     float us_default;     /* microseconds per launch of the default tile at the tuning size (0: not timed) */
 } afg_tile;
 
-/* Time every valid tile of each distinct layer geometry (channels, lengths,
- * stride, taps, residual) on n_win synthetic windows (n_win <= 0: 1024; at
- * most 4096) and keep the fastest for later inference calls.  Synchronous:
- * synchronises `stream` and returns when done.  Uses the context's activation
- * workspaces.  Errors: AFG_ERR_UNSUPPORTED if the context has no per-layer
- * tensor-core plan (FP32 contexts, or the fused 16-channel network);
- * AFG_ERR_STATE if `stream` is capturing; AFG_ERR_TIMEOUT if a bounded
- * device wait gave up; AFG_ERR_CUDA / AFG_ERR_OOM / AFG_ERR_BUDGET. */
+/* Wide networks: time every valid tile of each distinct layer geometry
+ * (channels, lengths, stride, taps, residual) on n_win synthetic windows
+ * (n_win <= 0: 1024; at most 4096) and keep the fastest for later inference
+ * calls; uses the context's activation workspaces.
+ * The fused 16-channel network (BF16, 8 GroupNorm groups, 3072-position
+ * windows, whose geometry is compiled with fixed counts): time every
+ * candidate of afg_fused_tuning_candidates (epilogue warps, MMA-issue warps,
+ * polling sleep) on n_win windows, 64 samples apart, of synthetic whitened
+ * strain (n_win <= 0: 4096; at most 65536) and keep the fastest; uses the
+ * context's whitened-strain and logit workspaces.
+ * Synchronous: synchronises `stream` and returns when done.  Errors:
+ * AFG_ERR_UNSUPPORTED if the context has neither (FP32 contexts, or a fused
+ * network of another geometry); AFG_ERR_STATE if `stream` is capturing;
+ * AFG_ERR_TIMEOUT if a bounded device wait gave up; AFG_ERR_CUDA /
+ * AFG_ERR_OOM / AFG_ERR_BUDGET. */
 int afg_autotune(afg_ctx *ctx, int64_t n_win, void *stream);
 
 /* Current tile of every convolution after the stem, in execution order:
@@ -494,6 +501,34 @@ int afg_tile_candidates(afg_ctx *ctx, int32_t layer, afg_tile *out, int32_t cap,
  * stages and acc_bufs.  All entries are checked first; AFG_ERR_ARG (and no
  * change) if one does not fit its layer. */
 int afg_tiles_set(afg_ctx *ctx, const afg_tile *tiles, int32_t n);
+
+/* Launch knobs of the fused 16-channel BF16 network (one window per CTA
+ * pass, its layers pipelined; Sec. II network, Sec. IX batches).  Every
+ * candidate computes the same network (up to the summation order of the
+ * GroupNorm statistics across warps); they differ in speed only. */
+typedef struct afg_fused_tuning {
+    int32_t epi_warps;    /* epilogue warps: 8 or 12 (2 or 3 quads of four) */
+    int32_t issue_warps;  /* MMA-issue warps: 1 or 2 */
+    int32_t spin_ns;      /* the issue warps' sleep between polls of an incomplete barrier (0: spin) */
+    int32_t tuned;        /* 1: chosen by afg_autotune (or set so by afg_fused_tuning_set) */
+    int32_t n_candidates; /* candidates timed */
+    float us_chosen;      /* microseconds per launch of the chosen candidate at the tuning size (0: not timed) */
+    float us_default;     /* microseconds per launch of the default (12, 2, 64) (0: not timed) */
+} afg_fused_tuning;
+
+/* Current knobs of the context's fused network.  AFG_ERR_UNSUPPORTED without a
+ * fused 16-channel BF16 network. */
+int afg_fused_tuning_get(afg_ctx *ctx, afg_fused_tuning *out);
+
+/* Every candidate afg_autotune times (timing fields 0): writes min(cap, count)
+ * entries and the count to *n_out.  AFG_ERR_UNSUPPORTED unless the fused
+ * network has the tunable geometry (8 groups, 3072 positions). */
+int afg_fused_tuning_candidates(afg_ctx *ctx, afg_fused_tuning *out, int32_t cap, int32_t *n_out);
+
+/* Apply knobs (e.g. a saved tuning): epi_warps 8 or 12, issue_warps 1 or 2,
+ * spin_ns in [0, 100000]; AFG_ERR_ARG (and no change) otherwise,
+ * AFG_ERR_UNSUPPORTED as for afg_fused_tuning_candidates. */
+int afg_fused_tuning_set(afg_ctx *ctx, const afg_fused_tuning *in);
 
 /* ---------------------------------------------------------------- allocation-free PSD */
 

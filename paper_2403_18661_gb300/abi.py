@@ -85,6 +85,15 @@ def _tile_dict(t: AfgTile) -> dict:
     return {name: getattr(t, name) for name, _ in AfgTile._fields_}
 
 
+class AfgFusedTuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("epi_warps", "issue_warps", "spin_ns", "tuned", "n_candidates")] + \
+               [("us_chosen", ctypes.c_float), ("us_default", ctypes.c_float)]
+
+
+def _fused_dict(t: AfgFusedTuning) -> dict:
+    return {name: getattr(t, name) for name, _ in AfgFusedTuning._fields_}
+
+
 STREAM_RESULT_DTYPE = np.dtype([("window", np.int64), ("stat", np.float32), ("logit", np.float32),
                                 ("t_push", np.float64), ("t_done", np.float64)])
 
@@ -129,6 +138,9 @@ SIGNATURES = {
     "afg_tiles_get": ([_vp, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_tile_candidates": ([_vp, _i32, ctypes.POINTER(AfgTile), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
     "afg_tiles_set": ([_vp, ctypes.POINTER(AfgTile), _i32], ctypes.c_int),
+    "afg_fused_tuning_get": ([_vp, ctypes.POINTER(AfgFusedTuning)], ctypes.c_int),
+    "afg_fused_tuning_candidates": ([_vp, ctypes.POINTER(AfgFusedTuning), _i32, ctypes.POINTER(_i32)], ctypes.c_int),
+    "afg_fused_tuning_set": ([_vp, ctypes.POINTER(AfgFusedTuning)], ctypes.c_int),
     "afg_resample": ([_vp, _vp, _i64, _i32, _i64, _i32, _vp, _i64, ctypes.POINTER(_i64), _vp], ctypes.c_int),
     "afg_resample_size": ([_i64, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
     "afg_far": ([_vp, _vp, _vp, _vp, _i64, ctypes.c_double, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -333,8 +345,29 @@ class Context:
 
     # ---------------------------------------------------------------- conv tiles
     def autotune(self, n_win: int = 1024, stream=None):
-        """Time every tile of each layer geometry of the BF16 tensor-core path and keep the fastest."""
+        """Time every tile of each layer geometry of the BF16 tensor-core path (or every candidate of the
+        fused 16-channel network) and keep the fastest."""
         self._check(self._lib.afg_autotune(self._h, int(n_win), _stream(stream)))
+
+    def fused_tuning(self) -> dict:
+        t = AfgFusedTuning()
+        self._check(self._lib.afg_fused_tuning_get(self._h, ctypes.byref(t)))
+        return _fused_dict(t)
+
+    def fused_tuning_candidates(self) -> list:
+        cap = 64
+        arr = (AfgFusedTuning * cap)()
+        n = _i32()
+        self._check(self._lib.afg_fused_tuning_candidates(self._h, arr, cap, ctypes.byref(n)))
+        return [_fused_dict(t) for t in arr[:min(n.value, cap)]]
+
+    def set_fused_tuning(self, d: dict):
+        """Apply the fused network's knobs given as a dict with the afg_fused_tuning fields."""
+        t = AfgFusedTuning()
+        for name, _ in AfgFusedTuning._fields_:
+            if name in d:
+                setattr(t, name, d[name])
+        self._check(self._lib.afg_fused_tuning_set(self._h, ctypes.byref(t)))
 
     def tiles(self) -> list:
         cap = 256

@@ -75,6 +75,11 @@ struct NetPlan {
     int64_t max_act_per_window;    // floats of the largest padded activation of one window
     float *tc_params = nullptr;    // fused tensor-core network: FP32 parameter block
     unsigned char *tc_wimg = nullptr;  // and BF16 weight image in shared-memory order
+    // fused network's tuning (afg_autotune / afg_fused_tuning_*): epilogue and issue warps, polling sleep
+    int tiny_ew = 12, tiny_mw = 2;
+    uint32_t tiny_spin_ns = 64;
+    int tiny_tuned = 0, tiny_n_cand = 0;
+    float tiny_us_chosen = 0.f, tiny_us_default = 0.f;
 };
 
 // One segment of a timeslide batch: its whitened span in the concatenated
@@ -328,6 +333,11 @@ bool net_tc_layers_available(const afg_ctx *ctx);
 int launch_infer_bf16_full(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_stride, int64_t first,
                            int64_t stride, int64_t n_win, int64_t shift, float *logits, cudaStream_t st);
 int net_tc_autotune(afg_ctx *ctx, int64_t n_win, cudaStream_t st);
+bool net_tc_tiny_tunable(const afg_ctx *ctx);
+int net_tc_tiny_autotune(afg_ctx *ctx, int64_t n_win, cudaStream_t st);
+int net_tc_tiny_tuning_get(afg_ctx *ctx, afg_fused_tuning *out);
+int net_tc_tiny_tuning_candidates(afg_ctx *ctx, afg_fused_tuning *out, int cap, int *n_out);
+int net_tc_tiny_tuning_set(afg_ctx *ctx, const afg_fused_tuning *in);
 int net_tc_tiles_get(afg_ctx *ctx, afg_tile *out, int cap, int *n_out);
 int net_tc_tile_candidates(afg_ctx *ctx, int layer, afg_tile *out, int cap, int *n_out);
 int net_tc_tiles_set(afg_ctx *ctx, const afg_tile *in, int n);

@@ -358,7 +358,33 @@ int afg_analyze_host(afg_ctx *ctx, const float *x_host, const afg_run_params *p,
 int afg_autotune(afg_ctx *ctx, int64_t n_win, void *stream) {
     if (!ctx) return AFG_ERR_ARG;
     ctx->err.clear();
+    if (net_tc_tiny_tunable(ctx)) return net_tc_tiny_autotune(ctx, n_win, S(stream));
     return net_tc_autotune(ctx, n_win, S(stream));
+}
+
+int afg_fused_tuning_get(afg_ctx *ctx, afg_fused_tuning *out) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (!out) return afg_fail(ctx, AFG_ERR_ARG, "fused_tuning_get: null output");
+    return net_tc_tiny_tuning_get(ctx, out);
+}
+
+int afg_fused_tuning_candidates(afg_ctx *ctx, afg_fused_tuning *out, int32_t cap, int32_t *n_out) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (!n_out || cap < 0 || (cap > 0 && !out))
+        return afg_fail(ctx, AFG_ERR_ARG, "fused_tuning_candidates: bad output arguments");
+    int n = 0;
+    int rc = net_tc_tiny_tuning_candidates(ctx, out, cap, &n);
+    *n_out = n;
+    return rc;
+}
+
+int afg_fused_tuning_set(afg_ctx *ctx, const afg_fused_tuning *in) {
+    if (!ctx) return AFG_ERR_ARG;
+    ctx->err.clear();
+    if (!in) return afg_fail(ctx, AFG_ERR_ARG, "fused_tuning_set: null input");
+    return net_tc_tiny_tuning_set(ctx, in);
 }
 
 int afg_tiles_get(afg_ctx *ctx, afg_tile *out, int32_t cap, int32_t *n_out) {

@@ -66,6 +66,7 @@ struct TinyArgs {
     int *err;
     int n_conv, k_stem, W, G;
     float eps;
+    uint32_t spin_ns;               // k_tiny_pipe: the issue warps' sleep between polls of an incomplete barrier
 };
 
 __host__ __device__ inline int tiny_param_count(int k_stem, int n_conv) {
@@ -920,15 +921,14 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_tiny_fused(const TinyArgs arg
 // 0 and W + 1 zero), the BF16 weight images (convs, then the stem), the FP32
 // parameters, reduction scratch and barriers, then the batch segment table.
 // ============================================================================
-constexpr int TP_EPI_WARPS = 12;           // 3 quads of epilogue warps
-constexpr int TP_NQ = TP_EPI_WARPS / 4;
-constexpr int TP_MMA_WARPS = 2;             // issue warps (even and odd units): 14 warps, 144 registers each
-constexpr int TP_EPI = TP_EPI_WARPS * 32;
-constexpr int TP_THREADS = TP_EPI + 32 * TP_MMA_WARPS;
+// The epilogue and issue warp counts are tunable (afg_autotune picks among 8 or 12 epilogue warps and 1 or 2
+// issue warps for the fixed geometry); the shared-memory layout is sized for the largest.
+constexpr int TP_EPI_WARPS = 12;           // default and largest: 3 quads of epilogue warps
+constexpr int TP_MMA_WARPS = 2;             // default: issue warps for the even and odd units
 constexpr int TP_MT_MAX = 32;
 constexpr int TP_STEM_IMG = 512;  // BF16 image of the stem weights: 16 channels x K = 16
 constexpr uint64_t TP_WAIT_NS = 1000000000ull;
-constexpr uint32_t TP_SPIN_NS = 64;  // issue warps: sleep between polls of an incomplete barrier
+constexpr uint32_t TP_SPIN_NS = 64;  // default sleep of the issue warps between polls of an incomplete barrier
 constexpr int TP_EPI_RED = TP_EPI_WARPS * 32 + 32;  // floats of one reduction scratch
 
 struct PipeSmem {
@@ -970,7 +970,7 @@ __device__ __forceinline__ void acc_channel_pairs(const uint32_t (&r)[16], float
 // (sc[c] = rstd_g gamma_c, sh[c] = beta_c - mean_g sc[c]) and a consistent copy of the abort
 // flag (stop).  red is this layer's half of a double buffer: a warp that runs ahead writes the
 // next layer's sums into the other half, and cannot get two layers ahead past the barrier.
-template <int G>
+template <int G, int EW>
 __device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, float eps, const float *gamma,
                                               const float *beta, float *red, float *maps, float (&sc)[TF_C],
                                               float (&sh)[TF_C], const volatile int *abort_flag, bool &stop) {
@@ -986,13 +986,13 @@ __device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, 
     if ((lane & (32 / NV - 1)) == 0) red[warp * 32 + lane / (32 / NV)] = v[0];
     int *stop_slot = reinterpret_cast<int *>(red + TP_EPI_WARPS * 32);
     if (threadIdx.x == 0) *stop_slot = *abort_flag;
-    tc::named_bar_sync(1, TP_EPI);
+    tc::named_bar_sync(1, EW * 32);
     // lane i < 2G: total i over the warps (sums, then sums of squares); lane c (mod 16) then forms
     // channel c's affine map, and the 16 maps are broadcast to every lane
     float t = 0.f;
     if (lane < NV)
 #pragma unroll
-        for (int w = 0; w < TP_EPI_WARPS; ++w) t += red[w * 32 + lane];
+        for (int w = 0; w < EW; ++w) t += red[w * 32 + lane];
     const int c = lane & (TF_C - 1), g = c / (TF_C / G);
     const float s_g = __shfl_sync(0xffffffffu, t, g), q_g = __shfl_sync(0xffffffffu, t, G + g);
     const float mean = s_g / cnt;
@@ -1066,11 +1066,14 @@ __device__ __forceinline__ void tiny_emit(const TinyArgs &args, int64_t out, flo
 // MTS: the window's subtiles as a compile-time constant (0: from args.W); with a constant that is even
 // and whose units divide evenly among the quads and issue warps, every loop over units has a fixed
 // trip count and no partial unit
-template <int G, int MTS = 0>
-__global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args) {
+// EW epilogue warps (EW / 4 quads) and MW issue warps.
+template <int G, int MTS = 0, int EW = TP_EPI_WARPS, int MW = TP_MMA_WARPS>
+__global__ void __launch_bounds__((EW + MW) * 32, 1) k_tiny_pipe(const TinyArgs args) {
     extern __shared__ __align__(1024) unsigned char sm[];
     pdl_trigger();
-    constexpr bool FIXED = MTS > 0 && MTS % 2 == 0 && (MTS / 2) % TP_NQ == 0 && (MTS / 2) % TP_MMA_WARPS == 0;
+    constexpr int NQ = EW / 4, EPI = EW * 32, THREADS = (EW + MW) * 32;
+    static_assert(EW % 4 == 0 && EW <= TP_EPI_WARPS, "whole quads, within the shared-memory layout");
+    constexpr bool FIXED = MTS > 0 && MTS % 2 == 0 && (MTS / 2) % NQ == 0 && (MTS / 2) % MW == 0;
     const int W = MTS > 0 ? 128 * MTS : args.W, n_conv = args.n_conv, MT = W / 128, k_stem = args.k_stem;
     const PipeSmem L = pipe_smem(W, n_conv, k_stem);
     unsigned char *actA = sm + L.off_a;
@@ -1088,8 +1091,8 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
 
     // ---- one-time set-up: parameters, weight images, zero pad rows, barriers, TMEM
     const int n_prm = tiny_param_count(k_stem, n_conv);
-    for (int i = tid; i < n_prm; i += TP_THREADS) prm[i] = args.params[i];
-    for (int i = tid; i < (n_conv * TF_WIMG + TP_STEM_IMG) / 16; i += TP_THREADS)
+    for (int i = tid; i < n_prm; i += THREADS) prm[i] = args.params[i];
+    for (int i = tid; i < (n_conv * TF_WIMG + TP_STEM_IMG) / 16; i += THREADS)
         reinterpret_cast<uint4 *>(wimg)[i] = reinterpret_cast<const uint4 *>(args.wimg)[i];
     if (tid < 8) {
         unsigned char *buf = (tid & 4) ? actB : actA;
@@ -1098,22 +1101,22 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
     }
     // the im2col tile's rows start finite (zero): the stem MMA's second K half (zero weights) also
     // reads the first row of the next subtile, which another quad may not have written yet
-    for (int i = tid; i < W; i += TP_THREADS)
+    for (int i = tid; i < W; i += THREADS)
         *reinterpret_cast<uint4 *>(actB + act_chunk + 16 + (size_t)i * 16) = make_uint4(0, 0, 0, 0);
     if (args.seg_cache > 0) {
         SegDesc *seg_sm = reinterpret_cast<SegDesc *>(sm + L.total);
-        for (int i = tid; i < args.seg_cache; i += TP_THREADS) seg_sm[i] = args.segs[i];
+        for (int i = tid; i < args.seg_cache; i += THREADS) seg_sm[i] = args.segs[i];
     }
     if (tid == 0) {
         for (int j = 0; j < TP_MT_MAX; ++j) {
             tc::mbar_init(&mma_done[j], 1);
             tc::mbar_init(&rows_ready[j], 4);
         }
-        tc::mbar_init(drain, TP_MMA_WARPS);
+        tc::mbar_init(drain, MW);
         tc::fence_mbar_init();
         *abort_flag = 0;
     }
-    if (warp == TP_EPI_WARPS) {
+    if (warp == EW) {
         tc::tmem_alloc(tmem_slot, 512);
         tc::tmem_relinquish();
     }
@@ -1126,9 +1129,9 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
     const int64_t win0 = blockIdx.x, win_step = gridDim.x;
     pdl_wait();  // list mode: the whitened rings come from the whitening launch before
 
-    if (warp >= TP_EPI_WARPS) {
+    if (warp >= EW) {
         // ================================================================ MMA warps
-        const int mw = warp - TP_EPI_WARPS;  // this warp issues the units u = mw, mw + TP_MMA_WARPS, ..
+        const int mw = warp - EW;  // this warp issues the units u = mw, mw + MW, ..
         const uint32_t idesc = tc::idesc_bf16_f32(128, TF_C);
         const uint64_t d_stem_a = tc::desc_kmajor_noswizzle(tc::smem_addr(actB + act_chunk + 16), 16, 128);
         const uint64_t d_stem_b = tc::desc_kmajor_noswizzle(tc::smem_addr(wimg + (size_t)n_conv * TF_WIMG), 256, 128);
@@ -1148,7 +1151,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 const bool rdy = lane >= NU || tc::mbar_test_wait(&rows_ready[lane], par);
                 const unsigned m = __ballot_sync(0xffffffffu, rdy);
                 ready = m == 0xffffffffu ? 32 : __ffs(~m) - 1;
-                if (ready < need && !tc::mbar_spin_warp(&rows_ready[ready], par, TP_WAIT_NS, TP_SPIN_NS)) {
+                if (ready < need && !tc::mbar_spin_warp(&rows_ready[ready], par, TP_WAIT_NS, args.spin_ns)) {
                     ok = false;
                     ready = NU;
                 }
@@ -1156,13 +1159,13 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
             tc::fence_after_sync();
         };
         // this warp's i-th unit of a layer, and its count
-        const int n_mu = FIXED ? NU / TP_MMA_WARPS : (NU - mw + TP_MMA_WARPS - 1) / TP_MMA_WARPS;
+        const int n_mu = FIXED ? NU / MW : (NU - mw + MW - 1) / MW;
         for (int64_t win = win0; win < args.n_win; win += win_step) {
             {   // stem: one K = 16 MMA per subtile over the im2col tile
                 const uint32_t par = seq & 1;
                 int ready = ok ? 0 : NU;
                 for (int i = 0; i < n_mu; ++i) {
-                    const int u = mw + TP_MMA_WARPS * i;
+                    const int u = mw + MW * i;
                     wait_rows(ready, u + 1, par);
                     const int j0 = 2 * u;
                     tc::mma_bf16_elect(tmem + (uint32_t)(j0 * TF_C), d_stem_a + (uint64_t)(128 * j0), d_stem_b, idesc, 0u);
@@ -1179,7 +1182,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 const uint64_t bd = d_w + (uint64_t)(l * (TF_WIMG / 16));
                 int ready = ok ? 0 : NU;
                 for (int i = 0; i < n_mu; ++i) {
-                    const int u = mw + TP_MMA_WARPS * i;
+                    const int u = mw + MW * i;
                     wait_rows(ready, min(u + 2, NU), par);
                     const int j0 = 2 * u;
                     const uint64_t a0 = ad + (uint64_t)(128 * j0);
@@ -1219,18 +1222,18 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
         unsigned char *im2col = actB + act_chunk + 16;       // stem im2col tile, [W][16 B]
         const int RP = W + 8;
         uint32_t seq = 0;
-        // this quad's i-th unit is u = q + TP_NQ i, i < n_qu
-        const int n_qu = FIXED ? (MT / 2) / TP_NQ : ((MT + 1) / 2 - q + TP_NQ - 1) / TP_NQ;
+        // this quad's i-th unit is u = q + NQ i, i < n_qu
+        const int n_qu = FIXED ? (MT / 2) / NQ : ((MT + 1) / 2 - q + NQ - 1) / NQ;
         WinLoc cur = locate_window(args, win0, segs);
-        if (win0 < args.n_win) load_window(args, cur, xs, W, 1, true, TP_EPI);
+        if (win0 < args.n_win) load_window(args, cur, xs, W, 1, true, EPI);
         for (int64_t win = win0; win < args.n_win; win += win_step) {
             const int64_t out = cur.out;
             float *out_ptr = cur.out_ptr;
             asm volatile("cp.async.wait_all;" ::: "memory");
-            tc::named_bar_sync(1, TP_EPI);
+            tc::named_bar_sync(1, EPI);
             // ---- stem im2col rows of this quad's units (BF16, six taps per 16-byte row)
             for (int i = 0; i < n_qu; ++i) {
-                const int u = q + TP_NQ * i;
+                const int u = q + NQ * i;
                 for (int j = 2 * u; j < (FIXED ? 2 * u + 2 : min(2 * u + 2, MT)); ++j) {
                     const int t = 128 * j + 32 * lq + lane;
                     const float *p0 = xs + 4 + t - 1, *p1 = xs + RP + 4 + t - 1;
@@ -1261,7 +1264,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 for (int i = 0; i < TF_C / 2; ++i) s2[i] = q2[i] = make_float2(0.f, 0.f);
                 bool ok = true;
                 for (int i = 0; i < n_qu; ++i) {
-                    const int u = q + TP_NQ * i;
+                    const int u = q + NQ * i;
                     const int j0 = 2 * u, j1 = j0 + 1;
                     const bool two = FIXED || j1 < MT;
                     uint32_t r0[16], r1[16];
@@ -1293,7 +1296,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                 }
                 float sc[TF_C], sh[TF_C];
                 bool stop_now = false;
-                gn_reduce_epi<G>(sq, cnt, args.eps, gam, gam + TF_C, red + (seq & 1) * TP_EPI_RED, red + 3 * TP_EPI_RED,
+                gn_reduce_epi<G, EW>(sq, cnt, args.eps, gam, gam + TF_C, red + (seq & 1) * TP_EPI_RED, red + 3 * TP_EPI_RED,
                                  sc, sh, abort_flag, stop_now);
                 if (stop_now) {
                     stopped = true;
@@ -1303,11 +1306,11 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
                     // every MMA of the last layer is done (its statistics are complete), so buffer B,
                     // its input, is free: stage the next window's samples while this one finishes
                     cur = locate_window(args, win + win_step, segs);
-                    load_window(args, cur, xs, W, 1, true, TP_EPI);
+                    load_window(args, cur, xs, W, 1, true, EPI);
                 }
                 // ---- normalise pass (+ residual) + ReLU -> BF16 rows of dst, or the pooled sums
                 for (int i = 0; i < n_qu; ++i) {
-                    const int u = q + TP_NQ * i;
+                    const int u = q + NQ * i;
                     const int j0 = 2 * u, j1 = j0 + 1;
                     const bool two = FIXED || j1 < MT;
                     uint32_t ra[16], rb[16];
@@ -1380,11 +1383,11 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
             }
             warp_reduce_scatter<TF_C>(hs, lane);  // lane 2c holds the warp's sum of channel c
             if (!(lane & 1)) hred[warp * 32 + (lane >> 1)] = hs[0];
-            tc::named_bar_sync(1, TP_EPI);
+            tc::named_bar_sync(1, EPI);
             if (warp == 0) {
                 float part = 0.f;
                 if (lane < TF_C) {
-                    for (int w = 0; w < TP_EPI_WARPS; ++w) part += hred[w * 32 + lane];
+                    for (int w = 0; w < EW; ++w) part += hred[w * 32 + lane];
                     part = fc_w[lane] * (part / (float)W);
                 }
 #pragma unroll
@@ -1398,7 +1401,7 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tiny_pipe(const TinyArgs args
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == TP_EPI_WARPS) tc::tmem_dealloc(tmem, 512);
+    if (warp == EW) tc::tmem_dealloc(tmem, 512);
 }
 
 bool tiny_compatible(const afg_ctx *ctx) {
@@ -1418,22 +1421,38 @@ __host__ inline int pipe_seg_cache_cap(size_t total) { return tiny_seg_cache_cap
 // subtiles of the 1.5 s window at 2048 Hz (3072 positions): compiled with a fixed geometry
 constexpr int TP_MT_FIXED = 24;
 
-template <int G, int MTS>
+template <int G, int MTS, int EW = TP_EPI_WARPS, int MW = TP_MMA_WARPS>
 cudaError_t launch_pipe_t(const TinyArgs &a, unsigned grid, size_t smem, cudaStream_t st, bool pdl) {
-    if (pdl) return launch_pdl(k_tiny_pipe<G, MTS>, dim3(grid), dim3(TP_THREADS), smem, st, a);
-    k_tiny_pipe<G, MTS><<<grid, TP_THREADS, smem, st>>>(a);
+    constexpr int threads = (EW + MW) * 32;
+    if (pdl) return launch_pdl(k_tiny_pipe<G, MTS, EW, MW>, dim3(grid), dim3(threads), smem, st, a);
+    k_tiny_pipe<G, MTS, EW, MW><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// The pipelined network over a.n_win windows; the fixed-geometry build for 8 groups and 3072 positions
-cudaError_t launch_pipe(const TinyArgs &a, unsigned grid, size_t smem, cudaStream_t st, bool pdl) {
+// Tuning candidates of the pipelined network's fixed geometry (8 groups, 3072 positions): epilogue warps,
+// issue warps and the issue warps' polling sleep; candidate 0 is the default.
+struct PipeVariant {
+    int ew, mw;
+    uint32_t spin_ns;
+};
+constexpr PipeVariant kPipeVariants[] = {{12, 2, 64}, {12, 2, 0}, {12, 2, 256}, {12, 1, 64},
+                                         {8, 2, 64},  {8, 1, 64}, {8, 1, 0},   {12, 1, 0}};
+constexpr int kNPipeVariants = (int)(sizeof(kPipeVariants) / sizeof(kPipeVariants[0]));
+
+// The pipelined network over a.n_win windows (a.spin_ns set by the caller); the fixed-geometry build for
+// 8 groups and 3072 positions, with the warp counts ew / mw the context chose
+cudaError_t launch_pipe(const TinyArgs &a, unsigned grid, size_t smem, cudaStream_t st, bool pdl, int ew = TP_EPI_WARPS,
+                        int mw = TP_MMA_WARPS) {
     switch (a.G) {
         case 1: return launch_pipe_t<1, 0>(a, grid, smem, st, pdl);
         case 2: return launch_pipe_t<2, 0>(a, grid, smem, st, pdl);
         case 4: return launch_pipe_t<4, 0>(a, grid, smem, st, pdl);
         case 8:
-            return a.W == 128 * TP_MT_FIXED ? launch_pipe_t<8, TP_MT_FIXED>(a, grid, smem, st, pdl)
-                                            : launch_pipe_t<8, 0>(a, grid, smem, st, pdl);
+            if (a.W != 128 * TP_MT_FIXED) return launch_pipe_t<8, 0>(a, grid, smem, st, pdl);
+            if (ew == 8) return mw == 1 ? launch_pipe_t<8, TP_MT_FIXED, 8, 1>(a, grid, smem, st, pdl)
+                                        : launch_pipe_t<8, TP_MT_FIXED, 8, 2>(a, grid, smem, st, pdl);
+            return mw == 1 ? launch_pipe_t<8, TP_MT_FIXED, 12, 1>(a, grid, smem, st, pdl)
+                           : launch_pipe_t<8, TP_MT_FIXED, 12, 2>(a, grid, smem, st, pdl);
         default: return launch_pipe_t<16, 0>(a, grid, smem, st, pdl);
     }
 }
@@ -1501,7 +1520,10 @@ int net_tc_prepare(afg_ctx *ctx) {
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
     AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
-    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8, TP_MT_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8, TP_MT_FIXED, 12, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8, TP_MT_FIXED, 12, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8, TP_MT_FIXED, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
+    AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_pipe<8, TP_MT_FIXED, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem));
     if (ctx->cfg.win_len % (128 * TF_CLUSTER) == 0) {  // list mode on clusters: a quarter window per CTA
         const int smem_c = (int)tiny_smem(ctx->cfg.win_len / TF_CLUSTER, n_conv, k).total + TF_XCH;
         AFG_CUDA(ctx, cudaFuncSetAttribute(k_tiny_fused<1, TF_CLUSTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1555,7 +1577,8 @@ int launch_infer_bf16_batch(afg_ctx *ctx, const float *white, int64_t y_stride, 
     const unsigned grid = (unsigned)std::min<int64_t>(total_win, std::max(sms, 1));
     const double flops = 2.0 * total_win * W * TF_C * ((3.0 * TF_C) * n_conv + 2.0 * a.k_stem);
     KScope ks(ctx, st, KK_TINY_TC, flops, (double)total_win * (2.0 * W * 4.0 + 4.0));
-    cudaError_t e = launch_pipe(a, grid, smem, st, false);
+    a.spin_ns = P.tiny_spin_ns;
+    cudaError_t e = launch_pipe(a, grid, smem, st, false, P.tiny_ew, P.tiny_mw);
     if (e != cudaSuccess) return afg_cuda_fail(ctx, e, "k_tiny_pipe(batch)");
     return AFG_OK;
 }
@@ -1609,7 +1632,8 @@ int launch_infer_bf16_list(afg_ctx *ctx, const WinPtr *wins_dev, int64_t n_win, 
         return AFG_OK;
     }
     const size_t psmem = pipe_smem(W, n_conv, a.k_stem).total;
-    AFG_CUDA(ctx, launch_pipe(a, grid, psmem, st, true));
+    a.spin_ns = P.tiny_spin_ns;
+    AFG_CUDA(ctx, launch_pipe(a, grid, psmem, st, true, P.tiny_ew, P.tiny_mw));
     return AFG_OK;
 }
 
@@ -1653,7 +1677,145 @@ int launch_infer_bf16(afg_ctx *ctx, const float *y, int64_t n_y, int64_t y_strid
     const double flops_stem = 2.0 * n_win * W * TF_C * 2.0 * a.k_stem;
     KScope ks(ctx, st, KK_TINY_TC, flops_conv + flops_stem, (double)n_win * (2.0 * W * 4.0 + 4.0));
     const size_t psmem = pipe_smem(W, n_conv, a.k_stem).total;
-    cudaError_t e = launch_pipe(a, grid, psmem, st, false);
+    a.spin_ns = P.tiny_spin_ns;
+    cudaError_t e = launch_pipe(a, grid, psmem, st, false, P.tiny_ew, P.tiny_mw);
     if (e != cudaSuccess) return afg_cuda_fail(ctx, e, "k_tiny_pipe");
+    return AFG_OK;
+}
+
+namespace {
+
+__global__ void k_fill_f32(float *x, int64_t n, uint32_t seed) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B1u ^ seed;
+        h ^= h >> 16;
+        h *= 0x85EBCA6Bu;
+        h ^= h >> 13;
+        x[i] = (float)(h >> 8) * (4.0f / 16777216.0f) - 2.0f;
+    }
+}
+
+void tiny_tuning_record(const NetPlan &P, afg_fused_tuning &t) {
+    memset(&t, 0, sizeof t);
+    t.epi_warps = P.tiny_ew;
+    t.issue_warps = P.tiny_mw;
+    t.spin_ns = (int32_t)P.tiny_spin_ns;
+    t.tuned = P.tiny_tuned;
+    t.n_candidates = P.tiny_n_cand;
+    t.us_chosen = P.tiny_us_chosen;
+    t.us_default = P.tiny_us_default;
+}
+
+}  // namespace
+
+// The fused 16-channel network's knobs are tuned where its fixed geometry is compiled (BF16 context,
+// 8 GroupNorm groups, 3072-position windows).
+bool net_tc_tiny_tunable(const afg_ctx *ctx) {
+    return ctx->cfg.precision == AFG_BF16 && tiny_compatible(ctx) && ctx->plan.tc_params &&
+           ctx->plan.net.groups == 8 && ctx->cfg.win_len == 128 * TP_MT_FIXED;
+}
+
+// Time every candidate of kPipeVariants on nw windows (stride 64) of synthetic whitened strain and keep the fastest.
+int net_tc_tiny_autotune(afg_ctx *ctx, int64_t n_win, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    AFG_CUDA(ctx, cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return afg_fail(ctx, AFG_ERR_STATE, "autotune: stream is capturing");
+    NetPlan &P = ctx->plan;
+    const int64_t nw = std::max<int64_t>(1, std::min<int64_t>(n_win > 0 ? n_win : 4096, 65536));
+    const int64_t stride = 64, n_y = (nw - 1) * stride + ctx->cfg.win_len;
+    float *y = nullptr, *z = nullptr;
+    int rc = afg_ws_reserve(ctx, WS_WHITE, (size_t)2 * n_y * sizeof(float), (void **)&y);
+    if (!rc) rc = afg_ws_reserve(ctx, WS_LOGITS, (size_t)nw * sizeof(float), (void **)&z);
+    if (rc) return rc;
+    k_fill_f32<<<1024, 256, 0, st>>>(y, 2 * n_y, 0x2468ACEu);
+    AFG_LAUNCH_CHECK(ctx, "k_fill_f32");
+    cudaEvent_t e0, e1;
+    AFG_CUDA(ctx, cudaEventCreate(&e0));
+    AFG_CUDA(ctx, cudaEventCreate(&e1));
+    const NetPlan saved = P;
+    const int reps = 3;
+    float best = 0.f, t_dflt = 0.f;
+    int best_i = 0, err = AFG_OK;
+    for (int i = 0; i < kNPipeVariants && !err; ++i) {
+        P.tiny_ew = kPipeVariants[i].ew;
+        P.tiny_mw = kPipeVariants[i].mw;
+        P.tiny_spin_ns = kPipeVariants[i].spin_ns;
+        err = launch_infer_bf16(ctx, y, n_y, n_y, 0, stride, nw, 0, z, st);  // warm
+        if (err) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) err = afg_cuda_fail(ctx, cudaGetLastError(), "autotune: event");
+        for (int r = 0; r < reps && !err; ++r) err = launch_infer_bf16(ctx, y, n_y, n_y, 0, stride, nw, 0, z, st);
+        if (err) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            err = afg_cuda_fail(ctx, cudaGetLastError(), "autotune: event timing");
+            break;
+        }
+        const float us = ms * 1000.f / reps;
+        if (i == 0) t_dflt = us;
+        if (best == 0.f || us < best) {
+            best = us;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err) {
+        P.tiny_ew = saved.tiny_ew;
+        P.tiny_mw = saved.tiny_mw;
+        P.tiny_spin_ns = saved.tiny_spin_ns;
+        return err;
+    }
+    P.tiny_ew = kPipeVariants[best_i].ew;
+    P.tiny_mw = kPipeVariants[best_i].mw;
+    P.tiny_spin_ns = kPipeVariants[best_i].spin_ns;
+    P.tiny_tuned = 1;
+    P.tiny_n_cand = kNPipeVariants;
+    P.tiny_us_chosen = best;
+    P.tiny_us_default = t_dflt;
+    AFG_CUDA(ctx, cudaStreamSynchronize(st));
+    int flag = 0;
+    AFG_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        AFG_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return afg_fail(ctx, AFG_ERR_TIMEOUT, "autotune: a bounded device-side wait gave up");
+    }
+    return AFG_OK;
+}
+
+int net_tc_tiny_tuning_get(afg_ctx *ctx, afg_fused_tuning *out) {
+    if (ctx->cfg.precision != AFG_BF16 || !tiny_compatible(ctx) || !ctx->plan.tc_params)
+        return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "fused tuning: the context has no fused 16-channel BF16 network");
+    tiny_tuning_record(ctx->plan, *out);
+    return AFG_OK;
+}
+
+int net_tc_tiny_tuning_candidates(afg_ctx *ctx, afg_fused_tuning *out, int cap, int *n_out) {
+    if (!net_tc_tiny_tunable(ctx))
+        return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "fused tuning: no tunable fused network (BF16, 8 groups, 3072 positions)");
+    *n_out = kNPipeVariants;
+    for (int i = 0; i < kNPipeVariants && i < cap; ++i) {
+        memset(&out[i], 0, sizeof out[i]);
+        out[i].epi_warps = kPipeVariants[i].ew;
+        out[i].issue_warps = kPipeVariants[i].mw;
+        out[i].spin_ns = (int32_t)kPipeVariants[i].spin_ns;
+    }
+    return AFG_OK;
+}
+
+int net_tc_tiny_tuning_set(afg_ctx *ctx, const afg_fused_tuning *in) {
+    if (!net_tc_tiny_tunable(ctx))
+        return afg_fail(ctx, AFG_ERR_UNSUPPORTED, "fused tuning: no tunable fused network (BF16, 8 groups, 3072 positions)");
+    if ((in->epi_warps != 8 && in->epi_warps != 12) || (in->issue_warps != 1 && in->issue_warps != 2) ||
+        in->spin_ns < 0 || in->spin_ns > 100000)
+        return afg_fail(ctx, AFG_ERR_ARG, "fused tuning: epi_warps 8 or 12, issue_warps 1 or 2, spin_ns in [0, 1e5]");
+    NetPlan &P = ctx->plan;
+    P.tiny_ew = in->epi_warps;
+    P.tiny_mw = in->issue_warps;
+    P.tiny_spin_ns = (uint32_t)in->spin_ns;
+    P.tiny_tuned = in->tuned ? 1 : 0;
+    P.tiny_us_chosen = in->us_chosen;
+    P.tiny_us_default = in->us_default;
+    P.tiny_n_cand = in->n_candidates;
     return AFG_OK;
 }

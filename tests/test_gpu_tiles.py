@@ -121,3 +121,53 @@ def test_autotune_is_refused_without_a_tensor_core_plan():
         ctx.autotune(64)
     assert ei.value.status == abi.AFG_ERR_UNSUPPORTED
     ctx.close()
+
+
+def test_fused_network_candidates_compute_the_same_network(capsys):
+    """Every tuning candidate of the fused 16-channel network (8 or 12 epilogue warps, 1 or 2 issue warps,
+    polling sleep) computes the same network: each candidate's logits against the oracle within the BF16
+    tolerance of that network (2e-3 (1 + |z|)), and bit-identical to the default where only the issue warps
+    or the polling sleep differ (the arithmetic and its order are the same).  afg_autotune then keeps the
+    fastest, and the context computes the same logits with it."""
+    from oracle import oracle as orc
+    wl = inputs.PLAIN_64S
+    w = inputs.make_weights(wl.net, wl.weight_seed)
+    rng = np.random.default_rng(7)
+    y = rng.standard_normal((2, 40000))
+    stride, n_win = 131, 200
+    want = orc.infer_windows(wl.net, w, y, wl.win_len, 0, stride, n_win)
+    yd = torch.from_numpy(y.astype(np.float32)).cuda()
+    ctx = abi.Context(wl, w, precision=abi.AFG_BF16)
+    cands = ctx.fused_tuning_candidates()
+    assert len(cands) >= 4 and cands[0]["epi_warps"] == 12 and cands[0]["issue_warps"] == 2
+    got = {}
+    for c in cands:
+        ctx.set_fused_tuning(c)
+        z = ctx.infer_windows(yd, 0, stride, n_win).cpu().numpy()
+        ctx.sync()
+        err = np.abs(z - want) / (1 + np.abs(want))
+        with capsys.disabled():
+            print(f"\nfused candidate {c['epi_warps']} epilogue / {c['issue_warps']} issue warps, "
+                  f"{c['spin_ns']} ns: max |dz|/(1+|z|) vs oracle = {err.max():.2e}")
+        assert err.max() < 2e-3, (c, err.max())
+        got[(c["epi_warps"], c["issue_warps"], c["spin_ns"])] = z
+    for k, z in got.items():
+        same_order = next(v for kk, v in got.items() if kk[0] == k[0])
+        assert np.array_equal(z, same_order), k
+    ctx.autotune(1024)
+    t = ctx.fused_tuning()
+    assert t["tuned"] == 1 and t["n_candidates"] == len(cands) and 0 < t["us_chosen"] <= t["us_default"]
+    z = ctx.infer_windows(yd, 0, stride, n_win).cpu().numpy()
+    ctx.sync()
+    assert np.array_equal(z, got[(t["epi_warps"], t["issue_warps"], t["spin_ns"])])
+    with capsys.disabled():
+        print(f"fused tuning: {t}")
+    with pytest.raises(abi.AfgError) as ei:
+        ctx.set_fused_tuning({"epi_warps": 16, "issue_warps": 2, "spin_ns": 64})
+    assert ei.value.status == abi.AFG_ERR_ARG
+    ctx.close()
+    ctx32 = abi.Context(wl, w, precision=abi.AFG_FP32)
+    with pytest.raises(abi.AfgError) as ei:
+        ctx32.fused_tuning()
+    assert ei.value.status == abi.AFG_ERR_UNSUPPORTED
+    ctx32.close()
