@@ -112,6 +112,38 @@ def test_whiten_ragged_and_epochs(c1, ctx_tiny):
             assert np.max(np.abs(got[d, lo:hi] - ref)) < WHITE_ATOL
 
 
+@pytest.mark.parametrize("fir_len,epoch_len,out_len", [
+    (2048, 16384, 16384 * 2 + 15000),  # each epoch: 14,336 outputs on 16384 points + 2,048 on 4096; ragged last
+    (2048, 16384, 16384 + 10000),      # the last epoch ends inside its 16384-point block
+    (4096, 16384, 16384 * 2 + 5000),   # 12,288 + a 4,096-output remainder, too long for 4096 points
+    (1024, 16384, 16384 * 2 + 16000),  # 15,360 + 1,024 on 4096 points
+    (2048, 0, 40000),                  # one filter: 2 x 14,336 + 11,328 on 16384 points
+    (2048, 0, 30000),                  # 2 x 14,336 + 1,328 on 4096 points
+])
+def test_whiten_block_layouts(c1, fir_len, epoch_len, out_len):
+    """Whitening blocks are laid out per filter epoch (the most outputs a 16384-point transform keeps,
+    the epoch's remainder on a 4096-point one where it fits): every layout against the oracle's direct
+    FIR with the same PSDs, for 1 s, 0.5 s and 2 s filters, epoch and plain mode, ragged ends."""
+    import dataclasses
+    wl, x, w, _ = c1
+    ctx = abi.Context(dataclasses.replace(wl, fir_len=fir_len), w)
+    xd = _dev(x)
+    out_first = 40000
+    n_psd = (out_len + epoch_len - 1) // epoch_len if epoch_len else 1
+    psd = ctx.psd_estimate(xd, n_psd=n_psd, psd_step=16384 if n_psd > 1 else 0, psd_span=65536)
+    got = ctx.whiten(xd, psd, out_first, out_len, epoch_len=epoch_len).cpu().numpy()
+    ctx.sync()
+    ctx.close()
+    p = psd.cpu().numpy()
+    span = epoch_len if epoch_len else out_len
+    for d in range(2):
+        for e in range(n_psd):
+            lo, hi = e * span, min((e + 1) * span, out_len)
+            taps = orc.whitening_taps(p[d, e], 16384, 2048.0, 32.0, fir_len)
+            ref = orc.fir(x[d].astype(np.float64), taps, out_first + lo, hi - lo)
+            assert np.max(np.abs(got[d, lo:hi] - ref)) < WHITE_ATOL, (d, e)
+
+
 def test_infer_windows_tiny_with_shift(c1, ctx_tiny):
     wl, x, w, ref = c1
     white = ref["white"].astype(np.float32)
