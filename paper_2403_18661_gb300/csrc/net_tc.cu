@@ -1732,7 +1732,8 @@ int net_tc_tiny_autotune(afg_ctx *ctx, int64_t n_win, cudaStream_t st) {
     cudaEvent_t e0, e1;
     AFG_CUDA(ctx, cudaEventCreate(&e0));
     AFG_CUDA(ctx, cudaEventCreate(&e1));
-    const NetPlan saved = P;
+    const int saved_ew = P.tiny_ew, saved_mw = P.tiny_mw;
+    const uint32_t saved_spin = P.tiny_spin_ns;
     const int reps = 3;
     float best = 0.f, t_dflt = 0.f;
     int best_i = 0, err = AFG_OK;
@@ -1761,9 +1762,9 @@ int net_tc_tiny_autotune(afg_ctx *ctx, int64_t n_win, cudaStream_t st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err) {
-        P.tiny_ew = saved.tiny_ew;
-        P.tiny_mw = saved.tiny_mw;
-        P.tiny_spin_ns = saved.tiny_spin_ns;
+        P.tiny_ew = saved_ew;
+        P.tiny_mw = saved_mw;
+        P.tiny_spin_ns = saved_spin;
         return err;
     }
     P.tiny_ew = kPipeVariants[best_i].ew;
