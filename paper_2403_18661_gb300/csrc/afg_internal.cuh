@@ -25,7 +25,7 @@ constexpr int WB = 8192;
 
 // Epochs per thread of the Welch averaging kernel; its grid's y extent is
 // ceil(n_psd / PSD_EPT), which must stay within 65535.
-constexpr int PSD_EPT = 16;
+constexpr int PSD_EPT = 32;
 
 // Validate the layout of a Welch request (x: [n_det][n], n_psd epochs of
 // psd_span samples every psd_step, segments of NFFT every hop) without

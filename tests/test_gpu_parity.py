@@ -79,8 +79,8 @@ def test_psd_epochs_share_segments(c1, ctx_tiny):
 @pytest.mark.parametrize("step", [8192, 16384])
 def test_psd_many_epochs(ctx_tiny, step, capsys):
     # 40 epochs every 4 s (a sliding sum over the periodograms) or every 8 s (the running prefix of the
-    # epoch workloads' 64 s PSDs in 8 s epochs), each the mean of 15 segments: the per-thread runs of
-    # epochs of the averaging kernel end at epochs 16 and 32 and leave a partial last run
+    # epoch workloads' 64 s PSDs in 8 s epochs), each the mean of 15 segments: the per-thread run of
+    # 32 epochs of the averaging kernel is followed by a partial run of 8
     n_psd, span = 40, 131072
     x = np.stack([inputs.coloured_noise(step * (n_psd - 1) + span, 31 + d, inputs.NoiseModel(), 2048)
                   for d in range(2)]).astype(np.float32)
