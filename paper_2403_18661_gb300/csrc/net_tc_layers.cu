@@ -157,10 +157,12 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
 // of value l.
 template <int CO, int CG>
 __device__ __forceinline__ float pos_group_partials(uint32_t tb, int hsel, int MT, int lane) {
-    static_assert(CO / CG <= 16 && CO % 32 == 0, "at most 16 groups");
-    float2 acc[16];  // per group: (sum, sum of squares), one packed FMA per value
+    static_assert(CO / CG <= 16 && CO % 32 == 0 && CG % 2 == 0, "at most 16 groups of an even channel count");
+    // per group: the sums and the sums of squares of its even and of its odd channels, one packed add and one
+    // packed FMA per two adjacent channels (the loaded registers are the operand pairs as they stand)
+    float2 s2[16], q2[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 16; ++i) s2[i] = q2[i] = make_float2(0.f, 0.f);
     for (int j = hsel; j < MT; j += EPI_PARTS) {
 #pragma unroll
         for (int c0 = 0; c0 < CO; c0 += 16) {
@@ -168,18 +170,19 @@ __device__ __forceinline__ float pos_group_partials(uint32_t tb, int hsel, int M
             tc::tmem_ld16_nowait(tb + (uint32_t)(j * CO + c0), r);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const float v = __uint_as_float(r[c]);
+            for (int c = 0; c < 16; c += 2) {
+                const float2 v = make_float2(__uint_as_float(r[c]), __uint_as_float(r[c + 1]));
                 const int g = (c0 + c) / CG;
-                acc[g] = __ffma2_rn(make_float2(v, v), make_float2(1.f, v), acc[g]);
+                s2[g] = __fadd2_rn(s2[g], v);
+                q2[g] = __ffma2_rn(v, v, q2[g]);
             }
         }
     }
     float gp[32];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        gp[i] = acc[i].x;
-        gp[16 + i] = acc[i].y;
+        gp[i] = s2[i].x + s2[i].y;
+        gp[16 + i] = q2[i].x + q2[i].y;
     }
     return warp_reduce_scatter32(gp, lane);
 }
@@ -677,8 +680,9 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                     }
                     float s = 0.f, qq = 0.f;
                     if (active) {
-                        // (sum, sum of squares) in two packed accumulators, one packed FMA per value
-                        float2 m0 = make_float2(0.f, 0.f), m1 = make_float2(0.f, 0.f);
+                        // sums and sums of squares of adjacent positions as packed pairs: one packed add and
+                        // one packed FMA per two values, on the loaded registers as they stand
+                        float2 s0 = make_float2(0.f, 0.f), q0 = s0, s1 = s0, q1 = s0;
                         int p0 = 0;
                         for (; p0 + 32 <= Lh; p0 += 32) {
                             uint32_t r0[16], r1[16];
@@ -686,10 +690,13 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                             tc::tmem_ld16_nowait(tw + (uint32_t)(p0 + 16), r1);
                             tc::tmem_wait_ld();
 #pragma unroll
-                            for (int p = 0; p < 16; ++p) {
-                                const float v0 = __uint_as_float(r0[p]), v1 = __uint_as_float(r1[p]);
-                                m0 = __ffma2_rn(make_float2(v0, v0), make_float2(1.f, v0), m0);
-                                m1 = __ffma2_rn(make_float2(v1, v1), make_float2(1.f, v1), m1);
+                            for (int p = 0; p < 16; p += 2) {
+                                const float2 v0 = make_float2(__uint_as_float(r0[p]), __uint_as_float(r0[p + 1]));
+                                const float2 v1 = make_float2(__uint_as_float(r1[p]), __uint_as_float(r1[p + 1]));
+                                s0 = __fadd2_rn(s0, v0);
+                                q0 = __ffma2_rn(v0, v0, q0);
+                                s1 = __fadd2_rn(s1, v1);
+                                q1 = __ffma2_rn(v1, v1, q1);
                             }
                         }
                         if (p0 < Lh) {
@@ -697,13 +704,14 @@ __global__ void __launch_bounds__(LT, 1) k_conv_tc(const LayerArgs a) {
                             tc::tmem_ld16_nowait(tw + (uint32_t)p0, r0);
                             tc::tmem_wait_ld();
 #pragma unroll
-                            for (int p = 0; p < 16; ++p) {
-                                const float v0 = __uint_as_float(r0[p]);
-                                m0 = __ffma2_rn(make_float2(v0, v0), make_float2(1.f, v0), m0);
+                            for (int p = 0; p < 16; p += 2) {
+                                const float2 v0 = make_float2(__uint_as_float(r0[p]), __uint_as_float(r0[p + 1]));
+                                s0 = __fadd2_rn(s0, v0);
+                                q0 = __ffma2_rn(v0, v0, q0);
                             }
                         }
-                        s = m0.x + m1.x;
-                        qq = m0.y + m1.y;
+                        s = (s0.x + s0.y) + (s1.x + s1.y);
+                        qq = (q0.x + q0.y) + (q1.x + q1.y);
                         for (int o = cg / 2; o > 0; o >>= 1) {
                             s += __shfl_xor_sync(0xffffffffu, s, o);
                             qq += __shfl_xor_sync(0xffffffffu, qq, o);
@@ -1116,9 +1124,9 @@ __global__ void __launch_bounds__(STC_T, 2) k_stem_tc(const float *__restrict__ 
     };
 
     // ---- pass 1: GroupNorm sums (sum, sum of squares) of the warp's NLG groups
-    float2 gs[NLG];
+    float2 gs2[NLG], gq2[NLG];  // per group: sums and sums of squares of its even and odd channels
 #pragma unroll
-    for (int g = 0; g < NLG; ++g) gs[g] = make_float2(0.f, 0.f);
+    for (int g = 0; g < NLG; ++g) gs2[g] = gq2[g] = make_float2(0.f, 0.f);
     for (int rd = 0; rd < rounds; ++rd) {
         mma_round(rd);
 #pragma unroll 1
@@ -1126,11 +1134,18 @@ __global__ void __launch_bounds__(STC_T, 2) k_stem_tc(const float *__restrict__ 
             float v[32];
             tc::tmem_ld32(tq + (uint32_t)(64 * m), v);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) gs[c / CG] = __ffma2_rn(make_float2(v[c], v[c]), make_float2(1.f, v[c]), gs[c / CG]);
+            for (int c = 0; c < 32; c += 2) {  // adjacent channels of a group as packed pairs
+                const float2 vv = make_float2(v[c], v[c + 1]);
+                gs2[c / CG] = __fadd2_rn(gs2[c / CG], vv);
+                gq2[c / CG] = __ffma2_rn(vv, vv, gq2[c / CG]);
+            }
         }
         tc::fence_before_sync();
         __syncthreads();  // every TMEM read of the round is done before the next round's MMAs
     }
+    float2 gs[NLG];
+#pragma unroll
+    for (int g = 0; g < NLG; ++g) gs[g] = make_float2(gs2[g].x + gs2[g].y, gq2[g].x + gq2[g].y);
 #pragma unroll
     for (int g = 0; g < NLG; ++g)
 #pragma unroll
