@@ -971,7 +971,7 @@ __device__ __forceinline__ void acc_channel_pairs(const uint32_t (&r)[16], float
 // flag (stop).  red is this layer's half of a double buffer: a warp that runs ahead writes the
 // next layer's sums into the other half, and cannot get two layers ahead past the barrier.
 template <int G, int EW>
-__device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, float eps, const float *gamma,
+__device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float inv_cnt, float eps, const float *gamma,
                                               const float *beta, float *red, float *maps, float (&sc)[TF_C],
                                               float (&sh)[TF_C], const volatile int *abort_flag, bool &stop) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -995,8 +995,8 @@ __device__ __forceinline__ void gn_reduce_epi(const float2 (&sq)[G], float cnt, 
         for (int w = 0; w < EW; ++w) t += red[w * 32 + lane];
     const int c = lane & (TF_C - 1), g = c / (TF_C / G);
     const float s_g = __shfl_sync(0xffffffffu, t, g), q_g = __shfl_sync(0xffffffffu, t, G + g);
-    const float mean = s_g / cnt;
-    const float a = rsqrtf(fmaxf(q_g / cnt - mean * mean, 0.f) + eps) * gamma[c];
+    const float mean = s_g * inv_cnt;  // (a multiply by the reciprocal of the group's element count: no divide)
+    const float a = rsqrtf(fmaxf(q_g * inv_cnt - mean * mean, 0.f) + eps) * gamma[c];
     const float b = beta[c] - mean * a;
     // the 16 maps to every lane through the warp's own slot (broadcast loads, adjacent pairs aligned for
     // the packed normalisation)
@@ -1296,7 +1296,7 @@ __global__ void __launch_bounds__((EW + MW) * 32, 1) k_tiny_pipe(const TinyArgs 
                 }
                 float sc[TF_C], sh[TF_C];
                 bool stop_now = false;
-                gn_reduce_epi<G, EW>(sq, cnt, args.eps, gam, gam + TF_C, red + (seq & 1) * TP_EPI_RED, red + 3 * TP_EPI_RED,
+                gn_reduce_epi<G, EW>(sq, 1.0f / cnt, args.eps, gam, gam + TF_C, red + (seq & 1) * TP_EPI_RED, red + 3 * TP_EPI_RED,
                                  sc, sh, abort_flag, stop_now);
                 if (stop_now) {
                     stopped = true;
