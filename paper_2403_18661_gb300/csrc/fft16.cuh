@@ -4,10 +4,10 @@
 //
 // Layout: 512 threads, one radix-16 butterfly per thread per pass; the 8192
 // points live in shared memory with one pad slot after every 16, so that
-// every pass below reads and writes without bank conflicts.  Twiddles are
-// computed in registers (sincospif of the butterfly's base angle and of its
-// 4th and 8th multiples, other powers by products of those) instead of read
-// from a table.
+// every pass below reads and writes without bank conflicts.  A butterfly
+// reads three twiddles (its base angle's and the 4th and 8th multiples', FP32
+// values rounded from FP64 ones) from a per-pass table ordered by butterfly
+// offset, so a warp's reads coalesce; the other powers are products of those.
 //
 // Forward transform (Stockham auto-sort, natural order in and out): radix 16
 // at strides Ns = 1, 16, 256, then radix 2 at Ns = 4096.  The first pass takes
@@ -49,19 +49,43 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 template <int S> __device__ __forceinline__ float2 mul_i(float2 a) {
     return S < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
 }
-// exp(S i pi x)
-template <int S> __device__ __forceinline__ float2 cis(float x) {
-    float s, c;
-    sincospif(x, &s, &c);
-    return make_float2(c, S < 0 ? -s : s);
+// Packed complex add and subtract: one FP32x2 instruction each (a - b as the exact fma(b, -1, a)).
+__device__ __forceinline__ float2 cadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+// ---- twiddle table: FP32 values of exp(-i pi a), rounded from FP64 (k_tw32 fills it once per device)
+//   [tw16_off(Ns), +3 Ns): radix-16 passes of the 8192-point plan, Ns in {2, 16, 32, 256, 512}:
+//       w1, w4, w8 of butterfly offset k < Ns at +k, +Ns + k, +2 Ns + k (a = m k / 8 Ns, m = 1, 4, 8)
+//   [tw4_off(Ns), +Ns): radix-4 passes of the 2048-point plan, Ns = 2 .. 512: w1 (a = k / 2 Ns)
+//   [TW_SPLIT, +4097): the split and radix-2 table, a = j / 8192 for j = 0 .. 4096
+__host__ __device__ constexpr int tw16_off(int Ns) {
+    return Ns == 2 ? 0 : Ns == 16 ? 6 : Ns == 32 ? 54 : Ns == 256 ? 150 : Ns == 512 ? 918 : -1;
 }
+constexpr int TW16_END = 918 + 3 * 512;
+__host__ __device__ constexpr int tw4_off(int Ns) { return TW16_END + Ns - 2; }  // 2 + 4 + .. + Ns/2 = Ns - 2
+constexpr int TW_SPLIT = tw4_off(1024);
+constexpr int TW_TOTAL = TW_SPLIT + 4097;
+static_assert(tw16_off(16) == 3 * 2 && tw16_off(32) == tw16_off(16) + 3 * 16 && tw16_off(256) == tw16_off(32) + 3 * 32 &&
+                  tw16_off(512) == tw16_off(256) + 3 * 256,
+              "radix-16 pass tables are packed back to back");
+static __device__ float2 g_tw[TW_TOTAL];
+
+// exp(S i pi a) from table entry i (the table holds the S = -1 value)
+template <int S> __device__ __forceinline__ float2 tw_at(int i) {
+    const float2 w = __ldg(&g_tw[i]);
+    return S < 0 ? w : make_float2(w.x, -w.y);
+}
+// exp(S i pi j / 8192), 0 <= j <= 4096
+template <int S> __device__ __forceinline__ float2 tw_split(int j) { return tw_at<S>(TW_SPLIT + j); }
 
 // DFT of 4 points in natural order, kernel exp(S 2 pi i / 4)
+// (The sums whose operands are register pairs as they stand are packed; the two that take S i (v1 - v3),
+// whose parts trade places, stay scalar.)
 template <int S> __device__ __forceinline__ void dft4(float2 &v0, float2 &v1, float2 &v2, float2 &v3) {
-    const float2 e0 = cadd(v0, v2), e1 = csub(v0, v2);
-    const float2 o0 = cadd(v1, v3), o1 = mul_i<S>(csub(v1, v3));
-    v0 = cadd(e0, o0);
-    v2 = csub(e0, o0);
+    const float2 e0 = cadd2(v0, v2), e1 = csub2(v0, v2);
+    const float2 o0 = cadd2(v1, v3), o1 = mul_i<S>(csub2(v1, v3));
+    v0 = cadd2(e0, o0);
+    v2 = csub2(e0, o0);
     v1 = cadd(e1, o1);
     v3 = csub(e1, o1);
 }
@@ -96,9 +120,11 @@ template <int S> __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 }
 __device__ __forceinline__ int out16(int q) { return 4 * (q & 3) + (q >> 2); }
 
-// v[r] *= exp(S i pi x r), r = 1..15 (x = 2 k / (16 Ns) for butterfly offset k)
-template <int S> __device__ __forceinline__ void twiddle16(float2 (&v)[16], float x) {
-    const float2 w1 = cis<S>(x), w4 = cis<S>(4.0f * x), w8 = cis<S>(8.0f * x);
+// v[r] *= exp(S i pi x r), r = 1..15 (x = k / 8 Ns for butterfly offset k < Ns)
+template <int S, int Ns> __device__ __forceinline__ void twiddle16(float2 (&v)[16], int k) {
+    constexpr int T = tw16_off(Ns);
+    static_assert(T >= 0, "no twiddle table for this stride");
+    const float2 w1 = tw_at<S>(T + k), w4 = tw_at<S>(T + Ns + k), w8 = tw_at<S>(T + 2 * Ns + k);
     const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1), w12 = cmul(w8, w4);
     v[1] = cmul(v[1], w1);
     v[2] = cmul(v[2], w2);
@@ -120,22 +146,29 @@ template <int S> __device__ __forceinline__ void twiddle16(float2 (&v)[16], floa
 // Radix-16 butterfly of thread j at stride Ns on inputs already in v (read
 // from positions j + 512 r): twiddles, DFT; outputs stay in v (out16 order).
 template <int S, int Ns> __device__ __forceinline__ void butterfly16(float2 (&v)[16], int j) {
-    if (Ns > 1) twiddle16<S>(v, (float)(j & (Ns - 1)) / (float)(8 * Ns));
+    if constexpr (Ns > 1) twiddle16<S, Ns>(v, j & (Ns - 1));
     dft16<S>(v);
 }
 
 // Store thread j's butterfly outputs of a pass at stride Ns (Stockham order).
+// (For a power-of-two Ns, pad(base + q Ns) = pad(base) + off(q) with the constant off(q) = q Ns + (q Ns >> 4):
+// base = 16 (j - k) + k with k < Ns, so adding q Ns to base & 15 = k crosses a multiple of 16 exactly when
+// q Ns does.  The same holds for the radix-4 bases 4 (j - k) + k, whose low four bits plus r Ns stay below
+// the next multiple of 16 that r Ns passes.)
+__host__ __device__ constexpr int pad_off(int i) { return i + (i >> 4); }
 template <int Ns> __device__ __forceinline__ void store16(float2 *d, const float2 (&v)[16], int j) {
     const int k = j & (Ns - 1);
-    const int base = (j - k) * 16 + k;
+    float2 *p = d + pad((j - k) * 16 + k);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) d[pad(base + q * Ns)] = v[out16(q)];
+    for (int q = 0; q < 16; ++q) p[pad_off(q * Ns)] = v[out16(q)];
 }
 
 // the 16 inputs of butterfly j of a radix-16 pass over LEN = 16 NTX points
 template <int NTX = NT> __device__ __forceinline__ void load16(float2 (&v)[16], const float2 *d, int j) {
+    static_assert(NTX % 16 == 0, "pad(j + NTX r) = pad(j) + pad(NTX r)");
+    const float2 *p = d + pad(j);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = d[pad(j + NTX * r)];
+    for (int r = 0; r < 16; ++r) v[r] = p[pad_off(NTX * r)];
 }
 
 // One in-place Stockham radix-16 pass at stride Ns over 16 NTX points (NTX threads;
@@ -208,8 +241,8 @@ constexpr int SLOTS_S = NC_S + NC_S / 16;
 
 // radix-4 butterfly of thread j at stride Ns: twiddles exp(S 2 pi i r k / 4 Ns), k = j mod Ns, DFT
 template <int S, int Ns> __device__ __forceinline__ void butterfly4_s(float2 (&v)[4], int j) {
-    if (Ns > 1) {
-        const float2 w1 = cis<S>((float)(j & (Ns - 1)) / (float)(2 * Ns));
+    if constexpr (Ns > 1) {
+        const float2 w1 = tw_at<S>(tw4_off(Ns) + (j & (Ns - 1)));
         const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
         v[1] = cmul(v[1], w1);
         v[2] = cmul(v[2], w2);
@@ -219,14 +252,16 @@ template <int S, int Ns> __device__ __forceinline__ void butterfly4_s(float2 (&v
 }
 
 template <int Ns> __device__ __forceinline__ void store4_s(float2 *d, const float2 (&v)[4], int j) {
-    const int k = j & (Ns - 1), base = (j - k) * 4 + k;
+    const int k = j & (Ns - 1);
+    float2 *p = d + pad((j - k) * 4 + k);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) d[pad(base + r * Ns)] = v[r];
+    for (int r = 0; r < 4; ++r) p[pad_off(r * Ns)] = v[r];
 }
 
 __device__ __forceinline__ void load4_s(float2 (&v)[4], const float2 *d, int j) {
+    const float2 *p = d + pad(j);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) v[r] = d[pad(j + NT_S * r)];
+    for (int r = 0; r < 4; ++r) v[r] = p[pad_off(NT_S * r)];
 }
 
 template <int S, int Ns> __device__ __forceinline__ void pass4_s(float2 *d) {

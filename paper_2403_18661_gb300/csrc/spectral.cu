@@ -26,6 +26,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "afg_internal.cuh"
 #include "fft.cuh"
 #include "fft16.cuh"
@@ -42,6 +44,30 @@ __global__ void k_twiddles(double2 *tw64) {
     tw64[k] = make_double2(c, -s);
 }
 
+// The FP32 transforms' twiddle table (layout in fft16.cuh): entry i = exp(-i pi a_i), a_i an exact
+// binary fraction, evaluated in FP64 and rounded to FP32.
+__global__ void k_tw32() {
+    using namespace r16;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= TW_TOTAL) return;
+    double a;
+    if (i < TW16_END) {
+        const int ns = i < tw16_off(16) ? 2 : i < tw16_off(32) ? 16 : i < tw16_off(256) ? 32 : i < tw16_off(512) ? 256 : 512;
+        const int loc = i - tw16_off(ns), m = loc / ns, k = loc % ns;  // m = 0, 1, 2: w1, w4, w8
+        a = (double)((m == 0 ? 1 : m == 1 ? 4 : 8) * k) / (double)(8 * ns);
+    } else if (i < TW_SPLIT) {
+        const int loc = i - TW16_END;  // Ns - 2 <= loc < 2 Ns - 2
+        int ns = 2;
+        while (loc >= 2 * ns - 2) ns *= 2;
+        a = (double)(loc - (ns - 2)) / (double)(2 * ns);
+    } else {
+        a = (double)(i - TW_SPLIT) / 8192.0;
+    }
+    double s, c;
+    sincospi(a, &s, &c);
+    g_tw[i] = make_float2((float)c, (float)-s);
+}
+
 // Forward radix-2 pass (Ns = 4096) and real-FFT split for task j of the
 // Welch kernel, 1 <= j <= 2048: the butterflies j and 4096 - j give Z at
 // j, j + 4096, 4096 - j and 8192 - j, i.e. the split pairs (j, NC - j) and
@@ -52,8 +78,8 @@ __global__ void k_twiddles(double2 *tw64) {
 __device__ __forceinline__ void welch_mid_task(float2 *d, int j) {
     using namespace r16;
     const float2 a = d[pad(j)], b = d[pad(j + 4096)], c = d[pad(4096 - j)], e = d[pad(8192 - j)];
-    const float2 w = cis<-1>((float)j / 8192.0f);  // W^j
-    const float2 u = cis<-1>((float)j / 4096.0f);  // radix-2 twiddle of butterfly j
+    const float2 w = tw_split<-1>(j);      // W^j
+    const float2 u = tw_split<-1>(2 * j);  // radix-2 twiddle of butterfly j
     const float2 u2 = make_float2(-u.x, u.y);      // of butterfly 4096 - j: -conj(u)
     const float2 ub = cmul(u, b), ue = cmul(u2, e);
     const float2 zj = cadd(a, ub), zj4 = csub(a, ub), zc = cadd(c, ue), zc4 = csub(c, ue);
@@ -416,8 +442,10 @@ __device__ __forceinline__ void whiten_mid_task(const float2 *d, const float *g,
     using namespace r16;
     constexpr int H = NCX / 2;
     const float2 a = d[pad(j)], b = d[pad(j + H)], c = d[pad(H - j)], e = d[pad(NCX - j)];
-    const float2 w = cis<-1>((float)j / (float)NCX);        // W^j, W = exp(-2 pi i / 2 NCX)
-    const float2 u = cis<-1>((float)j / (float)(NCX / 2));  // radix-2 twiddle of butterfly j
+    static_assert(8192 % NCX == 0, "split table step");
+    constexpr int SP = 8192 / NCX;
+    const float2 w = tw_split<-1>(SP * j);      // W^j, W = exp(-2 pi i / 2 NCX)
+    const float2 u = tw_split<-1>(2 * SP * j);  // radix-2 twiddle of butterfly j
     const float2 u2 = make_float2(-u.x, u.y);               // of butterfly H - j
     const float2 ub = cmul(u, b), ue = cmul(u2, e);
     const float2 zj = cadd(a, ub), zj4 = csub(a, ub), zc = cadd(c, ue), zc4 = csub(c, ue);
@@ -472,12 +500,13 @@ __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *_
     const int t = threadIdx.x;
     for (int k = t; k < NBIN; k += NT) cp_async4(gs + k, gk + k);
     const int half = F / 2;
-    const int64_t need = cnt + F - 1;  // samples that reach a kept output
-    const int64_t lim = need < avail ? need : avail;
+    // samples that reach a kept output (cnt + F - 1 <= 16384: indices within the block are ints)
+    const int need = (int)cnt + F - 1;
+    const int lim = avail <= 0 ? 0 : avail < (int64_t)need ? (int)avail : need;
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const int64_t i0 = 2 * (int64_t)(t + NT * r);
+        const int i0 = 2 * (t + NT * r);
         v[r] = make_float2(i0 < lim ? src[i0] : 0.0f, i0 + 1 < lim ? src[i0 + 1] : 0.0f);
     }
     forward_r16(d, v);
@@ -507,12 +536,13 @@ __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *_
     __syncthreads();
     inverse_r16(d, v);
     // complex sample c = t + 512 q holds real samples 2c, 2c + 1; output q0 = 2c - F/2
+    const int cnt32 = (int)cnt;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const float2 y = v[out16(q)];
-        const int64_t q0 = 2 * (int64_t)(t + NT * q) - half;
-        if (q0 >= 0 && q0 < cnt) out(q0, y.x);
-        if (q0 + 1 >= 0 && q0 + 1 < cnt) out(q0 + 1, y.y);
+        const int q0 = 2 * (t + NT * q) - half;
+        if (q0 >= 0 && q0 < cnt32) out(q0, y.x);
+        if (q0 + 1 >= 0 && q0 + 1 < cnt32) out(q0 + 1, y.y);
     }
 }
 
@@ -784,12 +814,36 @@ int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, floa
     return AFG_OK;
 }
 
+// Fill the FP32 twiddle table of the current device once per process (it is a per-module device variable;
+// every context on the device and the context-free Welch entry point share it).  Synchronous: the table is
+// complete when this returns, before any transform can be launched on the device.
+static cudaError_t ensure_tw32() {
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    cudaStream_t st;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    k_tw32<<<(r16::TW_TOTAL + 255) / 256, 256, 0, st>>>();
+    e = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 int afg_make_twiddles(afg_ctx *ctx) {
     {
         KScope ks(ctx, 0, KK_TWIDDLES, 0.0, (double)NFFT * sizeof(double2));
         k_twiddles<<<NFFT / 256, 256>>>(ctx->tw64);
     }
     AFG_LAUNCH_CHECK(ctx, "k_twiddles");
+    if (ensure_tw32() != cudaSuccess) return AFG_ERR_CUDA;
     return set_attrs(ctx);
 }
 
@@ -935,7 +989,10 @@ cudaError_t launch_psd_on(const float *x, int64_t n, int n_det, int64_t n_psd, i
     return cudaGetLastError();
 }
 
-// Opt the periodogram kernel into its 68 KiB of dynamic shared memory on the current device.
+// Fill the twiddle table and opt the periodogram kernel into its 68 KiB of dynamic shared memory on the
+// current device.
 cudaError_t prepare_psd_kernels() {
+    const cudaError_t e = ensure_tw32();
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_periodogram, cudaFuncAttributeMaxDynamicSharedMemorySize, WELCH_SMEM);
 }
