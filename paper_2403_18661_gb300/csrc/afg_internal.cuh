@@ -21,6 +21,7 @@
 constexpr int NFFT = 16384;
 constexpr int NC = NFFT / 2;
 constexpr int NBIN = NFFT / 2 + 1;
+constexpr int FILTER_LAGS = 2048;  // lags of the tapered taps the many-CTA filter build keeps
 constexpr int WB = 8192;
 
 // Epochs per thread of the Welch averaging kernel; its grid's y extent is
@@ -192,6 +193,8 @@ struct afg_ctx {
     float *d_params = nullptr;        // all network parameters (device)
     size_t d_params_bytes = 0;
     double2 *tw64 = nullptr;          // exp(-2 pi i k / NFFT), k < NFFT, double (filter build)
+    double *taper64 = nullptr;        // sqrt(2 / fs) taper(m) / NFFT at m + FILTER_LAGS / 2, m in
+                                      // [-FILTER_LAGS / 2, FILTER_LAGS / 2) (after tw64, same allocation)
     int64_t bytes_held = 0;
     int *d_err = nullptr;             // device-side failure record (bounded waits that gave up)
     Workspace ws[32];

@@ -144,14 +144,15 @@ int afg_ctx_create(const afg_config *cfg, const float *weights_host, int64_t n_w
     afg_ctx *ctx = new afg_ctx();
     ctx->cfg = *cfg;
     cudaGetDevice(&ctx->device);
-    size_t tw_bytes = NFFT * sizeof(double2);
-    cudaError_t e = cudaMalloc(&ctx->tw64, NFFT * sizeof(double2));
+    size_t tw_bytes = NFFT * sizeof(double2) + FILTER_LAGS * sizeof(double);
+    cudaError_t e = cudaMalloc(&ctx->tw64, tw_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         afg_ctx_destroy(ctx);
         return AFG_ERR_OOM;
     }
     ctx->bytes_held += (int64_t)tw_bytes;
+    ctx->taper64 = reinterpret_cast<double *>(ctx->tw64 + NFFT);
     if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess || cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
         cudaGetLastError();
         afg_ctx_destroy(ctx);

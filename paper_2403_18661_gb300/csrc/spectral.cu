@@ -44,6 +44,18 @@ __global__ void k_twiddles(double2 *tw64) {
     tw64[k] = make_double2(c, -s);
 }
 
+// The taper of the many-CTA filter build with its constant factors: tap[m + FILTER_LAGS / 2] =
+// sqrt(2 / fs) (1 - cos(2 pi (m + F/2) / F)) / 2 / NFFT for the F taps m in [-F/2, F/2), else 0
+// (the 1 / NFFT of the inverse transform is a power of two, so folding it in here is exact).
+__global__ void k_taper64(double *tap, double fs, int F) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= FILTER_LAGS) return;
+    const int m = i - FILTER_LAGS / 2, half = F / 2;
+    tap[i] = (m >= -half && m < half)
+                 ? sqrt(2.0 / fs) * (0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F)) / (double)NFFT
+                 : 0.0;
+}
+
 // The FP32 transforms' twiddle table (layout in fft16.cuh): entry i = exp(-i pi a_i), a_i an exact
 // binary fraction, evaluated in FP64 and rounded to FP32.
 __global__ void k_tw32() {
@@ -251,7 +263,7 @@ __global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict_
     for (int k = threadIdx.x; k < NBIN; k += NT64) {
         double f = (double)k * fs / (double)NFFT;
         double pk = p[k];
-        double a = (f >= f_hp && pk > 0.0) ? 1.0 / sqrt(pk) : 0.0;
+        double a = (f >= f_hp && pk > 0.0) ? rsqrt(pk) : 0.0;
         d[k] = make_double2(a, 0.0);
     }
     __syncthreads();
@@ -290,9 +302,15 @@ __global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict_
 //             y_r[n] = sum_{m = n mod L} g_m e^{-2 pi i r m / N}   (P forward FFTs of L points;
 //             at L = 2048 each slot n holds one lag, at L = 512 it folds four)
 // The same FP64 arithmetic as k_filter_build (up to rounding order), on many CTAs per filter
-// instead of one; the inverse and forward stages each pair two sub-transforms into one
-// complex FFT (real amplitude response; Hermitian folded taps), P / 2 CTAs per stage.
-constexpr int FB_LAGS = 2048;  // lags m in [-FB_LAGS / 2, FB_LAGS / 2)
+// instead of one.  A and G are real and even in k, so residue P - r is residue r reversed:
+// A_{P j + P - r} = A_{P (L - 1 - j) + r}, hence Z_{P-r}[n] = e^{-2 pi i n / L} conj Z_r[n], and
+// the same for G.  Only the residues r = 0 .. P/2 are transformed:
+//   h_m = (1/N) (Re Z_0[n] + Re(e^{+2 pi i (P/2) m / N} Z_{P/2}[n]) + 2 sum_{0<r<P/2} Re(e^{+2 pi i r m / N} Z_r[n]))
+// and G at bins k > N/2 of residues 0 < r < P/2 is written to bin N - k (residue P - r).
+// Each stage pairs two real sub-transforms into one complex FFT (real amplitude response;
+// Hermitian folded taps): CTA 0 takes residues (0, P/2), CTA b > 0 takes (2b - 1, 2b), the last
+// one 2b - 1 alone; P / 4 + 1 CTAs per filter and stage.
+constexpr int FB_LAGS = FILTER_LAGS;  // lags m in [-FB_LAGS / 2, FB_LAGS / 2)
 constexpr int FB_T = 256;
 
 template <int L>
@@ -306,73 +324,81 @@ __device__ __forceinline__ void fb_fft(double2 *d, const double2 *tw, bool inver
     }
 }
 
-// grid (P / 2, n_filters): Z_r and Z_{r + P/2} of filter f = det * n_psd + e from one
-// complex transform.  Both inputs A_{P j + r} are real, so each Z is Hermitian and
-// C = IFFT(A_r + i A_{r'}) splits as Z_r[n] = (C[n] + conj C[-n]) / 2,
-// Z_{r'}[n] = (C[n] - conj C[-n]) / 2i.
+// the residue pair of CTA b of the inverse and forward stages (r2 < 0: r1 alone)
+template <int P> __device__ __forceinline__ void fb_pair(int b, int &r1, int &r2) {
+    r1 = b == 0 ? 0 : 2 * b - 1;
+    r2 = b == 0 ? P / 2 : (2 * b < P / 2 ? 2 * b : -1);
+}
+
+// grid (P / 4 + 1, n_filters): Z_r1 and Z_r2 of filter f = det * n_psd + e from one complex
+// transform.  Both inputs A_{P j + r} are real, so each Z is Hermitian and
+// C = IFFT(A_r1 + i A_r2) splits as Z_r1[n] = (C[n] + conj C[-n]) / 2,
+// Z_r2[n] = (C[n] - conj C[-n]) / 2i.
 template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ psd, double fs, double f_hp,
                                                      const double2 *__restrict__ tw, double2 *__restrict__ Z) {
     constexpr int P = NFFT / L;
     __shared__ double2 d[L];
-    const int r1 = blockIdx.x, r2 = r1 + P / 2;
+    int r1, r2;
+    fb_pair<P>(blockIdx.x, r1, r2);
     const int64_t f = blockIdx.y;
     const double *p = psd + f * NBIN;
     auto amp = [&](int k) {
         const int kk = k <= NFFT / 2 ? k : NFFT - k;  // the amplitude response is even in k
         const double fr = (double)kk * fs / (double)NFFT;
         const double pk = p[kk];
-        return (fr >= f_hp && pk > 0.0) ? 1.0 / sqrt(pk) : 0.0;
+        return (fr >= f_hp && pk > 0.0) ? rsqrt(pk) : 0.0;
     };
-    for (int j = threadIdx.x; j < L; j += FB_T) d[j] = make_double2(amp(P * j + r1), amp(P * j + r2));
+    for (int j = threadIdx.x; j < L; j += FB_T)
+        d[j] = make_double2(amp(P * j + r1), r2 >= 0 ? amp(P * j + r2) : 0.0);
     __syncthreads();
     fb_fft<L>(d, tw, true);
-    double2 *z1 = Z + (f * P + r1) * L, *z2 = Z + (f * P + r2) * L;
+    double2 *z1 = Z + (f * P + r1) * L, *z2 = Z + (f * P + (r2 >= 0 ? r2 : 0)) * L;
     for (int n = threadIdx.x; n < L; n += FB_T) {
         const double2 c = d[n], cm = d[(L - n) & (L - 1)];
         z1[n] = make_double2(0.5 * (c.x + cm.x), 0.5 * (c.y - cm.y));
-        z2[n] = make_double2(0.5 * (c.y + cm.y), -0.5 * (c.x - cm.x));
+        if (r2 >= 0) z2[n] = make_double2(0.5 * (c.y + cm.y), -0.5 * (c.x - cm.x));
     }
 }
 
-// g_m of lag m from the P partial transforms (slot m mod L)
+// g_m of lag m from the P partial transforms (slot m mod L), with the taper table tap
 template <int P, int L>
-__device__ __forceinline__ double fb_tap(const double2 *__restrict__ Zf, int m, double fs, int F,
+__device__ __forceinline__ double fb_tap(const double2 *__restrict__ Zf, int m, const double *__restrict__ tap,
                                          const double2 *__restrict__ tw) {
     const int slot = m & (L - 1);
-    double h = 0.0;
+    double s = 0.0;
 #pragma unroll 8
-    for (int r = 0; r < P; ++r) {
+    for (int r = 1; r < P / 2; ++r) {
         const double2 w = tw[(r * m) & (NFFT - 1)];  // e^{-2 pi i r m / N}; use its conjugate
         const double2 v = Zf[(int64_t)r * L + slot];
-        h += w.x * v.x + w.y * v.y;  // Re(conj(w) v)
+        s += w.x * v.x + w.y * v.y;  // Re(conj(w) v)
     }
-    h /= (double)NFFT;
-    const int half = F / 2;
-    return (m >= -half && m < half) ? h * sqrt(2.0 / fs) * (0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F))
-                                    : 0.0;
+    const double2 wh = tw[((P / 2) * m) & (NFFT - 1)], vh = Zf[(int64_t)(P / 2) * L + slot];
+    const double h = Zf[slot].x + (wh.x * vh.x + wh.y * vh.y) + 2.0 * s;
+    return h * tap[m + FB_LAGS / 2];
 }
 
 // L = 2048: grid (FB_LAGS / FB_T, n_filters), one lag per thread, one lag per slot
-__global__ void __launch_bounds__(FB_T) k_fb_taper(const double2 *__restrict__ Z, double fs, int F,
+__global__ void __launch_bounds__(FB_T) k_fb_taper(const double2 *__restrict__ Z, const double *__restrict__ tap,
                                                    const double2 *__restrict__ tw, double2 *__restrict__ Y) {
     constexpr int L = 2048, P = NFFT / L;
     const int64_t f = blockIdx.y;
     const int m = blockIdx.x * FB_T + threadIdx.x - FB_LAGS / 2;  // lag in [-1024, 1024)
-    const double g = fb_tap<P, L>(Z + f * P * L, m, fs, F, tw);
+    const double g = fb_tap<P, L>(Z + f * P * L, m, tap, tw);
     double2 *y = Y + f * P * L + (m & (L - 1));
 #pragma unroll
-    for (int r = 0; r < P; ++r) {
+    for (int r = 0; r <= P / 2; ++r) {  // the residues the forward stage transforms
         const double2 w = tw[(r * m) & (NFFT - 1)];
         y[(int64_t)r * L] = make_double2(g * w.x, g * w.y);
     }
 }
 
 // L = 512: grid (L / FB_FS, n_filters), FB_FS slots x 4 lags per CTA.  Thread (slot n, lag t)
-// forms g_m of m = n + L t - 1024, then y_r[n] for its quarter of the P = 32 r, summed over
+// forms g_m of m = n + L t - 1024, then y_r[n] for every fourth r <= P/2 from r = t, summed over
 // the slot's four lags.
 constexpr int FB_FS = 32;
-__global__ void __launch_bounds__(FB_FS * 4) k_fb_taper_fold(const double2 *__restrict__ Z, double fs, int F,
+__global__ void __launch_bounds__(FB_FS * 4) k_fb_taper_fold(const double2 *__restrict__ Z,
+                                                             const double *__restrict__ tap,
                                                              const double2 *__restrict__ tw,
                                                              double2 *__restrict__ Y) {
     constexpr int L = 512, P = NFFT / L, FOLD = FB_LAGS / L;
@@ -381,10 +407,10 @@ __global__ void __launch_bounds__(FB_FS * 4) k_fb_taper_fold(const double2 *__re
     const int64_t f = blockIdx.y;
     const int nl = threadIdx.x % FB_FS, t = threadIdx.x / FB_FS;
     const int n = blockIdx.x * FB_FS + nl;
-    gs[t][nl] = fb_tap<P, L>(Z + f * P * L, n + L * t - FB_LAGS / 2, fs, F, tw);
+    gs[t][nl] = fb_tap<P, L>(Z + f * P * L, n + L * t - FB_LAGS / 2, tap, tw);
     __syncthreads();
     double2 *y = Y + f * P * L + n;
-    for (int r = t * (P / FOLD); r < (t + 1) * (P / FOLD); ++r) {
+    for (int r = t; r <= P / 2; r += FOLD) {  // the residues the forward stage transforms
         double ax = 0.0, ay = 0.0;
 #pragma unroll
         for (int u = 0; u < FOLD; ++u) {
@@ -397,28 +423,33 @@ __global__ void __launch_bounds__(FB_FS * 4) k_fb_taper_fold(const double2 *__re
     }
 }
 
-// grid (P / 2, n_filters): gains G_k / NC for k = P j + r <= NFFT / 2, r and r + P/2 from
-// one complex transform.  The taps are even, so each y_r is Hermitian and its transform
-// real: FFT(y_r + i y_{r'}) = G_{P j + r} + i G_{P j + r'}.
+// grid (P / 4 + 1, n_filters): gains G_k / NC for k <= NFFT / 2 of the residues r1, r2 (fb_pair)
+// from one complex transform.  The taps are even, so each y_r is Hermitian and its transform
+// real: FFT(y_r1 + i y_r2) = G_{P j + r1} + i G_{P j + r2}.  Bins k > NFFT / 2 of residues
+// 0 < r < P/2 give bin NFFT - k (G is even), which belongs to residue P - r.
 template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_forward(const double2 *__restrict__ Y, const double2 *__restrict__ tw,
                                                      float *__restrict__ gains) {
     constexpr int P = NFFT / L;
     __shared__ double2 d[L];
-    const int r1 = blockIdx.x, r2 = r1 + P / 2;
+    int r1, r2;
+    fb_pair<P>(blockIdx.x, r1, r2);
     const int64_t f = blockIdx.y;
-    const double2 *y1 = Y + (f * P + r1) * L, *y2 = Y + (f * P + r2) * L;
+    const double2 *y1 = Y + (f * P + r1) * L, *y2 = Y + (f * P + (r2 >= 0 ? r2 : 0)) * L;
     for (int n = threadIdx.x; n < L; n += FB_T) {
-        const double2 a = y1[n], b = y2[n];
+        const double2 a = y1[n], b = r2 >= 0 ? y2[n] : make_double2(0.0, 0.0);
         d[n] = make_double2(a.x - b.y, a.y + b.x);
     }
     __syncthreads();
     fb_fft<L>(d, tw, false);
     float *out = gains + f * NBIN;
+    auto put = [&](int r, int k, double v) {
+        if (k <= NFFT / 2) out[k] = (float)(v / (double)NC);
+        else if (r != 0 && r != P / 2) out[NFFT - k] = (float)(v / (double)NC);
+    };
     for (int j = threadIdx.x; j < L; j += FB_T) {
-        const int k1 = P * j + r1, k2 = P * j + r2;
-        if (k1 <= NFFT / 2) out[k1] = (float)(d[j].x / (double)NC);
-        if (k2 <= NFFT / 2) out[k2] = (float)(d[j].y / (double)NC);
+        put(r1, P * j + r1, d[j].x);
+        if (r2 >= 0) put(r2, P * j + r2, d[j].y);
     }
 }
 
@@ -780,9 +811,10 @@ size_t filter_build_scratch_bytes(const afg_ctx *ctx, int64_t nf) {
 int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, float *gains, cudaStream_t st) {
     const int64_t nf = (int64_t)n_det * n_psd;
     if (nf <= 0) return AFG_OK;
-    // algorithmic FP64 work of one filter: an inverse and a forward real FFT of NFFT points,
-    // 2.5 N log2 N flops each
-    const double flops = (double)nf * 2.0 * 2.5 * NFFT * 14.0;
+    // algorithmic FP64 work of one filter: an inverse and a forward transform of a real, even
+    // sequence of NFFT points (the amplitude response and the taps), 1.25 N log2 N flops each
+    // (half of a real FFT's 2.5 N log2 N)
+    const double flops = (double)nf * 2.0 * 1.25 * NFFT * 14.0;
     static_assert(NFFT == 1 << 14, "flop count assumes log2(NFFT) = 14");
     if (ctx->cfg.fir_len <= FB_LAGS && nf <= 65535) {
         void *scr = nullptr;
@@ -792,18 +824,16 @@ int filter_build(afg_ctx *ctx, const double *psd, int n_det, int64_t n_psd, floa
         KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
         if (nf * (NFFT / 2048) >= 152) {  // enough filters to fill the GPU with 2048-point transforms
             constexpr int L = 2048, P = NFFT / L;
-            k_fb_inverse<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs,
+            k_fb_inverse<L><<<dim3(P / 4 + 1, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs,
                                                                         ctx->cfg.f_highpass, ctx->tw64, Z);
-            k_fb_taper<<<dim3(FB_LAGS / FB_T, (unsigned)nf), FB_T, 0, st>>>(Z, (double)ctx->cfg.fs,
-                                                                            ctx->cfg.fir_len, ctx->tw64, Y);
-            k_fb_forward<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+            k_fb_taper<<<dim3(FB_LAGS / FB_T, (unsigned)nf), FB_T, 0, st>>>(Z, ctx->taper64, ctx->tw64, Y);
+            k_fb_forward<L><<<dim3(P / 4 + 1, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
         } else {  // few filters: 32 sub-transforms of 512 points each (16 paired transforms per stage)
             constexpr int L = 512, P = NFFT / L;
-            k_fb_inverse<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs,
+            k_fb_inverse<L><<<dim3(P / 4 + 1, (unsigned)nf), FB_T, 0, st>>>(psd, (double)ctx->cfg.fs,
                                                                         ctx->cfg.f_highpass, ctx->tw64, Z);
-            k_fb_taper_fold<<<dim3(L / FB_FS, (unsigned)nf), FB_FS * 4, 0, st>>>(Z, (double)ctx->cfg.fs,
-                                                                                 ctx->cfg.fir_len, ctx->tw64, Y);
-            k_fb_forward<L><<<dim3(P / 2, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
+            k_fb_taper_fold<<<dim3(L / FB_FS, (unsigned)nf), FB_FS * 4, 0, st>>>(Z, ctx->taper64, ctx->tw64, Y);
+            k_fb_forward<L><<<dim3(P / 4 + 1, (unsigned)nf), FB_T, 0, st>>>(Y, ctx->tw64, gains);
         }
     } else {
         KScope ks(ctx, st, KK_FILTER, flops, (double)nf * NBIN * (8.0 + 4.0));
@@ -841,6 +871,8 @@ int afg_make_twiddles(afg_ctx *ctx) {
     {
         KScope ks(ctx, 0, KK_TWIDDLES, 0.0, (double)NFFT * sizeof(double2));
         k_twiddles<<<NFFT / 256, 256>>>(ctx->tw64);
+        if (ctx->cfg.fir_len <= FILTER_LAGS)
+            k_taper64<<<FILTER_LAGS / 256, 256>>>(ctx->taper64, (double)ctx->cfg.fs, ctx->cfg.fir_len);
     }
     AFG_LAUNCH_CHECK(ctx, "k_twiddles");
     if (ensure_tw32() != cudaSuccess) return AFG_ERR_CUDA;
