@@ -308,8 +308,9 @@ __global__ void __launch_bounds__(NT64) k_filter_build(const double *__restrict_
 //   h_m = (1/N) (Re Z_0[n] + Re(e^{+2 pi i (P/2) m / N} Z_{P/2}[n]) + 2 sum_{0<r<P/2} Re(e^{+2 pi i r m / N} Z_r[n]))
 // and G at bins k > N/2 of residues 0 < r < P/2 is written to bin N - k (residue P - r).
 // Each stage pairs two real sub-transforms into one complex FFT (real amplitude response;
-// Hermitian folded taps): CTA 0 takes residues (0, P/2), CTA b > 0 takes (2b - 1, 2b), the last
-// one 2b - 1 alone; P / 4 + 1 CTAs per filter and stage.
+// Hermitian folded taps): CTA (b, f) takes residues (0, P/2) of filter f for b = 0, (2b - 1, 2b)
+// for 0 < b < P/4, and for b = P/4 residue P/2 - 1 of the filters f and f + 1 (f even; the
+// CTAs of odd f at b = P/4 have no work).  P / 4 + 1 CTAs per filter and stage.
 constexpr int FB_LAGS = FILTER_LAGS;  // lags m in [-FB_LAGS / 2, FB_LAGS / 2)
 constexpr int FB_T = 256;
 
@@ -324,15 +325,26 @@ __device__ __forceinline__ void fb_fft(double2 *d, const double2 *tw, bool inver
     }
 }
 
-// the residue pair of CTA b of the inverse and forward stages (r2 < 0: r1 alone)
-template <int P> __device__ __forceinline__ void fb_pair(int b, int &r1, int &r2) {
-    r1 = b == 0 ? 0 : 2 * b - 1;
-    r2 = b == 0 ? P / 2 : (2 * b < P / 2 ? 2 * b : -1);
+// The two real sub-transforms (filter f1, residue r1) and (f2, r2) of CTA (b, f) of the inverse
+// and forward stages (r2 < 0: the first alone); false for a CTA without work.
+template <int P>
+__device__ __forceinline__ bool fb_task(int b, int64_t f, int64_t nf, int64_t &f1, int &r1, int64_t &f2, int &r2) {
+    f1 = f2 = f;
+    if (b < P / 4) {
+        r1 = b == 0 ? 0 : 2 * b - 1;
+        r2 = b == 0 ? P / 2 : 2 * b;
+        return true;
+    }
+    if (f & 1) return false;
+    r1 = r2 = P / 2 - 1;
+    f2 = f + 1;
+    if (f2 >= nf) r2 = -1;
+    return true;
 }
 
-// grid (P / 4 + 1, n_filters): Z_r1 and Z_r2 of filter f = det * n_psd + e from one complex
-// transform.  Both inputs A_{P j + r} are real, so each Z is Hermitian and
-// C = IFFT(A_r1 + i A_r2) splits as Z_r1[n] = (C[n] + conj C[-n]) / 2,
+// grid (P / 4 + 1, n_filters): Z_r1 of filter f1 and Z_r2 of filter f2 (fb_task; filter
+// f = det * n_psd + e) from one complex transform.  Both inputs A_{P j + r} are real, so each Z
+// is Hermitian and C = IFFT(A_r1 + i A_r2) splits as Z_r1[n] = (C[n] + conj C[-n]) / 2,
 // Z_r2[n] = (C[n] - conj C[-n]) / 2i.
 template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ psd, double fs, double f_hp,
@@ -340,20 +352,20 @@ __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ 
     constexpr int P = NFFT / L;
     __shared__ double2 d[L];
     int r1, r2;
-    fb_pair<P>(blockIdx.x, r1, r2);
-    const int64_t f = blockIdx.y;
-    const double *p = psd + f * NBIN;
-    auto amp = [&](int k) {
+    int64_t f1, f2;
+    if (!fb_task<P>(blockIdx.x, blockIdx.y, gridDim.y, f1, r1, f2, r2)) return;
+    auto amp = [&](const double *p, int k) {
         const int kk = k <= NFFT / 2 ? k : NFFT - k;  // the amplitude response is even in k
         const double fr = (double)kk * fs / (double)NFFT;
         const double pk = p[kk];
         return (fr >= f_hp && pk > 0.0) ? rsqrt(pk) : 0.0;
     };
+    const double *p1 = psd + f1 * NBIN, *p2 = psd + f2 * NBIN;
     for (int j = threadIdx.x; j < L; j += FB_T)
-        d[j] = make_double2(amp(P * j + r1), r2 >= 0 ? amp(P * j + r2) : 0.0);
+        d[j] = make_double2(amp(p1, P * j + r1), r2 >= 0 ? amp(p2, P * j + r2) : 0.0);
     __syncthreads();
     fb_fft<L>(d, tw, true);
-    double2 *z1 = Z + (f * P + r1) * L, *z2 = Z + (f * P + (r2 >= 0 ? r2 : 0)) * L;
+    double2 *z1 = Z + (f1 * P + r1) * L, *z2 = Z + (f2 * P + (r2 >= 0 ? r2 : 0)) * L;
     for (int n = threadIdx.x; n < L; n += FB_T) {
         const double2 c = d[n], cm = d[(L - n) & (L - 1)];
         z1[n] = make_double2(0.5 * (c.x + cm.x), 0.5 * (c.y - cm.y));
@@ -423,8 +435,8 @@ __global__ void __launch_bounds__(FB_FS * 4) k_fb_taper_fold(const double2 *__re
     }
 }
 
-// grid (P / 4 + 1, n_filters): gains G_k / NC for k <= NFFT / 2 of the residues r1, r2 (fb_pair)
-// from one complex transform.  The taps are even, so each y_r is Hermitian and its transform
+// grid (P / 4 + 1, n_filters): gains G_k / NC for k <= NFFT / 2 of the residue r1 of filter f1
+// and r2 of f2 (fb_task) from one complex transform.  The taps are even, so each y_r is Hermitian and its transform
 // real: FFT(y_r1 + i y_r2) = G_{P j + r1} + i G_{P j + r2}.  Bins k > NFFT / 2 of residues
 // 0 < r < P/2 give bin NFFT - k (G is even), which belongs to residue P - r.
 template <int L>
@@ -433,23 +445,23 @@ __global__ void __launch_bounds__(FB_T) k_fb_forward(const double2 *__restrict__
     constexpr int P = NFFT / L;
     __shared__ double2 d[L];
     int r1, r2;
-    fb_pair<P>(blockIdx.x, r1, r2);
-    const int64_t f = blockIdx.y;
-    const double2 *y1 = Y + (f * P + r1) * L, *y2 = Y + (f * P + (r2 >= 0 ? r2 : 0)) * L;
+    int64_t f1, f2;
+    if (!fb_task<P>(blockIdx.x, blockIdx.y, gridDim.y, f1, r1, f2, r2)) return;
+    const double2 *y1 = Y + (f1 * P + r1) * L, *y2 = Y + (f2 * P + (r2 >= 0 ? r2 : 0)) * L;
     for (int n = threadIdx.x; n < L; n += FB_T) {
         const double2 a = y1[n], b = r2 >= 0 ? y2[n] : make_double2(0.0, 0.0);
         d[n] = make_double2(a.x - b.y, a.y + b.x);
     }
     __syncthreads();
     fb_fft<L>(d, tw, false);
-    float *out = gains + f * NBIN;
-    auto put = [&](int r, int k, double v) {
+    auto put = [&](float *out, int r, int k, double v) {
         if (k <= NFFT / 2) out[k] = (float)(v / (double)NC);
         else if (r != 0 && r != P / 2) out[NFFT - k] = (float)(v / (double)NC);
     };
+    float *out1 = gains + f1 * NBIN, *out2 = gains + f2 * NBIN;
     for (int j = threadIdx.x; j < L; j += FB_T) {
-        put(r1, P * j + r1, d[j].x);
-        if (r2 >= 0) put(r2, P * j + r2, d[j].y);
+        put(out1, r1, P * j + r1, d[j].x);
+        if (r2 >= 0) put(out2, r2, P * j + r2, d[j].y);
     }
 }
 
