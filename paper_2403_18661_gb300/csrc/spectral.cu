@@ -124,10 +124,16 @@ __global__ void __launch_bounds__(r16::NT, 2) k_periodogram(const float *__restr
     const float *src = (rows ? rows[det] : x + det * x_stride) + g * (int64_t)hop;
     // z_n = x_2n + i x_2n+1, n = t + 512 r (the first pass's inputs)
     float2 v[16];
+    if ((reinterpret_cast<uintptr_t>(src) & 7) == 0) {  // 8-byte loads of (x_2n, x_2n+1)
+        const float2 *s2 = reinterpret_cast<const float2 *>(src);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int i0 = 2 * (t + NT * r);
-        v[r] = make_float2(src[i0], src[i0 + 1]);
+        for (int r = 0; r < 16; ++r) v[r] = s2[t + NT * r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int i0 = 2 * (t + NT * r);
+            v[r] = make_float2(src[i0], src[i0 + 1]);
+        }
     }
     forward_r16(d, v);
     // the unwindowed spectrum U_0 .. U_NC into the transform's slots
@@ -531,12 +537,14 @@ inline float psd_scale(int64_t K, int fs) { return (float)(1.0 / ((double)K * (d
 constexpr int WELCH_SMEM = (r16::SLOTS + 1) * (int)sizeof(float2) + (r16::NT / 32) * (int)sizeof(float);
 
 // One overlap-save block: the FIR of src[0 .. cnt + F - 1) (cnt <= 16385 - F; samples past
-// `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value).
+// `avail` read as zero) -> outputs q in [0, cnt) written as out(q, value), or straight to lin[q]
+// when the caller's destination is the linear row lin (nullptr: always through out).
 // smem: r16::SLOTS float2 for the transform, then NBIN floats for the gains gk,
 // which are copied in asynchronously while the forward transform runs.
 template <typename Out>
 __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *__restrict__ src, int64_t avail,
-                                             const float *__restrict__ gk, int F, int64_t cnt, Out out) {
+                                             const float *__restrict__ gk, int F, int64_t cnt, Out out,
+                                             float *__restrict__ lin = nullptr) {
     using namespace r16;
     float2 *d = reinterpret_cast<float2 *>(smem);
     float *gs = reinterpret_cast<float *>(smem + SLOTS * sizeof(float2));
@@ -547,10 +555,24 @@ __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *_
     const int need = (int)cnt + F - 1;
     const int lim = avail <= 0 ? 0 : avail < (int64_t)need ? (int)avail : need;
     float2 v[16];
+    if (avail >= 2 * NC && (reinterpret_cast<uintptr_t>(src) & 7) == 0) {  // whole block in memory: 8-byte loads
+        const float2 *s2 = reinterpret_cast<const float2 *>(src);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int i0 = 2 * (t + NT * r);
-        v[r] = make_float2(i0 < lim ? src[i0] : 0.0f, i0 + 1 < lim ? src[i0 + 1] : 0.0f);
+        for (int r = 0; r < 16; ++r) v[r] = s2[t + NT * r];
+        if (2 * (t + NT * 15) + 1 >= lim) {  // this thread holds samples past `need`: they read as zero
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int i0 = 2 * (t + NT * r);
+                if (i0 >= lim) v[r].x = 0.0f;
+                if (i0 + 1 >= lim) v[r].y = 0.0f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int i0 = 2 * (t + NT * r);
+            v[r] = make_float2(i0 < lim ? src[i0] : 0.0f, i0 + 1 < lim ? src[i0 + 1] : 0.0f);
+        }
     }
     forward_r16(d, v);
     cp_async_wait_all();
@@ -580,12 +602,18 @@ __device__ __forceinline__ void whiten_block(unsigned char *smem, const float *_
     inverse_r16(d, v);
     // complex sample c = t + 512 q holds real samples 2c, 2c + 1; output q0 = 2c - F/2
     const int cnt32 = (int)cnt;
+    // outputs (q0, q0 + 1) as one 8-byte store where the destination is linear and q0 lands 8-byte aligned
+    const bool pairs = lin != nullptr && (half & 1) == 0 && (reinterpret_cast<uintptr_t>(lin) & 7) == 0;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const float2 y = v[out16(q)];
         const int q0 = 2 * (t + NT * q) - half;
-        if (q0 >= 0 && q0 < cnt32) out(q0, y.x);
-        if (q0 + 1 >= 0 && q0 + 1 < cnt32) out(q0 + 1, y.y);
+        if (pairs && q0 >= 0 && q0 + 1 < cnt32) {
+            *reinterpret_cast<float2 *>(lin + q0) = y;
+        } else {
+            if (q0 >= 0 && q0 < cnt32) out(q0, y.x);
+            if (q0 + 1 >= 0 && q0 + 1 < cnt32) out(q0 + 1, y.y);
+        }
     }
 }
 
@@ -647,7 +675,7 @@ __global__ void __launch_bounds__(r16::NT, 2) k_whiten(const float *__restrict__
     const int64_t s0 = out_first + b.o - F / 2;  // raw index of block sample 0
     float *dst = y + det * y_stride + b.o;
     whiten_block(smem_raw, x + det * x_stride + s0, n - s0, gains + ((int64_t)det * n_psd + b.ep) * NBIN, F, b.cnt,
-                 [dst](int64_t q, float v) { dst[q] = v; });
+                 [dst](int64_t q, float v) { dst[q] = v; }, dst);
 }
 
 // grid (n_ep, n_det): each epoch's remainder block on the 4096-point transform (whiten_layout().small_rem).
