@@ -360,11 +360,18 @@ __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ 
     int r1, r2;
     int64_t f1, f2;
     if (!fb_task<P>(blockIdx.x, blockIdx.y, gridDim.y, f1, r1, f2, r2)) return;
+    // The highpass test fr >= f_hp with fr = kk fs / NFFT, as the first bin k_hp that passes it (the same
+    // FP64 expression, evaluated once per thread), and pk > 0 as a test of its bits (a positive finite or
+    // infinite double; NaN and -0 fail as they do in the FP64 comparison): no FP64 instruction per bin but
+    // the reciprocal square root.
+    const double k0 = floor(f_hp * (double)NFFT / fs) - 1.0;
+    int k_hp = f_hp != f_hp ? NFFT / 2 + 1 : k0 <= 0.0 ? 0 : k0 >= (double)NFFT ? NFFT / 2 + 1 : (int)k0;  // NaN: none
+    while (k_hp <= NFFT / 2 && (double)k_hp * fs / (double)NFFT < f_hp) ++k_hp;
     auto amp = [&](const double *p, int k) {
         const int kk = k <= NFFT / 2 ? k : NFFT - k;  // the amplitude response is even in k
-        const double fr = (double)kk * fs / (double)NFFT;
         const double pk = p[kk];
-        return (fr >= f_hp && pk > 0.0) ? rsqrt(pk) : 0.0;
+        const long long b = __double_as_longlong(pk);
+        return (kk >= k_hp && b > 0 && b <= 0x7FF0000000000000LL) ? rsqrt(pk) : 0.0;
     };
     const double *p1 = psd + f1 * NBIN, *p2 = psd + f2 * NBIN;
     for (int j = threadIdx.x; j < L; j += FB_T)
