@@ -193,7 +193,7 @@ struct afg_ctx {
     float *d_params = nullptr;        // all network parameters (device)
     size_t d_params_bytes = 0;
     double2 *tw64 = nullptr;          // exp(-2 pi i k / NFFT), k < NFFT, double (filter build)
-    double *taper64 = nullptr;        // sqrt(2 / fs) taper(m) / NFFT at m + FILTER_LAGS / 2, m in
+    double *taper64 = nullptr;        // sqrt(2 / fs) taper(m) / (2 NFFT NC) at m + FILTER_LAGS / 2, m in
                                       // [-FILTER_LAGS / 2, FILTER_LAGS / 2) (after tw64, same allocation)
     int64_t bytes_held = 0;
     int *d_err = nullptr;             // device-side failure record (bounded waits that gave up)

@@ -45,14 +45,17 @@ __global__ void k_twiddles(double2 *tw64) {
 }
 
 // The taper of the many-CTA filter build with its constant factors: tap[m + FILTER_LAGS / 2] =
-// sqrt(2 / fs) (1 - cos(2 pi (m + F/2) / F)) / 2 / NFFT for the F taps m in [-F/2, F/2), else 0
-// (the 1 / NFFT of the inverse transform is a power of two, so folding it in here is exact).
+// sqrt(2 / fs) (1 - cos(2 pi (m + F/2) / F)) / 2 / (2 NFFT NC) for the F taps m in [-F/2, F/2), else 0.
+// The 1 / NFFT of the inverse transform, the 1 / 2 of the inverse stage's Hermitian split and the
+// 1 / NC the gains are stored with are powers of two and every later step is linear, so folding them
+// in here is exact.
 __global__ void k_taper64(double *tap, double fs, int F) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= FILTER_LAGS) return;
     const int m = i - FILTER_LAGS / 2, half = F / 2;
     tap[i] = (m >= -half && m < half)
-                 ? sqrt(2.0 / fs) * (0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F)) / (double)NFFT
+                 ? sqrt(2.0 / fs) * (0.5 - 0.5 * cospi(2.0 * (double)(m + half) / (double)F)) /
+                       (2.0 * (double)NFFT * (double)NC)
                  : 0.0;
 }
 
@@ -350,8 +353,8 @@ __device__ __forceinline__ bool fb_task(int b, int64_t f, int64_t nf, int64_t &f
 
 // grid (P / 4 + 1, n_filters): Z_r1 of filter f1 and Z_r2 of filter f2 (fb_task; filter
 // f = det * n_psd + e) from one complex transform.  Both inputs A_{P j + r} are real, so each Z
-// is Hermitian and C = IFFT(A_r1 + i A_r2) splits as Z_r1[n] = (C[n] + conj C[-n]) / 2,
-// Z_r2[n] = (C[n] - conj C[-n]) / 2i.
+// is Hermitian and C = IFFT(A_r1 + i A_r2) splits as 2 Z_r1[n] = C[n] + conj C[-n],
+// 2 Z_r2[n] = (C[n] - conj C[-n]) / i.  Z holds 2 Z_r (the 1/2 is in the taper table).
 template <int L>
 __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ psd, double fs, double f_hp,
                                                      const double2 *__restrict__ tw, double2 *__restrict__ Z) {
@@ -381,8 +384,8 @@ __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ 
     double2 *z1 = Z + (f1 * P + r1) * L, *z2 = Z + (f2 * P + (r2 >= 0 ? r2 : 0)) * L;
     for (int n = threadIdx.x; n < L; n += FB_T) {
         const double2 c = d[n], cm = d[(L - n) & (L - 1)];
-        z1[n] = make_double2(0.5 * (c.x + cm.x), 0.5 * (c.y - cm.y));
-        if (r2 >= 0) z2[n] = make_double2(0.5 * (c.y + cm.y), -0.5 * (c.x - cm.x));
+        z1[n] = make_double2(c.x + cm.x, c.y - cm.y);        // 2 Z_r1 (the 1/2 is in the taper table)
+        if (r2 >= 0) z2[n] = make_double2(c.y + cm.y, cm.x - c.x);  // 2 Z_r2
     }
 }
 
@@ -468,8 +471,8 @@ __global__ void __launch_bounds__(FB_T) k_fb_forward(const double2 *__restrict__
     __syncthreads();
     fb_fft<L>(d, tw, false);
     auto put = [&](float *out, int r, int k, double v) {
-        if (k <= NFFT / 2) out[k] = (float)(v / (double)NC);
-        else if (r != 0 && r != P / 2) out[NFFT - k] = (float)(v / (double)NC);
+        if (k <= NFFT / 2) out[k] = (float)v;  // G_k / NC (the 1 / NC is in the taper table)
+        else if (r != 0 && r != P / 2) out[NFFT - k] = (float)v;
     };
     float *out1 = gains + f1 * NBIN, *out2 = gains + f2 * NBIN;
     for (int j = threadIdx.x; j < L; j += FB_T) {
