@@ -221,8 +221,8 @@ def roofline_for(dom: dict, peaks: dict, step_ms_total: float) -> dict:
 
 
 def tune_tiles(ctx, stream, n_win: int = 1024):
-    """Autotune the conv tiles of a BF16 context (set-up, outside every timed region).
-    Returns a summary, or None where the network runs fused (no per-layer tiles)."""
+    """Autotune a BF16 context (set-up, outside every timed region): the conv tiles of a per-layer
+    network, or the launch knobs of a fused one.  Returns a summary, or None where nothing is tunable."""
     from paper_2403_18661_gb300 import abi
     try:
         ctx.autotune(n_win, stream=stream)
@@ -230,7 +230,12 @@ def tune_tiles(ctx, stream, n_win: int = 1024):
         if e.status == abi.AFG_ERR_UNSUPPORTED:
             return None
         raise
-    tiles = ctx.tiles()
+    try:
+        tiles = ctx.tiles()
+    except abi.AfgError as e:
+        if e.status != abi.AFG_ERR_UNSUPPORTED:
+            raise
+        return {"n_win": n_win, "fused_tuning": ctx.fused_tuning()}  # fused network: no per-layer tiles
     return {"n_win": n_win, "layers": len(tiles),
             "sum_us_default": round(sum(t["us_default"] for t in tiles), 1),
             "sum_us_chosen": round(sum(t["us_chosen"] for t in tiles), 1),
