@@ -154,6 +154,26 @@ def test_whiten_block_layouts(c1, fir_len, epoch_len, out_len):
             assert np.max(np.abs(got[d, lo:hi] - ref)) < WHITE_ATOL, (d, e)
 
 
+@pytest.mark.parametrize("n_psd", [3, 21])
+def test_whiten_one_detector_odd_filter_count(ctx_tiny, n_psd):
+    """An odd number of filters (one detector).  The filter build shares one transform between the
+    unpaired residue of two adjacent filters, so the last filter's stands alone.  3 filters take the
+    512-point sub-transforms, 21 the 2048-point ones.  Every epoch against the oracle's direct FIR
+    with the same PSD."""
+    step, span, out_first = 8192, 65536, 65536
+    out_len = n_psd * step
+    n = out_first + out_len + 4096
+    x = inputs.coloured_noise(n, 77, inputs.NoiseModel(), 2048).astype(np.float32)[None, :]
+    xd = _dev(x)
+    psd = ctx_tiny.psd_estimate(xd, n_psd=n_psd, psd_step=step, psd_span=span)
+    got = ctx_tiny.whiten(xd, psd, out_first, out_len, epoch_len=step).cpu().numpy()
+    p = psd.cpu().numpy()
+    for e in range(n_psd):
+        taps = orc.whitening_taps(p[0, e], 16384, 2048.0, 32.0, 2048)
+        ref = orc.fir(x[0].astype(np.float64), taps, out_first + e * step, step)
+        assert np.max(np.abs(got[0, e * step:(e + 1) * step] - ref)) < WHITE_ATOL, e
+
+
 def test_infer_windows_tiny_with_shift(c1, ctx_tiny):
     wl, x, w, ref = c1
     white = ref["white"].astype(np.float32)
