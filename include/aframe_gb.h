@@ -550,17 +550,20 @@ int afg_fused_tuning_set(afg_ctx *ctx, const afg_fused_tuning *in);
  * x: [n_det][n] float32 (device); psd: [n_det][n_psd][8193] float64 (device).
  *
  * Memory: the periodogram scratch (AFG_NOALLOC_MAX_PERIODOGRAMS x 8193
- * doubles, 4.2 MB) is a static __device__ array that every GPU which loads
- * the library holds until the process exits.
+ * doubles, 4.2 MB) and the FP32 transforms' twiddle table (60 KB) are static
+ * __device__ arrays that every GPU which loads the library holds until the
+ * process exits.
  * This call allocates and frees nothing.  It refuses with AFG_ERR_BUDGET
  * when n_det * ((n_psd-1)*psd_step/hop + (psd_span-nfft)/hop + 1) exceeds
  * AFG_NOALLOC_MAX_PERIODOGRAMS, and with AFG_ERR_ARG on the requirements of
  * afg_psd_estimate.  AFG_ERR_CUDA if a launch or the set-up fails.
  *
  * Set-up: the first call on each device (made with that device current)
- * resolves the array's device address and configures the kernel, both
- * synchronous runtime calls; make that first call before any stream
- * capture.  Later calls only launch kernels on `stream`.
+ * resolves the array's device address, fills the twiddle table (unless a
+ * context on that device already has: one small kernel on a stream of its
+ * own, waited for) and configures the kernel, all synchronous; make that
+ * first call before any stream capture.  Later calls only launch kernels on
+ * `stream`.
  *
  * Sharing: all calls on a device use the same scratch, which keeps the last
  * call's contents (every value a call reads is written earlier in that same

@@ -3,7 +3,8 @@
 // For callers that must not call cudaMalloc (see the header for who and
 // why): the periodogram scratch the Welch kernels need lives in a file-scope
 // __device__ array of fixed size that every GPU loading this library holds
-// until the process exits.  No call here allocates or frees device memory.
+// until the process exits, as does the transforms' twiddle table.  No call
+// here allocates or frees device memory.
 //
 // Host code must not use the array's name as a device address (on the host
 // it is a stand-in symbol); the address is looked up once per device with
@@ -29,8 +30,9 @@ DeviceState g_dev[kMaxDevices];
 std::mutex g_mu;
 
 // Once per device, with that device current: resolve the array's device
-// address and opt the periodogram kernel into its shared memory (both
-// synchronous runtime calls, so this must not run under stream capture).
+// address, fill the FP32 twiddle table if no context has, and opt the
+// periodogram kernel into its shared memory (all synchronous, so this must
+// not run under stream capture).
 int setup(int dev, DeviceState **out) {
     std::lock_guard<std::mutex> lock(g_mu);
     DeviceState &s = g_dev[dev];
