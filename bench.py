@@ -945,8 +945,9 @@ def run_whiten(args):
         cpu = oracle_whiten_sample(wl, x, n_epochs=128)
         cpu.pop("seconds")
     peaks = load_peaks()
-    hbm = [k for k in kstats if k["name"] in ("whiten_overlap_save", "welch_periodogram", "welch_mean")]
-    dom = max(hbm, key=lambda k: k["total_ms"])
+    # the dominant kernel of the step (the FP64 filter build, ALU-bound); the HBM-bound FP32 kernels carry
+    # their own rooflines in "kernels"
+    dom = max((k for k in kstats if k["launches"]), key=lambda k: k["total_ms"])
     per_kernel = {k["name"]: roofline_for(k, peaks, job_s * 1000.0) for k in kstats if k["launches"]}
     out = {"metric": "strain-seconds/s Welch+filter+whitening", "value": value, "unit": "strain-s/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": job_s * 1000.0 / args.steps,
