@@ -377,8 +377,22 @@ __global__ void __launch_bounds__(FB_T) k_fb_inverse(const double *__restrict__ 
         return (kk >= k_hp && b > 0 && b <= 0x7FF0000000000000LL) ? rsqrt(pk) : 0.0;
     };
     const double *p1 = psd + f1 * NBIN, *p2 = psd + f2 * NBIN;
-    for (int j = threadIdx.x; j < L; j += FB_T)
-        d[j] = make_double2(amp(p1, P * j + r1), r2 >= 0 ? amp(p2, P * j + r2) : 0.0);
+    if (blockIdx.x == 0) {
+        // residues 0 and P/2 are their own mirrors: A_{P j} = A_{P (L - j)}, A_{P j + P/2} = A_{P (L - 1 - j) + P/2};
+        // each amplitude is evaluated once and copied to its mirror
+        for (int j = threadIdx.x; j <= L / 2; j += FB_T) {
+            d[j].x = amp(p1, P * j);
+            if (j < L / 2) d[j].y = amp(p1, P * j + P / 2);
+        }
+        __syncthreads();
+        for (int j = L / 2 + threadIdx.x; j < L; j += FB_T) {
+            if (j > L / 2) d[j].x = d[L - j].x;
+            d[j].y = d[L - 1 - j].y;
+        }
+    } else {
+        for (int j = threadIdx.x; j < L; j += FB_T)
+            d[j] = make_double2(amp(p1, P * j + r1), r2 >= 0 ? amp(p2, P * j + r2) : 0.0);
+    }
     __syncthreads();
     fb_fft<L>(d, tw, true);
     double2 *z1 = Z + (f1 * P + r1) * L, *z2 = Z + (f2 * P + (r2 >= 0 ? r2 : 0)) * L;
@@ -415,7 +429,9 @@ __global__ void __launch_bounds__(FB_T) k_fb_taper(const double2 *__restrict__ Z
     const double g = fb_tap<P, L>(Z + f * P * L, m, tap, tw);
     double2 *y = Y + f * P * L + (m & (L - 1));
 #pragma unroll
-    for (int r = 0; r <= P / 2; ++r) {  // the residues the forward stage transforms
+    y[0] = make_double2(g, 0.0);  // residue 0: twiddle 1
+#pragma unroll
+    for (int r = 1; r <= P / 2; ++r) {  // the other residues the forward stage transforms
         const double2 w = tw[(r * m) & (NFFT - 1)];
         y[(int64_t)r * L] = make_double2(g * w.x, g * w.y);
     }
